@@ -1,0 +1,223 @@
+/*
+ * dcopf_dual.h -- C ABI of the GB300 Lagrange-dual DCOPF library (libdcopfdual.so).
+ *
+ * The library computes lower bounds on the cost of DC optimal power flow by
+ * projected gradient ascent on the Lagrange dual of
+ *
+ *     min  sum_j cost_j(p_j)
+ *     s.t. 1^T p - 1^T p_d = 0                        : lambda   (power balance)
+ *          f_min <= H_a (G p - p_d) <= f_max           : mu_lo, mu_hi >= 0
+ *          p_min <= p <= p_max
+ *
+ * ("GPU-Accelerated DCOPF using Gradient-Based Optimization", arXiv 2406.13191,
+ * Section 2 problem (1); PTDF H = Omega E (E^T Omega E)^{-1} with a zero slack
+ * column; cost_j(p) = a_j (S p)^2 + b_j S p, a_j = 0 for linear costs, S = base MVA).
+ * The dual function g(lambda, mu) = inf_p L(p, lambda, mu) (Section 3, eqs. (3)-(5))
+ * is evaluated in closed form: the inner minimiser is the box-clipped dispatch
+ * (eq. (6) via the dual norm for linear costs, eq. (16) for quadratic costs).
+ * Any lambda and any mu >= 0 give a valid lower bound (Remarks 1 and 2).
+ *
+ * Conventions shared by every entry point:
+ *  - Powers are in p.u. on base_mva; costs in $/h; multipliers in $/h per p.u.
+ *  - Batched arrays are row-major [batch][n]: instance b's row starts at b*n.
+ *  - Unless stated otherwise, array arguments of eval / solve_batch /
+ *    certify_bound are caller-owned DEVICE pointers on the handle's device; the
+ *    library never frees them.  They must not alias one another.
+ *  - All device work is enqueued on the caller's stream `stream` (a cudaStream_t
+ *    passed as void*; NULL = legacy default stream) and is asynchronous unless the
+ *    entry point says it synchronises.  Host-side validation errors return before
+ *    anything is enqueued.
+ *  - No C++ exception crosses this ABI.  Every entry point returns a dcopf_status.
+ *  - A handle may be used from one host thread at a time.
+ */
+#ifndef DCOPF_DUAL_H
+#define DCOPF_DUAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dcopf_dual* dcopf_dual_t; /* opaque; owned by the library */
+
+typedef enum {
+  DCOPF_OK = 0,
+  DCOPF_ERR_INVALID_ARG = 1, /* null pointer, size out of range, bad enum value, NaN */
+  DCOPF_ERR_NETWORK = 2,     /* islanded network, b <= 0, pmin > pmax, bridge outage */
+  DCOPF_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed */
+  DCOPF_ERR_OOM = 4,         /* device allocation failed */
+  DCOPF_ERR_TIMEOUT = 5,     /* a bounded device wait (grid barrier, mbarrier) gave up */
+  DCOPF_ERR_UNSUPPORTED = 6  /* size or option combination this build does not handle */
+} dcopf_status;
+
+/* Arithmetic of the operator products (adjoint Phi^T eta, forward Phi x).
+ * The dual value is always accumulated in FP64. */
+typedef enum {
+  DCOPF_FP64 = 0,  /* FP64 products on CUDA cores */
+  DCOPF_FP32 = 1,  /* FP32 products with FP32 accumulation on CUDA cores */
+  DCOPF_BF16X3 = 2 /* BF16 hi/lo split products on tcgen05 tensor cores, FP32 accumulation */
+} dcopf_precision;
+
+/* Ascent rule (Section 3.3). */
+typedef enum {
+  DCOPF_GDM = 0,    /* Algorithm 1 read as heavy-ball momentum */
+  DCOPF_ADAM = 1,   /* Adam, bias-corrected moments */
+  DCOPF_ADAGRAD = 2 /* AdaGrad */
+} dcopf_rule;
+
+/* Execution path of dcopf_dual_solve_batch. */
+typedef enum {
+  DCOPF_PATH_AUTO = 0,   /* fused persistent kernel for batch 1, batched kernels otherwise */
+  DCOPF_PATH_PLAIN = 1,  /* one launch per phase per iteration (the unfused baseline) */
+  DCOPF_PATH_FUSED = 2,  /* one persistent cooperative kernel per instance */
+  DCOPF_PATH_BATCHED = 3 /* batched contraction kernels replayed from a CUDA graph */
+} dcopf_path;
+
+/* Network description (Section 2, problem (1)).  Host pointers, copied by
+ * dcopf_dual_create; the caller may free them afterwards. */
+typedef struct {
+  int32_t n_bus, n_line, n_gen;
+  int32_t slack_bus;          /* 0-based; the zero column of H_a */
+  const int32_t* line_from;   /* [n_line] 0-based bus index */
+  const int32_t* line_to;     /* [n_line] */
+  const double* line_b;       /* [n_line] susceptance, p.u., > 0 */
+  const double* flow_max;     /* [n_line] upper flow limit, p.u. */
+  const double* flow_min;     /* [n_line] lower flow limit; NULL => -flow_max */
+  const int32_t* gen_bus;     /* [n_gen] 0-based bus of each generator */
+  const double* pmin;         /* [n_gen] p.u. */
+  const double* pmax;         /* [n_gen] p.u., >= pmin */
+  const double* cost_lin;     /* [n_gen] b_j, $/MWh */
+  const double* cost_quad;    /* [n_gen] a_j >= 0, $/MW^2h; NULL => linear costs */
+  double base_mva;            /* S, MVA (> 0) */
+} dcopf_network_desc;
+
+typedef struct {
+  int32_t device;    /* CUDA device ordinal; -1 = current device */
+  int32_t max_batch; /* largest batch the handle will see (workspaces sized lazily anyway) */
+  int32_t verbose;   /* 1 = print setup statistics to stderr */
+  int32_t reserved;
+} dcopf_options;
+
+/* Parameters of dcopf_dual_solve_batch.  Zero-initialise and set what you need;
+ * dcopf_solve_params_default fills the documented defaults. */
+typedef struct {
+  int32_t rule;        /* dcopf_rule */
+  int32_t precision;   /* dcopf_precision of the in-loop operator products */
+  int32_t path;        /* dcopf_path */
+  int32_t max_iters;   /* iteration cap per instance (> 0) */
+  int32_t warm_start;  /* 1 = start from lambda/mu given in the in/out arrays */
+  int32_t as_printed;  /* 1 = GDM applies Algorithm 1's printed extra gradient update */
+  int32_t check_every; /* certify a candidate at most every k iterations (>= 1) */
+  int32_t reserved;
+  double alpha;        /* step size for mu (and lambda unless alpha_lambda > 0) */
+  double alpha_lambda; /* step size for lambda; <= 0 => alpha */
+  double rho;          /* GDM momentum */
+  double beta1, beta2; /* Adam moments */
+  double eps;          /* Adam / AdaGrad denominator guard */
+  double decay;        /* step size multiplied by decay every iteration (1 = none) */
+  double gap;          /* stop when certified bound >= target - gap*|target| */
+  double tol;          /* > 0: also stop when |g_k - g_{k-1}| < tol (Algorithm 1 stop test) */
+  const double* target_value; /* DEVICE [batch] optimal costs to stop at; NULL => run max_iters
+                                 or until the tol test */
+} dcopf_solve_params;
+
+/* Library version string. */
+const char* dcopf_version(void);
+
+/* Human-readable text of a status code (static storage). */
+const char* dcopf_status_string(dcopf_status s);
+
+/* Fills p with the defaults: ADAM, FP32, PATH_AUTO, max_iters 5000, alpha 1000,
+ * rho 0.9, beta1 0.9, beta2 0.999, eps 1e-8, decay 1, gap 1e-3, check_every 1. */
+void dcopf_solve_params_default(dcopf_solve_params* p);
+
+/* Validates the network, factorises the reduced Laplacian E^T Omega E (FP64 sparse
+ * LDL^T, minimum-degree order, slack removed), builds Phi = H_a G (the PTDF at the
+ * generator buses, Section 2 below problem (1)) in FP64, normalises generator
+ * outputs to the unit box (Appendix A1), uploads everything to the device and
+ * returns a handle in *out.  Synchronises the device.  Errors: INVALID_ARG (null
+ * pointers, sizes < 1, NaN/Inf, bad slack index), NETWORK (islanded network, b <= 0,
+ * pmin > pmax, flow_min > flow_max), OOM, CUDA. */
+dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_options* opt,
+                               dcopf_dual_t* out);
+
+/* Frees the handle and all device memory it owns.  NULL is accepted. */
+dcopf_status dcopf_dual_destroy(dcopf_dual_t h);
+
+/* Network sizes and flags of a handle (host pointers; NULL outputs are skipped).
+ * bridge_mask: host array [n_line] receiving 1 for lines whose outage islands the
+ * network (such outages are rejected by every entry point). */
+dcopf_status dcopf_dual_info(dcopf_dual_t h, int32_t* n_bus, int32_t* n_line, int32_t* n_gen,
+                             int32_t* is_qp, uint8_t* bridge_mask);
+
+/* One evaluation of the dual function and its supergradient at given multipliers
+ * (Section 3.1 eq. (6) / Section 3.2 eq. (16) in closed form; gradient as in
+ * Algorithm 1's gradient lines, read as the primal residuals).
+ *   loads    [batch][n_bus]  p_d of each instance
+ *   outage   [batch] or NULL line index removed from instance b (-1 = none); the
+ *            outaged line's multipliers are ignored and its gradient is 0
+ *   lambda   [batch]; mu_hi, mu_lo [batch][n_line], used as given (negative mu are
+ *            allowed: the dual function is defined for them, they just do not bound)
+ *   precision dcopf_precision of the operator products
+ * Outputs (NULL = skip, except value):
+ *   value    [batch]  g(lambda, mu) = sum_j cost_j(p*) + lambda (1^T p* - 1^T p_d)
+ *                     + mu_hi^T (f - f_max) + mu_lo^T (f_min - f), FP64 accumulation
+ *   g_lambda [batch]  1^T p* - 1^T p_d
+ *   g_mu_hi, g_mu_lo [batch][n_line]  f - f_max, f_min - f
+ *   dispatch [batch][n_gen]  the minimiser p* (ties take the box midpoint)
+ * Errors: INVALID_ARG, NETWORK (bridge outage), UNSUPPORTED, OOM, CUDA. */
+dcopf_status dcopf_dual_eval(dcopf_dual_t h, int32_t batch, const double* loads,
+                             const int32_t* outage, const double* lambda, const double* mu_hi,
+                             const double* mu_lo, int32_t precision, double* value,
+                             double* g_lambda, double* g_mu_hi, double* g_mu_lo,
+                             double* dispatch, void* stream);
+
+/* Certified FP64 lower bound at given multipliers (Remarks 1 and 2): mu is first
+ * projected to mu >= 0, the bus prices nu = lambda + H_a^T (mu_hi - mu_lo) are
+ * computed in FP64 by sparse triangular solves, and
+ *   bound = sum_j min_p [cost_j(p) + nu_bus(j) p] - nu^T p_d - mu_hi^T f_max + mu_lo^T f_min
+ * is accumulated in FP64 (eq. (4) evaluated through the bus prices).  err_bound
+ * receives an upper bound on the rounding error of that final accumulation; the
+ * reported bound already has it subtracted.
+ *   loads [batch][n_bus]; outage [batch] or NULL; lambda [batch]; mu_hi, mu_lo
+ *   [batch][n_line]; bound [batch] (required); err_bound [batch] (NULL = skip). */
+dcopf_status dcopf_dual_certify_bound(dcopf_dual_t h, int32_t batch, const double* loads,
+                                      const int32_t* outage, const double* lambda,
+                                      const double* mu_hi, const double* mu_lo, double* bound,
+                                      double* err_bound, void* stream);
+
+/* Projected gradient ascent on the dual for a batch of instances of one network
+ * (Section 3.3, Algorithm 1 and the Adam / AdaGrad rules), from the cold start
+ * lambda = mu = 0 (Algorithm 1, Require) or from the given warm start.
+ *   loads [batch][n_bus]; outage [batch] or NULL
+ *   lambda [batch], mu_hi, mu_lo [batch][n_line]: in = warm start (if
+ *     params->warm_start), out = the best iterate found (largest certified bound)
+ *   best_bound [batch]: certified FP64 bound at that iterate (dcopf_dual_certify_bound)
+ *   iters [batch]: iterations taken; inst_status [batch]: 0 = reached target,
+ *     1 = stopped at max_iters or by the tol test, 2 = dual unbounded (infeasible
+ *     primal suspected: the bound exceeded the cost of any dispatch)
+ * Stopping: when target_value is given, an instance stops once its certified bound
+ * is >= target - gap*|target|; candidates are certified when the in-loop value
+ * (reduced precision) first reaches the target.  All output arrays are device
+ * pointers.  The call enqueues its work on `stream` and synchronises that stream
+ * before returning (the iteration count is data dependent).
+ * Errors: INVALID_ARG, NETWORK, UNSUPPORTED, OOM, CUDA, TIMEOUT. */
+dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double* loads,
+                                    const int32_t* outage, const dcopf_solve_params* params,
+                                    double* lambda, double* mu_hi, double* mu_lo,
+                                    double* best_bound, int32_t* iters, int32_t* inst_status,
+                                    void* stream);
+
+/* Number of kernels this handle has launched since creation (for launch accounting). */
+int64_t dcopf_dual_kernel_launches(dcopf_dual_t h);
+
+/* Sticky device-side error word of the handle's last solve (0 = none, else a
+ * dcopf_status value such as DCOPF_ERR_TIMEOUT).  Synchronises the device. */
+dcopf_status dcopf_dual_device_error(dcopf_dual_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DCOPF_DUAL_H */

@@ -41,9 +41,10 @@ def _GT_mul(phi, v, nl, ng):
 def ipm(net: Net, loads, max_iter=200, tol=1e-12, feas_tol=1e-9, verbose=False):
     """Solve min 1/2 p^T Q p + q^T p s.t. 1^T p = D, G p <= h (problem (1)).
 
-    Returns dict(status, p, lam, mu_hi, mu_lo, ub, lb, rel_gap, iters).  ``status`` is
-    "optimal" when the sandwich (ub - lb)/|ub| <= 1e-9 holds, "infeasible" when the
-    iteration diverges, else "failed".
+    Returns dict(status, p, lam, mu_hi, mu_lo, ub, lb, rel_gap, iters) for the iterate
+    with the tightest sandwich.  ``status`` is "optimal" when the sandwich
+    (ub - lb)/|ub| <= 1e-9 holds with a primal point feasible to ``feas_tol``,
+    "infeasible" when the iteration diverges, else "failed".
     """
     loads = np.asarray(loads, dtype=np.float64)
     phi, fd, h, qd, q, D = _problem(net, loads)
@@ -59,6 +60,20 @@ def ipm(net: Net, loads, max_iter=200, tol=1e-12, feas_tol=1e-9, verbose=False):
     z = np.full(m, zscale)
     status = "failed"
     it = 0
+    best = None                    # (rel_gap, p, y, z) of the tightest feasible sandwich seen
+
+    def sandwich(p, y, z):
+        mh = np.maximum(z[:nl], 0.0)
+        ml = np.maximum(z[nl:2 * nl], 0.0)
+        f = phi @ p - fd
+        viol = max(0.0, float(np.max(f - net.fmax, initial=0.0)),
+                   float(np.max(net.fmin - f, initial=0.0)),
+                   float(np.max(p - net.pmax, initial=0.0)),
+                   float(np.max(net.pmin - p, initial=0.0)), abs(p.sum() - D))
+        ub = net.cost(p)
+        lb = dual_value_prices(net, loads, y, mh, ml)
+        return (ub - lb) / max(1.0, abs(ub)), viol, ub, lb
+
     for it in range(1, max_iter + 1):
         rd = qd * p + q + y * np.ones(ng) + _GT_mul(phi, z, nl, ng)
         rp = p.sum() - D
@@ -68,6 +83,16 @@ def ipm(net: Net, loads, max_iter=200, tol=1e-12, feas_tol=1e-9, verbose=False):
         nrm_p = (abs(rp) + np.linalg.norm(ri)) / (1.0 + np.linalg.norm(h) + abs(D))
         if verbose:
             print(it, nrm_d, nrm_p, mu)
+        if not (np.all(np.isfinite(p)) and np.all(np.isfinite(z)) and np.isfinite(y)):
+            status = "stalled"
+            break
+        if it >= 3:
+            rel, viol, _, _ = sandwich(p, y, z)
+            if viol <= feas_tol and (best is None or rel < best[0]):
+                best = (rel, p.copy(), y, z.copy())
+            if best is not None and best[0] <= 1e-12:
+                status = "converged"
+                break
         if nrm_d < tol and nrm_p < tol and mu < tol * (1.0 + abs(float(np.dot(q, p)))) / m:
             status = "converged"
             break
@@ -80,8 +105,11 @@ def ipm(net: Net, loads, max_iter=200, tol=1e-12, feas_tol=1e-9, verbose=False):
         try:
             Lc = np.linalg.cholesky(K)
         except np.linalg.LinAlgError:
-            status = "stalled"          # numerically converged as far as FP64 allows
-            break
+            try:                        # regularise once; FP64 has run out of digits
+                Lc = np.linalg.cholesky(K + np.eye(ng) * (1e-12 * np.trace(K) / ng))
+            except np.linalg.LinAlgError:
+                status = "stalled"
+                break
 
         def ksolve(r):
             return np.linalg.solve(Lc.T, np.linalg.solve(Lc, r))
@@ -115,15 +143,11 @@ def ipm(net: Net, loads, max_iter=200, tol=1e-12, feas_tol=1e-9, verbose=False):
         y = y + a * dy
         s = s + a * ds
         z = z + a * dz
+    if status != "infeasible" and best is not None:
+        _, p, y, z = best
     mu_hi = np.maximum(z[:nl], 0.0)
     mu_lo = np.maximum(z[nl:2 * nl], 0.0)
-    f = phi @ p - fd
-    viol = max(0.0, float(np.max(f - net.fmax, initial=0.0)), float(np.max(net.fmin - f, initial=0.0)),
-               float(np.max(p - net.pmax, initial=0.0)), float(np.max(net.pmin - p, initial=0.0)),
-               abs(p.sum() - D))
-    ub = net.cost(p)
-    lb = dual_value_prices(net, loads, y, mu_hi, mu_lo)
-    rel = (ub - lb) / max(1.0, abs(ub))
+    rel, viol, ub, lb = sandwich(p, y, z)
     if status != "infeasible":
         status = "optimal" if (rel <= 1e-9 and viol <= feas_tol) else "failed"
     return dict(status=status, p=p, lam=float(y), mu_hi=mu_hi, mu_lo=mu_lo, ub=ub, lb=lb,

@@ -1,0 +1,94 @@
+"""ctypes view of include/dcopf_dual.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdcopfdual.so")
+
+# The exported C symbols, in the order include/dcopf_dual.h declares them.
+EXPORTS = ("dcopf_version", "dcopf_status_string", "dcopf_solve_params_default",
+           "dcopf_dual_create", "dcopf_dual_destroy", "dcopf_dual_info", "dcopf_dual_eval",
+           "dcopf_dual_certify_bound", "dcopf_dual_solve_batch", "dcopf_dual_kernel_launches",
+           "dcopf_dual_device_error")
+
+STATUS = {0: "DCOPF_OK", 1: "DCOPF_ERR_INVALID_ARG", 2: "DCOPF_ERR_NETWORK", 3: "DCOPF_ERR_CUDA",
+          4: "DCOPF_ERR_OOM", 5: "DCOPF_ERR_TIMEOUT", 6: "DCOPF_ERR_UNSUPPORTED"}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16x3": 2}
+RULE = {"gdm": 0, "adam": 1, "adagrad": 2}
+PATH = {"auto": 0, "plain": 1, "fused": 2, "batched": 3}
+
+P = C.c_void_p
+I32P = C.POINTER(C.c_int32)
+F64P = C.POINTER(C.c_double)
+
+
+class NetworkDesc(C.Structure):
+    _fields_ = [("n_bus", C.c_int32), ("n_line", C.c_int32), ("n_gen", C.c_int32),
+                ("slack_bus", C.c_int32), ("line_from", I32P), ("line_to", I32P),
+                ("line_b", F64P), ("flow_max", F64P), ("flow_min", F64P), ("gen_bus", I32P),
+                ("pmin", F64P), ("pmax", F64P), ("cost_lin", F64P), ("cost_quad", F64P),
+                ("base_mva", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("device", C.c_int32), ("max_batch", C.c_int32), ("verbose", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("rule", C.c_int32), ("precision", C.c_int32), ("path", C.c_int32),
+                ("max_iters", C.c_int32), ("warm_start", C.c_int32), ("as_printed", C.c_int32),
+                ("check_every", C.c_int32), ("reserved", C.c_int32), ("alpha", C.c_double),
+                ("alpha_lambda", C.c_double), ("rho", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double), ("decay", C.c_double),
+                ("gap", C.c_double), ("tol", C.c_double), ("target_value", P)]
+
+
+class DcopfError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Loads libdcopfdual.so (building it with nvcc if it is missing or stale).  Raises if the
+    native library cannot be loaded: there is no fallback implementation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and os.path.isdir(os.path.join(HERE, "csrc")):
+        from . import build as _build
+        _build.build()          # no-op when the library is newer than its sources
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"native library missing: {LIB_PATH}")
+    lib = C.CDLL(LIB_PATH)
+    lib.dcopf_version.restype = C.c_char_p
+    lib.dcopf_status_string.restype = C.c_char_p
+    lib.dcopf_status_string.argtypes = [C.c_int]
+    lib.dcopf_solve_params_default.argtypes = [C.POINTER(SolveParams)]
+    lib.dcopf_solve_params_default.restype = None
+    lib.dcopf_dual_create.argtypes = [C.POINTER(NetworkDesc), C.POINTER(Options), C.POINTER(P)]
+    lib.dcopf_dual_destroy.argtypes = [P]
+    lib.dcopf_dual_info.argtypes = [P, I32P, I32P, I32P, I32P, C.POINTER(C.c_uint8)]
+    lib.dcopf_dual_eval.argtypes = [P, C.c_int32, P, P, P, P, P, C.c_int32, P, P, P, P, P, P]
+    lib.dcopf_dual_certify_bound.argtypes = [P, C.c_int32, P, P, P, P, P, P, P, P]
+    lib.dcopf_dual_solve_batch.argtypes = [P, C.c_int32, P, P, C.POINTER(SolveParams), P, P, P, P,
+                                           P, P, P]
+    lib.dcopf_dual_kernel_launches.argtypes = [P]
+    lib.dcopf_dual_kernel_launches.restype = C.c_int64
+    lib.dcopf_dual_device_error.argtypes = [P]
+    for name in ("dcopf_dual_create", "dcopf_dual_destroy", "dcopf_dual_info", "dcopf_dual_eval",
+                 "dcopf_dual_certify_bound", "dcopf_dual_solve_batch", "dcopf_dual_device_error"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def check(code: int, where: str) -> None:
+    if code != 0:
+        raise DcopfError(code, where)

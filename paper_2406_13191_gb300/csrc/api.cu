@@ -1,0 +1,498 @@
+// C ABI of libdcopfdual.so: argument validation, handle and workspace management,
+// and the solve driver that alternates device iterations with FP64 certification.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+
+#include "dcopf_dual.h"
+#include "kernels.h"
+
+using namespace dcopf;
+
+dcopf_dual::~dcopf_dual() {
+  for (auto* b : owned) delete b;
+  if (d_err) cudaFree(d_err);
+  if (d_bar) cudaFree(d_bar);
+}
+
+namespace dcopf {
+
+namespace {
+
+#define CUDA_TRY(h, x)                                               \
+  do {                                                               \
+    cudaError_t e_ = (x);                                            \
+    if (e_ != cudaSuccess) {                                         \
+      (h)->last_error = cudaGetErrorString(e_);                      \
+      return e_ == cudaErrorMemoryAllocation ? DCOPF_ERR_OOM : DCOPF_ERR_CUDA; \
+    }                                                                \
+  } while (0)
+
+template <typename T>
+dcopf_status upload(dcopf_dual* h, const std::vector<T>& v, const T** out) {
+  auto* b = new DBuf();
+  h->owned.push_back(b);
+  CUDA_TRY(h, b->alloc(v.size() * sizeof(T)));
+  if (!v.empty()) CUDA_TRY(h, cudaMemcpy(b->p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = (const T*)b->p;
+  return DCOPF_OK;
+}
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+dcopf_status ensure_workspace(dcopf_dual* h, int B) {
+  Workspace& w = h->ws;
+  if (B <= w.cap) return DCOPF_OK;
+  const size_t nl = h->dev.n_line, ng = h->dev.n_gen;
+  const size_t bl = (size_t)B * nl, bg = (size_t)B * ng;
+  CUDA_TRY(h, w.f0.alloc(bl * 8));
+  CUDA_TRY(h, w.f0_32.alloc(bl * 4));
+  CUDA_TRY(h, w.u64.alloc(bl * 8));
+  CUDA_TRY(h, w.u32.alloc(bl * 4));
+  CUDA_TRY(h, w.demand.alloc((size_t)B * 8));
+  CUDA_TRY(h, w.eta64.alloc(bl * 8));
+  CUDA_TRY(h, w.eta32.alloc(bl * 4));
+  CUDA_TRY(h, w.pit64.alloc(bg * 8));
+  CUDA_TRY(h, w.pit32.alloc(bg * 4));
+  CUDA_TRY(h, w.x64.alloc(bg * 8));
+  CUDA_TRY(h, w.x32.alloc(bg * 4));
+  CUDA_TRY(h, w.f.alloc(bl * 8));
+  CUDA_TRY(h, w.sumcost.alloc((size_t)B * 8));
+  CUDA_TRY(h, w.sump.alloc((size_t)B * 8));
+  CUDA_TRY(h, w.value.alloc((size_t)B * 8));
+  CUDA_TRY(h, w.glam.alloc((size_t)B * 8));
+  CUDA_TRY(h, w.ghi.alloc(bl * 8));
+  CUDA_TRY(h, w.glo.alloc(bl * 8));
+  w.cap = B;
+  return DCOPF_OK;
+}
+
+template <typename S>
+dcopf_status ensure_state(dcopf_dual* h, int B, SolveState<S>* st) {
+  StateBufs& sb = sizeof(S) == 8 ? h->st64 : h->st32;
+  const size_t nl = h->dev.n_line;
+  if (B > sb.cap) {
+    CUDA_TRY(h, sb.ints.alloc((size_t)B * 6 * sizeof(int)));
+    CUDA_TRY(h, sb.dbls.alloc((size_t)B * 12 * sizeof(double)));
+    CUDA_TRY(h, sb.mus.alloc((size_t)B * nl * 8 * sizeof(S)));
+    sb.cap = B;
+  }
+  int* I = sb.ints.as<int>();
+  st->done = I; st->cand = I + B; st->iter = I + 2 * B; st->best_iter = I + 3 * B;
+  st->status = I + 4 * B;
+  double* D = sb.dbls.as<double>();
+  st->best = D; st->best_next = D + B; st->best_lam = D + 2 * B; st->thresh = D + 3 * B;
+  st->margin = D + 4 * B; st->prev = D + 5 * B; st->prev2 = D + 6 * B; st->lam = D + 7 * B;
+  st->lam_s1 = D + 8 * B; st->lam_s2 = D + 9 * B; st->cert = D + 10 * B;
+  S* M = sb.mus.as<S>();
+  const size_t bl = (size_t)B * nl;
+  st->mu_hi = M; st->mu_lo = M + bl; st->s1_hi = M + 2 * bl; st->s2_hi = M + 3 * bl;
+  st->s1_lo = M + 4 * bl; st->s2_lo = M + 5 * bl; st->best_hi = M + 6 * bl; st->best_lo = M + 7 * bl;
+  return DCOPF_OK;
+}
+
+template dcopf_status ensure_state<float>(dcopf_dual*, int, SolveState<float>*);
+template dcopf_status ensure_state<double>(dcopf_dual*, int, SolveState<double>*);
+
+// ---------------------------------------------------------------- solver bookkeeping kernels
+template <typename S>
+__global__ void k_init_state(int B, int nl, int warm, const double* __restrict__ lam_in,
+                             const double* __restrict__ mh_in, const double* __restrict__ ml_in,
+                             const double* __restrict__ target, double gap, SolveState<S> st) {
+  const size_t n = (size_t)B * nl;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    S h = warm ? (S)fmax(mh_in[q], 0.0) : S(0);
+    S l = warm ? (S)fmax(ml_in[q], 0.0) : S(0);
+    st.mu_hi[q] = h; st.mu_lo[q] = l;
+    st.best_hi[q] = h; st.best_lo[q] = l;
+    st.s1_hi[q] = S(0); st.s2_hi[q] = S(0); st.s1_lo[q] = S(0); st.s2_lo[q] = S(0);
+  }
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    double lam = warm ? lam_in[b] : 0.0;
+    st.lam[b] = lam; st.best_lam[b] = lam; st.lam_s1[b] = 0.0; st.lam_s2[b] = 0.0;
+    st.best[b] = -INFINITY; st.best_next[b] = -INFINITY;
+    st.iter[b] = 0; st.best_iter[b] = 0; st.done[b] = 0; st.cand[b] = 0; st.status[b] = 1;
+    st.thresh[b] = target ? target[b] - gap * fabs(target[b]) : INFINITY;
+    st.margin[b] = 0.0; st.prev[b] = 0.0; st.prev2[b] = 0.0; st.cert[b] = -INFINITY;
+  }
+}
+
+// After certification of the candidates: accept (certified bound reaches the
+// threshold), stop (cap / tol), or raise the in-loop margin and continue.
+__global__ void k_accept(int B, double ub_any, SolveStateBase st, int* active) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  if (!st.done[b] && st.cand[b]) {
+    double c = st.cert[b];
+    if (st.cand[b] == 1) {
+      if (c >= st.thresh[b]) {
+        st.done[b] = 1;
+        st.status[b] = 0;
+      } else {
+        double short_by = st.thresh[b] - c;
+        st.margin[b] += fmax(short_by, 1e-7 * fabs(st.thresh[b]));
+        st.cand[b] = 0;
+      }
+    } else {
+      st.done[b] = 1;
+      st.status[b] = (c >= st.thresh[b]) ? 0 : 1;
+    }
+    if (c > ub_any) { st.done[b] = 1; st.status[b] = 2; }
+  }
+  if (!st.done[b]) atomicAdd(active, 1);
+}
+
+template <typename S>
+__global__ void k_output(int B, int nl, SolveState<S> st, double* __restrict__ lam,
+                         double* __restrict__ mh, double* __restrict__ ml, double* __restrict__ bound,
+                         int* __restrict__ iters, int* __restrict__ status) {
+  const size_t n = (size_t)B * nl;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    mh[q] = (double)st.best_hi[q];
+    ml[q] = (double)st.best_lo[q];
+  }
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    lam[b] = st.best_lam[b];
+    if (bound) bound[b] = st.cert[b];
+    if (iters) iters[b] = st.iter[b];
+    if (status) status[b] = st.status[b];
+  }
+}
+
+template <typename S>
+dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* outage,
+                        const dcopf_solve_params& p, int path, double* lam, double* mh, double* ml,
+                        double* bound, int* iters, int* status, cudaStream_t s) {
+  SolveState<S> st{};
+  dcopf_status r = ensure_state<S>(h, B, &st);
+  if (r) return r;
+  const int nl = h->dev.n_line;
+  st.has_target = p.target_value != nullptr;
+  unsigned g = std::min<unsigned>(cdiv((long long)B * nl, 256), 4096);
+  k_init_state<S><<<g, 256, 0, s>>>(B, nl, p.warm_start, lam, mh, ml, p.target_value, p.gap, st);
+  h->launches += 1;
+  StepArgs P{};
+  P.rule = p.rule;
+  P.as_printed = p.as_printed;
+  P.alpha = p.alpha;
+  P.alpha_lambda = p.alpha_lambda > 0 ? p.alpha_lambda : p.alpha;
+  P.rho = p.rho;
+  P.beta1 = p.beta1;
+  P.beta2 = p.beta2;
+  P.eps = p.eps;
+  P.decay = p.decay;
+  CUDA_TRY(h, h->active.alloc(16));
+  int* d_active = h->active.as<int>();
+  const int chunk = std::max(1, p.check_every);
+  const double ub_any = h->ub_any;
+  for (int round = 0;; ++round) {
+    if constexpr (sizeof(S) == 4) {
+      if (path == DCOPF_PATH_FUSED) r = run_iters_fused(h, P, st, p.max_iters, p.tol, s);
+    }
+    if (path != DCOPF_PATH_FUSED) {
+      int prec = path == DCOPF_PATH_PLAIN ? DCOPF_FP64 : p.precision;
+      r = run_iters_unfused<S>(h, B, outage, prec, P, st, chunk, p.max_iters, p.tol, s);
+    }
+    if (r) return r;
+    r = run_certify_t<S>(h, B, loads, outage, st.best_lam, st.best_hi, st.best_lo, st.cert, nullptr,
+                         st.cand, st.done, s);
+    if (r) return r;
+    CUDA_TRY(h, cudaMemsetAsync(d_active, 0, sizeof(int), s));
+    k_accept<<<cdiv(B, 128), 128, 0, s>>>(B, ub_any, st, d_active);
+    h->launches += 1;
+    int active = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&active, d_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    int derr = 0;
+    CUDA_TRY(h, cudaMemcpy(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (derr) return (dcopf_status)derr;
+    if (active == 0) break;
+    if (round > 4 * (p.max_iters / chunk + 2) + 64) break;  // cannot happen unless stuck
+  }
+  k_output<S><<<std::min<unsigned>(cdiv((long long)B * nl, 256), 4096), 256, 0, s>>>(
+      B, nl, st, lam, mh, ml, bound, iters, status);
+  h->launches += 1;
+  CUDA_TRY(h, cudaGetLastError());
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  return DCOPF_OK;
+}
+
+}  // namespace dcopf
+
+// ==================================================================== C ABI
+extern "C" {
+
+const char* dcopf_version(void) { return "dcopfdual 0.1 (sm_103a)"; }
+
+const char* dcopf_status_string(dcopf_status s) {
+  switch (s) {
+    case DCOPF_OK: return "ok";
+    case DCOPF_ERR_INVALID_ARG: return "invalid argument";
+    case DCOPF_ERR_NETWORK: return "invalid network (islanded, b <= 0, pmin > pmax or bridge outage)";
+    case DCOPF_ERR_CUDA: return "CUDA error";
+    case DCOPF_ERR_OOM: return "out of device memory";
+    case DCOPF_ERR_TIMEOUT: return "bounded device wait timed out";
+    case DCOPF_ERR_UNSUPPORTED: return "unsupported size or option";
+  }
+  return "unknown status";
+}
+
+void dcopf_solve_params_default(dcopf_solve_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->rule = DCOPF_ADAM;
+  p->precision = DCOPF_FP32;
+  p->path = DCOPF_PATH_AUTO;
+  p->max_iters = 5000;
+  p->check_every = 1;
+  p->alpha = 1000.0;
+  p->alpha_lambda = 0.0;
+  p->rho = 0.9;
+  p->beta1 = 0.9;
+  p->beta2 = 0.999;
+  p->eps = 1e-8;
+  p->decay = 1.0;
+  p->gap = 1e-3;
+  p->tol = 0.0;
+  p->target_value = nullptr;
+}
+
+dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_options* opt,
+                               dcopf_dual_t* out) {
+  if (!out) return DCOPF_ERR_INVALID_ARG;
+  *out = nullptr;
+  // host-side validation and setup first: invalid networks are rejected without
+  // touching the GPU
+  dcopf_dual* h = new dcopf_dual();
+  h->verbose = opt && opt->verbose;
+  std::string err;
+  dcopf_status st = build_host_net(net, &h->host, &err, h->verbose);
+  if (st != DCOPF_OK) {
+    if (h->verbose) fprintf(stderr, "[dcopf] create: %s\n", err.c_str());
+    delete h;
+    return st;
+  }
+  int dev = opt && opt->device >= 0 ? opt->device : -1;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1 ||
+      (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) || dev >= ndev) {
+    delete h;
+    return DCOPF_ERR_CUDA;
+  }
+  DeviceGuard guard(dev);
+  h->device = dev;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) { delete h; return DCOPF_ERR_CUDA; }
+  h->sm_count = prop.multiProcessorCount;
+  h->smem_optin = prop.sharedMemPerBlockOptin;
+  const HostNet& H = h->host;
+  DevNet& D = h->dev;
+  D.n_bus = H.n_bus; D.n_line = H.n_line; D.n_gen = H.n_gen; D.slack = H.slack; D.qp = H.qp;
+  D.S = H.S;
+  D.nr = H.F.n;
+  D.n_fwd_lev = (int)H.F.fwd_level_ptr.size() - 1;
+  D.n_bwd_lev = (int)H.F.bwd_level_ptr.size() - 1;
+  const int nl = H.n_line, ng = H.n_gen;
+  std::vector<float> fmax32(H.fmax.begin(), H.fmax.end()), fmin32(H.fmin.begin(), H.fmin.end());
+  std::vector<float> sig32(H.sigma.begin(), H.sigma.end()), ctil32(H.ctil.begin(), H.ctil.end()),
+      mq32(H.mq.begin(), H.mq.end());
+  std::vector<double> phit((size_t)nl * ng);
+  std::vector<float> phi32((size_t)nl * ng), phit32((size_t)nl * ng);
+  for (int i = 0; i < nl; ++i)
+    for (int j = 0; j < ng; ++j) {
+      double v = H.phi[(size_t)i * ng + j];
+      phit[(size_t)j * nl + i] = v;
+      phi32[(size_t)i * ng + j] = (float)v;
+      phit32[(size_t)j * nl + i] = (float)v;
+    }
+#define UP(vec, field) \
+  if ((st = upload(h, vec, &D.field)) != DCOPF_OK) { delete h; return st; }
+  UP(H.F.pos_of_bus, pos_of_bus) UP(H.F.bus_of_pos, bus_of_pos)
+  UP(H.F.lrow_ptr, lrow_ptr) UP(H.F.lrow_col, lrow_col) UP(H.F.lrow_val, lrow_val)
+  UP(H.F.lcol_ptr, lcol_ptr) UP(H.F.lcol_row, lcol_row) UP(H.F.lcol_val, lcol_val)
+  UP(H.F.diag, diag) UP(H.F.fwd_rows, fwd_rows) UP(H.F.fwd_level_ptr, fwd_lev)
+  UP(H.F.bwd_rows, bwd_rows) UP(H.F.bwd_level_ptr, bwd_lev)
+  UP(H.line_from, line_from) UP(H.line_to, line_to) UP(H.b, line_b) UP(H.fmax, fmax)
+  UP(H.fmin, fmin) UP(fmax32, fmax32) UP(fmin32, fmin32) UP(H.phim, phim)
+  UP(H.bus_line_ptr, bus_line_ptr) UP(H.bus_line_idx, bus_line_idx)
+  UP(H.bus_line_coef, bus_line_coef) UP(H.gen_bus, gen_bus) UP(H.pmin, pmin) UP(H.pmax, pmax)
+  UP(H.cost_lin, cost_lin) UP(H.cost_quad, cost_quad) UP(H.sigma, sigma) UP(H.mid, mid)
+  UP(H.ctil, ctil) UP(H.mq, mq) UP(H.cconst, cconst) UP(sig32, sigma32) UP(ctil32, ctil32)
+  UP(mq32, mq32) UP(H.phi, phi64) UP(phit, phit64) UP(phi32, phi32) UP(phit32, phit32)
+#undef UP
+  if (cudaMalloc(&h->d_err, 16) != cudaSuccess || cudaMalloc(&h->d_bar, 64) != cudaSuccess ||
+      cudaMemset(h->d_err, 0, 16) != cudaSuccess || cudaMemset(h->d_bar, 0, 64) != cudaSuccess) {
+    delete h;
+    return DCOPF_ERR_CUDA;
+  }
+  // an upper bound on the cost of any dispatch: a dual bound above it proves the
+  // primal infeasible (Remarks 1-2 with weak duality)
+  double ub = 0.0;
+  for (int j = 0; j < ng; ++j) {
+    auto cost = [&](double pp) {
+      double sp = H.S * pp;
+      return H.cost_quad[j] * sp * sp + H.cost_lin[j] * sp;
+    };
+    ub += std::max(cost(H.pmin[j]), cost(H.pmax[j]));
+  }
+  h->ub_any = ub + 1e-9 * std::fabs(ub) + 1e-9;
+  if (cudaDeviceSynchronize() != cudaSuccess) { delete h; return DCOPF_ERR_CUDA; }
+  *out = h;
+  return DCOPF_OK;
+}
+
+dcopf_status dcopf_dual_destroy(dcopf_dual_t h) {
+  if (!h) return DCOPF_OK;
+  DeviceGuard guard(h->device);
+  cudaDeviceSynchronize();
+  delete h;
+  return DCOPF_OK;
+}
+
+dcopf_status dcopf_dual_info(dcopf_dual_t h, int32_t* n_bus, int32_t* n_line, int32_t* n_gen,
+                             int32_t* is_qp, uint8_t* bridge_mask) {
+  if (!h) return DCOPF_ERR_INVALID_ARG;
+  if (n_bus) *n_bus = h->host.n_bus;
+  if (n_line) *n_line = h->host.n_line;
+  if (n_gen) *n_gen = h->host.n_gen;
+  if (is_qp) *is_qp = h->host.qp ? 1 : 0;
+  if (bridge_mask) memcpy(bridge_mask, h->host.bridge.data(), h->host.bridge.size());
+  return DCOPF_OK;
+}
+
+static dcopf_status check_batch(dcopf_dual_t h, int32_t batch, const double* loads) {
+  if (!h || batch < 1 || !loads) return DCOPF_ERR_INVALID_ARG;
+  if ((long long)batch * h->host.n_line > (1ll << 31)) return DCOPF_ERR_UNSUPPORTED;
+  if (certify_smem(h, true) > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
+  return DCOPF_OK;
+}
+
+// Outage indices arrive in device memory; they are copied back and checked on the
+// host (range and bridges) before any kernel indexes arrays with them.
+static dcopf_status check_outage(dcopf_dual_t h, int32_t batch, const int32_t* outage,
+                                 cudaStream_t s) {
+  if (!outage) return DCOPF_OK;
+  std::vector<int32_t> o(batch);
+  if (cudaMemcpyAsync(o.data(), outage, sizeof(int32_t) * batch, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DCOPF_ERR_INVALID_ARG;  // not a readable device pointer
+  for (int32_t k : o) {
+    if (k < -1 || k >= h->host.n_line) return DCOPF_ERR_INVALID_ARG;
+    if (k >= 0 && h->host.bridge[k]) return DCOPF_ERR_NETWORK;
+  }
+  return DCOPF_OK;
+}
+
+static dcopf_status finish(dcopf_dual_t h, cudaStream_t s) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    h->last_error = cudaGetErrorString(e);
+    return DCOPF_ERR_CUDA;
+  }
+  (void)s;
+  return DCOPF_OK;
+}
+
+dcopf_status dcopf_dual_eval(dcopf_dual_t h, int32_t batch, const double* loads,
+                             const int32_t* outage, const double* lambda, const double* mu_hi,
+                             const double* mu_lo, int32_t precision, double* value,
+                             double* g_lambda, double* g_mu_hi, double* g_mu_lo, double* dispatch,
+                             void* stream) {
+  dcopf_status r = check_batch(h, batch, loads);
+  if (r) return r;
+  if (!lambda || !mu_hi || !mu_lo || !value) return DCOPF_ERR_INVALID_ARG;
+  if (precision != DCOPF_FP64 && precision != DCOPF_FP32 && precision != DCOPF_BF16X3)
+    return DCOPF_ERR_INVALID_ARG;
+  if (precision == DCOPF_BF16X3) return DCOPF_ERR_UNSUPPORTED;
+  DeviceGuard guard(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((r = check_outage(h, batch, outage, s))) return r;
+  if ((r = ensure_workspace(h, batch))) return r;
+  if ((r = run_base_flows(h, batch, loads, outage, s))) return r;
+  if ((r = run_eval_unfused(h, batch, outage, lambda, mu_hi, mu_lo, precision, value, g_lambda,
+                            g_mu_hi, g_mu_lo, dispatch, s)))
+    return r;
+  return finish(h, s);
+}
+
+dcopf_status dcopf_dual_certify_bound(dcopf_dual_t h, int32_t batch, const double* loads,
+                                      const int32_t* outage, const double* lambda,
+                                      const double* mu_hi, const double* mu_lo, double* bound,
+                                      double* err_bound, void* stream) {
+  dcopf_status r = check_batch(h, batch, loads);
+  if (r) return r;
+  if (!lambda || !mu_hi || !mu_lo || !bound) return DCOPF_ERR_INVALID_ARG;
+  DeviceGuard guard(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((r = check_outage(h, batch, outage, s))) return r;
+  if ((r = run_certify_t<double>(h, batch, loads, outage, lambda, mu_hi, mu_lo, bound, err_bound,
+                                 nullptr, nullptr, s)))
+    return r;
+  return finish(h, s);
+}
+
+dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double* loads,
+                                    const int32_t* outage, const dcopf_solve_params* params,
+                                    double* lambda, double* mu_hi, double* mu_lo,
+                                    double* best_bound, int32_t* iters, int32_t* inst_status,
+                                    void* stream) {
+  dcopf_status r = check_batch(h, batch, loads);
+  if (r) return r;
+  if (!params || !lambda || !mu_hi || !mu_lo || !best_bound) return DCOPF_ERR_INVALID_ARG;
+  const dcopf_solve_params& p = *params;
+  if (p.rule < DCOPF_GDM || p.rule > DCOPF_ADAGRAD || p.max_iters < 1 || !(p.alpha > 0) ||
+      !std::isfinite(p.alpha) || p.check_every < 0 || !(p.gap >= 0) || !(p.decay > 0) ||
+      !(p.beta1 >= 0 && p.beta1 < 1) || !(p.beta2 >= 0 && p.beta2 < 1) || !(p.eps >= 0) ||
+      p.path < DCOPF_PATH_AUTO || p.path > DCOPF_PATH_BATCHED)
+    return DCOPF_ERR_INVALID_ARG;
+  if (p.precision != DCOPF_FP64 && p.precision != DCOPF_FP32 && p.precision != DCOPF_BF16X3)
+    return DCOPF_ERR_INVALID_ARG;
+  int path = p.path;
+  if (path == DCOPF_PATH_AUTO) path = (batch == 1 && !outage) ? DCOPF_PATH_FUSED : DCOPF_PATH_BATCHED;
+  if (path == DCOPF_PATH_FUSED && (batch != 1 || outage)) return DCOPF_ERR_UNSUPPORTED;
+  int prec = p.precision;
+  if (path == DCOPF_PATH_BATCHED && prec == DCOPF_BF16X3) prec = DCOPF_FP32;
+  DeviceGuard guard(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((r = check_outage(h, batch, outage, s))) return r;
+  if ((r = ensure_workspace(h, batch))) return r;
+  CUDA_TRY(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+  if ((r = run_base_flows(h, batch, loads, outage, s))) return r;
+  dcopf_solve_params q = p;
+  q.precision = prec;
+  if (path == DCOPF_PATH_PLAIN)
+    return solve_loop<double>(h, batch, loads, outage, q, path, lambda, mu_hi, mu_lo, best_bound,
+                              iters, inst_status, s);
+  return solve_loop<float>(h, batch, loads, outage, q, path, lambda, mu_hi, mu_lo, best_bound, iters,
+                           inst_status, s);
+}
+
+int64_t dcopf_dual_kernel_launches(dcopf_dual_t h) { return h ? (int64_t)h->launches : 0; }
+
+dcopf_status dcopf_dual_device_error(dcopf_dual_t h) {
+  if (!h) return DCOPF_ERR_INVALID_ARG;
+  DeviceGuard guard(h->device);
+  int e = 0;
+  if (cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  return (dcopf_status)e;
+}
+
+}  // extern "C"

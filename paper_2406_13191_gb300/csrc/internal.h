@@ -1,0 +1,57 @@
+// Internal declarations shared by the host setup code and the CUDA translation units.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dcopf_dual.h"
+
+namespace dcopf {
+
+// Sparse LDL^T factor of the reduced Laplacian B_r = E^T Omega E (slack removed),
+// in a minimum-degree elimination order.  Row/column indices are elimination
+// positions 0..n-1.
+struct SparseFactor {
+  int n = 0;
+  std::vector<int> bus_of_pos;  // position -> bus
+  std::vector<int> pos_of_bus;  // bus -> position, -1 for the slack bus
+  // strictly lower L, unit diagonal, by rows (row i holds columns k < i)
+  std::vector<int> lrow_ptr, lrow_col;
+  std::vector<double> lrow_val;
+  // strictly lower L by columns (column k holds rows i > k) = rows of L^T
+  std::vector<int> lcol_ptr, lcol_row;
+  std::vector<double> lcol_val;
+  std::vector<double> diag;
+  // level schedules: rows listed level by level
+  std::vector<int> fwd_rows, fwd_level_ptr;
+  std::vector<int> bwd_rows, bwd_level_ptr;
+  int64_t nnz() const { return (int64_t)lrow_col.size(); }
+};
+
+// Validated copy of the network plus everything derived from it on the host.
+struct HostNet {
+  int n_bus = 0, n_line = 0, n_gen = 0, slack = 0;
+  bool qp = false;
+  double S = 100.0;
+  std::vector<int> line_from, line_to, gen_bus;
+  std::vector<double> b, fmax, fmin, pmin, pmax, cost_lin, cost_quad;
+  std::vector<uint8_t> bridge;
+  // normalised generator data (Appendix A1): p = mid + sigma x, x in [-1, 1]
+  std::vector<double> sigma, mid, ctil, mq, cconst;
+  // bus -> incident lines (+1 from-bus, -1 to-bus), for E^T Omega eta
+  std::vector<int> bus_line_ptr, bus_line_idx;
+  std::vector<double> bus_line_coef;  // +b_l or -b_l
+  SparseFactor F;
+  std::vector<double> phi;  // Phi~ = Phi diag(sigma), row-major [n_line][n_gen]
+  std::vector<double> phim; // Phi mid, [n_line] (flows of the mid-box dispatch)
+};
+
+// Builds a HostNet from the C description (validation, ordering, factorisation,
+// PTDF build).  Returns DCOPF_OK or an error with a message in *err.
+dcopf_status build_host_net(const dcopf_network_desc* d, HostNet* out, std::string* err,
+                            bool verbose);
+
+// Solves B_r theta = rhs in place (rhs indexed by elimination position).
+void host_ldl_solve(const SparseFactor& F, double* x);
+
+}  // namespace dcopf

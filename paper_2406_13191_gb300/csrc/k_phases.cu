@@ -1,0 +1,356 @@
+// Per-phase kernels of one dual evaluation and one ascent step, batched over
+// instances (row b of every [batch][n] array is instance b).
+//
+// One iteration of the method (Section 3.3, Algorithm 1) is
+//   eta      = mu_hi - mu_lo  (+ rank-1 outage term)          k_eta
+//   pi~      = Phi~^T eta          (adjoint, eq. (6) C^T mu)    k_adjoint
+//   x*       = closed-form minimiser (eq. (6) / eq. (16))       k_minimize
+//   f        = Phi~ x* + f0        (forward, constraint (1c))   k_forward
+//   value, supergradient (FP64 accumulation)                    k_grad_value
+//   projected GDM / Adam / AdaGrad step on (lambda, mu)         k_step
+// These kernels are the unfused building blocks: dcopf_dual_eval and the plain
+// path launch them one by one; the other paths replace the two operator products.
+#include "dev.cuh"
+#include "kernels.h"
+
+namespace dcopf {
+
+// eta[b][i] = mu_hi - mu_lo for i != k; for an outaged line k, eta'_k = u^T eta
+// (the adjoint of the post-outage PTDF (I + u e_k^T) H_a is H_a^T (I + e_k u^T)).
+template <typename T, typename S>
+__global__ void k_eta(int nl, const S* __restrict__ mh, const S* __restrict__ ml,
+                      const int* __restrict__ outage, const T* __restrict__ u,
+                      T* __restrict__ eta) {
+  __shared__ T red[32];
+  const int b = blockIdx.x;
+  const int k = outage ? outage[b] : -1;
+  const S* h = mh + (size_t)b * nl;
+  const S* lo = ml + (size_t)b * nl;
+  T* e = eta + (size_t)b * nl;
+  T s = T(0);
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+    T v = (i == k) ? T(0) : (T)((double)h[i] - (double)lo[i]);
+    e[i] = v;
+    if (k >= 0) s += u[(size_t)b * nl + i] * v;
+  }
+  if (k >= 0) {
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) e[k] = s;
+  }
+}
+
+// pit[b][j] = sum_i Phi~[i][j] eta[b][i]; one warp per (b, j) over row j of Phi~^T.
+template <typename T>
+__global__ void k_adjoint(int nl, int ng, const T* __restrict__ phit, const T* __restrict__ eta,
+                          T* __restrict__ pit) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.y;
+  if (warp >= ng) return;
+  const T* row = phit + (size_t)warp * nl;
+  const T* e = eta + (size_t)b * nl;
+  T s = T(0);
+  for (int i = lane; i < nl; i += 32) s += row[i] * e[i];
+  s = warp_sum(s);
+  if (lane == 0) pit[(size_t)b * ng + warp] = s;
+}
+
+// x*[b][j] from w = ctil_j + sigma_j lambda_b + pi~_bj (FP64), plus per-instance
+// sums of the generation cost and of the dispatch.
+template <typename T>
+__global__ void k_minimize(DevNet N, const double* __restrict__ lambda, const T* __restrict__ pit,
+                           T* __restrict__ x, double* __restrict__ sumcost,
+                           double* __restrict__ sump, const int* __restrict__ done) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  if (done && done[b]) return;
+  const int ng = N.n_gen;
+  const double lam = lambda[b];
+  double c = 0.0, p = 0.0;
+  for (int j = threadIdx.x; j < ng; j += blockDim.x) {
+    double w = N.ctil[j] + N.sigma[j] * lam + (double)pit[(size_t)b * ng + j];
+    double xx = inner_x<double>(w, N.mq[j]);
+    x[(size_t)b * ng + j] = (T)xx;
+    c += (N.mq[j] * xx + N.ctil[j]) * xx + N.cconst[j];
+    p += N.mid[j] + N.sigma[j] * xx;
+  }
+  c = block_sum(c, red);
+  p = block_sum(p, red);
+  if (threadIdx.x == 0) {
+    sumcost[b] = c;
+    sump[b] = p;
+  }
+}
+
+// f[b][i] = sum_j Phi~[i][j] x[b][j] + f0[b][i]; one warp per (b, i).
+template <typename T>
+__global__ void k_forward(int nl, int ng, const T* __restrict__ phi, const T* __restrict__ x,
+                          const double* __restrict__ f0, double* __restrict__ f,
+                          const int* __restrict__ done) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.y;
+  if (warp >= nl) return;
+  if (done && done[b]) return;
+  const T* row = phi + (size_t)warp * ng;
+  const T* xx = x + (size_t)b * ng;
+  T s = T(0);
+  for (int j = lane; j < ng; j += 32) s += row[j] * xx[j];
+  s = warp_sum(s);
+  if (lane == 0) f[(size_t)b * nl + warp] = (double)s + f0[(size_t)b * nl + warp];
+}
+
+// Outage correction f' = f + u f_k, supergradient (f - fmax, fmin - f; zero for the
+// outaged line) and the FP64 dual value
+//   g = sum_j cost_j(p*) + lambda (1^T p* - D) + mu_hi^T (f - fmax) + mu_lo^T (fmin - f).
+template <typename S, typename G>
+__global__ void k_grad_value(DevNet N, const int* __restrict__ outage, const double* __restrict__ u,
+                             const double* __restrict__ lambda, const S* __restrict__ mh,
+                             const S* __restrict__ ml, double* __restrict__ f,
+                             const double* __restrict__ sumcost, const double* __restrict__ sump,
+                             const double* __restrict__ demand, double* __restrict__ value,
+                             double* __restrict__ glam, G* __restrict__ ghi, G* __restrict__ glo,
+                             const int* __restrict__ done) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  if (done && done[b]) return;
+  const int nl = N.n_line;
+  const int k = outage ? outage[b] : -1;
+  double* fr = f + (size_t)b * nl;
+  double fk = 0.0;
+  if (k >= 0) fk = fr[k];
+  __syncthreads();
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+    double fi = fr[i];
+    if (k >= 0) fi += u[(size_t)b * nl + i] * fk;
+    fr[i] = fi;
+    double gh = fi - N.fmax[i], gl = N.fmin[i] - fi;
+    if (i == k) { gh = 0.0; gl = 0.0; }
+    if (ghi) ghi[(size_t)b * nl + i] = (G)gh;
+    if (glo) glo[(size_t)b * nl + i] = (G)gl;
+    acc += (double)mh[(size_t)b * nl + i] * gh + (double)ml[(size_t)b * nl + i] * gl;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    double gl = sump[b] - demand[b];
+    value[b] = sumcost[b] + lambda[b] * gl + acc;
+    if (glam) glam[b] = gl;
+  }
+}
+
+__global__ void k_dispatch(DevNet N, int B, const double* __restrict__ x, double* __restrict__ p) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B * N.n_gen) return;
+  int j = t % N.n_gen;
+  p[t] = N.mid[j] + N.sigma[j] * x[t];
+}
+__global__ void k_dispatch32(DevNet N, int B, const float* __restrict__ x, double* __restrict__ p) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B * N.n_gen) return;
+  int j = t % N.n_gen;
+  p[t] = N.mid[j] + N.sigma[j] * (double)x[t];
+}
+
+// ---------------------------------------------------------------- ascent step
+// One projected step of the chosen rule on one coordinate (Section 3.3):
+//   GDM  (Algorithm 1, heavy ball): s1 <- rho s1 + a g;  theta <- theta + s1
+//        (as printed: additionally theta <- theta + a g)
+//   Adam: s1 <- b1 s1 + (1-b1) g; s2 <- b2 s2 + (1-b2) g^2;
+//         theta <- theta + a (s1/c1) / (sqrt(s2/c2) + eps), c = 1 - beta^t
+//   AdaGrad: s1 <- s1 + g^2; theta <- theta + a g / (sqrt(s1) + eps)
+template <typename S>
+__device__ __forceinline__ S rule_step(const StepArgs& P, S theta, S g, S& s1, S& s2, S a) {
+  if (P.rule == DCOPF_GDM) {
+    s1 = S(P.rho) * s1 + a * g;
+    theta += s1;
+    if (P.as_printed) theta += a * g;
+  } else if (P.rule == DCOPF_ADAM) {
+    s1 = S(P.beta1) * s1 + (S(1) - S(P.beta1)) * g;
+    s2 = S(P.beta2) * s2 + (S(1) - S(P.beta2)) * g * g;
+    theta += a * (s1 / S(P.bc1)) / (sqrt(s2 / S(P.bc2)) + S(P.eps));
+  } else {
+    s1 += g * g;
+    theta += a * g / (sqrt(s1) + S(P.eps));
+  }
+  return theta;
+}
+
+// Step kernel: records the best point (largest in-loop value) before stepping,
+// then updates mu (projected to >= 0) and lambda.  Grid (ceil(nl/256), B).
+template <typename S>
+__global__ void k_step(int nl, StepArgs P, const double* __restrict__ value,
+                       const double* __restrict__ glam, const double* __restrict__ ghi,
+                       const double* __restrict__ glo, SolveState<S> st) {
+  const int b = blockIdx.y;
+  if (st.done[b] || st.cand[b] == 2) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = st.iter[b] + 1;  // evaluation count of this step (1-based)
+  StepArgs Q = P;
+  Q.bc1 = 1.0 - pow(P.beta1, (double)t);
+  Q.bc2 = 1.0 - pow(P.beta2, (double)t);
+  const double scale = pow(P.decay, (double)(t - 1));
+  const bool better = value[b] > st.best[b];
+  const size_t o = (size_t)b * nl + i;
+  if (i < nl) {
+    S h = st.mu_hi[o], l = st.mu_lo[o];
+    if (better) {
+      st.best_hi[o] = h;
+      st.best_lo[o] = l;
+    }
+    S a = (S)(P.alpha * scale);
+    S h2 = rule_step<S>(Q, h, (S)ghi[o], st.s1_hi[o], st.s2_hi[o], a);
+    S l2 = rule_step<S>(Q, l, (S)glo[o], st.s1_lo[o], st.s2_lo[o], a);
+    st.mu_hi[o] = h2 > S(0) ? h2 : S(0);
+    st.mu_lo[o] = l2 > S(0) ? l2 : S(0);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // lambda and per-instance bookkeeping.  st.best is read by every block of this
+    // instance row, so the new best value goes to st.best_next and is published by
+    // k_close_iter after this kernel.
+    double lam = st.lam[b];
+    if (better) {
+      st.best_next[b] = value[b];
+      st.best_lam[b] = lam;
+      st.best_iter[b] = t;
+    }
+    double a = P.alpha_lambda * scale;
+    double s1 = st.lam_s1[b], s2 = st.lam_s2[b];
+    lam = rule_step<double>(Q, lam, glam[b], s1, s2, a);
+    st.lam[b] = lam;
+    st.lam_s1[b] = s1;
+    st.lam_s2[b] = s2;
+    st.prev[b] = value[b];
+    st.iter[b] = t;
+  }
+}
+
+// Closes an iteration: publishes best_next, applies the stop tests on the in-loop
+// value (target crossing -> candidate for certification; |g_t - g_{t-1}| < tol;
+// iteration cap).  One thread per instance.
+__global__ void k_close_iter(int B, int max_iters, double tol, SolveStateBase st) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || st.done[b] || st.cand[b] == 2) return;
+  double bn = st.best_next[b];
+  if (bn > st.best[b]) st.best[b] = bn;
+  if (st.has_target && st.best[b] >= st.thresh[b] + st.margin[b]) st.cand[b] = 1;
+  if (st.iter[b] >= max_iters) st.cand[b] = 2;
+  if (tol > 0.0 && st.iter[b] > 1 && fabs(st.prev[b] - st.prev2[b]) < tol) st.cand[b] = 2;
+  st.prev2[b] = st.prev[b];
+}
+
+// ---------------------------------------------------------------- host drivers
+namespace {
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+}  // namespace
+
+dcopf_status run_eval_unfused(dcopf_dual* h, int B, const int* outage, const double* lambda,
+                              const double* mh, const double* ml, int precision, double* value,
+                              double* glam, double* ghi, double* glo, double* dispatch,
+                              cudaStream_t s) {
+  const DevNet& N = h->dev;
+  Workspace& w = h->ws;
+  const int nl = N.n_line, ng = N.n_gen;
+  dim3 gl(cdiv(nl, 8), B), gg(cdiv(ng, 8), B);
+  if (precision == DCOPF_FP64) {
+    k_eta<double, double><<<B, 256, 0, s>>>(nl, mh, ml, outage, w.u64.as<double>(), w.eta64.as<double>());
+    k_adjoint<double><<<gg, 256, 0, s>>>(nl, ng, N.phit64, w.eta64.as<double>(), w.pit64.as<double>());
+    k_minimize<double><<<B, 256, 0, s>>>(N, lambda, w.pit64.as<double>(), w.x64.as<double>(),
+                                         w.sumcost.as<double>(), w.sump.as<double>(), nullptr);
+    k_forward<double><<<gl, 256, 0, s>>>(nl, ng, N.phi64, w.x64.as<double>(), w.f0.as<double>(),
+                                         w.f.as<double>(), nullptr);
+    if (dispatch) k_dispatch<<<cdiv((long long)B * ng, 256), 256, 0, s>>>(N, B, w.x64.as<double>(), dispatch);
+  } else {
+    k_eta<float, double><<<B, 256, 0, s>>>(nl, mh, ml, outage, w.u32.as<float>(), w.eta32.as<float>());
+    k_adjoint<float><<<gg, 256, 0, s>>>(nl, ng, N.phit32, w.eta32.as<float>(), w.pit32.as<float>());
+    k_minimize<float><<<B, 256, 0, s>>>(N, lambda, w.pit32.as<float>(), w.x32.as<float>(),
+                                        w.sumcost.as<double>(), w.sump.as<double>(), nullptr);
+    k_forward<float><<<gl, 256, 0, s>>>(nl, ng, N.phi32, w.x32.as<float>(), w.f0.as<double>(),
+                                        w.f.as<double>(), nullptr);
+    if (dispatch) k_dispatch32<<<cdiv((long long)B * ng, 256), 256, 0, s>>>(N, B, w.x32.as<float>(), dispatch);
+  }
+  k_grad_value<double, double><<<B, 256, 0, s>>>(N, outage, w.u64.as<double>(), lambda, mh, ml,
+                                                 w.f.as<double>(), w.sumcost.as<double>(),
+                                                 w.sump.as<double>(), w.demand.as<double>(), value,
+                                                 glam, ghi, glo, nullptr);
+  h->launches += 5 + (dispatch ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
+  return DCOPF_OK;
+}
+
+template <typename S>
+dcopf_status run_iters_unfused(dcopf_dual* h, int B, const int* outage, int precision,
+                               const StepArgs& P, SolveState<S>& st, int n_iters, int max_iters,
+                               double tol, cudaStream_t s) {
+  const DevNet& N = h->dev;
+  Workspace& w = h->ws;
+  const int nl = N.n_line, ng = N.n_gen;
+  dim3 gl(cdiv(nl, 8), B), gg(cdiv(ng, 8), B), gs(cdiv(nl, 256), B);
+  for (int it = 0; it < n_iters; ++it) {
+    if (precision == DCOPF_FP64) {
+      k_eta<double, S><<<B, 256, 0, s>>>(nl, st.mu_hi, st.mu_lo, outage, w.u64.as<double>(), w.eta64.as<double>());
+      k_adjoint<double><<<gg, 256, 0, s>>>(nl, ng, N.phit64, w.eta64.as<double>(), w.pit64.as<double>());
+      k_minimize<double><<<B, 256, 0, s>>>(N, st.lam, w.pit64.as<double>(), w.x64.as<double>(),
+                                           w.sumcost.as<double>(), w.sump.as<double>(), st.done);
+      k_forward<double><<<gl, 256, 0, s>>>(nl, ng, N.phi64, w.x64.as<double>(), w.f0.as<double>(),
+                                           w.f.as<double>(), st.done);
+    } else {
+      k_eta<float, S><<<B, 256, 0, s>>>(nl, st.mu_hi, st.mu_lo, outage, w.u32.as<float>(), w.eta32.as<float>());
+      k_adjoint<float><<<gg, 256, 0, s>>>(nl, ng, N.phit32, w.eta32.as<float>(), w.pit32.as<float>());
+      k_minimize<float><<<B, 256, 0, s>>>(N, st.lam, w.pit32.as<float>(), w.x32.as<float>(),
+                                          w.sumcost.as<double>(), w.sump.as<double>(), st.done);
+      k_forward<float><<<gl, 256, 0, s>>>(nl, ng, N.phi32, w.x32.as<float>(), w.f0.as<double>(),
+                                          w.f.as<double>(), st.done);
+    }
+    k_grad_value<S, double><<<B, 256, 0, s>>>(N, outage, w.u64.as<double>(), st.lam, st.mu_hi,
+                                              st.mu_lo, w.f.as<double>(), w.sumcost.as<double>(),
+                                              w.sump.as<double>(), w.demand.as<double>(),
+                                              w.value.as<double>(), w.glam.as<double>(),
+                                              w.ghi.as<double>(), w.glo.as<double>(), st.done);
+    k_step<S><<<gs, 256, 0, s>>>(nl, P, w.value.as<double>(), w.glam.as<double>(),
+                                 w.ghi.as<double>(), w.glo.as<double>(), st);
+    k_close_iter<<<cdiv(B, 128), 128, 0, s>>>(B, max_iters, tol, st);
+    h->launches += 7;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
+  return DCOPF_OK;
+}
+
+template dcopf_status run_iters_unfused<double>(dcopf_dual*, int, const int*, int, const StepArgs&,
+                                                SolveState<double>&, int, int, double, cudaStream_t);
+template dcopf_status run_iters_unfused<float>(dcopf_dual*, int, const int*, int, const StepArgs&,
+                                               SolveState<float>&, int, int, double, cudaStream_t);
+
+// ---------------------------------------------------------------- instantiations
+template __global__ void k_eta<double, double>(int, const double*, const double*, const int*,
+                                               const double*, double*);
+template __global__ void k_eta<float, double>(int, const double*, const double*, const int*,
+                                              const float*, float*);
+template __global__ void k_eta<float, float>(int, const float*, const float*, const int*,
+                                             const float*, float*);
+template __global__ void k_adjoint<double>(int, int, const double*, const double*, double*);
+template __global__ void k_adjoint<float>(int, int, const float*, const float*, float*);
+template __global__ void k_minimize<double>(DevNet, const double*, const double*, double*, double*,
+                                            double*, const int*);
+template __global__ void k_minimize<float>(DevNet, const double*, const float*, float*, double*,
+                                           double*, const int*);
+template __global__ void k_forward<double>(int, int, const double*, const double*, const double*,
+                                           double*, const int*);
+template __global__ void k_forward<float>(int, int, const float*, const float*, const double*,
+                                          double*, const int*);
+template __global__ void k_grad_value<double, double>(DevNet, const int*, const double*,
+                                                      const double*, const double*, const double*,
+                                                      double*, const double*, const double*,
+                                                      const double*, double*, double*, double*,
+                                                      double*, const int*);
+template __global__ void k_grad_value<float, double>(DevNet, const int*, const double*,
+                                                     const double*, const float*, const float*,
+                                                     double*, const double*, const double*,
+                                                     const double*, double*, double*, double*,
+                                                     double*, const int*);
+template __global__ void k_step<double>(int, StepArgs, const double*, const double*, const double*,
+                                        const double*, SolveState<double>);
+template __global__ void k_step<float>(int, StepArgs, const double*, const double*, const double*,
+                                       const double*, SolveState<float>);
+
+}  // namespace dcopf

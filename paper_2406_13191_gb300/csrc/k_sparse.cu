@@ -1,0 +1,256 @@
+// FP64 sparse kernels on the LDL^T factor of the reduced Laplacian E^T Omega E.
+//
+// One CTA per instance; the solution vector lives in shared memory and the
+// triangular solves walk the level schedules with one thread per row of a level.
+//   k_base_flows : flows of the loads and of the mid-box dispatch,
+//                  f0 = H_a (G mid - p_d) (Section 2, constraint (1c)), and for an
+//                  outaged line k the rank-1 outage vector u (line outage
+//                  distribution factors, f' = f + u f_k).
+//   k_certify    : the FP64 dual bound through bus prices nu = lambda + H_a^T eta
+//                  (eq. (4) with the closed-form inner minimum of eqs. (6)/(16);
+//                  Remarks 1-2 make it a valid bound for mu >= 0).
+#include "dev.cuh"
+#include "kernels.h"
+
+#include <algorithm>
+
+namespace dcopf {
+
+__device__ void ldl_solve_smem(const DevNet& N, double* X) {
+  for (int lev = 0; lev < N.n_fwd_lev; ++lev) {
+    int s = N.fwd_lev[lev], e = N.fwd_lev[lev + 1];
+    for (int idx = s + threadIdx.x; idx < e; idx += blockDim.x) {
+      int i = N.fwd_rows[idx];
+      double v = X[i];
+      for (int p = N.lrow_ptr[i]; p < N.lrow_ptr[i + 1]; ++p) v -= N.lrow_val[p] * X[N.lrow_col[p]];
+      X[i] = v;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < N.nr; i += blockDim.x) X[i] /= N.diag[i];
+  __syncthreads();
+  for (int lev = 0; lev < N.n_bwd_lev; ++lev) {
+    int s = N.bwd_lev[lev], e = N.bwd_lev[lev + 1];
+    for (int idx = s + threadIdx.x; idx < e; idx += blockDim.x) {
+      int i = N.bwd_rows[idx];
+      double v = X[i];
+      for (int p = N.lcol_ptr[i]; p < N.lcol_ptr[i + 1]; ++p) v -= N.lcol_val[p] * X[N.lcol_row[p]];
+      X[i] = v;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double theta_at(const DevNet& N, const double* X, int bus) {
+  int p = N.pos_of_bus[bus];
+  return p >= 0 ? X[p] : 0.0;
+}
+
+__global__ void k_base_flows(DevNet N, const double* __restrict__ loads,
+                             const int* __restrict__ outage, double* __restrict__ f0,
+                             float* __restrict__ f0_32, double* __restrict__ u64,
+                             float* __restrict__ u32, double* __restrict__ demand, int* err) {
+  extern __shared__ double X[];
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  const int nl = N.n_line;
+  const double* d = loads + (size_t)b * N.n_bus;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < N.n_bus; i += blockDim.x) s += d[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) demand[b] = s;
+  for (int k = threadIdx.x; k < N.nr; k += blockDim.x) X[k] = -d[N.bus_of_pos[k]];
+  __syncthreads();
+  ldl_solve_smem(N, X);
+  double* frow = f0 + (size_t)b * nl;
+  for (int l = threadIdx.x; l < nl; l += blockDim.x)
+    frow[l] = N.phim[l] + N.line_b[l] * (theta_at(N, X, N.line_from[l]) - theta_at(N, X, N.line_to[l]));
+  const int k = outage ? outage[b] : -1;
+  __syncthreads();
+  if (k >= 0) {
+    for (int q = threadIdx.x; q < N.nr; q += blockDim.x) X[q] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int pa = N.pos_of_bus[N.line_from[k]], pb = N.pos_of_bus[N.line_to[k]];
+      if (pa >= 0) X[pa] += 1.0;
+      if (pb >= 0) X[pb] -= 1.0;
+    }
+    __syncthreads();
+    ldl_solve_smem(N, X);
+    // PTDF of a transfer from the outaged line's from-bus to its to-bus
+    const double ptdf_kk =
+        N.line_b[k] * (theta_at(N, X, N.line_from[k]) - theta_at(N, X, N.line_to[k]));
+    const double denom = 1.0 - ptdf_kk;
+    const bool bridge = fabs(denom) < 1e-9;
+    if (bridge && threadIdx.x == 0) atomicExch(err, (int)DCOPF_ERR_NETWORK);
+    const double f0k = frow[k];
+    __syncthreads();
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+      double u = 0.0;
+      if (!bridge) {
+        double ptdf = N.line_b[l] * (theta_at(N, X, N.line_from[l]) - theta_at(N, X, N.line_to[l]));
+        u = (l == k) ? -1.0 : ptdf / denom;
+      }
+      if (u64) u64[(size_t)b * nl + l] = u;
+      if (u32) u32[(size_t)b * nl + l] = (float)u;
+      frow[l] += u * f0k;
+    }
+  } else {
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+      if (u64) u64[(size_t)b * nl + l] = 0.0;
+      if (u32) u32[(size_t)b * nl + l] = 0.0f;
+    }
+  }
+  __syncthreads();
+  if (f0_32)
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) f0_32[(size_t)b * nl + l] = (float)frow[l];
+}
+
+// gamma_m = m u / (1 - m u), u = 2^-53: the classical bound on the relative error
+// of m successive FP64 roundings.
+__device__ __forceinline__ double gamma_fp64(double m) {
+  const double u = 1.1102230246251565e-16;
+  return (m * u) / (1.0 - m * u);
+}
+
+// S is the storage type of the multipliers (double for the API, float for the FP32
+// solver state); `mask` (nullable) selects the instances to certify (mask[b] != 0).
+template <typename S>
+__global__ void k_certify(DevNet N, const double* __restrict__ loads, const int* __restrict__ outage,
+                          const double* __restrict__ lambda, const S* __restrict__ mu_hi,
+                          const S* __restrict__ mu_lo, double* __restrict__ bound,
+                          double* __restrict__ errb, const int* __restrict__ mask,
+                          const int* __restrict__ done) {
+  extern __shared__ double X[];  // [nr] prices, then [nr] outage transfer
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  if (mask && (mask[b] == 0 || (done && done[b]))) return;
+  const int nl = N.n_line;
+  const int k = outage ? outage[b] : -1;
+  const S* mh = mu_hi + (size_t)b * nl;
+  const S* ml = mu_lo + (size_t)b * nl;
+  const double* d = loads + (size_t)b * N.n_bus;
+  const double lam = lambda[b];
+  // rhs = E_r^T Omega eta with eta = max(mu_hi,0) - max(mu_lo,0), eta_k = 0
+  for (int q = threadIdx.x; q < N.nr; q += blockDim.x) {
+    int bus = N.bus_of_pos[q];
+    double r = 0.0;
+    for (int p = N.bus_line_ptr[bus]; p < N.bus_line_ptr[bus + 1]; ++p) {
+      int l = N.bus_line_idx[p];
+      if (l == k) continue;
+      double eta = fmax((double)mh[l], 0.0) - fmax((double)ml[l], 0.0);
+      r += N.bus_line_coef[p] * eta;
+    }
+    X[q] = r;
+  }
+  __syncthreads();
+  ldl_solve_smem(N, X);
+  if (k >= 0) {
+    double* W = X + N.nr;
+    for (int q = threadIdx.x; q < N.nr; q += blockDim.x) W[q] = 0.0;
+    __syncthreads();
+    const int a = N.line_from[k], c = N.line_to[k];
+    if (threadIdx.x == 0) {
+      int pa = N.pos_of_bus[a], pc = N.pos_of_bus[c];
+      if (pa >= 0) W[pa] += 1.0;
+      if (pc >= 0) W[pc] -= 1.0;
+    }
+    __syncthreads();
+    ldl_solve_smem(N, W);
+    // eta'_k = u^T eta = (z_a - z_c) / (1 - PTDF_kk); z' = z + eta'_k b_k W
+    const double denom = 1.0 - N.line_b[k] * (theta_at(N, W, a) - theta_at(N, W, c));
+    const double s = (theta_at(N, X, a) - theta_at(N, X, c)) / denom;
+    __syncthreads();
+    for (int q = threadIdx.x; q < N.nr; q += blockDim.x) X[q] += s * N.line_b[k] * W[q];
+    __syncthreads();
+  }
+  double g = 0.0, A = 0.0;
+  for (int j = threadIdx.x; j < N.n_gen; j += blockDim.x) {
+    double nu = lam + theta_at(N, X, N.gen_bus[j]);
+    double p;
+    double t = gen_min_value(nu, N.cost_quad[j], N.cost_lin[j], N.S, N.pmin[j], N.pmax[j], &p);
+    g += t;
+    A += fabs(t);
+  }
+  for (int i = threadIdx.x; i < N.n_bus; i += blockDim.x) {
+    double t = -(lam + theta_at(N, X, i)) * d[i];
+    g += t;
+    A += fabs(t);
+  }
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    if (l == k) continue;
+    double t = -fmax((double)mh[l], 0.0) * N.fmax[l] + fmax((double)ml[l], 0.0) * N.fmin[l];
+    g += t;
+    A += fabs(t);
+  }
+  g = block_sum(g, red);
+  A = block_sum(A, red);
+  if (threadIdx.x == 0) {
+    int n_terms = N.n_gen + N.n_bus + nl;
+    double m = (double)((n_terms + blockDim.x - 1) / blockDim.x) + 6.0 + 8.0;  // per-thread sums,
+    // tree depth (<= 5 + 5), and the few roundings inside each term
+    double e = gamma_fp64(m) * A;
+    bound[b] = g - e;
+    if (errb) errb[b] = e;
+  }
+}
+
+template __global__ void k_certify<double>(DevNet, const double*, const int*, const double*,
+                                           const double*, const double*, double*, double*,
+                                           const int*, const int*);
+template __global__ void k_certify<float>(DevNet, const double*, const int*, const double*,
+                                          const float*, const float*, double*, double*, const int*,
+                                          const int*);
+
+size_t certify_smem(const dcopf_dual* h, bool outages) {
+  return (size_t)(outages ? 2 : 1) * (size_t)std::max(1, h->dev.nr) * sizeof(double);
+}
+
+static int sparse_threads(const dcopf_dual* h) {
+  // one thread per row of the widest level, rounded to warps, 128..512
+  int w = 128;
+  while (w < 512 && w < h->host.F.n / 8) w *= 2;
+  return w;
+}
+
+dcopf_status run_base_flows(dcopf_dual* h, int B, const double* loads, const int* outage,
+                            cudaStream_t s) {
+  size_t smem = (size_t)std::max(1, h->dev.nr) * sizeof(double);
+  if (smem > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(k_base_flows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  Workspace& w = h->ws;
+  k_base_flows<<<B, sparse_threads(h), smem, s>>>(h->dev, loads, outage, w.f0.as<double>(),
+                                                  w.f0_32.as<float>(), w.u64.as<double>(),
+                                                  w.u32.as<float>(), w.demand.as<double>(), h->d_err);
+  h->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
+  return DCOPF_OK;
+}
+
+template <typename S>
+dcopf_status run_certify_t(dcopf_dual* h, int B, const double* loads, const int* outage,
+                           const double* lam, const S* mh, const S* ml, double* bound, double* errb,
+                           const int* mask, const int* done, cudaStream_t s) {
+  size_t smem = certify_smem(h, outage != nullptr);
+  if (smem > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(k_certify<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  k_certify<S><<<B, sparse_threads(h), smem, s>>>(h->dev, loads, outage, lam, mh, ml, bound, errb,
+                                                  mask, done);
+  h->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
+  return DCOPF_OK;
+}
+template dcopf_status run_certify_t<double>(dcopf_dual*, int, const double*, const int*,
+                                            const double*, const double*, const double*, double*,
+                                            double*, const int*, const int*, cudaStream_t);
+template dcopf_status run_certify_t<float>(dcopf_dual*, int, const double*, const int*,
+                                           const double*, const float*, const float*, double*,
+                                           double*, const int*, const int*, cudaStream_t);
+
+}  // namespace dcopf

@@ -1,0 +1,131 @@
+// Library handle, workspaces and the host-side drivers of each execution path.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "dev.cuh"
+#include "internal.h"
+
+namespace dcopf {
+
+struct StepArgs {
+  int rule, as_printed;
+  double alpha, alpha_lambda, rho, beta1, beta2, eps, decay;
+  double bc1, bc2;  // Adam bias corrections of the current step (set per step)
+};
+
+// Per-instance solver bookkeeping (device pointers, [batch] each).
+struct SolveStateBase {
+  int* done;       // 1 once the instance has stopped
+  int* cand;       // 1 = in-loop value reached the target (certify), 2 = stop (cap / tol)
+  int* iter;       // evaluations so far
+  int* best_iter;  // evaluation index of the best point
+  int* status;     // per-instance result code
+  double* best;    // best in-loop value
+  double* best_next;
+  double* best_lam;
+  double* thresh;  // target - gap |target|
+  double* margin;  // extra in-loop margin before certifying
+  double* prev;
+  double* prev2;
+  double* lam;
+  double* lam_s1;
+  double* lam_s2;
+  double* cert;    // certified bound of the best point
+  int has_target;
+};
+
+template <typename S>
+struct SolveState : SolveStateBase {
+  S* mu_hi; S* mu_lo;      // [batch][n_line]
+  S* s1_hi; S* s2_hi; S* s1_lo; S* s2_lo;
+  S* best_hi; S* best_lo;
+};
+
+// Device buffer that frees itself.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { if (p) cudaFree(p); }
+  cudaError_t alloc(size_t n) {
+    if (n <= bytes && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n ? n : 16);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  template <typename T> T* as() const { return (T*)p; }
+};
+
+struct Workspace {
+  int cap = 0;  // batch capacity
+  DBuf f0, f0_32, u64, u32, demand;
+  DBuf eta64, eta32, pit64, pit32, x64, x32, f, sumcost, sump, value, glam, ghi, glo;
+  DBuf misc;  // small per-batch scratch
+};
+
+struct StateBufs {
+  int cap = 0;
+  int elem = 0;  // sizeof(S) of the arrays below
+  DBuf ints, dbls, mus;
+};
+
+}  // namespace dcopf
+
+struct dcopf_dual {
+  int device = 0;
+  dcopf::HostNet host;
+  dcopf::DevNet dev{};
+  std::vector<dcopf::DBuf*> owned;  // network arrays
+  dcopf::Workspace ws;
+  dcopf::StateBufs st32, st64;
+  int* d_err = nullptr;  // sticky device error word
+  unsigned* d_bar = nullptr;  // grid-barrier counters
+  dcopf::DBuf active;  // one int: instances still running
+  double ub_any = 0.0;  // cost of the dearest dispatch (upper bound on any primal cost)
+  long long launches = 0;
+  int sm_count = 0;
+  size_t smem_optin = 0;
+  bool verbose = false;
+  std::string last_error;
+  ~dcopf_dual();
+};
+
+namespace dcopf {
+
+// Upload helpers and workspace management (api.cu).
+dcopf_status ensure_workspace(dcopf_dual* h, int batch);
+template <typename S>
+dcopf_status ensure_state(dcopf_dual* h, int batch, SolveState<S>* st);
+
+// k_sparse.cu
+dcopf_status run_base_flows(dcopf_dual* h, int batch, const double* loads, const int* outage,
+                            cudaStream_t s);
+template <typename S>
+dcopf_status run_certify_t(dcopf_dual* h, int batch, const double* loads, const int* outage,
+                           const double* lam, const S* mh, const S* ml, double* bound, double* errb,
+                           const int* mask, const int* done, cudaStream_t s);
+size_t certify_smem(const dcopf_dual* h, bool outages);
+
+// k_phases.cu
+dcopf_status run_eval_unfused(dcopf_dual* h, int batch, const int* outage, const double* lambda,
+                              const double* mh, const double* ml, int precision, double* value,
+                              double* glam, double* ghi, double* glo, double* dispatch,
+                              cudaStream_t s);
+template <typename S>
+dcopf_status run_iters_unfused(dcopf_dual* h, int batch, const int* outage, int precision,
+                               const StepArgs& P, SolveState<S>& st, int n_iters, int max_iters,
+                               double tol, cudaStream_t s);
+
+// k_fused.cu
+dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>& st, int max_iters,
+                             double tol, cudaStream_t s);
+
+}  // namespace dcopf

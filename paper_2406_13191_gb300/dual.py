@@ -1,0 +1,201 @@
+"""Python binding of the C ABI: torch tensors in, torch tensors out.
+
+Every numeric step runs in libdcopfdual.so; this module only checks shapes, moves
+arguments to contiguous float64/int32 CUDA tensors and passes raw pointers and the
+current CUDA stream.  There is no CPU implementation: without the native library
+or without a CUDA device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _as_dev(x, dtype, device):
+    if x is None:
+        return None
+    t = x if isinstance(x, torch.Tensor) else torch.as_tensor(np.asarray(x))
+    return t.to(device=device, dtype=dtype).contiguous()
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class SolveResult:
+    lam: torch.Tensor          # [B] best iterate, lambda
+    mu_hi: torch.Tensor        # [B][n_line]
+    mu_lo: torch.Tensor        # [B][n_line]
+    bound: torch.Tensor        # [B] certified FP64 lower bound
+    iters: torch.Tensor        # [B] iterations taken
+    status: torch.Tensor       # [B] 0 target reached, 1 cap/tol, 2 infeasible suspected
+
+
+class DcopfDual:
+    """One network on one GPU (``dcopf_dual_create``).
+
+    ``net`` is a ``synth.Network`` or any object/dict with its fields (n_bus,
+    line_from, line_to, line_b, flow_max, flow_min, gen_bus, pmin, pmax, cost_lin,
+    cost_quad, base_mva, slack_bus)."""
+
+    def __init__(self, net, device: int | None = None, verbose: bool = False):
+        self.lib = _lib.load()
+        d = net.as_dict() if hasattr(net, "as_dict") else dict(net)
+        self._keep = []
+
+        def arr(v, dt):
+            if v is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(v, dtype=dt))
+            self._keep.append(a)
+            ct = C.c_int32 if dt == np.int32 else C.c_double
+            return a.ctypes.data_as(C.POINTER(ct))
+
+        desc = _lib.NetworkDesc()
+        desc.n_bus = int(d["n_bus"])
+        desc.n_line = len(d["line_from"])
+        desc.n_gen = len(d["gen_bus"])
+        desc.slack_bus = int(d.get("slack_bus", 0))
+        desc.line_from = arr(d["line_from"], np.int32)
+        desc.line_to = arr(d["line_to"], np.int32)
+        desc.line_b = arr(d["line_b"], np.float64)
+        desc.flow_max = arr(d["flow_max"], np.float64)
+        desc.flow_min = arr(d.get("flow_min"), np.float64)
+        desc.gen_bus = arr(d["gen_bus"], np.int32)
+        desc.pmin = arr(d["pmin"], np.float64)
+        desc.pmax = arr(d["pmax"], np.float64)
+        desc.cost_lin = arr(d["cost_lin"], np.float64)
+        desc.cost_quad = arr(d.get("cost_quad"), np.float64)
+        desc.base_mva = float(d.get("base_mva", 100.0))
+        opt = _lib.Options()
+        opt.device = -1 if device is None else int(device)
+        opt.verbose = 1 if verbose else 0
+        h = C.c_void_p()
+        _lib.check(self.lib.dcopf_dual_create(C.byref(desc), C.byref(opt), C.byref(h)),
+                   "dcopf_dual_create")
+        self._keep = []
+        self.h = h
+        self.n_bus, self.n_line, self.n_gen = desc.n_bus, desc.n_line, desc.n_gen
+        self.is_qp = desc.cost_quad is not None and bool(desc.cost_quad)
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = torch.device("cuda", int(device))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dcopf_dual_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ helpers
+    def _stream(self):
+        return C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _batch_inputs(self, loads, outage):
+        loads = _as_dev(loads, torch.float64, self.device)
+        if loads.dim() == 1:
+            loads = loads[None]
+        if loads.shape[1] != self.n_bus:
+            raise ValueError("loads must be [batch][n_bus]")
+        out = _as_dev(outage, torch.int32, self.device)
+        if out is not None and out.numel() != loads.shape[0]:
+            raise ValueError("outage must be [batch]")
+        return loads, out
+
+    def bridge_mask(self) -> np.ndarray:
+        m = np.zeros(self.n_line, dtype=np.uint8)
+        _lib.check(self.lib.dcopf_dual_info(self.h, None, None, None, None,
+                                            m.ctypes.data_as(C.POINTER(C.c_uint8))),
+                   "dcopf_dual_info")
+        return m.astype(bool)
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.dcopf_dual_kernel_launches(self.h))
+
+    # ------------------------------------------------------------------ entry points
+    def eval(self, loads, lam, mu_hi, mu_lo, outage=None, precision: str = "fp64",
+             want_grad: bool = True, want_dispatch: bool = True):
+        """``dcopf_dual_eval``: dual value, supergradient and minimiser at (lambda, mu)."""
+        loads, out = self._batch_inputs(loads, outage)
+        B = loads.shape[0]
+        lam = _as_dev(lam, torch.float64, self.device).reshape(B)
+        mh = _as_dev(mu_hi, torch.float64, self.device).reshape(B, self.n_line)
+        ml = _as_dev(mu_lo, torch.float64, self.device).reshape(B, self.n_line)
+        kw = dict(dtype=torch.float64, device=self.device)
+        value = torch.empty(B, **kw)
+        gl = torch.empty(B, **kw) if want_grad else None
+        ghi = torch.empty(B, self.n_line, **kw) if want_grad else None
+        glo = torch.empty(B, self.n_line, **kw) if want_grad else None
+        disp = torch.empty(B, self.n_gen, **kw) if want_dispatch else None
+        _lib.check(self.lib.dcopf_dual_eval(self.h, B, _ptr(loads), _ptr(out), _ptr(lam), _ptr(mh),
+                                            _ptr(ml), _lib.PRECISION[precision], _ptr(value),
+                                            _ptr(gl), _ptr(ghi), _ptr(glo), _ptr(disp),
+                                            self._stream()), "dcopf_dual_eval")
+        return dict(value=value, g_lambda=gl, g_mu_hi=ghi, g_mu_lo=glo, dispatch=disp)
+
+    def certify(self, loads, lam, mu_hi, mu_lo, outage=None):
+        """``dcopf_dual_certify_bound``: certified FP64 bound and its rounding allowance."""
+        loads, out = self._batch_inputs(loads, outage)
+        B = loads.shape[0]
+        lam = _as_dev(lam, torch.float64, self.device).reshape(B)
+        mh = _as_dev(mu_hi, torch.float64, self.device).reshape(B, self.n_line)
+        ml = _as_dev(mu_lo, torch.float64, self.device).reshape(B, self.n_line)
+        bound = torch.empty(B, dtype=torch.float64, device=self.device)
+        err = torch.empty(B, dtype=torch.float64, device=self.device)
+        _lib.check(self.lib.dcopf_dual_certify_bound(self.h, B, _ptr(loads), _ptr(out), _ptr(lam),
+                                                     _ptr(mh), _ptr(ml), _ptr(bound), _ptr(err),
+                                                     self._stream()), "dcopf_dual_certify_bound")
+        return bound, err
+
+    def solve(self, loads, outage=None, rule="adam", precision="fp32", path="auto",
+              max_iters=5000, alpha=1000.0, alpha_lambda=0.0, rho=0.9, beta1=0.9, beta2=0.999,
+              eps=1e-8, decay=1.0, gap=1e-3, tol=0.0, target=None, warm=None,
+              as_printed=False, check_every=1) -> SolveResult:
+        """``dcopf_dual_solve_batch``.  ``target`` ([B] optimal costs) enables the
+        certified-gap stop; ``warm`` = (lambda, mu_hi, mu_lo) warm start."""
+        loads, out = self._batch_inputs(loads, outage)
+        B = loads.shape[0]
+        kw = dict(dtype=torch.float64, device=self.device)
+        if warm is not None:
+            lam = _as_dev(warm[0], torch.float64, self.device).reshape(B).clone()
+            mh = _as_dev(warm[1], torch.float64, self.device).reshape(B, self.n_line).clone()
+            ml = _as_dev(warm[2], torch.float64, self.device).reshape(B, self.n_line).clone()
+        else:
+            lam = torch.zeros(B, **kw)
+            mh = torch.zeros(B, self.n_line, **kw)
+            ml = torch.zeros(B, self.n_line, **kw)
+        bound = torch.empty(B, **kw)
+        iters = torch.empty(B, dtype=torch.int32, device=self.device)
+        status = torch.empty(B, dtype=torch.int32, device=self.device)
+        tgt = _as_dev(target, torch.float64, self.device)
+        if tgt is not None:
+            tgt = tgt.reshape(B)
+        p = _lib.SolveParams()
+        self.lib.dcopf_solve_params_default(C.byref(p))
+        p.rule = _lib.RULE[rule]
+        p.precision = _lib.PRECISION[precision]
+        p.path = _lib.PATH[path]
+        p.max_iters = int(max_iters)
+        p.warm_start = 1 if warm is not None else 0
+        p.as_printed = 1 if as_printed else 0
+        p.check_every = int(check_every)
+        p.alpha, p.alpha_lambda, p.rho = float(alpha), float(alpha_lambda), float(rho)
+        p.beta1, p.beta2, p.eps, p.decay = float(beta1), float(beta2), float(eps), float(decay)
+        p.gap, p.tol = float(gap), float(tol)
+        p.target_value = None if tgt is None else tgt.data_ptr()
+        _lib.check(self.lib.dcopf_dual_solve_batch(self.h, B, _ptr(loads), _ptr(out), C.byref(p),
+                                                   _ptr(lam), _ptr(mh), _ptr(ml), _ptr(bound),
+                                                   _ptr(iters), _ptr(status), self._stream()),
+                   "dcopf_dual_solve_batch")
+        return SolveResult(lam, mh, ml, bound, iters, status)

@@ -21,6 +21,7 @@ costs ``a*(S*p)**2 + b*(S*p)`` $/h with ``S = base_mva``.
 """
 from __future__ import annotations
 
+import functools
 from dataclasses import dataclass, field
 import numpy as np
 
@@ -169,8 +170,7 @@ def bridges(n_bus: int, line_from: np.ndarray, line_to: np.ndarray) -> np.ndarra
     return is_bridge
 
 
-def _dc_flows(n_bus, line_from, line_to, line_b, inj, slack=0):
-    """DC power flow of one injection vector, used only to place line limits."""
+def _laplacian_lu(n_bus, line_from, line_to, line_b, slack=0):
     import scipy.sparse as sp
     import scipy.sparse.linalg as spl
     n_line = len(line_from)
@@ -180,29 +180,67 @@ def _dc_flows(n_bus, line_from, line_to, line_b, inj, slack=0):
     inc = sp.csr_matrix((vals, (rows, cols)), shape=(n_line, n_bus))
     lap = (inc.T @ sp.diags(line_b) @ inc).tocsc()
     keep = np.setdiff1d(np.arange(n_bus), [slack])
-    theta = np.zeros(n_bus)
-    theta[keep] = spl.spsolve(lap[keep][:, keep], inj[keep])
-    return line_b * (theta[line_from] - theta[line_to])
+    return spl.splu(lap[keep][:, keep]), keep
 
 
-def _place_limits(rng, net_parts, loads_base, frac_tight=0.10):
+def _dc_flows(n_bus, line_from, line_to, line_b, inj, slack=0, lu=None):
+    """DC power flow of injection vectors (columns of ``inj``), used only to place
+    line limits."""
+    if lu is None:
+        lu, keep = _laplacian_lu(n_bus, line_from, line_to, line_b, slack)
+    else:
+        lu, keep = lu
+    inj = np.asarray(inj, dtype=np.float64)
+    theta = np.zeros((n_bus,) + inj.shape[1:])
+    theta[keep] = lu.solve(np.ascontiguousarray(inj[keep]))
+    return (line_b[:, None] if inj.ndim == 2 else line_b) * (theta[line_from] - theta[line_to])
+
+
+def _proportional_injections(loads, gen_bus, pmax):
+    """Columns: injections of the proportional dispatch p_j = pmax_j D / sum(pmax)."""
+    L = np.atleast_2d(loads)
+    inj = -L.T.copy()
+    share = pmax / pmax.sum()
+    for b in range(L.shape[0]):
+        np.add.at(inj[:, b], gen_bus, share * L[b].sum())
+    return inj
+
+
+def _place_limits(rng, net_parts, loads_ref, frac_tight=0.10, outages=None):
+    """Line limits relative to the proportional-dispatch flows.
+
+    ``loads_ref`` is one load vector or a [k][n_bus] reference set; the flow of line l
+    is taken as its largest |flow| over the reference instances (for an instance
+    with an outaged line, the flows of the network without that line).  Limits are
+    U[1.1, 1.5] times that envelope, 1.02 times for a random 10 % of lines, and at
+    least 5 % of the median envelope.  Every reference instance is then feasible
+    (its proportional dispatch satisfies every limit)."""
     n_bus, lf, lt, lb, gen_bus, pmax = net_parts
-    dem = loads_base.sum()
-    p_base = pmax * dem / pmax.sum()
-    inj = -loads_base.copy()
-    np.add.at(inj, gen_bus, p_base)
-    f_base = _dc_flows(n_bus, lf, lt, lb, inj)
+    L = np.atleast_2d(loads_ref)
+    inj = _proportional_injections(L, gen_bus, pmax)
+    lu = _laplacian_lu(n_bus, lf, lt, lb)
+    env = np.abs(_dc_flows(n_bus, lf, lt, lb, inj, lu=lu)).max(1)
+    if outages is not None:
+        for b in np.flatnonzero(outages >= 0):
+            k = int(outages[b])
+            keep = np.arange(len(lf)) != k
+            fk = _dc_flows(n_bus, lf[keep], lt[keep], lb[keep], inj[:, b])
+            env[keep] = np.maximum(env[keep], np.abs(fk))
     factor = rng.uniform(1.1, 1.5, size=len(lf))
     tight = rng.random(len(lf)) < frac_tight
     factor[tight] = 1.02
-    floor = 0.05 * np.median(np.abs(f_base))
-    fmax = np.maximum(factor * np.abs(f_base), floor)
-    return fmax, f_base
+    floor = 0.05 * np.median(env)
+    fmax = np.maximum(factor * env, floor)
+    return fmax, env
 
 
 def make_network(seed: int, n_bus: int, n_line: int, n_gen: int, quadratic: bool,
-                 load_law: str, load_frac: float, name: str = ""):
-    """Build a network and its base load profile (returned as (Network, loads_base))."""
+                 load_law: str, load_frac: float, name: str = "", scenarios=None):
+    """Build a network and its base load profile (returned as (Network, loads_base)).
+
+    ``scenarios`` = (count, seed, outage_count, outage_seed) adds that workload's own
+    scenario instances (per-bus multipliers U[0.85, 1.15] on the base profile, and
+    line outages) to the reference set the limits are placed on."""
     rng = _rng(seed)
     lf, lt, _ = _geo_topology(rng, n_bus, n_line)
     lb = rng.uniform(5.0, 50.0, size=n_line)
@@ -222,7 +260,16 @@ def make_network(seed: int, n_bus: int, n_line: int, n_gen: int, quadratic: bool
     else:
         raise ValueError(load_law)
     loads *= load_frac * pmax.sum() / loads.sum()
-    fmax, _ = _place_limits(rng, (n_bus, lf, lt, lb, gen_bus, pmax), loads)
+    ref = loads[None, :]
+    outs = None
+    if scenarios is not None:
+        count, sseed, n_out, oseed = scenarios
+        sc = scenario_loads(loads, count, sseed)
+        ref = np.vstack([ref, sc])
+        if n_out:
+            o = _outage_choice(n_bus, lf, lt, count, n_out, oseed)
+            outs = np.concatenate([[-1], o])
+    fmax, _ = _place_limits(rng, (n_bus, lf, lt, lb, gen_bus, pmax), ref, outages=outs)
     net = Network(n_bus=n_bus, line_from=lf, line_to=lt, line_b=lb, flow_max=fmax,
                   flow_min=-fmax, gen_bus=gen_bus, pmin=pmin, pmax=pmax,
                   cost_lin=cost_lin, cost_quad=cost_quad, name=name)
@@ -240,18 +287,28 @@ CONFIG_NAMES = {
 }
 
 
+# scenario streams: (count, load seed, outage count, outage seed) per workload
+SCENARIOS = {1: (256, 1001, 0, 0), 2: (1024, 2001, 512, 2002), 3: (256, 3001, 0, 0)}
+
+
+@functools.lru_cache(maxsize=8)
 def network_for(cfg: int):
-    """The network of workload ``cfg`` and its base load profile."""
+    """The network of workload ``cfg`` and its base load profile (cached; treat the
+    returned arrays as read-only)."""
     if cfg == 0:
         return make_network(1000, 30, 41, 6, False, "uniform", 0.60, "syn30")
     if cfg == 1:
-        return make_network(1000 * 1, 2000, 3200, 540, True, "lognormal", 0.65, "syn2000")
+        return make_network(1000 * 1, 2000, 3200, 540, True, "lognormal", 0.65, "syn2000",
+                            scenarios=SCENARIOS[1])
     if cfg == 2:
-        return make_network(1000 * 2, 4600, 7200, 410, False, "uniform", 0.60, "syn4600")
+        return make_network(1000 * 2, 4600, 7200, 410, False, "uniform", 0.60, "syn4600",
+                            scenarios=SCENARIOS[2])
     if cfg == 3:
-        return make_network(1000 * 3, 10000, 12700, 2500, True, "lognormal", 0.65, "syn10000")
+        return make_network(1000 * 3, 10000, 12700, 2500, True, "lognormal", 0.65, "syn10000",
+                            scenarios=SCENARIOS[3])
     if cfg == 300:
-        return make_network(1000 * 4 + 300, 300, 480, 81, True, "lognormal", 0.65, "syn300")
+        return make_network(1000 * 4 + 300, 300, 480, 81, True, "lognormal", 0.65, "syn300",
+                            scenarios=(256, 4301, 0, 0))
     raise ValueError(cfg)
 
 
@@ -261,31 +318,37 @@ def scenario_loads(base_loads: np.ndarray, batch: int, seed: int, lo=0.85, hi=1.
     return base_loads[None, :] * rng.uniform(lo, hi, size=(batch, base_loads.shape[0]))
 
 
-def outages_for(net: Network, batch: int, n_out: int, seed: int) -> np.ndarray:
-    """-1 for intact instances; a uniform non-bridge line for ``n_out`` random instances."""
+def _outage_choice(n_bus, line_from, line_to, batch, n_out, seed):
     rng = _rng(seed)
-    ok = np.flatnonzero(~bridges(net.n_bus, net.line_from, net.line_to))
+    ok = np.flatnonzero(~bridges(n_bus, line_from, line_to))
     out = -np.ones(batch, dtype=np.int32)
     which = rng.choice(batch, size=n_out, replace=False)
     out[which] = rng.choice(ok, size=n_out, replace=True).astype(np.int32)
     return out
 
 
+def outages_for(net: Network, batch: int, n_out: int, seed: int) -> np.ndarray:
+    """-1 for intact instances; a uniform non-bridge line for ``n_out`` random instances."""
+    return _outage_choice(net.n_bus, net.line_from, net.line_to, batch, n_out, seed)
+
+
 def workload(cfg: int, batch: int | None = None) -> Workload:
-    """Instances of workload ``cfg``; ``batch`` trims (or sets) the instance count."""
+    """Instances of workload ``cfg`` (the first ``batch`` of its scenario stream)."""
     net, base = network_for(cfg)
-    if cfg in (0, 1):
+    if cfg == 0:
         b = 1 if batch is None else batch
-        loads = np.repeat(base[None, :], b, 0) if b == 1 else scenario_loads(base, b, 1000 * cfg + 1)
+        loads = np.repeat(base[None, :], b, 0)
         out = -np.ones(b, dtype=np.int32)
-    elif cfg == 2:
-        b = 1024 if batch is None else batch
-        loads = scenario_loads(base, b, 2001)
-        out = outages_for(net, b, b // 2, 2002)
-    elif cfg == 3:
-        b = 256 if batch is None else batch
-        loads = scenario_loads(base, b, 3001)
+    elif cfg == 1:
+        b = 1 if batch is None else batch
+        loads = base[None, :] if b == 1 else scenario_loads(base, b, SCENARIOS[1][1])
         out = -np.ones(b, dtype=np.int32)
+    elif cfg in (2, 3):
+        count, sseed, n_out, oseed = SCENARIOS[cfg]
+        b = count if batch is None else batch
+        loads = scenario_loads(base, count, sseed)[:b]
+        out = (_outage_choice(net.n_bus, net.line_from, net.line_to, count, n_out, oseed)[:b]
+               if n_out else -np.ones(b, dtype=np.int32))
     else:
         raise ValueError(cfg)
     return Workload(net=net, loads=np.ascontiguousarray(loads), outage=out,

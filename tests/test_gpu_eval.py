@@ -1,0 +1,151 @@
+"""GPU parity of dcopf_dual_eval and dcopf_dual_certify_bound against the FP64 oracle.
+
+Tolerances: FP64 products match the oracle's dual value to 1e-9 relative (the
+oracle and the GPU sum in different orders; both are FP64), FP32 products to 1e-5
+relative with FP64 accumulation.  Gradients are compared elementwise, dispatches
+per generator; LP points with a near-zero reduced cost (a legitimate tie) are
+redrawn."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dcopf
+from paper_2406_13191_gb300 import DcopfDual, synth
+
+from gpu_common import drop_line, near_tie, onet, rand_point
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cases():
+    out = {}
+    for name, (net, base) in {
+        "c0": synth.network_for(0),
+        "c1": synth.network_for(1),
+        "tiny_qp": synth.tiny_network(5, 40, 60, 9, quadratic=True),
+        "tiny_lp": synth.tiny_network(6, 37, 55, 7),
+    }.items():
+        out[name] = (net, base, onet(net), DcopfDual(net))
+    return out
+
+
+def _points(on, loads, rng, n, **kw):
+    pts = []
+    while len(pts) < n:
+        p = rand_point(rng, on.n_line, **kw)
+        if not near_tie(on, loads, *p):
+            pts.append(p)
+    return pts
+
+
+@pytest.mark.parametrize("name", ["c0", "c1", "tiny_qp", "tiny_lp"])
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-9), ("fp32", 1e-5)])
+def test_eval_matches_oracle(cases, name, precision, rtol):
+    net, base, on, g = cases[name]
+    rng = np.random.default_rng(17)
+    B = 3
+    loads = synth.scenario_loads(base, B, 99)
+    pts = []
+    for b in range(B):
+        pts += _points(on, loads[b], rng, 1)
+    lam = np.array([p[0] for p in pts])
+    mh = np.stack([p[1] for p in pts])
+    ml = np.stack([p[2] for p in pts])
+    r = g.eval(loads, lam, mh, ml, precision=precision)
+    torch.cuda.synchronize()
+    for b in range(B):
+        val, gl, ghi, glo, p = dcopf.evaluate(on, loads[b], lam[b], mh[b], ml[b])
+        v = r["value"][b].item()
+        assert abs(v - val) <= rtol * abs(val), (v, val)
+        fscale = 1.0 + np.max(np.abs(on.fmax))
+        gtol = (1e-9 if precision == "fp64" else 2e-4) * fscale
+        assert np.max(np.abs(r["g_mu_hi"][b].cpu().numpy() - ghi)) <= gtol
+        assert np.max(np.abs(r["g_mu_lo"][b].cpu().numpy() - glo)) <= gtol
+        assert abs(r["g_lambda"][b].item() - gl) <= (1e-9 if precision == "fp64" else 1e-4) * (1 + loads[b].sum())
+        ptol = 1e-9 if precision == "fp64" else 1e-4
+        assert np.max(np.abs(r["dispatch"][b].cpu().numpy() - p)) <= ptol * (1 + np.max(on.pmax))
+
+
+def test_eval_outage_matches_rebuilt_network(cases):
+    net, base, on, g = cases["tiny_lp"]
+    br = g.bridge_mask()
+    cand = np.flatnonzero(~br)
+    rng = np.random.default_rng(23)
+    B = 4
+    loads = synth.scenario_loads(base, B, 5)
+    outage = np.array([-1, cand[0], cand[len(cand) // 2], cand[-1]], dtype=np.int32)
+    pts = [rand_point(rng, on.n_line) for _ in range(B)]
+    lam = np.array([p[0] for p in pts])
+    mh = np.stack([p[1] for p in pts])
+    ml = np.stack([p[2] for p in pts])
+    for prec, rtol in (("fp64", 1e-9), ("fp32", 1e-5)):
+        r = g.eval(loads, lam, mh, ml, outage=outage, precision=prec)
+        for b in range(B):
+            k = outage[b]
+            if k < 0:
+                o, mhb, mlb = on, mh[b], ml[b]
+            else:
+                o = drop_line(net, k)
+                keep = np.arange(on.n_line) != k
+                mhb, mlb = mh[b][keep], ml[b][keep]
+            val, gl, ghi, glo, p = dcopf.evaluate(o, loads[b], lam[b], mhb, mlb)
+            assert abs(r["value"][b].item() - val) <= rtol * abs(val)
+            gh = r["g_mu_hi"][b].cpu().numpy()
+            if k >= 0:
+                assert gh[k] == 0.0
+                gh = gh[np.arange(on.n_line) != k]
+            assert np.max(np.abs(gh - ghi)) <= (1e-9 if prec == "fp64" else 2e-4) * (1 + on.fmax.max())
+
+
+@pytest.mark.parametrize("name", ["c0", "c1", "tiny_qp"])
+def test_certify_matches_oracle_and_bounds(cases, name):
+    net, base, on, g = cases[name]
+    rng = np.random.default_rng(31)
+    B = 4
+    loads = synth.scenario_loads(base, B, 7)
+    pts = [rand_point(rng, on.n_line) for _ in range(B)]
+    lam = np.array([p[0] for p in pts])
+    mh = np.stack([p[1] for p in pts]) - 50.0   # some negative entries: projected by certify
+    ml = np.stack([p[2] for p in pts])
+    bound, err = g.certify(loads, lam, mh, ml)
+    for b in range(B):
+        ref = dcopf.dual_value_prices(on, loads[b], lam[b], np.maximum(mh[b], 0), np.maximum(ml[b], 0))
+        e = err[b].item()
+        assert 0 <= e <= 1e-9 * (1 + abs(ref))
+        assert abs(bound[b].item() + e - ref) <= 1e-11 * abs(ref)
+
+
+def test_certify_outage_matches_rebuilt(cases):
+    net, base, on, g = cases["tiny_qp"]
+    cand = np.flatnonzero(~g.bridge_mask())
+    rng = np.random.default_rng(37)
+    loads = synth.scenario_loads(base, 3, 8)
+    outage = np.array([cand[1], -1, cand[-2]], dtype=np.int32)
+    pts = [rand_point(rng, on.n_line) for _ in range(3)]
+    lam = np.array([p[0] for p in pts])
+    mh = np.stack([p[1] for p in pts])
+    ml = np.stack([p[2] for p in pts])
+    bound, err = g.certify(loads, lam, mh, ml, outage=outage)
+    for b in range(3):
+        k = outage[b]
+        keep = np.arange(on.n_line) != k
+        o = on if k < 0 else drop_line(net, k)
+        ref = dcopf.dual_value_prices(o, loads[b], lam[b], mh[b][keep] if k >= 0 else mh[b],
+                                      ml[b][keep] if k >= 0 else ml[b])
+        assert abs(bound[b].item() + err[b].item() - ref) <= 1e-10 * abs(ref)
+
+
+def test_eval_rejects_bad_outages(cases):
+    from paper_2406_13191_gb300._lib import DcopfError
+    net, base, on, g = cases["c0"]
+    z = np.zeros((1, on.n_line))
+    br = np.flatnonzero(g.bridge_mask())
+    assert len(br) > 0          # the 30-bus network is tree-like: it has bridges
+    with pytest.raises(DcopfError) as e:
+        g.eval(base[None], np.zeros(1), z, z, outage=np.array([br[0]], dtype=np.int32))
+    assert e.value.code == 2
+    for bad in (-2, on.n_line):
+        with pytest.raises(DcopfError) as e:
+            g.eval(base[None], np.zeros(1), z, z, outage=np.array([bad], dtype=np.int32))
+        assert e.value.code == 1

@@ -1,0 +1,144 @@
+"""GPU solves (dcopf_dual_solve_batch) against the oracle's exact optimum gamma*.
+
+Bar: every certified bound is a valid lower bound (<= gamma*, up to the oracle's
+1e-9 sandwich) and instances that report status 0 are within the 0.1 % gap
+(bound >= gamma* (1 - 1e-3)).  The returned bound is the oracle's dual value at the
+returned (projected) point, to FP64 accuracy."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dcopf
+from paper_2406_13191_gb300 import DcopfDual, synth
+
+from gpu_common import drop_line, gamma, onet
+
+pytestmark = pytest.mark.gpu
+
+ADAM_LP = dict(rule="adam", alpha=1000.0, beta1=0.9, beta2=0.999, decay=0.99, max_iters=5000)
+ADAM_QP = dict(rule="adam", alpha=1000.0, beta1=0.95, beta2=0.999, decay=0.999, max_iters=4000)
+
+
+@pytest.fixture(scope="module")
+def c0():
+    net, base = synth.network_for(0)
+    on = onet(net)
+    return net, base, on, DcopfDual(net), gamma(on, base)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    net, base = synth.network_for(1)
+    on = onet(net)
+    return net, base, on, DcopfDual(net), gamma(on, base)
+
+
+def _check(res, on, loads, gam, b=0, status0=True):
+    bnd = res.bound[b].item()
+    assert bnd <= gam + 1e-9 * abs(gam)
+    if status0:
+        assert res.status[b].item() == 0
+        assert bnd >= gam * (1 - 1e-3) - 1e-9 * abs(gam)
+    lam = res.lam[b].item()
+    mh = res.mu_hi[b].cpu().numpy()
+    ml = res.mu_lo[b].cpu().numpy()
+    ref = dcopf.dual_value_prices(on, loads, lam, np.maximum(mh, 0), np.maximum(ml, 0))
+    assert abs(bnd - ref) <= 1e-10 * abs(ref)
+
+
+@pytest.mark.parametrize("path", ["plain", "fused", "batched"])
+def test_solve_c0_reaches_gap(c0, path):
+    net, base, on, g, gam = c0
+    res = g.solve(base[None], path=path, precision="fp64" if path == "plain" else "fp32",
+                  target=[gam], **ADAM_LP)
+    torch.cuda.synchronize()
+    _check(res, on, base, gam)
+    assert 10 < res.iters[0].item() < 5000
+
+
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_solve_c1_reaches_gap(c1, path):
+    net, base, on, g, gam = c1
+    res = g.solve(base[None], path=path, target=[gam], **ADAM_QP)
+    _check(res, on, base, gam)
+
+
+def test_plain_trajectory_follows_oracle(c1):
+    """The plain FP64 path runs Algorithm 1 (heavy-ball GDM) like the oracle: after 40
+    iterations without a target both hold the same best value (smooth QP dual, FP64)."""
+    net, base, on, g, gam = c1
+    kw = dict(rule="gdm", alpha=10.0, alpha_lambda=0.1, rho=0.995, max_iters=40)
+    res = g.solve(base[None], path="plain", **kw)
+    ref = dcopf.solve(on, base, **kw)
+    assert res.iters[0].item() == 40 and res.status[0].item() == 1
+    assert abs(res.lam[0].item() - ref["lam"]) <= 1e-8 * abs(ref["lam"])
+    assert np.allclose(res.mu_hi[0].cpu().numpy(), ref["mu_hi"], rtol=1e-7, atol=1e-7)
+    assert abs(res.bound[0].item() - ref["best"]) <= 1e-8 * abs(ref["best"])
+
+
+def test_fused_trajectory_follows_oracle(c1):
+    """FP32 operators in the fused kernel: after 60 Adam iterations the best value
+    stays within 1e-4 of the FP64 oracle's."""
+    net, base, on, g, gam = c1
+    kw = dict(rule="adam", alpha=1000.0, beta1=0.95, beta2=0.999, max_iters=60)
+    res = g.solve(base[None], path="fused", **kw)
+    ref = dcopf.solve(on, base, **kw)
+    assert res.iters[0].item() == 60
+    assert abs(res.bound[0].item() - ref["best"]) <= 1e-4 * abs(ref["best"])
+
+
+def test_gdm_as_printed_and_adagrad_run(c0):
+    net, base, on, g, gam = c0
+    for kw in (dict(rule="gdm", alpha=10.0, rho=0.9, as_printed=True, max_iters=300),
+               dict(rule="adagrad", alpha=1000.0, max_iters=300)):
+        for path in ("plain", "fused"):
+            res = g.solve(base[None], path=path, **kw)
+            ref = dcopf.solve(on, base, **kw)
+            assert res.status[0].item() == 1 and res.iters[0].item() == 300
+            _check(res, on, base, gam, status0=False)
+            # same method, same start: the best values agree to the FP32 operator precision
+            assert abs(res.bound[0].item() - ref["best"]) <= 2e-3 * abs(ref["best"])
+
+
+def test_tol_stop(c0):
+    net, base, on, g, gam = c0
+    res = g.solve(base[None], path="plain", rule="adam", alpha=1000.0, decay=0.9, tol=1e-3,
+                  max_iters=5000)
+    assert res.status[0].item() == 1 and res.iters[0].item() < 5000
+
+
+def test_warm_start_from_solution_stops_immediately(c0):
+    net, base, on, g, gam = c0
+    r1 = g.solve(base[None], path="batched", target=[gam], **ADAM_LP)
+    r2 = g.solve(base[None], path="batched", target=[gam],
+                 warm=(r1.lam, r1.mu_hi, r1.mu_lo), **ADAM_LP)
+    assert r2.status[0].item() == 0 and r2.iters[0].item() <= 2
+
+
+def test_batched_scenarios_and_outages_c0(c0):
+    net, base, on, g, gam = c0
+    B = 6
+    loads = synth.scenario_loads(base, B, 41)
+    cand = np.flatnonzero(~g.bridge_mask())
+    outage = -np.ones(B, dtype=np.int32)
+    outage[1], outage[4] = cand[0], cand[-1]
+    gams = []
+    onets = []
+    for b in range(B):
+        o = on if outage[b] < 0 else drop_line(net, outage[b])
+        onets.append(o)
+        gams.append(gamma(o, loads[b]))
+    res = g.solve(loads, outage=outage, path="batched", target=gams, **ADAM_LP)
+    for b in range(B):
+        k = outage[b]
+        keep = np.arange(on.n_line) != k
+        bnd = res.bound[b].item()
+        assert res.status[b].item() == 0
+        assert gams[b] * (1 - 1e-3) - 1e-9 <= bnd <= gams[b] * (1 + 1e-9)
+        mh = res.mu_hi[b].cpu().numpy()
+        ml = res.mu_lo[b].cpu().numpy()
+        if k >= 0:
+            mh, ml = mh[keep], ml[keep]
+        ref = dcopf.dual_value_prices(onets[b], loads[b], res.lam[b].item(), np.maximum(mh, 0),
+                                      np.maximum(ml, 0))
+        assert abs(bnd - ref) <= 1e-10 * abs(ref)
