@@ -1,0 +1,300 @@
+"""Benchmark: DCOPF instances reaching a certified 0.1 % dual gap per second.
+
+Workload: the synthetic 2000-bus network (3200 lines, 540 generators, quadratic
+costs; single instance at its base loads, stand-in for the paper's 2000-bus case).
+One step = one complete solve through the library: base flows, projected Adam
+ascent in the fused persistent kernel (FP32 operator products, FP64 value), FP64
+certification, until the certified bound is within 0.1 % of gamma* (the oracle's
+stored optimum, tests/golden/gamma.json).  The plain FP64 GPU path (Algorithm 1
+heavy-ball GDM, one launch per phase, cold start) is timed on the same instance.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DCOPF instances to 0.1% dual gap/sec on 1 GB300 vs plain FP64 GPU path"
+UNIT = "instances/s"
+GAP = 1e-3
+OURS = dict(rule="adam", alpha=1000.0, beta1=0.95, beta2=0.999, decay=0.999, max_iters=4000,
+            path="fused", precision="fp32")
+PLAIN = dict(rule="gdm", alpha=30.0, alpha_lambda=0.1, rho=0.995, max_iters=20000, path="plain",
+             precision="fp64", check_every=20)
+WORKLOAD = ("synthetic 2000-bus DCOPF, 3200 lines, 540 generators, quadratic costs, single "
+            "instance at base loads")
+# DRAM bytes per launch of the dominant kernel from ncu, valid only for the kernel
+# source with this digest (see profiles/); null when the kernel has changed since.
+NCU_TRAFFIC = {}
+
+
+def kernel_digest() -> str:
+    p = os.path.join(ROOT, "paper_2406_13191_gb300", "csrc", "k_fused.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def gamma_star():
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "gamma.json")))
+    return g["1/0"]["gamma"]
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                          f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sms, maxs, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                maxs.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs),
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def cpu_baseline(target_s=10.0):
+    """The oracle (plain FP64 numpy/scipy, one thread) solving the same instance with
+    the same ascent rule until its FP64 value is within 0.1 % of gamma*."""
+    from oracle import dcopf
+    from paper_2406_13191_gb300 import synth
+    net, base = synth.network_for(1)
+    on = dcopf.Net.from_dict(net.as_dict())
+    gam = gamma_star()
+    kw = {k: OURS[k] for k in ("rule", "alpha", "beta1", "beta2", "decay", "max_iters")}
+    n, iters = 0, []
+    t0 = time.perf_counter()
+    while True:
+        r = dcopf.solve(on, base, target=gam, gap=GAP, **kw)
+        iters.append(r["iters"])
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= target_s:
+            break
+    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} complete solves of the 2000-bus instance ({el:.1f} s, "
+                      f"{statistics.mean(iters):.0f} iterations each, single thread)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    a = ap.parse_args()
+    world, rank, local, dist = dist_setup(a.gpus)
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        for _ in range(a.warmup):
+            cpu_baseline(target_s=0.0)
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            cpu_baseline(target_s=0.0)
+        el = time.perf_counter() - t0
+        v = a.steps / el
+        cb = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"{a.steps} complete solves of the 2000-bus instance by the FP64 oracle"}
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+                          "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+                          "ms_per_step": 1e3 * el / a.steps, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": WORKLOAD},
+                          "cpu_baseline": cb,
+                          "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    import numpy as np
+    import torch
+    from paper_2406_13191_gb300 import DcopfDual, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    net, base = synth.network_for(1)
+    gam = gamma_star()
+    g = DcopfDual(net, device=local)
+    loads = torch.tensor(base[None], dtype=torch.float64, device=dev)
+    target = torch.tensor([gam], dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MiB)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def one(kw):
+        return g.solve(loads, target=target, gap=GAP, **kw)
+
+    for _ in range(a.warmup):
+        r = one(OURS)
+    assert r.status[0].item() == 0, "warm-up solve did not reach the gap"
+    g.set_timing(True)
+    g.read_timing()
+    launches0 = g.kernel_launches()
+    times, iters, bounds = [], [], []
+    barrier()
+    with Clocks(local) as clk:
+        for _ in range(a.steps):
+            flush.zero_()                       # L2 flushed between timed steps (untimed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = one(OURS)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            iters.append(r.iters[0].item())
+            bounds.append(r.bound[0].item())
+            assert r.status[0].item() == 0
+    barrier()
+    launches = g.kernel_launches() - launches0
+    it_ms, it_launches, evals = g.read_timing()
+    g.set_timing(False)
+    total_ms = sum(times)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    value = world * a.steps / (total_ms / 1e3)
+
+    # e2e: public API, pinned host inputs in, results read back to the host each step
+    loads_h = torch.tensor(base[None], dtype=torch.float64).pin_memory()
+    target_h = torch.tensor([gam], dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for _ in range(max(3, a.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = g.solve(loads_h, target=target_h, gap=GAP, **OURS)
+        out = (r.bound.cpu(), r.lam.cpu(), r.mu_hi.cpu(), r.mu_lo.cpu(), r.iters.cpu(), r.status.cpu())
+        e2e_times.append(time.perf_counter() - t0)
+    h2d = loads_h.numel() * 8 + 8
+    d2h = 8 + 8 + 2 * net.n_line * 8 + 4 + 4
+    e2e = {"value": world * len(e2e_times) / sum(e2e_times), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # the plain FP64 GPU path on the same instance (the metric's comparison)
+    pt, pit = [], []
+    for k in range(a.plain_steps + 1):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rp = one(PLAIN)
+        e1.record(stream)
+        e1.synchronize()
+        if k > 0:                               # first run is its warm-up
+            pt.append(e0.elapsed_time(e1))
+            pit.append(rp.iters[0].item())
+    plain = {"value": len(pt) / (sum(pt) / 1e3), "unit": UNIT, "ms_per_solve": statistics.mean(pt),
+             "iterations": statistics.mean(pit), "status": int(rp.status[0].item()),
+             "rule": "gdm (Algorithm 1, heavy ball)", "precision": "fp64", "launch": "one per phase"}
+
+    peaks, which = load_peaks()
+    nl, ng = net.n_line, net.n_gen
+    bytes_per_eval = 2 * 4 * nl * ng + nl * (12 * 4 + 3 * 4) + ng * 5 * 8
+    avg_launch_ms = it_ms / max(1, it_launches)
+    evals_per_launch = evals / max(1, it_launches)
+    achieved = bytes_per_eval * evals_per_launch / (avg_launch_ms * 1e-3) / 1e9
+    tr = NCU_TRAFFIC.get(kernel_digest())
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": tr, "peak_source": which,
+            "kernel": "k_fused_solve", "bytes_per_iteration": bytes_per_eval,
+            "iterations_per_launch": evals_per_launch, "us_per_iteration": 1e3 * it_ms / max(1, evals)}
+    if rank != 0:
+        return
+    cb = cpu_baseline(a.cpu_seconds) if world == 1 else None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_bus": net.n_bus, "n_line": nl, "n_gen": ng,
+                       "batch": 1, "gap": GAP, "rule": "adam", "path": "fused persistent kernel",
+                       "operator_precision": "fp32", "value_and_certificate": "fp64",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "iterations": statistics.mean(iters), "certified_gap": (gam - statistics.mean(bounds)) / gam,
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb,
+            "plain_fp64_gpu": plain, "speedup_vs_plain_fp64_gpu": value / plain["value"],
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

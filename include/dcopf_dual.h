@@ -212,6 +212,18 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
 /* Number of kernels this handle has launched since creation (for launch accounting). */
 int64_t dcopf_dual_kernel_launches(dcopf_dual_t h);
 
+/* Timing of the iteration kernels of dcopf_dual_solve_batch (the fused persistent
+ * kernel, or the per-iteration kernels of the plain and batched paths), measured
+ * with CUDA events recorded on the caller's stream around each launch group.
+ * enable != 0 switches it on (off by default; it adds no synchronisation). */
+dcopf_status dcopf_dual_set_timing(dcopf_dual_t h, int32_t enable);
+
+/* Reads and resets the accumulated timing: total milliseconds of the iteration
+ * kernels, the number of iteration-kernel launches, and the dual evaluations they
+ * performed summed over instances.  Host pointers; NULL outputs are skipped. */
+dcopf_status dcopf_dual_read_timing(dcopf_dual_t h, double* iter_ms, int64_t* iter_launches,
+                                    int64_t* evaluations);
+
 /* Sticky device-side error word of the handle's last solve (0 = none, else a
  * dcopf_status value such as DCOPF_ERR_TIMEOUT).  Synchronises the device. */
 dcopf_status dcopf_dual_device_error(dcopf_dual_t h);

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <vector>
 
 #include "dcopf_dual.h"
 #include "kernels.h"
@@ -14,6 +15,8 @@ dcopf_dual::~dcopf_dual() {
   for (auto* b : owned) delete b;
   if (d_err) cudaFree(d_err);
   if (d_bar) cudaFree(d_bar);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
 }
 
 namespace dcopf {
@@ -201,7 +204,13 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
   int* d_active = h->active.as<int>();
   const int chunk = std::max(1, p.check_every);
   const double ub_any = h->ub_any;
+  if (h->timing && !h->ev0) {
+    CUDA_TRY(h, cudaEventCreate(&h->ev0));
+    CUDA_TRY(h, cudaEventCreate(&h->ev1));
+  }
   for (int round = 0;; ++round) {
+    long long launches_before = h->launches;
+    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev0, s));
     if constexpr (sizeof(S) == 4) {
       if (path == DCOPF_PATH_FUSED) r = run_iters_fused(h, P, st, p.max_iters, p.tol, s);
     }
@@ -210,6 +219,8 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
       r = run_iters_unfused<S>(h, B, outage, prec, P, st, chunk, p.max_iters, p.tol, s);
     }
     if (r) return r;
+    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev1, s));
+    long long iter_launches = h->launches - launches_before;
     r = run_certify_t<S>(h, B, loads, outage, st.best_lam, st.best_hi, st.best_lo, st.cert, nullptr,
                          st.cand, st.done, s);
     if (r) return r;
@@ -219,6 +230,12 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
     int active = 0;
     CUDA_TRY(h, cudaMemcpyAsync(&active, d_active, sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
+    if (h->timing) {
+      float ms = 0.f;
+      CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+      h->t_iter_ms += ms;
+      h->t_iter_launches += iter_launches;
+    }
     int derr = 0;
     CUDA_TRY(h, cudaMemcpy(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (derr) return (dcopf_status)derr;
@@ -230,6 +247,11 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
   h->launches += 1;
   CUDA_TRY(h, cudaGetLastError());
   CUDA_TRY(h, cudaStreamSynchronize(s));
+  if (h->timing) {
+    std::vector<int> it(B);
+    CUDA_TRY(h, cudaMemcpy(it.data(), st.iter, sizeof(int) * B, cudaMemcpyDeviceToHost));
+    for (int v : it) h->t_evals += v;
+  }
   return DCOPF_OK;
 }
 
@@ -336,6 +358,14 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
   UP(H.ctil, ctil) UP(H.mq, mq) UP(H.cconst, cconst) UP(sig32, sigma32) UP(ctil32, ctil32)
   UP(mq32, mq32) UP(H.phi, phi64) UP(phit, phit64) UP(phi32, phi32) UP(phit32, phit32)
 #undef UP
+  if (!H.F.blob.empty()) {
+    if ((st = upload(h, H.F.blob, &D.fac_blob)) != DCOPF_OK) { delete h; return st; }
+    D.fac_bytes = (int)H.F.blob.size();
+    D.off_diag = H.F.off_diag; D.off_val = H.F.off_val; D.off_rptr = H.F.off_rptr;
+    D.off_cptr = H.F.off_cptr; D.off_rcol = H.F.off_rcol; D.off_crow = H.F.off_crow;
+    D.off_cmap = H.F.off_cmap; D.off_frows = H.F.off_frows; D.off_brows = H.F.off_brows;
+    D.off_flev = H.F.off_flev; D.off_blev = H.F.off_blev;
+  }
   if (cudaMalloc(&h->d_err, 16) != cudaSuccess || cudaMalloc(&h->d_bar, 64) != cudaSuccess ||
       cudaMemset(h->d_err, 0, 16) != cudaSuccess || cudaMemset(h->d_bar, 0, 64) != cudaSuccess) {
     delete h;
@@ -485,6 +515,24 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
 }
 
 int64_t dcopf_dual_kernel_launches(dcopf_dual_t h) { return h ? (int64_t)h->launches : 0; }
+
+dcopf_status dcopf_dual_set_timing(dcopf_dual_t h, int32_t enable) {
+  if (!h) return DCOPF_ERR_INVALID_ARG;
+  h->timing = enable != 0;
+  return DCOPF_OK;
+}
+
+dcopf_status dcopf_dual_read_timing(dcopf_dual_t h, double* iter_ms, int64_t* iter_launches,
+                                    int64_t* evaluations) {
+  if (!h) return DCOPF_ERR_INVALID_ARG;
+  if (iter_ms) *iter_ms = h->t_iter_ms;
+  if (iter_launches) *iter_launches = h->t_iter_launches;
+  if (evaluations) *evaluations = h->t_evals;
+  h->t_iter_ms = 0.0;
+  h->t_iter_launches = 0;
+  h->t_evals = 0;
+  return DCOPF_OK;
+}
 
 dcopf_status dcopf_dual_device_error(dcopf_dual_t h) {
   if (!h) return DCOPF_ERR_INVALID_ARG;

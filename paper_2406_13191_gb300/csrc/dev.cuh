@@ -23,6 +23,10 @@ struct DevNet {
   const double* diag;
   const int* fwd_rows; const int* fwd_lev; int n_fwd_lev;
   const int* bwd_rows; const int* bwd_lev; int n_bwd_lev;
+  // packed copy of the factor for shared-memory staging (nullptr when unavailable)
+  const unsigned char* fac_blob; int fac_bytes;
+  int off_diag, off_val, off_rptr, off_cptr, off_rcol, off_crow, off_cmap, off_frows, off_brows,
+      off_flev, off_blev;
   // lines
   const int* line_from; const int* line_to;
   const double* line_b;

@@ -26,6 +26,11 @@ struct SparseFactor {
   std::vector<int> fwd_rows, fwd_level_ptr;
   std::vector<int> bwd_rows, bwd_level_ptr;
   int64_t nnz() const { return (int64_t)lrow_col.size(); }
+  // Packed copy for shared-memory staging (empty when indices do not fit 16 bits):
+  // 16-byte aligned sections at the byte offsets below.
+  std::vector<unsigned char> blob;
+  int off_diag = 0, off_val = 0, off_rptr = 0, off_cptr = 0, off_rcol = 0, off_crow = 0,
+      off_cmap = 0, off_frows = 0, off_brows = 0, off_flev = 0, off_blev = 0;
 };
 
 // Validated copy of the network plus everything derived from it on the host.

@@ -1,27 +1,38 @@
 // Fused persistent solve of one instance: every iteration of the projected dual
 // ascent (Section 3.3, Algorithm 1 and the Adam / AdaGrad rules) runs inside one
-// cooperative kernel with one CTA per SM.
+// kernel whose CTAs (one per SM) form thread-block clusters of C CTAs.
 //
 // Data placement: CTA c owns a contiguous block of lines (rows of Phi~), keeps those
-// rows of Phi~ (FP32) in shared memory for the whole solve, and owns the dual state
-// of its lines (mu_hi, mu_lo, optimiser moments).  lambda and its moments are
-// replicated in every CTA and updated identically.
+// rows (FP32) in shared memory for the whole solve, and owns the dual state of its
+// lines (mu_hi, mu_lo, optimiser moments).  lambda and its moments are replicated in
+// every CTA and updated identically (same inputs, same order).
 //
-// Iteration t (all CTAs):
-//   A  eta = mu_hi - mu_lo on own rows; partial adjoint Phi~_c^T eta_c for all gens
-//      -> Pp[j][c]                                   (eq. (6): C^T mu)
-//   -- grid barrier 1 --
-//   B  value of evaluation t-1 (sums of the per-CTA FP64 partials in a fixed order,
-//      identical in every CTA) -> best-point tracking and the stop tests;
-//      gens slice of CTA c: pi~_j = sum_c Pp[j][c], closed-form x*_j (eq. (6)/(16))
-//      -> X[j], partial cost and dispatch sums -> Q[c]
-//   -- grid barrier 2 --
-//   C  forward f = Phi~_c X + f0 on own rows (constraint (1c)); supergradient and the
-//      line part of the value -> R[c]; projected step of own mu and of lambda.
-// The value of evaluation t is complete only after barrier 1 of iteration t+1, so
-// the best point is taken from a copy of the previous iterate.
+// Iteration (all CTAs):
+//   A   eta = mu_hi - mu_lo on own rows; partial adjoint Phi~_c^T eta_c for all gens
+//       into own shared memory                                (eq. (6): C^T mu)
+//   A2  [cluster sync] CTA r of a cluster sums gens slice S_r over the cluster's
+//       partials through distributed shared memory -> Pc[j][cluster]
+//   --  grid barrier (cluster leaders only; bounded wait)
+//   B   every cluster reads Pc for its slices (one coalesced pass, L2 only), sums the
+//       clusters in a fixed order, takes the closed-form minimiser x*_j (eq. (6) /
+//       eq. (16)) and partial cost / dispatch sums; the FP64 line partials R of the
+//       previous evaluation complete its dual value -> best point, stop tests
+//   C   [cluster sync] gather x* of all gens from the cluster's CTAs (DSMEM); forward
+//       f = Phi~_c x* + f0 on own rows (constraint (1c)); supergradient; FP64 line
+//       partial -> R[c]; projected step of own mu and of lambda
+// Every cluster computes the same x* from the same data in the same order, so one
+// grid-wide barrier per iteration suffices.  Pc and R are double-buffered by the
+// parity of the loop iteration: a cluster can only be one barrier ahead of another,
+// so a buffer is rewritten only after every reader has passed the next barrier.  The value of an evaluation is complete
+// one iteration later; the best point is copied from the previous iterate.
+#include <cooperative_groups.h>
+
+#include <cstdio>
+
 #include "dev.cuh"
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace dcopf {
 
@@ -31,17 +42,17 @@ struct FusedArgs {
   SolveState<float> st;
   const float* f0;        // [n_line]
   double demand;
-  float* Pp;              // [n_gen][G]
-  float* X;               // [n_gen]
-  double* Q;              // [G][2]
-  double* R;              // [G]
+  float* Pc;              // [2][n_gen][n_clusters rounded up to 4] (parity of the loop iteration)
+  double* R;              // [2][G]
   unsigned* bar;
   int* err;
   int max_iters;
   double tol;
   int rows_per_cta;
-  int gens_per_cta;
+  int slice;              // gens per cluster rank
   int phi_in_smem;
+  int C, G;               // launch shape the shared-memory layout was sized for
+  unsigned smem_bytes;    // dynamic shared memory the layout needs
   uint64_t timeout_ns;
 };
 
@@ -63,29 +74,106 @@ __device__ __forceinline__ S fused_rule(const StepArgs& P, S theta, S g, S& s1, 
   return theta;
 }
 
+// Barrier over all clusters: every thread publishes its global writes, the cluster
+// synchronises, its leader arrives on the grid counter and waits (bounded), and the
+// cluster synchronises again.  Returns false (and records DCOPF_ERR_TIMEOUT) when the
+// wait gave up; the result is identical in every CTA of the cluster.
+__device__ __forceinline__ bool cluster_grid_barrier(cg::cluster_group& cl, unsigned* counter,
+                                                     unsigned n_clusters, unsigned& epoch, int* err,
+                                                     uint64_t timeout_ns, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) __threadfence();  // cumulative: covers the CTA's writes ordered by bar.sync
+  cl.sync();
+  epoch += 1;
+  if (cl.block_rank() == 0 && threadIdx.x == 0) {
+    const unsigned target = epoch * n_clusters;
+    atomicAdd(counter, 1u);
+    int ok = 1;
+    uint64_t t0 = 0;
+    int spins = 0;
+    while ((int)(ld_acquire_u32(counter) - target) < 0) {
+      if (++spins == 32) t0 = global_ns();
+      if (spins > 32 && (spins & 127) == 0) {
+        if (global_ns() - t0 > timeout_ns) { atomicExch(err, (int)DCOPF_ERR_TIMEOUT); ok = 0; break; }
+        if (ld_relaxed_s32(err) != 0) { ok = 0; break; }
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  cl.sync();
+  return *cl.map_shared_rank(s_ok, 0) != 0;
+}
+
+// Sums two values over the block in one pass (fixed tree); every thread gets both.
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0) { sh[w] = a; sh[16 + w] = b; }
+  __syncthreads();
+  double x = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  double y = (threadIdx.x < nw) ? sh[16 + threadIdx.x] : 0.0;
+  if (w == 0) { x = warp_sum(x); y = warp_sum(y); }
+  if (threadIdx.x == 0) { sh[0] = x; sh[16] = y; }
+  __syncthreads();
+  a = sh[0];
+  b = sh[16];
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
   const DevNet& N = A.N;
   const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x;
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int NCL = G / C, cid = c / C;
+  const int NCLp = (NCL + 3) & ~3;  // Pc row stride: float4-aligned rows
   const int nl = N.n_line, ng = N.n_gen;
   const int r0 = min(nl, c * A.rows_per_cta), r1 = min(nl, r0 + A.rows_per_cta);
   const int nr = r1 - r0;
-  const int j0 = min(ng, c * A.gens_per_cta), j1 = min(ng, j0 + A.gens_per_cta);
-  // shared memory carve-up
-  float* xs = (float*)smem_raw;                                  // [ng]
-  float* row = xs + ((ng + 3) & ~3);                             // per-row arrays, 12 x rpc
+  const int SL = A.slice;
+  const int j0 = min(ng, rank * SL), j1 = min(ng, j0 + SL);
+  const int ngp = (ng + 3) & ~3;
   const int rpc = A.rows_per_cta;
+  // The layout below was sized on the host for (A.C, A.G); refuse any other shape.
+  {
+    unsigned dyn;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    if (C != A.C || G != A.G || dyn < A.smem_bytes || C > 8) {
+      if (tid == 0) atomicExch(A.err, (int)DCOPF_ERR_UNSUPPORTED);
+      return;
+    }
+  }
+  // shared memory carve-up: per-slice generator constants (FP64), then floats
+  double* gk = (double*)smem_raw;                // [5][SLp] ctil, sigma, mq, cconst, mid
+  const int SLp = (SL + 1) & ~1;
+  float* pp = (float*)(gk + 5 * SLp);            // [ngp] partial adjoint of own rows
+  float* xs = pp + ngp;                          // [ngp] x* of all gens (gathered)
+  float* xsl = xs + ngp;                         // [SL]  x* of own slice (read by peers)
+  float* pis = xsl + ((SL + 3) & ~3);            // [SL]  pi~ of own slice
+  float* tmp = pis + ((SL + 3) & ~3);            // [SL * NCLp] cluster partials of own slice
+  float* row = tmp + SL * NCLp;                  // per-row arrays, 12 x rpc
   float *eta = row, *mh = row + rpc, *ml = row + 2 * rpc, *h1 = row + 3 * rpc, *h2 = row + 4 * rpc,
         *l1 = row + 5 * rpc, *l2 = row + 6 * rpc, *ph = row + 7 * rpc, *pl = row + 8 * rpc,
         *fmx = row + 9 * rpc, *fmn = row + 10 * rpc, *f0 = row + 11 * rpc;
-  float* phis = row + 12 * rpc;                                  // [rpc][ng] when resident
+  float* phis = row + 12 * rpc;                  // [rpc][ng] when resident
   __shared__ double red[32];
-  __shared__ double s_lam[4];  // lam, s1, s2, lam_prev
-  __shared__ int s_stop;
+  __shared__ double s_lam[4];   // lam, s1, s2, lam at the pending evaluation
+  __shared__ double s_cs[2];    // cost / dispatch sums of own slice
+  __shared__ double s_pw[6];    // decay^(t-1), 1 - beta1^t, 1 - beta2^t; running powers
+  __shared__ int s_ok;
 
   const float* phi = A.phi_in_smem ? phis : (N.phi32 + (size_t)r0 * ng);
   if (A.phi_in_smem)
     for (int q = tid; q < nr * ng; q += blockDim.x) phis[q] = N.phi32[(size_t)r0 * ng + q];
+  for (int jj = tid; jj < j1 - j0; jj += blockDim.x) {
+    const int j = j0 + jj;
+    gk[jj] = N.ctil[j]; gk[SLp + jj] = N.sigma[j]; gk[2 * SLp + jj] = N.mq[j];
+    gk[3 * SLp + jj] = N.cconst[j]; gk[4 * SLp + jj] = N.mid[j];
+  }
   SolveState<float>& st = A.st;
   for (int r = tid; r < nr; r += blockDim.x) {
     int i = r0 + r;
@@ -95,7 +183,12 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   }
   if (tid == 0) {
     s_lam[0] = st.lam[0]; s_lam[1] = st.lam_s1[0]; s_lam[2] = st.lam_s2[0]; s_lam[3] = st.lam[0];
-    s_stop = 0;
+    // running powers decay^t, beta1^t, beta2^t at the evaluation count of the state
+    // (one pow each per launch; FP64 pow is slow on this part)
+    const double t0 = (double)st.iter[0];
+    s_pw[3] = pow(A.P.decay, t0);
+    s_pw[4] = pow(A.P.beta1, t0);
+    s_pw[5] = pow(A.P.beta2, t0);
   }
   double best = st.best[0];
   double prev_val = st.prev[0];
@@ -103,83 +196,125 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   int best_iter = st.best_iter[0];
   double best_lam = st.best_lam[0];
   int cand = 0;
-  bool pending = false;         // an evaluation whose value is not yet assembled
+  bool pending = false;
   double cost_t = 0.0, psum_t = 0.0;
   unsigned epoch = 0;
+  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   __syncthreads();
 
-  for (;;) {
-    // ---------------- phase A: partial adjoint over own rows
+  for (unsigned k = 0;; ++k) {
+    float* Pc = A.Pc + (size_t)(k & 1u) * ng * NCLp;
+    const double* Rprev = A.R + (size_t)((k + 1u) & 1u) * G;   // written in loop k-1
+    double* Rcur = A.R + (size_t)(k & 1u) * G;
+    // ---------------- A: partial adjoint of own rows into shared memory
     for (int r = tid; r < nr; r += blockDim.x) eta[r] = mh[r] - ml[r];
     __syncthreads();
     for (int j = tid; j < ng; j += blockDim.x) {
       float s = 0.f;
       for (int r = 0; r < nr; ++r) s = fmaf(phi[(size_t)r * ng + j], eta[r], s);
-      A.Pp[(size_t)j * G + c] = s;
+      pp[j] = s;
     }
-    if (!grid_barrier(A.bar, G, epoch, A.err, A.timeout_ns)) break;
-    // ---------------- phase B: value of the pending evaluation, stop tests
-    if (pending) {
-      double lsum = 0.0;
-      for (int q = tid; q < G; q += blockDim.x) lsum += A.R[q];
-      // fixed-order reduction: identical in every CTA
-      lsum = block_sum(lsum, red);
-      double lamp = s_lam[3];
-      double val = cost_t + lamp * (psum_t - A.demand) + lsum;
-      bool better = val > best;
-      if (better) {
-        best = val; best_lam = lamp; best_iter = t;
-        for (int r = tid; r < nr; r += blockDim.x) { st.best_hi[r0 + r] = ph[r]; st.best_lo[r0 + r] = pl[r]; }
+    cl.sync();
+    // ---------------- A2: cluster sum of own slice (fixed rank order) -> Pc
+    for (int j = j0 + tid; j < j1; j += blockDim.x) {
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = q < C ? cl.map_shared_rank(pp, q)[j] : 0.f;  // issued together
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s += v[q];  // fixed rank order
+      Pc[(size_t)j * NCLp + cid] = s;
+    }
+    if (!cluster_grid_barrier(cl, A.bar, NCL, epoch, A.err, A.timeout_ns, &s_ok)) break;
+    // ---------------- B: one batched read of the slice's cluster partials and of R
+    {
+      const int n4 = (j1 - j0) * NCLp / 4;
+      const float4* src = (const float4*)(Pc + (size_t)j0 * NCLp);
+      double rv = 0.0;
+      if (pending && tid < G) rv = __ldcg(Rprev + tid);   // G <= blockDim.x (checked on host)
+      // all loads of a batch are issued before any store, so a batch costs one round trip
+      for (int base = 0; base < n4; base += 8 * (int)blockDim.x) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int q = base + u * blockDim.x + tid;
+          if (q < n4) v[u] = __ldcg(src + q);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int q = base + u * blockDim.x + tid;
+          if (q < n4) ((float4*)tmp)[q] = v[u];
+        }
       }
-      if (st.has_target && best >= st.thresh[0] + st.margin[0]) cand = 1;
-      if (t >= A.max_iters) cand = 2;
-      if (A.tol > 0.0 && t > 1 && fabs(val - prev_val) < A.tol) cand = 2;
-      if (best > 1e300) cand = 2;
-      prev_val = val;
-      pending = false;
-      if (cand) break;
+      if (pending) {
+        const double lsum = block_sum(rv, red);
+        const double lamp = s_lam[3];
+        const double val = cost_t + lamp * (psum_t - A.demand) + lsum;
+        if (val > best) {
+          best = val; best_lam = lamp; best_iter = t;
+          for (int r = tid; r < nr; r += blockDim.x) { st.best_hi[r0 + r] = ph[r]; st.best_lo[r0 + r] = pl[r]; }
+        }
+        if (st.has_target && best >= st.thresh[0] + st.margin[0]) cand = 1;
+        if (t >= A.max_iters) cand = 2;
+        if (A.tol > 0.0 && t > 1 && fabs(val - prev_val) < A.tol) cand = 2;
+        prev_val = val;
+        pending = false;
+      }
+      __syncthreads();
     }
-    // gens slice: reduce partials, closed-form minimiser
+    if (cand) break;  // uniform: every CTA assembled the same value
     {
       const double lam = s_lam[0];
       double cs = 0.0, ps = 0.0;
-      const int nj = j1 - j0;
-      // (gen, part) pairs spread over the whole block; 8 lanes per gen
-      const int lanes_per = 8;
-      for (int base = 0; base < nj * lanes_per; base += blockDim.x) {
-        int q = base + tid;
-        int jj = q / lanes_per, part = q % lanes_per;
+      // one thread per generator of the slice: sum the clusters in a fixed order
+      // (identical in every cluster), then the closed-form minimiser; the w that
+      // cancels (ctil + sigma lambda + pi~) is formed in FP64
+      for (int jj = tid; jj < j1 - j0; jj += blockDim.x) {
+        const float4* tp = (const float4*)(tmp + jj * NCLp);
         float s = 0.f;
-        if (jj < nj)
-          for (int cc = part; cc < G; cc += lanes_per) s += A.Pp[(size_t)(j0 + jj) * G + cc];
-        // reduce the 8 lanes of this gen (aligned groups of 8 inside a warp)
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        s += __shfl_xor_sync(0xffffffffu, s, 4);
-        if (jj < nj && part == 0) {
-          int j = j0 + jj;
-          double w = N.ctil[j] + N.sigma[j] * lam + (double)s;
-          double x = inner_x<double>(w, N.mq[j]);
-          A.X[j] = (float)x;
-          cs += (N.mq[j] * x + N.ctil[j]) * x + N.cconst[j];
-          ps += N.mid[j] + N.sigma[j] * x;
+        for (int q = 0; q < NCLp / 4; ++q) {  // padding entries are never read: NCLp - NCL < 4
+          const float4 v = tp[q];
+          const int b4 = 4 * q;
+          s += v.x;
+          if (b4 + 1 < NCL) s += v.y;
+          if (b4 + 2 < NCL) s += v.z;
+          if (b4 + 3 < NCL) s += v.w;
         }
+        const double ct = gk[jj], sg = gk[SLp + jj], mq = gk[2 * SLp + jj];
+        const double w = ct + sg * lam + (double)s;
+        const float x = inner_x<float>((float)w, (float)mq);
+        xsl[jj] = x;
+        const double xd = (double)x;
+        cs += (mq * xd + ct) * xd + gk[3 * SLp + jj];
+        ps += gk[4 * SLp + jj] + sg * xd;
       }
-      cs = block_sum(cs, red);
-      ps = block_sum(ps, red);
-      if (tid == 0) { A.Q[2 * c] = cs; A.Q[2 * c + 1] = ps; }
+      block_sum2(cs, ps, red);
+      if (tid == 0) { s_cs[0] = cs; s_cs[1] = ps; }
     }
-    if (!grid_barrier(A.bar, G, epoch, A.err, A.timeout_ns)) break;
-    // ---------------- phase C: forward on own rows, supergradient, step
-    for (int j = tid; j < ng; j += blockDim.x) xs[j] = A.X[j];
-    {
+    cl.sync();
+    // ---------------- C: gather x*, forward on own rows, supergradient, step
+    for (int j = tid; j < ng; j += blockDim.x) {
+      int q = j / SL;
+      xs[j] = cl.map_shared_rank(xsl, q)[j - q * SL];
+    }
+    if (tid == 0) {
+      double cv[8], pv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const double* o = cl.map_shared_rank(s_cs, q < C ? q : 0);
+        cv[q] = q < C ? o[0] : 0.0;
+        pv[q] = q < C ? o[1] : 0.0;
+      }
       double cs = 0.0, ps = 0.0;
-      for (int q = tid; q < G; q += blockDim.x) { cs += A.Q[2 * q]; ps += A.Q[2 * q + 1]; }
-      cost_t = block_sum(cs, red);
-      psum_t = block_sum(ps, red);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { cs += cv[q]; ps += pv[q]; }
+      red[0] = cs;
+      red[1] = ps;
     }
     __syncthreads();
-    const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    cost_t = red[0];
+    psum_t = red[1];
+    __syncthreads();
     for (int r = warp; r < nr; r += nw) {
       float s = 0.f;
       const float* pr = phi + (size_t)r * ng;
@@ -189,10 +324,30 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     }
     __syncthreads();
     t += 1;
-    const float scale = (float)pow(A.P.decay, (double)(t - 1));
-    const float bc1 = (float)(1.0 - pow(A.P.beta1, (double)t));
-    const float bc2 = (float)(1.0 - pow(A.P.beta2, (double)t));
-    const float am = (float)(A.P.alpha * scale);
+    if (tid == 0) {  // step-size factors of step t from the running powers
+      s_pw[0] = s_pw[3];
+      s_pw[4] *= A.P.beta1;
+      s_pw[5] *= A.P.beta2;
+      s_pw[3] *= A.P.decay;
+      s_pw[1] = 1.0 - s_pw[4];
+      s_pw[2] = 1.0 - s_pw[5];
+    }
+    __syncthreads();
+    const float bc1 = (float)s_pw[1];
+    const float bc2 = (float)s_pw[2];
+    const float am = (float)(A.P.alpha * s_pw[0]);
+    if (tid == 32) {
+      // lambda step, concurrent with the line steps: the direction in FP32, the
+      // update of lambda in FP64
+      double lam = s_lam[0];
+      s_lam[3] = lam;
+      float s1 = (float)s_lam[1], s2 = (float)s_lam[2];
+      const float al = (float)(A.P.alpha_lambda * s_pw[0]);
+      const float gl = (float)(psum_t - A.demand);
+      const float th = fused_rule<float>(A.P, 0.f, gl, s1, s2, al, bc1, bc2);
+      lam += (double)th;
+      s_lam[0] = lam; s_lam[1] = s1; s_lam[2] = s2;
+    }
     double lacc = 0.0;
     for (int r = tid; r < nr; r += blockDim.x) {
       float f = eta[r];
@@ -206,21 +361,12 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       ml[r] = nlo > 0.f ? nlo : 0.f;
     }
     lacc = block_sum(lacc, red);
-    if (tid == 0) {
-      A.R[c] = lacc;
-      double lam = s_lam[0], s1 = s_lam[1], s2 = s_lam[2];
-      s_lam[3] = lam;
-      double al = A.P.alpha_lambda * (double)pow(A.P.decay, (double)(t - 1));
-      double gl = psum_t - A.demand;
-      lam = fused_rule<double>(A.P, lam, gl, s1, s2, al, 1.0 - pow(A.P.beta1, (double)t),
-                               1.0 - pow(A.P.beta2, (double)t));
-      s_lam[0] = lam; s_lam[1] = s1; s_lam[2] = s2;
-    }
+    if (tid == 0) Rcur[c] = lacc;
     pending = true;
     __syncthreads();
   }
-  // ---------------- write back (resumable state)
-  __syncthreads();
+  // ---------------- write back (resumable state); peers may still read our smem
+  cl.sync();
   for (int r = tid; r < nr; r += blockDim.x) {
     int i = r0 + r;
     st.mu_hi[i] = mh[r]; st.mu_lo[i] = ml[r];
@@ -235,31 +381,122 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   }
 }
 
+// Largest cluster shape the device can keep resident with one CTA per SM.
+struct FusedShape {
+  int C = 0, G = 0;
+  size_t smem = 0;
+  int phi_in_smem = 0;
+  int rows_per_cta = 0, slice = 0;
+};
+
+static size_t fused_smem(int ng, int rpc, int C, int NCL, bool phi) {
+  int ngp = (ng + 3) & ~3;
+  int SL = (ng + C - 1) / C;
+  int SLp = (SL + 1) & ~1;
+  int NCLp = (NCL + 3) & ~3;
+  size_t f = 2 * (size_t)ngp + 2 * ((SL + 3) & ~3) + (size_t)SL * NCLp + 12 * (size_t)rpc;
+  if (phi) f += (size_t)rpc * ng;
+  return f * sizeof(float) + 5 * (size_t)SLp * sizeof(double);
+}
+
+static cudaError_t fused_config(const dcopf_dual* h, int C, FusedShape* out) {
+  const int nl = h->dev.n_line, ng = h->dev.n_gen;
+  const int sms = h->sm_count;
+  for (int pass = 0; pass < 2; ++pass) {
+    // pass 0: assume all SMs usable; pass 1: use the occupancy answer
+    int G = (sms / C) * C;
+    if (G < C) return cudaErrorInvalidValue;
+    int rpc = (nl + G - 1) / G;
+    bool phi = fused_smem(ng, rpc, C, G / C, true) + 2048 <= h->smem_optin;
+    size_t smem = fused_smem(ng, rpc, C, G / C, phi);
+    if (smem + 2048 > h->smem_optin) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_fused_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    if (C > 8) cudaFuncSetAttribute(k_fused_solve, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    e = cudaOccupancyMaxActiveClusters(&ncl, k_fused_solve, &cfg);
+    if (e != cudaSuccess) return e;
+    if (ncl * C >= G) {
+      out->C = C; out->G = G; out->smem = smem; out->phi_in_smem = phi ? 1 : 0;
+      out->rows_per_cta = rpc; out->slice = (ng + C - 1) / C;
+      return cudaSuccess;
+    }
+    if (ncl < 1) return cudaErrorInvalidValue;
+    // fewer clusters fit: shrink the grid to what is resident
+    int G2 = ncl * C;
+    rpc = (nl + G2 - 1) / G2;
+    phi = fused_smem(ng, rpc, C, ncl, true) + 2048 <= h->smem_optin;
+    smem = fused_smem(ng, rpc, C, ncl, phi);
+    if (smem + 2048 > h->smem_optin) return cudaErrorInvalidValue;
+    out->C = C; out->G = G2; out->smem = smem; out->phi_in_smem = phi ? 1 : 0;
+    out->rows_per_cta = rpc; out->slice = (ng + C - 1) / C;
+    return cudaFuncSetAttribute(k_fused_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  return cudaErrorInvalidValue;
+}
+
 dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>& st, int max_iters,
                              double tol, cudaStream_t s) {
   const DevNet& N = h->dev;
-  const int G = h->sm_count;
-  const int nl = N.n_line, ng = N.n_gen;
+  const int ng = N.n_gen;
+  if (h->fused_C == 0) {
+    // pick the cluster size that keeps the most SMs busy (ties: larger clusters)
+    // Per iteration a CTA reduces (n_gen / C) generators over G / C cluster partials,
+    // so larger clusters cut that work; accept a larger cluster unless it leaves
+    // more than 1/8 of the SMs idle.
+    FusedShape best;
+    for (int C : {8, 4, 2, 1}) {
+      FusedShape sh;
+      if (fused_config(h, C, &sh) != cudaSuccess) continue;
+      if (h->verbose)
+        fprintf(stderr, "[dcopf] fused candidate: cluster %d, %d CTAs resident\n", C, sh.G);
+      if (best.G == 0 || 8 * sh.G > 9 * best.G) best = sh;
+    }
+    cudaGetLastError();
+    if (best.G == 0) return DCOPF_ERR_UNSUPPORTED;
+    h->fused_C = best.C;
+    h->fused_G = best.G;
+    if (h->verbose)
+      fprintf(stderr, "[dcopf] fused kernel: cluster %d x %d CTAs, %zu B shared, Phi rows %s, %d rows/CTA\n",
+              best.G / best.C, best.C, best.smem, best.phi_in_smem ? "resident" : "streamed",
+              best.rows_per_cta);
+  }
+  FusedShape sh;
+  if (fused_config(h, h->fused_C, &sh) != cudaSuccess || sh.G != h->fused_G) {
+    cudaGetLastError();
+    return DCOPF_ERR_UNSUPPORTED;
+  }
+  const int G = sh.G, C = sh.C, NCL = G / C;
   FusedArgs A{};
   A.N = N;
   A.P = P;
   A.st = st;
   A.f0 = h->ws.f0_32.as<float>();
-  A.rows_per_cta = (nl + G - 1) / G;
-  A.gens_per_cta = (ng + G - 1) / G;
-  size_t base = (size_t)(((ng + 3) & ~3) + 12 * A.rows_per_cta) * sizeof(float);
-  size_t phi_bytes = (size_t)A.rows_per_cta * ng * sizeof(float);
-  A.phi_in_smem = (base + phi_bytes + 4096 <= h->smem_optin) ? 1 : 0;
-  size_t smem = base + (A.phi_in_smem ? phi_bytes : 0);
-  if (smem + 1024 > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
-  // scratch: Pp [ng][G] f32, X [ng] f32, Q [G][2] f64, R [G] f64, demand read back below
-  size_t need = (size_t)ng * G * 4 + (size_t)ng * 4 + 256 + (size_t)G * 24 + 256;
-  if (h->ws.misc.alloc(need) != cudaSuccess) return DCOPF_ERR_OOM;
+  A.rows_per_cta = sh.rows_per_cta;
+  A.slice = sh.slice;
+  A.phi_in_smem = sh.phi_in_smem;
+  A.C = C;
+  A.G = G;
+  A.smem_bytes = (unsigned)sh.smem;
+  const int NCLp = (NCL + 3) & ~3;
+  size_t pc_bytes = ((size_t)2 * ng * NCLp * 4 + 255) & ~(size_t)255;
+  if (G > 256) return DCOPF_ERR_UNSUPPORTED;  // R is read with one thread per CTA
+  if (h->ws.misc.alloc(pc_bytes + (size_t)2 * G * 8 + 256) != cudaSuccess) return DCOPF_ERR_OOM;
   char* m = h->ws.misc.as<char>();
-  A.Pp = (float*)m;
-  A.X = (float*)(m + (size_t)ng * G * 4);
-  A.Q = (double*)(m + (((size_t)ng * G * 4 + (size_t)ng * 4 + 255) & ~(size_t)255));
-  A.R = A.Q + 2 * G;
+  A.Pc = (float*)m;
+  A.R = (double*)(m + pc_bytes);
   A.bar = h->d_bar;
   A.err = h->d_err;
   A.max_iters = max_iters;
@@ -271,15 +508,33 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
       cudaStreamSynchronize(s) != cudaSuccess)
     return DCOPF_ERR_CUDA;
   A.demand = demand;
-  if (cudaFuncSetAttribute(k_fused_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return DCOPF_ERR_CUDA;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_solve, 256, smem);
-  if (per_sm < 1) return DCOPF_ERR_UNSUPPORTED;
   if (cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned), s) != cudaSuccess) return DCOPF_ERR_CUDA;
-  void* args[] = {&A};
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_fused_solve, G, 256, args, smem, s);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = sh.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeCooperative;
+  at[1].val.cooperative = 1;
+  cfg.attrs = at;
+  // Co-residency of all clusters: requested from the driver (cooperative launch) when
+  // it accepts that together with clusters; otherwise the grid is sized from
+  // cudaOccupancyMaxActiveClusters and the barrier's bounded wait is the guard.
+  cfg.numAttrs = h->fused_coop == 0 ? 1 : 2;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_fused_solve, A);
+  if (e != cudaSuccess && cfg.numAttrs == 2) {
+    cudaGetLastError();
+    h->fused_coop = 0;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_fused_solve, A);
+  } else if (e == cudaSuccess && cfg.numAttrs == 2) {
+    h->fused_coop = 1;
+  }
   h->launches += 1;
   if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
   return DCOPF_OK;

@@ -39,19 +39,19 @@ __global__ void k_eta(int nl, const S* __restrict__ mh, const S* __restrict__ ml
   }
 }
 
-// pit[b][j] = sum_i Phi~[i][j] eta[b][i]; one warp per (b, j) over row j of Phi~^T.
+// pit[b][j] = sum_i Phi~[i][j] eta[b][i]: one block per (j, b) over row j of Phi~^T,
+// deterministic block reduction.
 template <typename T>
 __global__ void k_adjoint(int nl, int ng, const T* __restrict__ phit, const T* __restrict__ eta,
                           T* __restrict__ pit) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.y;
-  if (warp >= ng) return;
-  const T* row = phit + (size_t)warp * nl;
+  __shared__ T red[32];
+  const int j = blockIdx.x, b = blockIdx.y;
+  const T* row = phit + (size_t)j * nl;
   const T* e = eta + (size_t)b * nl;
   T s = T(0);
-  for (int i = lane; i < nl; i += 32) s += row[i] * e[i];
-  s = warp_sum(s);
-  if (lane == 0) pit[(size_t)b * ng + warp] = s;
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) s += row[i] * e[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) pit[(size_t)b * ng + j] = s;
 }
 
 // x*[b][j] from w = ctil_j + sigma_j lambda_b + pi~_bj (FP64), plus per-instance
@@ -81,21 +81,20 @@ __global__ void k_minimize(DevNet N, const double* __restrict__ lambda, const T*
   }
 }
 
-// f[b][i] = sum_j Phi~[i][j] x[b][j] + f0[b][i]; one warp per (b, i).
+// f[b][i] = sum_j Phi~[i][j] x[b][j] + f0[b][i]: one block per (i, b).
 template <typename T>
 __global__ void k_forward(int nl, int ng, const T* __restrict__ phi, const T* __restrict__ x,
                           const double* __restrict__ f0, double* __restrict__ f,
                           const int* __restrict__ done) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.y;
-  if (warp >= nl) return;
+  __shared__ T red[32];
+  const int i = blockIdx.x, b = blockIdx.y;
   if (done && done[b]) return;
-  const T* row = phi + (size_t)warp * ng;
+  const T* row = phi + (size_t)i * ng;
   const T* xx = x + (size_t)b * ng;
   T s = T(0);
-  for (int j = lane; j < ng; j += 32) s += row[j] * xx[j];
-  s = warp_sum(s);
-  if (lane == 0) f[(size_t)b * nl + warp] = (double)s + f0[(size_t)b * nl + warp];
+  for (int j = threadIdx.x; j < ng; j += blockDim.x) s += row[j] * xx[j];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) f[(size_t)b * nl + i] = (double)s + f0[(size_t)b * nl + i];
 }
 
 // Outage correction f' = f + u f_k, supergradient (f - fmax, fmin - f; zero for the
@@ -184,10 +183,17 @@ __global__ void k_step(int nl, StepArgs P, const double* __restrict__ value,
   if (st.done[b] || st.cand[b] == 2) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = st.iter[b] + 1;  // evaluation count of this step (1-based)
+  __shared__ double s_pw[3];       // step-size factors, once per block (FP64 pow is slow)
+  if (threadIdx.x == 0) {
+    s_pw[0] = pow(P.decay, (double)(t - 1));
+    s_pw[1] = 1.0 - pow(P.beta1, (double)t);
+    s_pw[2] = 1.0 - pow(P.beta2, (double)t);
+  }
+  __syncthreads();
   StepArgs Q = P;
-  Q.bc1 = 1.0 - pow(P.beta1, (double)t);
-  Q.bc2 = 1.0 - pow(P.beta2, (double)t);
-  const double scale = pow(P.decay, (double)(t - 1));
+  Q.bc1 = s_pw[1];
+  Q.bc2 = s_pw[2];
+  const double scale = s_pw[0];
   const bool better = value[b] > st.best[b];
   const size_t o = (size_t)b * nl + i;
   if (i < nl) {
@@ -240,6 +246,12 @@ __global__ void k_close_iter(int B, int max_iters, double tol, SolveStateBase st
 // ---------------------------------------------------------------- host drivers
 namespace {
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+// threads per output of the reduction kernels: about 8 elements per thread, 32..256
+inline int red_threads(int n) {
+  int t = 32;
+  while (t < 256 && t * 8 < n) t *= 2;
+  return t;
+}
 }  // namespace
 
 dcopf_status run_eval_unfused(dcopf_dual* h, int B, const int* outage, const double* lambda,
@@ -249,21 +261,22 @@ dcopf_status run_eval_unfused(dcopf_dual* h, int B, const int* outage, const dou
   const DevNet& N = h->dev;
   Workspace& w = h->ws;
   const int nl = N.n_line, ng = N.n_gen;
-  dim3 gl(cdiv(nl, 8), B), gg(cdiv(ng, 8), B);
+  dim3 gl(nl, B), gg(ng, B);
+  const int ta = red_threads(nl), tf = red_threads(ng);
   if (precision == DCOPF_FP64) {
     k_eta<double, double><<<B, 256, 0, s>>>(nl, mh, ml, outage, w.u64.as<double>(), w.eta64.as<double>());
-    k_adjoint<double><<<gg, 256, 0, s>>>(nl, ng, N.phit64, w.eta64.as<double>(), w.pit64.as<double>());
+    k_adjoint<double><<<gg, ta, 0, s>>>(nl, ng, N.phit64, w.eta64.as<double>(), w.pit64.as<double>());
     k_minimize<double><<<B, 256, 0, s>>>(N, lambda, w.pit64.as<double>(), w.x64.as<double>(),
                                          w.sumcost.as<double>(), w.sump.as<double>(), nullptr);
-    k_forward<double><<<gl, 256, 0, s>>>(nl, ng, N.phi64, w.x64.as<double>(), w.f0.as<double>(),
+    k_forward<double><<<gl, tf, 0, s>>>(nl, ng, N.phi64, w.x64.as<double>(), w.f0.as<double>(),
                                          w.f.as<double>(), nullptr);
     if (dispatch) k_dispatch<<<cdiv((long long)B * ng, 256), 256, 0, s>>>(N, B, w.x64.as<double>(), dispatch);
   } else {
     k_eta<float, double><<<B, 256, 0, s>>>(nl, mh, ml, outage, w.u32.as<float>(), w.eta32.as<float>());
-    k_adjoint<float><<<gg, 256, 0, s>>>(nl, ng, N.phit32, w.eta32.as<float>(), w.pit32.as<float>());
+    k_adjoint<float><<<gg, ta, 0, s>>>(nl, ng, N.phit32, w.eta32.as<float>(), w.pit32.as<float>());
     k_minimize<float><<<B, 256, 0, s>>>(N, lambda, w.pit32.as<float>(), w.x32.as<float>(),
                                         w.sumcost.as<double>(), w.sump.as<double>(), nullptr);
-    k_forward<float><<<gl, 256, 0, s>>>(nl, ng, N.phi32, w.x32.as<float>(), w.f0.as<double>(),
+    k_forward<float><<<gl, tf, 0, s>>>(nl, ng, N.phi32, w.x32.as<float>(), w.f0.as<double>(),
                                         w.f.as<double>(), nullptr);
     if (dispatch) k_dispatch32<<<cdiv((long long)B * ng, 256), 256, 0, s>>>(N, B, w.x32.as<float>(), dispatch);
   }
@@ -284,21 +297,22 @@ dcopf_status run_iters_unfused(dcopf_dual* h, int B, const int* outage, int prec
   const DevNet& N = h->dev;
   Workspace& w = h->ws;
   const int nl = N.n_line, ng = N.n_gen;
-  dim3 gl(cdiv(nl, 8), B), gg(cdiv(ng, 8), B), gs(cdiv(nl, 256), B);
+  dim3 gl(nl, B), gg(ng, B), gs(cdiv(nl, 256), B);
+  const int ta = red_threads(nl), tf = red_threads(ng);
   for (int it = 0; it < n_iters; ++it) {
     if (precision == DCOPF_FP64) {
       k_eta<double, S><<<B, 256, 0, s>>>(nl, st.mu_hi, st.mu_lo, outage, w.u64.as<double>(), w.eta64.as<double>());
-      k_adjoint<double><<<gg, 256, 0, s>>>(nl, ng, N.phit64, w.eta64.as<double>(), w.pit64.as<double>());
+      k_adjoint<double><<<gg, ta, 0, s>>>(nl, ng, N.phit64, w.eta64.as<double>(), w.pit64.as<double>());
       k_minimize<double><<<B, 256, 0, s>>>(N, st.lam, w.pit64.as<double>(), w.x64.as<double>(),
                                            w.sumcost.as<double>(), w.sump.as<double>(), st.done);
-      k_forward<double><<<gl, 256, 0, s>>>(nl, ng, N.phi64, w.x64.as<double>(), w.f0.as<double>(),
+      k_forward<double><<<gl, tf, 0, s>>>(nl, ng, N.phi64, w.x64.as<double>(), w.f0.as<double>(),
                                            w.f.as<double>(), st.done);
     } else {
       k_eta<float, S><<<B, 256, 0, s>>>(nl, st.mu_hi, st.mu_lo, outage, w.u32.as<float>(), w.eta32.as<float>());
-      k_adjoint<float><<<gg, 256, 0, s>>>(nl, ng, N.phit32, w.eta32.as<float>(), w.pit32.as<float>());
+      k_adjoint<float><<<gg, ta, 0, s>>>(nl, ng, N.phit32, w.eta32.as<float>(), w.pit32.as<float>());
       k_minimize<float><<<B, 256, 0, s>>>(N, st.lam, w.pit32.as<float>(), w.x32.as<float>(),
                                           w.sumcost.as<double>(), w.sump.as<double>(), st.done);
-      k_forward<float><<<gl, 256, 0, s>>>(nl, ng, N.phi32, w.x32.as<float>(), w.f0.as<double>(),
+      k_forward<float><<<gl, tf, 0, s>>>(nl, ng, N.phi32, w.x32.as<float>(), w.f0.as<double>(),
                                           w.f.as<double>(), st.done);
     }
     k_grad_value<S, double><<<B, 256, 0, s>>>(N, outage, w.u64.as<double>(), st.lam, st.mu_hi,

@@ -41,6 +41,62 @@ __device__ void ldl_solve_smem(const DevNet& N, double* X) {
   }
 }
 
+// The factor staged in shared memory: FP64 values once in CSR order (the CSC walk
+// reads them through cmap), 16-bit row/column indices, 32-bit pointers.
+struct PackedFactor {
+  const double* diag; const double* val;
+  const uint32_t* rptr; const uint32_t* cptr; const uint32_t* cmap;
+  const uint16_t* rcol; const uint16_t* crow; const uint16_t* frows; const uint16_t* brows;
+  const uint16_t* flev; const uint16_t* blev;
+};
+
+// Copies the packed factor into shared memory (16-byte loads) and returns its view.
+__device__ PackedFactor stage_factor(const DevNet& N, unsigned char* sm) {
+  const int4* src = (const int4*)N.fac_blob;
+  int4* dst = (int4*)sm;
+  for (int q = threadIdx.x; q < N.fac_bytes / 16; q += blockDim.x) dst[q] = src[q];
+  __syncthreads();
+  PackedFactor F;
+  F.diag = (const double*)(sm + N.off_diag); F.val = (const double*)(sm + N.off_val);
+  F.rptr = (const uint32_t*)(sm + N.off_rptr); F.cptr = (const uint32_t*)(sm + N.off_cptr);
+  F.cmap = (const uint32_t*)(sm + N.off_cmap);
+  F.rcol = (const uint16_t*)(sm + N.off_rcol); F.crow = (const uint16_t*)(sm + N.off_crow);
+  F.frows = (const uint16_t*)(sm + N.off_frows); F.brows = (const uint16_t*)(sm + N.off_brows);
+  F.flev = (const uint16_t*)(sm + N.off_flev); F.blev = (const uint16_t*)(sm + N.off_blev);
+  return F;
+}
+
+__device__ void ldl_solve_packed(const DevNet& N, const PackedFactor& F, double* X) {
+  for (int lev = 0; lev < N.n_fwd_lev; ++lev) {
+    const int s = F.flev[lev], e = F.flev[lev + 1];
+    for (int idx = s + threadIdx.x; idx < e; idx += blockDim.x) {
+      const int i = F.frows[idx];
+      double v = X[i];
+      for (uint32_t p = F.rptr[i]; p < F.rptr[i + 1]; ++p) v -= F.val[p] * X[F.rcol[p]];
+      X[i] = v;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < N.nr; i += blockDim.x) X[i] /= F.diag[i];
+  __syncthreads();
+  for (int lev = 0; lev < N.n_bwd_lev; ++lev) {
+    const int s = F.blev[lev], e = F.blev[lev + 1];
+    for (int idx = s + threadIdx.x; idx < e; idx += blockDim.x) {
+      const int i = F.brows[idx];
+      double v = X[i];
+      for (uint32_t p = F.cptr[i]; p < F.cptr[i + 1]; ++p) v -= F.val[F.cmap[p]] * X[F.crow[p]];
+      X[i] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Solve with the staged factor when `staged`, else walk the factor in global memory.
+__device__ __forceinline__ void ldl_solve(const DevNet& N, const PackedFactor* F, double* X) {
+  if (F) ldl_solve_packed(N, *F, X);
+  else ldl_solve_smem(N, X);
+}
+
 __device__ __forceinline__ double theta_at(const DevNet& N, const double* X, int bus) {
   int p = N.pos_of_bus[bus];
   return p >= 0 ? X[p] : 0.0;
@@ -49,9 +105,14 @@ __device__ __forceinline__ double theta_at(const DevNet& N, const double* X, int
 __global__ void k_base_flows(DevNet N, const double* __restrict__ loads,
                              const int* __restrict__ outage, double* __restrict__ f0,
                              float* __restrict__ f0_32, double* __restrict__ u64,
-                             float* __restrict__ u32, double* __restrict__ demand, int* err) {
-  extern __shared__ double X[];
+                             float* __restrict__ u32, double* __restrict__ demand, int* err,
+                             int staged) {
+  extern __shared__ __align__(16) unsigned char sm[];
   __shared__ double red[32];
+  PackedFactor PF;
+  const PackedFactor* pf = nullptr;
+  if (staged) { PF = stage_factor(N, sm); pf = &PF; }
+  double* X = (double*)(sm + (staged ? N.fac_bytes : 0));
   const int b = blockIdx.x;
   const int nl = N.n_line;
   const double* d = loads + (size_t)b * N.n_bus;
@@ -61,7 +122,7 @@ __global__ void k_base_flows(DevNet N, const double* __restrict__ loads,
   if (threadIdx.x == 0) demand[b] = s;
   for (int k = threadIdx.x; k < N.nr; k += blockDim.x) X[k] = -d[N.bus_of_pos[k]];
   __syncthreads();
-  ldl_solve_smem(N, X);
+  ldl_solve(N, pf, X);
   double* frow = f0 + (size_t)b * nl;
   for (int l = threadIdx.x; l < nl; l += blockDim.x)
     frow[l] = N.phim[l] + N.line_b[l] * (theta_at(N, X, N.line_from[l]) - theta_at(N, X, N.line_to[l]));
@@ -76,7 +137,7 @@ __global__ void k_base_flows(DevNet N, const double* __restrict__ loads,
       if (pb >= 0) X[pb] -= 1.0;
     }
     __syncthreads();
-    ldl_solve_smem(N, X);
+    ldl_solve(N, pf, X);
     // PTDF of a transfer from the outaged line's from-bus to its to-bus
     const double ptdf_kk =
         N.line_b[k] * (theta_at(N, X, N.line_from[k]) - theta_at(N, X, N.line_to[k]));
@@ -120,11 +181,16 @@ __global__ void k_certify(DevNet N, const double* __restrict__ loads, const int*
                           const double* __restrict__ lambda, const S* __restrict__ mu_hi,
                           const S* __restrict__ mu_lo, double* __restrict__ bound,
                           double* __restrict__ errb, const int* __restrict__ mask,
-                          const int* __restrict__ done) {
-  extern __shared__ double X[];  // [nr] prices, then [nr] outage transfer
+                          const int* __restrict__ done, int staged) {
+  // shared memory: [staged factor] [nr] prices [nr] outage transfer
+  extern __shared__ __align__(16) unsigned char sm[];
   __shared__ double red[32];
   const int b = blockIdx.x;
   if (mask && (mask[b] == 0 || (done && done[b]))) return;
+  PackedFactor PF;
+  const PackedFactor* pf = nullptr;
+  if (staged) { PF = stage_factor(N, sm); pf = &PF; }
+  double* X = (double*)(sm + (staged ? N.fac_bytes : 0));
   const int nl = N.n_line;
   const int k = outage ? outage[b] : -1;
   const S* mh = mu_hi + (size_t)b * nl;
@@ -144,7 +210,7 @@ __global__ void k_certify(DevNet N, const double* __restrict__ loads, const int*
     X[q] = r;
   }
   __syncthreads();
-  ldl_solve_smem(N, X);
+  ldl_solve(N, pf, X);
   if (k >= 0) {
     double* W = X + N.nr;
     for (int q = threadIdx.x; q < N.nr; q += blockDim.x) W[q] = 0.0;
@@ -156,7 +222,7 @@ __global__ void k_certify(DevNet N, const double* __restrict__ loads, const int*
       if (pc >= 0) W[pc] -= 1.0;
     }
     __syncthreads();
-    ldl_solve_smem(N, W);
+    ldl_solve(N, pf, W);
     // eta'_k = u^T eta = (z_a - z_c) / (1 - PTDF_kk); z' = z + eta'_k b_k W
     const double denom = 1.0 - N.line_b[k] * (theta_at(N, W, a) - theta_at(N, W, c));
     const double s = (theta_at(N, X, a) - theta_at(N, X, c)) / denom;
@@ -197,13 +263,26 @@ __global__ void k_certify(DevNet N, const double* __restrict__ loads, const int*
 
 template __global__ void k_certify<double>(DevNet, const double*, const int*, const double*,
                                            const double*, const double*, double*, double*,
-                                           const int*, const int*);
+                                           const int*, const int*, int);
 template __global__ void k_certify<float>(DevNet, const double*, const int*, const double*,
                                           const float*, const float*, double*, double*, const int*,
-                                          const int*);
+                                          const int*, int);
+
+// Shared memory of a sparse kernel with n_vec solution vectors; *staged tells whether
+// the packed factor fits beside them.
+static size_t sparse_smem(const dcopf_dual* h, int n_vec, int* staged) {
+  size_t vec = (size_t)n_vec * (size_t)std::max(1, h->dev.nr) * sizeof(double);
+  if (h->dev.fac_blob && (size_t)h->dev.fac_bytes + vec + 1024 <= h->smem_optin) {
+    *staged = 1;
+    return (size_t)h->dev.fac_bytes + vec;
+  }
+  *staged = 0;
+  return vec;
+}
 
 size_t certify_smem(const dcopf_dual* h, bool outages) {
-  return (size_t)(outages ? 2 : 1) * (size_t)std::max(1, h->dev.nr) * sizeof(double);
+  int st = 0;
+  return sparse_smem(h, outages ? 2 : 1, &st);
 }
 
 static int sparse_threads(const dcopf_dual* h) {
@@ -215,7 +294,8 @@ static int sparse_threads(const dcopf_dual* h) {
 
 dcopf_status run_base_flows(dcopf_dual* h, int B, const double* loads, const int* outage,
                             cudaStream_t s) {
-  size_t smem = (size_t)std::max(1, h->dev.nr) * sizeof(double);
+  int staged = 0;
+  size_t smem = sparse_smem(h, 1, &staged);
   if (smem > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(k_base_flows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
@@ -223,7 +303,8 @@ dcopf_status run_base_flows(dcopf_dual* h, int B, const double* loads, const int
   Workspace& w = h->ws;
   k_base_flows<<<B, sparse_threads(h), smem, s>>>(h->dev, loads, outage, w.f0.as<double>(),
                                                   w.f0_32.as<float>(), w.u64.as<double>(),
-                                                  w.u32.as<float>(), w.demand.as<double>(), h->d_err);
+                                                  w.u32.as<float>(), w.demand.as<double>(), h->d_err,
+                                                  staged);
   h->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
@@ -234,13 +315,14 @@ template <typename S>
 dcopf_status run_certify_t(dcopf_dual* h, int B, const double* loads, const int* outage,
                            const double* lam, const S* mh, const S* ml, double* bound, double* errb,
                            const int* mask, const int* done, cudaStream_t s) {
-  size_t smem = certify_smem(h, outage != nullptr);
+  int staged = 0;
+  size_t smem = sparse_smem(h, outage != nullptr ? 2 : 1, &staged);
   if (smem > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(k_certify<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return DCOPF_ERR_CUDA;
   k_certify<S><<<B, sparse_threads(h), smem, s>>>(h->dev, loads, outage, lam, mh, ml, bound, errb,
-                                                  mask, done);
+                                                  mask, done, staged);
   h->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }

@@ -91,7 +91,14 @@ struct dcopf_dual {
   dcopf::DBuf active;  // one int: instances still running
   double ub_any = 0.0;  // cost of the dearest dispatch (upper bound on any primal cost)
   long long launches = 0;
+  // optional event timing of the iteration kernels
+  bool timing = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double t_iter_ms = 0.0;
+  long long t_iter_launches = 0, t_evals = 0;
   int sm_count = 0;
+  int fused_C = 0, fused_G = 0;  // cluster shape of the fused kernel (chosen on first use)
+  int fused_coop = -1;           // -1 unknown, 1 cooperative+cluster launch accepted, 0 not
   size_t smem_optin = 0;
   bool verbose = false;
   std::string last_error;

@@ -7,6 +7,7 @@
 // generator bus at a time by sparse solves, and the normalised Phi~ = Phi diag(sigma)
 // of Appendix A1.
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <cstdio>
 #include <numeric>
@@ -338,6 +339,55 @@ dcopf_status build_host_net(const dcopf_network_desc* d, HostNet* H, std::string
   };
   schedule(true, &F.fwd_rows, &F.fwd_level_ptr);
   schedule(false, &F.bwd_rows, &F.bwd_level_ptr);
+  // packed factor for shared-memory staging: FP64 values stored once (CSR order),
+  // the CSC walk reads them through a position map; indices in 16 bits
+  if (n > 0 && n < 65535) {
+    size_t nnz = F.lrow_col.size();
+    size_t off = 0;
+    auto sec = [&](size_t bytes) { size_t o = off; off = (off + bytes + 15) & ~(size_t)15; return (int)o; };
+    F.off_diag = sec(8 * (size_t)n);
+    F.off_val = sec(8 * nnz);
+    F.off_rptr = sec(4 * (size_t)(n + 1));
+    F.off_cptr = sec(4 * (size_t)(n + 1));
+    F.off_cmap = sec(4 * nnz);
+    F.off_rcol = sec(2 * nnz);
+    F.off_crow = sec(2 * nnz);
+    F.off_frows = sec(2 * (size_t)n);
+    F.off_brows = sec(2 * (size_t)n);
+    F.off_flev = sec(2 * F.fwd_level_ptr.size());
+    F.off_blev = sec(2 * F.bwd_level_ptr.size());
+    F.blob.assign(off, 0);
+    unsigned char* B = F.blob.data();
+    memcpy(B + F.off_diag, F.diag.data(), 8 * (size_t)n);
+    memcpy(B + F.off_val, F.lrow_val.data(), 8 * nnz);
+    for (int i = 0; i <= n; ++i) {
+      ((uint32_t*)(B + F.off_rptr))[i] = (uint32_t)F.lrow_ptr[i];
+      ((uint32_t*)(B + F.off_cptr))[i] = (uint32_t)F.lcol_ptr[i];
+    }
+    // position of each CSC entry in the CSR value array
+    std::vector<int> fill(F.lrow_ptr.begin(), F.lrow_ptr.end() - 1);
+    std::vector<uint32_t> cmap(nnz);
+    for (int k = 0; k < n; ++k)
+      for (int p = F.lcol_ptr[k]; p < F.lcol_ptr[k + 1]; ++p) {
+        int i = F.lcol_row[p];
+        // CSR row i lists its columns in increasing order, and columns k are visited in
+        // increasing order here, so the next unused slot of row i is entry (i, k)
+        cmap[p] = (uint32_t)fill[i]++;
+      }
+    memcpy(B + F.off_cmap, cmap.data(), 4 * nnz);
+    for (size_t p = 0; p < nnz; ++p) {
+      ((uint16_t*)(B + F.off_rcol))[p] = (uint16_t)F.lrow_col[p];
+      ((uint16_t*)(B + F.off_crow))[p] = (uint16_t)F.lcol_row[p];
+    }
+    for (int i = 0; i < n; ++i) {
+      ((uint16_t*)(B + F.off_frows))[i] = (uint16_t)F.fwd_rows[i];
+      ((uint16_t*)(B + F.off_brows))[i] = (uint16_t)F.bwd_rows[i];
+    }
+    for (size_t l = 0; l < F.fwd_level_ptr.size(); ++l)
+      ((uint16_t*)(B + F.off_flev))[l] = (uint16_t)F.fwd_level_ptr[l];
+    for (size_t l = 0; l < F.bwd_level_ptr.size(); ++l)
+      ((uint16_t*)(B + F.off_blev))[l] = (uint16_t)F.bwd_level_ptr[l];
+  }
 
   // ---- Phi~ = H_a G diag(sigma), built one generator bus at a time (FP64)
   h.phi.assign((size_t)nl * ng, 0.0);

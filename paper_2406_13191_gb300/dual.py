@@ -123,6 +123,18 @@ class DcopfDual:
     def kernel_launches(self) -> int:
         return int(self.lib.dcopf_dual_kernel_launches(self.h))
 
+    def set_timing(self, enable: bool = True) -> None:
+        _lib.check(self.lib.dcopf_dual_set_timing(self.h, 1 if enable else 0), "set_timing")
+
+    def read_timing(self):
+        """(iteration-kernel milliseconds, their launches, evaluations), then reset."""
+        ms = C.c_double()
+        nl = C.c_int64()
+        ne = C.c_int64()
+        _lib.check(self.lib.dcopf_dual_read_timing(self.h, C.byref(ms), C.byref(nl), C.byref(ne)),
+                   "read_timing")
+        return ms.value, nl.value, ne.value
+
     # ------------------------------------------------------------------ entry points
     def eval(self, loads, lam, mu_hi, mu_lo, outage=None, precision: str = "fp64",
              want_grad: bool = True, want_dispatch: bool = True):
