@@ -224,6 +224,14 @@ dcopf_status dcopf_dual_set_timing(dcopf_dual_t h, int32_t enable);
 dcopf_status dcopf_dual_read_timing(dcopf_dual_t h, double* iter_ms, int64_t* iter_launches,
                                     int64_t* evaluations);
 
+/* Self-test of the bounded device wait used by every cross-CTA synchronisation of
+ * the persistent kernels: one thread waits, with an acquire load in a loop, for a
+ * device counter that nothing increments, and must give up after timeout_ns
+ * (1 us .. 10 s) of wall-clock time.  Returns DCOPF_ERR_TIMEOUT when the wait gave up
+ * (the expected outcome), DCOPF_OK if it did not.  The device stays usable
+ * either way.  Synchronises `stream`. */
+dcopf_status dcopf_selftest_bounded_wait(dcopf_dual_t h, int64_t timeout_ns, void* stream);
+
 /* Sticky device-side error word of the handle's last solve (0 = none, else a
  * dcopf_status value such as DCOPF_ERR_TIMEOUT).  Synchronises the device. */
 dcopf_status dcopf_dual_device_error(dcopf_dual_t h);

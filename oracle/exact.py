@@ -99,7 +99,10 @@ def ipm(net: Net, loads, max_iter=200, tol=1e-12, feas_tol=1e-9, verbose=False):
         if not np.isfinite(mu) or mu > 1e30 or np.linalg.norm(p) > 1e12:
             status = "infeasible"
             break
-        w = z / s
+        w = z / np.maximum(s, 1e-300)
+        if not np.all(np.isfinite(w)):
+            status = "stalled"
+            break
         K = (phi.T * (w[:nl] + w[nl:2 * nl])) @ phi
         K[np.diag_indices(ng)] += w[2 * nl:2 * nl + ng] + w[2 * nl + ng:] + qd
         try:
@@ -115,7 +118,11 @@ def ipm(net: Net, loads, max_iter=200, tol=1e-12, feas_tol=1e-9, verbose=False):
             return np.linalg.solve(Lc.T, np.linalg.solve(Lc, r))
 
         ones = np.ones(ng)
-        Kinv1 = ksolve(ones)
+        try:
+            Kinv1 = ksolve(ones)
+        except np.linalg.LinAlgError:
+            status = "stalled"
+            break
         s1k1 = float(ones @ Kinv1)
 
         def newton(rc):
@@ -131,13 +138,21 @@ def ipm(net: Net, loads, max_iter=200, tol=1e-12, feas_tol=1e-9, verbose=False):
             neg = dv < 0
             return min(1.0, float(np.min(-v[neg] / dv[neg]))) if np.any(neg) else 1.0
 
-        # predictor (affine scaling)
-        dp, dy, ds, dz = newton(s * z)
+        # predictor (affine scaling); a singular step means FP64 has run out of digits
+        try:
+            dp, dy, ds, dz = newton(s * z)
+        except np.linalg.LinAlgError:
+            status = "stalled"
+            break
         a_aff = min(maxstep(s, ds), maxstep(z, dz))
         mu_aff = float(np.dot(s + a_aff * ds, z + a_aff * dz) / m)
         sigma = (mu_aff / mu) ** 3
         # corrector
-        dp, dy, ds, dz = newton(s * z + ds * dz - sigma * mu)
+        try:
+            dp, dy, ds, dz = newton(s * z + ds * dz - sigma * mu)
+        except np.linalg.LinAlgError:
+            status = "stalled"
+            break
         a = 0.99 * min(maxstep(s, ds), maxstep(z, dz))
         p = p + a * dp
         y = y + a * dy

@@ -534,6 +534,12 @@ dcopf_status dcopf_dual_read_timing(dcopf_dual_t h, double* iter_ms, int64_t* it
   return DCOPF_OK;
 }
 
+dcopf_status dcopf_selftest_bounded_wait(dcopf_dual_t h, int64_t timeout_ns, void* stream) {
+  if (!h || timeout_ns < 1000 || timeout_ns > 10000000000ll) return DCOPF_ERR_INVALID_ARG;
+  DeviceGuard guard(h->device);
+  return run_wait_selftest(h, (long long)timeout_ns, (cudaStream_t)stream);
+}
+
 dcopf_status dcopf_dual_device_error(dcopf_dual_t h) {
   if (!h) return DCOPF_ERR_INVALID_ARG;
   DeviceGuard guard(h->device);

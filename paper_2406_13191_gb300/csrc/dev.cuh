@@ -122,6 +122,23 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// Waits until *ctr >= target (wrap-safe), reading it with acquire semantics; gives up
+// after timeout_ns of wall-clock time and returns false.  Used by every cross-CTA wait
+// of the persistent kernels.
+__device__ __forceinline__ bool bounded_wait_geq(const unsigned* ctr, unsigned target,
+                                                 uint64_t timeout_ns) {
+  uint64_t t0 = 0;
+  int spins = 0;
+  while ((int)(ld_acquire_u32(ctr) - target) < 0) {
+    if ((++spins & 31) == 0) {
+      const uint64_t now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > timeout_ns) return false;
+    }
+  }
+  return true;
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned nblocks, unsigned& epoch,
                                              int* err, uint64_t timeout_ns) {
   __shared__ int s_ok;

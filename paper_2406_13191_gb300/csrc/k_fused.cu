@@ -7,26 +7,33 @@
 // lines (mu_hi, mu_lo, optimiser moments).  lambda and its moments are replicated in
 // every CTA and updated identically (same inputs, same order).
 //
-// Iteration (all CTAs):
+// Iteration k (all CTAs):
 //   A   eta = mu_hi - mu_lo on own rows; partial adjoint Phi~_c^T eta_c for all gens
 //       into own shared memory                                (eq. (6): C^T mu)
-//   A2  [cluster sync] CTA r of a cluster sums gens slice S_r over the cluster's
-//       partials through distributed shared memory -> Pc[j][cluster]
-//   --  grid barrier (cluster leaders only; bounded wait)
-//   B   every cluster reads Pc for its slices (one coalesced pass, L2 only), sums the
-//       clusters in a fixed order, takes the closed-form minimiser x*_j (eq. (6) /
-//       eq. (16)) and partial cost / dispatch sums; the FP64 line partials R of the
-//       previous evaluation complete its dual value -> best point, stop tests
-//   C   [cluster sync] gather x* of all gens from the cluster's CTAs (DSMEM); forward
+//   A2  [cluster sync] CTA r of a cluster sums its gens slice S_r over the cluster's
+//       partials (distributed shared memory) and publishes them -> Pc[j][cluster]
+//   B   every cluster reads Pc for its slices and the line partials R of the previous
+//       evaluation, sums the clusters in a fixed order, takes the closed-form
+//       minimiser x*_j (eq. (6) / eq. (16)) and partial cost / dispatch sums; the
+//       previous evaluation's dual value -> best point, stop tests
+//   C   [cluster sync] gather x* of all gens from the cluster (DSMEM); forward
 //       f = Phi~_c x* + f0 on own rows (constraint (1c)); supergradient; FP64 line
-//       partial -> R[c]; projected step of own mu and of lambda
-// Every cluster computes the same x* from the same data in the same order, so one
-// grid-wide barrier per iteration suffices.  Pc and R are double-buffered by the
-// parity of the loop iteration: a cluster can only be one barrier ahead of another,
-// so a buffer is rewritten only after every reader has passed the next barrier.  The value of an evaluation is complete
-// one iteration later; the best point is copied from the previous iterate.
+//       partial -> R[c]; projected step of own mu and of lambda.
+//
+// Synchronisation between clusters: after publishing its slice, each CTA makes its
+// writes visible (fence) and increments the arrival counter of its cluster rank; a CTA
+// then waits until all C counters show every cluster's arrival for this loop, and
+// reads the slice's partials (and the line partials R of the previous loop, written
+// before the writer's arrival) from L2.  Pc and R are double-buffered by loop parity:
+// a CTA can run at most one loop ahead of the slowest one, so a buffer is rewritten
+// only after all its readers are done.  Every wait is bounded; a wait that gives up
+// is made uniform across the cluster before any CTA leaves, so no CTA exits while a
+// peer may still read its shared memory.
+// Every cluster computes the same x* and the same dual value from the same data in
+// the same order, so stop decisions are identical everywhere.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cstdio>
 
 #include "dev.cuh"
@@ -40,19 +47,19 @@ struct FusedArgs {
   DevNet N;
   StepArgs P;
   SolveState<float> st;
-  const float* f0;        // [n_line]
+  const float* f0;               // [n_line]
   double demand;
-  float* Pc;              // [2][n_gen][n_clusters rounded up to 4] (parity of the loop iteration)
-  double* R;              // [2][G]
-  unsigned* bar;
+  float* Pc;                     // [2][n_gen][NCLp] cluster partial adjoints
+  double* R;                     // [2][G] line partials of the dual value
+  unsigned* cnt;                 // [8] arrival counters, one per cluster rank
   int* err;
   int max_iters;
   double tol;
   int rows_per_cta;
-  int slice;              // gens per cluster rank
+  int slice;                     // gens per cluster rank
   int phi_in_smem;
-  int C, G;               // launch shape the shared-memory layout was sized for
-  unsigned smem_bytes;    // dynamic shared memory the layout needs
+  int C, G;                      // launch shape the shared-memory layout was sized for
+  unsigned smem_bytes;           // dynamic shared memory the layout needs
   uint64_t timeout_ns;
 };
 
@@ -72,37 +79,6 @@ __device__ __forceinline__ S fused_rule(const StepArgs& P, S theta, S g, S& s1, 
     theta += a * g / (sqrt(s1) + S(P.eps));
   }
   return theta;
-}
-
-// Barrier over all clusters: every thread publishes its global writes, the cluster
-// synchronises, its leader arrives on the grid counter and waits (bounded), and the
-// cluster synchronises again.  Returns false (and records DCOPF_ERR_TIMEOUT) when the
-// wait gave up; the result is identical in every CTA of the cluster.
-__device__ __forceinline__ bool cluster_grid_barrier(cg::cluster_group& cl, unsigned* counter,
-                                                     unsigned n_clusters, unsigned& epoch, int* err,
-                                                     uint64_t timeout_ns, int* s_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) __threadfence();  // cumulative: covers the CTA's writes ordered by bar.sync
-  cl.sync();
-  epoch += 1;
-  if (cl.block_rank() == 0 && threadIdx.x == 0) {
-    const unsigned target = epoch * n_clusters;
-    atomicAdd(counter, 1u);
-    int ok = 1;
-    uint64_t t0 = 0;
-    int spins = 0;
-    while ((int)(ld_acquire_u32(counter) - target) < 0) {
-      if (++spins == 32) t0 = global_ns();
-      if (spins > 32 && (spins & 127) == 0) {
-        if (global_ns() - t0 > timeout_ns) { atomicExch(err, (int)DCOPF_ERR_TIMEOUT); ok = 0; break; }
-        if (ld_relaxed_s32(err) != 0) { ok = 0; break; }
-      }
-    }
-    __threadfence();
-    *s_ok = ok;
-  }
-  cl.sync();
-  return *cl.map_shared_rank(s_ok, 0) != 0;
 }
 
 // Sums two values over the block in one pass (fixed tree); every thread gets both.
@@ -129,32 +105,32 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   const DevNet& N = A.N;
   const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x;
   const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  // The layout below was sized on the host for (A.C, A.G); refuse any other shape.
+  {
+    unsigned dyn;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    if (C != A.C || G != A.G || dyn < A.smem_bytes || C > 8 || G > (int)blockDim.x) {
+      if (tid == 0) atomicExch(A.err, (int)DCOPF_ERR_UNSUPPORTED);
+      return;
+    }
+  }
   const int NCL = G / C, cid = c / C;
-  const int NCLp = (NCL + 3) & ~3;  // Pc row stride: float4-aligned rows
+  const int NCLp = (NCL + 3) & ~3;
   const int nl = N.n_line, ng = N.n_gen;
   const int r0 = min(nl, c * A.rows_per_cta), r1 = min(nl, r0 + A.rows_per_cta);
   const int nr = r1 - r0;
   const int SL = A.slice;
   const int j0 = min(ng, rank * SL), j1 = min(ng, j0 + SL);
+  const int nj = j1 - j0;
   const int ngp = (ng + 3) & ~3;
   const int rpc = A.rows_per_cta;
-  // The layout below was sized on the host for (A.C, A.G); refuse any other shape.
-  {
-    unsigned dyn;
-    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
-    if (C != A.C || G != A.G || dyn < A.smem_bytes || C > 8) {
-      if (tid == 0) atomicExch(A.err, (int)DCOPF_ERR_UNSUPPORTED);
-      return;
-    }
-  }
   // shared memory carve-up: per-slice generator constants (FP64), then floats
   double* gk = (double*)smem_raw;                // [5][SLp] ctil, sigma, mq, cconst, mid
   const int SLp = (SL + 1) & ~1;
   float* pp = (float*)(gk + 5 * SLp);            // [ngp] partial adjoint of own rows
   float* xs = pp + ngp;                          // [ngp] x* of all gens (gathered)
   float* xsl = xs + ngp;                         // [SL]  x* of own slice (read by peers)
-  float* pis = xsl + ((SL + 3) & ~3);            // [SL]  pi~ of own slice
-  float* tmp = pis + ((SL + 3) & ~3);            // [SL * NCLp] cluster partials of own slice
+  float* tmp = xsl + ((SL + 3) & ~3);            // [SL * NCLp] cluster partials of own slice
   float* row = tmp + SL * NCLp;                  // per-row arrays, 12 x rpc
   float *eta = row, *mh = row + rpc, *ml = row + 2 * rpc, *h1 = row + 3 * rpc, *h2 = row + 4 * rpc,
         *l1 = row + 5 * rpc, *l2 = row + 6 * rpc, *ph = row + 7 * rpc, *pl = row + 8 * rpc,
@@ -162,14 +138,15 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   float* phis = row + 12 * rpc;                  // [rpc][ng] when resident
   __shared__ double red[32];
   __shared__ double s_lam[4];   // lam, s1, s2, lam at the pending evaluation
-  __shared__ double s_cs[2];    // cost / dispatch sums of own slice
+  __shared__ double s_cs[2];    // cost / dispatch sums of own slice (read by peers)
+  __shared__ double s_csp[16];  // the cluster's cost / dispatch sums gathered
   __shared__ double s_pw[6];    // decay^(t-1), 1 - beta1^t, 1 - beta2^t; running powers
-  __shared__ int s_ok;
+  __shared__ int s_flag;        // this CTA gave up waiting (read by peers)
 
   const float* phi = A.phi_in_smem ? phis : (N.phi32 + (size_t)r0 * ng);
   if (A.phi_in_smem)
     for (int q = tid; q < nr * ng; q += blockDim.x) phis[q] = N.phi32[(size_t)r0 * ng + q];
-  for (int jj = tid; jj < j1 - j0; jj += blockDim.x) {
+  for (int jj = tid; jj < nj; jj += blockDim.x) {
     const int j = j0 + jj;
     gk[jj] = N.ctil[j]; gk[SLp + jj] = N.sigma[j]; gk[2 * SLp + jj] = N.mq[j];
     gk[3 * SLp + jj] = N.cconst[j]; gk[4 * SLp + jj] = N.mid[j];
@@ -198,81 +175,90 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   int cand = 0;
   bool pending = false;
   double cost_t = 0.0, psum_t = 0.0;
-  unsigned epoch = 0;
   const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   __syncthreads();
 
   for (unsigned k = 0;; ++k) {
-    float* Pc = A.Pc + (size_t)(k & 1u) * ng * NCLp;
-    const double* Rprev = A.R + (size_t)((k + 1u) & 1u) * G;   // written in loop k-1
+    float* Pcb = A.Pc + (size_t)(k & 1u) * ng * NCLp;
+    const double* Rprev = A.R + (size_t)((k + 1u) & 1u) * G;  // written in loop k-1
     double* Rcur = A.R + (size_t)(k & 1u) * G;
-    // ---------------- A: partial adjoint of own rows into shared memory
+    // ---------------- A: partial adjoint of own rows (4 gens per thread in flight)
     for (int r = tid; r < nr; r += blockDim.x) eta[r] = mh[r] - ml[r];
     __syncthreads();
-    for (int j = tid; j < ng; j += blockDim.x) {
-      float s = 0.f;
-      for (int r = 0; r < nr; ++r) s = fmaf(phi[(size_t)r * ng + j], eta[r], s);
-      pp[j] = s;
+    for (int jb = tid; jb < ng; jb += 4 * blockDim.x) {
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      const int b = blockDim.x;
+      const bool v1 = jb + b < ng, v2 = jb + 2 * b < ng, v3 = jb + 3 * b < ng;
+      for (int r = 0; r < nr; ++r) {
+        const float e = eta[r];
+        const float* pr = phi + (size_t)r * ng + jb;
+        a0 = fmaf(pr[0], e, a0);
+        if (v1) a1 = fmaf(pr[b], e, a1);
+        if (v2) a2 = fmaf(pr[2 * b], e, a2);
+        if (v3) a3 = fmaf(pr[3 * b], e, a3);
+      }
+      pp[jb] = a0;
+      if (v1) pp[jb + b] = a1;
+      if (v2) pp[jb + 2 * b] = a2;
+      if (v3) pp[jb + 3 * b] = a3;
     }
     cl.sync();
-    // ---------------- A2: cluster sum of own slice (fixed rank order) -> Pc
-    for (int j = j0 + tid; j < j1; j += blockDim.x) {
+    // ---------------- A2: cluster sum of own slice (fixed rank order), published
+    for (int jj = tid; jj < nj; jj += blockDim.x) {
+      const int j = j0 + jj;
       float v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = q < C ? cl.map_shared_rank(pp, q)[j] : 0.f;  // issued together
+      for (int q = 0; q < 8; ++q) v[q] = q < C ? cl.map_shared_rank(pp, q)[j] : 0.f;
       float s = 0.f;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) s += v[q];  // fixed rank order
-      Pc[(size_t)j * NCLp + cid] = s;
+      for (int q = 0; q < 8; ++q) s += v[q];
+      Pcb[(size_t)j * NCLp + cid] = s;
     }
-    if (!cluster_grid_barrier(cl, A.bar, NCL, epoch, A.err, A.timeout_ns, &s_ok)) break;
-    // ---------------- B: one batched read of the slice's cluster partials and of R
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();  // cumulative over the CTA's writes ordered by bar.sync
+      atomicAdd(A.cnt + rank, 1u);
+    }
+    // ---------------- B: wait for every cluster's arrival, read partials (and R), x*
     {
-      const int n4 = (j1 - j0) * NCLp / 4;
-      const float4* src = (const float4*)(Pc + (size_t)j0 * NCLp);
-      double rv = 0.0;
-      if (pending && tid < G) rv = __ldcg(Rprev + tid);   // G <= blockDim.x (checked on host)
-      // all loads of a batch are issued before any store, so a batch costs one round trip
-      for (int base = 0; base < n4; base += 8 * (int)blockDim.x) {
-        float4 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int q = base + u * blockDim.x + tid;
-          if (q < n4) v[u] = __ldcg(src + q);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int q = base + u * blockDim.x + tid;
-          if (q < n4) ((float4*)tmp)[q] = v[u];
-        }
+      bool ok = true;
+      if (tid < C) {
+        // counter `tid` counts the arrivals of rank-tid CTAs: NCL per loop
+        ok = bounded_wait_geq(A.cnt + tid, (unsigned)NCL * (k + 1u), A.timeout_ns);
+        __threadfence();
       }
-      if (pending) {
-        const double lsum = block_sum(rv, red);
-        const double lamp = s_lam[3];
-        const double val = cost_t + lamp * (psum_t - A.demand) + lsum;
-        if (val > best) {
-          best = val; best_lam = lamp; best_iter = t;
-          for (int r = tid; r < nr; r += blockDim.x) { st.best_hi[r0 + r] = ph[r]; st.best_lo[r0 + r] = pl[r]; }
+      const int waited_out = __syncthreads_or(ok ? 0 : 1);
+      ok = waited_out == 0;
+      double rv = 0.0;
+      if (ok) {
+        if (pending && tid < G) rv = __ldcg(Rprev + tid);
+        const int n4 = nj * NCLp / 4;
+        const float4* src = (const float4*)(Pcb + (size_t)j0 * NCLp);
+        // all loads of a batch are issued before any store: one round trip per batch
+        for (int base = 0; base < n4; base += 8 * (int)blockDim.x) {
+          float4 v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int q = base + u * blockDim.x + tid;
+            if (q < n4) v[u] = __ldcg(src + q);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int q = base + u * blockDim.x + tid;
+            if (q < n4) ((float4*)tmp)[q] = v[u];
+          }
         }
-        if (st.has_target && best >= st.thresh[0] + st.margin[0]) cand = 1;
-        if (t >= A.max_iters) cand = 2;
-        if (A.tol > 0.0 && t > 1 && fabs(val - prev_val) < A.tol) cand = 2;
-        prev_val = val;
-        pending = false;
       }
       __syncthreads();
-    }
-    if (cand) break;  // uniform: every CTA assembled the same value
-    {
       const double lam = s_lam[0];
       double cs = 0.0, ps = 0.0;
       // one thread per generator of the slice: sum the clusters in a fixed order
       // (identical in every cluster), then the closed-form minimiser; the w that
       // cancels (ctil + sigma lambda + pi~) is formed in FP64
-      for (int jj = tid; jj < j1 - j0; jj += blockDim.x) {
+      for (int jj = tid; jj < nj; jj += blockDim.x) {
         const float4* tp = (const float4*)(tmp + jj * NCLp);
         float s = 0.f;
-        for (int q = 0; q < NCLp / 4; ++q) {  // padding entries are never read: NCLp - NCL < 4
+        for (int q = 0; q < NCLp / 4; ++q) {
           const float4 v = tp[q];
           const int b4 = 4 * q;
           s += v.x;
@@ -290,41 +276,51 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       }
       block_sum2(cs, ps, red);
       if (tid == 0) { s_cs[0] = cs; s_cs[1] = ps; }
+      if (pending) {
+        const double lsum = block_sum(rv, red);
+        const double lamp = s_lam[3];
+        const double val = cost_t + lamp * (psum_t - A.demand) + lsum;
+        if (val > best) {
+          best = val; best_lam = lamp; best_iter = t;
+          for (int r = tid; r < nr; r += blockDim.x) { st.best_hi[r0 + r] = ph[r]; st.best_lo[r0 + r] = pl[r]; }
+        }
+        if (st.has_target && best >= st.thresh[0] + st.margin[0]) cand = 1;
+        if (t >= A.max_iters) cand = 2;
+        if (A.tol > 0.0 && t > 1 && fabs(val - prev_val) < A.tol) cand = 2;
+        prev_val = val;
+        pending = false;
+      }
+      const int gave_up = __syncthreads_or(ok ? 0 : 1);
+      if (tid == 0) s_flag = gave_up;
     }
     cl.sync();
-    // ---------------- C: gather x*, forward on own rows, supergradient, step
+    // ---------------- C: uniform exit decisions, gather x*, forward, supergradient, step
+    {
+      int any = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) any |= (q < C) ? *cl.map_shared_rank(&s_flag, q) : 0;
+      if (any) {
+        if (tid == 0) atomicExch(A.err, (int)DCOPF_ERR_TIMEOUT);
+        break;  // uniform in the cluster
+      }
+    }
+    if (cand) break;  // uniform everywhere: every CTA assembled the same value
     for (int j = tid; j < ng; j += blockDim.x) {
-      int q = j / SL;
+      const int q = j / SL;
       xs[j] = cl.map_shared_rank(xsl, q)[j - q * SL];
     }
+    if (tid >= 32 && tid < 32 + C) {
+      const double* o = cl.map_shared_rank(s_cs, tid - 32);
+      s_csp[2 * (tid - 32)] = o[0];
+      s_csp[2 * (tid - 32) + 1] = o[1];
+    }
+    __syncthreads();
     if (tid == 0) {
-      double cv[8], pv[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const double* o = cl.map_shared_rank(s_cs, q < C ? q : 0);
-        cv[q] = q < C ? o[0] : 0.0;
-        pv[q] = q < C ? o[1] : 0.0;
-      }
-      double cs = 0.0, ps = 0.0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) { cs += cv[q]; ps += pv[q]; }
-      red[0] = cs;
-      red[1] = ps;
-    }
-    __syncthreads();
-    cost_t = red[0];
-    psum_t = red[1];
-    __syncthreads();
-    for (int r = warp; r < nr; r += nw) {
-      float s = 0.f;
-      const float* pr = phi + (size_t)r * ng;
-      for (int j = lane; j < ng; j += 32) s = fmaf(pr[j], xs[j], s);
-      s = warp_sum(s);
-      if (lane == 0) eta[r] = s + f0[r];  // eta[] reused as the flow of own rows
-    }
-    __syncthreads();
-    t += 1;
-    if (tid == 0) {  // step-size factors of step t from the running powers
+      double cs2 = 0.0, ps2 = 0.0;
+      for (int q = 0; q < C; ++q) { cs2 += s_csp[2 * q]; ps2 += s_csp[2 * q + 1]; }
+      red[0] = cs2;
+      red[1] = ps2;
+      // step-size factors of the next step from the running powers
       s_pw[0] = s_pw[3];
       s_pw[4] *= A.P.beta1;
       s_pw[5] *= A.P.beta2;
@@ -332,13 +328,38 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       s_pw[1] = 1.0 - s_pw[4];
       s_pw[2] = 1.0 - s_pw[5];
     }
+    // forward on own rows: a warp per row, 3 rows of a warp in flight
+    for (int rb = warp; rb < nr; rb += 3 * nw) {
+      const bool v1 = rb + nw < nr, v2 = rb + 2 * nw < nr;
+      const float* p0 = phi + (size_t)rb * ng;
+      const float* p1 = p0 + (size_t)nw * ng;
+      const float* p2 = p1 + (size_t)nw * ng;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      for (int j = lane; j < ng; j += 32) {
+        const float x = xs[j];
+        a0 = fmaf(p0[j], x, a0);
+        if (v1) a1 = fmaf(p1[j], x, a1);
+        if (v2) a2 = fmaf(p2[j], x, a2);
+      }
+      a0 = warp_sum(a0);
+      a1 = warp_sum(a1);
+      a2 = warp_sum(a2);
+      if (lane == 0) {
+        eta[rb] = a0 + f0[rb];  // eta[] reused as the flow of own rows
+        if (v1) eta[rb + nw] = a1 + f0[rb + nw];
+        if (v2) eta[rb + 2 * nw] = a2 + f0[rb + 2 * nw];
+      }
+    }
     __syncthreads();
+    cost_t = red[0];
+    psum_t = red[1];
+    t += 1;
     const float bc1 = (float)s_pw[1];
     const float bc2 = (float)s_pw[2];
     const float am = (float)(A.P.alpha * s_pw[0]);
     if (tid == 32) {
-      // lambda step, concurrent with the line steps: the direction in FP32, the
-      // update of lambda in FP64
+      // lambda step, concurrent with the line steps: the direction in FP32, the update
+      // of lambda in FP64
       double lam = s_lam[0];
       s_lam[3] = lam;
       float s1 = (float)s_lam[1], s2 = (float)s_lam[2];
@@ -361,7 +382,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       ml[r] = nlo > 0.f ? nlo : 0.f;
     }
     lacc = block_sum(lacc, red);
-    if (tid == 0) Rcur[c] = lacc;
+    if (tid == 0) Rcur[c] = lacc;  // published by the fence before the next arrival
     pending = true;
     __syncthreads();
   }
@@ -394,26 +415,24 @@ static size_t fused_smem(int ng, int rpc, int C, int NCL, bool phi) {
   int SL = (ng + C - 1) / C;
   int SLp = (SL + 1) & ~1;
   int NCLp = (NCL + 3) & ~3;
-  size_t f = 2 * (size_t)ngp + 2 * ((SL + 3) & ~3) + (size_t)SL * NCLp + 12 * (size_t)rpc;
+  size_t f = 2 * (size_t)ngp + ((SL + 3) & ~3) + (size_t)SL * NCLp + 12 * (size_t)rpc;
   if (phi) f += (size_t)rpc * ng;
   return f * sizeof(float) + 5 * (size_t)SLp * sizeof(double);
 }
 
 static cudaError_t fused_config(const dcopf_dual* h, int C, FusedShape* out) {
   const int nl = h->dev.n_line, ng = h->dev.n_gen;
-  const int sms = h->sm_count;
+  const int sms = std::min(h->sm_count, 256);  // R is read with one thread per CTA
+  int G = (sms / C) * C;
+  if (G < C) return cudaErrorInvalidValue;
   for (int pass = 0; pass < 2; ++pass) {
-    // pass 0: assume all SMs usable; pass 1: use the occupancy answer
-    int G = (sms / C) * C;
-    if (G < C) return cudaErrorInvalidValue;
-    int rpc = (nl + G - 1) / G;
-    bool phi = fused_smem(ng, rpc, C, G / C, true) + 2048 <= h->smem_optin;
-    size_t smem = fused_smem(ng, rpc, C, G / C, phi);
+    const int rpc = (nl + G - 1) / G;
+    const bool phi = fused_smem(ng, rpc, C, G / C, true) + 2048 <= h->smem_optin;
+    const size_t smem = fused_smem(ng, rpc, C, G / C, phi);
     if (smem + 2048 > h->smem_optin) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_fused_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    if (C > 8) cudaFuncSetAttribute(k_fused_solve, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(256);
@@ -433,16 +452,8 @@ static cudaError_t fused_config(const dcopf_dual* h, int C, FusedShape* out) {
       out->rows_per_cta = rpc; out->slice = (ng + C - 1) / C;
       return cudaSuccess;
     }
-    if (ncl < 1) return cudaErrorInvalidValue;
-    // fewer clusters fit: shrink the grid to what is resident
-    int G2 = ncl * C;
-    rpc = (nl + G2 - 1) / G2;
-    phi = fused_smem(ng, rpc, C, ncl, true) + 2048 <= h->smem_optin;
-    smem = fused_smem(ng, rpc, C, ncl, phi);
-    if (smem + 2048 > h->smem_optin) return cudaErrorInvalidValue;
-    out->C = C; out->G = G2; out->smem = smem; out->phi_in_smem = phi ? 1 : 0;
-    out->rows_per_cta = rpc; out->slice = (ng + C - 1) / C;
-    return cudaFuncSetAttribute(k_fused_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ncl < 1 || pass == 1) return cudaErrorInvalidValue;
+    G = ncl * C;  // fewer clusters fit: size the grid to what is resident
   }
   return cudaErrorInvalidValue;
 }
@@ -452,7 +463,6 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
   const DevNet& N = h->dev;
   const int ng = N.n_gen;
   if (h->fused_C == 0) {
-    // pick the cluster size that keeps the most SMs busy (ties: larger clusters)
     // Per iteration a CTA reduces (n_gen / C) generators over G / C cluster partials,
     // so larger clusters cut that work; accept a larger cluster unless it leaves
     // more than 1/8 of the SMs idle.
@@ -479,6 +489,7 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
     return DCOPF_ERR_UNSUPPORTED;
   }
   const int G = sh.G, C = sh.C, NCL = G / C;
+  const int NCLp = (NCL + 3) & ~3;
   FusedArgs A{};
   A.N = N;
   A.P = P;
@@ -490,14 +501,14 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
   A.C = C;
   A.G = G;
   A.smem_bytes = (unsigned)sh.smem;
-  const int NCLp = (NCL + 3) & ~3;
-  size_t pc_bytes = ((size_t)2 * ng * NCLp * 4 + 255) & ~(size_t)255;
-  if (G > 256) return DCOPF_ERR_UNSUPPORTED;  // R is read with one thread per CTA
-  if (h->ws.misc.alloc(pc_bytes + (size_t)2 * G * 8 + 256) != cudaSuccess) return DCOPF_ERR_OOM;
+  // exchange buffers; the arrival counters are zeroed before every launch
+  const size_t pc_bytes = ((size_t)2 * ng * NCLp * 4 + 255) & ~(size_t)255;
+  const size_t r_bytes = ((size_t)2 * G * 8 + 255) & ~(size_t)255;
+  if (h->ws.misc.alloc(pc_bytes + r_bytes + 256) != cudaSuccess) return DCOPF_ERR_OOM;
   char* m = h->ws.misc.as<char>();
   A.Pc = (float*)m;
   A.R = (double*)(m + pc_bytes);
-  A.bar = h->d_bar;
+  A.cnt = (unsigned*)(m + pc_bytes + r_bytes);
   A.err = h->d_err;
   A.max_iters = max_iters;
   A.tol = tol;
@@ -508,7 +519,7 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
       cudaStreamSynchronize(s) != cudaSuccess)
     return DCOPF_ERR_CUDA;
   A.demand = demand;
-  if (cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned), s) != cudaSuccess) return DCOPF_ERR_CUDA;
+  if (cudaMemsetAsync(A.cnt, 0, 256, s) != cudaSuccess) return DCOPF_ERR_CUDA;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(G);
   cfg.blockDim = dim3(256);
@@ -524,7 +535,7 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
   cfg.attrs = at;
   // Co-residency of all clusters: requested from the driver (cooperative launch) when
   // it accepts that together with clusters; otherwise the grid is sized from
-  // cudaOccupancyMaxActiveClusters and the barrier's bounded wait is the guard.
+  // cudaOccupancyMaxActiveClusters and the bounded waits are the guard.
   cfg.numAttrs = h->fused_coop == 0 ? 1 : 2;
   cudaError_t e = cudaLaunchKernelEx(&cfg, k_fused_solve, A);
   if (e != cudaSuccess && cfg.numAttrs == 2) {
@@ -538,6 +549,26 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
   h->launches += 1;
   if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
   return DCOPF_OK;
+}
+
+// Self-test of the bounded wait: one thread waits for a counter that nothing
+// increments; the wait must give up and report it.
+__global__ void k_wait_selftest(const unsigned* ctr, uint64_t timeout_ns, int* gave_up) {
+  if (threadIdx.x == 0) *gave_up = bounded_wait_geq(ctr, 1u, timeout_ns) ? 0 : 1;
+}
+
+dcopf_status run_wait_selftest(dcopf_dual* h, long long timeout_ns, cudaStream_t s) {
+  if (h->ws.misc.alloc(std::max<size_t>(h->ws.misc.bytes, 256)) != cudaSuccess) return DCOPF_ERR_OOM;
+  unsigned* ctr = (unsigned*)h->ws.misc.p;
+  int* flag = (int*)((char*)h->ws.misc.p + 64);
+  if (cudaMemsetAsync(h->ws.misc.p, 0, 128, s) != cudaSuccess) return DCOPF_ERR_CUDA;
+  k_wait_selftest<<<1, 32, 0, s>>>(ctr, (uint64_t)timeout_ns, flag);
+  h->launches += 1;
+  int gave_up = 0;
+  if (cudaMemcpyAsync(&gave_up, flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  return gave_up ? DCOPF_ERR_TIMEOUT : DCOPF_OK;
 }
 
 }  // namespace dcopf

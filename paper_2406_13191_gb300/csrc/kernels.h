@@ -132,6 +132,7 @@ dcopf_status run_iters_unfused(dcopf_dual* h, int batch, const int* outage, int 
                                double tol, cudaStream_t s);
 
 // k_fused.cu
+dcopf_status run_wait_selftest(dcopf_dual* h, long long timeout_ns, cudaStream_t s);
 dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>& st, int max_iters,
                              double tol, cudaStream_t s);
 

@@ -355,6 +355,21 @@ def workload(cfg: int, batch: int | None = None) -> Workload:
                     meta=dict(config=cfg, name=CONFIG_NAMES.get(cfg, "")))
 
 
+def scenario_workload(seed: int, n_bus: int, n_line: int, n_gen: int, quadratic: bool,
+                      batch: int, n_out: int) -> Workload:
+    """A small network whose limits are placed on its own scenario set (multipliers
+    U[0.85, 1.15] and ``n_out`` line outages), returned with that set."""
+    sc = (batch, seed + 1, n_out, seed + 2)
+    net, base = make_network(seed, n_bus, n_line, n_gen, quadratic,
+                             "lognormal" if quadratic else "uniform", 0.6,
+                             f"scen{n_bus}", scenarios=sc)
+    loads = scenario_loads(base, batch, seed + 1)
+    out = (_outage_choice(n_bus, net.line_from, net.line_to, batch, n_out, seed + 2) if n_out
+           else -np.ones(batch, dtype=np.int32))
+    return Workload(net=net, loads=np.ascontiguousarray(loads), outage=out,
+                    meta=dict(config=None, name=net.name))
+
+
 def tiny_network(seed: int, n_bus: int, n_line: int, n_gen: int, quadratic=False,
                  tight=0.3):
     """Small random networks for brute-force and property tests."""

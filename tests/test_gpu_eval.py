@@ -149,3 +149,47 @@ def test_eval_rejects_bad_outages(cases):
         with pytest.raises(DcopfError) as e:
             g.eval(base[None], np.zeros(1), z, z, outage=np.array([bad], dtype=np.int32))
         assert e.value.code == 1
+
+
+def test_bounded_wait_gives_up_and_device_stays_usable(cases):
+    """A device wait on a flag that nothing sets returns DCOPF_ERR_TIMEOUT after its
+    limit; afterwards the same handle still evaluates correctly."""
+    import ctypes as C
+    import time
+    net, base, on, g = cases["c0"]
+    t0 = time.time()
+    code = g.lib.dcopf_selftest_bounded_wait(g.h, 20_000_000, C.c_void_p(0))   # 20 ms
+    assert code == 5
+    assert time.time() - t0 < 5.0
+    assert g.lib.dcopf_dual_device_error(g.h) == 0
+    r = g.eval(base[None], [-3000.0], np.zeros((1, on.n_line)), np.zeros((1, on.n_line)))
+    ref = dcopf.dual_value_prices(on, base, -3000.0, np.zeros(on.n_line), np.zeros(on.n_line))
+    assert abs(r["value"][0].item() - ref) <= 1e-9 * abs(ref)
+
+
+@pytest.mark.parametrize("cfg,batch", [(2, 4), (3, 2)])
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-9), ("fp32", 1e-5)])
+def test_eval_full_size_sampled(cfg, batch, precision, rtol):
+    """The 4600-bus (with line outages) and 10000-bus workloads at full size: the first
+    instances of each, at seeded dual points, against the oracle (rebuilt network for
+    an outage)."""
+    w = synth.workload(cfg, batch=batch)
+    net = w.net
+    on = onet(net)
+    g = DcopfDual(net)
+    rng = np.random.default_rng(100 + cfg)
+    pts = [rand_point(rng, net.n_line, density=0.05) for _ in range(batch)]
+    lam = np.array([p[0] for p in pts])
+    mh = np.stack([p[1] for p in pts])
+    ml = np.stack([p[2] for p in pts])
+    out = w.outage if (w.outage >= 0).any() else None
+    r = g.eval(w.loads, lam, mh, ml, outage=out, precision=precision)
+    for b in range(batch):
+        k = w.outage[b]
+        if k >= 0:
+            o = drop_line(net, k)
+            keep = np.arange(net.n_line) != k
+            val = dcopf.dual_value_lagrangian(o, w.loads[b], lam[b], mh[b][keep], ml[b][keep])
+        else:
+            val = dcopf.dual_value_lagrangian(on, w.loads[b], lam[b], mh[b], ml[b])
+        assert abs(r["value"][b].item() - val) <= rtol * abs(val), (b, r["value"][b].item(), val)

@@ -115,21 +115,22 @@ def test_warm_start_from_solution_stops_immediately(c0):
     assert r2.status[0].item() == 0 and r2.iters[0].item() <= 2
 
 
-def test_batched_scenarios_and_outages_c0(c0):
-    net, base, on, g, gam = c0
-    B = 6
-    loads = synth.scenario_loads(base, B, 41)
-    cand = np.flatnonzero(~g.bridge_mask())
-    outage = -np.ones(B, dtype=np.int32)
-    outage[1], outage[4] = cand[0], cand[-1]
-    gams = []
-    onets = []
-    for b in range(B):
+@pytest.mark.parametrize("quadratic", [False, True])
+def test_batched_scenarios_and_outages(quadratic):
+    """Batch of load scenarios with line outages on one network (limits placed on the
+    scenario set, so every instance is feasible), batched path."""
+    w = synth.scenario_workload(77, 60, 90, 12, quadratic, batch=8, n_out=3)
+    net, loads, outage = w.net, w.loads, w.outage
+    on = onet(net)
+    g = DcopfDual(net)
+    gams, onets = [], []
+    for b in range(w.batch):
         o = on if outage[b] < 0 else drop_line(net, outage[b])
         onets.append(o)
         gams.append(gamma(o, loads[b]))
-    res = g.solve(loads, outage=outage, path="batched", target=gams, **ADAM_LP)
-    for b in range(B):
+    kw = ADAM_QP if quadratic else ADAM_LP
+    res = g.solve(loads, outage=outage, path="batched", target=gams, **kw)
+    for b in range(w.batch):
         k = outage[b]
         keep = np.arange(on.n_line) != k
         bnd = res.bound[b].item()
