@@ -450,15 +450,18 @@ dcopf_status dcopf_dual_eval(dcopf_dual_t h, int32_t batch, const double* loads,
   if (!lambda || !mu_hi || !mu_lo || !value) return DCOPF_ERR_INVALID_ARG;
   if (precision != DCOPF_FP64 && precision != DCOPF_FP32 && precision != DCOPF_BF16X3)
     return DCOPF_ERR_INVALID_ARG;
-  if (precision == DCOPF_BF16X3) return DCOPF_ERR_UNSUPPORTED;
   DeviceGuard guard(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   if ((r = check_outage(h, batch, outage, s))) return r;
   if ((r = ensure_workspace(h, batch))) return r;
   if ((r = run_base_flows(h, batch, loads, outage, s))) return r;
-  if ((r = run_eval_unfused(h, batch, outage, lambda, mu_hi, mu_lo, precision, value, g_lambda,
-                            g_mu_hi, g_mu_lo, dispatch, s)))
-    return r;
+  if (precision == DCOPF_BF16X3)
+    r = run_eval_tensor(h, batch, outage, lambda, mu_hi, mu_lo, value, g_lambda, g_mu_hi, g_mu_lo,
+                        dispatch, s);
+  else
+    r = run_eval_unfused(h, batch, outage, lambda, mu_hi, mu_lo, precision, value, g_lambda,
+                         g_mu_hi, g_mu_lo, dispatch, s);
+  if (r) return r;
   return finish(h, s);
 }
 

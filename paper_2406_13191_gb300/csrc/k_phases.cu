@@ -280,11 +280,24 @@ dcopf_status run_eval_unfused(dcopf_dual* h, int B, const int* outage, const dou
                                         w.f.as<double>(), nullptr);
     if (dispatch) k_dispatch32<<<cdiv((long long)B * ng, 256), 256, 0, s>>>(N, B, w.x32.as<float>(), dispatch);
   }
+  h->launches += 4 + (dispatch ? 1 : 0);
+  return run_eval_finish(h, B, outage, lambda, mh, ml, value, glam, ghi, glo, nullptr, s);
+}
+
+// Tail of an evaluation once the flows f (FP64, before the outage correction) and the
+// cost / dispatch sums are in the workspace; `dispatch` takes x from w.x64.
+dcopf_status run_eval_finish(dcopf_dual* h, int B, const int* outage, const double* lambda,
+                             const double* mh, const double* ml, double* value, double* glam,
+                             double* ghi, double* glo, double* dispatch, cudaStream_t s) {
+  const DevNet& N = h->dev;
+  Workspace& w = h->ws;
+  if (dispatch)
+    k_dispatch<<<cdiv((long long)B * N.n_gen, 256), 256, 0, s>>>(N, B, w.x64.as<double>(), dispatch);
   k_grad_value<double, double><<<B, 256, 0, s>>>(N, outage, w.u64.as<double>(), lambda, mh, ml,
                                                  w.f.as<double>(), w.sumcost.as<double>(),
                                                  w.sump.as<double>(), w.demand.as<double>(), value,
                                                  glam, ghi, glo, nullptr);
-  h->launches += 5 + (dispatch ? 1 : 0);
+  h->launches += 1 + (dispatch ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
   return DCOPF_OK;

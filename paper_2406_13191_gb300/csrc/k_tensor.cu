@@ -1,0 +1,395 @@
+// Batched operator products on tcgen05 tensor cores for many instances of one
+// network: the adjoint Pi~ = H Phi~ (H = [batch][n_line] line multipliers) and the
+// forward F = X Phi~^T (X = [batch][n_gen] normalised dispatch), the two dense
+// contractions of every iteration (eq. (6): c + A^T lambda + C^T mu, and C x*).
+//
+// Precision: each FP32 operand v is split into BF16 v_hi = bf16(v) and
+// v_lo = bf16(v - v_hi) and the product is hi*hi + hi*lo + lo*hi with FP32 accumulation
+// in TMEM (3 MMAs per K step).  When one operand is exact in BF16 (the LP dispatch
+// x in {-1, 0, 1}) its lo part is zero and 2 MMAs suffice.
+//
+// Kernel shape: one 128 x 128 output tile per CTA (split along K for the adjoint,
+// whose K = n_line is long and whose N = n_gen is short), 6 warps: warp 0 issues TMA
+// loads of the four BF16 tiles of a 64-wide K block into a 3- or 4-stage ring
+// (128-byte swizzle), warp 1 allocates TMEM and one of its threads issues the MMAs,
+// warps 2-5 read the accumulator from TMEM (tcgen05.ld) and run the epilogue.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "dev.cuh"
+#include "kernels.h"
+#include "umma.cuh"
+
+namespace dcopf {
+
+enum { EPI_PARTIAL = 0, EPI_FLOW = 1 };
+
+struct GemmArgs {
+  int M, N, K;           // rows of A (instances), rows of B (outputs), contraction length
+  int kb_per_split;      // 64-wide K blocks per split
+  int epi;
+  float* P; int ldp;     // EPI_PARTIAL: P[split][M][ldp]
+  const double* f0; double* f; int ldf;  // EPI_FLOW: f = acc + f0, [M][ldf]
+  int* err;
+  uint64_t timeout_ns;
+};
+
+constexpr int GBM = 128, GBN = 128, GBK = 64;
+constexpr uint32_t TILE_BYTES = GBM * GBK * 2;  // 16 KB, also GBN * GBK * 2
+
+template <int NPROD>
+struct GemmCfg {
+  static constexpr int STAGES = NPROD == 3 ? 3 : 4;
+  static constexpr uint32_t STAGE_BYTES = (NPROD == 3 ? 4 : 3) * TILE_BYTES;
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
+};
+
+template <int NPROD>
+__global__ void __launch_bounds__(192, 1)
+    k_gemm_bf16x(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+                 const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
+                 GemmArgs g) {
+  using Cfg = GemmCfg<NPROD>;
+  constexpr int ST = Cfg::STAGES;
+  extern __shared__ __align__(16) unsigned char gsm_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[ST], empty[ST], accf;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  const int kb_total = (g.K + GBK - 1) / GBK;
+  const int kb0 = blockIdx.z * g.kb_per_split;
+  const int nkb = min(kb_total, kb0 + g.kb_per_split) - kb0;
+  auto a_hi = [&](int s) { return base + (size_t)s * Cfg::STAGE_BYTES; };
+  auto a_lo = [&](int s) { return a_hi(s) + TILE_BYTES; };
+  auto b_hi = [&](int s) { return a_hi(s) + (NPROD == 3 ? 2 : 1) * TILE_BYTES; };
+  auto b_lo = [&](int s) { return b_hi(s) + TILE_BYTES; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      umma::mbar_init(&full[s], 1);
+      umma::mbar_init(&empty[s], 1);
+    }
+    umma::mbar_init(&accf, 1);
+    s_abort = 0;
+    umma::fence_mbar_init();
+  }
+  if (warp == 1) umma::tmem_alloc(&tmem_base, GBN);
+  __syncthreads();
+  umma::tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  int issued = 0;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int i = 0; i < nkb && nkb > 0; ++i) {
+      const int s = i % ST;
+      if (i >= ST && !umma::mbar_wait(&empty[s], ((i / ST) & 1) ^ 1, g.timeout_ns)) {
+        s_abort = 1;
+        break;
+      }
+      umma::mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
+      const int x = (kb0 + i) * GBK;
+      umma::tma_load_2d(&tAh, &full[s], a_hi(s), x, m0);
+      if (NPROD == 3) umma::tma_load_2d(&tAl, &full[s], a_lo(s), x, m0);
+      umma::tma_load_2d(&tBh, &full[s], b_hi(s), x, n0);
+      umma::tma_load_2d(&tBl, &full[s], b_lo(s), x, n0);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(GBN);
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % ST;
+      if (!umma::mbar_wait(&full[s], (i / ST) & 1, g.timeout_ns)) {
+        s_abort = 1;
+        break;
+      }
+      umma::tc_fence_after();
+      const uint64_t dah = umma::desc_sw128(umma::smem_u32(a_hi(s)));
+      const uint64_t dal = umma::desc_sw128(umma::smem_u32(a_lo(s)));
+      const uint64_t dbh = umma::desc_sw128(umma::smem_u32(b_hi(s)));
+      const uint64_t dbl = umma::desc_sw128(umma::smem_u32(b_lo(s)));
+#pragma unroll
+      for (int kk = 0; kk < GBK / 16; ++kk) {
+        const uint64_t o = (uint64_t)(kk * 32) >> 4;  // 16 BF16 = 32 bytes along the row
+        umma::mma_bf16(tmem, dah + o, dbh + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        umma::mma_bf16(tmem, dah + o, dbl + o, idesc, 1u);
+        if (NPROD == 3) umma::mma_bf16(tmem, dal + o, dbh + o, idesc, 1u);
+      }
+      umma::mma_commit(&empty[s]);
+    }
+    umma::mma_commit(&accf);
+  } else if (warp >= 2) {
+    // ---------------- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
+    const bool ready = __all_sync(0xffffffffu, umma::mbar_wait(&accf, 0, g.timeout_ns));
+    umma::tc_fence_after();
+    const int q = warp & 3;
+    const int row = m0 + 32 * q + lane;
+    if (!ready) s_abort = 1;
+    if (ready && nkb > 0) {
+#pragma unroll 1
+      for (int cc = 0; cc < GBN / 32; ++cc) {
+        float v[32];
+        umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cc), v);
+        const int col0 = n0 + 32 * cc;
+        if (row < g.M) {
+          if (g.epi == EPI_PARTIAL) {
+            float* dst = g.P + ((size_t)blockIdx.z * g.M + row) * g.ldp + col0;
+            if (col0 + 32 <= g.N) {
+#pragma unroll
+              for (int u = 0; u < 8; ++u)
+                reinterpret_cast<float4*>(dst)[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+            } else {
+              for (int u = 0; u < 32 && col0 + u < g.N; ++u) dst[u] = v[u];
+            }
+          } else {
+            const double* f0 = g.f0 + (size_t)row * g.ldf + col0;
+            double* f = g.f + (size_t)row * g.ldf + col0;
+            for (int u = 0; u < 32 && col0 + u < g.N; ++u) f[u] = (double)v[u] + f0[u];
+          }
+        }
+      }
+    }
+  }
+  umma::tc_fence_before();  // order this thread's tcgen05 work before the teardown barrier
+  __syncthreads();
+  if (threadIdx.x == 0 && s_abort) {
+    atomicExch(g.err, (int)DCOPF_ERR_TIMEOUT);
+    // let the copies still in flight land before the CTA's shared memory is released
+    for (int i = max(0, issued - ST); i < issued; ++i)
+      umma::mbar_wait(&full[i % ST], (i / ST) & 1, g.timeout_ns);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    umma::tc_fence_after();
+    umma::tmem_dealloc(tmem, GBN);
+  }
+}
+
+// ------------------------------------------------------------------ operand preparation
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  *hi = h;
+  *lo = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// H[b][i] = mu_hi - mu_lo (outaged line: u^T eta, the adjoint of the post-outage PTDF),
+// split into BF16 hi/lo rows of stride ld.
+template <typename S>
+__global__ void k_split_eta(int nl, int ld, const S* __restrict__ mh, const S* __restrict__ ml,
+                            const int* __restrict__ outage, const float* __restrict__ u,
+                            __nv_bfloat16* __restrict__ Hh, __nv_bfloat16* __restrict__ Hl) {
+  __shared__ float red[32];
+  const int b = blockIdx.x;
+  const int k = outage ? outage[b] : -1;
+  float s = 0.f;
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+    const float v = (i == k) ? 0.f : (float)((double)mh[(size_t)b * nl + i] - (double)ml[(size_t)b * nl + i]);
+    split_bf16(v, Hh + (size_t)b * ld + i, Hl + (size_t)b * ld + i);
+    if (k >= 0) s += u[(size_t)b * nl + i] * v;
+  }
+  if (k >= 0) {
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) split_bf16(s, Hh + (size_t)b * ld + k, Hl + (size_t)b * ld + k);
+  }
+}
+
+// pi~ = sum of the split-K partials, closed-form minimiser, BF16 split of x, FP64
+// x for the dispatch output, per-instance cost and dispatch sums.
+__global__ void k_reduce_min(DevNet N, int splits, int M, int ldp, const float* __restrict__ P,
+                             const double* __restrict__ lambda, int ldx,
+                             __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl,
+                             double* __restrict__ x64, double* __restrict__ sumcost,
+                             double* __restrict__ sump) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  const int ng = N.n_gen;
+  const double lam = lambda[b];
+  double c = 0.0, p = 0.0;
+  for (int j = threadIdx.x; j < ng; j += blockDim.x) {
+    float s = 0.f;
+    for (int q = 0; q < splits; ++q) s += P[((size_t)q * M + b) * ldp + j];
+    const double w = N.ctil[j] + N.sigma[j] * lam + (double)s;
+    const double x = inner_x<double>(w, N.mq[j]);
+    split_bf16((float)x, Xh + (size_t)b * ldx + j, Xl + (size_t)b * ldx + j);
+    if (x64) x64[(size_t)b * ng + j] = x;
+    c += (N.mq[j] * x + N.ctil[j]) * x + N.cconst[j];
+    p += N.mid[j] + N.sigma[j] * x;
+  }
+  c = block_sum(c, red);
+  p = block_sum(p, red);
+  if (threadIdx.x == 0) {
+    sumcost[b] = c;
+    sump[b] = p;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 2-D BF16 tensor map over [rows][cols] with row stride ld elements (ld * 2 bytes a
+// multiple of 16), box of 64 columns x box_rows rows, 128-byte swizzle, zero fill
+// outside the tensor.
+static bool make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint64_t ld,
+                     uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || ((uintptr_t)ptr & 15) || ((ld * 2) & 15)) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld * 2};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static int round8(int n) { return (n + 7) & ~7; }
+
+// BF16 hi/lo copies of Phi~ (forward B operand, [n_line][ld_g]) and Phi~^T (adjoint B
+// operand, [n_gen][ld_l]), built once per handle.
+dcopf_status ensure_tensor_operands(dcopf_dual* h) {
+  TensorOps& T = h->tops;
+  if (T.ready) return DCOPF_OK;
+  const HostNet& H = h->host;
+  const int nl = H.n_line, ng = H.n_gen;
+  T.ld_l = round8(nl);
+  T.ld_g = round8(ng);
+  std::vector<__nv_bfloat16> ph((size_t)nl * T.ld_g), pl((size_t)nl * T.ld_g);
+  std::vector<__nv_bfloat16> th((size_t)ng * T.ld_l), tl((size_t)ng * T.ld_l);
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+  std::fill(ph.begin(), ph.end(), z); std::fill(pl.begin(), pl.end(), z);
+  std::fill(th.begin(), th.end(), z); std::fill(tl.begin(), tl.end(), z);
+  for (int i = 0; i < nl; ++i)
+    for (int j = 0; j < ng; ++j) {
+      const float v = (float)H.phi[(size_t)i * ng + j];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+      ph[(size_t)i * T.ld_g + j] = hi; pl[(size_t)i * T.ld_g + j] = lo;
+      th[(size_t)j * T.ld_l + i] = hi; tl[(size_t)j * T.ld_l + i] = lo;
+    }
+  auto up = [&](DBuf& d, const std::vector<__nv_bfloat16>& v) {
+    if (d.alloc(v.size() * 2) != cudaSuccess) return false;
+    return cudaMemcpy(d.p, v.data(), v.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  if (!up(T.phi_hi, ph) || !up(T.phi_lo, pl) || !up(T.phit_hi, th) || !up(T.phit_lo, tl))
+    return DCOPF_ERR_OOM;
+  if (!make_map(&T.m_phi_hi, T.phi_hi.p, nl, ng, T.ld_g, GBN) ||
+      !make_map(&T.m_phi_lo, T.phi_lo.p, nl, ng, T.ld_g, GBN) ||
+      !make_map(&T.m_phit_hi, T.phit_hi.p, ng, nl, T.ld_l, GBN) ||
+      !make_map(&T.m_phit_lo, T.phit_lo.p, ng, nl, T.ld_l, GBN))
+    return DCOPF_ERR_CUDA;
+  T.ready = true;
+  return DCOPF_OK;
+}
+
+// Per-batch BF16 operands and split-K partials.
+dcopf_status ensure_tensor_batch(dcopf_dual* h, int B) {
+  TensorOps& T = h->tops;
+  if (B <= T.cap) return DCOPF_OK;
+  const int nl = h->host.n_line, ng = h->host.n_gen;
+  const int ldp = (ng + 3) & ~3;
+  if (T.H_hi.alloc((size_t)B * T.ld_l * 2) || T.H_lo.alloc((size_t)B * T.ld_l * 2) ||
+      T.X_hi.alloc((size_t)B * T.ld_g * 2) || T.X_lo.alloc((size_t)B * T.ld_g * 2) ||
+      T.P.alloc((size_t)64 * B * ldp * 4))
+    return DCOPF_ERR_OOM;
+  cudaMemset(T.H_hi.p, 0, (size_t)B * T.ld_l * 2);
+  cudaMemset(T.H_lo.p, 0, (size_t)B * T.ld_l * 2);
+  cudaMemset(T.X_hi.p, 0, (size_t)B * T.ld_g * 2);
+  cudaMemset(T.X_lo.p, 0, (size_t)B * T.ld_g * 2);
+  if (!make_map(&T.m_H_hi, T.H_hi.p, B, nl, T.ld_l, GBM) ||
+      !make_map(&T.m_H_lo, T.H_lo.p, B, nl, T.ld_l, GBM) ||
+      !make_map(&T.m_X_hi, T.X_hi.p, B, ng, T.ld_g, GBM) ||
+      !make_map(&T.m_X_lo, T.X_lo.p, B, ng, T.ld_g, GBM))
+    return DCOPF_ERR_CUDA;
+  T.cap = B;
+  return DCOPF_OK;
+}
+
+template <int NPROD>
+static cudaError_t launch_gemm(dcopf_dual* h, const CUtensorMap& Ah, const CUtensorMap& Al,
+                               const CUtensorMap& Bh, const CUtensorMap& Bl, GemmArgs g, int splits,
+                               cudaStream_t s) {
+  using Cfg = GemmCfg<NPROD>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x<NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, splits);
+  k_gemm_bf16x<NPROD><<<grid, 192, Cfg::SMEM, s>>>(Ah, Al, Bh, Bl, g);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+// Split-K factor of the adjoint: enough CTAs to cover the SMs twice.
+static void adjoint_split(const dcopf_dual* h, int B, int* splits, int* kbps) {
+  const int tiles = ((B + GBM - 1) / GBM) * ((h->host.n_gen + GBN - 1) / GBN);
+  const int kb = (h->host.n_line + GBK - 1) / GBK;
+  int s = std::max(1, std::min(kb, std::min(64, (2 * h->sm_count + tiles - 1) / tiles)));
+  int per = (kb + s - 1) / s;
+  *kbps = per;
+  *splits = (kb + per - 1) / per;
+}
+
+// dcopf_dual_eval with BF16 split tensor-core products.
+dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const double* lambda,
+                             const double* mh, const double* ml, double* value, double* glam,
+                             double* ghi, double* glo, double* dispatch, cudaStream_t s) {
+  dcopf_status r;
+  if ((r = ensure_tensor_operands(h)) || (r = ensure_tensor_batch(h, B))) return r;
+  TensorOps& T = h->tops;
+  Workspace& w = h->ws;
+  const int nl = h->host.n_line, ng = h->host.n_gen;
+  k_split_eta<double><<<B, 256, 0, s>>>(nl, T.ld_l, mh, ml, outage, w.u32.as<float>(),
+                                        T.H_hi.as<__nv_bfloat16>(), T.H_lo.as<__nv_bfloat16>());
+  h->launches += 1;
+  int splits, kbps;
+  adjoint_split(h, B, &splits, &kbps);
+  GemmArgs g{};
+  g.M = B; g.N = ng; g.K = nl; g.kb_per_split = kbps; g.epi = EPI_PARTIAL;
+  g.P = T.P.as<float>(); g.ldp = (ng + 3) & ~3; g.err = h->d_err; g.timeout_ns = 2000000000ull;
+  if (launch_gemm<3>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi, T.m_phit_lo, g, splits, s) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  k_reduce_min<<<B, 256, 0, s>>>(h->dev, splits, B, g.ldp, T.P.as<float>(), lambda, T.ld_g,
+                                 T.X_hi.as<__nv_bfloat16>(), T.X_lo.as<__nv_bfloat16>(),
+                                 w.x64.as<double>(), w.sumcost.as<double>(), w.sump.as<double>());
+  h->launches += 1;
+  GemmArgs f{};
+  f.M = B; f.N = nl; f.K = ng; f.kb_per_split = (ng + GBK - 1) / GBK; f.epi = EPI_FLOW;
+  f.f0 = w.f0.as<double>(); f.f = w.f.as<double>(); f.ldf = nl; f.err = h->d_err;
+  f.timeout_ns = 2000000000ull;
+  cudaError_t e = h->host.qp
+                      ? launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, f, 1, s)
+                      : launch_gemm<2>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, f, 1, s);
+  if (e != cudaSuccess) return DCOPF_ERR_CUDA;
+  return run_eval_finish(h, B, outage, lambda, mh, ml, value, glam, ghi, glo, dispatch, s);
+}
+
+template __global__ void k_split_eta<float>(int, int, const float*, const float*, const int*,
+                                            const float*, __nv_bfloat16*, __nv_bfloat16*);
+
+}  // namespace dcopf

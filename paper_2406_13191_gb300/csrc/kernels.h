@@ -1,5 +1,6 @@
 // Library handle, workspaces and the host-side drivers of each execution path.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -71,6 +72,17 @@ struct Workspace {
   DBuf misc;  // small per-batch scratch
 };
 
+// BF16 hi/lo operands and TMA descriptors of the tensor-core path.
+struct TensorOps {
+  bool ready = false;
+  int ld_l = 0, ld_g = 0;  // padded row strides (elements) of [*][n_line] and [*][n_gen]
+  int cap = 0;             // batch capacity of the per-batch operands
+  DBuf phi_hi, phi_lo, phit_hi, phit_lo;
+  CUtensorMap m_phi_hi, m_phi_lo, m_phit_hi, m_phit_lo;
+  DBuf H_hi, H_lo, X_hi, X_lo, P;
+  CUtensorMap m_H_hi, m_H_lo, m_X_hi, m_X_lo;
+};
+
 struct StateBufs {
   int cap = 0;
   int elem = 0;  // sizeof(S) of the arrays below
@@ -86,6 +98,7 @@ struct dcopf_dual {
   std::vector<dcopf::DBuf*> owned;  // network arrays
   dcopf::Workspace ws;
   dcopf::StateBufs st32, st64;
+  dcopf::TensorOps tops;
   int* d_err = nullptr;  // sticky device error word
   unsigned* d_bar = nullptr;  // grid-barrier counters
   dcopf::DBuf active;  // one int: instances still running
@@ -126,10 +139,20 @@ dcopf_status run_eval_unfused(dcopf_dual* h, int batch, const int* outage, const
                               const double* mh, const double* ml, int precision, double* value,
                               double* glam, double* ghi, double* glo, double* dispatch,
                               cudaStream_t s);
+dcopf_status run_eval_finish(dcopf_dual* h, int batch, const int* outage, const double* lambda,
+                             const double* mh, const double* ml, double* value, double* glam,
+                             double* ghi, double* glo, double* dispatch, cudaStream_t s);
 template <typename S>
 dcopf_status run_iters_unfused(dcopf_dual* h, int batch, const int* outage, int precision,
                                const StepArgs& P, SolveState<S>& st, int n_iters, int max_iters,
                                double tol, cudaStream_t s);
+
+// k_tensor.cu
+dcopf_status ensure_tensor_operands(dcopf_dual* h);
+dcopf_status ensure_tensor_batch(dcopf_dual* h, int batch);
+dcopf_status run_eval_tensor(dcopf_dual* h, int batch, const int* outage, const double* lambda,
+                             const double* mh, const double* ml, double* value, double* glam,
+                             double* ghi, double* glo, double* dispatch, cudaStream_t s);
 
 // k_fused.cu
 dcopf_status run_wait_selftest(dcopf_dual* h, long long timeout_ns, cudaStream_t s);
