@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "DCOPF instances to 0.1% dual gap/sec on 1 GB300 vs plain FP64 GPU path"
 UNIT = "instances/s"
 GAP = 1e-3
-OURS = dict(rule="adam", alpha=1000.0, beta1=0.95, beta2=0.999, decay=0.999, max_iters=4000,
+OURS = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=4000,
             path="fused", precision="fp32")
 PLAIN = dict(rule="gdm", alpha=30.0, alpha_lambda=0.1, rho=0.995, max_iters=20000, path="plain",
              precision="fp64", check_every=20)

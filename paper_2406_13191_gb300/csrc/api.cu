@@ -17,6 +17,8 @@ dcopf_dual::~dcopf_dual() {
   if (d_bar) cudaFree(d_bar);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
+  if (tev) cudaEventDestroy(tev);
+  if (tstream) cudaStreamDestroy(tstream);
 }
 
 namespace dcopf {
@@ -176,6 +178,17 @@ __global__ void k_output(int B, int nl, SolveState<S> st, double* __restrict__ l
     if (iters) iters[b] = st.iter[b];
     if (status) status[b] = st.status[b];
   }
+}
+
+void k_init_state_f32(unsigned grid, cudaStream_t s, int B, int nl, int warm, const double* lam,
+                      const double* mh, const double* ml, const double* target, double gap,
+                      SolveState<float> st) {
+  k_init_state<float><<<grid, 256, 0, s>>>(B, nl, warm, lam, mh, ml, target, gap, st);
+}
+
+void k_output_f32(unsigned grid, cudaStream_t s, int B, int nl, SolveState<float> st, double* lam,
+                  double* mh, double* ml, double* bound, int* iters, int* status) {
+  k_output<float><<<grid, 256, 0, s>>>(B, nl, st, lam, mh, ml, bound, iters, status);
 }
 
 template <typename S>
@@ -501,7 +514,6 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
   if (path == DCOPF_PATH_AUTO) path = (batch == 1 && !outage) ? DCOPF_PATH_FUSED : DCOPF_PATH_BATCHED;
   if (path == DCOPF_PATH_FUSED && (batch != 1 || outage)) return DCOPF_ERR_UNSUPPORTED;
   int prec = p.precision;
-  if (path == DCOPF_PATH_BATCHED && prec == DCOPF_BF16X3) prec = DCOPF_FP32;
   DeviceGuard guard(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   if ((r = check_outage(h, batch, outage, s))) return r;
@@ -513,6 +525,9 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
   if (path == DCOPF_PATH_PLAIN)
     return solve_loop<double>(h, batch, loads, outage, q, path, lambda, mu_hi, mu_lo, best_bound,
                               iters, inst_status, s);
+  if (path == DCOPF_PATH_BATCHED && prec == DCOPF_BF16X3)
+    return solve_tensor<float>(h, batch, loads, outage, q, lambda, mu_hi, mu_lo, best_bound, iters,
+                               inst_status, s);
   return solve_loop<float>(h, batch, loads, outage, q, path, lambda, mu_hi, mu_lo, best_bound, iters,
                            inst_status, s);
 }

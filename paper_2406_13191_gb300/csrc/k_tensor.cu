@@ -26,7 +26,25 @@
 
 namespace dcopf {
 
-enum { EPI_PARTIAL = 0, EPI_FLOW = 1 };
+enum { EPI_PARTIAL = 0, EPI_FLOW = 1, EPI_STEP = 2 };
+
+// Fused epilogue of the forward product inside the batched solve: flows, supergradient,
+// line part of the dual value, projected step of mu, BF16 split of the next eta.
+struct StepEpi {
+  StepArgs P;
+  const float* f0;            // [B][nl] flows of the mid-box dispatch minus the loads
+  const float* u;             // [B][nl] outage vectors (rows of outage instances)
+  const int* outage;          // [B] or null
+  const float* tout;          // [B] pre-outage flow on the outaged line, (Phi~ x)_k
+  const float* fmax; const float* fmin;
+  const int* iter;            // [B] evaluations done: parity selects the state buffer
+  const int* frozen;          // [B] done or waiting for certification
+  const float* stepf;         // [B][4] alpha scale, 1 - beta1^t, 1 - beta2^t
+  float* mu_hi[2]; float* mu_lo[2];
+  float* s1_hi; float* s2_hi; float* s1_lo; float* s2_lo;
+  __nv_bfloat16* Hh; __nv_bfloat16* Hl; int ldh;
+  double* line_part; double* out_part; int n_tiles;   // [B][n_tiles]
+};
 
 struct GemmArgs {
   int M, N, K;           // rows of A (instances), rows of B (outputs), contraction length
@@ -36,6 +54,7 @@ struct GemmArgs {
   const double* f0; double* f; int ldf;  // EPI_FLOW: f = acc + f0, [M][ldf]
   int* err;
   uint64_t timeout_ns;
+  StepEpi se;
 };
 
 constexpr int GBM = 128, GBN = 128, GBK = 64;
@@ -47,6 +66,61 @@ struct GemmCfg {
   static constexpr uint32_t STAGE_BYTES = (NPROD == 3 ? 4 : 3) * TILE_BYTES;
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 };
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo);
+
+__device__ __forceinline__ float step_rule(const StepArgs& P, float theta, float g, float& s1,
+                                           float& s2, float a, float bc1, float bc2) {
+  if (P.rule == DCOPF_GDM) {
+    s1 = (float)P.rho * s1 + a * g;
+    theta += s1;
+    if (P.as_printed) theta += a * g;
+  } else if (P.rule == DCOPF_ADAM) {
+    s1 = (float)P.beta1 * s1 + (1.f - (float)P.beta1) * g;
+    s2 = (float)P.beta2 * s2 + (1.f - (float)P.beta2) * g * g;
+    theta += a * (s1 / bc1) / (sqrtf(s2 / bc2) + (float)P.eps);
+  } else {
+    s1 += g * g;
+    theta += a * g / (sqrtf(s1) + (float)P.eps);
+  }
+  return theta;
+}
+
+// One row (instance b) x 32 columns (lines) of the fused step epilogue.
+__device__ __forceinline__ void step_epilogue(const StepEpi& E, int nl, int b, int col0,
+                                              const float* v, double& lacc, double& oacc) {
+  const int k = E.outage ? E.outage[b] : -1;
+  const float t_out = k >= 0 ? E.tout[b] : 0.f;
+  const int pb = E.iter[b] & 1;
+  const float* mhc = E.mu_hi[pb] + (size_t)b * nl;
+  const float* mlc = E.mu_lo[pb] + (size_t)b * nl;
+  float* mhn = E.mu_hi[pb ^ 1] + (size_t)b * nl;
+  float* mln = E.mu_lo[pb ^ 1] + (size_t)b * nl;
+  const float am = E.stepf[4 * b], bc1 = E.stepf[4 * b + 1], bc2 = E.stepf[4 * b + 2];
+  const size_t o = (size_t)b * nl;
+  for (int u = 0; u < 32; ++u) {
+    const int i = col0 + u;
+    if (i >= nl) break;
+    float f = v[u] + E.f0[o + i];
+    float ui = 0.f;
+    if (k >= 0) { ui = E.u[o + i]; f += ui * t_out; }
+    float gh = f - E.fmax[i], gl = E.fmin[i] - f;
+    const float mh = mhc[i], ml = mlc[i];
+    float nh = 0.f, nlo = 0.f;
+    if (i != k) {
+      lacc += (double)mh * (double)gh + (double)ml * (double)gl;
+      float a1 = E.s1_hi[o + i], a2 = E.s2_hi[o + i], b1 = E.s1_lo[o + i], b2 = E.s2_lo[o + i];
+      nh = fmaxf(step_rule(E.P, mh, gh, a1, a2, am, bc1, bc2), 0.f);
+      nlo = fmaxf(step_rule(E.P, ml, gl, b1, b2, am, bc1, bc2), 0.f);
+      E.s1_hi[o + i] = a1; E.s2_hi[o + i] = a2; E.s1_lo[o + i] = b1; E.s2_lo[o + i] = b2;
+    }
+    mhn[i] = nh;
+    mln[i] = nlo;
+    const float eta = nh - nlo;
+    split_bf16(eta, E.Hh + (size_t)b * E.ldh + i, E.Hl + (size_t)b * E.ldh + i);
+    if (k >= 0) oacc += (double)ui * (double)eta;
+  }
+}
 
 template <int NPROD>
 __global__ void __launch_bounds__(192, 1)
@@ -132,13 +206,17 @@ __global__ void __launch_bounds__(192, 1)
     const int q = warp & 3;
     const int row = m0 + 32 * q + lane;
     if (!ready) s_abort = 1;
+    const bool step_row = g.epi == EPI_STEP && row < g.M && !g.se.frozen[row];
+    double lacc = 0.0, oacc = 0.0;
     if (ready && nkb > 0) {
 #pragma unroll 1
       for (int cc = 0; cc < GBN / 32; ++cc) {
         float v[32];
         umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cc), v);
         const int col0 = n0 + 32 * cc;
-        if (row < g.M) {
+        if (g.epi == EPI_STEP) {
+          if (step_row) step_epilogue(g.se, g.N, row, col0, v, lacc, oacc);
+        } else if (row < g.M) {
           if (g.epi == EPI_PARTIAL) {
             float* dst = g.P + ((size_t)blockIdx.z * g.M + row) * g.ldp + col0;
             if (col0 + 32 <= g.N) {
@@ -155,6 +233,10 @@ __global__ void __launch_bounds__(192, 1)
           }
         }
       }
+    }
+    if (step_row) {
+      g.se.line_part[(size_t)row * g.se.n_tiles + blockIdx.x] = lacc;
+      g.se.out_part[(size_t)row * g.se.n_tiles + blockIdx.x] = oacc;
     }
   }
   umma::tc_fence_before();  // order this thread's tcgen05 work before the teardown barrier
@@ -266,6 +348,7 @@ static bool make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t co
 }
 
 static int round8(int n) { return (n + 7) & ~7; }
+static cudaError_t prepare_gemm();
 
 // BF16 hi/lo copies of Phi~ (forward B operand, [n_line][ld_g]) and Phi~^T (adjoint B
 // operand, [n_gen][ld_l]), built once per handle.
@@ -300,6 +383,7 @@ dcopf_status ensure_tensor_operands(dcopf_dual* h) {
       !make_map(&T.m_phit_hi, T.phit_hi.p, ng, nl, T.ld_l, GBN) ||
       !make_map(&T.m_phit_lo, T.phit_lo.p, ng, nl, T.ld_l, GBN))
     return DCOPF_ERR_CUDA;
+  if (prepare_gemm() != cudaSuccess) return DCOPF_ERR_CUDA;
   T.ready = true;
   return DCOPF_OK;
 }
@@ -327,18 +411,20 @@ dcopf_status ensure_tensor_batch(dcopf_dual* h, int B) {
   return DCOPF_OK;
 }
 
+// Sets the GEMM kernels' shared-memory limits (outside any stream capture).
+static cudaError_t prepare_gemm() {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)GemmCfg<2>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gemm_bf16x<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)GemmCfg<3>::SMEM);
+}
+
 template <int NPROD>
 static cudaError_t launch_gemm(dcopf_dual* h, const CUtensorMap& Ah, const CUtensorMap& Al,
                                const CUtensorMap& Bh, const CUtensorMap& Bl, GemmArgs g, int splits,
                                cudaStream_t s) {
   using Cfg = GemmCfg<NPROD>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x<NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, splits);
   k_gemm_bf16x<NPROD><<<grid, 192, Cfg::SMEM, s>>>(Ah, Al, Bh, Bl, g);
   h->launches += 1;
@@ -391,5 +477,308 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
 
 template __global__ void k_split_eta<float>(int, int, const float*, const float*, const int*,
                                             const float*, __nv_bfloat16*, __nv_bfloat16*);
+
+
+// ------------------------------------------------------------------ batched solve
+// pi~ from the split-K partials, minimiser, BF16 split of x, per-instance cost and
+// dispatch, the pre-outage flow (Phi~ x)_k of an outaged line, the step factors of
+// this step (running powers), and the lambda step (Section 3.3).
+__global__ void k_bt_minimize(DevNet N, int splits, int M, int ldp, const float* __restrict__ P,
+                              SolveStateBase st, BatchView bb, StepArgs SP, int ldx,
+                              __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl,
+                              const int* __restrict__ outage, const double* __restrict__ demand) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  if (bb.frozen[b]) return;
+  const int ng = N.n_gen;
+  const int k = outage ? outage[b] : -1;
+  const double lam = st.lam[b];
+  double c = 0.0, p = 0.0, to = 0.0;
+  for (int j = threadIdx.x; j < ng; j += blockDim.x) {
+    float s = 0.f;
+    for (int q = 0; q < splits; ++q) s += P[((size_t)q * M + b) * ldp + j];
+    const double w = N.ctil[j] + N.sigma[j] * lam + (double)s;
+    const double x = inner_x<double>(w, N.mq[j]);
+    split_bf16((float)x, Xh + (size_t)b * ldx + j, Xl + (size_t)b * ldx + j);
+    c += (N.mq[j] * x + N.ctil[j]) * x + N.cconst[j];
+    p += N.mid[j] + N.sigma[j] * x;
+    if (k >= 0) to += (double)N.phi32[(size_t)k * ng + j] * x;
+  }
+  c = block_sum(c, red);
+  p = block_sum(p, red);
+  if (k >= 0) to = block_sum(to, red);
+  if (threadIdx.x == 0) {
+    bb.cost[b] = c;
+    bb.psum[b] = p;
+    bb.tout[b] = (float)to;
+    bb.lam_eval[b] = lam;
+    // step t = iter + 1: scale decay^(t-1), bias corrections 1 - beta^t
+    const double d = bb.pw[3 * b], b1 = bb.pw[3 * b + 1] * SP.beta1, b2 = bb.pw[3 * b + 2] * SP.beta2;
+    bb.stepf[4 * b] = (float)(SP.alpha * d);
+    bb.stepf[4 * b + 1] = (float)(1.0 - b1);
+    bb.stepf[4 * b + 2] = (float)(1.0 - b2);
+    bb.pw[3 * b] = d * SP.decay;
+    bb.pw[3 * b + 1] = b1;
+    bb.pw[3 * b + 2] = b2;
+    const double g = p - demand[b], a = SP.alpha_lambda * d;
+    double s1 = st.lam_s1[b], s2 = st.lam_s2[b], l = lam;
+    if (SP.rule == DCOPF_GDM) {
+      s1 = SP.rho * s1 + a * g;
+      l += s1;
+      if (SP.as_printed) l += a * g;
+    } else if (SP.rule == DCOPF_ADAM) {
+      s1 = SP.beta1 * s1 + (1.0 - SP.beta1) * g;
+      s2 = SP.beta2 * s2 + (1.0 - SP.beta2) * g * g;
+      l += a * (s1 / (1.0 - b1)) / (sqrt(s2 / (1.0 - b2)) + SP.eps);
+    } else {
+      s1 += g * g;
+      l += a * g / (sqrt(s1) + SP.eps);
+    }
+    st.lam[b] = l;
+    st.lam_s1[b] = s1;
+    st.lam_s2[b] = s2;
+  }
+}
+
+// Dual value of the evaluated point (FP64), best value, outage patch of the next
+// eta, stop tests.  A stopping instance is frozen with its point in the state buffer
+// of parity iter & 1.  One warp per instance.
+__global__ void k_bt_finalize(int B, int ld_l, int max_iters, double tol, SolveStateBase st,
+                              BatchView bb, const int* __restrict__ outage,
+                              const double* __restrict__ demand,
+                              __nv_bfloat16* __restrict__ Hh, __nv_bfloat16* __restrict__ Hl) {
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (b >= B || bb.frozen[b]) return;
+  const int nt = bb.n_tiles;
+  double ls = 0.0, os = 0.0;
+  for (int q = lane; q < nt; q += 32) {
+    ls += bb.line_part[(size_t)b * nt + q];
+    os += bb.out_part[(size_t)b * nt + q];
+  }
+  ls = warp_sum(ls);
+  os = warp_sum(os);
+  if (lane != 0) return;
+  const double val = bb.cost[b] + bb.lam_eval[b] * (bb.psum[b] - demand[b]) + ls;
+  const int t = st.iter[b] + 1;
+  if (val > st.best[b]) { st.best[b] = val; st.best_iter[b] = t; }
+  const int k = outage ? outage[b] : -1;
+  if (k >= 0) split_bf16((float)os, Hh + (size_t)b * ld_l + k, Hl + (size_t)b * ld_l + k);
+  int c = 0;
+  if (st.has_target && val >= st.thresh[b] + st.margin[b]) c = 1;
+  else if (t >= max_iters) c = 2;
+  else if (tol > 0.0 && t > 1 && fabs(val - st.prev[b]) < tol) c = 2;
+  st.prev[b] = val;
+  if (c) {
+    st.cand[b] = c;
+    bb.frozen[b] = 1;
+    st.best_lam[b] = bb.lam_eval[b];
+  } else {
+    st.iter[b] = t;
+  }
+}
+
+// Copies the frozen candidates' points (state buffer of parity iter & 1) to best_*.
+__global__ void k_bt_select(int B, int nl, SolveState<float> st, BatchView bb) {
+  const int b = blockIdx.y;
+  if (!st.cand[b] || st.done[b]) return;
+  const int pb = st.iter[b] & 1;
+  const float* sh = pb ? bb.mu2_hi : st.mu_hi;
+  const float* sl = pb ? bb.mu2_lo : st.mu_lo;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
+    st.best_hi[(size_t)b * nl + i] = sh[(size_t)b * nl + i];
+    st.best_lo[(size_t)b * nl + i] = sl[(size_t)b * nl + i];
+  }
+}
+
+// After certification: accept, stop, or unfreeze with a larger in-loop margin.  The
+// evaluation of a frozen point counts; an unfrozen instance moves on to the point
+// already stepped to.
+__global__ void k_bt_accept(int B, double ub_any, SolveStateBase st, BatchView bb, int* active) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  if (!st.done[b] && st.cand[b]) {
+    const double c = st.cert[b];
+    if (st.cand[b] == 1) {
+      if (c >= st.thresh[b]) {
+        st.done[b] = 1;
+        st.status[b] = 0;
+      } else {
+        st.margin[b] += fmax(st.thresh[b] - c, 1e-7 * fabs(st.thresh[b]));
+        st.cand[b] = 0;
+        bb.frozen[b] = 0;
+      }
+    } else {
+      st.done[b] = 1;
+      st.status[b] = (c >= st.thresh[b]) ? 0 : 1;
+    }
+    if (c > ub_any) { st.done[b] = 1; st.status[b] = 2; bb.frozen[b] = 1; }
+    st.iter[b] += 1;
+  }
+  if (!st.done[b]) atomicAdd(active, 1);
+}
+
+__global__ void k_bt_init(int B, BatchView bb) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    bb.frozen[b] = 0;
+    bb.pw[3 * b] = 1.0;
+    bb.pw[3 * b + 1] = 1.0;
+    bb.pw[3 * b + 2] = 1.0;
+  }
+}
+
+static dcopf_status ensure_batch_bufs(dcopf_dual* h, int B, int n_tiles) {
+  BatchBufs& bb = h->bb;
+  BatchView& v = bb.v;
+  const size_t nl = h->host.n_line;
+  if (bb.mu2.alloc((size_t)B * nl * 2 * sizeof(float)) ||
+      bb.parts.alloc((size_t)B * n_tiles * 2 * sizeof(double)) ||
+      bb.small.alloc((size_t)B * 6 * sizeof(double) + (size_t)B * 6 * sizeof(float) + 1024))
+    return DCOPF_ERR_OOM;
+  v.mu2_hi = bb.mu2.as<float>();
+  v.mu2_lo = v.mu2_hi + (size_t)B * nl;
+  v.line_part = bb.parts.as<double>();
+  v.out_part = v.line_part + (size_t)B * n_tiles;
+  double* d = bb.small.as<double>();
+  v.lam_eval = d; v.cost = d + B; v.psum = d + 2 * (size_t)B; v.pw = d + 3 * (size_t)B;  // pw: [B][3]
+  float* f = (float*)(d + 6 * (size_t)B);
+  v.tout = f; v.stepf = f + B;  // stepf: [B][4]
+  v.frozen = (int*)(f + 5 * (size_t)B);
+  v.n_tiles = n_tiles;
+  return DCOPF_OK;
+}
+
+template <typename S>
+dcopf_status solve_tensor(dcopf_dual* h, int B, const double* loads, const int* outage,
+                          const dcopf_solve_params& p, double* lam, double* mh, double* ml,
+                          double* bound, int* iters, int* status, cudaStream_t s) {
+  static_assert(sizeof(S) == 4, "the tensor-core solve keeps FP32 state");
+  dcopf_status r;
+  if ((r = ensure_tensor_operands(h)) || (r = ensure_tensor_batch(h, B))) return r;
+  SolveState<float> st{};
+  if ((r = ensure_state<float>(h, B, &st))) return r;
+  const int nl = h->host.n_line, ng = h->host.n_gen;
+  const int n_tiles = (nl + GBN - 1) / GBN;
+  if ((r = ensure_batch_bufs(h, B, n_tiles))) return r;
+  TensorOps& T = h->tops;
+  Workspace& w = h->ws;
+  BatchView& bb = h->bb.v;
+  st.has_target = p.target_value != nullptr;
+  StepArgs P{};
+  P.rule = p.rule; P.as_printed = p.as_printed; P.alpha = p.alpha;
+  P.alpha_lambda = p.alpha_lambda > 0 ? p.alpha_lambda : p.alpha;
+  P.rho = p.rho; P.beta1 = p.beta1; P.beta2 = p.beta2; P.eps = p.eps; P.decay = p.decay;
+  // work on an internal stream (graph capture needs a capturable stream)
+  if (!h->tstream && cudaStreamCreateWithFlags(&h->tstream, cudaStreamNonBlocking) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  cudaStream_t cs = h->tstream;
+  if (!h->tev && cudaEventCreateWithFlags(&h->tev, cudaEventDisableTiming) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  if (cudaEventRecord(h->tev, s) != cudaSuccess || cudaStreamWaitEvent(cs, h->tev, 0) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  unsigned gi = std::min<unsigned>((unsigned)(((long long)B * nl + 255) / 256), 4096);
+  k_init_state_f32(gi, cs, B, nl, p.warm_start, lam, mh, ml, p.target_value, p.gap, st);
+  k_bt_init<<<(B + 255) / 256, 256, 0, cs>>>(B, bb);
+  k_split_eta<float><<<B, 256, 0, cs>>>(nl, T.ld_l, st.mu_hi, st.mu_lo, outage, w.u32.as<float>(),
+                                        T.H_hi.as<__nv_bfloat16>(), T.H_lo.as<__nv_bfloat16>());
+  h->launches += 3;
+  int splits, kbps;
+  adjoint_split(h, B, &splits, &kbps);
+  GemmArgs ga{};
+  ga.M = B; ga.N = ng; ga.K = nl; ga.kb_per_split = kbps; ga.epi = EPI_PARTIAL;
+  ga.P = T.P.as<float>(); ga.ldp = (ng + 3) & ~3; ga.err = h->d_err; ga.timeout_ns = 2000000000ull;
+  GemmArgs gf{};
+  gf.M = B; gf.N = nl; gf.K = ng; gf.kb_per_split = (ng + GBK - 1) / GBK; gf.epi = EPI_STEP;
+  gf.err = h->d_err; gf.timeout_ns = 2000000000ull;
+  StepEpi& E = gf.se;
+  E.P = P; E.f0 = w.f0_32.as<float>(); E.u = w.u32.as<float>(); E.outage = outage; E.tout = bb.tout;
+  E.fmax = h->dev.fmax32; E.fmin = h->dev.fmin32; E.iter = st.iter; E.frozen = bb.frozen;
+  E.stepf = bb.stepf;
+  E.mu_hi[0] = st.mu_hi; E.mu_hi[1] = bb.mu2_hi; E.mu_lo[0] = st.mu_lo; E.mu_lo[1] = bb.mu2_lo;
+  E.s1_hi = st.s1_hi; E.s2_hi = st.s2_hi; E.s1_lo = st.s1_lo; E.s2_lo = st.s2_lo;
+  E.Hh = T.H_hi.as<__nv_bfloat16>(); E.Hl = T.H_lo.as<__nv_bfloat16>(); E.ldh = T.ld_l;
+  E.line_part = bb.line_part; E.out_part = bb.out_part; E.n_tiles = n_tiles;
+  const int chunk = std::max(16, p.check_every);
+  // capture `chunk` iterations in a CUDA graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const long long launches_before_capture = h->launches;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DCOPF_ERR_CUDA;
+  bool cap_ok = true;
+  for (int it = 0; it < chunk && cap_ok; ++it) {
+    cap_ok &= launch_gemm<3>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi, T.m_phit_lo, ga, splits, cs) == cudaSuccess;
+    k_bt_minimize<<<B, 256, 0, cs>>>(h->dev, splits, B, ga.ldp, T.P.as<float>(), st, bb, P, T.ld_g,
+                                     T.X_hi.as<__nv_bfloat16>(), T.X_lo.as<__nv_bfloat16>(), outage,
+                                     w.demand.as<double>());
+    cap_ok &= (h->host.qp ? launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, gf, 1, cs)
+                          : launch_gemm<2>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, gf, 1, cs)) ==
+              cudaSuccess;
+    k_bt_finalize<<<(B + 3) / 4, 128, 0, cs>>>(B, T.ld_l, p.max_iters, p.tol, st, bb, outage,
+                                               w.demand.as<double>(), T.H_hi.as<__nv_bfloat16>(),
+                                               T.H_lo.as<__nv_bfloat16>());
+  }
+  cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+  h->launches = launches_before_capture;  // counted per replay below
+  if (!cap_ok || ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return DCOPF_ERR_CUDA;
+  }
+  const long long per_chunk = 4LL * chunk;
+  dcopf_status out = DCOPF_OK;
+  if (h->active.alloc(16) != cudaSuccess) out = DCOPF_ERR_OOM;
+  int* d_active = h->active.as<int>();
+  if (h->timing && !h->ev0) {
+    cudaEventCreate(&h->ev0);
+    cudaEventCreate(&h->ev1);
+  }
+  for (int round = 0; out == DCOPF_OK; ++round) {
+    if (h->timing) cudaEventRecord(h->ev0, cs);
+    if (cudaGraphLaunch(exec, cs) != cudaSuccess) { out = DCOPF_ERR_CUDA; break; }
+    h->launches += per_chunk;
+    if (h->timing) cudaEventRecord(h->ev1, cs);
+    k_bt_select<<<dim3((nl + 255) / 256, B), 256, 0, cs>>>(B, nl, st, bb);
+    if ((out = run_certify_t<float>(h, B, loads, outage, st.best_lam, st.best_hi, st.best_lo, st.cert,
+                                    nullptr, st.cand, st.done, cs)))
+      break;
+    cudaMemsetAsync(d_active, 0, sizeof(int), cs);
+    k_bt_accept<<<(B + 127) / 128, 128, 0, cs>>>(B, h->ub_any, st, bb, d_active);
+    h->launches += 2;
+    int active = 0;
+    if (cudaMemcpyAsync(&active, d_active, sizeof(int), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess) {
+      out = DCOPF_ERR_CUDA;
+      break;
+    }
+    if (h->timing) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+      h->t_iter_ms += ms;
+      h->t_iter_launches += per_chunk;
+    }
+    int derr = 0;
+    cudaMemcpy(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (derr) { out = (dcopf_status)derr; break; }
+    if (active == 0) break;
+    if ((long long)round * chunk > 4LL * p.max_iters + 64) break;
+  }
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  if (out != DCOPF_OK) return out;
+  k_output_f32(gi, cs, B, nl, st, lam, mh, ml, bound, iters, status);
+  h->launches += 1;
+  if (cudaEventRecord(h->tev, cs) != cudaSuccess || cudaStreamWaitEvent(s, h->tev, 0) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  if (h->timing) {
+    std::vector<int> it(B);
+    cudaMemcpy(it.data(), st.iter, sizeof(int) * B, cudaMemcpyDeviceToHost);
+    for (int v : it) h->t_evals += v;
+  }
+  return DCOPF_OK;
+}
+
+template dcopf_status solve_tensor<float>(dcopf_dual*, int, const double*, const int*,
+                                          const dcopf_solve_params&, double*, double*, double*,
+                                          double*, int*, int*, cudaStream_t);
 
 }  // namespace dcopf

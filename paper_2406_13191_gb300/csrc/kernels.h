@@ -83,6 +83,27 @@ struct TensorOps {
   CUtensorMap m_H_hi, m_H_lo, m_X_hi, m_X_lo;
 };
 
+// Extra per-instance state of the batched tensor-core solve (device pointers).
+struct BatchView {
+  int n_tiles = 0;             // line tiles of the forward product
+  int* frozen = nullptr;       // [B] done or waiting for certification
+  double* lam_eval = nullptr;  // [B] lambda of the evaluated point
+  double* cost = nullptr;      // [B] generation cost at the minimiser
+  double* psum = nullptr;      // [B] total dispatch
+  double* pw = nullptr;        // [B][3] decay^t, beta1^t, beta2^t
+  float* tout = nullptr;       // [B] pre-outage flow on the outaged line
+  float* stepf = nullptr;      // [B][4] step factors of the current step
+  float* mu2_hi = nullptr;     // [B][nl] second state buffer (parity 1)
+  float* mu2_lo = nullptr;
+  double* line_part = nullptr; // [B][n_tiles]
+  double* out_part = nullptr;  // [B][n_tiles]
+};
+
+struct BatchBufs {
+  DBuf mu2, parts, small;
+  BatchView v;
+};
+
 struct StateBufs {
   int cap = 0;
   int elem = 0;  // sizeof(S) of the arrays below
@@ -99,10 +120,13 @@ struct dcopf_dual {
   dcopf::Workspace ws;
   dcopf::StateBufs st32, st64;
   dcopf::TensorOps tops;
+  dcopf::BatchBufs bb;
   int* d_err = nullptr;  // sticky device error word
   unsigned* d_bar = nullptr;  // grid-barrier counters
   dcopf::DBuf active;  // one int: instances still running
-  double ub_any = 0.0;  // cost of the dearest dispatch (upper bound on any primal cost)
+  double ub_any = 0.0;
+  cudaStream_t tstream = nullptr;  // internal stream of the graph-captured batched solve
+  cudaEvent_t tev = nullptr;  // cost of the dearest dispatch (upper bound on any primal cost)
   long long launches = 0;
   // optional event timing of the iteration kernels
   bool timing = false;
@@ -124,6 +148,12 @@ namespace dcopf {
 dcopf_status ensure_workspace(dcopf_dual* h, int batch);
 template <typename S>
 dcopf_status ensure_state(dcopf_dual* h, int batch, SolveState<S>* st);
+
+void k_init_state_f32(unsigned grid, cudaStream_t s, int B, int nl, int warm, const double* lam,
+                      const double* mh, const double* ml, const double* target, double gap,
+                      SolveState<float> st);
+void k_output_f32(unsigned grid, cudaStream_t s, int B, int nl, SolveState<float> st, double* lam,
+                  double* mh, double* ml, double* bound, int* iters, int* status);
 
 // k_sparse.cu
 dcopf_status run_base_flows(dcopf_dual* h, int batch, const double* loads, const int* outage,
@@ -150,6 +180,10 @@ dcopf_status run_iters_unfused(dcopf_dual* h, int batch, const int* outage, int 
 // k_tensor.cu
 dcopf_status ensure_tensor_operands(dcopf_dual* h);
 dcopf_status ensure_tensor_batch(dcopf_dual* h, int batch);
+template <typename S>
+dcopf_status solve_tensor(dcopf_dual* h, int batch, const double* loads, const int* outage,
+                          const dcopf_solve_params& p, double* lam, double* mh, double* ml,
+                          double* bound, int* iters, int* status, cudaStream_t s);
 dcopf_status run_eval_tensor(dcopf_dual* h, int batch, const int* outage, const double* lambda,
                              const double* mh, const double* ml, double* value, double* glam,
                              double* ghi, double* glo, double* dispatch, cudaStream_t s);
