@@ -209,6 +209,32 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
                                     double* best_bound, int32_t* iters, int32_t* inst_status,
                                     void* stream);
 
+/* dcopf_dual_eval without any device allocation, for callers that cannot allocate
+ * device memory (a host framework that owns every allocation, or a real-time loop
+ * where cudaMalloc's implicit synchronisation and latency are not acceptable).  The
+ * paper has no counterpart: this is an interface convenience.
+ *
+ * Same arguments, results and errors as dcopf_dual_eval, for precision DCOPF_FP64 or
+ * DCOPF_FP32 (DCOPF_BF16X3 returns DCOPF_ERR_UNSUPPORTED).  Instead of the handle's
+ * workspace, every intermediate array lives in one fixed device array of 16 MiB
+ * compiled into the library (each GPU that loads the library holds it until the
+ * process exits).  A call needs 256-byte-aligned sections of about
+ * batch * (8 * (4 * n_line + 2 * n_gen) + 24) bytes for FP64 (less for FP32); a batch
+ * that does not fit returns DCOPF_ERR_INVALID_ARG before anything is enqueued.
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, which may also load the library's device code); make that
+ * first call before any stream capture.  All calls on a device share the one array
+ * and it keeps the last call's contents, which every call fully overwrites before
+ * reading: calls whose device work overlaps (different streams, or different host
+ * threads) race on it and must be serialised by the caller.  Outage indices are
+ * copied back and checked on the host, which synchronises `stream`. */
+dcopf_status dcopf_dual_eval_noalloc(dcopf_dual_t h, int32_t batch, const double* loads,
+                                     const int32_t* outage, const double* lambda,
+                                     const double* mu_hi, const double* mu_lo, int32_t precision,
+                                     double* value, double* g_lambda, double* g_mu_hi,
+                                     double* g_mu_lo, double* dispatch, void* stream);
+
 /* Number of kernels this handle has launched since creation (for launch accounting). */
 int64_t dcopf_dual_kernel_launches(dcopf_dual_t h);
 

@@ -12,7 +12,7 @@ EXPORTS = ("dcopf_version", "dcopf_status_string", "dcopf_solve_params_default",
            "dcopf_dual_create", "dcopf_dual_destroy", "dcopf_dual_info", "dcopf_dual_eval",
            "dcopf_dual_certify_bound", "dcopf_dual_solve_batch", "dcopf_dual_kernel_launches",
            "dcopf_dual_device_error", "dcopf_dual_set_timing", "dcopf_dual_read_timing",
-           "dcopf_selftest_bounded_wait")
+           "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc")
 
 STATUS = {0: "DCOPF_OK", 1: "DCOPF_ERR_INVALID_ARG", 2: "DCOPF_ERR_NETWORK", 3: "DCOPF_ERR_CUDA",
           4: "DCOPF_ERR_OOM", 5: "DCOPF_ERR_TIMEOUT", 6: "DCOPF_ERR_UNSUPPORTED"}
@@ -85,11 +85,13 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.dcopf_dual_device_error.argtypes = [P]
     lib.dcopf_dual_set_timing.argtypes = [P, C.c_int32]
     lib.dcopf_selftest_bounded_wait.argtypes = [P, C.c_int64, P]
+    lib.dcopf_dual_eval_noalloc.argtypes = [P, C.c_int32, P, P, P, P, P, C.c_int32, P, P, P, P,
+                                            P, P]
     lib.dcopf_dual_read_timing.argtypes = [P, F64P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     for name in ("dcopf_dual_create", "dcopf_dual_destroy", "dcopf_dual_info", "dcopf_dual_eval",
                  "dcopf_dual_certify_bound", "dcopf_dual_solve_batch", "dcopf_dual_device_error",
                  "dcopf_dual_set_timing", "dcopf_dual_read_timing",
-                 "dcopf_selftest_bounded_wait"):
+                 "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib

@@ -136,6 +136,11 @@ __global__ void k_grad_value(DevNet N, const int* __restrict__ outage, const dou
   }
 }
 
+__global__ void k_to_float(long long n, const double* __restrict__ a, float* __restrict__ b) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) b[t] = (float)a[t];
+}
+
 __global__ void k_dispatch(DevNet N, int B, const double* __restrict__ x, double* __restrict__ p) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= B * N.n_gen) return;
@@ -338,6 +343,39 @@ dcopf_status run_iters_unfused(dcopf_dual* h, int B, const int* outage, int prec
     k_close_iter<<<cdiv(B, 128), 128, 0, s>>>(B, max_iters, tol, st);
     h->launches += 7;
   }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
+  return DCOPF_OK;
+}
+
+// FP64 or FP32 evaluation with every intermediate in caller-provided buffers (same
+// kernels as run_eval_unfused; nothing of the handle's workspace is used).
+dcopf_status launch_eval_into(dcopf_dual* h, int B, const int* outage, const double* lambda,
+                              const double* mh, const double* ml, int precision,
+                              const EvalBuffers& E, double* value, double* glam, double* ghi,
+                              double* glo, double* dispatch, cudaStream_t s) {
+  const DevNet& N = h->dev;
+  const int nl = N.n_line, ng = N.n_gen;
+  dim3 gl(nl, B), gg(ng, B);
+  const int ta = red_threads(nl), tf = red_threads(ng);
+  if (precision == DCOPF_FP64) {
+    k_eta<double, double><<<B, 256, 0, s>>>(nl, mh, ml, outage, E.u64, E.eta64);
+    k_adjoint<double><<<gg, ta, 0, s>>>(nl, ng, N.phit64, E.eta64, E.pit64);
+    k_minimize<double><<<B, 256, 0, s>>>(N, lambda, E.pit64, E.x64, E.sumcost, E.sump, nullptr);
+    k_forward<double><<<gl, tf, 0, s>>>(nl, ng, N.phi64, E.x64, E.f0, E.f, nullptr);
+    if (dispatch) k_dispatch<<<cdiv((long long)B * ng, 256), 256, 0, s>>>(N, B, E.x64, dispatch);
+  } else {
+    k_to_float<<<cdiv((long long)B * nl, 256), 256, 0, s>>>((long long)B * nl, E.u64, E.u32);
+    k_eta<float, double><<<B, 256, 0, s>>>(nl, mh, ml, outage, E.u32, E.eta32);
+    k_adjoint<float><<<gg, ta, 0, s>>>(nl, ng, N.phit32, E.eta32, E.pit32);
+    k_minimize<float><<<B, 256, 0, s>>>(N, lambda, E.pit32, E.x32, E.sumcost, E.sump, nullptr);
+    k_forward<float><<<gl, tf, 0, s>>>(nl, ng, N.phi32, E.x32, E.f0, E.f, nullptr);
+    if (dispatch) k_dispatch32<<<cdiv((long long)B * ng, 256), 256, 0, s>>>(N, B, E.x32, dispatch);
+    h->launches += 1;
+  }
+  k_grad_value<double, double><<<B, 256, 0, s>>>(N, outage, E.u64, lambda, mh, ml, E.f, E.sumcost,
+                                                 E.sump, E.demand, value, glam, ghi, glo, nullptr);
+  h->launches += 5 + (dispatch ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
   return DCOPF_OK;

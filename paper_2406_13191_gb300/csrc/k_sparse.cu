@@ -335,4 +335,22 @@ template dcopf_status run_certify_t<float>(dcopf_dual*, int, const double*, cons
                                            const double*, const float*, const float*, double*,
                                            double*, const int*, const int*, cudaStream_t);
 
+// Base flows into caller-provided buffers (f0 and u64 [batch][n_line], demand [batch]);
+// the same kernel as run_base_flows without touching the handle's workspace.
+dcopf_status launch_base_flows_into(dcopf_dual* h, int B, const double* loads, const int* outage,
+                                    double* f0, double* u64, double* demand, cudaStream_t s) {
+  int staged = 0;
+  size_t smem = sparse_smem(h, 1, &staged);
+  if (smem > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(k_base_flows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  k_base_flows<<<B, sparse_threads(h), smem, s>>>(h->dev, loads, outage, f0, nullptr, u64, nullptr,
+                                                  demand, h->d_err, staged);
+  h->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
+  return DCOPF_OK;
+}
+
 }  // namespace dcopf

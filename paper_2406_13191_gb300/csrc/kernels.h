@@ -164,6 +164,18 @@ dcopf_status run_certify_t(dcopf_dual* h, int batch, const double* loads, const 
                            const int* mask, const int* done, cudaStream_t s);
 size_t certify_smem(const dcopf_dual* h, bool outages);
 
+// Intermediate buffers of one evaluation, all caller-provided ([batch][n] arrays).
+struct EvalBuffers {
+  double *f0, *u64, *demand, *eta64, *pit64, *x64, *f, *sumcost, *sump;
+  float *u32, *eta32, *pit32, *x32;
+};
+dcopf_status launch_base_flows_into(dcopf_dual* h, int B, const double* loads, const int* outage,
+                                    double* f0, double* u64, double* demand, cudaStream_t s);
+dcopf_status launch_eval_into(dcopf_dual* h, int B, const int* outage, const double* lambda,
+                              const double* mh, const double* ml, int precision,
+                              const EvalBuffers& E, double* value, double* glam, double* ghi,
+                              double* glo, double* dispatch, cudaStream_t s);
+
 // k_phases.cu
 dcopf_status run_eval_unfused(dcopf_dual* h, int batch, const int* outage, const double* lambda,
                               const double* mh, const double* ml, int precision, double* value,
