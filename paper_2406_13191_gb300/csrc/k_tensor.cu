@@ -26,12 +26,15 @@
 
 namespace dcopf {
 
-enum { EPI_PARTIAL = 0, EPI_FLOW = 1, EPI_STEP = 2 };
+enum { EPI_PARTIAL = 0, EPI_FLOW = 1, EPI_TILE = 2 };
 
-// Fused epilogue of the forward product inside the batched solve: flows, supergradient,
-// line part of the dual value, projected step of mu, BF16 split of the next eta.
+// Step of the batched solve after the forward product: flows (with the rank-1 outage
+// term), supergradient, line part of the dual value, projected step of mu into the
+// parity-buffered state, BF16 split of the next eta, outage partial u^T eta.
 struct StepEpi {
   StepArgs P;
+  const float* F;             // [B][ldF] forward product Phi~ x
+  int ldF;
   const float* f0;            // [B][nl] flows of the mid-box dispatch minus the loads
   const float* u;             // [B][nl] outage vectors (rows of outage instances)
   const int* outage;          // [B] or null
@@ -43,7 +46,7 @@ struct StepEpi {
   float* mu_hi[2]; float* mu_lo[2];
   float* s1_hi; float* s2_hi; float* s1_lo; float* s2_lo;
   __nv_bfloat16* Hh; __nv_bfloat16* Hl; int ldh;
-  double* line_part; double* out_part; int n_tiles;   // [B][n_tiles]
+  double* line_part; double* out_part; int n_tiles;   // [B][n_tiles] per chunk of lines
 };
 
 struct GemmArgs {
@@ -52,12 +55,13 @@ struct GemmArgs {
   int epi;
   float* P; int ldp;     // EPI_PARTIAL: P[split][M][ldp]
   const double* f0; double* f; int ldf;  // EPI_FLOW: f = acc + f0, [M][ldf]
+  float* F32; int ldf32;  // EPI_TILE: raw accumulator, [M][ldf32]
   int* err;
   uint64_t timeout_ns;
-  StepEpi se;
 };
 
 constexpr int GBM = 128, GBN = 128, GBK = 64;
+constexpr int GBM_ = GBM, GBN_ = GBN;
 constexpr uint32_t TILE_BYTES = GBM * GBK * 2;  // 16 KB, also GBN * GBK * 2
 
 template <int NPROD>
@@ -84,42 +88,6 @@ __device__ __forceinline__ float step_rule(const StepArgs& P, float theta, float
     theta += a * g / (sqrtf(s1) + (float)P.eps);
   }
   return theta;
-}
-
-// One row (instance b) x 32 columns (lines) of the fused step epilogue.
-__device__ __forceinline__ void step_epilogue(const StepEpi& E, int nl, int b, int col0,
-                                              const float* v, double& lacc, double& oacc) {
-  const int k = E.outage ? E.outage[b] : -1;
-  const float t_out = k >= 0 ? E.tout[b] : 0.f;
-  const int pb = E.iter[b] & 1;
-  const float* mhc = E.mu_hi[pb] + (size_t)b * nl;
-  const float* mlc = E.mu_lo[pb] + (size_t)b * nl;
-  float* mhn = E.mu_hi[pb ^ 1] + (size_t)b * nl;
-  float* mln = E.mu_lo[pb ^ 1] + (size_t)b * nl;
-  const float am = E.stepf[4 * b], bc1 = E.stepf[4 * b + 1], bc2 = E.stepf[4 * b + 2];
-  const size_t o = (size_t)b * nl;
-  for (int u = 0; u < 32; ++u) {
-    const int i = col0 + u;
-    if (i >= nl) break;
-    float f = v[u] + E.f0[o + i];
-    float ui = 0.f;
-    if (k >= 0) { ui = E.u[o + i]; f += ui * t_out; }
-    float gh = f - E.fmax[i], gl = E.fmin[i] - f;
-    const float mh = mhc[i], ml = mlc[i];
-    float nh = 0.f, nlo = 0.f;
-    if (i != k) {
-      lacc += (double)mh * (double)gh + (double)ml * (double)gl;
-      float a1 = E.s1_hi[o + i], a2 = E.s2_hi[o + i], b1 = E.s1_lo[o + i], b2 = E.s2_lo[o + i];
-      nh = fmaxf(step_rule(E.P, mh, gh, a1, a2, am, bc1, bc2), 0.f);
-      nlo = fmaxf(step_rule(E.P, ml, gl, b1, b2, am, bc1, bc2), 0.f);
-      E.s1_hi[o + i] = a1; E.s2_hi[o + i] = a2; E.s1_lo[o + i] = b1; E.s2_lo[o + i] = b2;
-    }
-    mhn[i] = nh;
-    mln[i] = nlo;
-    const float eta = nh - nlo;
-    split_bf16(eta, E.Hh + (size_t)b * E.ldh + i, E.Hl + (size_t)b * E.ldh + i);
-    if (k >= 0) oacc += (double)ui * (double)eta;
-  }
 }
 
 template <int NPROD>
@@ -206,16 +174,17 @@ __global__ void __launch_bounds__(192, 1)
     const int q = warp & 3;
     const int row = m0 + 32 * q + lane;
     if (!ready) s_abort = 1;
-    const bool step_row = g.epi == EPI_STEP && row < g.M && !g.se.frozen[row];
-    double lacc = 0.0, oacc = 0.0;
     if (ready && nkb > 0) {
 #pragma unroll 1
       for (int cc = 0; cc < GBN / 32; ++cc) {
         float v[32];
         umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cc), v);
         const int col0 = n0 + 32 * cc;
-        if (g.epi == EPI_STEP) {
-          if (step_row) step_epilogue(g.se, g.N, row, col0, v, lacc, oacc);
+        if (g.epi == EPI_TILE) {
+          // stage the accumulator in the (now idle) pipeline ring, stride GBN + 1
+          float* tile = (float*)base;
+#pragma unroll
+          for (int u = 0; u < 32; ++u) tile[(32 * q + lane) * (GBN + 1) + 32 * cc + u] = v[u];
         } else if (row < g.M) {
           if (g.epi == EPI_PARTIAL) {
             float* dst = g.P + ((size_t)blockIdx.z * g.M + row) * g.ldp + col0;
@@ -234,13 +203,24 @@ __global__ void __launch_bounds__(192, 1)
         }
       }
     }
-    if (step_row) {
-      g.se.line_part[(size_t)row * g.se.n_tiles + blockIdx.x] = lacc;
-      g.se.out_part[(size_t)row * g.se.n_tiles + blockIdx.x] = oacc;
-    }
   }
   umma::tc_fence_before();  // order this thread's tcgen05 work before the teardown barrier
   __syncthreads();
+  if (g.epi == EPI_TILE && !s_abort && nkb > 0) {
+    // coalesced store of the staged tile: a warp per row, lanes along columns
+    const float* tile = (const float*)base;
+    for (int m = warp; m < GBM; m += 6) {
+      const int r = m0 + m;
+      if (r >= g.M) break;
+      float* dst = g.F32 + (size_t)r * g.ldf32;
+#pragma unroll
+      for (int q = 0; q < GBN / 32; ++q) {
+        const int c = lane + 32 * q;
+        if (n0 + c < g.N) dst[n0 + c] = tile[m * (GBN + 1) + c];
+      }
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0 && s_abort) {
     atomicExch(g.err, (int)DCOPF_ERR_TIMEOUT);
     // let the copies still in flight land before the CTA's shared memory is released
@@ -251,6 +231,86 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 1) {
     umma::tc_fence_after();
     umma::tmem_dealloc(tmem, GBN);
+  }
+}
+
+// One block per (chunk of STEP_CHUNK lines, instance): elementwise, full occupancy,
+// coalesced; per-chunk FP64 partials of the value and of u^T eta.
+constexpr int STEP_THREADS = 256, STEP_PER_THREAD = 4;
+constexpr int STEP_CHUNK = STEP_THREADS * STEP_PER_THREAD;
+
+__global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
+  __shared__ double red[32];
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if (E.frozen[b]) return;
+  const int k = E.outage ? E.outage[b] : -1;
+  const float t_out = k >= 0 ? E.tout[b] : 0.f;
+  const int pb = E.iter[b] & 1;
+  const size_t o = (size_t)b * nl;
+  const float* mhc = E.mu_hi[pb] + o;
+  const float* mlc = E.mu_lo[pb] + o;
+  float* mhn = E.mu_hi[pb ^ 1] + o;
+  float* mln = E.mu_lo[pb ^ 1] + o;
+  const float am = E.stepf[4 * b], bc1 = E.stepf[4 * b + 1], bc2 = E.stepf[4 * b + 2];
+  const float* Fr = E.F + (size_t)b * E.ldF;
+  // a thread's few terms are summed in FP32 and the block sum is FP64 (FP64 throughput
+  // is low on this part: per-element FP64 would dominate the kernel)
+  float lacc = 0.f, oacc = 0.f;
+  const int i0 = chunk * STEP_CHUNK + threadIdx.x;
+  float fl[STEP_PER_THREAD], ui[STEP_PER_THREAD], mh[STEP_PER_THREAD], ml[STEP_PER_THREAD],
+      a1[STEP_PER_THREAD], a2[STEP_PER_THREAD], b1[STEP_PER_THREAD], b2[STEP_PER_THREAD],
+      fx[STEP_PER_THREAD], fn[STEP_PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < STEP_PER_THREAD; ++q) {  // all loads in flight before any arithmetic
+    const int i = i0 + q * STEP_THREADS;
+    const bool in = i < nl;
+    fl[q] = in ? Fr[i] + E.f0[o + i] : 0.f;
+    ui[q] = (in && k >= 0) ? E.u[o + i] : 0.f;
+    fx[q] = in ? E.fmax[i] : 0.f;
+    fn[q] = in ? E.fmin[i] : 0.f;
+    mh[q] = in ? mhc[i] : 0.f;
+    ml[q] = in ? mlc[i] : 0.f;
+    a1[q] = in ? E.s1_hi[o + i] : 0.f;
+    a2[q] = in ? E.s2_hi[o + i] : 0.f;
+    b1[q] = in ? E.s1_lo[o + i] : 0.f;
+    b2[q] = in ? E.s2_lo[o + i] : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < STEP_PER_THREAD; ++q) {
+    const int i = i0 + q * STEP_THREADS;
+    if (i >= nl) continue;
+    const float f = fl[q] + ui[q] * t_out;
+    const float gh = f - fx[q], gl = fn[q] - f;
+    float nh = 0.f, nlo = 0.f;
+    if (i != k) {
+      lacc = fmaf(mh[q], gh, fmaf(ml[q], gl, lacc));
+      nh = fmaxf(step_rule(E.P, mh[q], gh, a1[q], a2[q], am, bc1, bc2), 0.f);
+      nlo = fmaxf(step_rule(E.P, ml[q], gl, b1[q], b2[q], am, bc1, bc2), 0.f);
+      E.s1_hi[o + i] = a1[q]; E.s2_hi[o + i] = a2[q]; E.s1_lo[o + i] = b1[q]; E.s2_lo[o + i] = b2[q];
+    }
+    mhn[i] = nh;
+    mln[i] = nlo;
+    const float eta = nh - nlo;
+    split_bf16(eta, E.Hh + (size_t)b * E.ldh + i, E.Hl + (size_t)b * E.ldh + i);
+    if (k >= 0) oacc = fmaf(ui[q], eta, oacc);
+  }
+  // warp sums in FP32, the 8 warp partials in FP64 (fixed order)
+  lacc = warp_sum(lacc);
+  oacc = warp_sum(oacc);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[w] = (double)lacc;
+    red[16 + w] = (double)oacc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ls = 0.0, os = 0.0;
+    for (int q = 0; q < STEP_THREADS / 32; ++q) {
+      ls += red[q];
+      os += red[16 + q];
+    }
+    E.line_part[(size_t)b * E.n_tiles + chunk] = ls;
+    E.out_part[(size_t)b * E.n_tiles + chunk] = os;
   }
 }
 
@@ -497,9 +557,12 @@ __global__ void k_bt_minimize(DevNet N, int splits, int M, int ldp, const float*
   for (int j = threadIdx.x; j < ng; j += blockDim.x) {
     float s = 0.f;
     for (int q = 0; q < splits; ++q) s += P[((size_t)q * M + b) * ldp + j];
+    // w cancels (ctil + sigma lambda ~ -pi~), so it is formed in FP64; the clip of
+    // -w / (2 mq) is taken in FP32 (FP64 division is slow on this part)
     const double w = N.ctil[j] + N.sigma[j] * lam + (double)s;
-    const double x = inner_x<double>(w, N.mq[j]);
-    split_bf16((float)x, Xh + (size_t)b * ldx + j, Xl + (size_t)b * ldx + j);
+    const float xf = inner_x<float>((float)w, N.mq32[j]);
+    const double x = (double)xf;
+    split_bf16(xf, Xh + (size_t)b * ldx + j, Xl + (size_t)b * ldx + j);
     c += (N.mq[j] * x + N.ctil[j]) * x + N.cconst[j];
     p += N.mid[j] + N.sigma[j] * x;
     if (k >= 0) to += (double)N.phi32[(size_t)k * ng + j] * x;
@@ -657,8 +720,10 @@ dcopf_status solve_tensor(dcopf_dual* h, int B, const double* loads, const int* 
   SolveState<float> st{};
   if ((r = ensure_state<float>(h, B, &st))) return r;
   const int nl = h->host.n_line, ng = h->host.n_gen;
-  const int n_tiles = (nl + GBN - 1) / GBN;
+  const int n_tiles = (nl + STEP_CHUNK - 1) / STEP_CHUNK;
   if ((r = ensure_batch_bufs(h, B, n_tiles))) return r;
+  const int ldF = (nl + 3) & ~3;
+  if (h->bb.F.alloc((size_t)B * ldF * sizeof(float)) != cudaSuccess) return DCOPF_ERR_OOM;
   TensorOps& T = h->tops;
   Workspace& w = h->ws;
   BatchView& bb = h->bb.v;
@@ -687,10 +752,11 @@ dcopf_status solve_tensor(dcopf_dual* h, int B, const double* loads, const int* 
   ga.M = B; ga.N = ng; ga.K = nl; ga.kb_per_split = kbps; ga.epi = EPI_PARTIAL;
   ga.P = T.P.as<float>(); ga.ldp = (ng + 3) & ~3; ga.err = h->d_err; ga.timeout_ns = 2000000000ull;
   GemmArgs gf{};
-  gf.M = B; gf.N = nl; gf.K = ng; gf.kb_per_split = (ng + GBK - 1) / GBK; gf.epi = EPI_STEP;
+  gf.M = B; gf.N = nl; gf.K = ng; gf.kb_per_split = (ng + GBK - 1) / GBK; gf.epi = EPI_TILE;
+  gf.F32 = h->bb.F.as<float>(); gf.ldf32 = ldF;
   gf.err = h->d_err; gf.timeout_ns = 2000000000ull;
-  StepEpi& E = gf.se;
-  E.P = P; E.f0 = w.f0_32.as<float>(); E.u = w.u32.as<float>(); E.outage = outage; E.tout = bb.tout;
+  StepEpi E{};
+  E.P = P; E.F = gf.F32; E.ldF = ldF; E.f0 = w.f0_32.as<float>(); E.u = w.u32.as<float>(); E.outage = outage; E.tout = bb.tout;
   E.fmax = h->dev.fmax32; E.fmin = h->dev.fmin32; E.iter = st.iter; E.frozen = bb.frozen;
   E.stepf = bb.stepf;
   E.mu_hi[0] = st.mu_hi; E.mu_hi[1] = bb.mu2_hi; E.mu_lo[0] = st.mu_lo; E.mu_lo[1] = bb.mu2_lo;
@@ -712,6 +778,7 @@ dcopf_status solve_tensor(dcopf_dual* h, int B, const double* loads, const int* 
     cap_ok &= (h->host.qp ? launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, gf, 1, cs)
                           : launch_gemm<2>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, gf, 1, cs)) ==
               cudaSuccess;
+    k_bt_step<<<dim3(n_tiles, B), STEP_THREADS, 0, cs>>>(E, nl);
     k_bt_finalize<<<(B + 3) / 4, 128, 0, cs>>>(B, T.ld_l, p.max_iters, p.tol, st, bb, outage,
                                                w.demand.as<double>(), T.H_hi.as<__nv_bfloat16>(),
                                                T.H_lo.as<__nv_bfloat16>());
@@ -723,7 +790,7 @@ dcopf_status solve_tensor(dcopf_dual* h, int B, const double* loads, const int* 
     cudaGetLastError();
     return DCOPF_ERR_CUDA;
   }
-  const long long per_chunk = 4LL * chunk;
+  const long long per_chunk = 5LL * chunk;
   dcopf_status out = DCOPF_OK;
   if (h->active.alloc(16) != cudaSuccess) out = DCOPF_ERR_OOM;
   int* d_active = h->active.as<int>();

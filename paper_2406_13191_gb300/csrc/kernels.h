@@ -95,12 +95,12 @@ struct BatchView {
   float* stepf = nullptr;      // [B][4] step factors of the current step
   float* mu2_hi = nullptr;     // [B][nl] second state buffer (parity 1)
   float* mu2_lo = nullptr;
-  double* line_part = nullptr; // [B][n_tiles]
+  double* line_part = nullptr; // [B][n_tiles] per chunk of lines of the step kernel
   double* out_part = nullptr;  // [B][n_tiles]
 };
 
 struct BatchBufs {
-  DBuf mu2, parts, small;
+  DBuf mu2, parts, small, F;
   BatchView v;
 };
 
