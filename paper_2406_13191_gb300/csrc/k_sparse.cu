@@ -54,7 +54,20 @@ struct PackedFactor {
 __device__ PackedFactor stage_factor(const DevNet& N, unsigned char* sm) {
   const int4* src = (const int4*)N.fac_blob;
   int4* dst = (int4*)sm;
-  for (int q = threadIdx.x; q < N.fac_bytes / 16; q += blockDim.x) dst[q] = src[q];
+  const int n16 = N.fac_bytes / 16;
+  for (int base = 0; base < n16; base += 8 * blockDim.x) {  // 8 loads in flight per thread
+    int4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = base + u * blockDim.x + threadIdx.x;
+      if (q < n16) v[u] = __ldg(src + q);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = base + u * blockDim.x + threadIdx.x;
+      if (q < n16) dst[q] = v[u];
+    }
+  }
   __syncthreads();
   PackedFactor F;
   F.diag = (const double*)(sm + N.off_diag); F.val = (const double*)(sm + N.off_val);
@@ -294,6 +307,7 @@ static int sparse_threads(const dcopf_dual* h) {
 
 dcopf_status run_base_flows(dcopf_dual* h, int B, const double* loads, const int* outage,
                             cudaStream_t s) {
+  if (dense_path_applies(h, B, outage)) return run_dense_base_flows(h, B, loads, s);
   int staged = 0;
   size_t smem = sparse_smem(h, 1, &staged);
   if (smem > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
@@ -315,6 +329,8 @@ template <typename S>
 dcopf_status run_certify_t(dcopf_dual* h, int B, const double* loads, const int* outage,
                            const double* lam, const S* mh, const S* ml, double* bound, double* errb,
                            const int* mask, const int* done, cudaStream_t s) {
+  if (dense_path_applies(h, B, outage))
+    return run_dense_certify<S>(h, B, loads, lam, mh, ml, bound, errb, mask, done, s);
   int staged = 0;
   size_t smem = sparse_smem(h, outage != nullptr ? 2 : 1, &staged);
   if (smem > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;

@@ -120,6 +120,7 @@ struct dcopf_dual {
   dcopf::Workspace ws;
   dcopf::StateBufs st32, st64;
   dcopf::TensorOps tops;
+  dcopf::DBuf dense_ha, dense_part;  // dense FP64 PTDF [n_line][n_bus] (built on first use)
   dcopf::BatchBufs bb;
   int* d_err = nullptr;  // sticky device error word
   unsigned* d_bar = nullptr;  // grid-barrier counters
@@ -188,6 +189,14 @@ template <typename S>
 dcopf_status run_iters_unfused(dcopf_dual* h, int batch, const int* outage, int precision,
                                const StepArgs& P, SolveState<S>& st, int n_iters, int max_iters,
                                double tol, cudaStream_t s);
+
+// k_dense.cu
+bool dense_path_applies(const dcopf_dual* h, int batch, const int* outage);
+dcopf_status run_dense_base_flows(dcopf_dual* h, int batch, const double* loads, cudaStream_t s);
+template <typename S>
+dcopf_status run_dense_certify(dcopf_dual* h, int batch, const double* loads, const double* lam,
+                               const S* mh, const S* ml, double* bound, double* errb,
+                               const int* mask, const int* done, cudaStream_t s);
 
 // k_tensor.cu
 dcopf_status ensure_tensor_operands(dcopf_dual* h);
