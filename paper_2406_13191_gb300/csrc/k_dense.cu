@@ -54,12 +54,14 @@ __global__ void k_dense_base_flows(int nb, int nl, const double* __restrict__ H,
 }
 
 // Partial bus prices: part[b][split][j] = sum over the split's lines of H_a[i][j] eta_i,
-// eta = max(mu_hi, 0) - max(mu_lo, 0).  Block = (column tile, row split, instance).
+// eta = max(mu_hi, 0) - max(mu_lo, 0), formed once per block in shared memory.
+// Block = (column tile, row split, instance).
 template <typename S>
 __global__ void k_dense_prices(int nb, int nl, const double* __restrict__ H,
                                const S* __restrict__ mu_hi, const S* __restrict__ mu_lo,
                                double* __restrict__ part, const int* __restrict__ mask,
                                const int* __restrict__ done) {
+  extern __shared__ double eta_s[];
   const int b = blockIdx.z;
   if (mask && (mask[b] == 0 || (done && done[b]))) return;
   const int j = blockIdx.x * DN_TILE + threadIdx.x;
@@ -67,25 +69,24 @@ __global__ void k_dense_prices(int nb, int nl, const double* __restrict__ H,
   const int i0 = blockIdx.y * rows, i1 = min(nl, i0 + rows);
   const S* mh = mu_hi + (size_t)b * nl;
   const S* ml = mu_lo + (size_t)b * nl;
-  double s = 0.0;
-  if (j < nb) {
-    int i = i0;
-    for (; i + 4 <= i1; i += 4) {  // four rows in flight
-      const double e0 = fmax((double)mh[i], 0.0) - fmax((double)ml[i], 0.0);
-      const double e1 = fmax((double)mh[i + 1], 0.0) - fmax((double)ml[i + 1], 0.0);
-      const double e2 = fmax((double)mh[i + 2], 0.0) - fmax((double)ml[i + 2], 0.0);
-      const double e3 = fmax((double)mh[i + 3], 0.0) - fmax((double)ml[i + 3], 0.0);
-      const double h0 = H[(size_t)i * nb + j], h1 = H[(size_t)(i + 1) * nb + j];
-      const double h2 = H[(size_t)(i + 2) * nb + j], h3 = H[(size_t)(i + 3) * nb + j];
-      s = fma(h0, e0, s);
-      s = fma(h1, e1, s);
-      s = fma(h2, e2, s);
-      s = fma(h3, e3, s);
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+    eta_s[i - i0] = fmax((double)mh[i], 0.0) - fmax((double)ml[i], 0.0);
+  __syncthreads();
+  if (j >= nb) return;
+  double s0 = 0.0, s1 = 0.0;
+  int i = i0;
+  for (; i + 8 <= i1; i += 8) {  // eight rows in flight, two chains
+    double h[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) h[u] = H[(size_t)(i + u) * nb + j];
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      s0 = fma(h[u], eta_s[i + u - i0], s0);
+      s1 = fma(h[u + 1], eta_s[i + u + 1 - i0], s1);
     }
-    for (; i < i1; ++i)
-      s = fma(H[(size_t)i * nb + j], fmax((double)mh[i], 0.0) - fmax((double)ml[i], 0.0), s);
-    part[((size_t)b * DN_SPLITS + blockIdx.y) * nb + j] = s;
   }
+  for (; i < i1; ++i) s0 = fma(H[(size_t)i * nb + j], eta_s[i - i0], s0);
+  part[((size_t)b * DN_SPLITS + blockIdx.y) * nb + j] = s0 + s1;
 }
 
 __device__ __forceinline__ double gamma_fp64_d(double m) {
@@ -109,11 +110,18 @@ __global__ void k_dense_certify(DevNet N, const double* __restrict__ part,
   const S* mh = mu_hi + (size_t)b * nl;
   const S* ml = mu_lo + (size_t)b * nl;
   const double lam = lambda[b];
-  auto z_at = [&](int j) {
+  extern __shared__ double zs[];  // bus prices z = H_a^T eta, reduced once
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    double p[DN_SPLITS];
+#pragma unroll
+    for (int q = 0; q < DN_SPLITS; ++q) p[q] = pz[(size_t)q * nb + j];
     double z = 0.0;
-    for (int q = 0; q < DN_SPLITS; ++q) z += pz[(size_t)q * nb + j];
-    return z;
-  };
+#pragma unroll
+    for (int q = 0; q < DN_SPLITS; ++q) z += p[q];
+    zs[j] = z;
+  }
+  __syncthreads();
+  auto z_at = [&](int j) { return zs[j]; };
   double g = 0.0, A = 0.0;
   for (int j = threadIdx.x; j < N.n_gen; j += blockDim.x) {
     double p;
@@ -179,7 +187,8 @@ dcopf_status ensure_dense_ha(dcopf_dual* h) {
 // Whether the dense path applies: few instances, no outages, H_a of modest size.
 bool dense_path_applies(const dcopf_dual* h, int B, const int* outage) {
   const size_t bytes = (size_t)h->host.n_line * h->host.n_bus * sizeof(double);
-  return outage == nullptr && B <= 8 && bytes <= ((size_t)2 << 30);
+  const size_t zs = (size_t)h->host.n_bus * sizeof(double);
+  return outage == nullptr && B <= 8 && bytes <= ((size_t)2 << 30) && zs + 1024 <= h->smem_optin;
 }
 
 dcopf_status run_dense_base_flows(dcopf_dual* h, int B, const double* loads, cudaStream_t s) {
@@ -207,10 +216,18 @@ dcopf_status run_dense_certify(dcopf_dual* h, int B, const double* loads, const 
   if (h->dense_part.alloc((size_t)std::max(B, 8) * DN_SPLITS * nb * sizeof(double)) != cudaSuccess)
     return DCOPF_ERR_OOM;
   dim3 grid((nb + DN_TILE - 1) / DN_TILE, DN_SPLITS, B);
-  k_dense_prices<S><<<grid, DN_TILE, 0, s>>>(nb, nl, h->dense_ha.as<double>(), mh, ml,
-                                             h->dense_part.as<double>(), mask, done);
-  k_dense_certify<S><<<B, 256, 0, s>>>(h->dev, h->dense_part.as<double>(), loads, lam, mh, ml, bound,
-                                       errb, mask, done);
+  const size_t eta_smem = (size_t)((nl + DN_SPLITS - 1) / DN_SPLITS) * sizeof(double);
+  const size_t z_smem = (size_t)nb * sizeof(double);
+  if (eta_smem > h->smem_optin || z_smem > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(k_dense_prices<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)eta_smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_dense_certify<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)z_smem) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  k_dense_prices<S><<<grid, DN_TILE, eta_smem, s>>>(nb, nl, h->dense_ha.as<double>(), mh, ml,
+                                                    h->dense_part.as<double>(), mask, done);
+  k_dense_certify<S><<<B, 256, z_smem, s>>>(h->dev, h->dense_part.as<double>(), loads, lam, mh, ml,
+                                            bound, errb, mask, done);
   h->launches += 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
