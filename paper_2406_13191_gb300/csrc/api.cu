@@ -346,7 +346,8 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
   const int nl = H.n_line, ng = H.n_gen;
   std::vector<float> fmax32(H.fmax.begin(), H.fmax.end()), fmin32(H.fmin.begin(), H.fmin.end());
   std::vector<float> sig32(H.sigma.begin(), H.sigma.end()), ctil32(H.ctil.begin(), H.ctil.end()),
-      mq32(H.mq.begin(), H.mq.end());
+      mq32(H.mq.begin(), H.mq.end()), cconst32(H.cconst.begin(), H.cconst.end()),
+      mid32(H.mid.begin(), H.mid.end());
   std::vector<double> phit((size_t)nl * ng);
   std::vector<float> phi32((size_t)nl * ng), phit32((size_t)nl * ng);
   for (int i = 0; i < nl; ++i)
@@ -369,7 +370,7 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
   UP(H.bus_line_coef, bus_line_coef) UP(H.gen_bus, gen_bus) UP(H.pmin, pmin) UP(H.pmax, pmax)
   UP(H.cost_lin, cost_lin) UP(H.cost_quad, cost_quad) UP(H.sigma, sigma) UP(H.mid, mid)
   UP(H.ctil, ctil) UP(H.mq, mq) UP(H.cconst, cconst) UP(sig32, sigma32) UP(ctil32, ctil32)
-  UP(mq32, mq32) UP(H.phi, phi64) UP(phit, phit64) UP(phi32, phi32) UP(phit32, phit32)
+  UP(mq32, mq32) UP(cconst32, cconst32) UP(mid32, mid32) UP(H.phi, phi64) UP(phit, phit64) UP(phi32, phi32) UP(phit32, phit32)
 #undef UP
   if (!H.F.blob.empty()) {
     if ((st = upload(h, H.F.blob, &D.fac_blob)) != DCOPF_OK) { delete h; return st; }

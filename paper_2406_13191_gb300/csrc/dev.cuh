@@ -38,7 +38,8 @@ struct DevNet {
   const int* gen_bus;
   const double* pmin; const double* pmax; const double* cost_lin; const double* cost_quad;
   const double* sigma; const double* mid; const double* ctil; const double* mq; const double* cconst;
-  const float* sigma32; const float* ctil32; const float* mq32;
+  const float* sigma32; const float* ctil32; const float* mq32; const float* cconst32;
+  const float* mid32;
   // dense operators
   const double* phi64; const double* phit64;
   const float* phi32; const float* phit32;

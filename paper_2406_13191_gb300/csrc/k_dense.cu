@@ -112,12 +112,14 @@ __global__ void k_dense_certify(DevNet N, const double* __restrict__ part,
   const double lam = lambda[b];
   extern __shared__ double zs[];  // bus prices z = H_a^T eta, reduced once
   for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-    double p[DN_SPLITS];
-#pragma unroll
-    for (int q = 0; q < DN_SPLITS; ++q) p[q] = pz[(size_t)q * nb + j];
     double z = 0.0;
+    for (int q0 = 0; q0 < DN_SPLITS; q0 += 8) {  // eight partials in flight
+      double p[8];
 #pragma unroll
-    for (int q = 0; q < DN_SPLITS; ++q) z += p[q];
+      for (int u = 0; u < 8; ++u) p[u] = pz[(size_t)(q0 + u) * nb + j];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) z += p[u];
+    }
     zs[j] = z;
   }
   __syncthreads();
@@ -145,6 +147,8 @@ __global__ void k_dense_certify(DevNet N, const double* __restrict__ part,
   if (threadIdx.x == 0) {
     const int n_terms = N.n_gen + nb + nl;
     const double m = (double)((n_terms + blockDim.x - 1) / blockDim.x) + 6.0 + 8.0 + DN_SPLITS;
+    // (per-thread sums, the block tree, the roundings inside a term, and the row-split
+    // partials of the prices)
     const double e = gamma_fp64_d(m) * A;
     bound[b] = g - e;
     if (errb) errb[b] = e;

@@ -28,11 +28,48 @@ namespace dcopf {
 
 enum { EPI_PARTIAL = 0, EPI_FLOW = 1, EPI_TILE = 2 };
 
+// Step-rule constants in FP32, converted once on the host (FP64 conversions per
+// element are not free on this part).
+struct StepArgsF {
+  int rule, as_printed;
+  float rho, beta1, omb1, beta2, omb2, eps;
+};
+
+static StepArgsF to_float_args(const StepArgs& P) {
+  StepArgsF f;
+  f.rule = P.rule;
+  f.as_printed = P.as_printed;
+  f.rho = (float)P.rho;
+  f.beta1 = (float)P.beta1;
+  f.omb1 = (float)(1.0 - P.beta1);
+  f.beta2 = (float)P.beta2;
+  f.omb2 = (float)(1.0 - P.beta2);
+  f.eps = (float)P.eps;
+  return f;
+}
+
+__device__ __forceinline__ float step_rule(const StepArgsF& P, float theta, float g, float& s1,
+                                           float& s2, float a, float bc1, float bc2) {
+  if (P.rule == DCOPF_GDM) {
+    s1 = P.rho * s1 + a * g;
+    theta += s1;
+    if (P.as_printed) theta += a * g;
+  } else if (P.rule == DCOPF_ADAM) {
+    s1 = P.beta1 * s1 + P.omb1 * g;
+    s2 = P.beta2 * s2 + P.omb2 * g * g;
+    theta += a * (s1 / bc1) / (sqrtf(s2 / bc2) + P.eps);
+  } else {
+    s1 += g * g;
+    theta += a * g / (sqrtf(s1) + P.eps);
+  }
+  return theta;
+}
+
 // Step of the batched solve after the forward product: flows (with the rank-1 outage
 // term), supergradient, line part of the dual value, projected step of mu into the
 // parity-buffered state, BF16 split of the next eta, outage partial u^T eta.
 struct StepEpi {
-  StepArgs P;
+  StepArgsF P;
   const float* F;             // [B][ldF] forward product Phi~ x
   int ldF;
   const float* f0;            // [B][nl] flows of the mid-box dispatch minus the loads
@@ -73,22 +110,7 @@ struct GemmCfg {
 
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo);
 
-__device__ __forceinline__ float step_rule(const StepArgs& P, float theta, float g, float& s1,
-                                           float& s2, float a, float bc1, float bc2) {
-  if (P.rule == DCOPF_GDM) {
-    s1 = (float)P.rho * s1 + a * g;
-    theta += s1;
-    if (P.as_printed) theta += a * g;
-  } else if (P.rule == DCOPF_ADAM) {
-    s1 = (float)P.beta1 * s1 + (1.f - (float)P.beta1) * g;
-    s2 = (float)P.beta2 * s2 + (1.f - (float)P.beta2) * g * g;
-    theta += a * (s1 / bc1) / (sqrtf(s2 / bc2) + (float)P.eps);
-  } else {
-    s1 += g * g;
-    theta += a * g / (sqrtf(s1) + (float)P.eps);
-  }
-  return theta;
-}
+
 
 template <int NPROD>
 __global__ void __launch_bounds__(192, 1)
@@ -553,27 +575,31 @@ __global__ void k_bt_minimize(DevNet N, int splits, int M, int ldp, const float*
   const int ng = N.n_gen;
   const int k = outage ? outage[b] : -1;
   const double lam = st.lam[b];
-  double c = 0.0, p = 0.0, to = 0.0;
+  // the in-loop value and the lambda gradient only steer the iteration (the bound is
+  // certified in FP64 later): per-generator terms and warp sums in FP32, FP64 across
+  // warps.  w cancels (ctil + sigma lambda ~ -pi~), so it is formed in FP64.
+  float c = 0.f, p = 0.f, to = 0.f;
   for (int j = threadIdx.x; j < ng; j += blockDim.x) {
     float s = 0.f;
     for (int q = 0; q < splits; ++q) s += P[((size_t)q * M + b) * ldp + j];
-    // w cancels (ctil + sigma lambda ~ -pi~), so it is formed in FP64; the clip of
-    // -w / (2 mq) is taken in FP32 (FP64 division is slow on this part)
     const double w = N.ctil[j] + N.sigma[j] * lam + (double)s;
-    const float xf = inner_x<float>((float)w, N.mq32[j]);
-    const double x = (double)xf;
-    split_bf16(xf, Xh + (size_t)b * ldx + j, Xl + (size_t)b * ldx + j);
-    c += (N.mq[j] * x + N.ctil[j]) * x + N.cconst[j];
-    p += N.mid[j] + N.sigma[j] * x;
-    if (k >= 0) to += (double)N.phi32[(size_t)k * ng + j] * x;
+    const float x = inner_x<float>((float)w, N.mq32[j]);
+    split_bf16(x, Xh + (size_t)b * ldx + j, Xl + (size_t)b * ldx + j);
+    c += fmaf(fmaf(N.mq32[j], x, N.ctil32[j]), x, N.cconst32[j]);
+    p += fmaf(N.sigma32[j], x, N.mid32[j]);
+    if (k >= 0) to = fmaf(N.phi32[(size_t)k * ng + j], x, to);
   }
-  c = block_sum(c, red);
-  p = block_sum(p, red);
-  if (k >= 0) to = block_sum(to, red);
+  c = warp_sum(c); p = warp_sum(p); to = warp_sum(to);
+  const int wid = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { red[wid] = c; red[8 + wid] = p; red[16 + wid] = to; }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    bb.cost[b] = c;
-    bb.psum[b] = p;
-    bb.tout[b] = (float)to;
+    double cs = 0.0, ps = 0.0, ts = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { cs += red[q]; ps += red[8 + q]; ts += red[16 + q]; }
+    const double p = ps;
+    bb.cost[b] = cs;
+    bb.psum[b] = ps;
+    bb.tout[b] = (float)ts;
     bb.lam_eval[b] = lam;
     // step t = iter + 1: scale decay^(t-1), bias corrections 1 - beta^t
     const double d = bb.pw[3 * b], b1 = bb.pw[3 * b + 1] * SP.beta1, b2 = bb.pw[3 * b + 2] * SP.beta2;
@@ -756,7 +782,7 @@ dcopf_status solve_tensor(dcopf_dual* h, int B, const double* loads, const int* 
   gf.F32 = h->bb.F.as<float>(); gf.ldf32 = ldF;
   gf.err = h->d_err; gf.timeout_ns = 2000000000ull;
   StepEpi E{};
-  E.P = P; E.F = gf.F32; E.ldF = ldF; E.f0 = w.f0_32.as<float>(); E.u = w.u32.as<float>(); E.outage = outage; E.tout = bb.tout;
+  E.P = to_float_args(P); E.F = gf.F32; E.ldF = ldF; E.f0 = w.f0_32.as<float>(); E.u = w.u32.as<float>(); E.outage = outage; E.tout = bb.tout;
   E.fmax = h->dev.fmax32; E.fmin = h->dev.fmin32; E.iter = st.iter; E.frozen = bb.frozen;
   E.stepf = bb.stepf;
   E.mu_hi[0] = st.mu_hi; E.mu_hi[1] = bb.mu2_hi; E.mu_lo[0] = st.mu_lo; E.mu_lo[1] = bb.mu2_lo;
