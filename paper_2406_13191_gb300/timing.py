@@ -1,0 +1,120 @@
+"""Timing utility for the library's paths on the seeded synthetic workloads.
+
+    python -m paper_2406_13191_gb300.timing batched --config 2 --batch 1024 --iters 16
+    python -m paper_2406_13191_gb300.timing certify --config 1 --batch 1
+    python -m paper_2406_13191_gb300.timing fused --config 1 --repeat 3
+
+``batched`` runs the tensor-core batched solve (BF16 hi/lo split products) for a
+fixed number of iterations and reports the time of the iteration kernels per batched
+iteration (CUDA events recorded by the library on its stream).  ``certify`` times the
+FP64 certificate and one FP64 evaluation.  ``fused`` times single-instance solves to
+the certified 0.1 % gap with the fused persistent kernel (needs the stored optimum of
+the 2000-bus instance, tests/golden/gamma.json).  These are measurements of the
+library, used for the kernel profiles; they are not the benchmark line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import DcopfDual, synth
+
+
+def _seeded_point(rng, batch, n_line, density=0.1):
+    lam = -rng.uniform(1000, 5000, batch)
+    mh = rng.exponential(300.0, (batch, n_line)) * (rng.random((batch, n_line)) < density)
+    return lam, mh, np.zeros_like(mh)
+
+
+def batched(cfg, batch, iters):
+    w = synth.workload(cfg, batch=batch)
+    g = DcopfDual(w.net, device=0)
+    out = w.outage if (w.outage >= 0).any() else None
+    kw = dict(rule="adam", alpha=4000.0 if w.net.is_qp else 1000.0, beta1=0.95, beta2=0.999,
+              decay=0.997, max_iters=iters, path="batched", precision="bf16x3")
+    g.solve(w.loads, outage=out, **kw)                 # warm-up (graph capture, operands)
+    g.set_timing(True)
+    g.read_timing()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = g.solve(w.loads, outage=out, **kw)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms, launches, evals = g.read_timing()
+    per_iter_us = 1e3 * ms / max(1.0, evals / batch)
+    print(json.dumps(dict(mode="batched", config=cfg, batch=batch, iters=iters,
+                          wall_ms=1e3 * wall, iteration_kernels_ms=ms,
+                          us_per_batched_iteration=per_iter_us,
+                          instance_iterations_per_s=evals / (ms * 1e-3),
+                          status=np.bincount(r.status.cpu().numpy(), minlength=3).tolist())))
+
+
+def certify(cfg, batch, repeat=10):
+    w = synth.workload(cfg, batch=batch)
+    g = DcopfDual(w.net, device=0)
+    dev = torch.device("cuda", 0)
+    loads = torch.tensor(w.loads, dtype=torch.float64, device=dev)
+    lam, mh, ml = _seeded_point(np.random.default_rng(0), batch, w.net.n_line)
+    lam, mh, ml = (torch.tensor(a, dtype=torch.float64, device=dev) for a in (lam, mh, ml))
+    out = torch.tensor(w.outage, device=dev) if (w.outage >= 0).any() else None
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(repeat):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return 1e3 * e0.elapsed_time(e1) / repeat
+
+    res = dict(mode="certify", config=cfg, batch=batch,
+               certify_us=timed(lambda: g.certify(loads, lam, mh, ml, outage=out)),
+               eval_fp64_us=timed(lambda: g.eval(loads, lam, mh, ml, outage=out, precision="fp64",
+                                                 want_grad=False, want_dispatch=False)))
+    print(json.dumps(res))
+
+
+def fused(repeat):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    gam = json.load(open(os.path.join(root, "tests", "golden", "gamma.json")))["1/0"]["gamma"]
+    net, base = synth.network_for(1)
+    g = DcopfDual(net, device=0)
+    kw = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=4000,
+              path="fused")
+    g.solve(base[None], target=[gam], **kw)
+    g.set_timing(True)
+    g.read_timing()
+    for _ in range(repeat):
+        r = g.solve(base[None], target=[gam], **kw)
+    ms, launches, evals = g.read_timing()
+    print(json.dumps(dict(mode="fused", repeat=repeat, status=int(r.status[0].item()),
+                          iterations=int(r.iters[0].item()), fused_kernel_ms=ms,
+                          us_per_iteration=1e3 * ms / max(1, evals))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("mode", choices=["batched", "certify", "fused"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--iters", type=int, default=16)
+    ap.add_argument("--repeat", type=int, default=3)
+    a = ap.parse_args()
+    if a.mode == "batched":
+        batched(a.config, a.batch, a.iters)
+    elif a.mode == "certify":
+        certify(a.config, a.batch)
+    else:
+        fused(a.repeat)
+
+
+if __name__ == "__main__":
+    main()
