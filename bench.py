@@ -124,6 +124,17 @@ def dist_setup(n_gpus):
     return world, rank, local, pg
 
 
+def aggregate(total_ms: float, steps: int, world: int, dist, device=None):
+    """Whole-job throughput: every rank solved ``steps`` instances; the job took the
+    slowest rank's time (max over ranks).  Returns (value per second, max total ms)."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    return world * steps / (total_ms / 1e3), total_ms
+
+
 def cpu_baseline(target_s=10.0):
     """The oracle (plain FP64 numpy/scipy, one thread) solving the same instance with
     the same ascent rule until its FP64 value is within 0.1 % of gamma*."""
@@ -227,12 +238,7 @@ def main():
     launches = g.kernel_launches() - launches0
     it_ms, it_launches, evals = g.read_timing()
     g.set_timing(False)
-    total_ms = sum(times)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
-    value = world * a.steps / (total_ms / 1e3)
+    value, total_ms = aggregate(sum(times), a.steps, world, dist, dev)
 
     # e2e: public API, pinned host inputs in, results read back to the host each step
     loads_h = torch.tensor(base[None], dtype=torch.float64).pin_memory()

@@ -9,6 +9,9 @@ Modules:
              forms, the supergradient, and the GDM / Adam / AdaGrad ascent rules.
   exact   -- an exact LP/QP solver (dense primal-dual interior point with a
              weak-duality sandwich) and brute-force vertex enumeration for tiny LPs.
+  mlp     -- the warm-start perceptron: forward pass, mean-squared-error gradient
+             and Adam, in FP64 (the paper has no learned part; any dual proposal
+             is a valid bound by Remarks 1-2).
 
 Every function names the passage of "GPU-Accelerated DCOPF using Gradient-Based
 Optimization" (arXiv 2406.13191) it follows.  All functions are pinned by
