@@ -12,7 +12,11 @@ EXPORTS = ("dcopf_version", "dcopf_status_string", "dcopf_solve_params_default",
            "dcopf_dual_create", "dcopf_dual_destroy", "dcopf_dual_info", "dcopf_dual_eval",
            "dcopf_dual_certify_bound", "dcopf_dual_solve_batch", "dcopf_dual_kernel_launches",
            "dcopf_dual_device_error", "dcopf_dual_set_timing", "dcopf_dual_read_timing",
-           "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc")
+           "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc",
+           "dcopf_mlp_create", "dcopf_mlp_destroy", "dcopf_mlp_num_params", "dcopf_mlp_set_params",
+           "dcopf_mlp_get_params", "dcopf_mlp_set_normalization", "dcopf_mlp_forward",
+           "dcopf_mlp_loss_grad", "dcopf_mlp_train_step", "dcopf_mlp_warm_start",
+           "dcopf_mlp_device_error", "dcopf_mlp_kernel_launches")
 
 STATUS = {0: "DCOPF_OK", 1: "DCOPF_ERR_INVALID_ARG", 2: "DCOPF_ERR_NETWORK", 3: "DCOPF_ERR_CUDA",
           4: "DCOPF_ERR_OOM", 5: "DCOPF_ERR_TIMEOUT", 6: "DCOPF_ERR_UNSUPPORTED"}
@@ -45,6 +49,16 @@ class SolveParams(C.Structure):
                 ("alpha_lambda", C.c_double), ("rho", C.c_double), ("beta1", C.c_double),
                 ("beta2", C.c_double), ("eps", C.c_double), ("decay", C.c_double),
                 ("gap", C.c_double), ("tol", C.c_double), ("target_value", P)]
+
+
+class MlpDesc(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("n_hidden", C.c_int32), ("n_out", C.c_int32),
+                ("max_batch", C.c_int32)]
+
+
+class AdamParams(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("eps", C.c_double)]
 
 
 class DcopfError(RuntimeError):
@@ -88,10 +102,34 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.dcopf_dual_eval_noalloc.argtypes = [P, C.c_int32, P, P, P, P, P, C.c_int32, P, P, P, P,
                                             P, P]
     lib.dcopf_dual_read_timing.argtypes = [P, F64P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.dcopf_mlp_create.argtypes = [C.POINTER(MlpDesc), C.POINTER(P)]
+    lib.dcopf_mlp_destroy.argtypes = [P]
+    lib.dcopf_mlp_num_params.argtypes = [P]
+    lib.dcopf_mlp_num_params.restype = C.c_int64
+    lib.dcopf_mlp_set_params.argtypes = [P, P, P]
+    lib.dcopf_mlp_get_params.argtypes = [P, P, P]
+    lib.dcopf_mlp_set_normalization.argtypes = [P, P, P, P, P, P]
+    lib.dcopf_mlp_forward.argtypes = [P, C.c_int32, P, P, P]
+    lib.dcopf_mlp_loss_grad.argtypes = [P, C.c_int32, P, C.c_int64, P, P, P, P, P]
+    lib.dcopf_mlp_train_step.argtypes = [P, C.c_int32, P, C.c_int64, P, P,
+                                         C.POINTER(AdamParams), P, P]
+    lib.dcopf_mlp_warm_start.argtypes = [P, C.c_int32, P, P, P, P, P]
+    lib.dcopf_mlp_device_error.argtypes = [P]
+    lib.dcopf_mlp_kernel_launches.argtypes = [P]
+    lib.dcopf_mlp_kernel_launches.restype = C.c_int64
+    for name in ("dcopf_mlp_create", "dcopf_mlp_destroy", "dcopf_mlp_set_params",
+                 "dcopf_mlp_get_params", "dcopf_mlp_set_normalization", "dcopf_mlp_forward",
+                 "dcopf_mlp_loss_grad", "dcopf_mlp_train_step", "dcopf_mlp_warm_start",
+                 "dcopf_mlp_device_error"):
+        getattr(lib, name).restype = C.c_int
     for name in ("dcopf_dual_create", "dcopf_dual_destroy", "dcopf_dual_info", "dcopf_dual_eval",
                  "dcopf_dual_certify_bound", "dcopf_dual_solve_batch", "dcopf_dual_device_error",
                  "dcopf_dual_set_timing", "dcopf_dual_read_timing",
-                 "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc"):
+                 "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc",
+           "dcopf_mlp_create", "dcopf_mlp_destroy", "dcopf_mlp_num_params", "dcopf_mlp_set_params",
+           "dcopf_mlp_get_params", "dcopf_mlp_set_normalization", "dcopf_mlp_forward",
+           "dcopf_mlp_loss_grad", "dcopf_mlp_train_step", "dcopf_mlp_warm_start",
+           "dcopf_mlp_device_error", "dcopf_mlp_kernel_launches"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libdcopfdual.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["network.cpp", "api.cu", "k_sparse.cu", "k_phases.cu", "k_fused.cu", "k_tensor.cu", "k_noalloc.cu", "k_dense.cu"]
+SOURCES = ["network.cpp", "api.cu", "k_sparse.cu", "k_phases.cu", "k_fused.cu", "k_tensor.cu", "k_noalloc.cu", "k_dense.cu",
+           "k_mlp.cu"]
 
 
 def nvcc() -> str:
@@ -48,7 +49,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    hdrs.append(os.path.join(INCLUDE, "dcopf_dual.h"))
+    hdrs += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(f) < t for f in srcs + hdrs):

@@ -1,0 +1,481 @@
+// Learned warm start: a two-hidden-layer GELU perceptron from bus loads to a dual
+// point, with its training (forward, mean-squared-error gradient, Adam) on the GPU.
+// Any proposal with mu >= 0 is a valid dual point (Section 3, Remarks 1-2), so the
+// network only changes where the ascent of Algorithm 1 starts.
+//
+// Every product is one FP32 SIMT GEMM kernel with a fused epilogue (bias, GELU and
+// the stored pre-activation on the way forward; the GELU derivative on the way
+// back); the small kernels around it gather and normalise a minibatch, form the
+// output gradient and loss, sum bias gradients and apply Adam.  All reductions have
+// a fixed order, so a call is deterministic for a given launch shape.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <new>
+
+#include "dcopf_mlp.h"
+#include "kernels.h"
+
+using namespace dcopf;
+
+namespace {
+
+constexpr int TBM = 64, TBN = 64, TBK = 16, GEMM_THREADS = 256;
+enum { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_GELU = 2, EPI_GELU_BACK = 3 };
+
+// GELU(z) = z Phi(z), Phi the standard normal CDF, and its derivative
+// Phi(z) + z phi(z).
+__device__ __forceinline__ float gelu_f(float z) {
+  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
+  const float pdf = 0.39894228040143268f * expf(-0.5f * z * z);
+  return cdf + z * pdf;
+}
+
+// C[M][N] = op(A)[M][K] op(B)[K][N] with the epilogue EPI.  op(A)(m, k) is
+// A[m*lda + k], or A[k*lda + m] when TA; op(B)(k, n) is B[k*ldb + n], or B[n*ldb + k]
+// when TB.  64 x 64 output tile per block, 16-deep K slices staged in shared memory,
+// a 4 x 4 register tile per thread (rows ty + 16i, columns tx + 16j).
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(GEMM_THREADS)
+    k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda, const float* __restrict__ B,
+            int ldb, float* __restrict__ C, int ldc, const float* __restrict__ bias,
+            float* __restrict__ Z, int ldz) {
+  __shared__ float As[TBK][TBM + 1];
+  __shared__ float Bs[TBK][TBN + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += TBK) {
+#pragma unroll
+    for (int e = 0; e < (TBM * TBK) / GEMM_THREADS; ++e) {
+      const int q = tid + e * GEMM_THREADS;
+      int m, k;
+      if (TA) { m = q % TBM; k = q / TBM; } else { k = q % TBK; m = q / TBK; }
+      const int gm = m0 + m, gk = k0 + k;
+      float v = 0.f;
+      if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+      As[k][m] = v;
+    }
+#pragma unroll
+    for (int e = 0; e < (TBN * TBK) / GEMM_THREADS; ++e) {
+      const int q = tid + e * GEMM_THREADS;
+      int n, k;
+      if (TB) { k = q % TBK; n = q / TBK; } else { n = q % TBN; k = q / TBN; }
+      const int gn = n0 + n, gk = k0 + k;
+      float v = 0.f;
+      if (gn < N && gk < K) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
+      Bs[k][n] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TBK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      if (EPI == EPI_BIAS || EPI == EPI_BIAS_GELU) v += bias[n];
+      if (EPI == EPI_BIAS_GELU) {
+        Z[(size_t)m * ldz + n] = v;
+        v = gelu_f(v);
+      }
+      if (EPI == EPI_GELU_BACK) v *= gelu_grad_f(Z[(size_t)m * ldz + n]);
+      C[(size_t)m * ldc + n] = v;
+    }
+  }
+}
+
+// Xn[b][i] = (X[r][i] - shift[i]) * scale[i], r = idx[b] (or b without idx).  A row
+// index outside [0, n_rows) records DCOPF_ERR_INVALID_ARG and yields a zero row.
+template <typename T>
+__global__ void k_mlp_in(int Bn, int n_in, const int* __restrict__ idx, int64_t n_rows,
+                         const T* __restrict__ X, const float* __restrict__ shift,
+                         const float* __restrict__ scale, float* __restrict__ Xn, int* err) {
+  const int b = blockIdx.y;
+  const int64_t r = idx ? (int64_t)idx[b] : (int64_t)b;
+  const bool ok = r >= 0 && r < n_rows;
+  if (!ok && blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(err, 0, (int)DCOPF_ERR_INVALID_ARG);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_in; i += gridDim.x * blockDim.x)
+    Xn[(size_t)b * n_in + i] = ok ? ((float)X[r * n_in + i] - shift[i]) * scale[i] : 0.f;
+}
+
+constexpr int OUT_BLOCKS = 296, OUT_THREADS = 256;
+
+// dU = 2 / (B n_out) (U - T) with T the normalised targets of rows idx; the squared
+// error summed per block (FP32 per thread, FP64 across the block) into part[block].
+__global__ void __launch_bounds__(OUT_THREADS)
+    k_mlp_out_grad(int Bn, int n_out, const float* __restrict__ U, const int* __restrict__ idx,
+                   int64_t n_rows, const float* __restrict__ Y, const float* __restrict__ shift,
+                   const float* __restrict__ inv_scale, float* __restrict__ dU, double* part) {
+  __shared__ double sh[OUT_THREADS / 32];
+  const int64_t total = (int64_t)Bn * n_out;
+  const float g = 2.0f / (float)total;
+  float s = 0.f;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / n_out), o = (int)(e - (int64_t)b * n_out);
+    const int64_t r = idx ? (int64_t)idx[b] : (int64_t)b;
+    float d = 0.f;
+    if (r >= 0 && r < n_rows) d = U[e] - (Y[r * n_out + o] - shift[o]) * inv_scale[o];
+    dU[e] = g * d;
+    s = fmaf(d, d, s);
+  }
+  const double t = block_sum((double)s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_mlp_loss(int nparts, const double* __restrict__ part, double denom, float* loss) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int q = threadIdx.x; q < nparts; q += blockDim.x) s += part[q];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *loss = (float)(s / denom);
+}
+
+// db[n] = sum over rows of D[m][n] (fixed row order).
+__global__ void k_colsum(int M, int N, const float* __restrict__ D, float* __restrict__ db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int m = 0; m < M; ++m) s += D[(size_t)m * N + n];
+  db[n] = s;
+}
+
+__global__ void k_adam(int64_t P, float* __restrict__ p, const float* __restrict__ g,
+                       float* __restrict__ m, float* __restrict__ v, float b1, float b2, float c1,
+                       float c2, float eps) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= c1 * mi / (sqrtf(vi * c2) + eps);
+  }
+}
+
+__global__ void k_out_map(int64_t total, int n_out, const float* __restrict__ U,
+                          const float* __restrict__ shift, const float* __restrict__ scale,
+                          float* __restrict__ Yo) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int o = (int)(e % n_out);
+    Yo[e] = fmaf(scale[o], U[e], shift[o]);
+  }
+}
+
+// (lambda, eta) = output map of U; mu_hi = max(eta, 0), mu_lo = max(-eta, 0).
+__global__ void k_to_duals(int Bn, int n_out, const float* __restrict__ U,
+                           const float* __restrict__ shift, const float* __restrict__ scale,
+                           double* __restrict__ lam, double* __restrict__ mh,
+                           double* __restrict__ ml) {
+  const int b = blockIdx.y, nl = n_out - 1;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out; o += gridDim.x * blockDim.x) {
+    const double y = (double)shift[o] + (double)scale[o] * (double)U[(size_t)b * n_out + o];
+    if (o == 0) {
+      lam[b] = y;
+    } else {
+      mh[(size_t)b * nl + o - 1] = y > 0.0 ? y : 0.0;
+      ml[(size_t)b * nl + o - 1] = y < 0.0 ? -y : 0.0;
+    }
+  }
+}
+
+__global__ void k_recip(int n, const float* __restrict__ a, float* __restrict__ r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = 1.0f / a[i];
+}
+
+__global__ void k_fill(int64_t n, float* __restrict__ a, float v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+struct dcopf_mlp {
+  int n_in = 0, nh = 0, n_out = 0, max_batch = 0;
+  int64_t P = 0, o_b1 = 0, o_W2 = 0, o_b2 = 0, o_W3 = 0, o_b3 = 0;
+  int64_t adam_t = 0;
+  int64_t launches = 0;
+  DBuf params, grad, mom1, mom2, norm, part, err;
+  DBuf Xn, Z1, H1, Z2, H2, U, dU, D1, D2;
+  float* in_shift() const { return norm.as<float>(); }
+  float* in_scale() const { return norm.as<float>() + n_in; }
+  float* out_shift() const { return norm.as<float>() + 2 * n_in; }
+  float* out_scale() const { return norm.as<float>() + 2 * n_in + n_out; }
+  float* out_inv() const { return norm.as<float>() + 2 * n_in + 2 * n_out; }
+};
+
+namespace {
+
+template <bool TA, bool TB, int EPI>
+void gemm(dcopf_mlp* h, cudaStream_t s, int M, int N, int K, const float* A, int lda,
+          const float* B, int ldb, float* C, int ldc, const float* bias = nullptr,
+          float* Z = nullptr, int ldz = 0) {
+  dim3 grid(cdiv(N, TBN), cdiv(M, TBM));
+  k_sgemm<TA, TB, EPI><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, ldz);
+  h->launches += 1;
+}
+
+// Forward pass of the rows already normalised in Xn: Z1, H1, Z2, H2 and U (the
+// normalised output).
+void forward_rows(dcopf_mlp* h, cudaStream_t s, int Bn) {
+  const float* P = h->params.as<float>();
+  const int ni = h->n_in, nh = h->nh, no = h->n_out;
+  gemm<false, false, EPI_BIAS_GELU>(h, s, Bn, nh, ni, h->Xn.as<float>(), ni, P, nh,
+                                    h->H1.as<float>(), nh, P + h->o_b1, h->Z1.as<float>(), nh);
+  gemm<false, false, EPI_BIAS_GELU>(h, s, Bn, nh, nh, h->H1.as<float>(), nh, P + h->o_W2, nh,
+                                    h->H2.as<float>(), nh, P + h->o_b2, h->Z2.as<float>(), nh);
+  gemm<false, false, EPI_BIAS>(h, s, Bn, no, nh, h->H2.as<float>(), nh, P + h->o_W3, no,
+                               h->U.as<float>(), no, P + h->o_b3);
+}
+
+template <typename T>
+void gather_rows(dcopf_mlp* h, cudaStream_t s, int Bn, const int* idx, int64_t n_rows, const T* X) {
+  dim3 grid(cdiv(h->n_in, 256), Bn);
+  k_mlp_in<T><<<grid, 256, 0, s>>>(Bn, h->n_in, idx, n_rows, X, h->in_shift(), h->in_scale(),
+                                   h->Xn.as<float>(), h->err.as<int>());
+  h->launches += 1;
+}
+
+// Loss and gradient into h->grad (and *loss when given).
+void loss_grad_rows(dcopf_mlp* h, cudaStream_t s, int Bn, const int* idx, int64_t n_rows,
+                    const float* X, const float* Y, float* loss) {
+  const float* P = h->params.as<float>();
+  float* G = h->grad.as<float>();
+  const int ni = h->n_in, nh = h->nh, no = h->n_out;
+  gather_rows<float>(h, s, Bn, idx, n_rows, X);
+  forward_rows(h, s, Bn);
+  k_mlp_out_grad<<<OUT_BLOCKS, OUT_THREADS, 0, s>>>(Bn, no, h->U.as<float>(), idx, n_rows, Y,
+                                                    h->out_shift(), h->out_inv(),
+                                                    h->dU.as<float>(), h->part.as<double>());
+  h->launches += 1;
+  if (loss) {
+    k_mlp_loss<<<1, 256, 0, s>>>(OUT_BLOCKS, h->part.as<double>(), (double)Bn * no, loss);
+    h->launches += 1;
+  }
+  // layer 3: dW3 = H2^T dU, db3 = column sums of dU, dZ2 = (dU W3^T) * GELU'(Z2)
+  gemm<true, false, EPI_STORE>(h, s, nh, no, Bn, h->H2.as<float>(), nh, h->dU.as<float>(), no,
+                               G + h->o_W3, no);
+  k_colsum<<<cdiv(no, 256), 256, 0, s>>>(Bn, no, h->dU.as<float>(), G + h->o_b3);
+  h->launches += 1;
+  gemm<false, true, EPI_GELU_BACK>(h, s, Bn, nh, no, h->dU.as<float>(), no, P + h->o_W3, no,
+                                   h->D2.as<float>(), nh, nullptr, h->Z2.as<float>(), nh);
+  // layer 2
+  gemm<true, false, EPI_STORE>(h, s, nh, nh, Bn, h->H1.as<float>(), nh, h->D2.as<float>(), nh,
+                               G + h->o_W2, nh);
+  k_colsum<<<cdiv(nh, 256), 256, 0, s>>>(Bn, nh, h->D2.as<float>(), G + h->o_b2);
+  h->launches += 1;
+  gemm<false, true, EPI_GELU_BACK>(h, s, Bn, nh, nh, h->D2.as<float>(), nh, P + h->o_W2, nh,
+                                   h->D1.as<float>(), nh, nullptr, h->Z1.as<float>(), nh);
+  // layer 1
+  gemm<true, false, EPI_STORE>(h, s, ni, nh, Bn, h->Xn.as<float>(), ni, h->D1.as<float>(), nh, G,
+                               nh);
+  k_colsum<<<cdiv(nh, 256), 256, 0, s>>>(Bn, nh, h->D1.as<float>(), G + h->o_b1);
+  h->launches += 1;
+}
+
+dcopf_status launch_status() {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return DCOPF_OK;
+  return e == cudaErrorMemoryAllocation ? DCOPF_ERR_OOM : DCOPF_ERR_CUDA;
+}
+
+bool valid(const dcopf_mlp* h, int Bn) { return h && Bn >= 1 && Bn <= h->max_batch; }
+
+}  // namespace
+
+extern "C" {
+
+dcopf_status dcopf_mlp_create(const dcopf_mlp_desc* d, dcopf_mlp_t* out) {
+  if (!d || !out) return DCOPF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (d->n_in < 1 || d->n_hidden < 1 || d->n_out < 1 || d->max_batch < 1) return DCOPF_ERR_INVALID_ARG;
+  const int64_t ni = d->n_in, nh = d->n_hidden, no = d->n_out, mb = d->max_batch;
+  if (ni * nh > (1LL << 31) || nh * no > (1LL << 31) || mb * (ni > no ? ni : no) > (1LL << 31))
+    return DCOPF_ERR_INVALID_ARG;
+  dcopf_mlp* h = new (std::nothrow) dcopf_mlp();
+  if (!h) return DCOPF_ERR_OOM;
+  h->n_in = d->n_in;
+  h->nh = d->n_hidden;
+  h->n_out = d->n_out;
+  h->max_batch = d->max_batch;
+  h->o_b1 = ni * nh;
+  h->o_W2 = h->o_b1 + nh;
+  h->o_b2 = h->o_W2 + nh * nh;
+  h->o_W3 = h->o_b2 + nh;
+  h->o_b3 = h->o_W3 + nh * no;
+  h->P = h->o_b3 + no;
+  const size_t P4 = (size_t)h->P * 4;
+  bool ok = h->params.alloc(P4) == cudaSuccess && h->grad.alloc(P4) == cudaSuccess &&
+            h->mom1.alloc(P4) == cudaSuccess && h->mom2.alloc(P4) == cudaSuccess &&
+            h->norm.alloc((size_t)(2 * ni + 3 * no) * 4) == cudaSuccess &&
+            h->part.alloc(OUT_BLOCKS * 8) == cudaSuccess && h->err.alloc(16) == cudaSuccess &&
+            h->Xn.alloc((size_t)mb * ni * 4) == cudaSuccess &&
+            h->U.alloc((size_t)mb * no * 4) == cudaSuccess &&
+            h->dU.alloc((size_t)mb * no * 4) == cudaSuccess;
+  for (DBuf* b : {&h->Z1, &h->H1, &h->Z2, &h->H2, &h->D1, &h->D2})
+    ok = ok && b->alloc((size_t)mb * nh * 4) == cudaSuccess;
+  if (!ok) {
+    delete h;
+    cudaGetLastError();
+    return DCOPF_ERR_OOM;
+  }
+  cudaMemset(h->params.p, 0, P4);
+  cudaMemset(h->grad.p, 0, P4);
+  cudaMemset(h->mom1.p, 0, P4);
+  cudaMemset(h->mom2.p, 0, P4);
+  cudaMemset(h->err.p, 0, 16);
+  cudaMemset(h->norm.p, 0, (size_t)(2 * ni + 3 * no) * 4);
+  k_fill<<<cdiv(ni, 256), 256>>>(ni, h->in_scale(), 1.f);
+  k_fill<<<cdiv(no, 256), 256>>>(no, h->out_scale(), 1.f);
+  k_fill<<<cdiv(no, 256), 256>>>(no, h->out_inv(), 1.f);
+  h->launches += 3;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    delete h;
+    return DCOPF_ERR_CUDA;
+  }
+  *out = h;
+  return DCOPF_OK;
+}
+
+dcopf_status dcopf_mlp_destroy(dcopf_mlp_t h) {
+  if (!h) return DCOPF_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  delete h;
+  return DCOPF_OK;
+}
+
+int64_t dcopf_mlp_num_params(dcopf_mlp_t h) { return h ? h->P : -1; }
+
+dcopf_status dcopf_mlp_set_params(dcopf_mlp_t h, const float* params, void* stream) {
+  if (!h || !params) return DCOPF_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t P4 = (size_t)h->P * 4;
+  if (cudaMemcpyAsync(h->params.p, params, P4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(h->mom1.p, 0, P4, s) != cudaSuccess ||
+      cudaMemsetAsync(h->mom2.p, 0, P4, s) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  h->adam_t = 0;
+  return DCOPF_OK;
+}
+
+dcopf_status dcopf_mlp_get_params(dcopf_mlp_t h, float* params, void* stream) {
+  if (!h || !params) return DCOPF_ERR_INVALID_ARG;
+  if (cudaMemcpyAsync(params, h->params.p, (size_t)h->P * 4, cudaMemcpyDeviceToDevice,
+                      (cudaStream_t)stream) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  return DCOPF_OK;
+}
+
+dcopf_status dcopf_mlp_set_normalization(dcopf_mlp_t h, const float* in_shift, const float* in_scale,
+                                         const float* out_shift, const float* out_scale,
+                                         void* stream) {
+  if (!h || !in_shift || !in_scale || !out_shift || !out_scale) return DCOPF_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ni4 = (size_t)h->n_in * 4, no4 = (size_t)h->n_out * 4;
+  if (cudaMemcpyAsync(h->in_shift(), in_shift, ni4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(h->in_scale(), in_scale, ni4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(h->out_shift(), out_shift, no4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(h->out_scale(), out_scale, no4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  k_recip<<<cdiv(h->n_out, 256), 256, 0, s>>>(h->n_out, h->out_scale(), h->out_inv());
+  h->launches += 1;
+  return launch_status();
+}
+
+dcopf_status dcopf_mlp_forward(dcopf_mlp_t h, int32_t batch, const float* x, float* y, void* stream) {
+  if (!valid(h, batch) || !x || !y) return DCOPF_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  gather_rows<float>(h, s, batch, nullptr, batch, x);
+  forward_rows(h, s, batch);
+  const int64_t total = (int64_t)batch * h->n_out;
+  k_out_map<<<cdiv(total, 256) < 2048 ? cdiv(total, 256) : 2048, 256, 0, s>>>(
+      total, h->n_out, h->U.as<float>(), h->out_shift(), h->out_scale(), y);
+  h->launches += 1;
+  return launch_status();
+}
+
+dcopf_status dcopf_mlp_loss_grad(dcopf_mlp_t h, int32_t batch, const int32_t* idx, int64_t n_rows,
+                                 const float* X, const float* Y, float* loss, float* grad,
+                                 void* stream) {
+  if (!valid(h, batch) || !idx || n_rows < 1 || !X || !Y) return DCOPF_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  loss_grad_rows(h, s, batch, idx, n_rows, X, Y, loss);
+  if (grad && cudaMemcpyAsync(grad, h->grad.p, (size_t)h->P * 4, cudaMemcpyDeviceToDevice, s) !=
+                  cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  return launch_status();
+}
+
+dcopf_status dcopf_mlp_train_step(dcopf_mlp_t h, int32_t batch, const int32_t* idx, int64_t n_rows,
+                                  const float* X, const float* Y, const dcopf_adam_params* a,
+                                  float* loss, void* stream) {
+  if (!valid(h, batch) || !idx || n_rows < 1 || !X || !Y || !a) return DCOPF_ERR_INVALID_ARG;
+  if (!(a->lr > 0.0) || !(a->beta1 >= 0.0 && a->beta1 < 1.0) || !(a->beta2 >= 0.0 && a->beta2 < 1.0) ||
+      !(a->eps > 0.0))
+    return DCOPF_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  loss_grad_rows(h, s, batch, idx, n_rows, X, Y, loss);
+  h->adam_t += 1;
+  const double c1 = a->lr / (1.0 - pow(a->beta1, (double)h->adam_t));
+  const double c2 = 1.0 / (1.0 - pow(a->beta2, (double)h->adam_t));
+  k_adam<<<cdiv(h->P, 256) < 4096 ? cdiv(h->P, 256) : 4096, 256, 0, s>>>(
+      h->P, h->params.as<float>(), h->grad.as<float>(), h->mom1.as<float>(), h->mom2.as<float>(),
+      (float)a->beta1, (float)a->beta2, (float)c1, (float)c2, (float)a->eps);
+  h->launches += 1;
+  return launch_status();
+}
+
+dcopf_status dcopf_mlp_warm_start(dcopf_mlp_t h, int32_t batch, const double* loads, double* lambda,
+                                  double* mu_hi, double* mu_lo, void* stream) {
+  if (!valid(h, batch) || !loads || !lambda || !mu_hi || !mu_lo || h->n_out < 2)
+    return DCOPF_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  gather_rows<double>(h, s, batch, nullptr, batch, loads);
+  forward_rows(h, s, batch);
+  dim3 grid(cdiv(h->n_out, 256), batch);
+  k_to_duals<<<grid, 256, 0, s>>>(batch, h->n_out, h->U.as<float>(), h->out_shift(),
+                                  h->out_scale(), lambda, mu_hi, mu_lo);
+  h->launches += 1;
+  return launch_status();
+}
+
+dcopf_status dcopf_mlp_device_error(dcopf_mlp_t h) {
+  if (!h) return DCOPF_ERR_INVALID_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return DCOPF_ERR_CUDA;
+  int e = 0;
+  if (cudaMemcpy(&e, h->err.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(h->err.p, 0, sizeof(int)) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  return (dcopf_status)e;
+}
+
+int64_t dcopf_mlp_kernel_launches(dcopf_mlp_t h) { return h ? h->launches : -1; }
+
+}  // extern "C"

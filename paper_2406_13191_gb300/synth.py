@@ -12,8 +12,9 @@ relative to the flows of a proportional base dispatch.
 This module is shared by the oracle-side tests and the CUDA-side callers.  It
 holds none of the dual method's arithmetic (no dual value, no inner minimiser,
 no ascent step).  The one linear solve it performs is the DC power flow of the
-proportional base dispatch, used only to place the line limits; it goes through
-``scipy.sparse.linalg.spsolve`` and nothing else in the repository uses it.
+proportional dispatch, used only to build inputs (placing the line limits, and keeping
+warm-start scenarios that this dispatch makes feasible); it goes through a scipy
+sparse LU and nothing else in the repository uses it.
 
 Units: powers in p.u. on ``base_mva`` (100 MVA); linear cost coefficients in
 $/MWh and quadratic ones in $/MW^2h, so that a generator producing ``p`` p.u.
@@ -184,8 +185,8 @@ def _laplacian_lu(n_bus, line_from, line_to, line_b, slack=0):
 
 
 def _dc_flows(n_bus, line_from, line_to, line_b, inj, slack=0, lu=None):
-    """DC power flow of injection vectors (columns of ``inj``), used only to place
-    line limits."""
+    """DC power flow of injection vectors (columns of ``inj``), used only to build
+    inputs (line limits, feasible warm-start scenarios)."""
     if lu is None:
         lu, keep = _laplacian_lu(n_bus, line_from, line_to, line_b, slack)
     else:
@@ -353,6 +354,33 @@ def workload(cfg: int, batch: int | None = None) -> Workload:
         raise ValueError(cfg)
     return Workload(net=net, loads=np.ascontiguousarray(loads), outage=out,
                     meta=dict(config=cfg, name=CONFIG_NAMES.get(cfg, "")))
+
+
+# learned warm start on the 2000-bus network: (count, load seed) of the training set
+# and of the held-out evaluation set
+WARM_SETS = {"train": (50000, 4101), "heldout": (4096, 4102)}
+
+
+def warm_loads(split: str, count: int | None = None) -> np.ndarray:
+    """Load vectors of the warm-start sets on the 2000-bus network: per-bus multipliers
+    U[0.85, 1.15] on the base profile, kept only when the proportional dispatch of the
+    scenario meets every line limit (so every instance is feasible by construction).
+    Candidates are drawn in fixed chunks, so a shorter ``count`` is a prefix."""
+    n, seed = WARM_SETS[split]
+    net, base = network_for(1)
+    n = n if count is None else min(n, count)
+    rng = _rng(seed)
+    lu = _laplacian_lu(net.n_bus, net.line_from, net.line_to, net.line_b)
+    out, have = np.empty((n, base.shape[0])), 0
+    while have < n:
+        cand = base[None, :] * rng.uniform(0.85, 1.15, size=(4096, base.shape[0]))
+        inj = _proportional_injections(cand, net.gen_bus, net.pmax)
+        f = _dc_flows(net.n_bus, net.line_from, net.line_to, net.line_b, inj, lu=lu)
+        ok = np.flatnonzero(((f <= net.flow_max[:, None]) & (f >= net.flow_min[:, None])).all(0))
+        take = ok[:n - have]
+        out[have:have + len(take)] = cand[take]
+        have += len(take)
+    return out
 
 
 def scenario_workload(seed: int, n_bus: int, n_line: int, n_gen: int, quadratic: bool,

@@ -1,5 +1,5 @@
 """C ABI checks that need no GPU: the library builds and loads, exports every
-function include/dcopf_dual.h declares, and rejects invalid networks on the host
+function the headers in include/ declare, and rejects invalid networks on the host
 before touching the device."""
 import ctypes as C
 import os
@@ -14,7 +14,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def header_functions():
-    src = open(os.path.join(ROOT, "include", "dcopf_dual.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc))
+                  if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(dcopf_[a-z0-9_]+)\s*\(", src)))
 
