@@ -158,6 +158,74 @@ def cpu_baseline(target_s=10.0):
                       f"{statistics.mean(iters):.0f} iterations each, single thread)"}
 
 
+def warm_start_eval(n_train: int, epochs: int, n_eval: int) -> dict:
+    """Learned warm start on the 2000-bus network: targets from the method's own batched
+    solves of ``n_train`` training scenarios, GPU training, then cold vs warm solves of
+    ``n_eval`` held-out scenarios to the certified 0.1 % gap against the oracle's gamma*."""
+    import numpy as np
+    import torch
+    from paper_2406_13191_gb300 import DcopfDual, synth, warmstart
+    net, _ = synth.network_for(1)
+    g = DcopfDual(net)
+    gold = os.path.join(ROOT, "tests", "golden", "warm_gamma.json")
+    gam = np.array(json.load(open(gold))["gamma"][:n_eval], dtype=float)
+    tk = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=1500,
+              tol=0.0, path="batched", precision="bf16x3")
+    out = {"mode": "warm_start_eval", "network": "synthetic 2000-bus QP", "n_train": n_train,
+           "epochs": epochs, "n_eval": n_eval}
+    Xtr = synth.warm_loads("train", n_train)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    Y, _ = warmstart.dual_targets(g, Xtr, **tk)
+    torch.cuda.synchronize()
+    out["targets_s"] = time.perf_counter() - t
+    m = warmstart.WarmStartMLP(net.n_bus, 1 + net.n_line, 512, max_batch=1024)
+    m.set_params(warmstart.init_params(net.n_bus, 512, 1 + net.n_line, 7))
+    m.set_normalization(*warmstart.normalization(Xtr, Y.cpu().numpy()))
+    Xd = torch.as_tensor(Xtr, dtype=torch.float32, device=m.device)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    launches0 = m.kernel_launches()
+    losses = warmstart.train(m, Xd, Y.contiguous(), epochs, batch=512, lr=1e-3, lr_final=1e-5, seed=11)
+    torch.cuda.synchronize()
+    out["train_s"] = time.perf_counter() - t
+    out["train_steps"] = epochs * (n_train // 512)
+    out["train_kernel_launches"] = m.kernel_launches() - launches0
+    out["train_tflops"] = (3 * 2 * 512 * m.num_params * out["train_steps"]) / out["train_s"] / 1e12
+    out["loss_first_epoch"], out["loss_last_epoch"] = losses[0], losses[-1]
+    del Xd
+    Xev = synth.warm_loads("heldout", n_eval)
+    lam, mh, ml = m.warm_start(Xev)
+    b0 = g.certify(Xev, lam, mh, ml)[0].cpu().numpy()
+    out["proposal_gap_median"] = float(np.median((gam - b0) / np.abs(gam)))
+    out["proposal_gap_p90"] = float(np.percentile((gam - b0) / np.abs(gam), 90))
+    arms = {"cold": dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=4000),
+            "warm": dict(rule="adam", alpha=300.0, beta1=0.9, beta2=0.999, decay=0.997, max_iters=4000)}
+    Ld = torch.tensor(Xev, dtype=torch.float64, device=m.device)
+    Td = torch.tensor(gam, dtype=torch.float64, device=m.device)
+    for name, kw in arms.items():
+        for rep in range(2):                         # first pass warms up graphs and buffers
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            w = m.warm_start(Ld) if name == "warm" else None
+            r = g.solve(Ld, target=Td, warm=w, path="batched", precision="bf16x3", **kw)
+            e1.record()
+            e1.synchronize()
+        it = r.iters.cpu().numpy()
+        st = r.status.cpu().numpy()
+        b = r.bound.cpu().numpy()
+        out[name] = {"instances_per_s": n_eval / (e0.elapsed_time(e1) / 1e3),
+                     "ms": e0.elapsed_time(e1), "mean_iters": float(it.mean()),
+                     "p90_iters": float(np.percentile(it, 90)), "most_iters": int(it.max()),
+                     "reached_gap": int((st == 0).sum()),
+                     "all_bounds_valid": bool(np.all(b <= gam + 1e-9 * np.abs(gam))),
+                     "settings": kw}
+    out["iteration_ratio"] = out["warm"]["mean_iters"] / out["cold"]["mean_iters"]
+    out["throughput_ratio"] = out["warm"]["instances_per_s"] / out["cold"]["instances_per_s"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -166,7 +234,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--warm-start-eval", action="store_true",
+                    help="evaluate the learned warm start (prints its own JSON, not the bench line)")
+    ap.add_argument("--n-train", type=int, default=50000)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--n-eval", type=int, default=4096)
     a = ap.parse_args()
+    if a.warm_start_eval:
+        print(json.dumps(warm_start_eval(a.n_train, a.epochs, a.n_eval)))
+        return
     world, rank, local, dist = dist_setup(a.gpus)
 
     if a.impl == "reference":

@@ -209,6 +209,45 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
                                     double* best_bound, int32_t* iters, int32_t* inst_status,
                                     void* stream);
 
+/* One network's instances in a group solve (dcopf_dual_solve_group).  Arrays as in
+ * dcopf_dual_solve_batch, for this item's handle; target_value [batch] (DEVICE,
+ * nullable) plays the role of params->target_value for these instances; params
+ * (HOST, nullable) overrides the group's ascent settings for this network (its
+ * check_every and target_value are ignored). */
+typedef struct {
+  dcopf_dual_t net;
+  int32_t batch;
+  int32_t reserved;
+  const dcopf_solve_params* params;
+  const double* loads;
+  const int32_t* outage;
+  const double* target_value;
+  double* lambda;
+  double* mu_hi;
+  double* mu_lo;
+  double* best_bound;
+  int32_t* iters;
+  int32_t* inst_status;
+} dcopf_group_item;
+
+/* Batched solves of several networks of different sizes in one go: the same method
+ * and results as dcopf_dual_solve_batch on each item (Section 3.3, Algorithm 1 and
+ * Adam / AdaGrad), with the iterations of every network issued together.  Each round
+ * of check_every (at least 16) iterations is ONE launch of a CUDA graph that holds
+ * every network's iteration kernels as parallel branches; the FP64 certification of
+ * the round's candidates follows per network.  The paper solves one instance at a
+ * time; this is the batching it leaves to future work.
+ *   n_items >= 1 items with pairwise distinct handles, all created on one device
+ *   params: shared ascent settings (items may override them); precision must be
+ *     DCOPF_BF16X3 and path DCOPF_PATH_AUTO or DCOPF_PATH_BATCHED in every set used
+ *     (else DCOPF_ERR_UNSUPPORTED); params->target_value is ignored (each item has
+ *     its own); the round length is the shared check_every
+ * Synchronises `stream` before returning.
+ * Errors: INVALID_ARG (a NULL or repeated handle, handles on different devices, bad
+ * sizes or parameters), NETWORK, UNSUPPORTED, OOM, CUDA, TIMEOUT. */
+dcopf_status dcopf_dual_solve_group(int32_t n_items, const dcopf_group_item* items,
+                                    const dcopf_solve_params* params, void* stream);
+
 /* dcopf_dual_eval without any device allocation, for callers that cannot allocate
  * device memory (a host framework that owns every allocation, or a real-time loop
  * where cudaMalloc's implicit synchronisation and latency are not acceptable).  The

@@ -4,4 +4,4 @@ The compute path is libdcopfdual.so (hand-written sm_103a CUDA behind the C ABI 
 include/dcopf_dual.h).  ``DcopfDual`` marshals torch tensors into that ABI; torch is
 used only for device memory and streams.
 """
-from .dual import DcopfDual, SolveResult  # noqa: F401
+from .dual import DcopfDual, SolveResult, solve_group  # noqa: F401

@@ -12,7 +12,7 @@ EXPORTS = ("dcopf_version", "dcopf_status_string", "dcopf_solve_params_default",
            "dcopf_dual_create", "dcopf_dual_destroy", "dcopf_dual_info", "dcopf_dual_eval",
            "dcopf_dual_certify_bound", "dcopf_dual_solve_batch", "dcopf_dual_kernel_launches",
            "dcopf_dual_device_error", "dcopf_dual_set_timing", "dcopf_dual_read_timing",
-           "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc",
+           "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc", "dcopf_dual_solve_group",
            "dcopf_mlp_create", "dcopf_mlp_destroy", "dcopf_mlp_num_params", "dcopf_mlp_set_params",
            "dcopf_mlp_get_params", "dcopf_mlp_set_normalization", "dcopf_mlp_forward",
            "dcopf_mlp_loss_grad", "dcopf_mlp_train_step", "dcopf_mlp_warm_start",
@@ -49,6 +49,12 @@ class SolveParams(C.Structure):
                 ("alpha_lambda", C.c_double), ("rho", C.c_double), ("beta1", C.c_double),
                 ("beta2", C.c_double), ("eps", C.c_double), ("decay", C.c_double),
                 ("gap", C.c_double), ("tol", C.c_double), ("target_value", P)]
+
+
+class GroupItem(C.Structure):
+    _fields_ = [("net", P), ("batch", C.c_int32), ("reserved", C.c_int32), ("params", P), ("loads", P),
+                ("outage", P), ("target_value", P), ("lambda_", P), ("mu_hi", P), ("mu_lo", P),
+                ("best_bound", P), ("iters", P), ("inst_status", P)]
 
 
 class MlpDesc(C.Structure):
@@ -102,6 +108,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.dcopf_dual_eval_noalloc.argtypes = [P, C.c_int32, P, P, P, P, P, C.c_int32, P, P, P, P,
                                             P, P]
     lib.dcopf_dual_read_timing.argtypes = [P, F64P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.dcopf_dual_solve_group.argtypes = [C.c_int32, C.POINTER(GroupItem), C.POINTER(SolveParams), P]
+    lib.dcopf_dual_solve_group.restype = C.c_int
     lib.dcopf_mlp_create.argtypes = [C.POINTER(MlpDesc), C.POINTER(P)]
     lib.dcopf_mlp_destroy.argtypes = [P]
     lib.dcopf_mlp_num_params.argtypes = [P]
@@ -125,7 +133,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     for name in ("dcopf_dual_create", "dcopf_dual_destroy", "dcopf_dual_info", "dcopf_dual_eval",
                  "dcopf_dual_certify_bound", "dcopf_dual_solve_batch", "dcopf_dual_device_error",
                  "dcopf_dual_set_timing", "dcopf_dual_read_timing",
-                 "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc",
+                 "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc", "dcopf_dual_solve_group",
            "dcopf_mlp_create", "dcopf_mlp_destroy", "dcopf_mlp_num_params", "dcopf_mlp_set_params",
            "dcopf_mlp_get_params", "dcopf_mlp_set_normalization", "dcopf_mlp_forward",
            "dcopf_mlp_loss_grad", "dcopf_mlp_train_step", "dcopf_mlp_warm_start",

@@ -495,6 +495,17 @@ dcopf_status dcopf_dual_certify_bound(dcopf_dual_t h, int32_t batch, const doubl
   return finish(h, s);
 }
 
+static dcopf_status check_params(const dcopf_solve_params& p) {
+  if (p.rule < DCOPF_GDM || p.rule > DCOPF_ADAGRAD || p.max_iters < 1 || !(p.alpha > 0) ||
+      !std::isfinite(p.alpha) || p.check_every < 0 || !(p.gap >= 0) || !(p.decay > 0) ||
+      !(p.beta1 >= 0 && p.beta1 < 1) || !(p.beta2 >= 0 && p.beta2 < 1) || !(p.eps >= 0) ||
+      p.path < DCOPF_PATH_AUTO || p.path > DCOPF_PATH_BATCHED)
+    return DCOPF_ERR_INVALID_ARG;
+  if (p.precision != DCOPF_FP64 && p.precision != DCOPF_FP32 && p.precision != DCOPF_BF16X3)
+    return DCOPF_ERR_INVALID_ARG;
+  return DCOPF_OK;
+}
+
 dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double* loads,
                                     const int32_t* outage, const dcopf_solve_params* params,
                                     double* lambda, double* mu_hi, double* mu_lo,
@@ -504,13 +515,7 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
   if (r) return r;
   if (!params || !lambda || !mu_hi || !mu_lo || !best_bound) return DCOPF_ERR_INVALID_ARG;
   const dcopf_solve_params& p = *params;
-  if (p.rule < DCOPF_GDM || p.rule > DCOPF_ADAGRAD || p.max_iters < 1 || !(p.alpha > 0) ||
-      !std::isfinite(p.alpha) || p.check_every < 0 || !(p.gap >= 0) || !(p.decay > 0) ||
-      !(p.beta1 >= 0 && p.beta1 < 1) || !(p.beta2 >= 0 && p.beta2 < 1) || !(p.eps >= 0) ||
-      p.path < DCOPF_PATH_AUTO || p.path > DCOPF_PATH_BATCHED)
-    return DCOPF_ERR_INVALID_ARG;
-  if (p.precision != DCOPF_FP64 && p.precision != DCOPF_FP32 && p.precision != DCOPF_BF16X3)
-    return DCOPF_ERR_INVALID_ARG;
+  if ((r = check_params(p))) return r;
   int path = p.path;
   if (path == DCOPF_PATH_AUTO) path = (batch == 1 && !outage) ? DCOPF_PATH_FUSED : DCOPF_PATH_BATCHED;
   if (path == DCOPF_PATH_FUSED && (batch != 1 || outage)) return DCOPF_ERR_UNSUPPORTED;
@@ -531,6 +536,44 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
                                inst_status, s);
   return solve_loop<float>(h, batch, loads, outage, q, path, lambda, mu_hi, mu_lo, best_bound, iters,
                            inst_status, s);
+}
+
+dcopf_status dcopf_dual_solve_group(int32_t n_items, const dcopf_group_item* items,
+                                    const dcopf_solve_params* params, void* stream) {
+  if (n_items < 1 || !items || !params) return DCOPF_ERR_INVALID_ARG;
+  dcopf_status r = check_params(*params);
+  if (r) return r;
+  if (params->precision != DCOPF_BF16X3 ||
+      (params->path != DCOPF_PATH_AUTO && params->path != DCOPF_PATH_BATCHED))
+    return DCOPF_ERR_UNSUPPORTED;
+  std::vector<TensorItem> ti(n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const dcopf_group_item& it = items[i];
+    if ((r = check_batch(it.net, it.batch, it.loads))) return r;
+    if (!it.lambda || !it.mu_hi || !it.mu_lo || !it.best_bound) return DCOPF_ERR_INVALID_ARG;
+    if (it.net->device != items[0].net->device) return DCOPF_ERR_INVALID_ARG;
+    if (it.params) {
+      if ((r = check_params(*it.params))) return r;
+      if (it.params->precision != DCOPF_BF16X3 ||
+          (it.params->path != DCOPF_PATH_AUTO && it.params->path != DCOPF_PATH_BATCHED))
+        return DCOPF_ERR_UNSUPPORTED;
+    }
+    for (int j = 0; j < i; ++j)
+      if (items[j].net == it.net) return DCOPF_ERR_INVALID_ARG;
+    ti[i] = TensorItem{it.net,    it.params, it.batch,      it.loads, it.outage,
+                       it.target_value, it.lambda, it.mu_hi, it.mu_lo, it.best_bound,
+                       it.iters,  it.inst_status};
+  }
+  DeviceGuard guard(items[0].net->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < n_items; ++i) {
+    dcopf_dual* h = items[i].net;
+    if ((r = check_outage(h, items[i].batch, items[i].outage, s))) return r;
+    if ((r = ensure_workspace(h, items[i].batch))) return r;
+    CUDA_TRY(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+    if ((r = run_base_flows(h, items[i].batch, items[i].loads, items[i].outage, s))) return r;
+  }
+  return solve_tensor_group(ti.data(), n_items, *params, s);
 }
 
 int64_t dcopf_dual_kernel_launches(dcopf_dual_t h) { return h ? (int64_t)h->launches : 0; }

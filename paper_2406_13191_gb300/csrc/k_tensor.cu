@@ -736,25 +736,39 @@ static dcopf_status ensure_batch_bufs(dcopf_dual* h, int B, int n_tiles) {
   return DCOPF_OK;
 }
 
-template <typename S>
-dcopf_status solve_tensor(dcopf_dual* h, int B, const double* loads, const int* outage,
-                          const dcopf_solve_params& p, double* lam, double* mh, double* ml,
-                          double* bound, int* iters, int* status, cudaStream_t s) {
-  static_assert(sizeof(S) == 4, "the tensor-core solve keeps FP32 state");
+// One network's share of a batched tensor-core solve: the instances, the kernel
+// arguments of one iteration, and the solve state.
+struct TensorRun {
+  TensorItem it{};
+  dcopf_solve_params p{};
+  SolveState<float> st{};
+  StepArgs P{};
+  GemmArgs ga{}, gf{};
+  StepEpi E{};
+  int splits = 1, n_tiles = 0;
+  unsigned gi = 1;
+  bool running = true;
+};
+
+// Buffers, state initialisation and the iteration's kernel arguments; the work is
+// enqueued on the handle's internal stream, ordered after the caller's stream s.
+static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
+  dcopf_dual* h = R.it.h;
+  const int B = R.it.B;
   dcopf_status r;
   if ((r = ensure_tensor_operands(h)) || (r = ensure_tensor_batch(h, B))) return r;
-  SolveState<float> st{};
-  if ((r = ensure_state<float>(h, B, &st))) return r;
+  if ((r = ensure_state<float>(h, B, &R.st))) return r;
   const int nl = h->host.n_line, ng = h->host.n_gen;
-  const int n_tiles = (nl + STEP_CHUNK - 1) / STEP_CHUNK;
-  if ((r = ensure_batch_bufs(h, B, n_tiles))) return r;
+  R.n_tiles = (nl + STEP_CHUNK - 1) / STEP_CHUNK;
+  if ((r = ensure_batch_bufs(h, B, R.n_tiles))) return r;
   const int ldF = (nl + 3) & ~3;
   if (h->bb.F.alloc((size_t)B * ldF * sizeof(float)) != cudaSuccess) return DCOPF_ERR_OOM;
   TensorOps& T = h->tops;
   Workspace& w = h->ws;
   BatchView& bb = h->bb.v;
-  st.has_target = p.target_value != nullptr;
-  StepArgs P{};
+  const dcopf_solve_params& p = R.p;
+  R.st.has_target = R.it.target != nullptr;
+  StepArgs& P = R.P;
   P.rule = p.rule; P.as_printed = p.as_printed; P.alpha = p.alpha;
   P.alpha_lambda = p.alpha_lambda > 0 ? p.alpha_lambda : p.alpha;
   P.rho = p.rho; P.beta1 = p.beta1; P.beta2 = p.beta2; P.eps = p.eps; P.decay = p.decay;
@@ -766,108 +780,212 @@ dcopf_status solve_tensor(dcopf_dual* h, int B, const double* loads, const int* 
     return DCOPF_ERR_CUDA;
   if (cudaEventRecord(h->tev, s) != cudaSuccess || cudaStreamWaitEvent(cs, h->tev, 0) != cudaSuccess)
     return DCOPF_ERR_CUDA;
-  unsigned gi = std::min<unsigned>((unsigned)(((long long)B * nl + 255) / 256), 4096);
-  k_init_state_f32(gi, cs, B, nl, p.warm_start, lam, mh, ml, p.target_value, p.gap, st);
+  R.gi = std::min<unsigned>((unsigned)(((long long)B * nl + 255) / 256), 4096);
+  k_init_state_f32(R.gi, cs, B, nl, p.warm_start, R.it.lam, R.it.mh, R.it.ml, R.it.target, p.gap,
+                   R.st);
   k_bt_init<<<(B + 255) / 256, 256, 0, cs>>>(B, bb);
-  k_split_eta<float><<<B, 256, 0, cs>>>(nl, T.ld_l, st.mu_hi, st.mu_lo, outage, w.u32.as<float>(),
-                                        T.H_hi.as<__nv_bfloat16>(), T.H_lo.as<__nv_bfloat16>());
+  k_split_eta<float><<<B, 256, 0, cs>>>(nl, T.ld_l, R.st.mu_hi, R.st.mu_lo, R.it.outage,
+                                        w.u32.as<float>(), T.H_hi.as<__nv_bfloat16>(),
+                                        T.H_lo.as<__nv_bfloat16>());
   h->launches += 3;
-  int splits, kbps;
-  adjoint_split(h, B, &splits, &kbps);
-  GemmArgs ga{};
+  int kbps;
+  adjoint_split(h, B, &R.splits, &kbps);
+  GemmArgs& ga = R.ga;
   ga.M = B; ga.N = ng; ga.K = nl; ga.kb_per_split = kbps; ga.epi = EPI_PARTIAL;
   ga.P = T.P.as<float>(); ga.ldp = (ng + 3) & ~3; ga.err = h->d_err; ga.timeout_ns = 2000000000ull;
-  GemmArgs gf{};
+  GemmArgs& gf = R.gf;
   gf.M = B; gf.N = nl; gf.K = ng; gf.kb_per_split = (ng + GBK - 1) / GBK; gf.epi = EPI_TILE;
   gf.F32 = h->bb.F.as<float>(); gf.ldf32 = ldF;
   gf.err = h->d_err; gf.timeout_ns = 2000000000ull;
-  StepEpi E{};
-  E.P = to_float_args(P); E.F = gf.F32; E.ldF = ldF; E.f0 = w.f0_32.as<float>(); E.u = w.u32.as<float>(); E.outage = outage; E.tout = bb.tout;
-  E.fmax = h->dev.fmax32; E.fmin = h->dev.fmin32; E.iter = st.iter; E.frozen = bb.frozen;
+  StepEpi& E = R.E;
+  E.P = to_float_args(P); E.F = gf.F32; E.ldF = ldF; E.f0 = w.f0_32.as<float>(); E.u = w.u32.as<float>();
+  E.outage = R.it.outage; E.tout = bb.tout;
+  E.fmax = h->dev.fmax32; E.fmin = h->dev.fmin32; E.iter = R.st.iter; E.frozen = bb.frozen;
   E.stepf = bb.stepf;
-  E.mu_hi[0] = st.mu_hi; E.mu_hi[1] = bb.mu2_hi; E.mu_lo[0] = st.mu_lo; E.mu_lo[1] = bb.mu2_lo;
-  E.s1_hi = st.s1_hi; E.s2_hi = st.s2_hi; E.s1_lo = st.s1_lo; E.s2_lo = st.s2_lo;
+  E.mu_hi[0] = R.st.mu_hi; E.mu_hi[1] = bb.mu2_hi; E.mu_lo[0] = R.st.mu_lo; E.mu_lo[1] = bb.mu2_lo;
+  E.s1_hi = R.st.s1_hi; E.s2_hi = R.st.s2_hi; E.s1_lo = R.st.s1_lo; E.s2_lo = R.st.s2_lo;
   E.Hh = T.H_hi.as<__nv_bfloat16>(); E.Hl = T.H_lo.as<__nv_bfloat16>(); E.ldh = T.ld_l;
-  E.line_part = bb.line_part; E.out_part = bb.out_part; E.n_tiles = n_tiles;
-  const int chunk = std::max(16, p.check_every);
-  // capture `chunk` iterations in a CUDA graph
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  const long long launches_before_capture = h->launches;
-  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DCOPF_ERR_CUDA;
-  bool cap_ok = true;
-  for (int it = 0; it < chunk && cap_ok; ++it) {
-    cap_ok &= launch_gemm<3>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi, T.m_phit_lo, ga, splits, cs) == cudaSuccess;
-    k_bt_minimize<<<B, 256, 0, cs>>>(h->dev, splits, B, ga.ldp, T.P.as<float>(), st, bb, P, T.ld_g,
-                                     T.X_hi.as<__nv_bfloat16>(), T.X_lo.as<__nv_bfloat16>(), outage,
-                                     w.demand.as<double>());
-    cap_ok &= (h->host.qp ? launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, gf, 1, cs)
-                          : launch_gemm<2>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, gf, 1, cs)) ==
-              cudaSuccess;
-    k_bt_step<<<dim3(n_tiles, B), STEP_THREADS, 0, cs>>>(E, nl);
-    k_bt_finalize<<<(B + 3) / 4, 128, 0, cs>>>(B, T.ld_l, p.max_iters, p.tol, st, bb, outage,
-                                               w.demand.as<double>(), T.H_hi.as<__nv_bfloat16>(),
+  E.line_part = bb.line_part; E.out_part = bb.out_part; E.n_tiles = R.n_tiles;
+  return DCOPF_OK;
+}
+
+// Enqueues `chunk` iterations (adjoint GEMM, minimiser, forward GEMM, step, value) on
+// cs, which is capturing.
+static bool tensor_enqueue_chunk(TensorRun& R, int chunk, cudaStream_t cs) {
+  dcopf_dual* h = R.it.h;
+  const int B = R.it.B, nl = h->host.n_line;
+  TensorOps& T = h->tops;
+  Workspace& w = h->ws;
+  BatchView& bb = h->bb.v;
+  bool ok = true;
+  for (int it = 0; it < chunk && ok; ++it) {
+    ok &= launch_gemm<3>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi, T.m_phit_lo, R.ga, R.splits, cs) ==
+          cudaSuccess;
+    k_bt_minimize<<<B, 256, 0, cs>>>(h->dev, R.splits, B, R.ga.ldp, T.P.as<float>(), R.st, bb, R.P,
+                                     T.ld_g, T.X_hi.as<__nv_bfloat16>(), T.X_lo.as<__nv_bfloat16>(),
+                                     R.it.outage, w.demand.as<double>());
+    ok &= (h->host.qp ? launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, R.gf, 1, cs)
+                      : launch_gemm<2>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, R.gf, 1, cs)) ==
+          cudaSuccess;
+    k_bt_step<<<dim3(R.n_tiles, B), STEP_THREADS, 0, cs>>>(R.E, nl);
+    k_bt_finalize<<<(B + 3) / 4, 128, 0, cs>>>(B, T.ld_l, R.p.max_iters, R.p.tol, R.st, bb,
+                                               R.it.outage, w.demand.as<double>(),
+                                               T.H_hi.as<__nv_bfloat16>(),
                                                T.H_lo.as<__nv_bfloat16>());
   }
-  cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-  h->launches = launches_before_capture;  // counted per replay below
-  if (!cap_ok || ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    cudaGetLastError();
-    return DCOPF_ERR_CUDA;
-  }
-  const long long per_chunk = 5LL * chunk;
-  dcopf_status out = DCOPF_OK;
-  if (h->active.alloc(16) != cudaSuccess) out = DCOPF_ERR_OOM;
-  int* d_active = h->active.as<int>();
-  if (h->timing && !h->ev0) {
-    cudaEventCreate(&h->ev0);
-    cudaEventCreate(&h->ev1);
-  }
-  for (int round = 0; out == DCOPF_OK; ++round) {
-    if (h->timing) cudaEventRecord(h->ev0, cs);
-    if (cudaGraphLaunch(exec, cs) != cudaSuccess) { out = DCOPF_ERR_CUDA; break; }
-    h->launches += per_chunk;
-    if (h->timing) cudaEventRecord(h->ev1, cs);
-    k_bt_select<<<dim3((nl + 255) / 256, B), 256, 0, cs>>>(B, nl, st, bb);
-    if ((out = run_certify_t<float>(h, B, loads, outage, st.best_lam, st.best_hi, st.best_lo, st.cert,
-                                    nullptr, st.cand, st.done, cs)))
-      break;
-    cudaMemsetAsync(d_active, 0, sizeof(int), cs);
-    k_bt_accept<<<(B + 127) / 128, 128, 0, cs>>>(B, h->ub_any, st, bb, d_active);
-    h->launches += 2;
-    int active = 0;
-    if (cudaMemcpyAsync(&active, d_active, sizeof(int), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
-        cudaStreamSynchronize(cs) != cudaSuccess) {
-      out = DCOPF_ERR_CUDA;
-      break;
-    }
-    if (h->timing) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-      h->t_iter_ms += ms;
-      h->t_iter_launches += per_chunk;
-    }
-    int derr = 0;
-    cudaMemcpy(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (derr) { out = (dcopf_status)derr; break; }
-    if (active == 0) break;
-    if ((long long)round * chunk > 4LL * p.max_iters + 64) break;
-  }
-  cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
-  if (out != DCOPF_OK) return out;
-  k_output_f32(gi, cs, B, nl, st, lam, mh, ml, bound, iters, status);
+  return ok;
+}
+
+// After a chunk: stage the frozen candidates, certify them in FP64, then accept, stop
+// or resume each; adds the count of instances still running to *d_active.
+static dcopf_status tensor_post_round(TensorRun& R, int* d_active, cudaStream_t cs) {
+  dcopf_dual* h = R.it.h;
+  const int B = R.it.B, nl = h->host.n_line;
+  BatchView& bb = h->bb.v;
+  k_bt_select<<<dim3((nl + 255) / 256, B), 256, 0, cs>>>(B, nl, R.st, bb);
+  dcopf_status r = run_certify_t<float>(h, B, R.it.loads, R.it.outage, R.st.best_lam, R.st.best_hi,
+                                        R.st.best_lo, R.st.cert, nullptr, R.st.cand, R.st.done, cs);
+  if (r) return r;
+  k_bt_accept<<<(B + 127) / 128, 128, 0, cs>>>(B, h->ub_any, R.st, bb, d_active);
+  h->launches += 2;
+  return cudaGetLastError() == cudaSuccess ? DCOPF_OK : DCOPF_ERR_CUDA;
+}
+
+static dcopf_status tensor_finish(TensorRun& R, cudaStream_t s) {
+  dcopf_dual* h = R.it.h;
+  cudaStream_t cs = h->tstream;
+  k_output_f32(R.gi, cs, R.it.B, h->host.n_line, R.st, R.it.lam, R.it.mh, R.it.ml, R.it.bound,
+               R.it.iters, R.it.status);
   h->launches += 1;
   if (cudaEventRecord(h->tev, cs) != cudaSuccess || cudaStreamWaitEvent(s, h->tev, 0) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return DCOPF_ERR_CUDA;
   if (h->timing) {
-    std::vector<int> it(B);
-    cudaMemcpy(it.data(), st.iter, sizeof(int) * B, cudaMemcpyDeviceToHost);
-    for (int v : it) h->t_evals += v;
+    std::vector<int> its(R.it.B);
+    cudaMemcpy(its.data(), R.st.iter, sizeof(int) * R.it.B, cudaMemcpyDeviceToHost);
+    for (int v : its) h->t_evals += v;
   }
   return DCOPF_OK;
+}
+
+// Owns the CUDA objects of one group solve.
+struct GroupObjects {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> ev;
+  DBuf active;
+  ~GroupObjects() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
+// Batched solves of several networks (distinct handles on one device) that advance
+// together: each round is ONE launch of a CUDA graph holding every network's chunk
+// of iterations as parallel branches, followed by each network's FP64 certification.
+dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solve_params& p,
+                                cudaStream_t s) {
+  std::vector<TensorRun> runs(n);
+  for (int i = 0; i < n; ++i) {
+    runs[i].it = items[i];
+    runs[i].p = items[i].p ? *items[i].p : p;
+    dcopf_status r = tensor_setup(runs[i], s);
+    if (r) return r;
+  }
+  dcopf_dual* h0 = items[0].h;
+  cudaStream_t cs0 = h0->tstream;
+  const int chunk = std::max(16, p.check_every);
+  GroupObjects G;
+  G.ev.resize(2 * n + 1, nullptr);
+  for (auto& e : G.ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return DCOPF_ERR_CUDA;
+  if (G.active.alloc(sizeof(int) * (size_t)n) != cudaSuccess) return DCOPF_ERR_OOM;
+  int* d_active = G.active.as<int>();
+  // every stream starts after every setup
+  for (int i = 1; i < n; ++i) {
+    if (cudaEventRecord(G.ev[i], items[i].h->tstream) != cudaSuccess ||
+        cudaStreamWaitEvent(cs0, G.ev[i], 0) != cudaSuccess)
+      return DCOPF_ERR_CUDA;
+  }
+  std::vector<long long> before(n);
+  for (int i = 0; i < n; ++i) before[i] = items[i].h->launches;
+  if (cudaStreamBeginCapture(cs0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  bool cap_ok = cudaEventRecord(G.ev[0], cs0) == cudaSuccess;
+  for (int i = 1; i < n && cap_ok; ++i)
+    cap_ok = cudaStreamWaitEvent(items[i].h->tstream, G.ev[0], 0) == cudaSuccess;
+  for (int i = 0; i < n && cap_ok; ++i) cap_ok = tensor_enqueue_chunk(runs[i], chunk, items[i].h->tstream);
+  for (int i = 1; i < n && cap_ok; ++i)
+    cap_ok = cudaEventRecord(G.ev[n + i], items[i].h->tstream) == cudaSuccess &&
+             cudaStreamWaitEvent(cs0, G.ev[n + i], 0) == cudaSuccess;
+  cudaError_t ce = cudaStreamEndCapture(cs0, &G.graph);
+  for (int i = 0; i < n; ++i) items[i].h->launches = before[i];  // counted per replay below
+  if (!cap_ok || ce != cudaSuccess || cudaGraphInstantiate(&G.exec, G.graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return DCOPF_ERR_CUDA;
+  }
+  if (h0->timing && !h0->ev0) {
+    cudaEventCreate(&h0->ev0);
+    cudaEventCreate(&h0->ev1);
+  }
+  const long long per_chunk = 5LL * chunk;
+  long long max_iters = 0;
+  for (const TensorRun& R : runs) max_iters = std::max<long long>(max_iters, R.p.max_iters);
+  std::vector<int> act(n, 1);
+  for (int round = 0;; ++round) {
+    if (h0->timing) cudaEventRecord(h0->ev0, cs0);
+    if (cudaGraphLaunch(G.exec, cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
+    for (int i = 0; i < n; ++i) items[i].h->launches += per_chunk;
+    if (h0->timing) cudaEventRecord(h0->ev1, cs0);
+    if (cudaMemsetAsync(d_active, 0, sizeof(int) * (size_t)n, cs0) != cudaSuccess ||
+        cudaEventRecord(G.ev[2 * n], cs0) != cudaSuccess)
+      return DCOPF_ERR_CUDA;
+    for (int i = 0; i < n; ++i) {
+      cudaStream_t si = items[i].h->tstream;
+      if (i > 0 && cudaStreamWaitEvent(si, G.ev[2 * n], 0) != cudaSuccess) return DCOPF_ERR_CUDA;
+      if (!act[i]) continue;
+      dcopf_status r = tensor_post_round(runs[i], d_active + i, si);
+      if (r) return r;
+    }
+    for (int i = 1; i < n; ++i)
+      if (cudaEventRecord(G.ev[n + i], items[i].h->tstream) != cudaSuccess ||
+          cudaStreamWaitEvent(cs0, G.ev[n + i], 0) != cudaSuccess)
+        return DCOPF_ERR_CUDA;
+    if (cudaMemcpyAsync(act.data(), d_active, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, cs0) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(cs0) != cudaSuccess)
+      return DCOPF_ERR_CUDA;
+    if (h0->timing) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, h0->ev0, h0->ev1);
+      h0->t_iter_ms += ms;
+      h0->t_iter_launches += per_chunk * n;
+    }
+    int any = 0;
+    for (int i = 0; i < n; ++i) {
+      int derr = 0;
+      cudaMemcpy(&derr, items[i].h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+      if (derr) return (dcopf_status)derr;
+      any |= act[i];
+    }
+    if (!any) break;
+    if ((long long)round * chunk > 4LL * max_iters + 64) break;
+  }
+  for (int i = 0; i < n; ++i) {
+    dcopf_status r = tensor_finish(runs[i], s);
+    if (r) return r;
+  }
+  return DCOPF_OK;
+}
+
+template <typename S>
+dcopf_status solve_tensor(dcopf_dual* h, int B, const double* loads, const int* outage,
+                          const dcopf_solve_params& p, double* lam, double* mh, double* ml,
+                          double* bound, int* iters, int* status, cudaStream_t s) {
+  static_assert(sizeof(S) == 4, "the tensor-core solve keeps FP32 state");
+  TensorItem it{h, nullptr, B, loads, outage, p.target_value, lam, mh, ml, bound, iters, status};
+  return solve_tensor_group(&it, 1, p, s);
 }
 
 template dcopf_status solve_tensor<float>(dcopf_dual*, int, const double*, const int*,

@@ -205,6 +205,19 @@ template <typename S>
 dcopf_status solve_tensor(dcopf_dual* h, int batch, const double* loads, const int* outage,
                           const dcopf_solve_params& p, double* lam, double* mh, double* ml,
                           double* bound, int* iters, int* status, cudaStream_t s);
+// One network's instances in a group of batched solves (dcopf_dual_solve_group).
+struct TensorItem {
+  dcopf_dual* h;
+  const dcopf_solve_params* p;  // this network's settings (nullptr: the group's)
+  int B;
+  const double* loads;
+  const int* outage;
+  const double* target;
+  double *lam, *mh, *ml, *bound;
+  int *iters, *status;
+};
+dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solve_params& p,
+                                cudaStream_t s);
 dcopf_status run_eval_tensor(dcopf_dual* h, int batch, const int* outage, const double* lambda,
                              const double* mh, const double* ml, double* value, double* glam,
                              double* ghi, double* glo, double* dispatch, cudaStream_t s);

@@ -170,12 +170,23 @@ class DcopfDual:
                                                      self._stream()), "dcopf_dual_certify_bound")
         return bound, err
 
-    def solve(self, loads, outage=None, rule="adam", precision="fp32", path="auto",
-              max_iters=5000, alpha=1000.0, alpha_lambda=0.0, rho=0.9, beta1=0.9, beta2=0.999,
-              eps=1e-8, decay=1.0, gap=1e-3, tol=0.0, target=None, warm=None,
-              as_printed=False, check_every=1) -> SolveResult:
-        """``dcopf_dual_solve_batch``.  ``target`` ([B] optimal costs) enables the
-        certified-gap stop; ``warm`` = (lambda, mu_hi, mu_lo) warm start."""
+    def _params(self, rule, precision, path, max_iters, alpha, alpha_lambda, rho, beta1, beta2, eps,
+                decay, gap, tol, as_printed, check_every, warm=False):
+        p = _lib.SolveParams()
+        self.lib.dcopf_solve_params_default(C.byref(p))
+        p.rule = _lib.RULE[rule]
+        p.precision = _lib.PRECISION[precision]
+        p.path = _lib.PATH[path]
+        p.max_iters = int(max_iters)
+        p.warm_start = 1 if warm else 0
+        p.as_printed = 1 if as_printed else 0
+        p.check_every = int(check_every)
+        p.alpha, p.alpha_lambda, p.rho = float(alpha), float(alpha_lambda), float(rho)
+        p.beta1, p.beta2, p.eps, p.decay = float(beta1), float(beta2), float(eps), float(decay)
+        p.gap, p.tol = float(gap), float(tol)
+        return p
+
+    def _solve_arrays(self, loads, outage, target, warm):
         loads, out = self._batch_inputs(loads, outage)
         B = loads.shape[0]
         kw = dict(dtype=torch.float64, device=self.device)
@@ -187,27 +198,72 @@ class DcopfDual:
             lam = torch.zeros(B, **kw)
             mh = torch.zeros(B, self.n_line, **kw)
             ml = torch.zeros(B, self.n_line, **kw)
-        bound = torch.empty(B, **kw)
-        iters = torch.empty(B, dtype=torch.int32, device=self.device)
-        status = torch.empty(B, dtype=torch.int32, device=self.device)
         tgt = _as_dev(target, torch.float64, self.device)
         if tgt is not None:
             tgt = tgt.reshape(B)
-        p = _lib.SolveParams()
-        self.lib.dcopf_solve_params_default(C.byref(p))
-        p.rule = _lib.RULE[rule]
-        p.precision = _lib.PRECISION[precision]
-        p.path = _lib.PATH[path]
-        p.max_iters = int(max_iters)
-        p.warm_start = 1 if warm is not None else 0
-        p.as_printed = 1 if as_printed else 0
-        p.check_every = int(check_every)
-        p.alpha, p.alpha_lambda, p.rho = float(alpha), float(alpha_lambda), float(rho)
-        p.beta1, p.beta2, p.eps, p.decay = float(beta1), float(beta2), float(eps), float(decay)
-        p.gap, p.tol = float(gap), float(tol)
+        res = SolveResult(lam, mh, ml, torch.empty(B, **kw),
+                          torch.empty(B, dtype=torch.int32, device=self.device),
+                          torch.empty(B, dtype=torch.int32, device=self.device))
+        return loads, out, tgt, res
+
+    def solve(self, loads, outage=None, rule="adam", precision="fp32", path="auto",
+              max_iters=5000, alpha=1000.0, alpha_lambda=0.0, rho=0.9, beta1=0.9, beta2=0.999,
+              eps=1e-8, decay=1.0, gap=1e-3, tol=0.0, target=None, warm=None,
+              as_printed=False, check_every=1) -> SolveResult:
+        """``dcopf_dual_solve_batch``.  ``target`` ([B] optimal costs) enables the
+        certified-gap stop; ``warm`` = (lambda, mu_hi, mu_lo) warm start."""
+        loads, out, tgt, r = self._solve_arrays(loads, outage, target, warm)
+        p = self._params(rule, precision, path, max_iters, alpha, alpha_lambda, rho, beta1, beta2,
+                         eps, decay, gap, tol, as_printed, check_every, warm=warm is not None)
         p.target_value = None if tgt is None else tgt.data_ptr()
-        _lib.check(self.lib.dcopf_dual_solve_batch(self.h, B, _ptr(loads), _ptr(out), C.byref(p),
-                                                   _ptr(lam), _ptr(mh), _ptr(ml), _ptr(bound),
-                                                   _ptr(iters), _ptr(status), self._stream()),
+        _lib.check(self.lib.dcopf_dual_solve_batch(self.h, r.lam.shape[0], _ptr(loads), _ptr(out),
+                                                   C.byref(p), _ptr(r.lam), _ptr(r.mu_hi),
+                                                   _ptr(r.mu_lo), _ptr(r.bound), _ptr(r.iters),
+                                                   _ptr(r.status), self._stream()),
                    "dcopf_dual_solve_batch")
-        return SolveResult(lam, mh, ml, bound, iters, status)
+        return r
+
+
+_SOLVE_DEFAULTS = dict(rule="adam", precision="bf16x3", path="batched", max_iters=5000,
+                      alpha=1000.0, alpha_lambda=0.0, rho=0.9, beta1=0.9, beta2=0.999, eps=1e-8,
+                      decay=1.0, gap=1e-3, tol=0.0, as_printed=False, check_every=1)
+
+
+def solve_group(duals, loads, outage=None, target=None, warm=None, per_network=None,
+                **settings) -> list[SolveResult]:
+    """``dcopf_dual_solve_group``: batched solves of several networks (one ``DcopfDual``
+    each, distinct, on one device) advanced together, each round one CUDA-graph launch
+    over all of them.  ``loads``, ``outage``, ``target``, ``warm`` are per-network lists
+    (``None`` entries allowed); ``settings`` are the shared ascent settings (the keywords
+    of ``DcopfDual.solve``) and ``per_network`` an optional list of dicts overriding
+    them for one network."""
+    n = len(duals)
+    outage = outage or [None] * n
+    target = target or [None] * n
+    warm = warm or [None] * n
+    per_network = per_network or [None] * n
+    base = dict(_SOLVE_DEFAULTS, **settings)
+    keep, items, res = [], (_lib.GroupItem * n)(), []
+    for i, d in enumerate(duals):
+        ld, out, tgt, r = d._solve_arrays(loads[i], outage[i], target[i], warm[i])
+        keep += [ld, out, tgt]
+        it = items[i]
+        it.net = d.h.value
+        it.batch = r.lam.shape[0]
+        it.loads, it.outage = ld.data_ptr(), (None if out is None else out.data_ptr())
+        it.target_value = None if tgt is None else tgt.data_ptr()
+        it.lambda_, it.mu_hi, it.mu_lo = r.lam.data_ptr(), r.mu_hi.data_ptr(), r.mu_lo.data_ptr()
+        it.best_bound, it.iters, it.inst_status = (r.bound.data_ptr(), r.iters.data_ptr(),
+                                                   r.status.data_ptr())
+        if per_network[i]:
+            pi = d._params(**dict(base, **per_network[i]), warm=warm[i] is not None)
+            keep.append(pi)
+            it.params = C.cast(C.pointer(pi), C.c_void_p)
+        res.append(r)
+    d0 = duals[0]
+    if any((w is None) != (warm[0] is None) for w in warm):
+        raise ValueError("give a warm start for every network or for none")
+    p = d0._params(**base, warm=warm[0] is not None)
+    _lib.check(d0.lib.dcopf_dual_solve_group(n, items, C.byref(p), d0._stream()),
+               "dcopf_dual_solve_group")
+    return res
