@@ -12,6 +12,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <new>
 
 #include "dcopf_mlp.h"
@@ -35,21 +36,37 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
   return cdf + z * pdf;
 }
 
+__device__ __forceinline__ float epilogue(int epi, float v, int m, int n, const float* bias, float* Z,
+                                          int ldz) {
+  if (epi == EPI_BIAS || epi == EPI_BIAS_GELU) v += bias[n];
+  if (epi == EPI_BIAS_GELU) {
+    Z[(size_t)m * ldz + n] = v;
+    v = gelu_f(v);
+  }
+  if (epi == EPI_GELU_BACK) v *= gelu_grad_f(Z[(size_t)m * ldz + n]);
+  return v;
+}
+
 // C[M][N] = op(A)[M][K] op(B)[K][N] with the epilogue EPI.  op(A)(m, k) is
 // A[m*lda + k], or A[k*lda + m] when TA; op(B)(k, n) is B[k*ldb + n], or B[n*ldb + k]
 // when TB.  64 x 64 output tile per block, 16-deep K slices staged in shared memory,
-// a 4 x 4 register tile per thread (rows ty + 16i, columns tx + 16j).
+// a 4 x 4 register tile per thread (rows ty + 16i, columns tx + 16j).  Split K: block
+// z covers k in [z kper, (z+1) kper) and writes C + z czs (then EPI is EPI_STORE and
+// k_splitk_reduce finishes the sum in a fixed order).
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(GEMM_THREADS)
     k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda, const float* __restrict__ B,
             int ldb, float* __restrict__ C, int ldc, const float* __restrict__ bias,
-            float* __restrict__ Z, int ldz) {
+            float* __restrict__ Z, int ldz, int kper, size_t czs) {
   __shared__ float As[TBK][TBM + 1];
   __shared__ float Bs[TBK][TBN + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+  const int kbeg = blockIdx.z * kper;
+  const int kend = min(K, kbeg + kper);
+  C += blockIdx.z * czs;
   float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += TBK) {
+  for (int k0 = kbeg; k0 < kend; k0 += TBK) {
 #pragma unroll
     for (int e = 0; e < (TBM * TBK) / GEMM_THREADS; ++e) {
       const int q = tid + e * GEMM_THREADS;
@@ -57,7 +74,7 @@ __global__ void __launch_bounds__(GEMM_THREADS)
       if (TA) { m = q % TBM; k = q / TBM; } else { k = q % TBK; m = q / TBK; }
       const int gm = m0 + m, gk = k0 + k;
       float v = 0.f;
-      if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+      if (gm < M && gk < kend) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
       As[k][m] = v;
     }
 #pragma unroll
@@ -67,7 +84,7 @@ __global__ void __launch_bounds__(GEMM_THREADS)
       if (TB) { k = q % TBK; n = q / TBK; } else { n = q % TBN; k = q / TBN; }
       const int gn = n0 + n, gk = k0 + k;
       float v = 0.f;
-      if (gn < N && gk < K) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
+      if (gn < N && gk < kend) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
       Bs[k][n] = v;
     }
     __syncthreads();
@@ -93,15 +110,23 @@ __global__ void __launch_bounds__(GEMM_THREADS)
     for (int j = 0; j < 4; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= N) continue;
-      float v = acc[i][j];
-      if (EPI == EPI_BIAS || EPI == EPI_BIAS_GELU) v += bias[n];
-      if (EPI == EPI_BIAS_GELU) {
-        Z[(size_t)m * ldz + n] = v;
-        v = gelu_f(v);
-      }
-      if (EPI == EPI_GELU_BACK) v *= gelu_grad_f(Z[(size_t)m * ldz + n]);
-      C[(size_t)m * ldc + n] = v;
+      C[(size_t)m * ldc + n] = epilogue(EPI, acc[i][j], m, n, bias, Z, ldz);
     }
+  }
+}
+
+// C[m][n] = epilogue(sum over z = 0..S-1 of Pz[m][n]), slices S apart by M*N.
+template <int EPI>
+__global__ void k_splitk_reduce(int M, int N, int S, const float* __restrict__ Pz,
+                                float* __restrict__ C, int ldc, const float* __restrict__ bias,
+                                float* __restrict__ Z, int ldz) {
+  const size_t MN = (size_t)M * N;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN;
+       e += (size_t)gridDim.x * blockDim.x) {
+    float v = 0.f;
+    for (int z = 0; z < S; ++z) v += Pz[z * MN + e];
+    const int m = (int)(e / N), n = (int)(e - (size_t)m * N);
+    C[(size_t)m * ldc + n] = epilogue(EPI, v, m, n, bias, Z, ldz);
   }
 }
 
@@ -222,7 +247,9 @@ struct dcopf_mlp {
   int64_t P = 0, o_b1 = 0, o_W2 = 0, o_b2 = 0, o_W3 = 0, o_b3 = 0;
   int64_t adam_t = 0;
   int64_t launches = 0;
-  DBuf params, grad, mom1, mom2, norm, part, err;
+  int sm_count = 1;
+  size_t splitk_cap = 0;  // floats in `splitk`
+  DBuf params, grad, mom1, mom2, norm, part, err, splitk;
   DBuf Xn, Z1, H1, Z2, H2, U, dU, D1, D2;
   float* in_shift() const { return norm.as<float>(); }
   float* in_scale() const { return norm.as<float>() + n_in; }
@@ -233,13 +260,35 @@ struct dcopf_mlp {
 
 namespace {
 
+// One product with its epilogue.  When the output tiles cannot fill the SMs twice,
+// K is split into S slices (multiples of the K tile, at least 256 deep) written to the
+// split-K buffer and summed by k_splitk_reduce, which applies the epilogue.
 template <bool TA, bool TB, int EPI>
 void gemm(dcopf_mlp* h, cudaStream_t s, int M, int N, int K, const float* A, int lda,
           const float* B, int ldb, float* C, int ldc, const float* bias = nullptr,
           float* Z = nullptr, int ldz = 0) {
-  dim3 grid(cdiv(N, TBN), cdiv(M, TBM));
-  k_sgemm<TA, TB, EPI><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, ldz);
-  h->launches += 1;
+  const int tiles = cdiv(N, TBN) * cdiv(M, TBM);
+  int S = 1;
+  if (tiles < 2 * h->sm_count) {
+    S = std::min(cdiv(2 * h->sm_count, tiles), std::max(1, K / 256));
+    while (S > 1 && (size_t)S * M * N > h->splitk_cap) --S;
+  }
+  if (S <= 1) {
+    dim3 grid(cdiv(N, TBN), cdiv(M, TBM), 1);
+    k_sgemm<TA, TB, EPI><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, ldz,
+                                                       K, 0);
+    h->launches += 1;
+    return;
+  }
+  const int kper = cdiv(cdiv(K, S), TBK) * TBK;
+  S = cdiv(K, kper);
+  float* P = h->splitk.as<float>();
+  dim3 grid(cdiv(N, TBN), cdiv(M, TBM), S);
+  k_sgemm<TA, TB, EPI_STORE><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, P, N, nullptr,
+                                                           nullptr, 0, kper, (size_t)M * N);
+  const int rb = (int)std::min<int64_t>(cdiv((int64_t)M * N, 256), 8 * h->sm_count);
+  k_splitk_reduce<EPI><<<rb, 256, 0, s>>>(M, N, S, P, C, ldc, bias, Z, ldz);
+  h->launches += 2;
 }
 
 // Forward pass of the rows already normalised in Xn: Z1, H1, Z2, H2 and U (the
@@ -341,6 +390,13 @@ dcopf_status dcopf_mlp_create(const dcopf_mlp_desc* d, dcopf_mlp_t* out) {
             h->dU.alloc((size_t)mb * no * 4) == cudaSuccess;
   for (DBuf* b : {&h->Z1, &h->H1, &h->Z2, &h->H2, &h->D1, &h->D2})
     ok = ok && b->alloc((size_t)mb * nh * 4) == cudaSuccess;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    ok = false;
+  // split K only where tiles < 2 SMs: S * M * N < (2 SMs + tiles) * 64 * 64 <= 4 SMs * 4096
+  h->splitk_cap = (size_t)4 * h->sm_count * TBM * TBN;
+  ok = ok && h->splitk.alloc(h->splitk_cap * 4) == cudaSuccess;
   if (!ok) {
     delete h;
     cudaGetLastError();

@@ -95,6 +95,7 @@ struct GemmArgs {
   float* F32; int ldf32;  // EPI_TILE: raw accumulator, [M][ldf32]
   int* err;
   uint64_t timeout_ns;
+  const int* skip;       // nullable [M]: rows whose instance is frozen (a tile of them is skipped)
 };
 
 constexpr int GBM = 128, GBN = 128, GBK = 64;
@@ -134,6 +135,15 @@ __global__ void __launch_bounds__(192, 1)
   auto b_hi = [&](int s) { return a_hi(s) + (NPROD == 3 ? 2 : 1) * TILE_BYTES; };
   auto b_lo = [&](int s) { return b_hi(s) + TILE_BYTES; };
 
+  if (g.skip) {
+    // a tile whose instances are all frozen has nothing to compute: the kernels that
+    // read its output skip frozen instances too.  Decided before any barrier, TMA or
+    // TMEM work, by every thread alike.
+    int live = 0;
+    for (int r = threadIdx.x; r < GBM; r += blockDim.x)
+      live |= (m0 + r < g.M && !g.skip[m0 + r]) ? 1 : 0;
+    if (!__syncthreads_or(live)) return;
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       umma::mbar_init(&full[s], 1);
@@ -750,6 +760,91 @@ struct TensorRun {
   bool running = true;
 };
 
+// Initial state (cold or warm start), per-instance flags, and the BF16 split of the
+// first eta, on stream cs.
+static void tensor_init_state(TensorRun& R, cudaStream_t cs) {
+  dcopf_dual* h = R.it.h;
+  const int B = R.it.B, nl = h->host.n_line;
+  TensorOps& T = h->tops;
+  k_init_state_f32(R.gi, cs, B, nl, R.p.warm_start, R.it.lam, R.it.mh, R.it.ml, R.it.target, R.p.gap,
+                   R.st);
+  k_bt_init<<<(B + 255) / 256, 256, 0, cs>>>(B, h->bb.v);
+  k_split_eta<float><<<B, 256, 0, cs>>>(nl, T.ld_l, R.st.mu_hi, R.st.mu_lo, R.it.outage,
+                                        h->ws.u32.as<float>(), T.H_hi.as<__nv_bfloat16>(),
+                                        T.H_lo.as<__nv_bfloat16>());
+  h->launches += 3;
+}
+
+// Autotuner of the adjoint's split-K factor: more splits fill the SMs with CTAs but
+// add FP32 partial traffic to the minimiser's reduction.  Times the adjoint GEMM plus
+// the minimiser (the kernels the factor changes) for factors around the heuristic,
+// with CUDA events on the solve's stream, and keeps the fastest for this batch size.
+static dcopf_status tune_adjoint_split(TensorRun& R, cudaStream_t cs) {
+  dcopf_dual* h = R.it.h;
+  const int B = R.it.B;
+  TensorOps& T = h->tops;
+  Workspace& w = h->ws;
+  const int kb = (h->host.n_line + GBK - 1) / GBK;
+  const int s0 = R.splits;
+  std::vector<int> cand;
+  for (int num : {1, 2, 3, 4, 6, 8}) {
+    const int s = std::max(1, std::min(std::min(kb, 64), (s0 * num + 2) / 4));
+    const int per = (kb + s - 1) / s;
+    const int se = (kb + per - 1) / per;
+    if (std::find(cand.begin(), cand.end(), se) == cand.end()) cand.push_back(se);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return DCOPF_ERR_CUDA;
+  }
+  float best = 1e30f;
+  int best_s = s0, best_per = (kb + s0 - 1) / s0;
+  dcopf_status out = DCOPF_OK;
+  for (int se : cand) {
+    GemmArgs g = R.ga;
+    g.kb_per_split = (kb + se - 1) / se;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && out == DCOPF_OK; ++rep) {  // first pass warms up
+      if (cudaEventRecord(e0, cs) != cudaSuccess) { out = DCOPF_ERR_CUDA; break; }
+      for (int k = 0; k < 3; ++k) {
+        if (launch_gemm<3>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi, T.m_phit_lo, g, se, cs) != cudaSuccess) {
+          out = DCOPF_ERR_CUDA;
+          break;
+        }
+        k_bt_minimize<<<B, 256, 0, cs>>>(h->dev, se, B, g.ldp, T.P.as<float>(), R.st, h->bb.v, R.P,
+                                         T.ld_g, T.X_hi.as<__nv_bfloat16>(),
+                                         T.X_lo.as<__nv_bfloat16>(), R.it.outage,
+                                         w.demand.as<double>());
+        h->launches += 1;
+      }
+      if (out != DCOPF_OK || cudaEventRecord(e1, cs) != cudaSuccess ||
+          cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        out = DCOPF_ERR_CUDA;
+    }
+    if (out != DCOPF_OK) break;
+    if (ms < best) {
+      best = ms;
+      best_s = se;
+      best_per = g.kb_per_split;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (out != DCOPF_OK) return out;
+  int derr = 0;
+  if (cudaMemcpy(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  if (derr) return (dcopf_status)derr;
+  h->tune_B = B;
+  h->tune_splits = best_s;
+  h->tune_kbps = best_per;
+  if (h->verbose)
+    fprintf(stderr, "dcopf: batch %d adjoint split-K %d (heuristic %d), %.1f us per GEMM+min\n", B,
+            best_s, s0, 1e3f * best / 3.f);
+  return DCOPF_OK;
+}
+
 // Buffers, state initialisation and the iteration's kernel arguments; the work is
 // enqueued on the handle's internal stream, ordered after the caller's stream s.
 static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
@@ -781,13 +876,7 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   if (cudaEventRecord(h->tev, s) != cudaSuccess || cudaStreamWaitEvent(cs, h->tev, 0) != cudaSuccess)
     return DCOPF_ERR_CUDA;
   R.gi = std::min<unsigned>((unsigned)(((long long)B * nl + 255) / 256), 4096);
-  k_init_state_f32(R.gi, cs, B, nl, p.warm_start, R.it.lam, R.it.mh, R.it.ml, R.it.target, p.gap,
-                   R.st);
-  k_bt_init<<<(B + 255) / 256, 256, 0, cs>>>(B, bb);
-  k_split_eta<float><<<B, 256, 0, cs>>>(nl, T.ld_l, R.st.mu_hi, R.st.mu_lo, R.it.outage,
-                                        w.u32.as<float>(), T.H_hi.as<__nv_bfloat16>(),
-                                        T.H_lo.as<__nv_bfloat16>());
-  h->launches += 3;
+  tensor_init_state(R, cs);
   int kbps;
   adjoint_split(h, B, &R.splits, &kbps);
   GemmArgs& ga = R.ga;
@@ -806,6 +895,14 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   E.s1_hi = R.st.s1_hi; E.s2_hi = R.st.s2_hi; E.s1_lo = R.st.s1_lo; E.s2_lo = R.st.s2_lo;
   E.Hh = T.H_hi.as<__nv_bfloat16>(); E.Hl = T.H_lo.as<__nv_bfloat16>(); E.ldh = T.ld_l;
   E.line_part = bb.line_part; E.out_part = bb.out_part; E.n_tiles = R.n_tiles;
+  if (h->tune_B != B) {
+    if ((r = tune_adjoint_split(R, cs))) return r;
+    tensor_init_state(R, cs);  // the timed runs stepped lambda: start again
+  }
+  R.splits = h->tune_splits;
+  R.ga.kb_per_split = h->tune_kbps;
+  R.ga.skip = bb.frozen;
+  R.gf.skip = bb.frozen;
   return DCOPF_OK;
 }
 

@@ -137,6 +137,8 @@ struct dcopf_dual {
   int sm_count = 0;
   int fused_C = 0, fused_G = 0;  // cluster shape of the fused kernel (chosen on first use)
   int fused_coop = -1;           // -1 unknown, 1 cooperative+cluster launch accepted, 0 not
+  // split-K of the batched adjoint GEMM chosen by timing (for batch size tune_B)
+  int tune_B = 0, tune_splits = 0, tune_kbps = 0;
   size_t smem_optin = 0;
   bool verbose = false;
   std::string last_error;

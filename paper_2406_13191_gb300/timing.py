@@ -3,14 +3,19 @@
     python -m paper_2406_13191_gb300.timing batched --config 2 --batch 1024 --iters 16
     python -m paper_2406_13191_gb300.timing certify --config 1 --batch 1
     python -m paper_2406_13191_gb300.timing fused --config 1 --repeat 3
+    python -m paper_2406_13191_gb300.timing group --iters 400
 
 ``batched`` runs the tensor-core batched solve (BF16 hi/lo split products) for a
 fixed number of iterations and reports the time of the iteration kernels per batched
 iteration (CUDA events recorded by the library on its stream).  ``certify`` times the
 FP64 certificate and one FP64 evaluation.  ``fused`` times single-instance solves to
 the certified 0.1 % gap with the fused persistent kernel (needs the stored optimum of
-the 2000-bus instance, tests/golden/gamma.json).  These are measurements of the
-library, used for the kernel profiles; they are not the benchmark line.
+the 2000-bus instance, tests/golden/gamma.json).  ``group`` runs a mixed-size batch
+(1024 instances of a 300-bus network, 256 of the 2000-bus one, 128 of the 4600-bus one
+with line outages) for a fixed number of iterations, once network by network and once
+as one group solve (one CUDA-graph launch per round over all three).  These are
+measurements of the library, used for the kernel profiles; they are not the benchmark
+line.
 """
 from __future__ import annotations
 
@@ -22,7 +27,7 @@ import time
 import numpy as np
 import torch
 
-from . import DcopfDual, synth
+from . import DcopfDual, solve_group, synth
 
 
 def _seeded_point(rng, batch, n_line, density=0.1):
@@ -100,9 +105,43 @@ def fused(repeat):
                           us_per_iteration=1e3 * ms / max(1, evals))))
 
 
+def group(iters, repeat=3):
+    qp = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997)
+    lp = dict(rule="adam", alpha=1000.0, beta1=0.95, beta2=0.999, decay=0.997)
+    n300, b300 = synth.network_for(300)
+    w1 = synth.workload(1, batch=256)
+    w2 = synth.workload(2, batch=128)
+    items = [(n300, synth.scenario_loads(b300, 1024, 4301), None, qp), (w1.net, w1.loads, None, qp),
+             (w2.net, w2.loads, w2.outage, lp)]
+    duals = [DcopfDual(n) for n, _, _, _ in items]
+    common = dict(max_iters=iters, tol=0.0, precision="bf16x3", path="batched")
+
+    def seq():
+        return [d.solve(L, outage=o, **kw, **common) for d, (_, L, o, kw) in zip(duals, items)]
+
+    def grp():
+        return solve_group(duals, [L for _, L, _, _ in items], outage=[o for _, _, o, _ in items],
+                           per_network=[kw for *_, kw in items], **common)
+
+    res = dict(mode="group", iters=iters, networks=["300-bus QP x1024", "2000-bus QP x256",
+                                                    "4600-bus LP x128 (64 outages)"])
+    for name, fn in (("network_by_network", seq), ("group", grp)):
+        fn()
+        ts = []
+        for _ in range(repeat):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        res[f"{name}_ms"] = 1e3 * min(ts)
+    res["identical_bounds"] = all(torch.equal(a.bound, b.bound) for a, b in zip(seq(), grp()))
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("mode", choices=["batched", "certify", "fused"])
+    ap.add_argument("mode", choices=["batched", "certify", "fused", "group"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--iters", type=int, default=16)
@@ -112,6 +151,8 @@ def main():
         batched(a.config, a.batch, a.iters)
     elif a.mode == "certify":
         certify(a.config, a.batch)
+    elif a.mode == "group":
+        group(a.iters)
     else:
         fused(a.repeat)
 
