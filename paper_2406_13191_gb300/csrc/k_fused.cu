@@ -81,24 +81,6 @@ __device__ __forceinline__ S fused_rule(const StepArgs& P, S theta, S g, S& s1, 
   return theta;
 }
 
-// Sums two values over the block in one pass (fixed tree); every thread gets both.
-__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
-  a = warp_sum(a);
-  b = warp_sum(b);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-  __syncthreads();
-  if (l == 0) { sh[w] = a; sh[16 + w] = b; }
-  __syncthreads();
-  double x = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
-  double y = (threadIdx.x < nw) ? sh[16 + threadIdx.x] : 0.0;
-  if (w == 0) { x = warp_sum(x); y = warp_sum(y); }
-  if (threadIdx.x == 0) { sh[0] = x; sh[16] = y; }
-  __syncthreads();
-  a = sh[0];
-  b = sh[16];
-  __syncthreads();
-}
-
 __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cg::cluster_group cl = cg::this_cluster();
@@ -137,6 +119,10 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
         *fmx = row + 9 * rpc, *fmn = row + 10 * rpc, *f0 = row + 11 * rpc;
   float* phis = row + 12 * rpc;                  // [rpc][ng] when resident
   __shared__ double red[32];
+  __shared__ double rsh[256];   // line partials of the previous evaluation, one per CTA
+  __shared__ double s_dec[2];   // [0] value of the evaluation, [1] 1 if it improved the best
+  __shared__ double s_vbase;    // cost + lambda (sum p - D) of the pending evaluation
+  __shared__ int s_cand;        // stop decision of this loop (made by the last warp)
   __shared__ double s_lam[4];   // lam, s1, s2, lam at the pending evaluation
   __shared__ double s_cs[2];    // cost / dispatch sums of own slice (read by peers)
   __shared__ double s_csp[16];  // the cluster's cost / dispatch sums gathered
@@ -167,6 +153,8 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     s_pw[4] = pow(A.P.beta1, t0);
     s_pw[5] = pow(A.P.beta2, t0);
   }
+  // stop threshold of this launch (changed only between launches)
+  const double stop_at = st.has_target ? st.thresh[0] + st.margin[0] : INFINITY;
   double best = st.best[0];
   double prev_val = st.prev[0];
   int t = st.iter[0];
@@ -249,12 +237,18 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
           }
         }
       }
+      if (pending && tid < G) rsh[tid] = rv;
       __syncthreads();
       const double lam = s_lam[0];
-      double cs = 0.0, ps = 0.0;
       // one thread per generator of the slice: sum the clusters in a fixed order
       // (identical in every cluster), then the closed-form minimiser; the w that
-      // cancels (ctil + sigma lambda + pi~) is formed in FP64
+      // cancels (ctil + sigma lambda + pi~) is formed in FP64.  The dispatch sum feeds
+      // the lambda gradient sum(p) - D, a small difference of large sums: FP64 all the
+      // way.  A generator's cost term only enters the in-loop value (which decides
+      // when to certify; the certificate is FP64): FP32 per thread and warp, FP64
+      // across warps (FP64 shuffles are slow on this part).
+      float csf = 0.f;
+      double psd = 0.0;
       for (int jj = tid; jj < nj; jj += blockDim.x) {
         const float4* tp = (const float4*)(tmp + jj * NCLp);
         float s = 0.f;
@@ -270,30 +264,63 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
         const double w = ct + sg * lam + (double)s;
         const float x = inner_x<float>((float)w, (float)mq);
         xsl[jj] = x;
-        const double xd = (double)x;
-        cs += (mq * xd + ct) * xd + gk[3 * SLp + jj];
-        ps += gk[4 * SLp + jj] + sg * xd;
+        csf += fmaf(fmaf((float)mq, x, (float)ct), x, (float)gk[3 * SLp + jj]);
+        psd += gk[4 * SLp + jj] + sg * (double)x;
       }
-      block_sum2(cs, ps, red);
-      if (tid == 0) { s_cs[0] = cs; s_cs[1] = ps; }
-      if (pending) {
-        const double lsum = block_sum(rv, red);
-        const double lamp = s_lam[3];
-        const double val = cost_t + lamp * (psum_t - A.demand) + lsum;
-        if (val > best) {
-          best = val; best_lam = lamp; best_iter = t;
-          for (int r = tid; r < nr; r += blockDim.x) { st.best_hi[r0 + r] = ph[r]; st.best_lo[r0 + r] = pl[r]; }
-        }
-        if (st.has_target && best >= st.thresh[0] + st.margin[0]) cand = 1;
-        if (t >= A.max_iters) cand = 2;
-        if (A.tol > 0.0 && t > 1 && fabs(val - prev_val) < A.tol) cand = 2;
-        prev_val = val;
-        pending = false;
-      }
+      csf = warp_sum(csf);
+      psd = warp_sum(psd);
+      if (lane == 0) { red[warp] = (double)csf; red[16 + warp] = psd; }
       const int gave_up = __syncthreads_or(ok ? 0 : 1);
-      if (tid == 0) s_flag = gave_up;
+      if (warp == 0) {
+        // the slice's cost and dispatch sums: FP64 tree over the warp partials (FP64
+        // latency is high on this part: a tree, not a chain)
+        double cs = lane < nw ? red[lane] : 0.0;
+        double ps = lane < nw ? red[16 + lane] : 0.0;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          cs += __shfl_xor_sync(0xffffffffu, cs, o);
+          ps += __shfl_xor_sync(0xffffffffu, ps, o);
+        }
+        if (lane == 0) {
+          s_cs[0] = cs;
+          s_cs[1] = ps;
+          s_flag = gave_up;
+        }
+      }
+      // Split cluster barrier: each thread's writes read by peers (x* of the slice,
+      // the slice's sums, the flag) are released by its arrive; the value of the
+      // previous evaluation and the stop decision are made by the last warp while the
+      // barrier completes and the others gather x*, and are read after the gather.
+      cl.barrier_arrive();
+      if (warp == nw - 1) {
+        // line partials of the previous evaluation (FP64, fixed order), the value, the
+        // best point and the stop decision, made once and broadcast
+        double lsum = 0.0;
+        if (pending) {
+          double l2 = 0.0;  // two chains: FP64 add latency is high on this part
+          int q = lane;
+          for (; q + 32 < G; q += 64) { lsum += rsh[q]; l2 += rsh[q + 32]; }
+          if (q < G) lsum += rsh[q];
+          lsum = warp_sum(lsum + l2);
+        }
+        if (lane == 0) {
+          int cd = cand;
+          double val = 0.0;
+          int imp = 0;
+          if (pending) {
+            val = s_vbase + lsum;
+            imp = val > best;
+            if ((imp ? val : best) >= stop_at) cd = 1;
+            if (t >= A.max_iters) cd = 2;
+            if (A.tol > 0.0 && t > 1 && fabs(val - prev_val) < A.tol) cd = 2;
+          }
+          s_dec[0] = val;
+          s_dec[1] = (double)imp;
+          s_cand = cd;
+        }
+      }
     }
-    cl.sync();
+    cl.barrier_wait();
     // ---------------- C: uniform exit decisions, gather x*, forward, supergradient, step
     {
       int any = 0;
@@ -304,10 +331,28 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
         break;  // uniform in the cluster
       }
     }
-    if (cand) break;  // uniform everywhere: every CTA assembled the same value
-    for (int j = tid; j < ng; j += blockDim.x) {
-      const int q = j / SL;
-      xs[j] = cl.map_shared_rank(xsl, q)[j - q * SL];
+    if (warp < nw - 1) {
+      // x* of all gens from the cluster's slices, by every warp but the last (busy with
+      // the value); the remote loads of a thread are all issued before its stores
+      const int nt = (nw - 1) * 32;
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = tid + u * nt;
+        if (j < ng) {
+          const int q = j / SL;
+          v[u] = cl.map_shared_rank(xsl, q)[j - q * SL];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = tid + u * nt;
+        if (j < ng) xs[j] = v[u];
+      }
+      for (int j = tid + 4 * nt; j < ng; j += nt) {
+        const int q = j / SL;
+        xs[j] = cl.map_shared_rank(xsl, q)[j - q * SL];
+      }
     }
     if (tid >= 32 && tid < 32 + C) {
       const double* o = cl.map_shared_rank(s_cs, tid - 32);
@@ -315,11 +360,23 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       s_csp[2 * (tid - 32) + 1] = o[1];
     }
     __syncthreads();
+    if (pending) {
+      const double val = s_dec[0];
+      if (s_dec[1] != 0.0) {
+        best = val; best_lam = s_lam[3]; best_iter = t;
+        for (int r = tid; r < nr; r += blockDim.x) { st.best_hi[r0 + r] = ph[r]; st.best_lo[r0 + r] = pl[r]; }
+      }
+      cand = s_cand;
+      prev_val = val;
+      pending = false;
+    }
+    if (cand) break;  // uniform everywhere: every CTA assembled the same value
     if (tid == 0) {
       double cs2 = 0.0, ps2 = 0.0;
       for (int q = 0; q < C; ++q) { cs2 += s_csp[2 * q]; ps2 += s_csp[2 * q + 1]; }
       red[0] = cs2;
       red[1] = ps2;
+    } else if (tid == 64) {
       // step-size factors of the next step from the running powers
       s_pw[0] = s_pw[3];
       s_pw[4] *= A.P.beta1;
@@ -362,6 +419,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       // of lambda in FP64
       double lam = s_lam[0];
       s_lam[3] = lam;
+      s_vbase = cost_t + lam * (psum_t - A.demand);  // the value without its line sum
       float s1 = (float)s_lam[1], s2 = (float)s_lam[2];
       const float al = (float)(A.P.alpha_lambda * s_pw[0]);
       const float gl = (float)(psum_t - A.demand);
@@ -369,11 +427,11 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       lam += (double)th;
       s_lam[0] = lam; s_lam[1] = s1; s_lam[2] = s2;
     }
-    double lacc = 0.0;
+    float lacc = 0.f;
     for (int r = tid; r < nr; r += blockDim.x) {
       float f = eta[r];
       float gh = f - fmx[r], gl = fmn[r] - f;
-      lacc += (double)mh[r] * (double)gh + (double)ml[r] * (double)gl;
+      lacc = fmaf(mh[r], gh, fmaf(ml[r], gl, lacc));
       ph[r] = mh[r];
       pl[r] = ml[r];
       float nh = fused_rule<float>(A.P, mh[r], gh, h1[r], h2[r], am, bc1, bc2);
@@ -381,10 +439,19 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       mh[r] = nh > 0.f ? nh : 0.f;
       ml[r] = nlo > 0.f ? nlo : 0.f;
     }
-    lacc = block_sum(lacc, red);
-    if (tid == 0) Rcur[c] = lacc;  // published by the fence before the next arrival
+    // the line partial: FP32 per thread and warp, FP64 across warps; published by
+    // the fence before the next arrival
+    lacc = warp_sum(lacc);
+    if (lane == 0) rsh[warp] = (double)lacc;  // rsh is free until the next phase B
     pending = true;
     __syncthreads();
+    if (tid == 0) {
+      // only the warps that own rows (row r belongs to thread r) contribute
+      const int nwr = min(nw, (nr + 31) >> 5);
+      double l = 0.0;
+      for (int q = 0; q < nwr; ++q) l += rsh[q];
+      Rcur[c] = l;
+    }
   }
   // ---------------- write back (resumable state); peers may still read our smem
   cl.sync();
