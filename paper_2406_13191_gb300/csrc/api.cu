@@ -221,6 +221,59 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
     CUDA_TRY(h, cudaEventCreate(&h->ev0));
     CUDA_TRY(h, cudaEventCreate(&h->ev1));
   }
+  if constexpr (sizeof(S) == 4) {
+    if (path == DCOPF_PATH_FUSED && h->fused_C == 0) {
+      // Autotuner of the fused kernel's cluster shape (once per handle): every shape
+      // the device keeps resident runs 40 iterations from the initial state, timed
+      // with CUDA events; the fastest per iteration is kept and the state restarts.
+      int Cs[4], Gs[4];
+      const int n = fused_candidates(h, Cs, Gs, 4);
+      if (n == 0) return DCOPF_ERR_UNSUPPORTED;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      CUDA_TRY(h, cudaEventCreate(&e0));
+      CUDA_TRY(h, cudaEventCreate(&e1));
+      float best = 1e30f;
+      int bi = 0;
+      for (int i = 0; i < n; ++i) {
+        h->fused_C = Cs[i];
+        h->fused_G = Gs[i];
+        float per = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+          k_init_state<S><<<g, 256, 0, s>>>(B, nl, p.warm_start, lam, mh, ml, p.target_value, p.gap, st);
+          h->launches += 1;
+          cudaEventRecord(e0, s);
+          dcopf_status rr = run_iters_fused(h, P, st, 40, 0.0, s);
+          cudaEventRecord(e1, s);
+          int done_iters = 0, derr = 0;
+          if (rr || cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaMemcpy(&done_iters, st.iter, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+              cudaMemcpy(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || derr) {
+            cudaMemset(h->d_err, 0, sizeof(int));
+            cudaGetLastError();
+            per = 1e30f;
+            break;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          per = std::min(per, ms / (float)std::max(1, done_iters));
+        }
+        if (h->verbose)
+          fprintf(stderr, "[dcopf] fused tuning: cluster %d x %d CTAs: %.2f us per iteration\n",
+                  Gs[i] / Cs[i], Cs[i], 1e3f * per);
+        if (per < best) {
+          best = per;
+          bi = i;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (!(best < 1e30f)) return DCOPF_ERR_UNSUPPORTED;
+      h->fused_C = Cs[bi];
+      h->fused_G = Gs[bi];
+      k_init_state<S><<<g, 256, 0, s>>>(B, nl, p.warm_start, lam, mh, ml, p.target_value, p.gap, st);
+      h->launches += 1;
+    }
+  }
   for (int round = 0;; ++round) {
     long long launches_before = h->launches;
     if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev0, s));

@@ -525,6 +525,21 @@ static cudaError_t fused_config(const dcopf_dual* h, int C, FusedShape* out) {
   return cudaErrorInvalidValue;
 }
 
+// Cluster shapes (C, G) with C >= 2 the device keeps resident for this network,
+// largest cluster first; returns how many were written.
+int fused_candidates(dcopf_dual* h, int* Cs, int* Gs, int cap) {
+  int n = 0;
+  for (int C : {8, 4, 2}) {
+    FusedShape sh;
+    if (n >= cap || fused_config(h, C, &sh) != cudaSuccess) continue;
+    Cs[n] = sh.C;
+    Gs[n] = sh.G;
+    ++n;
+  }
+  cudaGetLastError();
+  return n;
+}
+
 dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>& st, int max_iters,
                              double tol, cudaStream_t s) {
   const DevNet& N = h->dev;
