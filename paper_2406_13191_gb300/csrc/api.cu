@@ -293,8 +293,10 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
     CUDA_TRY(h, cudaMemsetAsync(d_active, 0, sizeof(int), s));
     k_accept<<<cdiv(B, 128), 128, 0, s>>>(B, ub_any, st, d_active);
     h->launches += 1;
-    int active = 0;
+    // the active count and the device error word, read back with one synchronisation
+    int active = 0, derr = 0;
     CUDA_TRY(h, cudaMemcpyAsync(&active, d_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaMemcpyAsync(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
     if (h->timing) {
       float ms = 0.f;
@@ -302,8 +304,6 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
       h->t_iter_ms += ms;
       h->t_iter_launches += iter_launches;
     }
-    int derr = 0;
-    CUDA_TRY(h, cudaMemcpy(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (derr) return (dcopf_status)derr;
     if (active == 0) break;
     if (round > 4 * (p.max_iters / chunk + 2) + 64) break;  // cannot happen unless stuck

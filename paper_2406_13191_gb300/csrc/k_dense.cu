@@ -21,9 +21,11 @@
 namespace dcopf {
 
 constexpr int DN_TILE = 128;    // buses per column tile of the H_a^T eta product
-constexpr int DN_SPLITS = 16;   // row splits of that product
+constexpr int DN_SPLITS = 64;   // row splits of that product
+constexpr int DN_TERM_CTAS = 16;  // CTAs per instance summing the certificate's terms
 
-// f0[b][i] = phim[i] - H_a[i,:] . d_b, demand[b] = sum d_b; a warp per (line, instance).
+// f0[b][i] = phim[i] - H_a[i,:] . d_b, demand[b] = sum d_b; a warp per (line, instance),
+// four FMA chains with their loads in flight (FP64 latency is high on this part).
 __global__ void k_dense_base_flows(int nb, int nl, const double* __restrict__ H,
                                    const double* __restrict__ phim, const double* __restrict__ loads,
                                    double* __restrict__ f0, float* __restrict__ f0_32,
@@ -40,9 +42,18 @@ __global__ void k_dense_base_flows(int nb, int nl, const double* __restrict__ H,
   }
   if (warp >= nl) return;
   const double* row = H + (size_t)warp * nb;
-  double s = 0.0;
-  for (int j = lane; j < nb; j += 32) s = fma(row[j], d[j], s);
-  s = warp_sum(s);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int j = lane;
+  for (; j + 96 < nb; j += 128) {
+    const double a0 = row[j], a1 = row[j + 32], a2 = row[j + 64], a3 = row[j + 96];
+    const double d0 = d[j], d1 = d[j + 32], d2 = d[j + 64], d3 = d[j + 96];
+    s0 = fma(a0, d0, s0);
+    s1 = fma(a1, d1, s1);
+    s2 = fma(a2, d2, s2);
+    s3 = fma(a3, d3, s3);
+  }
+  for (; j < nb; j += 32) s0 = fma(row[j], d[j], s0);
+  double s = warp_sum((s0 + s1) + (s2 + s3));
   if (lane == 0) {
     const size_t o = (size_t)b * nl + warp;
     const double v = phim[warp] - s;
@@ -73,20 +84,41 @@ __global__ void k_dense_prices(int nb, int nl, const double* __restrict__ H,
     eta_s[i - i0] = fmax((double)mh[i], 0.0) - fmax((double)ml[i], 0.0);
   __syncthreads();
   if (j >= nb) return;
-  double s0 = 0.0, s1 = 0.0;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int i = i0;
-  for (; i + 8 <= i1; i += 8) {  // eight rows in flight, two chains
+  for (; i + 8 <= i1; i += 8) {  // eight rows in flight, four chains
     double h[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) h[u] = H[(size_t)(i + u) * nb + j];
 #pragma unroll
-    for (int u = 0; u < 8; u += 2) {
+    for (int u = 0; u < 8; u += 4) {
       s0 = fma(h[u], eta_s[i + u - i0], s0);
       s1 = fma(h[u + 1], eta_s[i + u + 1 - i0], s1);
+      s2 = fma(h[u + 2], eta_s[i + u + 2 - i0], s2);
+      s3 = fma(h[u + 3], eta_s[i + u + 3 - i0], s3);
     }
   }
   for (; i < i1; ++i) s0 = fma(H[(size_t)i * nb + j], eta_s[i - i0], s0);
-  part[((size_t)b * DN_SPLITS + blockIdx.y) * nb + j] = s0 + s1;
+  part[((size_t)b * DN_SPLITS + blockIdx.y) * nb + j] = (s0 + s1) + (s2 + s3);
+}
+
+// z[b][j] = sum of the row-split partials (fixed order, four chains).
+__global__ void k_dense_zreduce(int nb, const double* __restrict__ part, double* __restrict__ z,
+                                const int* __restrict__ mask, const int* __restrict__ done) {
+  const int b = blockIdx.y;
+  if (mask && (mask[b] == 0 || (done && done[b]))) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const double* p = part + (size_t)b * DN_SPLITS * nb + j;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+  for (int q = 0; q < DN_SPLITS; q += 4) {
+    a[0] += p[(size_t)q * nb];
+    a[1] += p[(size_t)(q + 1) * nb];
+    a[2] += p[(size_t)(q + 2) * nb];
+    a[3] += p[(size_t)(q + 3) * nb];
+  }
+  z[(size_t)b * nb + j] = (a[0] + a[1]) + (a[2] + a[3]);
 }
 
 __device__ __forceinline__ double gamma_fp64_d(double m) {
@@ -94,61 +126,70 @@ __device__ __forceinline__ double gamma_fp64_d(double m) {
   return (m * u) / (1.0 - m * u);
 }
 
-// Certified bound from the bus prices: the same sum as k_certify (eq. (4) through nu).
+// The certificate's terms (eq. (4) through the bus prices, as in k_certify) split over
+// DN_TERM_CTAS blocks per instance: tpart[b][block] = (sum of terms, sum of |terms|).
+// Term t < n_gen: generator minimum; then n_bus bus terms; then n_line line terms.
 template <typename S>
-__global__ void k_dense_certify(DevNet N, const double* __restrict__ part,
-                                const double* __restrict__ loads, const double* __restrict__ lambda,
-                                const S* __restrict__ mu_hi, const S* __restrict__ mu_lo,
-                                double* __restrict__ bound, double* __restrict__ errb,
-                                const int* __restrict__ mask, const int* __restrict__ done) {
+__global__ void k_dense_terms(DevNet N, const double* __restrict__ z, const double* __restrict__ loads,
+                              const double* __restrict__ lambda, const S* __restrict__ mu_hi,
+                              const S* __restrict__ mu_lo, double* __restrict__ tpart,
+                              const int* __restrict__ mask, const int* __restrict__ done) {
   __shared__ double red[32];
-  const int b = blockIdx.x;
+  const int b = blockIdx.y;
   if (mask && (mask[b] == 0 || (done && done[b]))) return;
-  const int nb = N.n_bus, nl = N.n_line;
-  const double* pz = part + (size_t)b * DN_SPLITS * nb;
+  const int nb = N.n_bus, nl = N.n_line, ng = N.n_gen;
+  const double* zb = z + (size_t)b * nb;
   const double* d = loads + (size_t)b * nb;
   const S* mh = mu_hi + (size_t)b * nl;
   const S* ml = mu_lo + (size_t)b * nl;
   const double lam = lambda[b];
-  extern __shared__ double zs[];  // bus prices z = H_a^T eta, reduced once
-  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-    double z = 0.0;
-    for (int q0 = 0; q0 < DN_SPLITS; q0 += 8) {  // eight partials in flight
-      double p[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) p[u] = pz[(size_t)(q0 + u) * nb + j];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) z += p[u];
-    }
-    zs[j] = z;
-  }
-  __syncthreads();
-  auto z_at = [&](int j) { return zs[j]; };
+  const int nt = ng + nb + nl;
+  const int stride = gridDim.x * blockDim.x;
   double g = 0.0, A = 0.0;
-  for (int j = threadIdx.x; j < N.n_gen; j += blockDim.x) {
-    double p;
-    const double t = gen_min_value(lam + z_at(N.gen_bus[j]), N.cost_quad[j], N.cost_lin[j], N.S,
-                                   N.pmin[j], N.pmax[j], &p);
-    g += t;
-    A += fabs(t);
-  }
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    const double t = -(lam + z_at(i)) * d[i];
-    g += t;
-    A += fabs(t);
-  }
-  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
-    const double t = -fmax((double)mh[l], 0.0) * N.fmax[l] + fmax((double)ml[l], 0.0) * N.fmin[l];
-    g += t;
-    A += fabs(t);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
+    double v;
+    if (t < ng) {
+      double p;
+      v = gen_min_value(lam + zb[N.gen_bus[t]], N.cost_quad[t], N.cost_lin[t], N.S, N.pmin[t],
+                        N.pmax[t], &p);
+    } else if (t < ng + nb) {
+      const int i = t - ng;
+      v = -(lam + zb[i]) * d[i];
+    } else {
+      const int l = t - ng - nb;
+      v = -fmax((double)mh[l], 0.0) * N.fmax[l] + fmax((double)ml[l], 0.0) * N.fmin[l];
+    }
+    g += v;
+    A += fabs(v);
   }
   g = block_sum(g, red);
   A = block_sum(A, red);
   if (threadIdx.x == 0) {
-    const int n_terms = N.n_gen + nb + nl;
-    const double m = (double)((n_terms + blockDim.x - 1) / blockDim.x) + 6.0 + 8.0 + DN_SPLITS;
-    // (per-thread sums, the block tree, the roundings inside a term, and the row-split
-    // partials of the prices)
+    tpart[((size_t)b * DN_TERM_CTAS + blockIdx.x) * 2] = g;
+    tpart[((size_t)b * DN_TERM_CTAS + blockIdx.x) * 2 + 1] = A;
+  }
+}
+
+// bound[b] = sum of the blocks' terms minus the a-priori rounding bound; one warp per
+// instance (fixed order).
+__global__ void k_dense_final(int B, int n_terms, int threads, const double* __restrict__ tpart,
+                              double* __restrict__ bound, double* __restrict__ errb,
+                              const int* __restrict__ mask, const int* __restrict__ done) {
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (b >= B) return;
+  if (mask && (mask[b] == 0 || (done && done[b]))) return;
+  double g = 0.0, A = 0.0;
+  for (int q = lane; q < DN_TERM_CTAS; q += 32) {
+    g += tpart[((size_t)b * DN_TERM_CTAS + q) * 2];
+    A += tpart[((size_t)b * DN_TERM_CTAS + q) * 2 + 1];
+  }
+  g = warp_sum(g);
+  A = warp_sum(A);
+  if (lane == 0) {
+    // per-thread sums, the block tree, the block partials' tree, the few roundings
+    // inside a term, and the row-split partials of the prices
+    const int total = DN_TERM_CTAS * threads;
+    const double m = (double)((n_terms + total - 1) / total) + 8.0 + 5.0 + 6.0 + DN_SPLITS;
     const double e = gamma_fp64_d(m) * A;
     bound[b] = g - e;
     if (errb) errb[b] = e;
@@ -191,8 +232,7 @@ dcopf_status ensure_dense_ha(dcopf_dual* h) {
 // Whether the dense path applies: few instances, no outages, H_a of modest size.
 bool dense_path_applies(const dcopf_dual* h, int B, const int* outage) {
   const size_t bytes = (size_t)h->host.n_line * h->host.n_bus * sizeof(double);
-  const size_t zs = (size_t)h->host.n_bus * sizeof(double);
-  return outage == nullptr && B <= 8 && bytes <= ((size_t)2 << 30) && zs + 1024 <= h->smem_optin;
+  return outage == nullptr && B <= 8 && bytes <= ((size_t)2 << 30);
 }
 
 dcopf_status run_dense_base_flows(dcopf_dual* h, int B, const double* loads, cudaStream_t s) {
@@ -217,22 +257,31 @@ dcopf_status run_dense_certify(dcopf_dual* h, int B, const double* loads, const 
   dcopf_status r = ensure_dense_ha(h);
   if (r) return r;
   const int nb = h->host.n_bus, nl = h->host.n_line;
-  if (h->dense_part.alloc((size_t)std::max(B, 8) * DN_SPLITS * nb * sizeof(double)) != cudaSuccess)
+  const int Bc = std::max(B, 8);
+  // [Bc][DN_SPLITS][nb] partials, [Bc][nb] prices, [Bc][DN_TERM_CTAS][2] term sums
+  const size_t part_n = (size_t)Bc * DN_SPLITS * nb, z_n = (size_t)Bc * nb;
+  if (h->dense_part.alloc((part_n + z_n + (size_t)Bc * DN_TERM_CTAS * 2) * sizeof(double)) !=
+      cudaSuccess)
     return DCOPF_ERR_OOM;
-  dim3 grid((nb + DN_TILE - 1) / DN_TILE, DN_SPLITS, B);
+  double* part = h->dense_part.as<double>();
+  double* z = part + part_n;
+  double* tpart = z + z_n;
   const size_t eta_smem = (size_t)((nl + DN_SPLITS - 1) / DN_SPLITS) * sizeof(double);
-  const size_t z_smem = (size_t)nb * sizeof(double);
-  if (eta_smem > h->smem_optin || z_smem > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
-  if (cudaFuncSetAttribute(k_dense_prices<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)eta_smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_dense_certify<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)z_smem) != cudaSuccess)
+  if (eta_smem > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
+  if (eta_smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_dense_prices<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)eta_smem) != cudaSuccess)
     return DCOPF_ERR_CUDA;
-  k_dense_prices<S><<<grid, DN_TILE, eta_smem, s>>>(nb, nl, h->dense_ha.as<double>(), mh, ml,
-                                                    h->dense_part.as<double>(), mask, done);
-  k_dense_certify<S><<<B, 256, z_smem, s>>>(h->dev, h->dense_part.as<double>(), loads, lam, mh, ml,
-                                            bound, errb, mask, done);
-  h->launches += 2;
+  dim3 grid((nb + DN_TILE - 1) / DN_TILE, DN_SPLITS, B);
+  k_dense_prices<S><<<grid, DN_TILE, eta_smem, s>>>(nb, nl, h->dense_ha.as<double>(), mh, ml, part,
+                                                    mask, done);
+  k_dense_zreduce<<<dim3((nb + 127) / 128, B), 128, 0, s>>>(nb, part, z, mask, done);
+  const int threads = 256;
+  k_dense_terms<S><<<dim3(DN_TERM_CTAS, B), threads, 0, s>>>(h->dev, z, loads, lam, mh, ml, tpart,
+                                                              mask, done);
+  k_dense_final<<<(B + 3) / 4, 128, 0, s>>>(B, h->host.n_gen + nb + nl, threads, tpart, bound, errb,
+                                            mask, done);
+  h->launches += 4;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
   return DCOPF_OK;
