@@ -19,6 +19,7 @@ dcopf_dual::~dcopf_dual() {
   if (ev1) cudaEventDestroy(ev1);
   if (tev) cudaEventDestroy(tev);
   if (tstream) cudaStreamDestroy(tstream);
+  if (h_pinned) cudaFreeHost(h_pinned);
 }
 
 namespace dcopf {
@@ -274,6 +275,7 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
       h->launches += 1;
     }
   }
+  if (!h->h_pinned) CUDA_TRY(h, cudaMallocHost(&h->h_pinned, 4 * sizeof(int)));
   for (int round = 0;; ++round) {
     long long launches_before = h->launches;
     if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev0, s));
@@ -292,12 +294,17 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
     if (r) return r;
     CUDA_TRY(h, cudaMemsetAsync(d_active, 0, sizeof(int), s));
     k_accept<<<cdiv(B, 128), 128, 0, s>>>(B, ub_any, st, d_active);
-    h->launches += 1;
+    // the outputs of the best points so far, written every round: when this round
+    // finishes every instance (the usual case) nothing is left to do after the read
+    // back (the caller's lambda / mu arrays were read only by the initialisation)
+    k_output<S><<<std::min<unsigned>(cdiv((long long)B * nl, 256), 4096), 256, 0, s>>>(
+        B, nl, st, lam, mh, ml, bound, iters, status);
+    h->launches += 2;
     // the active count and the device error word, read back with one synchronisation
-    int active = 0, derr = 0;
-    CUDA_TRY(h, cudaMemcpyAsync(&active, d_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(h, cudaMemcpyAsync(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_pinned + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
+    const int active = h->h_pinned[0], derr = h->h_pinned[1];
     if (h->timing) {
       float ms = 0.f;
       CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
@@ -308,11 +315,7 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
     if (active == 0) break;
     if (round > 4 * (p.max_iters / chunk + 2) + 64) break;  // cannot happen unless stuck
   }
-  k_output<S><<<std::min<unsigned>(cdiv((long long)B * nl, 256), 4096), 256, 0, s>>>(
-      B, nl, st, lam, mh, ml, bound, iters, status);
-  h->launches += 1;
   CUDA_TRY(h, cudaGetLastError());
-  CUDA_TRY(h, cudaStreamSynchronize(s));
   if (h->timing) {
     std::vector<int> it(B);
     CUDA_TRY(h, cudaMemcpy(it.data(), st.iter, sizeof(int) * B, cudaMemcpyDeviceToHost));

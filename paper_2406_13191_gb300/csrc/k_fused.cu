@@ -566,9 +566,20 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
               best.rows_per_cta);
   }
   FusedShape sh;
-  if (fused_config(h, h->fused_C, &sh) != cudaSuccess || sh.G != h->fused_G) {
-    cudaGetLastError();
-    return DCOPF_ERR_UNSUPPORTED;
+  if (h->fshape_C == h->fused_C && h->fshape_G == h->fused_G) {
+    sh.C = h->fshape_C; sh.G = h->fshape_G; sh.smem = h->fshape_smem; sh.phi_in_smem = h->fshape_phi;
+    sh.rows_per_cta = h->fshape_rpc; sh.slice = h->fshape_slice;
+    // the attribute is per function: another handle may have lowered it since
+    if (cudaFuncSetAttribute(k_fused_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sh.smem) != cudaSuccess)
+      return DCOPF_ERR_CUDA;
+  } else {
+    if (fused_config(h, h->fused_C, &sh) != cudaSuccess || sh.G != h->fused_G) {
+      cudaGetLastError();
+      return DCOPF_ERR_UNSUPPORTED;
+    }
+    h->fshape_C = sh.C; h->fshape_G = sh.G; h->fshape_smem = sh.smem; h->fshape_phi = sh.phi_in_smem;
+    h->fshape_rpc = sh.rows_per_cta; h->fshape_slice = sh.slice;
   }
   const int G = sh.G, C = sh.C, NCL = G / C;
   const int NCLp = (NCL + 3) & ~3;

@@ -125,6 +125,7 @@ struct dcopf_dual {
   int* d_err = nullptr;  // sticky device error word
   unsigned* d_bar = nullptr;  // grid-barrier counters
   dcopf::DBuf active;  // one int: instances still running
+  int* h_pinned = nullptr;  // pinned host mirror: [0] active count, [1] device error word
   double ub_any = 0.0;
   cudaStream_t tstream = nullptr;  // internal stream of the graph-captured batched solve
   cudaEvent_t tev = nullptr;  // cost of the dearest dispatch (upper bound on any primal cost)
@@ -136,6 +137,9 @@ struct dcopf_dual {
   long long t_iter_launches = 0, t_evals = 0;
   int sm_count = 0;
   int fused_C = 0, fused_G = 0;  // cluster shape of the fused kernel (chosen on first use)
+  // layout of that shape, validated once (occupancy queries cost host time per solve)
+  int fshape_C = 0, fshape_G = 0, fshape_phi = 0, fshape_rpc = 0, fshape_slice = 0;
+  size_t fshape_smem = 0;
   int fused_coop = -1;           // -1 unknown, 1 cooperative+cluster launch accepted, 0 not
   // split-K of the batched adjoint GEMM chosen by timing (for batch size tune_B)
   int tune_B = 0, tune_splits = 0, tune_kbps = 0;

@@ -186,21 +186,37 @@ class DcopfDual:
         p.gap, p.tol = float(gap), float(tol)
         return p
 
-    def _solve_arrays(self, loads, outage, target, warm):
+    def new_result(self, batch: int) -> SolveResult:
+        """Output tensors for ``solve(..., out=...)`` (reusable across calls)."""
+        kw = dict(dtype=torch.float64, device=self.device)
+        return SolveResult(torch.empty(batch, **kw), torch.empty(batch, self.n_line, **kw),
+                           torch.empty(batch, self.n_line, **kw), torch.empty(batch, **kw),
+                           torch.empty(batch, dtype=torch.int32, device=self.device),
+                           torch.empty(batch, dtype=torch.int32, device=self.device))
+
+    def _solve_arrays(self, loads, outage, target, warm, res=None):
         loads, out = self._batch_inputs(loads, outage)
         B = loads.shape[0]
+        tgt = _as_dev(target, torch.float64, self.device)
+        if tgt is not None:
+            tgt = tgt.reshape(B)
+        if res is not None:
+            if res.lam.shape != (B,) or res.mu_hi.shape != (B, self.n_line) or res.lam.device != self.device:
+                raise ValueError("out= does not match the batch")
+            if warm is not None:
+                res.lam.copy_(_as_dev(warm[0], torch.float64, self.device).reshape(B))
+                res.mu_hi.copy_(_as_dev(warm[1], torch.float64, self.device).reshape(B, self.n_line))
+                res.mu_lo.copy_(_as_dev(warm[2], torch.float64, self.device).reshape(B, self.n_line))
+            return loads, out, tgt, res
         kw = dict(dtype=torch.float64, device=self.device)
         if warm is not None:
             lam = _as_dev(warm[0], torch.float64, self.device).reshape(B).clone()
             mh = _as_dev(warm[1], torch.float64, self.device).reshape(B, self.n_line).clone()
             ml = _as_dev(warm[2], torch.float64, self.device).reshape(B, self.n_line).clone()
-        else:
-            lam = torch.zeros(B, **kw)
-            mh = torch.zeros(B, self.n_line, **kw)
-            ml = torch.zeros(B, self.n_line, **kw)
-        tgt = _as_dev(target, torch.float64, self.device)
-        if tgt is not None:
-            tgt = tgt.reshape(B)
+        else:  # cold start: the library initialises the state and only writes these
+            lam = torch.empty(B, **kw)
+            mh = torch.empty(B, self.n_line, **kw)
+            ml = torch.empty(B, self.n_line, **kw)
         res = SolveResult(lam, mh, ml, torch.empty(B, **kw),
                           torch.empty(B, dtype=torch.int32, device=self.device),
                           torch.empty(B, dtype=torch.int32, device=self.device))
@@ -209,14 +225,15 @@ class DcopfDual:
     def solve(self, loads, outage=None, rule="adam", precision="fp32", path="auto",
               max_iters=5000, alpha=1000.0, alpha_lambda=0.0, rho=0.9, beta1=0.9, beta2=0.999,
               eps=1e-8, decay=1.0, gap=1e-3, tol=0.0, target=None, warm=None,
-              as_printed=False, check_every=1) -> SolveResult:
+              as_printed=False, check_every=1, out: SolveResult | None = None) -> SolveResult:
         """``dcopf_dual_solve_batch``.  ``target`` ([B] optimal costs) enables the
-        certified-gap stop; ``warm`` = (lambda, mu_hi, mu_lo) warm start."""
-        loads, out, tgt, r = self._solve_arrays(loads, outage, target, warm)
+        certified-gap stop; ``warm`` = (lambda, mu_hi, mu_lo) warm start; ``out`` (from
+        ``new_result``) receives the results instead of new tensors."""
+        loads, outg, tgt, r = self._solve_arrays(loads, outage, target, warm, out)
         p = self._params(rule, precision, path, max_iters, alpha, alpha_lambda, rho, beta1, beta2,
                          eps, decay, gap, tol, as_printed, check_every, warm=warm is not None)
         p.target_value = None if tgt is None else tgt.data_ptr()
-        _lib.check(self.lib.dcopf_dual_solve_batch(self.h, r.lam.shape[0], _ptr(loads), _ptr(out),
+        _lib.check(self.lib.dcopf_dual_solve_batch(self.h, r.lam.shape[0], _ptr(loads), _ptr(outg),
                                                    C.byref(p), _ptr(r.lam), _ptr(r.mu_hi),
                                                    _ptr(r.mu_lo), _ptr(r.bound), _ptr(r.iters),
                                                    _ptr(r.status), self._stream()),
