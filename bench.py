@@ -226,6 +226,68 @@ def warm_start_eval(n_train: int, epochs: int, n_eval: int) -> dict:
     return out
 
 
+def optimizer_study(max_iters: int = 3000) -> dict:
+    """Ascent rules of Section 3.3 on the study instances (512 training scenarios of the
+    2000-bus QP network; 256 instances of the 4600-bus LP batch, half with an outage):
+    iterations to the certified 0.1 % gap against the oracle's gamma* for grids of
+    heavy-ball GDM (Algorithm 1; also its printed double update), Adam and AdaGrad, with
+    and without step decay.  One batched solve per setting (tensor-core path)."""
+    import numpy as np
+    from paper_2406_13191_gb300 import DcopfDual, synth
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "study_gamma.json")))
+    n1, _ = synth.network_for(1)
+    w2 = synth.workload(2, batch=256)
+    sets = {"2000-bus QP": (n1, synth.warm_loads("train", 512), None, gold["2000"], 4000.0),
+            "4600-bus LP": (w2.net, w2.loads, w2.outage, gold["4600"], 1000.0)}
+    out = {"mode": "optimizer_study", "max_iters": max_iters, "gap": GAP, "sets": {}}
+    for name, (net, loads, outage, gam, a0) in sets.items():
+        ok = np.array([x is not None for x in gam])
+        L = loads[ok]
+        O = None if outage is None else outage[ok]
+        T = np.array([x for x in gam if x is not None])
+        g = DcopfDual(net)
+        grid = []
+        for a in (a0 / 4, a0 / 2, a0, 2 * a0):
+            for b1 in (0.5, 0.9, 0.95):
+                for b2 in (0.99, 0.999):
+                    for dec in (1.0, 0.999, 0.997, 0.99):
+                        grid.append(dict(rule="adam", alpha=a, beta1=b1, beta2=b2, decay=dec))
+        for a in (a0 / 4, a0, 4 * a0):
+            for dec in (1.0, 0.997):
+                grid.append(dict(rule="adagrad", alpha=a, decay=dec))
+        for a in (10.0, 30.0, 100.0):
+            for al in (0.1, 1.0):
+                for rho in (0.9, 0.99, 0.995):
+                    grid.append(dict(rule="gdm", alpha=a, alpha_lambda=al, rho=rho, decay=1.0))
+        rows = []
+        g.solve(L, outage=O, target=T, path="batched", precision="bf16x3", max_iters=64, **grid[0])
+        for kw in grid:
+            t = time.perf_counter()
+            r = g.solve(L, outage=O, target=T, path="batched", precision="bf16x3",
+                        max_iters=max_iters, **kw)
+            el = time.perf_counter() - t
+            st = r.status.cpu().numpy()
+            it = np.where(st == 0, r.iters.cpu().numpy(), max_iters)
+            b = r.bound.cpu().numpy()
+            rows.append(dict(kw, mean_iters=float(it.mean()), p90_iters=float(np.percentile(it, 90)),
+                             reached=float((st == 0).mean()), seconds=el,
+                             bounds_valid=bool(np.all(b <= T + 1e-9 * np.abs(T)))))
+        best = {}
+        for rule in ("adam", "adagrad", "gdm"):
+            rr = [x for x in rows if x["rule"] == rule]
+            best[rule] = min(rr, key=lambda x: (-x["reached"], x["mean_iters"]))
+        bg = best["gdm"]
+        kw = {k: bg[k] for k in ("alpha", "alpha_lambda", "rho", "decay")}
+        r = g.solve(L, outage=O, target=T, path="batched", precision="bf16x3", max_iters=max_iters,
+                    rule="gdm", as_printed=True, **kw)
+        st = r.status.cpu().numpy()
+        it = np.where(st == 0, r.iters.cpu().numpy(), max_iters)
+        best["gdm_as_printed"] = dict(rule="gdm", as_printed=True, **kw, mean_iters=float(it.mean()),
+                                      reached=float((st == 0).mean()))
+        out["sets"][name] = {"instances": int(ok.sum()), "best": best, "all": rows}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -241,7 +303,12 @@ def main():
     ap.add_argument("--n-train", type=int, default=50000)
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--n-eval", type=int, default=4096)
+    ap.add_argument("--optimizer-study", action="store_true",
+                    help="sweep the ascent rules on the study instances (prints its own JSON)")
     a = ap.parse_args()
+    if a.optimizer_study:
+        print(json.dumps(optimizer_study()))
+        return
     if a.warm_start_eval:
         print(json.dumps(warm_start_eval(a.n_train, a.epochs, a.n_eval)))
         return

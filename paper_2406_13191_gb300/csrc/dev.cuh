@@ -23,6 +23,7 @@ struct DevNet {
   const double* diag;
   const int* fwd_rows; const int* fwd_lev; int n_fwd_lev;
   const int* bwd_rows; const int* bwd_lev; int n_bwd_lev;
+  const double* winv1;     // [nr] upper bound of B_r^{-1} 1 (entries >= 0: B_r is an M-matrix)
   // packed copy of the factor for shared-memory staging (nullptr when unavailable)
   const unsigned char* fac_blob; int fac_bytes;
   int off_diag, off_val, off_rptr, off_cptr, off_rcol, off_crow, off_cmap, off_frows, off_brows,
@@ -51,6 +52,30 @@ __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block maximum; `sh` needs blockDim.x/32 slots.  All threads receive the result.
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* sh) {
+  v = warp_max(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  T r = (threadIdx.x < nw) ? sh[threadIdx.x] : T(0);
+  if (w == 0) r = warp_max(r);
+  if (threadIdx.x == 0) sh[0] = r;
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
 }
 
 // Deterministic block sum (fixed tree); `sh` needs blockDim.x/32 slots.  All threads

@@ -12,6 +12,7 @@
 // built on first use from the same FP64 factor as Phi, so both paths evaluate the
 // same problem data.
 #include <algorithm>
+#include <cmath>
 #include <thread>
 #include <vector>
 
@@ -127,13 +128,18 @@ __device__ __forceinline__ double gamma_fp64_d(double m) {
 }
 
 // The certificate's terms (eq. (4) through the bus prices, as in k_certify) split over
-// DN_TERM_CTAS blocks per instance: tpart[b][block] = (sum of terms, sum of |terms|).
-// Term t < n_gen: generator minimum; then n_bus bus terms; then n_line line terms.
+// DN_TERM_CTAS blocks per instance: tpart[b][block] = (sum of terms, sum of |terms|,
+// K, max |eta|).  Term t < n_gen: generator minimum; then n_bus bus terms; then n_line
+// line terms.  K bounds how the rounding of the prices moves the terms: a generator
+// term is max(|pmin|, |pmax|)-Lipschitz in its bus price and a bus term |d_i|-Lipschitz,
+// and |z^_j - z_j| <= gamma_k max|eta| colabs_j, so the terms move by at most
+// gamma_k max|eta| K with K = sum_j max(|pmin_j|, |pmax_j|) colabs_bus(j) + sum_i |d_i| colabs_i.
 template <typename S>
 __global__ void k_dense_terms(DevNet N, const double* __restrict__ z, const double* __restrict__ loads,
                               const double* __restrict__ lambda, const S* __restrict__ mu_hi,
-                              const S* __restrict__ mu_lo, double* __restrict__ tpart,
-                              const int* __restrict__ mask, const int* __restrict__ done) {
+                              const S* __restrict__ mu_lo, const double* __restrict__ colabs,
+                              double* __restrict__ tpart, const int* __restrict__ mask,
+                              const int* __restrict__ done) {
   __shared__ double red[32];
   const int b = blockIdx.y;
   if (mask && (mask[b] == 0 || (done && done[b]))) return;
@@ -145,52 +151,76 @@ __global__ void k_dense_terms(DevNet N, const double* __restrict__ z, const doub
   const double lam = lambda[b];
   const int nt = ng + nb + nl;
   const int stride = gridDim.x * blockDim.x;
-  double g = 0.0, A = 0.0;
+  double g = 0.0, A = 0.0, K = 0.0, emax = 0.0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
     double v;
     if (t < ng) {
       double p;
-      v = gen_min_value(lam + zb[N.gen_bus[t]], N.cost_quad[t], N.cost_lin[t], N.S, N.pmin[t],
-                        N.pmax[t], &p);
+      const int bus = N.gen_bus[t];
+      v = gen_min_value(lam + zb[bus], N.cost_quad[t], N.cost_lin[t], N.S, N.pmin[t], N.pmax[t], &p);
+      K += fmax(fabs(N.pmin[t]), fabs(N.pmax[t])) * colabs[bus];
     } else if (t < ng + nb) {
       const int i = t - ng;
       v = -(lam + zb[i]) * d[i];
+      K += fabs(d[i]) * colabs[i];
     } else {
       const int l = t - ng - nb;
-      v = -fmax((double)mh[l], 0.0) * N.fmax[l] + fmax((double)ml[l], 0.0) * N.fmin[l];
+      const double eh = fmax((double)mh[l], 0.0), el = fmax((double)ml[l], 0.0);
+      v = -eh * N.fmax[l] + el * N.fmin[l];
+      emax = fmax(emax, fabs(eh - el));
     }
     g += v;
     A += fabs(v);
   }
   g = block_sum(g, red);
   A = block_sum(A, red);
+  K = block_sum(K, red);
+  emax = warp_max(emax);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    tpart[((size_t)b * DN_TERM_CTAS + blockIdx.x) * 2] = g;
-    tpart[((size_t)b * DN_TERM_CTAS + blockIdx.x) * 2 + 1] = A;
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) emax = fmax(emax, red[q]);
+    double* o = tpart + ((size_t)b * DN_TERM_CTAS + blockIdx.x) * 4;
+    o[0] = g;
+    o[1] = A;
+    o[2] = K;
+    o[3] = emax;
   }
 }
 
 // bound[b] = sum of the blocks' terms minus the a-priori rounding bound; one warp per
 // instance (fixed order).
-__global__ void k_dense_final(int B, int n_terms, int threads, const double* __restrict__ tpart,
+__global__ void k_dense_final(int B, int n_terms, int threads, int rows_per_split,
+                              const double* __restrict__ tpart,
                               double* __restrict__ bound, double* __restrict__ errb,
                               const int* __restrict__ mask, const int* __restrict__ done) {
   const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (b >= B) return;
   if (mask && (mask[b] == 0 || (done && done[b]))) return;
-  double g = 0.0, A = 0.0;
+  double g = 0.0, A = 0.0, K = 0.0, emax = 0.0;
   for (int q = lane; q < DN_TERM_CTAS; q += 32) {
-    g += tpart[((size_t)b * DN_TERM_CTAS + q) * 2];
-    A += tpart[((size_t)b * DN_TERM_CTAS + q) * 2 + 1];
+    const double* o = tpart + ((size_t)b * DN_TERM_CTAS + q) * 4;
+    g += o[0];
+    A += o[1];
+    K += o[2];
+    emax = fmax(emax, o[3]);
   }
   g = warp_sum(g);
   A = warp_sum(A);
+  K = warp_sum(K);
+  emax = warp_max(emax);
   if (lane == 0) {
-    // per-thread sums, the block tree, the block partials' tree, the few roundings
-    // inside a term, and the row-split partials of the prices
+    // summation: per-thread sums, the block tree, the block partials' tree, and the
+    // few roundings inside a term
     const int total = DN_TERM_CTAS * threads;
-    const double m = (double)((n_terms + total - 1) / total) + 8.0 + 5.0 + 6.0 + DN_SPLITS;
-    const double e = gamma_fp64_d(m) * A;
+    const double m = (double)((n_terms + total - 1) / total) + 8.0 + 5.0 + 6.0;
+    // prices: eta (1), the longest FMA chain of a row split (a quarter of its rows plus
+    // up to 7 tail rows), the split's 4-chain merge (2), the split sum's chains and merge
+    // (DN_SPLITS / 4 + 2); K is itself a rounded sum of non-negative terms (one more
+    // gamma of its length)
+    const double kz = 1.0 + (double)(rows_per_split / 4 + 8) + 2.0 + (double)(DN_SPLITS / 4 + 2);
+    const double ek = gamma_fp64_d(kz) * emax * K * (1.0 + gamma_fp64_d(m + kz));
+    const double e = gamma_fp64_d(m) * A + ek;
     bound[b] = g - e;
     if (errb) errb[b] = e;
   }
@@ -222,6 +252,15 @@ dcopf_status ensure_dense_ha(dcopf_dual* h) {
   for (unsigned t = 1; t < nt; ++t) th.emplace_back(worker, (int)t);
   worker(0);
   for (auto& t : th) t.join();
+  // column sums of |H_a| (rounded upward by a relative margin far above their rounding)
+  std::vector<double> colabs(nb, 0.0);
+  for (int l = 0; l < nl; ++l)
+    for (int j = 0; j < nb; ++j) colabs[j] += std::fabs(ha[(size_t)l * nb + j]);
+  for (double& c : colabs) c *= 1.0 + 1e-9;
+  if (h->dense_colabs.alloc(colabs.size() * sizeof(double)) != cudaSuccess ||
+      cudaMemcpy(h->dense_colabs.p, colabs.data(), colabs.size() * sizeof(double),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return DCOPF_ERR_OOM;
   if (h->dense_ha.alloc(ha.size() * sizeof(double)) != cudaSuccess) return DCOPF_ERR_OOM;
   if (cudaMemcpy(h->dense_ha.p, ha.data(), ha.size() * sizeof(double), cudaMemcpyHostToDevice) !=
       cudaSuccess)
@@ -260,7 +299,7 @@ dcopf_status run_dense_certify(dcopf_dual* h, int B, const double* loads, const 
   const int Bc = std::max(B, 8);
   // [Bc][DN_SPLITS][nb] partials, [Bc][nb] prices, [Bc][DN_TERM_CTAS][2] term sums
   const size_t part_n = (size_t)Bc * DN_SPLITS * nb, z_n = (size_t)Bc * nb;
-  if (h->dense_part.alloc((part_n + z_n + (size_t)Bc * DN_TERM_CTAS * 2) * sizeof(double)) !=
+  if (h->dense_part.alloc((part_n + z_n + (size_t)Bc * DN_TERM_CTAS * 4) * sizeof(double)) !=
       cudaSuccess)
     return DCOPF_ERR_OOM;
   double* part = h->dense_part.as<double>();
@@ -277,9 +316,10 @@ dcopf_status run_dense_certify(dcopf_dual* h, int B, const double* loads, const 
                                                     mask, done);
   k_dense_zreduce<<<dim3((nb + 127) / 128, B), 128, 0, s>>>(nb, part, z, mask, done);
   const int threads = 256;
-  k_dense_terms<S><<<dim3(DN_TERM_CTAS, B), threads, 0, s>>>(h->dev, z, loads, lam, mh, ml, tpart,
-                                                              mask, done);
-  k_dense_final<<<(B + 3) / 4, 128, 0, s>>>(B, h->host.n_gen + nb + nl, threads, tpart, bound, errb,
+  k_dense_terms<S><<<dim3(DN_TERM_CTAS, B), threads, 0, s>>>(
+      h->dev, z, loads, lam, mh, ml, h->dense_colabs.as<double>(), tpart, mask, done);
+  k_dense_final<<<(B + 3) / 4, 128, 0, s>>>(B, h->host.n_gen + nb + nl, threads,
+                                            (nl + DN_SPLITS - 1) / DN_SPLITS, tpart, bound, errb,
                                             mask, done);
   h->launches += 4;
   cudaError_t e = cudaGetLastError();

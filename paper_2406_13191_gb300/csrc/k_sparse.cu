@@ -224,8 +224,14 @@ __global__ void k_certify(DevNet N, const double* __restrict__ loads, const int*
   }
   __syncthreads();
   ldl_solve(N, pf, X);
+  // B'^{-1} 1 bound for the post-outage network (Sherman-Morrison on B_r^{-1} 1, its
+  // correction doubled as a margin over the rounding of W and denom): wq(q) =
+  // winv1[q] + corr |W[q]|
+  double corr = 0.0;
+  const double* Wv = nullptr;
   if (k >= 0) {
     double* W = X + N.nr;
+    Wv = W;
     for (int q = threadIdx.x; q < N.nr; q += blockDim.x) W[q] = 0.0;
     __syncthreads();
     const int a = N.line_from[k], c = N.line_to[k];
@@ -239,22 +245,58 @@ __global__ void k_certify(DevNet N, const double* __restrict__ loads, const int*
     // eta'_k = u^T eta = (z_a - z_c) / (1 - PTDF_kk); z' = z + eta'_k b_k W
     const double denom = 1.0 - N.line_b[k] * (theta_at(N, W, a) - theta_at(N, W, c));
     const double s = (theta_at(N, X, a) - theta_at(N, X, c)) / denom;
+    {
+      // winv1 carries a 1e-6 relative margin: widen |w_a - w_c| by it
+      const double wa = theta_at(N, N.winv1, a), wc = theta_at(N, N.winv1, c);
+      corr = 2.0 * N.line_b[k] * (fabs(wa - wc) + 2e-6 * (wa + wc)) / fabs(denom);
+    }
     __syncthreads();
     for (int q = threadIdx.x; q < N.nr; q += blockDim.x) X[q] += s * N.line_b[k] * W[q];
     __syncthreads();
   }
-  double g = 0.0, A = 0.0;
+  // Residual of the prices in the system they solve (the post-outage Laplacian B' and
+  // right-hand side when k >= 0), plus the rounding of its own evaluation:
+  // rmax >= |r - B' z^|_inf.  As B'^{-1} >= 0 elementwise, |z - z^| <= rmax B'^{-1} 1.
+  double rmax = 0.0;
+  for (int q = threadIdx.x; q < N.nr; q += blockDim.x) {
+    const int bus = N.bus_of_pos[q];
+    const double zi = X[q];
+    double r = 0.0, bz = 0.0, acc = 0.0;
+    int deg = 0;
+    for (int p = N.bus_line_ptr[bus]; p < N.bus_line_ptr[bus + 1]; ++p) {
+      const int l = N.bus_line_idx[p];
+      if (l == k) continue;
+      const double eta = fmax((double)mh[l], 0.0) - fmax((double)ml[l], 0.0);
+      const int o = N.line_from[l] == bus ? N.line_to[l] : N.line_from[l];
+      const double zo = theta_at(N, X, o);
+      r += N.bus_line_coef[p] * eta;
+      bz += N.line_b[l] * (zi - zo);
+      acc += fabs(N.bus_line_coef[p] * eta) + N.line_b[l] * (fabs(zi) + fabs(zo));
+      ++deg;
+    }
+    rmax = fmax(rmax, fabs(r - bz) + gamma_fp64(2.0 * deg + 6.0) * acc);
+  }
+  rmax = block_max(rmax, red);
+  auto wq = [&](int bus) {
+    const int q = N.pos_of_bus[bus];
+    return q < 0 ? 0.0 : N.winv1[q] + (Wv ? corr * fabs(Wv[q]) : 0.0);
+  };
+  // K: how far the terms can move per unit of price error (a generator term is
+  // max(|pmin|, |pmax|)-Lipschitz in its bus price, a bus term |d_i|-Lipschitz)
+  double g = 0.0, A = 0.0, K = 0.0;
   for (int j = threadIdx.x; j < N.n_gen; j += blockDim.x) {
     double nu = lam + theta_at(N, X, N.gen_bus[j]);
     double p;
     double t = gen_min_value(nu, N.cost_quad[j], N.cost_lin[j], N.S, N.pmin[j], N.pmax[j], &p);
     g += t;
     A += fabs(t);
+    K += fmax(fabs(N.pmin[j]), fabs(N.pmax[j])) * wq(N.gen_bus[j]);
   }
   for (int i = threadIdx.x; i < N.n_bus; i += blockDim.x) {
     double t = -(lam + theta_at(N, X, i)) * d[i];
     g += t;
     A += fabs(t);
+    K += fabs(d[i]) * wq(i);
   }
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
     if (l == k) continue;
@@ -264,11 +306,14 @@ __global__ void k_certify(DevNet N, const double* __restrict__ loads, const int*
   }
   g = block_sum(g, red);
   A = block_sum(A, red);
+  K = block_sum(K, red);
   if (threadIdx.x == 0) {
     int n_terms = N.n_gen + N.n_bus + nl;
     double m = (double)((n_terms + blockDim.x - 1) / blockDim.x) + 6.0 + 8.0;  // per-thread sums,
     // tree depth (<= 5 + 5), and the few roundings inside each term
-    double e = gamma_fp64(m) * A;
+    // summation bound, plus the prices' error through the terms (K is a rounded sum of
+    // non-negative terms: one more gamma of its length)
+    double e = gamma_fp64(m) * A + rmax * K * (1.0 + gamma_fp64(m + 4.0));
     bound[b] = g - e;
     if (errb) errb[b] = e;
   }

@@ -121,6 +121,7 @@ struct dcopf_dual {
   dcopf::StateBufs st32, st64;
   dcopf::TensorOps tops;
   dcopf::DBuf dense_ha, dense_part;  // dense FP64 PTDF [n_line][n_bus] (built on first use)
+  dcopf::DBuf dense_colabs;           // [n_bus] column sums of |H_a| (price rounding bound)
   dcopf::BatchBufs bb;
   int* d_err = nullptr;  // sticky device error word
   unsigned* d_bar = nullptr;  // grid-barrier counters

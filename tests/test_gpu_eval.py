@@ -114,8 +114,10 @@ def test_certify_matches_oracle_and_bounds(cases, name):
     for b in range(B):
         ref = dcopf.dual_value_prices(on, loads[b], lam[b], np.maximum(mh[b], 0), np.maximum(ml[b], 0))
         e = err[b].item()
-        assert 0 <= e <= 1e-9 * (1 + abs(ref))
+        assert 0 < e <= 1e-9 * (1 + abs(ref))
         assert abs(bound[b].item() + e - ref) <= 1e-11 * abs(ref)
+        # a lower bound of the value (up to the oracle's own FP64 rounding)
+        assert bound[b].item() <= ref + 1e-12 * abs(ref)
 
 
 def test_certify_outage_matches_rebuilt(cases):
@@ -136,6 +138,7 @@ def test_certify_outage_matches_rebuilt(cases):
         ref = dcopf.dual_value_prices(o, loads[b], lam[b], mh[b][keep] if k >= 0 else mh[b],
                                       ml[b][keep] if k >= 0 else ml[b])
         assert abs(bound[b].item() + err[b].item() - ref) <= 1e-10 * abs(ref)
+        assert 0 < err[b].item() and bound[b].item() <= ref + 1e-12 * abs(ref)
 
 
 def test_eval_rejects_bad_outages(cases):
