@@ -247,12 +247,12 @@ def optimizer_study(max_iters: int = 3000) -> dict:
         T = np.array([x for x in gam if x is not None])
         g = DcopfDual(net)
         grid = []
-        for a in (a0 / 4, a0 / 2, a0, 2 * a0):
-            for b1 in (0.5, 0.9, 0.95):
+        for a in (a0 / 4, a0 / 2, a0, 2 * a0, 4 * a0):
+            for b1 in (0.5, 0.9, 0.95, 0.98):
                 for b2 in (0.99, 0.999):
                     for dec in (1.0, 0.999, 0.997, 0.99):
                         grid.append(dict(rule="adam", alpha=a, beta1=b1, beta2=b2, decay=dec))
-        for a in (a0 / 4, a0, 4 * a0):
+        for a in (a0 / 4, a0, 4 * a0, 16 * a0, 64 * a0):
             for dec in (1.0, 0.997):
                 grid.append(dict(rule="adagrad", alpha=a, decay=dec))
         for a in (10.0, 30.0, 100.0):

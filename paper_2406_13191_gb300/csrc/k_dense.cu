@@ -45,13 +45,18 @@ __global__ void k_dense_base_flows(int nb, int nl, const double* __restrict__ H,
   const double* row = H + (size_t)warp * nb;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int j = lane;
-  for (; j + 96 < nb; j += 128) {
-    const double a0 = row[j], a1 = row[j + 32], a2 = row[j + 64], a3 = row[j + 96];
-    const double d0 = d[j], d1 = d[j + 32], d2 = d[j + 64], d3 = d[j + 96];
-    s0 = fma(a0, d0, s0);
-    s1 = fma(a1, d1, s1);
-    s2 = fma(a2, d2, s2);
-    s3 = fma(a3, d3, s3);
+  for (; j + 224 < nb; j += 256) {  // eight row loads in flight per lane
+    double a[8], e[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) { a[u] = row[j + 32 * u]; e[u] = d[j + 32 * u]; }
+    s0 = fma(a[0], e[0], s0);
+    s1 = fma(a[1], e[1], s1);
+    s2 = fma(a[2], e[2], s2);
+    s3 = fma(a[3], e[3], s3);
+    s0 = fma(a[4], e[4], s0);
+    s1 = fma(a[5], e[5], s1);
+    s2 = fma(a[6], e[6], s2);
+    s3 = fma(a[7], e[7], s3);
   }
   for (; j < nb; j += 32) s0 = fma(row[j], d[j], s0);
   double s = warp_sum((s0 + s1) + (s2 + s3));
@@ -104,22 +109,17 @@ __global__ void k_dense_prices(int nb, int nl, const double* __restrict__ H,
 }
 
 // z[b][j] = sum of the row-split partials (fixed order, four chains).
-__global__ void k_dense_zreduce(int nb, const double* __restrict__ part, double* __restrict__ z,
-                                const int* __restrict__ mask, const int* __restrict__ done) {
-  const int b = blockIdx.y;
-  if (mask && (mask[b] == 0 || (done && done[b]))) return;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nb) return;
-  const double* p = part + (size_t)b * DN_SPLITS * nb + j;
-  double a[4] = {0.0, 0.0, 0.0, 0.0};
+__device__ __forceinline__ double dense_z(const double* __restrict__ part_b, int nb, int j) {
+  const double* p = part_b + j;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
 #pragma unroll 4
   for (int q = 0; q < DN_SPLITS; q += 4) {
-    a[0] += p[(size_t)q * nb];
-    a[1] += p[(size_t)(q + 1) * nb];
-    a[2] += p[(size_t)(q + 2) * nb];
-    a[3] += p[(size_t)(q + 3) * nb];
+    a0 += p[(size_t)q * nb];
+    a1 += p[(size_t)(q + 1) * nb];
+    a2 += p[(size_t)(q + 2) * nb];
+    a3 += p[(size_t)(q + 3) * nb];
   }
-  z[(size_t)b * nb + j] = (a[0] + a[1]) + (a[2] + a[3]);
+  return (a0 + a1) + (a2 + a3);
 }
 
 __device__ __forceinline__ double gamma_fp64_d(double m) {
@@ -130,21 +130,28 @@ __device__ __forceinline__ double gamma_fp64_d(double m) {
 // The certificate's terms (eq. (4) through the bus prices, as in k_certify) split over
 // DN_TERM_CTAS blocks per instance: tpart[b][block] = (sum of terms, sum of |terms|,
 // K, max |eta|).  Term t < n_gen: generator minimum; then n_bus bus terms; then n_line
-// line terms.  K bounds how the rounding of the prices moves the terms: a generator
-// term is max(|pmin|, |pmax|)-Lipschitz in its bus price and a bus term |d_i|-Lipschitz,
-// and |z^_j - z_j| <= gamma_k max|eta| colabs_j, so the terms move by at most
+// line terms.  A term's bus price is summed from the row-split partials on demand.  K
+// bounds how the rounding of the prices moves the terms: a generator term is
+// max(|pmin|, |pmax|)-Lipschitz in its bus price and a bus term |d_i|-Lipschitz, and
+// |z^_j - z_j| <= gamma_k max|eta| colabs_j, so the terms move by at most
 // gamma_k max|eta| K with K = sum_j max(|pmin_j|, |pmax_j|) colabs_bus(j) + sum_i |d_i| colabs_i.
+// The last block of an instance to finish (arrival counter) adds the blocks' partials
+// in block order and writes the bound: the result does not depend on which block is
+// last.
 template <typename S>
-__global__ void k_dense_terms(DevNet N, const double* __restrict__ z, const double* __restrict__ loads,
-                              const double* __restrict__ lambda, const S* __restrict__ mu_hi,
-                              const S* __restrict__ mu_lo, const double* __restrict__ colabs,
-                              double* __restrict__ tpart, const int* __restrict__ mask,
-                              const int* __restrict__ done) {
+__global__ void k_dense_terms(DevNet N, const double* __restrict__ part,
+                              const double* __restrict__ loads, const double* __restrict__ lambda,
+                              const S* __restrict__ mu_hi, const S* __restrict__ mu_lo,
+                              const double* __restrict__ colabs, double* __restrict__ tpart,
+                              unsigned* __restrict__ arrive, int rows_per_split,
+                              double* __restrict__ bound, double* __restrict__ errb,
+                              const int* __restrict__ mask, const int* __restrict__ done) {
   __shared__ double red[32];
+  __shared__ int s_last;
   const int b = blockIdx.y;
   if (mask && (mask[b] == 0 || (done && done[b]))) return;
   const int nb = N.n_bus, nl = N.n_line, ng = N.n_gen;
-  const double* zb = z + (size_t)b * nb;
+  const double* pb = part + (size_t)b * DN_SPLITS * nb;
   const double* d = loads + (size_t)b * nb;
   const S* mh = mu_hi + (size_t)b * nl;
   const S* ml = mu_lo + (size_t)b * nl;
@@ -157,11 +164,13 @@ __global__ void k_dense_terms(DevNet N, const double* __restrict__ z, const doub
     if (t < ng) {
       double p;
       const int bus = N.gen_bus[t];
-      v = gen_min_value(lam + zb[bus], N.cost_quad[t], N.cost_lin[t], N.S, N.pmin[t], N.pmax[t], &p);
+      const double z = N.pos_of_bus[bus] < 0 ? 0.0 : dense_z(pb, nb, bus);
+      v = gen_min_value(lam + z, N.cost_quad[t], N.cost_lin[t], N.S, N.pmin[t], N.pmax[t], &p);
       K += fmax(fabs(N.pmin[t]), fabs(N.pmax[t])) * colabs[bus];
     } else if (t < ng + nb) {
       const int i = t - ng;
-      v = -(lam + zb[i]) * d[i];
+      const double z = N.pos_of_bus[i] < 0 ? 0.0 : dense_z(pb, nb, i);
+      v = -(lam + z) * d[i];
       K += fabs(d[i]) * colabs[i];
     } else {
       const int l = t - ng - nb;
@@ -175,55 +184,40 @@ __global__ void k_dense_terms(DevNet N, const double* __restrict__ z, const doub
   g = block_sum(g, red);
   A = block_sum(A, red);
   K = block_sum(K, red);
-  emax = warp_max(emax);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
-  __syncthreads();
+  emax = block_max(emax, red);
   if (threadIdx.x == 0) {
-    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) emax = fmax(emax, red[q]);
     double* o = tpart + ((size_t)b * DN_TERM_CTAS + blockIdx.x) * 4;
     o[0] = g;
     o[1] = A;
     o[2] = K;
     o[3] = emax;
+    __threadfence();
+    s_last = atomicAdd(arrive + b, 1u) == DN_TERM_CTAS - 1;
   }
-}
-
-// bound[b] = sum of the blocks' terms minus the a-priori rounding bound; one warp per
-// instance (fixed order).
-__global__ void k_dense_final(int B, int n_terms, int threads, int rows_per_split,
-                              const double* __restrict__ tpart,
-                              double* __restrict__ bound, double* __restrict__ errb,
-                              const int* __restrict__ mask, const int* __restrict__ done) {
-  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (b >= B) return;
-  if (mask && (mask[b] == 0 || (done && done[b]))) return;
-  double g = 0.0, A = 0.0, K = 0.0, emax = 0.0;
-  for (int q = lane; q < DN_TERM_CTAS; q += 32) {
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double gs = 0.0, As = 0.0, Ks = 0.0, em = 0.0;
+  for (int q = 0; q < DN_TERM_CTAS; ++q) {
     const double* o = tpart + ((size_t)b * DN_TERM_CTAS + q) * 4;
-    g += o[0];
-    A += o[1];
-    K += o[2];
-    emax = fmax(emax, o[3]);
+    gs += __ldcg(o);
+    As += __ldcg(o + 1);
+    Ks += __ldcg(o + 2);
+    em = fmax(em, __ldcg(o + 3));
   }
-  g = warp_sum(g);
-  A = warp_sum(A);
-  K = warp_sum(K);
-  emax = warp_max(emax);
-  if (lane == 0) {
-    // summation: per-thread sums, the block tree, the block partials' tree, and the
-    // few roundings inside a term
-    const int total = DN_TERM_CTAS * threads;
-    const double m = (double)((n_terms + total - 1) / total) + 8.0 + 5.0 + 6.0;
-    // prices: eta (1), the longest FMA chain of a row split (a quarter of its rows plus
-    // up to 7 tail rows), the split's 4-chain merge (2), the split sum's chains and merge
-    // (DN_SPLITS / 4 + 2); K is itself a rounded sum of non-negative terms (one more
-    // gamma of its length)
-    const double kz = 1.0 + (double)(rows_per_split / 4 + 8) + 2.0 + (double)(DN_SPLITS / 4 + 2);
-    const double ek = gamma_fp64_d(kz) * emax * K * (1.0 + gamma_fp64_d(m + kz));
-    const double e = gamma_fp64_d(m) * A + ek;
-    bound[b] = g - e;
-    if (errb) errb[b] = e;
-  }
+  arrive[b] = 0u;  // ready for the next certification
+  // summation: per-thread sums, the block tree, the blocks' sum, and the few
+  // roundings inside a term
+  const int total = DN_TERM_CTAS * blockDim.x;
+  const double m = (double)((nt + total - 1) / total) + 8.0 + (double)DN_TERM_CTAS + 6.0;
+  // prices: eta (1), the longest FMA chain of a row split (a quarter of its rows plus
+  // up to 7 tail rows), the split's 4-chain merge (2), the split sum's chains and merge
+  // (DN_SPLITS / 4 + 2); K is itself a rounded sum of non-negative terms (one more
+  // gamma of its length)
+  const double kz = 1.0 + (double)(rows_per_split / 4 + 8) + 2.0 + (double)(DN_SPLITS / 4 + 2);
+  const double e = gamma_fp64_d(m) * As + gamma_fp64_d(kz) * em * Ks * (1.0 + gamma_fp64_d(m + kz));
+  bound[b] = gs - e;
+  if (errb) errb[b] = e;
 }
 
 // ------------------------------------------------------------------ host side
@@ -297,14 +291,16 @@ dcopf_status run_dense_certify(dcopf_dual* h, int B, const double* loads, const 
   if (r) return r;
   const int nb = h->host.n_bus, nl = h->host.n_line;
   const int Bc = std::max(B, 8);
-  // [Bc][DN_SPLITS][nb] partials, [Bc][nb] prices, [Bc][DN_TERM_CTAS][2] term sums
-  const size_t part_n = (size_t)Bc * DN_SPLITS * nb, z_n = (size_t)Bc * nb;
-  if (h->dense_part.alloc((part_n + z_n + (size_t)Bc * DN_TERM_CTAS * 4) * sizeof(double)) !=
-      cudaSuccess)
-    return DCOPF_ERR_OOM;
+  // [Bc][DN_SPLITS][nb] partials, [Bc][DN_TERM_CTAS][4] term sums, [Bc] arrival counters
+  const size_t part_n = (size_t)Bc * DN_SPLITS * nb, tp_n = (size_t)Bc * DN_TERM_CTAS * 4;
+  const size_t need = (part_n + tp_n + (size_t)Bc) * sizeof(double);
+  if (h->dense_part.bytes < need) {
+    if (h->dense_part.alloc(need) != cudaSuccess) return DCOPF_ERR_OOM;
+    if (cudaMemset(h->dense_part.p, 0, need) != cudaSuccess) return DCOPF_ERR_CUDA;
+  }
   double* part = h->dense_part.as<double>();
-  double* z = part + part_n;
-  double* tpart = z + z_n;
+  double* tpart = part + part_n;
+  unsigned* arrive = (unsigned*)(tpart + tp_n);
   const size_t eta_smem = (size_t)((nl + DN_SPLITS - 1) / DN_SPLITS) * sizeof(double);
   if (eta_smem > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
   if (eta_smem > 48 * 1024 &&
@@ -314,14 +310,10 @@ dcopf_status run_dense_certify(dcopf_dual* h, int B, const double* loads, const 
   dim3 grid((nb + DN_TILE - 1) / DN_TILE, DN_SPLITS, B);
   k_dense_prices<S><<<grid, DN_TILE, eta_smem, s>>>(nb, nl, h->dense_ha.as<double>(), mh, ml, part,
                                                     mask, done);
-  k_dense_zreduce<<<dim3((nb + 127) / 128, B), 128, 0, s>>>(nb, part, z, mask, done);
-  const int threads = 256;
-  k_dense_terms<S><<<dim3(DN_TERM_CTAS, B), threads, 0, s>>>(
-      h->dev, z, loads, lam, mh, ml, h->dense_colabs.as<double>(), tpart, mask, done);
-  k_dense_final<<<(B + 3) / 4, 128, 0, s>>>(B, h->host.n_gen + nb + nl, threads,
-                                            (nl + DN_SPLITS - 1) / DN_SPLITS, tpart, bound, errb,
-                                            mask, done);
-  h->launches += 4;
+  k_dense_terms<S><<<dim3(DN_TERM_CTAS, B), 256, 0, s>>>(
+      h->dev, part, loads, lam, mh, ml, h->dense_colabs.as<double>(), tpart, arrive,
+      (nl + DN_SPLITS - 1) / DN_SPLITS, bound, errb, mask, done);
+  h->launches += 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
   return DCOPF_OK;
