@@ -138,7 +138,9 @@ void dcopf_solve_params_default(dcopf_solve_params* p);
  * outputs to the unit box (Appendix A1), uploads everything to the device and
  * returns a handle in *out.  Synchronises the device.  Errors: INVALID_ARG (null
  * pointers, sizes < 1, NaN/Inf, bad slack index), NETWORK (islanded network, b <= 0,
- * pmin > pmax, flow_min > flow_max), OOM, CUDA. */
+ * pmin > pmax, flow_min > flow_max), UNSUPPORTED (no lines: a single bus, whose dual
+ * has lambda alone and is solved by merit order; or sizes beyond the limits), OOM,
+ * CUDA. */
 dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_options* opt,
                                dcopf_dual_t* out);
 

@@ -124,6 +124,8 @@ dcopf_status build_host_net(const dcopf_network_desc* d, HostNet* H, std::string
     return fail(DCOPF_ERR_INVALID_ARG, "n_bus and n_gen must be >= 1, n_line >= 0");
   if (d->n_bus > (1 << 24) || d->n_line > (1 << 26) || d->n_gen > (1 << 24))
     return fail(DCOPF_ERR_UNSUPPORTED, "network too large");
+  if (d->n_line == 0)  // one bus: the dual has lambda only (merit order in closed form)
+    return fail(DCOPF_ERR_UNSUPPORTED, "a network without lines has no flow constraints to dualise");
   if (d->slack_bus < 0 || d->slack_bus >= d->n_bus)
     return fail(DCOPF_ERR_INVALID_ARG, "slack_bus out of range");
   if ((d->n_line > 0 && (!d->line_from || !d->line_to || !d->line_b || !d->flow_max)) ||

@@ -95,6 +95,9 @@ def _good():
                         line_b=np.array(d["line_b"][:2]), flow_max=np.array(d["flow_max"][:2]),
                         flow_min=np.array(d["flow_min"][:2])), 2),   # islanded
     (lambda d: d.update(base_mva=0.0), 1),
+    (lambda d: d.update(n_bus=1, line_from=np.zeros(0, np.int32), line_to=np.zeros(0, np.int32),
+                        line_b=np.zeros(0), flow_max=np.zeros(0), flow_min=np.zeros(0),
+                        gen_bus=np.zeros(len(d["gen_bus"]), np.int32)), 6),   # no lines
 ])
 def test_host_validation(mutate, expect):
     d = {k: (np.array(v, copy=True) if isinstance(v, np.ndarray) else v) for k, v in _good().items()}
