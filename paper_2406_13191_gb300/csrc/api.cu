@@ -192,6 +192,15 @@ void k_output_f32(unsigned grid, cudaStream_t s, int B, int nl, SolveState<float
   k_output<float><<<grid, 256, 0, s>>>(B, nl, st, lam, mh, ml, bound, iters, status);
 }
 
+// *out = sum of iters[0..B) (fixed order per thread, then a block tree)
+__global__ void k_sum_iters(int B, const int* __restrict__ iters, int* __restrict__ out) {
+  __shared__ long long sh[32];
+  long long s = 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) s += iters[b];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = (int)s;
+}
+
 template <typename S>
 dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* outage,
                         const dcopf_solve_params& p, int path, double* lam, double* mh, double* ml,
@@ -300,11 +309,16 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
     k_output<S><<<std::min<unsigned>(cdiv((long long)B * nl, 256), 4096), 256, 0, s>>>(
         B, nl, st, lam, mh, ml, bound, iters, status);
     h->launches += 2;
-    // the active count and the device error word, read back with one synchronisation
-    CUDA_TRY(h, cudaMemcpyAsync(h->h_pinned, d_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(h, cudaMemcpyAsync(h->h_pinned + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // the active count, the device error word (and, when timing, the evaluations so
+    // far), read back with one synchronisation
+    if (h->timing) {
+      k_sum_iters<<<1, 256, 0, s>>>(B, st.iter, d_active + 1);
+      h->launches += 1;
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_pinned, d_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_pinned + 2, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
-    const int active = h->h_pinned[0], derr = h->h_pinned[1];
+    const int active = h->h_pinned[0], derr = h->h_pinned[2];
     if (h->timing) {
       float ms = 0.f;
       CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
@@ -316,11 +330,7 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
     if (round > 4 * (p.max_iters / chunk + 2) + 64) break;  // cannot happen unless stuck
   }
   CUDA_TRY(h, cudaGetLastError());
-  if (h->timing) {
-    std::vector<int> it(B);
-    CUDA_TRY(h, cudaMemcpy(it.data(), st.iter, sizeof(int) * B, cudaMemcpyDeviceToHost));
-    for (int v : it) h->t_evals += v;
-  }
+  if (h->timing) h->t_evals += h->h_pinned[1];
   return DCOPF_OK;
 }
 

@@ -48,7 +48,7 @@ struct FusedArgs {
   StepArgs P;
   SolveState<float> st;
   const float* f0;               // [n_line]
-  double demand;
+  const double* demand;          // [1] total demand of the instance (device)
   float* Pc;                     // [2][n_gen][NCLp] cluster partial adjoints
   double* R;                     // [2][G] line partials of the dual value
   unsigned* cnt;                 // [8] arrival counters, one per cluster rank
@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   }
   // stop threshold of this launch (changed only between launches)
   const double stop_at = st.has_target ? st.thresh[0] + st.margin[0] : INFINITY;
+  const double demand = A.demand[0];
   double best = st.best[0];
   double prev_val = st.prev[0];
   int t = st.iter[0];
@@ -419,10 +420,10 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       // of lambda in FP64
       double lam = s_lam[0];
       s_lam[3] = lam;
-      s_vbase = cost_t + lam * (psum_t - A.demand);  // the value without its line sum
+      s_vbase = cost_t + lam * (psum_t - demand);  // the value without its line sum
       float s1 = (float)s_lam[1], s2 = (float)s_lam[2];
       const float al = (float)(A.P.alpha_lambda * s_pw[0]);
-      const float gl = (float)(psum_t - A.demand);
+      const float gl = (float)(psum_t - demand);
       const float th = fused_rule<float>(A.P, 0.f, gl, s1, s2, al, bc1, bc2);
       lam += (double)th;
       s_lam[0] = lam; s_lam[1] = s1; s_lam[2] = s2;
@@ -606,12 +607,7 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
   A.max_iters = max_iters;
   A.tol = tol;
   A.timeout_ns = 2000000000ull;
-  double demand = 0.0;
-  if (cudaMemcpyAsync(&demand, h->ws.demand.as<double>(), sizeof(double), cudaMemcpyDeviceToHost, s) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return DCOPF_ERR_CUDA;
-  A.demand = demand;
+  A.demand = h->ws.demand.as<double>();  // read on the device: no host round trip
   if (cudaMemsetAsync(A.cnt, 0, 256, s) != cudaSuccess) return DCOPF_ERR_CUDA;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(G);
