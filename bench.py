@@ -158,7 +158,7 @@ def cpu_baseline(target_s=10.0):
                       f"{statistics.mean(iters):.0f} iterations each, single thread)"}
 
 
-def warm_start_eval(n_train: int, epochs: int, n_eval: int) -> dict:
+def warm_start_eval(n_train: int, epochs: int, n_eval: int, keep_model: bool = False):
     """Learned warm start on the 2000-bus network: targets from the method's own batched
     solves of ``n_train`` training scenarios, GPU training, then cold vs warm solves of
     ``n_eval`` held-out scenarios to the certified 0.1 % gap against the oracle's gamma*."""
@@ -223,7 +223,7 @@ def warm_start_eval(n_train: int, epochs: int, n_eval: int) -> dict:
                      "settings": kw}
     out["iteration_ratio"] = out["warm"]["mean_iters"] / out["cold"]["mean_iters"]
     out["throughput_ratio"] = out["warm"]["instances_per_s"] / out["cold"]["instances_per_s"]
-    return out
+    return (out, m) if keep_model else out
 
 
 def optimizer_study(max_iters: int = 3000) -> dict:
@@ -431,9 +431,9 @@ def main():
             "frac": achieved / peaks["hbm_gbs"], "traffic": tr, "peak_source": which,
             "kernel": "k_fused_solve", "bytes_per_iteration": bytes_per_eval,
             "iterations_per_launch": evals_per_launch, "us_per_iteration": 1e3 * it_ms / max(1, evals)}
-    batched = None
+    batched = warm_single = None
     if a.batched_leg:
-        ws = warm_start_eval(8192, 30, 4096)
+        ws, mlp = warm_start_eval(8192, 30, 4096, keep_model=True)
         batched = {"workload": "4096 held-out load scenarios of the 2000-bus network, one batched "
                                "call (tensor-core BF16x3 path), certified 0.1 % gap vs gamma*",
                    "cold_instances_per_s": ws["cold"]["instances_per_s"],
@@ -444,6 +444,30 @@ def main():
                    "all_bounds_valid": ws["cold"]["all_bounds_valid"] and ws["warm"]["all_bounds_valid"],
                    "warm_start": "perceptron trained on the GPU on 8192 training scenarios "
                                  f"({ws['targets_s'] + ws['train_s']:.1f} s, not timed)"}
+        # the benchmark instance from the learned warm start: MLP inference, the warm-
+        # started fused solve and its FP64 certificate, all inside the timed region
+        wkw = dict(OURS, rule="adam", alpha=300.0, beta1=0.9, beta2=0.999, decay=0.997)
+        res_w = g.new_result(1)
+        for _ in range(a.warmup):
+            g.solve(loads, target=target, gap=GAP, warm=mlp.warm_start(loads), out=res_w, **wkw)
+        wt, wit, wb = [], [], []
+        for _ in range(a.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = g.solve(loads, target=target, gap=GAP, warm=mlp.warm_start(loads), out=res_w, **wkw)
+            e1.record(stream)
+            e1.synchronize()
+            wt.append(e0.elapsed_time(e1))
+            wit.append(r.iters[0].item())
+            wb.append(r.bound[0].item())
+            assert r.status[0].item() == 0 and r.bound[0].item() <= gam * (1 + 1e-12)
+        warm_single = {"value": len(wt) / (sum(wt) / 1e3), "unit": UNIT,
+                       "ms_per_step": statistics.mean(wt), "iterations": statistics.mean(wit),
+                       "certified_gap": (gam - statistics.mean(wb)) / gam,
+                       "settings": "adam alpha 300, beta1 0.9, beta2 0.999, decay 0.997",
+                       "timed": "perceptron inference + warm-started fused solve + FP64 certificate"}
     if rank != 0:
         return
     cb = cpu_baseline(a.cpu_seconds) if world == 1 else None
@@ -458,7 +482,7 @@ def main():
             "iterations": statistics.mean(iters), "certified_gap": (gam - statistics.mean(bounds)) / gam,
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb,
             "plain_fp64_gpu": plain, "speedup_vs_plain_fp64_gpu": value / plain["value"],
-            "batched_2000bus": batched,
+            "batched_2000bus": batched, "learned_warm_start_single": warm_single,
             "clocks": clk.summary()}
     print(json.dumps(line))
 
