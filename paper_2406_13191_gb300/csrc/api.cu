@@ -236,8 +236,8 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
       // Autotuner of the fused kernel's cluster shape (once per handle): every shape
       // the device keeps resident runs 40 iterations from the initial state, timed
       // with CUDA events; the fastest per iteration is kept and the state restarts.
-      int Cs[4], Gs[4];
-      const int n = fused_candidates(h, Cs, Gs, 4);
+      int Cs[9], Gs[9];
+      const int n = fused_candidates(h, Cs, Gs, 9);
       if (n == 0) return DCOPF_ERR_UNSUPPORTED;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       CUDA_TRY(h, cudaEventCreate(&e0));

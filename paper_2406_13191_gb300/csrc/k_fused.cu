@@ -488,9 +488,11 @@ static size_t fused_smem(int ng, int rpc, int C, int NCL, bool phi) {
   return f * sizeof(float) + 5 * (size_t)SLp * sizeof(double);
 }
 
-static cudaError_t fused_config(const dcopf_dual* h, int C, FusedShape* out) {
+// g_cap bounds the grid (fewer, larger CTAs: more rows each, fewer clusters to
+// exchange with).
+static cudaError_t fused_config(const dcopf_dual* h, int C, FusedShape* out, int g_cap = 1 << 30) {
   const int nl = h->dev.n_line, ng = h->dev.n_gen;
-  const int sms = std::min(h->sm_count, 256);  // R is read with one thread per CTA
+  const int sms = std::min(std::min(h->sm_count, 256), g_cap);  // R: one thread per CTA
   int G = (sms / C) * C;
   if (G < C) return cudaErrorInvalidValue;
   for (int pass = 0; pass < 2; ++pass) {
@@ -531,11 +533,17 @@ static cudaError_t fused_config(const dcopf_dual* h, int C, FusedShape* out) {
 int fused_candidates(dcopf_dual* h, int* Cs, int* Gs, int cap) {
   int n = 0;
   for (int C : {8, 4, 2}) {
-    FusedShape sh;
-    if (n >= cap || fused_config(h, C, &sh) != cudaSuccess) continue;
-    Cs[n] = sh.C;
-    Gs[n] = sh.G;
-    ++n;
+    for (int div : {1, 2, 4}) {  // all SMs, or a half / quarter of them with more rows each
+      FusedShape sh;
+      if (n >= cap || fused_config(h, C, &sh, std::max(C, h->sm_count / div)) != cudaSuccess)
+        continue;
+      bool dup = false;
+      for (int i = 0; i < n; ++i) dup |= Cs[i] == sh.C && Gs[i] == sh.G;
+      if (dup || (div > 1 && !sh.phi_in_smem)) continue;  // smaller grids only with Phi resident
+      Cs[n] = sh.C;
+      Gs[n] = sh.G;
+      ++n;
+    }
   }
   cudaGetLastError();
   return n;
@@ -575,7 +583,7 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
                              (int)sh.smem) != cudaSuccess)
       return DCOPF_ERR_CUDA;
   } else {
-    if (fused_config(h, h->fused_C, &sh) != cudaSuccess || sh.G != h->fused_G) {
+    if (fused_config(h, h->fused_C, &sh, h->fused_G) != cudaSuccess || sh.G != h->fused_G) {
       cudaGetLastError();
       return DCOPF_ERR_UNSUPPORTED;
     }
