@@ -63,23 +63,34 @@ struct FusedArgs {
   uint64_t timeout_ns;
 };
 
-template <typename S>
-__device__ __forceinline__ S fused_rule(const StepArgs& P, S theta, S g, S& s1, S& s2, S a, S bc1,
-                                        S bc2) {
-  if (P.rule == DCOPF_GDM) {
-    s1 = S(P.rho) * s1 + a * g;
+// The ascent rule's constants in FP32, converted once per launch (FP64 conversions and
+// arithmetic are slow on this part and every thread steps its lines each loop).
+struct RuleF {
+  int rule, as_printed;
+  float rho, beta1, beta2, omb1, omb2, eps;
+};
+__device__ __forceinline__ RuleF rule_f(const StepArgs& P) {
+  return RuleF{P.rule,           P.as_printed,           (float)P.rho,
+               (float)P.beta1,   (float)P.beta2,         1.0f - (float)P.beta1,
+               1.0f - (float)P.beta2, (float)P.eps};
+}
+__device__ __forceinline__ float fused_rule_f(const RuleF& R, float theta, float g, float& s1,
+                                              float& s2, float a, float bc1, float bc2) {
+  if (R.rule == DCOPF_GDM) {
+    s1 = R.rho * s1 + a * g;
     theta += s1;
-    if (P.as_printed) theta += a * g;
-  } else if (P.rule == DCOPF_ADAM) {
-    s1 = S(P.beta1) * s1 + (S(1) - S(P.beta1)) * g;
-    s2 = S(P.beta2) * s2 + (S(1) - S(P.beta2)) * g * g;
-    theta += a * (s1 / bc1) / (sqrt(s2 / bc2) + S(P.eps));
+    if (R.as_printed) theta += a * g;
+  } else if (R.rule == DCOPF_ADAM) {
+    s1 = R.beta1 * s1 + R.omb1 * g;
+    s2 = R.beta2 * s2 + R.omb2 * g * g;
+    theta += a * (s1 / bc1) / (sqrtf(s2 / bc2) + R.eps);
   } else {
     s1 += g * g;
-    theta += a * g / (sqrt(s1) + S(P.eps));
+    theta += a * g / (sqrtf(s1) + R.eps);
   }
   return theta;
 }
+
 
 __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -127,6 +138,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   __shared__ double s_cs[2];    // cost / dispatch sums of own slice (read by peers)
   __shared__ double s_csp[16];  // the cluster's cost / dispatch sums gathered
   __shared__ double s_pw[6];    // decay^(t-1), 1 - beta1^t, 1 - beta2^t; running powers
+  __shared__ float s_pwf[4];    // FP32 step factors: alpha decay^(t-1), bias corrections, alpha_lambda decay^(t-1)
   __shared__ int s_flag;        // this CTA gave up waiting (read by peers)
 
   const float* phi = A.phi_in_smem ? phis : (N.phi32 + (size_t)r0 * ng);
@@ -156,6 +168,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   // stop threshold of this launch (changed only between launches)
   const double stop_at = st.has_target ? st.thresh[0] + st.margin[0] : INFINITY;
   const double demand = A.demand[0];
+  const RuleF RF = rule_f(A.P);
   double best = st.best[0];
   double prev_val = st.prev[0];
   int t = st.iter[0];
@@ -378,13 +391,18 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       red[0] = cs2;
       red[1] = ps2;
     } else if (tid == 64) {
-      // step-size factors of the next step from the running powers
+      // step-size factors of the next step from the running powers (FP64), and their
+      // FP32 copies for every thread
       s_pw[0] = s_pw[3];
       s_pw[4] *= A.P.beta1;
       s_pw[5] *= A.P.beta2;
       s_pw[3] *= A.P.decay;
       s_pw[1] = 1.0 - s_pw[4];
       s_pw[2] = 1.0 - s_pw[5];
+      s_pwf[0] = (float)(A.P.alpha * s_pw[0]);
+      s_pwf[1] = (float)s_pw[1];
+      s_pwf[2] = (float)s_pw[2];
+      s_pwf[3] = (float)(A.P.alpha_lambda * s_pw[0]);
     }
     // forward on own rows: a warp per row, 3 rows of a warp in flight
     for (int rb = warp; rb < nr; rb += 3 * nw) {
@@ -412,9 +430,9 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     cost_t = red[0];
     psum_t = red[1];
     t += 1;
-    const float bc1 = (float)s_pw[1];
-    const float bc2 = (float)s_pw[2];
-    const float am = (float)(A.P.alpha * s_pw[0]);
+    const float bc1 = s_pwf[1];
+    const float bc2 = s_pwf[2];
+    const float am = s_pwf[0];
     if (tid == 32) {
       // lambda step, concurrent with the line steps: the direction in FP32, the update
       // of lambda in FP64
@@ -422,9 +440,9 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       s_lam[3] = lam;
       s_vbase = cost_t + lam * (psum_t - demand);  // the value without its line sum
       float s1 = (float)s_lam[1], s2 = (float)s_lam[2];
-      const float al = (float)(A.P.alpha_lambda * s_pw[0]);
+      const float al = s_pwf[3];
       const float gl = (float)(psum_t - demand);
-      const float th = fused_rule<float>(A.P, 0.f, gl, s1, s2, al, bc1, bc2);
+      const float th = fused_rule_f(RF, 0.f, gl, s1, s2, al, bc1, bc2);
       lam += (double)th;
       s_lam[0] = lam; s_lam[1] = s1; s_lam[2] = s2;
     }
@@ -435,8 +453,8 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       lacc = fmaf(mh[r], gh, fmaf(ml[r], gl, lacc));
       ph[r] = mh[r];
       pl[r] = ml[r];
-      float nh = fused_rule<float>(A.P, mh[r], gh, h1[r], h2[r], am, bc1, bc2);
-      float nlo = fused_rule<float>(A.P, ml[r], gl, l1[r], l2[r], am, bc1, bc2);
+      float nh = fused_rule_f(RF, mh[r], gh, h1[r], h2[r], am, bc1, bc2);
+      float nlo = fused_rule_f(RF, ml[r], gl, l1[r], l2[r], am, bc1, bc2);
       mh[r] = nh > 0.f ? nh : 0.f;
       ml[r] = nlo > 0.f ? nlo : 0.f;
     }
