@@ -4,6 +4,7 @@
     python -m paper_2406_13191_gb300.timing certify --config 1 --batch 1
     python -m paper_2406_13191_gb300.timing fused --config 1 --repeat 3
     python -m paper_2406_13191_gb300.timing group --iters 400
+    python -m paper_2406_13191_gb300.timing setup
 
 ``batched`` runs the tensor-core batched solve (BF16 hi/lo split products) for a
 fixed number of iterations and reports the time of the iteration kernels per batched
@@ -15,7 +16,9 @@ the 2000-bus instance, tests/golden/gamma.json).  ``group`` runs a mixed-size ba
 with line outages) for a fixed number of iterations, once network by network and once
 as one group solve (one CUDA-graph launch per round over all three).  These are
 measurements of the library, used for the kernel profiles; they are not the benchmark
-line.
+line.  ``setup`` times the per-network work of each workload's network: handle creation
+(validation, LDL^T factorisation, the FP64 Phi~ build and upload) and the first batched
+FP32/BF16 operator preparation.
 """
 from __future__ import annotations
 
@@ -139,9 +142,27 @@ def group(iters, repeat=3):
     print(json.dumps(res))
 
 
+def setup():
+    res = {"mode": "setup"}
+    for cfg in (0, 1, 2, 3):
+        net, base = synth.network_for(cfg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = DcopfDual(net, device=0)
+        t1 = time.perf_counter()
+        g.eval(base[None], [0.0], np.zeros((1, net.n_line)), np.zeros((1, net.n_line)),
+               precision="bf16x3")
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        res[f"{net.n_bus}-bus"] = dict(n_line=net.n_line, n_gen=net.n_gen, create_s=t1 - t0,
+                                       first_tensor_eval_s=t2 - t1)
+        del g
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("mode", choices=["batched", "certify", "fused", "group"])
+    ap.add_argument("mode", choices=["batched", "certify", "fused", "group", "setup"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--iters", type=int, default=16)
@@ -153,6 +174,8 @@ def main():
         certify(a.config, a.batch)
     elif a.mode == "group":
         group(a.iters)
+    elif a.mode == "setup":
+        setup()
     else:
         fused(a.repeat)
 
