@@ -401,11 +401,10 @@ def main():
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        r = g.solve(loads_h, target=target_h, gap=GAP, **OURS)
-        out = (r.bound.cpu(), r.lam.cpu(), r.mu_hi.cpu(), r.mu_lo.cpu(), r.iters.cpu(), r.status.cpu())
+        r = g.solve(loads_h, target=target_h, gap=GAP, **OURS).to_host()
         e2e_times.append(time.perf_counter() - t0)
     h2d = loads_h.numel() * 8 + 8
-    d2h = 8 + 8 + 2 * net.n_line * 8 + 4 + 4
+    d2h = (4 + 2 * net.n_line) * 8   # bound, lambda, iters, status, mu_hi, mu_lo (packed FP64)
     e2e = {"value": world * len(e2e_times) / sum(e2e_times), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 

@@ -36,6 +36,18 @@ class SolveResult:
     iters: torch.Tensor        # [B] iterations taken
     status: torch.Tensor       # [B] 0 target reached, 1 cap/tol, 2 infeasible suspected
 
+    def to_host(self) -> "SolveResult":
+        """The results in host memory with one device-to-host transfer (packed on the
+        device first; iteration counts and statuses travel exactly as FP64)."""
+        B = self.lam.shape[0]
+        packed = torch.cat([self.bound, self.lam, self.iters.double(), self.status.double(),
+                            self.mu_hi.reshape(-1), self.mu_lo.reshape(-1)]).cpu()
+        n = self.mu_hi.shape[1]
+        o = 4 * B
+        return SolveResult(packed[B:2 * B], packed[o:o + B * n].reshape(B, n),
+                           packed[o + B * n:].reshape(B, n), packed[:B],
+                           packed[2 * B:3 * B].int(), packed[3 * B:4 * B].int())
+
 
 class DcopfDual:
     """One network on one GPU (``dcopf_dual_create``).

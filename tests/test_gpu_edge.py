@@ -92,3 +92,14 @@ def test_infeasible_instance_is_reported(path):
     assert r.status[0].item() == 2
     # the bound itself is still a valid (finite) certified value of the dual
     assert np.isfinite(r.bound[0].item())
+
+
+def test_packed_host_results_equal_the_tensors():
+    net, base = synth.network_for(0)
+    g = DcopfDual(net)
+    r = g.solve(np.stack([base, base * 0.9]), path="batched", precision="bf16x3", rule="adam",
+                alpha=1000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=50)
+    h = r.to_host()
+    for f in ("lam", "mu_hi", "mu_lo", "bound", "iters", "status"):
+        a, b = getattr(r, f).cpu(), getattr(h, f)
+        assert a.shape == b.shape and torch.equal(a.to(b.dtype), b), f
