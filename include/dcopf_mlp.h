@@ -18,7 +18,9 @@
  * minimises the mean squared error in the normalised output space,
  *   L = 1 / (B * n_out) * sum_b sum_o (u_bo - (y_bo - out_shift_o) / out_scale_o)^2.
  *
- * Precision: FP32 storage and arithmetic (SIMT), FP64 loss accumulation.
+ * Precision: FP32 storage of parameters, moments and activations; products either on
+ * the tensor cores with BF16 hi/lo split operands (about 16 significant bits) or in
+ * FP32 SIMT; FP64 loss accumulation.
  *
  * Parameters: one flat FP32 vector, in this order, each matrix row-major:
  *   W1 [n_in][n_hidden], b1 [n_hidden], W2 [n_hidden][n_hidden], b2 [n_hidden],
@@ -50,6 +52,9 @@ typedef struct {
   int32_t n_hidden;  /* width of both hidden layers, >= 1 */
   int32_t n_out;     /* output width (1 + number of lines), >= 1 */
   int32_t max_batch; /* largest batch of any call on this handle, >= 1 */
+  int32_t precision; /* DCOPF_BF16X3: every product on the tcgen05 tensor cores with BF16
+                        hi/lo split operands (three products, FP32 accumulation);
+                        DCOPF_FP32: FP32 SIMT products */
 } dcopf_mlp_desc;
 
 typedef struct {

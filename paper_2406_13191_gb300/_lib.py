@@ -59,7 +59,7 @@ class GroupItem(C.Structure):
 
 class MlpDesc(C.Structure):
     _fields_ = [("n_in", C.c_int32), ("n_hidden", C.c_int32), ("n_out", C.c_int32),
-                ("max_batch", C.c_int32)]
+                ("max_batch", C.c_int32), ("precision", C.c_int32)]
 
 
 class AdamParams(C.Structure):

@@ -1,5 +1,7 @@
 // Learned warm start: a two-hidden-layer GELU perceptron from bus loads to a dual
 // point, with its training (forward, mean-squared-error gradient, Adam) on the GPU.
+// Two modes: every product on the tcgen05 tensor cores with BF16 hi/lo split operands
+// and FP32 accumulation (the tcgen05 GEMM of the batched solve), or FP32 SIMT.
 // Any proposal with mu >= 0 is a valid dual point (Section 3, Remarks 1-2), so the
 // network only changes where the ascent of Algorithm 1 starts.
 //
@@ -11,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <new>
@@ -130,6 +134,58 @@ __global__ void k_splitk_reduce(int M, int N, int S, const float* __restrict__ P
   }
 }
 
+// ---- tensor-core mode: BF16 hi/lo split operands for the tcgen05 GEMM
+//
+// BF16 hi/lo split of an FP32 matrix S [M][N] (leading dimension lds): row-major copies
+// (hi, lo, ld ldr) and/or transposed copies (hiT, loT: [N][ldt]).  The transposed copies
+// get zeros in columns [M, Mpad): the padding of a contraction over M.  32 x 32 tiles
+// through shared memory; block (32, 8).
+__global__ void k_split2d(int M, int N, int Mpad, const float* __restrict__ S, int lds,
+                          __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int ldr,
+                          __nv_bfloat16* __restrict__ hiT, __nv_bfloat16* __restrict__ loT,
+                          int ldt) {
+  __shared__ float t[32][33];
+  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) {
+    const int m = m0 + r, n = n0 + tx;
+    const bool in = m < M && n < N;
+    const float v = in ? S[(size_t)m * lds + n] : 0.f;
+    t[r][tx] = v;
+    if (hi && in) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      hi[(size_t)m * ldr + n] = h;
+      lo[(size_t)m * ldr + n] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+  }
+  if (!hiT) return;  // uniform across the block
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int n = n0 + r, m = m0 + tx;
+    if (n < N && m < Mpad) {
+      const float v = t[tx][r];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      hiT[(size_t)n * ldt + m] = h;
+      loT[(size_t)n * ldt + m] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+  }
+}
+
+// out[m][n] = epilogue(sum over the K slices s = 0..S-1 of P[s][m][n]) (fixed order).
+template <int EPI>
+__global__ void k_reduce_epi(int M, int N, int S, const float* __restrict__ P, int ldp,
+                             const float* __restrict__ bias, float* __restrict__ Z, int ldz,
+                             float* __restrict__ out, int ldo) {
+  const size_t MN = (size_t)M * N;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e / N), n = (int)(e - (size_t)m * N);
+    float v = 0.f;
+    for (int sl = 0; sl < S; ++sl) v += P[((size_t)sl * M + m) * ldp + n];
+    out[(size_t)m * ldo + n] = epilogue(EPI, v, m, n, bias, Z, ldz);
+  }
+}
+
 // Xn[b][i] = (X[r][i] - shift[i]) * scale[i], r = idx[b] (or b without idx).  A row
 // index outside [0, n_rows) records DCOPF_ERR_INVALID_ARG and yields a zero row.
 template <typename T>
@@ -242,8 +298,22 @@ inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
 
+// A BF16 hi/lo split operand of the tcgen05 GEMM and its tensor maps.
+struct TcOp {
+  DBuf hi, lo;
+  CUtensorMap mh, ml;
+  int ld = 0;
+};
+
 struct dcopf_mlp {
   int n_in = 0, nh = 0, n_out = 0, max_batch = 0;
+  // tensor-core mode: every product on tcgen05 with BF16 hi/lo split operands
+  int tensor = 0;
+  int ldi = 0, ldh = 0, ldo = 0, ldb = 0;  // padded leading dimensions (BF16 elements)
+  TcOp XnS, H1S, H2S, dUS, dZ2S;           // activations as A operands, [max_batch][features]
+  TcOp XnT, H1T, H2T, dZ2T, dZ1T, dUT;     // transposed, [features][ldb] (contractions over the batch)
+  TcOp W1T, W2T, W3T, W2R, W3R;            // weights: transposed for the forward, as stored for the backward
+  DBuf tcP;                                // split-K partial products
   int64_t P = 0, o_b1 = 0, o_W2 = 0, o_b2 = 0, o_W3 = 0, o_b3 = 0;
   int64_t adam_t = 0;
   int64_t launches = 0;
@@ -259,6 +329,92 @@ struct dcopf_mlp {
 };
 
 namespace {
+
+constexpr int TC_MAX_SPLITS = 16;
+
+inline int pad_to(int v, int q) { return (v + q - 1) / q * q; }
+
+// K slices tc_gemm_partial uses for an M x N x K product (the same rule).
+int tc_splits(int M, int N, int K, int sms) {
+  const int tiles = cdiv(M, 128) * cdiv(N, 128);
+  const int kb = cdiv(K, 64);
+  int sp = std::max(1, std::min(std::min(kb, TC_MAX_SPLITS), (int)cdiv(2 * sms, tiles)));
+  const int per = cdiv(kb, sp);
+  return (int)cdiv(kb, per);
+}
+
+bool tc_op_alloc(TcOp& o, int rows, int cols, int ld) {
+  o.ld = ld;
+  const size_t bytes = (size_t)rows * ld * 2;
+  if (o.hi.alloc(bytes) != cudaSuccess || o.lo.alloc(bytes) != cudaSuccess) return false;
+  if (cudaMemset(o.hi.p, 0, bytes) != cudaSuccess || cudaMemset(o.lo.p, 0, bytes) != cudaSuccess)
+    return false;
+  return tc_make_map(&o.mh, o.hi.p, rows, cols, ld) && tc_make_map(&o.ml, o.lo.p, rows, cols, ld);
+}
+
+// BF16 hi/lo copies of an FP32 matrix (row-major R and/or transposed T, see k_split2d).
+void tc_split(dcopf_mlp* h, cudaStream_t s, int M, int N, int Mpad, const float* S, int lds,
+              TcOp* R, TcOp* T) {
+  dim3 grid(cdiv(N, 32), cdiv(std::max(M, Mpad), 32));
+  k_split2d<<<grid, dim3(32, 8), 0, s>>>(
+      M, N, Mpad, S, lds, R ? R->hi.as<__nv_bfloat16>() : nullptr,
+      R ? R->lo.as<__nv_bfloat16>() : nullptr, R ? R->ld : 0, T ? T->hi.as<__nv_bfloat16>() : nullptr,
+      T ? T->lo.as<__nv_bfloat16>() : nullptr, T ? T->ld : 0);
+  h->launches += 1;
+}
+
+// out = epilogue(A B^T) for A [M][K], B [N][K] split operands; fixed-order K slices.
+template <int EPI>
+void tc_product(dcopf_mlp* h, cudaStream_t s, const TcOp& A, const TcOp& B, int M, int N, int K,
+                const float* bias, float* Z, int ldz, float* out, int ldo) {
+  const int ldp = pad_to(N, 4);
+  int sp = 1;
+  tc_gemm_partial(A.mh, A.ml, B.mh, B.ml, M, N, K, h->tcP.as<float>(), ldp, TC_MAX_SPLITS,
+                  h->sm_count, h->err.as<int>(), &sp, s);
+  const int64_t total = (int64_t)M * N;
+  k_reduce_epi<EPI><<<(int)std::min<int64_t>(cdiv(total, 256), 8 * h->sm_count), 256, 0, s>>>(
+      M, N, sp, h->tcP.as<float>(), ldp, bias, Z, ldz, out, ldo);
+  h->launches += 2;
+}
+
+// Weight operands from the FP32 parameters (after every change of the parameters).
+void tc_refresh_weights(dcopf_mlp* h, cudaStream_t s) {
+  const float* P = h->params.as<float>();
+  const int ni = h->n_in, nh = h->nh, no = h->n_out;
+  tc_split(h, s, ni, nh, ni, P, nh, nullptr, &h->W1T);
+  tc_split(h, s, nh, nh, nh, P + h->o_W2, nh, &h->W2R, &h->W2T);
+  tc_split(h, s, nh, no, nh, P + h->o_W3, no, &h->W3R, &h->W3T);
+}
+
+// Forward pass of the rows in Xn on the tensor cores; with `train`, also the
+// transposed operands the backward pass contracts over the batch.
+void forward_rows_tc(dcopf_mlp* h, cudaStream_t s, int Bn, bool train) {
+  const float* P = h->params.as<float>();
+  const int ni = h->n_in, nh = h->nh, no = h->n_out;
+  const int Bp = train ? pad_to(Bn, 64) : Bn;
+  tc_split(h, s, Bn, ni, Bp, h->Xn.as<float>(), ni, &h->XnS, train ? &h->XnT : nullptr);
+  tc_product<EPI_BIAS_GELU>(h, s, h->XnS, h->W1T, Bn, nh, ni, P + h->o_b1, h->Z1.as<float>(), nh,
+                            h->H1.as<float>(), nh);
+  tc_split(h, s, Bn, nh, Bp, h->H1.as<float>(), nh, &h->H1S, train ? &h->H1T : nullptr);
+  tc_product<EPI_BIAS_GELU>(h, s, h->H1S, h->W2T, Bn, nh, nh, P + h->o_b2, h->Z2.as<float>(), nh,
+                            h->H2.as<float>(), nh);
+  tc_split(h, s, Bn, nh, Bp, h->H2.as<float>(), nh, &h->H2S, train ? &h->H2T : nullptr);
+  tc_product<EPI_BIAS>(h, s, h->H2S, h->W3T, Bn, no, nh, P + h->o_b3, nullptr, 0, h->U.as<float>(), no);
+}
+
+// Splits of the products (and thus the partial buffer) for every product of a call
+// with batch Bn: the largest over the batches a handle accepts sizes the buffer.
+size_t tc_partial_floats(const dcopf_mlp* h) {
+  const int ni = h->n_in, nh = h->nh, no = h->n_out, sms = h->sm_count;
+  size_t most = 0;
+  for (int Bn = 1; Bn <= h->max_batch; ++Bn) {  // every batch: the maxima sit at tile edges
+    const int prod[8][3] = {{Bn, nh, ni}, {Bn, nh, nh}, {Bn, no, nh}, {nh, no, Bn},
+                            {Bn, nh, no}, {nh, nh, Bn}, {Bn, nh, nh}, {ni, nh, Bn}};
+    for (auto& q : prod)
+      most = std::max(most, (size_t)tc_splits(q[0], q[1], q[2], sms) * q[0] * pad_to(q[1], 4));
+  }
+  return most;
+}
 
 // One product with its epilogue.  When the output tiles cannot fill the SMs twice,
 // K is split into S slices (multiples of the K tile, at least 256 deep) written to the
@@ -293,7 +449,11 @@ void gemm(dcopf_mlp* h, cudaStream_t s, int M, int N, int K, const float* A, int
 
 // Forward pass of the rows already normalised in Xn: Z1, H1, Z2, H2 and U (the
 // normalised output).
-void forward_rows(dcopf_mlp* h, cudaStream_t s, int Bn) {
+void forward_rows(dcopf_mlp* h, cudaStream_t s, int Bn, bool train = false) {
+  if (h->tensor) {
+    forward_rows_tc(h, s, Bn, train);
+    return;
+  }
   const float* P = h->params.as<float>();
   const int ni = h->n_in, nh = h->nh, no = h->n_out;
   gemm<false, false, EPI_BIAS_GELU>(h, s, Bn, nh, ni, h->Xn.as<float>(), ni, P, nh,
@@ -319,7 +479,7 @@ void loss_grad_rows(dcopf_mlp* h, cudaStream_t s, int Bn, const int* idx, int64_
   float* G = h->grad.as<float>();
   const int ni = h->n_in, nh = h->nh, no = h->n_out;
   gather_rows<float>(h, s, Bn, idx, n_rows, X);
-  forward_rows(h, s, Bn);
+  forward_rows(h, s, Bn, true);
   k_mlp_out_grad<<<OUT_BLOCKS, OUT_THREADS, 0, s>>>(Bn, no, h->U.as<float>(), idx, n_rows, Y,
                                                     h->out_shift(), h->out_inv(),
                                                     h->dU.as<float>(), h->part.as<double>());
@@ -327,6 +487,26 @@ void loss_grad_rows(dcopf_mlp* h, cudaStream_t s, int Bn, const int* idx, int64_
   if (loss) {
     k_mlp_loss<<<1, 256, 0, s>>>(OUT_BLOCKS, h->part.as<double>(), (double)Bn * no, loss);
     h->launches += 1;
+  }
+  if (h->tensor) {
+    // the same chain rule on the tensor cores: weight gradients contract over the batch
+    // (transposed operands, zero-padded to the K tile), input gradients over the outputs
+    const int Bp = pad_to(Bn, 64);
+    tc_split(h, s, Bn, no, Bp, h->dU.as<float>(), no, &h->dUS, &h->dUT);
+    tc_product<EPI_STORE>(h, s, h->H2T, h->dUT, nh, no, Bn, nullptr, nullptr, 0, G + h->o_W3, no);
+    k_colsum<<<cdiv(no, 256), 256, 0, s>>>(Bn, no, h->dU.as<float>(), G + h->o_b3);
+    tc_product<EPI_GELU_BACK>(h, s, h->dUS, h->W3R, Bn, nh, no, nullptr, h->Z2.as<float>(), nh,
+                              h->D2.as<float>(), nh);
+    tc_split(h, s, Bn, nh, Bp, h->D2.as<float>(), nh, &h->dZ2S, &h->dZ2T);
+    tc_product<EPI_STORE>(h, s, h->H1T, h->dZ2T, nh, nh, Bn, nullptr, nullptr, 0, G + h->o_W2, nh);
+    k_colsum<<<cdiv(nh, 256), 256, 0, s>>>(Bn, nh, h->D2.as<float>(), G + h->o_b2);
+    tc_product<EPI_GELU_BACK>(h, s, h->dZ2S, h->W2R, Bn, nh, nh, nullptr, h->Z1.as<float>(), nh,
+                              h->D1.as<float>(), nh);
+    tc_split(h, s, Bn, nh, Bp, h->D1.as<float>(), nh, nullptr, &h->dZ1T);
+    tc_product<EPI_STORE>(h, s, h->XnT, h->dZ1T, ni, nh, Bn, nullptr, nullptr, 0, G, nh);
+    k_colsum<<<cdiv(nh, 256), 256, 0, s>>>(Bn, nh, h->D1.as<float>(), G + h->o_b1);
+    h->launches += 3;
+    return;
   }
   // layer 3: dW3 = H2^T dU, db3 = column sums of dU, dZ2 = (dU W3^T) * GELU'(Z2)
   gemm<true, false, EPI_STORE>(h, s, nh, no, Bn, h->H2.as<float>(), nh, h->dU.as<float>(), no,
@@ -365,11 +545,13 @@ dcopf_status dcopf_mlp_create(const dcopf_mlp_desc* d, dcopf_mlp_t* out) {
   if (!d || !out) return DCOPF_ERR_INVALID_ARG;
   *out = nullptr;
   if (d->n_in < 1 || d->n_hidden < 1 || d->n_out < 1 || d->max_batch < 1) return DCOPF_ERR_INVALID_ARG;
+  if (d->precision != DCOPF_FP32 && d->precision != DCOPF_BF16X3) return DCOPF_ERR_INVALID_ARG;
   const int64_t ni = d->n_in, nh = d->n_hidden, no = d->n_out, mb = d->max_batch;
   if (ni * nh > (1LL << 31) || nh * no > (1LL << 31) || mb * (ni > no ? ni : no) > (1LL << 31))
     return DCOPF_ERR_INVALID_ARG;
   dcopf_mlp* h = new (std::nothrow) dcopf_mlp();
   if (!h) return DCOPF_ERR_OOM;
+  h->tensor = d->precision == DCOPF_BF16X3 ? 1 : 0;
   h->n_in = d->n_in;
   h->nh = d->n_hidden;
   h->n_out = d->n_out;
@@ -397,6 +579,23 @@ dcopf_status dcopf_mlp_create(const dcopf_mlp_desc* d, dcopf_mlp_t* out) {
   // split K only where tiles < 2 SMs: S * M * N < (2 SMs + tiles) * 64 * 64 <= 4 SMs * 4096
   h->splitk_cap = (size_t)4 * h->sm_count * TBM * TBN;
   ok = ok && h->splitk.alloc(h->splitk_cap * 4) == cudaSuccess;
+  if (ok && h->tensor) {
+    const int ni_ = h->n_in, nh_ = h->nh, no_ = h->n_out, mb_ = h->max_batch;
+    h->ldi = pad_to(ni_, 8);
+    h->ldh = pad_to(nh_, 8);
+    h->ldo = pad_to(no_, 8);
+    h->ldb = pad_to(mb_, 64);
+    ok = tc_gemm_prepare() == cudaSuccess &&
+         tc_op_alloc(h->XnS, mb_, ni_, h->ldi) && tc_op_alloc(h->H1S, mb_, nh_, h->ldh) &&
+         tc_op_alloc(h->H2S, mb_, nh_, h->ldh) && tc_op_alloc(h->dUS, mb_, no_, h->ldo) &&
+         tc_op_alloc(h->dZ2S, mb_, nh_, h->ldh) && tc_op_alloc(h->XnT, ni_, h->ldb, h->ldb) &&
+         tc_op_alloc(h->H1T, nh_, h->ldb, h->ldb) && tc_op_alloc(h->H2T, nh_, h->ldb, h->ldb) &&
+         tc_op_alloc(h->dZ2T, nh_, h->ldb, h->ldb) && tc_op_alloc(h->dZ1T, nh_, h->ldb, h->ldb) &&
+         tc_op_alloc(h->dUT, no_, h->ldb, h->ldb) && tc_op_alloc(h->W1T, nh_, ni_, h->ldi) &&
+         tc_op_alloc(h->W2T, nh_, nh_, h->ldh) && tc_op_alloc(h->W2R, nh_, nh_, h->ldh) &&
+         tc_op_alloc(h->W3T, no_, nh_, h->ldh) && tc_op_alloc(h->W3R, nh_, no_, h->ldo) &&
+         h->tcP.alloc(tc_partial_floats(h) * 4) == cudaSuccess;
+  }
   if (!ok) {
     delete h;
     cudaGetLastError();
@@ -438,7 +637,8 @@ dcopf_status dcopf_mlp_set_params(dcopf_mlp_t h, const float* params, void* stre
       cudaMemsetAsync(h->mom2.p, 0, P4, s) != cudaSuccess)
     return DCOPF_ERR_CUDA;
   h->adam_t = 0;
-  return DCOPF_OK;
+  if (h->tensor) tc_refresh_weights(h, s);
+  return launch_status();
 }
 
 dcopf_status dcopf_mlp_get_params(dcopf_mlp_t h, float* params, void* stream) {
@@ -505,6 +705,7 @@ dcopf_status dcopf_mlp_train_step(dcopf_mlp_t h, int32_t batch, const int32_t* i
       h->P, h->params.as<float>(), h->grad.as<float>(), h->mom1.as<float>(), h->mom2.as<float>(),
       (float)a->beta1, (float)a->beta2, (float)c1, (float)c2, (float)a->eps);
   h->launches += 1;
+  if (h->tensor) tc_refresh_weights(h, s);
   return launch_status();
 }
 

@@ -567,6 +567,39 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
   return run_eval_finish(h, B, outage, lambda, mh, ml, value, glam, ghi, glo, dispatch, s);
 }
 
+// ------------------------------------------------------------------ for other users
+bool tc_make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint64_t ld) {
+  return make_map(m, ptr, rows, cols, ld, GBM);
+}
+
+// P[s][m][ldp] = the K-slice s of A[m][:] . B[n][:] (BF16 hi/lo split operands, three
+// products, FP32 accumulation in TMEM) for 0 <= m < M, 0 <= n < N; the number of K
+// slices is chosen to fill the SMs twice (at most max_splits) and returned.
+cudaError_t tc_gemm_partial(const CUtensorMap& Ah, const CUtensorMap& Al, const CUtensorMap& Bh,
+                            const CUtensorMap& Bl, int M, int N, int K, float* P, int ldp,
+                            int max_splits, int sm_count, int* err, int* splits_used,
+                            cudaStream_t s) {
+  const int tiles = ((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN);
+  const int kb = (K + GBK - 1) / GBK;
+  int sp = std::max(1, std::min(std::min(kb, max_splits), (2 * sm_count + tiles - 1) / tiles));
+  const int per = (kb + sp - 1) / sp;
+  sp = (kb + per - 1) / per;  // every slice has at least one K block
+  GemmArgs g{};
+  g.M = M; g.N = N; g.K = K; g.kb_per_split = per; g.epi = EPI_PARTIAL;
+  g.P = P; g.ldp = ldp; g.err = err; g.timeout_ns = 2000000000ull;
+  using Cfg = GemmCfg<3>;
+  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, sp);
+  k_gemm_bf16x<3><<<grid, 192, Cfg::SMEM, s>>>(Ah, Al, Bh, Bl, g);
+  *splits_used = sp;
+  return cudaGetLastError();
+}
+
+// Allows the three-product GEMM its shared memory (once per process).
+cudaError_t tc_gemm_prepare() {
+  return cudaFuncSetAttribute(k_gemm_bf16x<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)GemmCfg<3>::SMEM);
+}
+
 template __global__ void k_split_eta<float>(int, int, const float*, const float*, const int*,
                                             const float*, __nv_bfloat16*, __nv_bfloat16*);
 

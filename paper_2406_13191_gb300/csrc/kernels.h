@@ -212,6 +212,16 @@ template <typename S>
 dcopf_status solve_tensor(dcopf_dual* h, int batch, const double* loads, const int* outage,
                           const dcopf_solve_params& p, double* lam, double* mh, double* ml,
                           double* bound, int* iters, int* status, cudaStream_t s);
+// tcgen05 GEMM with BF16 hi/lo split operands for other users (k_tensor.cu): tensor
+// maps of row-major BF16 [rows][ld] with cols valid columns (K-major operands), and
+// split-K partial products C = A B^T.
+bool tc_make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint64_t ld);
+cudaError_t tc_gemm_partial(const CUtensorMap& Ah, const CUtensorMap& Al, const CUtensorMap& Bh,
+                            const CUtensorMap& Bl, int M, int N, int K, float* P, int ldp,
+                            int max_splits, int sm_count, int* err, int* splits_used,
+                            cudaStream_t s);
+cudaError_t tc_gemm_prepare();
+
 // One network's instances in a group of batched solves (dcopf_dual_solve_group).
 struct TensorItem {
   dcopf_dual* h;

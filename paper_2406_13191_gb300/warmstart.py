@@ -26,11 +26,14 @@ class WarmStartMLP:
     """One perceptron on one GPU (``dcopf_mlp_create``)."""
 
     def __init__(self, n_in: int, n_out: int, n_hidden: int = 512, max_batch: int = 1024,
-                 device: int | None = None):
+                 device: int | None = None, precision: str = "bf16x3"):
+        """``precision``: "bf16x3" (products on the tensor cores, BF16 hi/lo split
+        operands) or "fp32" (FP32 SIMT products)."""
         self.lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         with torch.cuda.device(self.device):
-            d = _lib.MlpDesc(int(n_in), int(n_hidden), int(n_out), int(max_batch))
+            d = _lib.MlpDesc(int(n_in), int(n_hidden), int(n_out), int(max_batch),
+                             _lib.PRECISION[precision])
             h = C.c_void_p()
             _lib.check(self.lib.dcopf_mlp_create(C.byref(d), C.byref(h)), "dcopf_mlp_create")
         self.h = h
