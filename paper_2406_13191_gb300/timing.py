@@ -5,6 +5,7 @@
     python -m paper_2406_13191_gb300.timing fused --config 1 --repeat 3
     python -m paper_2406_13191_gb300.timing group --iters 400
     python -m paper_2406_13191_gb300.timing setup
+    python -m paper_2406_13191_gb300.timing mlp --batch 512 --iters 50
 
 ``batched`` runs the tensor-core batched solve (BF16 hi/lo split products) for a
 fixed number of iterations and reports the time of the iteration kernels per batched
@@ -18,7 +19,8 @@ as one group solve (one CUDA-graph launch per round over all three).  These are
 measurements of the library, used for the kernel profiles; they are not the benchmark
 line.  ``setup`` times the per-network work of each workload's network: handle creation
 (validation, LDL^T factorisation, the FP64 Phi~ build and upload) and the first batched
-FP32/BF16 operator preparation.
+FP32/BF16 operator preparation.  ``mlp`` times training steps of the warm-start
+perceptron (2000 -> 512 -> 512 -> 3201, seeded random data) in both product modes.
 """
 from __future__ import annotations
 
@@ -160,9 +162,37 @@ def setup():
     print(json.dumps(res))
 
 
+def mlp(batch, steps):
+    from . import warmstart
+    rng = np.random.default_rng(0)
+    X = torch.as_tensor(rng.uniform(0, 1, (4 * batch, 2000)), dtype=torch.float32, device="cuda")
+    Y = torch.as_tensor(rng.normal(0, 1, (4 * batch, 3201)), dtype=torch.float32, device="cuda")
+    res = {"mode": "mlp", "batch": batch, "steps": steps}
+    for prec in ("bf16x3", "fp32"):
+        m = warmstart.WarmStartMLP(2000, 3201, 512, max_batch=batch, precision=prec)
+        m.set_params(warmstart.init_params(2000, 512, 3201, 1))
+        idx = torch.as_tensor(rng.permutation(4 * batch)[:batch].astype(np.int32), device="cuda")
+        for _ in range(3):
+            m.train_step(idx, X, Y, 1e-4)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = m.kernel_launches()
+        e0.record()
+        for _ in range(steps):
+            m.train_step(idx, X, Y, 1e-4)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        flops = 3 * 2 * batch * m.num_params
+        res[prec] = dict(ms_per_step=ms, tflops=flops / (ms * 1e-3) / 1e12,
+                         launches_per_step=(m.kernel_launches() - l0) / steps)
+        del m
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("mode", choices=["batched", "certify", "fused", "group", "setup"])
+    ap.add_argument("mode", choices=["batched", "certify", "fused", "group", "setup", "mlp"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--iters", type=int, default=16)
@@ -176,6 +206,8 @@ def main():
         group(a.iters)
     elif a.mode == "setup":
         setup()
+    elif a.mode == "mlp":
+        mlp(a.batch, a.iters)
     else:
         fused(a.repeat)
 
