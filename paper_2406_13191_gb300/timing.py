@@ -6,6 +6,7 @@
     python -m paper_2406_13191_gb300.timing group --iters 400
     python -m paper_2406_13191_gb300.timing setup
     python -m paper_2406_13191_gb300.timing mlp --batch 512 --iters 50
+    python -m paper_2406_13191_gb300.timing togap --config 2
 
 ``batched`` runs the tensor-core batched solve (BF16 hi/lo split products) for a
 fixed number of iterations and reports the time of the iteration kernels per batched
@@ -21,6 +22,9 @@ line.  ``setup`` times the per-network work of each workload's network: handle c
 (validation, LDL^T factorisation, the FP64 Phi~ build and upload) and the first batched
 FP32/BF16 operator preparation.  ``mlp`` times training steps of the warm-start
 perceptron (2000 -> 512 -> 512 -> 3201, seeded random data) in both product modes.
+``togap`` solves the first instances of the 4600-bus batch (256, half with an outage)
+or of the 10000-bus batch (64) to the certified 0.1 % gap against the oracle's optima
+(tests/golden/study_gamma.json, c3_gamma.json) in one batched tensor-core call.
 """
 from __future__ import annotations
 
@@ -190,9 +194,45 @@ def mlp(batch, steps):
     print(json.dumps(res))
 
 
+def togap(cfg, repeat=2):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if cfg == 2:
+        gam = json.load(open(os.path.join(root, "tests", "golden", "study_gamma.json")))["4600"]
+        kw = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99, max_iters=4000)
+    else:
+        gam = json.load(open(os.path.join(root, "tests", "golden", "c3_gamma.json")))["gamma"]
+        kw = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=4000)
+    w = synth.workload(cfg, batch=len(gam))
+    ok = np.array([x is not None for x in gam])
+    T = np.array([x for x in gam if x is not None])
+    L = torch.tensor(w.loads[ok], device="cuda")
+    O = torch.tensor(w.outage[ok], device="cuda") if (w.outage >= 0).any() else None
+    Td = torch.tensor(T, device="cuda")
+    g = DcopfDual(w.net, device=0)
+    g.solve(L, outage=O, target=Td, path="batched", precision="bf16x3", **kw)
+    best = None
+    for _ in range(repeat):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = g.solve(L, outage=O, target=Td, path="batched", precision="bf16x3", **kw)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    it = r.iters.cpu().numpy()
+    st = r.status.cpu().numpy()
+    b = r.bound.cpu().numpy()
+    print(json.dumps(dict(mode="togap", config=cfg, instances=int(ok.sum()),
+                          outages=int(0 if O is None else (O >= 0).sum().item()), settings=kw,
+                          ms=best, instances_per_s=ok.sum() / (best * 1e-3),
+                          mean_iters=float(it.mean()), p90_iters=float(np.percentile(it, 90)),
+                          most_iters=int(it.max()), reached_gap=int((st == 0).sum()),
+                          all_bounds_valid=bool(np.all(b <= T + 1e-9 * np.abs(T))))))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("mode", choices=["batched", "certify", "fused", "group", "setup", "mlp"])
+    ap.add_argument("mode", choices=["batched", "certify", "fused", "group", "setup", "mlp", "togap"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--iters", type=int, default=16)
@@ -208,6 +248,8 @@ def main():
         setup()
     elif a.mode == "mlp":
         mlp(a.batch, a.iters)
+    elif a.mode == "togap":
+        togap(a.config)
     else:
         fused(a.repeat)
 
