@@ -53,6 +53,7 @@ struct FusedArgs {
   double* R;                     // [2][G] line partials of the dual value
   unsigned* cnt;                 // [8] arrival counters, one per cluster rank
   int* err;
+  double pscale, pinv;           // fixed-point scale of the dispatch sum and its inverse
   int max_iters;
   double tol;
   int rows_per_cta;
@@ -135,8 +136,12 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   __shared__ double s_vbase;    // cost + lambda (sum p - D) of the pending evaluation
   __shared__ int s_cand;        // stop decision of this loop (made by the last warp)
   __shared__ double s_lam[4];   // lam, s1, s2, lam at the pending evaluation
-  __shared__ double s_cs[2];    // cost / dispatch sums of own slice (read by peers)
-  __shared__ double s_csp[16];  // the cluster's cost / dispatch sums gathered
+  __shared__ float redf[32];
+  __shared__ long long redq[32];
+  __shared__ double s_cs;       // cost sum of own slice (read by peers)
+  __shared__ long long s_psq;   // dispatch sum of own slice, fixed point (read by peers)
+  __shared__ double s_csp[8];   // the cluster's cost sums gathered
+  __shared__ long long s_psp[8];  // the cluster's dispatch sums gathered
   __shared__ double s_pw[6];    // decay^(t-1), 1 - beta1^t, 1 - beta2^t; running powers
   __shared__ float s_pwf[4];    // FP32 step factors: alpha decay^(t-1), bias corrections, alpha_lambda decay^(t-1)
   __shared__ int s_flag;        // this CTA gave up waiting (read by peers)
@@ -259,10 +264,13 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       // cancels (ctil + sigma lambda + pi~) is formed in FP64.  The dispatch sum feeds
       // the lambda gradient sum(p) - D, a small difference of large sums: FP64 all the
       // way.  A generator's cost term only enters the in-loop value (which decides
-      // when to certify; the certificate is FP64): FP32 per thread and warp, FP64
-      // across warps (FP64 shuffles are slow on this part).
+      // when to certify; the certificate is FP64): FP32 within the CTA, FP64 across
+      // the cluster.  Each thread's dispatch is formed in FP64 and rounded once to a
+      // 64-bit fixed point whose range covers the sum of |p| over all generators; the
+      // fixed-point sums are exact and independent of order, and integer shuffles
+      // are several times faster than FP64 ones on this part.
       float csf = 0.f;
-      double psd = 0.0;
+      long long psq = 0;
       for (int jj = tid; jj < nj; jj += blockDim.x) {
         const float4* tp = (const float4*)(tmp + jj * NCLp);
         float s = 0.f;
@@ -279,25 +287,24 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
         const float x = inner_x<float>((float)w, (float)mq);
         xsl[jj] = x;
         csf += fmaf(fmaf((float)mq, x, (float)ct), x, (float)gk[3 * SLp + jj]);
-        psd += gk[4 * SLp + jj] + sg * (double)x;
+        psq += __double2ll_rn((gk[4 * SLp + jj] + sg * (double)x) * A.pscale);
       }
       csf = warp_sum(csf);
-      psd = warp_sum(psd);
-      if (lane == 0) { red[warp] = (double)csf; red[16 + warp] = psd; }
+      psq = warp_sum(psq);
+      if (lane == 0) { redf[warp] = csf; redq[warp] = psq; }
       const int gave_up = __syncthreads_or(ok ? 0 : 1);
       if (warp == 0) {
-        // the slice's cost and dispatch sums: FP64 tree over the warp partials (FP64
-        // latency is high on this part: a tree, not a chain)
-        double cs = lane < nw ? red[lane] : 0.0;
-        double ps = lane < nw ? red[16 + lane] : 0.0;
+        // the slice's cost and dispatch sums: a tree over the warp partials
+        float cs = lane < nw ? redf[lane] : 0.f;
+        long long ps = lane < nw ? redq[lane] : 0ll;
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) {
           cs += __shfl_xor_sync(0xffffffffu, cs, o);
           ps += __shfl_xor_sync(0xffffffffu, ps, o);
         }
         if (lane == 0) {
-          s_cs[0] = cs;
-          s_cs[1] = ps;
+          s_cs = (double)cs;
+          s_psq = ps;
           s_flag = gave_up;
         }
       }
@@ -369,9 +376,8 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       }
     }
     if (tid >= 32 && tid < 32 + C) {
-      const double* o = cl.map_shared_rank(s_cs, tid - 32);
-      s_csp[2 * (tid - 32)] = o[0];
-      s_csp[2 * (tid - 32) + 1] = o[1];
+      s_csp[tid - 32] = *cl.map_shared_rank(&s_cs, tid - 32);
+      s_psp[tid - 32] = *cl.map_shared_rank(&s_psq, tid - 32);
     }
     __syncthreads();
     if (pending) {
@@ -386,10 +392,11 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     }
     if (cand) break;  // uniform everywhere: every CTA assembled the same value
     if (tid == 0) {
-      double cs2 = 0.0, ps2 = 0.0;
-      for (int q = 0; q < C; ++q) { cs2 += s_csp[2 * q]; ps2 += s_csp[2 * q + 1]; }
+      double cs2 = 0.0;
+      long long ps2 = 0;
+      for (int q = 0; q < C; ++q) { cs2 += s_csp[q]; ps2 += s_psp[q]; }
       red[0] = cs2;
-      red[1] = ps2;
+      red[1] = (double)ps2 * A.pinv;
     } else if (tid == 64) {
       // step-size factors of the next step from the running powers (FP64), and their
       // FP32 copies for every thread
@@ -630,6 +637,15 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
   A.R = (double*)(m + pc_bytes);
   A.cnt = (unsigned*)(m + pc_bytes + r_bytes);
   A.err = h->d_err;
+  {
+    // 2^e with sum_j (|mid_j| + |sigma_j|) * 2^e < 2^61, a bound on sum_j |p_j| 2^e:
+    // no partial sum of the rounded dispatches can overflow 64 bits
+    double pabs = 1.0;
+    for (int j = 0; j < ng; ++j) pabs += fabs(h->host.mid[j]) + fabs(h->host.sigma[j]);
+    const int e = 61 - (int)ceil(log2(pabs));
+    A.pscale = ldexp(1.0, e);
+    A.pinv = ldexp(1.0, -e);
+  }
   A.max_iters = max_iters;
   A.tol = tol;
   A.timeout_ns = 2000000000ull;
