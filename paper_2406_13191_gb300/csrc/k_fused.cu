@@ -121,10 +121,10 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   // shared memory carve-up: per-slice generator constants (FP64), then floats
   double* gk = (double*)smem_raw;                // [5][SLp] ctil, sigma, mq, cconst, mid
   const int SLp = (SL + 1) & ~1;
-  float* pp = (float*)(gk + 5 * SLp);            // [ngp] partial adjoint of own rows
-  float* xs = pp + ngp;                          // [ngp] x* of all gens (gathered)
-  float* xsl = xs + ngp;                         // [SL]  x* of own slice (read by peers)
-  float* tmp = xsl + ((SL + 3) & ~3);            // [SL * NCLp] cluster partials of own slice
+  // [C][SL] partial adjoints of own slice, one row per cluster rank (written by peers)
+  float* recv = (float*)(gk + 5 * SLp);
+  float* xs = recv + ((C * SL + 3) & ~3);        // [ngp] x* of all gens (written by peers)
+  float* tmp = xs + ngp;                         // [SL * NCLp] cluster partials of own slice
   float* row = tmp + SL * NCLp;                  // per-row arrays, 12 x rpc
   float *eta = row, *mh = row + rpc, *ml = row + 2 * rpc, *h1 = row + 3 * rpc, *h2 = row + 4 * rpc,
         *l1 = row + 5 * rpc, *l2 = row + 6 * rpc, *ph = row + 7 * rpc, *pl = row + 8 * rpc,
@@ -138,13 +138,11 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   __shared__ double s_lam[4];   // lam, s1, s2, lam at the pending evaluation
   __shared__ float redf[32];
   __shared__ long long redq[32];
-  __shared__ double s_cs;       // cost sum of own slice (read by peers)
-  __shared__ long long s_psq;   // dispatch sum of own slice, fixed point (read by peers)
-  __shared__ double s_csp[8];   // the cluster's cost sums gathered
-  __shared__ long long s_psp[8];  // the cluster's dispatch sums gathered
+  __shared__ double s_csp[8];     // the cluster's slice cost sums (written by peers)
+  __shared__ long long s_psp[8];  // the cluster's slice dispatch sums, fixed point (peers)
+  __shared__ int s_flags[8];      // the cluster's gave-up flags (written by peers)
   __shared__ double s_pw[6];    // decay^(t-1), 1 - beta1^t, 1 - beta2^t; running powers
   __shared__ float s_pwf[4];    // FP32 step factors: alpha decay^(t-1), bias corrections, alpha_lambda decay^(t-1)
-  __shared__ int s_flag;        // this CTA gave up waiting (read by peers)
 
   const float* phi = A.phi_in_smem ? phis : (N.phi32 + (size_t)r0 * ng);
   if (A.phi_in_smem)
@@ -189,9 +187,15 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     float* Pcb = A.Pc + (size_t)(k & 1u) * ng * NCLp;
     const double* Rprev = A.R + (size_t)((k + 1u) & 1u) * G;  // written in loop k-1
     double* Rcur = A.R + (size_t)(k & 1u) * G;
-    // ---------------- A: partial adjoint of own rows (4 gens per thread in flight)
+    // ---------------- A: partial adjoint of own rows (4 gens per thread in flight),
+    // each stored straight into the shared memory of the rank that owns the gen's slice
+    // (remote stores do not wait for a round trip; the cluster barrier publishes them)
     for (int r = tid; r < nr; r += blockDim.x) eta[r] = mh[r] - ml[r];
     __syncthreads();
+    auto push = [&](int j, float v) {
+      const int q = j / SL;
+      cl.map_shared_rank(recv, q)[rank * SL + (j - q * SL)] = v;
+    };
     for (int jb = tid; jb < ng; jb += 4 * blockDim.x) {
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
       const int b = blockDim.x;
@@ -204,10 +208,10 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
         if (v2) a2 = fmaf(pr[2 * b], e, a2);
         if (v3) a3 = fmaf(pr[3 * b], e, a3);
       }
-      pp[jb] = a0;
-      if (v1) pp[jb + b] = a1;
-      if (v2) pp[jb + 2 * b] = a2;
-      if (v3) pp[jb + 3 * b] = a3;
+      push(jb, a0);
+      if (v1) push(jb + b, a1);
+      if (v2) push(jb + 2 * b, a2);
+      if (v3) push(jb + 3 * b, a3);
     }
     cl.sync();
     // ---------------- A2: cluster sum of own slice (fixed rank order), published
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       const int j = j0 + jj;
       float v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = q < C ? cl.map_shared_rank(pp, q)[j] : 0.f;
+      for (int q = 0; q < 8; ++q) v[q] = q < C ? recv[q * SL + jj] : 0.f;
       float s = 0.f;
 #pragma unroll
       for (int q = 0; q < 8; ++q) s += v[q];
@@ -285,7 +289,9 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
         const double ct = gk[jj], sg = gk[SLp + jj], mq = gk[2 * SLp + jj];
         const double w = ct + sg * lam + (double)s;
         const float x = inner_x<float>((float)w, (float)mq);
-        xsl[jj] = x;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < C) cl.map_shared_rank(xs, q)[j0 + jj] = x;  // x* to every rank
         csf += fmaf(fmaf((float)mq, x, (float)ct), x, (float)gk[3 * SLp + jj]);
         psq += __double2ll_rn((gk[4 * SLp + jj] + sg * (double)x) * A.pscale);
       }
@@ -302,16 +308,16 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
           cs += __shfl_xor_sync(0xffffffffu, cs, o);
           ps += __shfl_xor_sync(0xffffffffu, ps, o);
         }
-        if (lane == 0) {
-          s_cs = (double)cs;
-          s_psq = ps;
-          s_flag = gave_up;
+        if (lane < C) {  // the slice's sums and flag to every rank
+          cl.map_shared_rank(s_csp, lane)[rank] = (double)cs;
+          cl.map_shared_rank(s_psp, lane)[rank] = ps;
+          cl.map_shared_rank(s_flags, lane)[rank] = gave_up;
         }
       }
-      // Split cluster barrier: each thread's writes read by peers (x* of the slice,
-      // the slice's sums, the flag) are released by its arrive; the value of the
-      // previous evaluation and the stop decision are made by the last warp while the
-      // barrier completes and the others gather x*, and are read after the gather.
+      // Split cluster barrier: each thread's stores into peers (x* of the slice, the
+      // slice's sums, the flag) are released by its arrive; the value of the previous
+      // evaluation and the stop decision are made by the last warp while the barrier
+      // completes.
       cl.barrier_arrive();
       if (warp == nw - 1) {
         // line partials of the previous evaluation (FP64, fixed order), the value, the
@@ -342,42 +348,15 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       }
     }
     cl.barrier_wait();
-    // ---------------- C: uniform exit decisions, gather x*, forward, supergradient, step
+    // ---------------- C: uniform exit decisions, forward, supergradient, step
     {
       int any = 0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) any |= (q < C) ? *cl.map_shared_rank(&s_flag, q) : 0;
+      for (int q = 0; q < 8; ++q) any |= (q < C) ? s_flags[q] : 0;
       if (any) {
         if (tid == 0) atomicExch(A.err, (int)DCOPF_ERR_TIMEOUT);
         break;  // uniform in the cluster
       }
-    }
-    if (warp < nw - 1) {
-      // x* of all gens from the cluster's slices, by every warp but the last (busy with
-      // the value); the remote loads of a thread are all issued before its stores
-      const int nt = (nw - 1) * 32;
-      float v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = tid + u * nt;
-        if (j < ng) {
-          const int q = j / SL;
-          v[u] = cl.map_shared_rank(xsl, q)[j - q * SL];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = tid + u * nt;
-        if (j < ng) xs[j] = v[u];
-      }
-      for (int j = tid + 4 * nt; j < ng; j += nt) {
-        const int q = j / SL;
-        xs[j] = cl.map_shared_rank(xsl, q)[j - q * SL];
-      }
-    }
-    if (tid >= 32 && tid < 32 + C) {
-      s_csp[tid - 32] = *cl.map_shared_rank(&s_cs, tid - 32);
-      s_psp[tid - 32] = *cl.map_shared_rank(&s_psq, tid - 32);
     }
     __syncthreads();
     if (pending) {
@@ -508,7 +487,7 @@ static size_t fused_smem(int ng, int rpc, int C, int NCL, bool phi) {
   int SL = (ng + C - 1) / C;
   int SLp = (SL + 1) & ~1;
   int NCLp = (NCL + 3) & ~3;
-  size_t f = 2 * (size_t)ngp + ((SL + 3) & ~3) + (size_t)SL * NCLp + 12 * (size_t)rpc;
+  size_t f = (size_t)((C * SL + 3) & ~3) + ngp + (size_t)SL * NCLp + 12 * (size_t)rpc;
   if (phi) f += (size_t)rpc * ng;
   return f * sizeof(float) + 5 * (size_t)SLp * sizeof(double);
 }
