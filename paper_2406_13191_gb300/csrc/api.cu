@@ -258,6 +258,9 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
           if (rr || cudaEventSynchronize(e1) != cudaSuccess ||
               cudaMemcpy(&done_iters, st.iter, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
               cudaMemcpy(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || derr) {
+            if (h->verbose)
+              fprintf(stderr, "[dcopf] fused tuning: cluster %d x %d CTAs failed (status %d, device %d)\n",
+                      Gs[i] / Cs[i], Cs[i], (int)rr, derr);
             cudaMemset(h->d_err, 0, sizeof(int));
             cudaGetLastError();
             per = 1e30f;

@@ -96,11 +96,11 @@ def certify(cfg, batch, repeat=10):
     print(json.dumps(res))
 
 
-def fused(repeat):
+def fused(repeat, verbose=False):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     gam = json.load(open(os.path.join(root, "tests", "golden", "gamma.json")))["1/0"]["gamma"]
     net, base = synth.network_for(1)
-    g = DcopfDual(net, device=0)
+    g = DcopfDual(net, device=0, verbose=verbose)
     kw = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=4000,
               path="fused")
     g.solve(base[None], target=[gam], **kw)
@@ -237,6 +237,7 @@ def main():
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--iters", type=int, default=16)
     ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--verbose", action="store_true", help="library setup and tuning messages")
     a = ap.parse_args()
     if a.mode == "batched":
         batched(a.config, a.batch, a.iters)
@@ -251,7 +252,7 @@ def main():
     elif a.mode == "togap":
         togap(a.config)
     else:
-        fused(a.repeat)
+        fused(a.repeat, a.verbose)
 
 
 if __name__ == "__main__":
