@@ -2,6 +2,7 @@
 // and the solve driver that alternates device iterations with FP64 certification.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <vector>
@@ -261,6 +262,7 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
             if (h->verbose)
               fprintf(stderr, "[dcopf] fused tuning: cluster %d x %d CTAs failed (status %d, device %d)\n",
                       Gs[i] / Cs[i], Cs[i], (int)rr, derr);
+            if (h->verbose && derr == DCOPF_ERR_UNSUPPORTED) fused_report_refusal(h);
             cudaMemset(h->d_err, 0, sizeof(int));
             cudaGetLastError();
             per = 1e30f;
@@ -385,6 +387,14 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
   // touching the GPU
   dcopf_dual* h = new dcopf_dual();
   h->verbose = opt && opt->verbose;
+  {
+    // DCOPF_FUSED_COOPERATIVE=0: launch the fused kernel as a plain cluster launch.
+    // Co-residency then rests on the occupancy-sized grid alone (the bounded waits
+    // still turn a missing cluster into DCOPF_ERR_TIMEOUT); profilers that rewrite
+    // cooperative launches keep the cluster shape of a plain one.
+    const char* e = getenv("DCOPF_FUSED_COOPERATIVE");
+    if (e && e[0] == '0') h->fused_coop = 0;
+  }
   std::string err;
   dcopf_status st = build_host_net(net, &h->host, &err, h->verbose);
   if (st != DCOPF_OK) {

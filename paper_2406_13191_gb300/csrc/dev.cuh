@@ -132,6 +132,13 @@ __device__ __forceinline__ double gen_min_value(double nu, double a, double c, d
 // only grows; `epoch` is the caller's private count of barriers passed.  The wait is
 // bounded by `timeout_ns` of wall-clock time: on expiry it records DCOPF_ERR_TIMEOUT
 // in *err and returns false, so callers can leave their loops.
+// Release-add at GPU scope: the writes that happen before it (the thread's own and,
+// through bar.sync, the CTA's) are visible to any thread whose acquire load reads the
+// result (PTX memory model, release pattern with cumulativity).
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

@@ -20,9 +20,10 @@
 //       f = Phi~_c x* + f0 on own rows (constraint (1c)); supergradient; FP64 line
 //       partial -> R[c]; projected step of own mu and of lambda.
 //
-// Synchronisation between clusters: after publishing its slice, each CTA makes its
-// writes visible (fence) and increments the arrival counter of its cluster rank; a CTA
-// then waits until all C counters show every cluster's arrival for this loop, and
+// Synchronisation between clusters: after publishing its slice, each CTA increments
+// the arrival counter of its cluster rank with a release-add (which makes the CTA's
+// writes visible); a CTA then waits, with acquire loads, until all C counters show
+// every cluster's arrival for this loop, and
 // reads the slice's partials (and the line partials R of the previous loop, written
 // before the writer's arrival) from L2.  Pc and R are double-buffered by loop parity:
 // a CTA can run at most one loop ahead of the slowest one, so a buffer is rewritten
@@ -105,6 +106,9 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
     if (C != A.C || G != A.G || dyn < A.smem_bytes || C > 8 || G > (int)blockDim.x) {
       if (tid == 0) atomicExch(A.err, (int)DCOPF_ERR_UNSUPPORTED);
+      if (tid == 0 && c == 0) {  // the shape this launch saw, for the host's diagnostics
+        A.cnt[8] = (unsigned)C; A.cnt[9] = (unsigned)G; A.cnt[10] = dyn; A.cnt[11] = blockDim.x;
+      }
       return;
     }
   }
@@ -226,17 +230,14 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       Pcb[(size_t)j * NCLp + cid] = s;
     }
     __syncthreads();
-    if (tid == 0) {
-      __threadfence();  // cumulative over the CTA's writes ordered by bar.sync
-      atomicAdd(A.cnt + rank, 1u);
-    }
+    if (tid == 0) red_release_add_u32(A.cnt + rank, 1u);  // releases the CTA's writes
     // ---------------- B: wait for every cluster's arrival, read partials (and R), x*
     {
       bool ok = true;
       if (tid < C) {
         // counter `tid` counts the arrivals of rank-tid CTAs: NCL per loop
+        // acquire loads; bar.sync below extends the ordering to the whole CTA
         ok = bounded_wait_geq(A.cnt + tid, (unsigned)NCL * (k + 1u), A.timeout_ns);
-        __threadfence();
       }
       const int waited_out = __syncthreads_or(ok ? 0 : 1);
       ok = waited_out == 0;
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       ml[r] = nlo > 0.f ? nlo : 0.f;
     }
     // the line partial: FP32 per thread and warp, FP64 across warps; published by
-    // the fence before the next arrival
+    // the release-add of the next arrival
     lacc = warp_sum(lacc);
     if (lane == 0) rsh[warp] = (double)lacc;  // rsh is free until the next phase B
     pending = true;
@@ -665,6 +666,25 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
 // increments; the wait must give up and report it.
 __global__ void k_wait_selftest(const unsigned* ctr, uint64_t timeout_ns, int* gave_up) {
   if (threadIdx.x == 0) *gave_up = bounded_wait_geq(ctr, 1u, timeout_ns) ? 0 : 1;
+}
+
+// Prints the launch shape a refused fused launch saw (its guard records it in the
+// counter block); for the verbose diagnostics of the shape tuner.
+void fused_report_refusal(dcopf_dual* h) {
+  unsigned v[4] = {0, 0, 0, 0};
+  const size_t ng = (size_t)h->dev.n_gen;
+  const int G = h->fused_G, C = std::max(1, h->fused_C);
+  const size_t NCLp = (size_t)((G / C + 3) & ~3);
+  const size_t pc_bytes = (2 * ng * NCLp * 4 + 255) & ~(size_t)255;
+  const size_t r_bytes = ((size_t)2 * G * 8 + 255) & ~(size_t)255;
+  if (!h->ws.misc.p || h->ws.misc.bytes < pc_bytes + r_bytes + 256) return;
+  if (cudaMemcpy(v, h->ws.misc.as<char>() + pc_bytes + r_bytes + 32, sizeof(v),
+                 cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  fprintf(stderr, "[dcopf] fused launch refused: saw cluster %u, grid %u, %u B dynamic shared, %u threads; "
+                  "sized for cluster %d, grid %d\n", v[0], v[1], v[2], v[3], C, G);
 }
 
 dcopf_status run_wait_selftest(dcopf_dual* h, long long timeout_ns, cudaStream_t s) {

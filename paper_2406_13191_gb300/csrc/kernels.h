@@ -242,6 +242,7 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int batch, const int* outage, const 
 // k_fused.cu
 dcopf_status run_wait_selftest(dcopf_dual* h, long long timeout_ns, cudaStream_t s);
 int fused_candidates(dcopf_dual* h, int* Cs, int* Gs, int cap);
+void fused_report_refusal(dcopf_dual* h);
 dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>& st, int max_iters,
                              double tol, cudaStream_t s);
 
