@@ -8,15 +8,17 @@
 // every CTA and updated identically (same inputs, same order).
 //
 // Iteration k (all CTAs):
-//   A   eta = mu_hi - mu_lo on own rows; partial adjoint Phi~_c^T eta_c for all gens
-//       into own shared memory                                (eq. (6): C^T mu)
-//   A2  [cluster sync] CTA r of a cluster sums its gens slice S_r over the cluster's
-//       partials (distributed shared memory) and publishes them -> Pc[j][cluster]
+//   A   eta = mu_hi - mu_lo on own rows; partial adjoint Phi~_c^T eta_c for all gens,
+//       each stored into the shared memory of the rank owning the gen's slice
+//                                                             (eq. (6): C^T mu)
+//   A2  [partials arrived] CTA r of a cluster sums its gens slice S_r over the
+//       cluster's partials and publishes them -> Pc[j][cluster]
 //   B   every cluster reads Pc for its slices and the line partials R of the previous
 //       evaluation, sums the clusters in a fixed order, takes the closed-form
-//       minimiser x*_j (eq. (6) / eq. (16)) and partial cost / dispatch sums; the
-//       previous evaluation's dual value -> best point, stop tests
-//   C   [cluster sync] gather x* of all gens from the cluster (DSMEM); forward
+//       minimiser x*_j (eq. (6) / eq. (16)), stored into every rank of the
+//       cluster, and partial cost / dispatch sums; the previous evaluation's dual
+//       value -> best point, stop tests
+//   C   [x* arrived] forward
 //       f = Phi~_c x* + f0 on own rows (constraint (1c)); supergradient; FP64 line
 //       partial -> R[c]; projected step of own mu and of lambda.
 //
@@ -27,9 +29,21 @@
 // reads the slice's partials (and the line partials R of the previous loop, written
 // before the writer's arrival) from L2.  Pc and R are double-buffered by loop parity:
 // a CTA can run at most one loop ahead of the slowest one, so a buffer is rewritten
-// only after all its readers are done.  Every wait is bounded; a wait that gives up
-// is made uniform across the cluster before any CTA leaves, so no CTA exits while a
-// peer may still read its shared memory.
+// only after all its readers are done.
+//
+// Exchanges inside a cluster: asynchronous stores into the peers' shared memory
+// (st.async), each counted on the receiving CTA's transaction barrier (an mbarrier
+// whose phase completes when its own arrival and every expected byte are in); no
+// cluster-wide barrier per loop.  Write-after-read safety of the receive buffers
+// follows from the data dependencies: a peer stores loop k+1's partials only after it
+// received this CTA's x* of loop k (sent after this CTA consumed loop k's partials),
+// and loop k+1's x* only after it received this CTA's loop k+1 partials (sent after
+// this CTA's forward of loop k read x*).
+//
+// Every wait is bounded.  Wait flags travel with x*, so a wait that gives up stops
+// every CTA of the cluster at the same loop, or (when a CTA's own x* wait gives up)
+// makes its peers' next waits give up; a final cluster barrier keeps every CTA's
+// shared memory alive until no peer can store into it.
 // Every cluster computes the same x* and the same dual value from the same data in
 // the same order, so stop decisions are identical everywhere.
 #include <cooperative_groups.h>
@@ -39,6 +53,7 @@
 
 #include "dev.cuh"
 #include "kernels.h"
+#include "umma.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -145,6 +160,9 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   __shared__ double s_csp[8];     // the cluster's slice cost sums (written by peers)
   __shared__ long long s_psp[8];  // the cluster's slice dispatch sums, fixed point (peers)
   __shared__ int s_flags[8];      // the cluster's gave-up flags (written by peers)
+  // transaction barriers of the peers' asynchronous stores: [0] adjoint partials of own
+  // slice, [1] x* of the other slices with the slice sums and flags
+  __shared__ __align__(8) uint64_t s_mb[2];
   __shared__ double s_pw[6];    // decay^(t-1), 1 - beta1^t, 1 - beta2^t; running powers
   __shared__ float s_pwf[4];    // FP32 step factors: alpha decay^(t-1), bias corrections, alpha_lambda decay^(t-1)
 
@@ -185,20 +203,39 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   bool pending = false;
   double cost_t = 0.0, psum_t = 0.0;
   const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  __syncthreads();
+  // bytes the peers store into this CTA per loop: their partials of own slice, and
+  // their x* slices with two 8-byte sums and a 4-byte flag each
+  const uint32_t tx_part = (uint32_t)((C - 1) * nj * 4);
+  const uint32_t tx_x = (uint32_t)((ng - nj) * 4 + (C - 1) * 20);
+  if (tid == 0) {
+    umma::mbar_init(&s_mb[0], 1);
+    umma::mbar_init(&s_mb[1], 1);
+    umma::fence_mbar_init();
+  }
+  cl.sync();  // every rank's barriers initialised before any store into it
 
   for (unsigned k = 0;; ++k) {
     float* Pcb = A.Pc + (size_t)(k & 1u) * ng * NCLp;
     const double* Rprev = A.R + (size_t)((k + 1u) & 1u) * G;  // written in loop k-1
     double* Rcur = A.R + (size_t)(k & 1u) * G;
     // ---------------- A: partial adjoint of own rows (4 gens per thread in flight),
-    // each stored straight into the shared memory of the rank that owns the gen's slice
-    // (remote stores do not wait for a round trip; the cluster barrier publishes them)
+    // each sent straight into the shared memory of the rank that owns the gen's slice
+    // by an asynchronous store counted on that rank's transaction barrier (no round
+    // trip, no cluster-wide barrier)
+    if (tid == 0) {
+      // this loop's phase of both barriers: one arrival each, plus the bytes expected
+      // (a peer's stores may land before this; the phase needs both)
+      umma::mbar_arrive_expect_tx(&s_mb[0], tx_part);
+      umma::mbar_arrive_expect_tx(&s_mb[1], tx_x);
+    }
     for (int r = tid; r < nr; r += blockDim.x) eta[r] = mh[r] - ml[r];
     __syncthreads();
     auto push = [&](int j, float v) {
       const int q = j / SL;
-      cl.map_shared_rank(recv, q)[rank * SL + (j - q * SL)] = v;
+      float* dst = recv + rank * SL + (j - q * SL);
+      if (q == rank) *dst = v;
+      else umma::st_async_b32(umma::cluster_addr(dst, q), __float_as_uint(v),
+                              umma::cluster_addr(&s_mb[0], q));
     };
     for (int jb = tid; jb < ng; jb += 4 * blockDim.x) {
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -217,7 +254,8 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       if (v2) push(jb + 2 * b, a2);
       if (v3) push(jb + 3 * b, a3);
     }
-    cl.sync();
+    __syncthreads();  // own rank's partials
+    const bool part_ok = umma::mbar_wait_cluster(&s_mb[0], k & 1u, A.timeout_ns);
     // ---------------- A2: cluster sum of own slice (fixed rank order), published
     for (int jj = tid; jj < nj; jj += blockDim.x) {
       const int j = j0 + jj;
@@ -233,11 +271,11 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     if (tid == 0) red_release_add_u32(A.cnt + rank, 1u);  // releases the CTA's writes
     // ---------------- B: wait for every cluster's arrival, read partials (and R), x*
     {
-      bool ok = true;
+      bool ok = part_ok;
       if (tid < C) {
         // counter `tid` counts the arrivals of rank-tid CTAs: NCL per loop
         // acquire loads; bar.sync below extends the ordering to the whole CTA
-        ok = bounded_wait_geq(A.cnt + tid, (unsigned)NCL * (k + 1u), A.timeout_ns);
+        ok = bounded_wait_geq(A.cnt + tid, (unsigned)NCL * (k + 1u), A.timeout_ns) && ok;
       }
       const int waited_out = __syncthreads_or(ok ? 0 : 1);
       ok = waited_out == 0;
@@ -290,9 +328,12 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
         const double ct = gk[jj], sg = gk[SLp + jj], mq = gk[2 * SLp + jj];
         const double w = ct + sg * lam + (double)s;
         const float x = inner_x<float>((float)w, (float)mq);
+        xs[j0 + jj] = x;  // x* to every rank
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-          if (q < C) cl.map_shared_rank(xs, q)[j0 + jj] = x;  // x* to every rank
+          if (q < C && q != rank)
+            umma::st_async_b32(umma::cluster_addr(xs + j0 + jj, q), __float_as_uint(x),
+                               umma::cluster_addr(&s_mb[1], q));
         csf += fmaf(fmaf((float)mq, x, (float)ct), x, (float)gk[3 * SLp + jj]);
         psq += __double2ll_rn((gk[4 * SLp + jj] + sg * (double)x) * A.pscale);
       }
@@ -310,16 +351,22 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
           ps += __shfl_xor_sync(0xffffffffu, ps, o);
         }
         if (lane < C) {  // the slice's sums and flag to every rank
-          cl.map_shared_rank(s_csp, lane)[rank] = (double)cs;
-          cl.map_shared_rank(s_psp, lane)[rank] = ps;
-          cl.map_shared_rank(s_flags, lane)[rank] = gave_up;
+          const double csd = (double)cs;
+          if (lane == rank) {
+            s_csp[rank] = csd;
+            s_psp[rank] = ps;
+            s_flags[rank] = gave_up;
+          } else {
+            const uint32_t bar = umma::cluster_addr(&s_mb[1], lane);
+            umma::st_async_b64(umma::cluster_addr(s_csp + rank, lane),
+                               (uint64_t)__double_as_longlong(csd), bar);
+            umma::st_async_b64(umma::cluster_addr(s_psp + rank, lane), (uint64_t)ps, bar);
+            umma::st_async_b32(umma::cluster_addr(s_flags + rank, lane), (uint32_t)gave_up, bar);
+          }
         }
       }
-      // Split cluster barrier: each thread's stores into peers (x* of the slice, the
-      // slice's sums, the flag) are released by its arrive; the value of the previous
-      // evaluation and the stop decision are made by the last warp while the barrier
-      // completes.
-      cl.barrier_arrive();
+      // The value of the previous evaluation and the stop decision are made by the
+      // last warp while the peers' x* and sums arrive.
       if (warp == nw - 1) {
         // line partials of the previous evaluation (FP64, fixed order), the value, the
         // best point and the stop decision, made once and broadcast
@@ -348,18 +395,21 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
         }
       }
     }
-    cl.barrier_wait();
     // ---------------- C: uniform exit decisions, forward, supergradient, step
     {
-      int any = 0;
+      // every rank's x* slice, sums and flag (peers' through the transaction barrier,
+      // own through bar.sync), and the last warp's decision
+      int any = __syncthreads_or(
+          umma::mbar_wait_cluster(&s_mb[1], k & 1u, A.timeout_ns) ? 0 : 1);
 #pragma unroll
       for (int q = 0; q < 8; ++q) any |= (q < C) ? s_flags[q] : 0;
       if (any) {
+        // uniform in the cluster when every rank's flag arrived; a rank whose own wait
+        // gave up leaves alone and its peers' bounded waits for it give up next loop
         if (tid == 0) atomicExch(A.err, (int)DCOPF_ERR_TIMEOUT);
-        break;  // uniform in the cluster
+        break;
       }
     }
-    __syncthreads();
     if (pending) {
       const double val = s_dec[0];
       if (s_dec[1] != 0.0) {
