@@ -149,7 +149,6 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
         *l1 = row + 5 * rpc, *l2 = row + 6 * rpc, *ph = row + 7 * rpc, *pl = row + 8 * rpc,
         *fmx = row + 9 * rpc, *fmn = row + 10 * rpc, *f0 = row + 11 * rpc;
   float* phis = row + 12 * rpc;                  // [rpc][ng] when resident
-  __shared__ double red[32];
   __shared__ double rsh[256];   // line partials of the previous evaluation, one per CTA
   __shared__ double s_dec[2];   // [0] value of the evaluation, [1] 1 if it improved the best
   __shared__ double s_vbase;    // cost + lambda (sum p - D) of the pending evaluation
@@ -159,12 +158,14 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   __shared__ long long redq[32];
   __shared__ double s_csp[8];     // the cluster's slice cost sums (written by peers)
   __shared__ long long s_psp[8];  // the cluster's slice dispatch sums, fixed point (peers)
+  __shared__ double s_cspc[8];    // copies of the two above for the lambda step, taken before
+  __shared__ long long s_pspc[8]; // the peers can store the next loop's sums
   __shared__ int s_flags[8];      // the cluster's gave-up flags (written by peers)
   // transaction barriers of the peers' asynchronous stores: [0] adjoint partials of own
   // slice, [1] x* of the other slices with the slice sums and flags
   __shared__ __align__(8) uint64_t s_mb[2];
   __shared__ double s_pw[6];    // decay^(t-1), 1 - beta1^t, 1 - beta2^t; running powers
-  __shared__ float s_pwf[4];    // FP32 step factors: alpha decay^(t-1), bias corrections, alpha_lambda decay^(t-1)
+  __shared__ float s_pwf[8];    // FP32 step factors by loop parity: alpha decay^(t-1), bias corrections, alpha_lambda decay^(t-1)
 
   const float* phi = A.phi_in_smem ? phis : (N.phi32 + (size_t)r0 * ng);
   if (A.phi_in_smem)
@@ -201,7 +202,6 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   double best_lam = st.best_lam[0];
   int cand = 0;
   bool pending = false;
-  double cost_t = 0.0, psum_t = 0.0;
   const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   // bytes the peers store into this CTA per loop: their partials of own slice, and
   // their x* slices with two 8-byte sums and a 4-byte flag each
@@ -276,6 +276,42 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
         // counter `tid` counts the arrivals of rank-tid CTAs: NCL per loop
         // acquire loads; bar.sync below extends the ordering to the whole CTA
         ok = bounded_wait_geq(A.cnt + tid, (unsigned)NCL * (k + 1u), A.timeout_ns) && ok;
+      }
+      // Scalar work of the loop, by lane 0 of the last two warps while the counters
+      // are polled (off the critical path):
+      if (tid == (int)blockDim.x - 32 && pending) {
+        // the previous loop's lambda step, from the cost and dispatch totals of its
+        // evaluation (FP64 over the cluster's slice sums, the dispatch exactly in
+        // fixed point): the value base cost + lambda (sum p - D), then the direction
+        // in FP32 and the update of lambda in FP64
+        double cost_t = 0.0;
+        long long ps2 = 0;
+        for (int q = 0; q < C; ++q) { cost_t += s_cspc[q]; ps2 += s_pspc[q]; }
+        const double psum_t = (double)ps2 * A.pinv;
+        double lam = s_lam[0];
+        s_lam[3] = lam;
+        s_vbase = cost_t + lam * (psum_t - demand);  // the value without its line sum
+        float s1 = (float)s_lam[1], s2 = (float)s_lam[2];
+        const float gl = (float)(psum_t - demand);
+        const float* pf = s_pwf + ((k + 1u) & 1u) * 4;  // the previous loop's factors
+        const float th = fused_rule_f(RF, 0.f, gl, s1, s2, pf[3], pf[1], pf[2]);
+        lam += (double)th;
+        s_lam[0] = lam; s_lam[1] = s1; s_lam[2] = s2;
+      } else if (tid == (int)blockDim.x - 64) {
+        // this loop's step-size factors from the running powers (FP64), with FP32
+        // copies for every thread (double-buffered by loop parity: the lambda step
+        // above reads the previous loop's at the same time)
+        float* pf = s_pwf + (k & 1u) * 4;
+        s_pw[0] = s_pw[3];
+        s_pw[4] *= A.P.beta1;
+        s_pw[5] *= A.P.beta2;
+        s_pw[3] *= A.P.decay;
+        s_pw[1] = 1.0 - s_pw[4];
+        s_pw[2] = 1.0 - s_pw[5];
+        pf[0] = (float)(A.P.alpha * s_pw[0]);
+        pf[1] = (float)s_pw[1];
+        pf[2] = (float)s_pw[2];
+        pf[3] = (float)(A.P.alpha_lambda * s_pw[0]);
       }
       const int waited_out = __syncthreads_or(ok ? 0 : 1);
       ok = waited_out == 0;
@@ -421,25 +457,8 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       pending = false;
     }
     if (cand) break;  // uniform everywhere: every CTA assembled the same value
-    if (tid == 0) {
-      double cs2 = 0.0;
-      long long ps2 = 0;
-      for (int q = 0; q < C; ++q) { cs2 += s_csp[q]; ps2 += s_psp[q]; }
-      red[0] = cs2;
-      red[1] = (double)ps2 * A.pinv;
-    } else if (tid == 64) {
-      // step-size factors of the next step from the running powers (FP64), and their
-      // FP32 copies for every thread
-      s_pw[0] = s_pw[3];
-      s_pw[4] *= A.P.beta1;
-      s_pw[5] *= A.P.beta2;
-      s_pw[3] *= A.P.decay;
-      s_pw[1] = 1.0 - s_pw[4];
-      s_pw[2] = 1.0 - s_pw[5];
-      s_pwf[0] = (float)(A.P.alpha * s_pw[0]);
-      s_pwf[1] = (float)s_pw[1];
-      s_pwf[2] = (float)s_pw[2];
-      s_pwf[3] = (float)(A.P.alpha_lambda * s_pw[0]);
+    if (tid == (int)blockDim.x - 32) {
+      for (int q = 0; q < C; ++q) { s_cspc[q] = s_csp[q]; s_pspc[q] = s_psp[q]; }
     }
     // forward on own rows: a warp per row, 3 rows of a warp in flight
     for (int rb = warp; rb < nr; rb += 3 * nw) {
@@ -464,36 +483,28 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       }
     }
     __syncthreads();
-    cost_t = red[0];
-    psum_t = red[1];
     t += 1;
-    const float bc1 = s_pwf[1];
-    const float bc2 = s_pwf[2];
-    const float am = s_pwf[0];
-    if (tid == 32) {
-      // lambda step, concurrent with the line steps: the direction in FP32, the update
-      // of lambda in FP64
-      double lam = s_lam[0];
-      s_lam[3] = lam;
-      s_vbase = cost_t + lam * (psum_t - demand);  // the value without its line sum
-      float s1 = (float)s_lam[1], s2 = (float)s_lam[2];
-      const float al = s_pwf[3];
-      const float gl = (float)(psum_t - demand);
-      const float th = fused_rule_f(RF, 0.f, gl, s1, s2, al, bc1, bc2);
-      lam += (double)th;
-      s_lam[0] = lam; s_lam[1] = s1; s_lam[2] = s2;
-    }
+    const float* pf = s_pwf + (k & 1u) * 4;
+    const float bc1 = pf[1];
+    const float bc2 = pf[2];
+    const float am = pf[0];
+    // projected steps of own lines: item i < nr steps mu_hi of row i, item nr + i
+    // steps mu_lo of row i (two threads per line); the lambda step of this loop runs
+    // in the next loop's A2
     float lacc = 0.f;
-    for (int r = tid; r < nr; r += blockDim.x) {
-      float f = eta[r];
-      float gh = f - fmx[r], gl = fmn[r] - f;
-      lacc = fmaf(mh[r], gh, fmaf(ml[r], gl, lacc));
-      ph[r] = mh[r];
-      pl[r] = ml[r];
-      float nh = fused_rule_f(RF, mh[r], gh, h1[r], h2[r], am, bc1, bc2);
-      float nlo = fused_rule_f(RF, ml[r], gl, l1[r], l2[r], am, bc1, bc2);
-      mh[r] = nh > 0.f ? nh : 0.f;
-      ml[r] = nlo > 0.f ? nlo : 0.f;
+    for (int i = tid; i < 2 * nr; i += blockDim.x) {
+      const bool hi = i < nr;
+      const int r = hi ? i : i - nr;
+      const float f = eta[r];
+      const float g = hi ? f - fmx[r] : fmn[r] - f;
+      float* mu = hi ? mh : ml;
+      float* s1 = hi ? h1 : l1;
+      float* s2 = hi ? h2 : l2;
+      const float m0 = mu[r];
+      lacc = fmaf(m0, g, lacc);
+      (hi ? ph : pl)[r] = m0;
+      const float nm = fused_rule_f(RF, m0, g, s1[r], s2[r], am, bc1, bc2);
+      mu[r] = nm > 0.f ? nm : 0.f;
     }
     // the line partial: FP32 per thread and warp, FP64 across warps; published by
     // the release-add of the next arrival
@@ -502,8 +513,8 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     pending = true;
     __syncthreads();
     if (tid == 0) {
-      // only the warps that own rows (row r belongs to thread r) contribute
-      const int nwr = min(nw, (nr + 31) >> 5);
+      // only the warps that own step items (item i belongs to thread i) contribute
+      const int nwr = min(nw, (2 * nr + 31) >> 5);
       double l = 0.0;
       for (int q = 0; q < nwr; ++q) l += rsh[q];
       Rcur[c] = l;
