@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   __shared__ double s_pw[6];    // decay^(t-1), 1 - beta1^t, 1 - beta2^t; running powers
   __shared__ float s_pwf[8];    // FP32 step factors by loop parity: alpha decay^(t-1), bias corrections, alpha_lambda decay^(t-1)
 
-  const float* phi = A.phi_in_smem ? phis : (N.phi32 + (size_t)r0 * ng);
+  const float* phig = N.phi32 + (size_t)r0 * ng;  // own rows in global memory
   if (A.phi_in_smem)
     for (int q = tid; q < nr * ng; q += blockDim.x) phis[q] = N.phi32[(size_t)r0 * ng + q];
   for (int jj = tid; jj < nj; jj += blockDim.x) {
@@ -237,23 +237,30 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       else umma::st_async_b32(umma::cluster_addr(dst, q), __float_as_uint(v),
                               umma::cluster_addr(&s_mb[0], q));
     };
-    for (int jb = tid; jb < ng; jb += 4 * blockDim.x) {
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      const int b = blockDim.x;
-      const bool v1 = jb + b < ng, v2 = jb + 2 * b < ng, v3 = jb + 3 * b < ng;
-      for (int r = 0; r < nr; ++r) {
-        const float e = eta[r];
-        const float* pr = phi + (size_t)r * ng + jb;
-        a0 = fmaf(pr[0], e, a0);
-        if (v1) a1 = fmaf(pr[b], e, a1);
-        if (v2) a2 = fmaf(pr[2 * b], e, a2);
-        if (v3) a3 = fmaf(pr[3 * b], e, a3);
+    // (instantiated once per home of Phi~ rows, so that shared-memory rows are read
+    // with shared-memory loads rather than generic ones)
+    auto adjoint = [&](const float* rows) {
+      for (int jb = tid; jb < ng; jb += 4 * blockDim.x) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const int b = blockDim.x;
+        const bool v1 = jb + b < ng, v2 = jb + 2 * b < ng, v3 = jb + 3 * b < ng;
+#pragma unroll 4
+        for (int r = 0; r < nr; ++r) {
+          const float e = eta[r];
+          const float* pr = rows + (size_t)r * ng + jb;
+          a0 = fmaf(pr[0], e, a0);
+          if (v1) a1 = fmaf(pr[b], e, a1);
+          if (v2) a2 = fmaf(pr[2 * b], e, a2);
+          if (v3) a3 = fmaf(pr[3 * b], e, a3);
+        }
+        push(jb, a0);
+        if (v1) push(jb + b, a1);
+        if (v2) push(jb + 2 * b, a2);
+        if (v3) push(jb + 3 * b, a3);
       }
-      push(jb, a0);
-      if (v1) push(jb + b, a1);
-      if (v2) push(jb + 2 * b, a2);
-      if (v3) push(jb + 3 * b, a3);
-    }
+    };
+    if (A.phi_in_smem) adjoint(phis);
+    else adjoint(phig);
     __syncthreads();  // own rank's partials
     const bool part_ok = umma::mbar_wait_cluster(&s_mb[0], k & 1u, A.timeout_ns);
     // ---------------- A2: cluster sum of own slice (fixed rank order), published
@@ -461,27 +468,32 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       for (int q = 0; q < C; ++q) { s_cspc[q] = s_csp[q]; s_pspc[q] = s_psp[q]; }
     }
     // forward on own rows: a warp per row, 3 rows of a warp in flight
-    for (int rb = warp; rb < nr; rb += 3 * nw) {
-      const bool v1 = rb + nw < nr, v2 = rb + 2 * nw < nr;
-      const float* p0 = phi + (size_t)rb * ng;
-      const float* p1 = p0 + (size_t)nw * ng;
-      const float* p2 = p1 + (size_t)nw * ng;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-      for (int j = lane; j < ng; j += 32) {
-        const float x = xs[j];
-        a0 = fmaf(p0[j], x, a0);
-        if (v1) a1 = fmaf(p1[j], x, a1);
-        if (v2) a2 = fmaf(p2[j], x, a2);
+    auto forward = [&](const float* rows) {
+      for (int rb = warp; rb < nr; rb += 3 * nw) {
+        const bool v1 = rb + nw < nr, v2 = rb + 2 * nw < nr;
+        const float* p0 = rows + (size_t)rb * ng;
+        const float* p1 = p0 + (size_t)nw * ng;
+        const float* p2 = p1 + (size_t)nw * ng;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 4
+        for (int j = lane; j < ng; j += 32) {
+          const float x = xs[j];
+          a0 = fmaf(p0[j], x, a0);
+          if (v1) a1 = fmaf(p1[j], x, a1);
+          if (v2) a2 = fmaf(p2[j], x, a2);
+        }
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        a2 = warp_sum(a2);
+        if (lane == 0) {
+          eta[rb] = a0 + f0[rb];  // eta[] reused as the flow of own rows
+          if (v1) eta[rb + nw] = a1 + f0[rb + nw];
+          if (v2) eta[rb + 2 * nw] = a2 + f0[rb + 2 * nw];
+        }
       }
-      a0 = warp_sum(a0);
-      a1 = warp_sum(a1);
-      a2 = warp_sum(a2);
-      if (lane == 0) {
-        eta[rb] = a0 + f0[rb];  // eta[] reused as the flow of own rows
-        if (v1) eta[rb + nw] = a1 + f0[rb + nw];
-        if (v2) eta[rb + 2 * nw] = a2 + f0[rb + 2 * nw];
-      }
-    }
+    };
+    if (A.phi_in_smem) forward(phis);
+    else forward(phig);
     __syncthreads();
     t += 1;
     const float* pf = s_pwf + (k & 1u) * 4;
