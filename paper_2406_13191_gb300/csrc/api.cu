@@ -262,7 +262,7 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
             if (h->verbose)
               fprintf(stderr, "[dcopf] fused tuning: cluster %d x %d CTAs failed (status %d, device %d)\n",
                       Gs[i] / Cs[i], Cs[i], (int)rr, derr);
-            if (h->verbose && derr == DCOPF_ERR_UNSUPPORTED) fused_report_refusal(h);
+            if (h->verbose) fused_report_refusal(h);
             cudaMemset(h->d_err, 0, sizeof(int));
             cudaGetLastError();
             per = 1e30f;

@@ -67,7 +67,9 @@ struct FusedArgs {
   const double* demand;          // [1] total demand of the instance (device)
   float* Pc;                     // [2][n_gen][NCLp] cluster partial adjoints
   double* R;                     // [2][G] line partials of the dual value
-  unsigned* cnt;                 // [8] arrival counters, one per cluster rank
+  unsigned* cnt;                 // [8] arrival counters, one per cluster rank; [16..19] the
+                                 // shape a refused launch saw; [20..23] the first wait
+                                 // that gave up
   int* err;
   double pscale, pinv;           // fixed-point scale of the dispatch sum and its inverse
   int max_iters;
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     if (C != A.C || G != A.G || dyn < A.smem_bytes || C > 8 || G > (int)blockDim.x) {
       if (tid == 0) atomicExch(A.err, (int)DCOPF_ERR_UNSUPPORTED);
       if (tid == 0 && c == 0) {  // the shape this launch saw, for the host's diagnostics
-        A.cnt[8] = (unsigned)C; A.cnt[9] = (unsigned)G; A.cnt[10] = dyn; A.cnt[11] = blockDim.x;
+        A.cnt[16] = (unsigned)C; A.cnt[17] = (unsigned)G; A.cnt[18] = dyn; A.cnt[19] = blockDim.x;
       }
       return;
     }
@@ -158,8 +160,8 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   __shared__ long long redq[32];
   __shared__ double s_csp[8];     // the cluster's slice cost sums (written by peers)
   __shared__ long long s_psp[8];  // the cluster's slice dispatch sums, fixed point (peers)
-  __shared__ double s_cspc[8];    // copies of the two above for the lambda step, taken before
-  __shared__ long long s_pspc[8]; // the peers can store the next loop's sums
+  __shared__ double s_cspc[8];    // copies of the two above for the lambda step, taken
+  __shared__ long long s_pspc[8]; // before the peers can store the next loop's sums
   __shared__ int s_flags[8];      // the cluster's gave-up flags (written by peers)
   // transaction barriers of the peers' asynchronous stores: [0] adjoint partials of own
   // slice, [1] x* of the other slices with the slice sums and flags
@@ -213,6 +215,13 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     umma::fence_mbar_init();
   }
   cl.sync();  // every rank's barriers initialised before any store into it
+  // the first wait that gives up records (which wait, loop, CTA, thread) for the host's
+  // diagnostics: 1 partials of own slice, 2 arrival counters, 3 x* and sums
+  auto record_gave_up = [&](unsigned what, unsigned loop) {
+    if (atomicCAS(A.cnt + 20, 0u, what) == 0u) {
+      A.cnt[21] = loop; A.cnt[22] = (unsigned)c; A.cnt[23] = (unsigned)tid;
+    }
+  };
 
   for (unsigned k = 0;; ++k) {
     float* Pcb = A.Pc + (size_t)(k & 1u) * ng * NCLp;
@@ -263,6 +272,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     else adjoint(phig);
     __syncthreads();  // own rank's partials
     const bool part_ok = umma::mbar_wait_cluster(&s_mb[0], k & 1u, A.timeout_ns);
+    if (!part_ok) record_gave_up(1, k);
     // ---------------- A2: cluster sum of own slice (fixed rank order), published
     for (int jj = tid; jj < nj; jj += blockDim.x) {
       const int j = j0 + jj;
@@ -282,7 +292,9 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       if (tid < C) {
         // counter `tid` counts the arrivals of rank-tid CTAs: NCL per loop
         // acquire loads; bar.sync below extends the ordering to the whole CTA
-        ok = bounded_wait_geq(A.cnt + tid, (unsigned)NCL * (k + 1u), A.timeout_ns) && ok;
+        const bool got = bounded_wait_geq(A.cnt + tid, (unsigned)NCL * (k + 1u), A.timeout_ns);
+        if (!got) record_gave_up(2, k);
+        ok = got && ok;
       }
       // Scalar work of the loop, by lane 0 of the last two warps while the counters
       // are polled (off the critical path):
@@ -442,8 +454,9 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     {
       // every rank's x* slice, sums and flag (peers' through the transaction barrier,
       // own through bar.sync), and the last warp's decision
-      int any = __syncthreads_or(
-          umma::mbar_wait_cluster(&s_mb[1], k & 1u, A.timeout_ns) ? 0 : 1);
+      const bool x_ok = umma::mbar_wait_cluster(&s_mb[1], k & 1u, A.timeout_ns);
+      if (!x_ok) record_gave_up(3, k);
+      int any = __syncthreads_or(x_ok ? 0 : 1);
 #pragma unroll
       for (int q = 0; q < 8; ++q) any |= (q < C) ? s_flags[q] : 0;
       if (any) {
@@ -741,23 +754,27 @@ __global__ void k_wait_selftest(const unsigned* ctr, uint64_t timeout_ns, int* g
   if (threadIdx.x == 0) *gave_up = bounded_wait_geq(ctr, 1u, timeout_ns) ? 0 : 1;
 }
 
-// Prints the launch shape a refused fused launch saw (its guard records it in the
-// counter block); for the verbose diagnostics of the shape tuner.
+// Prints the launch shape a refused fused launch saw and the first wait that gave up
+// (both recorded in the counter block); for the verbose diagnostics of the shape tuner.
 void fused_report_refusal(dcopf_dual* h) {
-  unsigned v[4] = {0, 0, 0, 0};
+  unsigned v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   const size_t ng = (size_t)h->dev.n_gen;
   const int G = h->fused_G, C = std::max(1, h->fused_C);
   const size_t NCLp = (size_t)((G / C + 3) & ~3);
   const size_t pc_bytes = (2 * ng * NCLp * 4 + 255) & ~(size_t)255;
   const size_t r_bytes = ((size_t)2 * G * 8 + 255) & ~(size_t)255;
   if (!h->ws.misc.p || h->ws.misc.bytes < pc_bytes + r_bytes + 256) return;
-  if (cudaMemcpy(v, h->ws.misc.as<char>() + pc_bytes + r_bytes + 32, sizeof(v),
+  if (cudaMemcpy(v, h->ws.misc.as<char>() + pc_bytes + r_bytes + 64, sizeof(v),
                  cudaMemcpyDeviceToHost) != cudaSuccess) {
     cudaGetLastError();
     return;
   }
-  fprintf(stderr, "[dcopf] fused launch refused: saw cluster %u, grid %u, %u B dynamic shared, %u threads; "
-                  "sized for cluster %d, grid %d\n", v[0], v[1], v[2], v[3], C, G);
+  if (v[0])
+    fprintf(stderr, "[dcopf] fused launch refused: saw cluster %u, grid %u, %u B dynamic shared, %u threads; "
+                    "sized for cluster %d, grid %d\n", v[0], v[1], v[2], v[3], C, G);
+  if (v[4])
+    fprintf(stderr, "[dcopf] fused wait gave up: kind %u (1 partials, 2 arrivals, 3 x*), loop %u, CTA %u, "
+                    "thread %u\n", v[4], v[5], v[6], v[7]);
 }
 
 dcopf_status run_wait_selftest(dcopf_dual* h, long long timeout_ns, cudaStream_t s) {
