@@ -163,9 +163,10 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   __shared__ double s_cspc[8];    // copies of the two above for the lambda step, taken
   __shared__ long long s_pspc[8]; // before the peers can store the next loop's sums
   __shared__ int s_flags[8];      // the cluster's gave-up flags (written by peers)
-  // transaction barriers of the peers' asynchronous stores: [0] adjoint partials of own
-  // slice, [1] x* of the other slices with the slice sums and flags
-  __shared__ __align__(8) uint64_t s_mb[2];
+  // transaction barriers: [0] the peers' asynchronous stores of adjoint partials of own
+  // slice, [1] theirs of x* of the other slices with the slice sums and flags, [2] the
+  // bulk copy of own slice's partials of every cluster
+  __shared__ __align__(8) uint64_t s_mb[3];
   __shared__ double s_pw[6];    // decay^(t-1), 1 - beta1^t, 1 - beta2^t; running powers
   __shared__ float s_pwf[8];    // FP32 step factors by loop parity: alpha decay^(t-1), bias corrections, alpha_lambda decay^(t-1)
 
@@ -212,11 +213,13 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   if (tid == 0) {
     umma::mbar_init(&s_mb[0], 1);
     umma::mbar_init(&s_mb[1], 1);
+    umma::mbar_init(&s_mb[2], 1);
     umma::fence_mbar_init();
   }
   cl.sync();  // every rank's barriers initialised before any store into it
   // the first wait that gives up records (which wait, loop, CTA, thread) for the host's
-  // diagnostics: 1 partials of own slice, 2 arrival counters, 3 x* and sums
+  // diagnostics: 1 partials of own slice, 2 arrival counters, 3 x* and sums, 4 the
+  // bulk copy
   auto record_gave_up = [&](unsigned what, unsigned loop) {
     if (atomicCAS(A.cnt + 20, 0u, what) == 0u) {
       A.cnt[21] = loop; A.cnt[22] = (unsigned)c; A.cnt[23] = (unsigned)tid;
@@ -335,24 +338,22 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       const int waited_out = __syncthreads_or(ok ? 0 : 1);
       ok = waited_out == 0;
       double rv = 0.0;
-      if (ok) {
-        if (pending && tid < G) rv = __ldcg(Rprev + tid);
-        const int n4 = nj * NCLp / 4;
-        const float4* src = (const float4*)(Pcb + (size_t)j0 * NCLp);
-        // all loads of a batch are issued before any store: one round trip per batch
-        for (int base = 0; base < n4; base += 8 * (int)blockDim.x) {
-          float4 v[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int q = base + u * blockDim.x + tid;
-            if (q < n4) v[u] = __ldcg(src + q);
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int q = base + u * blockDim.x + tid;
-            if (q < n4) ((float4*)tmp)[q] = v[u];
-          }
+      if (tid == 0) {
+        // the slice's partials of every cluster ([nj][NCLp] floats, contiguous) in one
+        // bulk copy; after the acquire, a proxy fence orders it behind the data
+        const uint32_t bytes = (uint32_t)(nj * NCLp * 4);
+        if (ok && bytes > 0) {
+          umma::fence_proxy_async_global();
+          umma::mbar_arrive_expect_tx(&s_mb[2], bytes);
+          umma::bulk_g2s(tmp, Pcb + (size_t)j0 * NCLp, bytes, &s_mb[2]);
+        } else {
+          umma::mbar_arrive(&s_mb[2]);  // keeps the phases in step
         }
+      }
+      if (ok && pending && tid < G) rv = __ldcg(Rprev + tid);
+      if (!umma::mbar_wait_cluster(&s_mb[2], k & 1u, A.timeout_ns)) {
+        record_gave_up(4, k);
+        ok = false;
       }
       if (pending && tid < G) rsh[tid] = rv;
       __syncthreads();
