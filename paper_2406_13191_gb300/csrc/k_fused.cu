@@ -140,10 +140,10 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   const int ngp = (ng + 3) & ~3;
   const int rpc = A.rows_per_cta;
   // shared memory carve-up: per-slice generator constants (FP64), then floats
-  double* gk = (double*)smem_raw;                // [5][SLp] ctil, sigma, mq, cconst, mid
+  double* gk = (double*)smem_raw;                // [6][SLp] ctil, sigma, mq, cconst, mid 2^e, sigma 2^e
   const int SLp = (SL + 1) & ~1;
   // [C][SL] partial adjoints of own slice, one row per cluster rank (written by peers)
-  float* recv = (float*)(gk + 5 * SLp);
+  float* recv = (float*)(gk + 6 * SLp);
   float* xs = recv + ((C * SL + 3) & ~3);        // [ngp] x* of all gens (written by peers)
   float* tmp = xs + ngp;                         // [SL * NCLp] cluster partials of own slice
   float* row = tmp + SL * NCLp;                  // per-row arrays, 12 x rpc
@@ -176,7 +176,10 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   for (int jj = tid; jj < nj; jj += blockDim.x) {
     const int j = j0 + jj;
     gk[jj] = N.ctil[j]; gk[SLp + jj] = N.sigma[j]; gk[2 * SLp + jj] = N.mq[j];
-    gk[3 * SLp + jj] = N.cconst[j]; gk[4 * SLp + jj] = N.mid[j];
+    gk[3 * SLp + jj] = N.cconst[j];
+    // the dispatch mid + sigma x in units of the fixed point (scaling by 2^e is exact,
+    // so one FMA rounds exactly as the unscaled expression would)
+    gk[4 * SLp + jj] = N.mid[j] * A.pscale; gk[5 * SLp + jj] = N.sigma[j] * A.pscale;
   }
   SolveState<float>& st = A.st;
   for (int r = tid; r < nr; r += blockDim.x) {
@@ -391,7 +394,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
             umma::st_async_b32(umma::cluster_addr(xs + j0 + jj, q), __float_as_uint(x),
                                umma::cluster_addr(&s_mb[1], q));
         csf += fmaf(fmaf((float)mq, x, (float)ct), x, (float)gk[3 * SLp + jj]);
-        psq += __double2ll_rn((gk[4 * SLp + jj] + sg * (double)x) * A.pscale);
+        psq += __double2ll_rn(fma(gk[5 * SLp + jj], (double)x, gk[4 * SLp + jj]));
       }
       csf = warp_sum(csf);
       psq = warp_sum(psq);
@@ -577,7 +580,7 @@ static size_t fused_smem(int ng, int rpc, int C, int NCL, bool phi) {
   int NCLp = (NCL + 3) & ~3;
   size_t f = (size_t)((C * SL + 3) & ~3) + ngp + (size_t)SL * NCLp + 12 * (size_t)rpc;
   if (phi) f += (size_t)rpc * ng;
-  return f * sizeof(float) + 5 * (size_t)SLp * sizeof(double);
+  return f * sizeof(float) + 6 * (size_t)SLp * sizeof(double);
 }
 
 // g_cap bounds the grid (fewer, larger CTAs: more rows each, fewer clusters to
