@@ -70,7 +70,10 @@ typedef enum {
 typedef enum {
   DCOPF_PATH_AUTO = 0,   /* fused persistent kernel for batch 1, batched kernels otherwise */
   DCOPF_PATH_PLAIN = 1,  /* one launch per phase per iteration (the unfused baseline) */
-  DCOPF_PATH_FUSED = 2,  /* one persistent cooperative kernel per instance */
+  DCOPF_PATH_FUSED = 2,  /* one persistent thread-block-cluster kernel per instance; it
+                            is launched cooperatively when the driver accepts that,
+                            unless the environment sets DCOPF_FUSED_COOPERATIVE=0
+                            (read by dcopf_dual_create) */
   DCOPF_PATH_BATCHED = 3 /* batched contraction kernels replayed from a CUDA graph */
 } dcopf_path;
 
