@@ -9,6 +9,9 @@ Modules:
              forms, the supergradient, and the GDM / Adam / AdaGrad ascent rules.
   exact   -- an exact LP/QP solver (dense primal-dual interior point with a
              weak-duality sandwich) and brute-force vertex enumeration for tiny LPs.
+  primal  -- primal recovery: a balanced box minimiser (uniform price shift by
+             bisection) repaired towards a feasible reference dispatch, whose cost
+             is an upper bound on gamma* (weak duality, Remarks 1-2).
   mlp     -- the warm-start perceptron: forward pass, mean-squared-error gradient
              and Adam, in FP64 (the paper has no learned part; any dual proposal
              is a valid bound by Remarks 1-2).
