@@ -19,9 +19,10 @@ Steps, at a dual point (lambda, mu_hi, mu_lo):
    balanced dispatch is the convex combination
    p_bal = p(hi) + phi (p(lo) - p(hi)) with phi = (D - P(hi)) / (P(lo) - P(hi)).
    It lies in the box, and its sum is D.
-3. Reference. p_ref is a dispatch of the caller that meets the balance and the box.
-   The default is the proportional dispatch pmin + theta (pmax - pmin). It must meet
-   the flow limits (to tol); otherwise there is no bound (status 2).
+3. Reference. p_ref is a dispatch of the caller. The default is the proportional
+   dispatch pmin + theta (pmax - pmin). It must meet the box and the balance (to
+   tol, the balance relative to max(1, D)) and the flow limits (to tol); otherwise
+   there is no bound (status 2).
 4. Line repair. The feasible set is convex. So p_ub = (1 - t) p_bal + t p_ref is
    feasible for the smallest t in [0, 1] that pulls every violated flow of p_bal back
    to its limit: for f_l(p_bal) > fmax_l, t >= (f_l(p_bal) - fmax_l) /
@@ -101,6 +102,10 @@ def recover(net: Net, loads, lam, mu_hi, mu_lo, p_ref=None, tol=1e-9):
     def flows(p):
         return net.flows(net.gen_injection(p) - loads)
 
+    if (np.any(p_ref < net.pmin - tol) or np.any(p_ref > net.pmax + tol)
+            or abs(p_ref.sum() - D) > tol * max(1.0, D)):
+        out.update(status=2)
+        return out
     f_bal, f_ref = flows(p_bal), flows(p_ref)
     if violation(net, f_ref) > tol:
         out.update(status=2)

@@ -153,3 +153,5 @@ def test_statuses():
     bad = np.array([1.5, 0.0])       # flow 1.5 > 1: infeasible reference
     r = primal.recover(net, loads, -10.0, zero, zero, p_ref=bad)
     assert r["status"] == 2 and r["ub"] == np.inf
+    for bad in ([0.5, 1.5 + 1e-6], [-0.5, 2.0], [2.5, -1.0]):   # unbalanced; outside the box
+        assert primal.recover(net, loads, -10.0, zero, zero, p_ref=np.array(bad))["status"] == 2
