@@ -192,6 +192,40 @@ dcopf_status dcopf_dual_certify_bound(dcopf_dual_t h, int32_t batch, const doubl
                                       const double* mu_hi, const double* mu_lo, double* bound,
                                       double* err_bound, void* stream);
 
+/* Upper bound from a dual point (primal recovery).  The paper builds no primal point;
+ * by its Remarks 1 and 2 no feasible dispatch costs less than any dual value, so the
+ * cost of the dispatch returned here, with dcopf_dual_certify_bound's lower bound,
+ * brackets gamma* without a stored optimum.  Steps, in FP64, per instance:
+ *   1. the closed-form minimiser (eq. (6) / eq. (16)) at the bus prices of
+ *      (lambda, mu) plus a uniform price shift, the shift found by bisection until
+ *      two adjacent shifts bracket the demand; the convex combination of those two
+ *      dispatches that meets the demand exactly (box and balance hold);
+ *   2. the smallest move t in [0, 1] towards the reference dispatch that brings
+ *      every flow within its limits (the feasible set is convex);
+ *   3. the flows of the result recomputed, and its cost.
+ *   loads [batch][n_bus]; outage [batch] or NULL (as in dcopf_dual_eval); lambda
+ *   [batch]; mu_hi, mu_lo [batch][n_line], used as given.
+ *   p_ref [batch][n_gen] or NULL: a dispatch in p.u. that meets the box, the balance
+ *            (to 1e-9 max(1, demand)) and every flow limit (to 1e-9 p.u.), e.g. the
+ *            current operating point; NULL = the proportional dispatch
+ *            pmin + theta (pmax - pmin) with sum = demand
+ * Outputs:
+ *   upper    [batch] (required)  the cost ($/h) of the recovered dispatch; +inf
+ *            where there is no bound
+ *   pstatus  [batch] or NULL     0 bound; 1 the demand lies outside
+ *            [sum pmin, sum pmax]; 2 the reference breaks the box, the balance or a
+ *            flow limit
+ *   dispatch [batch][n_gen] or NULL  the recovered dispatch (p.u.; NaN where there
+ *            is no bound)
+ *   max_violation [batch] or NULL  the largest flow-limit violation of that dispatch
+ *            with its flows recomputed (rounding only; NaN where there is no bound)
+ * Errors: INVALID_ARG, NETWORK (bridge outage), UNSUPPORTED, OOM, CUDA. */
+dcopf_status dcopf_dual_primal_bound(dcopf_dual_t h, int32_t batch, const double* loads,
+                                     const int32_t* outage, const double* lambda,
+                                     const double* mu_hi, const double* mu_lo, const double* p_ref,
+                                     double* upper, int32_t* pstatus, double* dispatch,
+                                     double* max_violation, void* stream);
+
 /* Projected gradient ascent on the dual for a batch of instances of one network
  * (Section 3.3, Algorithm 1 and the Adam / AdaGrad rules), from the cold start
  * lambda = mu = 0 (Algorithm 1, Require) or from the given warm start.

@@ -10,7 +10,8 @@ LIB_PATH = os.path.join(HERE, "libdcopfdual.so")
 # The exported C symbols, in the order include/dcopf_dual.h declares them.
 EXPORTS = ("dcopf_version", "dcopf_status_string", "dcopf_solve_params_default",
            "dcopf_dual_create", "dcopf_dual_destroy", "dcopf_dual_info", "dcopf_dual_eval",
-           "dcopf_dual_certify_bound", "dcopf_dual_solve_batch", "dcopf_dual_kernel_launches",
+           "dcopf_dual_certify_bound", "dcopf_dual_primal_bound", "dcopf_dual_solve_batch",
+           "dcopf_dual_kernel_launches",
            "dcopf_dual_device_error", "dcopf_dual_set_timing", "dcopf_dual_read_timing",
            "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc", "dcopf_dual_solve_group",
            "dcopf_mlp_create", "dcopf_mlp_destroy", "dcopf_mlp_num_params", "dcopf_mlp_set_params",

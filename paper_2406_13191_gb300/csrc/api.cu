@@ -580,6 +580,25 @@ dcopf_status dcopf_dual_certify_bound(dcopf_dual_t h, int32_t batch, const doubl
   return finish(h, s);
 }
 
+dcopf_status dcopf_dual_primal_bound(dcopf_dual_t h, int32_t batch, const double* loads,
+                                     const int32_t* outage, const double* lambda,
+                                     const double* mu_hi, const double* mu_lo, const double* p_ref,
+                                     double* upper, int32_t* pstatus, double* dispatch,
+                                     double* max_violation, void* stream) {
+  dcopf_status r = check_batch(h, batch, loads);
+  if (r) return r;
+  if (!lambda || !mu_hi || !mu_lo || !upper) return DCOPF_ERR_INVALID_ARG;
+  DeviceGuard guard(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((r = check_outage(h, batch, outage, s))) return r;
+  if ((r = ensure_workspace(h, batch))) return r;
+  if ((r = run_base_flows(h, batch, loads, outage, s))) return r;
+  if ((r = run_primal(h, batch, outage, lambda, mu_hi, mu_lo, p_ref, upper, pstatus, dispatch,
+                      max_violation, s)))
+    return r;
+  return finish(h, s);
+}
+
 static dcopf_status check_params(const dcopf_solve_params& p) {
   if (p.rule < DCOPF_GDM || p.rule > DCOPF_ADAGRAD || p.max_iters < 1 || !(p.alpha > 0) ||
       !std::isfinite(p.alpha) || p.check_every < 0 || !(p.gap >= 0) || !(p.decay > 0) ||

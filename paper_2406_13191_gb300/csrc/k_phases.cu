@@ -289,6 +289,25 @@ dcopf_status run_eval_unfused(dcopf_dual* h, int B, const int* outage, const dou
   return run_eval_finish(h, B, outage, lambda, mh, ml, value, glam, ghi, glo, nullptr, s);
 }
 
+void launch_adjoint64(dcopf_dual* h, int B, const int* outage, const double* mh,
+                      const double* ml, cudaStream_t s) {
+  const DevNet& N = h->dev;
+  Workspace& w = h->ws;
+  const int nl = N.n_line, ng = N.n_gen;
+  k_eta<double, double><<<B, 256, 0, s>>>(nl, mh, ml, outage, w.u64.as<double>(), w.eta64.as<double>());
+  k_adjoint<double><<<dim3(ng, B), red_threads(nl), 0, s>>>(nl, ng, N.phit64, w.eta64.as<double>(),
+                                                            w.pit64.as<double>());
+  h->launches += 2;
+}
+
+void launch_forward64(dcopf_dual* h, int B, const double* x, const double* f0, double* f,
+                      cudaStream_t s) {
+  const DevNet& N = h->dev;
+  const int nl = N.n_line, ng = N.n_gen;
+  k_forward<double><<<dim3(nl, B), red_threads(ng), 0, s>>>(nl, ng, N.phi64, x, f0, f, nullptr);
+  h->launches += 1;
+}
+
 // Tail of an evaluation once the flows f (FP64, before the outage correction) and the
 // cost / dispatch sums are in the workspace; `dispatch` takes x from w.x64.
 dcopf_status run_eval_finish(dcopf_dual* h, int B, const int* outage, const double* lambda,

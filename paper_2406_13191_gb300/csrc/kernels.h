@@ -104,6 +104,12 @@ struct BatchBufs {
   BatchView v;
 };
 
+// Workspace of the primal recovery (dcopf_dual_primal_bound).
+struct PrimalBufs {
+  int cap = 0;
+  DBuf xr, xu, fr, t, st;  // reference and repaired x [B][n_gen]; reference flows; t; status
+};
+
 struct StateBufs {
   int cap = 0;
   int elem = 0;  // sizeof(S) of the arrays below
@@ -123,6 +129,7 @@ struct dcopf_dual {
   dcopf::DBuf dense_ha, dense_part;  // dense FP64 PTDF [n_line][n_bus] (built on first use)
   dcopf::DBuf dense_colabs;           // [n_bus] column sums of |H_a| (price rounding bound)
   dcopf::BatchBufs bb;
+  dcopf::PrimalBufs pb;
   int* d_err = nullptr;  // sticky device error word
   unsigned* d_bar = nullptr;  // grid-barrier counters
   dcopf::DBuf active;  // one int: instances still running
@@ -166,6 +173,15 @@ void k_output_f32(unsigned grid, cudaStream_t s, int B, int nl, SolveState<float
 // k_sparse.cu
 dcopf_status run_base_flows(dcopf_dual* h, int batch, const double* loads, const int* outage,
                             cudaStream_t s);
+dcopf_status run_primal(dcopf_dual* h, int B, const int* outage, const double* lambda,
+                        const double* mh, const double* ml, const double* p_ref, double* upper,
+                        int* pstatus, double* dispatch, double* maxviol, cudaStream_t s);
+// FP64 per-phase building blocks of k_phases.cu for other files: eta and the adjoint
+// pi~ = Phi~^T eta into the workspace (eta64, pit64); and f = Phi~ x + f0.
+void launch_adjoint64(dcopf_dual* h, int B, const int* outage, const double* mh,
+                      const double* ml, cudaStream_t s);
+void launch_forward64(dcopf_dual* h, int B, const double* x, const double* f0, double* f,
+                      cudaStream_t s);
 template <typename S>
 dcopf_status run_certify_t(dcopf_dual* h, int batch, const double* loads, const int* outage,
                            const double* lam, const S* mh, const S* ml, double* bound, double* errb,

@@ -182,6 +182,27 @@ class DcopfDual:
                                                      self._stream()), "dcopf_dual_certify_bound")
         return bound, err
 
+    def primal_bound(self, loads, lam, mu_hi, mu_lo, outage=None, p_ref=None):
+        """``dcopf_dual_primal_bound``: a feasible dispatch recovered from the dual point and
+        its cost, an upper bound on gamma*.  Returns (upper, status, dispatch,
+        max_violation); upper is +inf and the dispatch NaN where status != 0 (1: demand
+        outside the generator box, 2: the reference dispatch is infeasible)."""
+        loads, out = self._batch_inputs(loads, outage)
+        B = loads.shape[0]
+        lam = _as_dev(lam, torch.float64, self.device).reshape(B)
+        mh = _as_dev(mu_hi, torch.float64, self.device).reshape(B, self.n_line)
+        ml = _as_dev(mu_lo, torch.float64, self.device).reshape(B, self.n_line)
+        pr = None if p_ref is None else _as_dev(p_ref, torch.float64, self.device).reshape(B, self.n_gen)
+        upper = torch.empty(B, dtype=torch.float64, device=self.device)
+        status = torch.empty(B, dtype=torch.int32, device=self.device)
+        disp = torch.empty(B, self.n_gen, dtype=torch.float64, device=self.device)
+        viol = torch.empty(B, dtype=torch.float64, device=self.device)
+        _lib.check(self.lib.dcopf_dual_primal_bound(self.h, B, _ptr(loads), _ptr(out), _ptr(lam),
+                                                    _ptr(mh), _ptr(ml), _ptr(pr), _ptr(upper),
+                                                    _ptr(status), _ptr(disp), _ptr(viol),
+                                                    self._stream()), "dcopf_dual_primal_bound")
+        return upper, status, disp, viol
+
     def _params(self, rule, precision, path, max_iters, alpha, alpha_lambda, rho, beta1, beta2, eps,
                 decay, gap, tol, as_printed, check_every, warm=False):
         p = _lib.SolveParams()

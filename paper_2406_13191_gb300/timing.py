@@ -7,6 +7,7 @@
     python -m paper_2406_13191_gb300.timing setup
     python -m paper_2406_13191_gb300.timing mlp --batch 512 --iters 50
     python -m paper_2406_13191_gb300.timing togap --config 2
+    python -m paper_2406_13191_gb300.timing primal --batch 1024
 
 ``batched`` runs the tensor-core batched solve (BF16 hi/lo split products) for a
 fixed number of iterations and reports the time of the iteration kernels per batched
@@ -25,6 +26,9 @@ perceptron (2000 -> 512 -> 512 -> 3201, seeded random data) in both product mode
 ``togap`` solves the first instances of the 4600-bus batch (256, half with an outage)
 or of the 10000-bus batch (64) to the certified 0.1 % gap against the oracle's optima
 (tests/golden/study_gamma.json, c3_gamma.json) in one batched tensor-core call.
+``primal`` times the primal recovery (an upper bound from the dual point) after solves
+of the 2000-bus instance and of held-out scenarios, and reports the gap it gives without
+a stored optimum.
 """
 from __future__ import annotations
 
@@ -230,9 +234,64 @@ def togap(cfg, repeat=2):
                           all_bounds_valid=bool(np.all(b <= T + 1e-9 * np.abs(T))))))
 
 
+def primal(batch=1024, repeat=5):
+    """Primal recovery after solves to the certified 0.1 % gap on the 2000-bus QP: the
+    single instance at base loads (fused path) and ``batch`` held-out load scenarios
+    (batched path).  Reports the time of dcopf_dual_primal_bound (CUDA events) and the
+    gap it gives without a stored optimum, (upper - lower) / upper, next to the true
+    gaps of both bounds against the oracle's gamma*."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    net, base = synth.network_for(1)
+    g = DcopfDual(net, device=0)
+    kw = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=4000)
+    out = dict(mode="primal", network="synthetic 2000-bus QP")
+
+    def timed(loads, r):
+        res = None
+        ts = []
+        for _ in range(repeat + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            res = g.primal_bound(loads, r.lam, r.mu_hi, r.mu_lo)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return res, float(np.median(ts[1:]))
+
+    def gaps(gam, lb, ub, st):
+        ok = st == 0
+        d = dict(bounded=int(ok.sum()), of=int(len(st)),
+                 all_valid=bool(np.all(lb <= gam * (1 + 1e-12)) and np.all(ub[ok] >= gam[ok] * (1 - 1e-12))))
+        if ok.any():
+            for name, v in (("gap_without_oracle", (ub - lb) / ub), ("upper_gap", (ub - gam) / gam)):
+                v = v[ok]
+                d[name] = dict(median=float(np.median(v)), p90=float(np.percentile(v, 90)),
+                               max=float(v.max()))
+        return d
+
+    gam1 = json.load(open(os.path.join(root, "tests", "golden", "gamma.json")))["1/0"]["gamma"]
+    r = g.solve(base[None], target=[gam1], path="fused", **kw)
+    (ub, st, _, viol), ms = timed(base[None], r)
+    out["single"] = dict(ms=ms, lower=r.bound.item(), upper=ub.item(), status=int(st.item()),
+                         max_violation=viol.item(), iterations=int(r.iters.item()),
+                         **gaps(np.array([gam1]), r.bound.cpu().numpy(), ub.cpu().numpy(),
+                                st.cpu().numpy()))
+    gam = np.array(json.load(open(os.path.join(root, "tests", "golden", "warm_gamma.json")))["gamma"][:batch])
+    X = synth.warm_loads("heldout", batch)
+    r = g.solve(X, target=gam, path="batched", precision="bf16x3", **kw)
+    (ub, st, _, viol), ms = timed(X, r)
+    st_h = st.cpu().numpy()
+    out["batch"] = dict(instances=batch, ms=ms, per_instance_us=1e3 * ms / batch,
+                        reached_gap=int((r.status == 0).sum().item()),
+                        max_violation=float(np.nanmax(viol.cpu().numpy())),
+                        **gaps(gam, r.bound.cpu().numpy(), ub.cpu().numpy(), st_h))
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("mode", choices=["batched", "certify", "fused", "group", "setup", "mlp", "togap"])
+    ap.add_argument("mode", choices=["batched", "certify", "fused", "group", "setup", "mlp", "togap",
+                                     "primal"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--iters", type=int, default=16)
@@ -251,6 +310,8 @@ def main():
         mlp(a.batch, a.iters)
     elif a.mode == "togap":
         togap(a.config)
+    elif a.mode == "primal":
+        primal(a.batch)
     else:
         fused(a.repeat, a.verbose)
 
