@@ -238,7 +238,10 @@ def solve(net: Net, loads, rule="gdm", alpha=1.0, rho=0.9, beta1=0.9, beta2=0.99
     is multiplied by ``decay`` after every iteration (Section 4.1 step decay).
     ``alpha_lambda`` optionally gives lambda its own step size (default: alpha).
     Starts from lambda = mu = 0 and zero optimiser state (Algorithm 1, Require) unless
-    a warm start is given.  Stops when the best value reaches target (1 - gap)
+    a warm start is given.  ``mean_dispatch`` is the mean of the minimisers of every
+    evaluation, the k-th weighted by k^2 (a candidate for the primal recovery in
+    oracle/primal.py: averages of a dual method's minimisers approach the primal
+    optimum, and the weights favour the late iterates).  Stops when the best value reaches target (1 - gap)
     (if target is given), when |g_{i+1} - g_i| < tol (Algorithm 1, stop test; tol > 0),
     or after max_iters evaluations.  Returns a dict with the best point and history
     (and, with ``record``, every evaluated point as (lambda, mu_hi, mu_lo)).
@@ -258,9 +261,12 @@ def solve(net: Net, loads, rule="gdm", alpha=1.0, rho=0.9, beta1=0.9, beta2=0.99
     prev = None
     it = 0
     stop = "max_iters"
+    psum, wsum = np.zeros(net.n_gen), 0.0
     for it in range(1, max_iters + 1):
-        val, gl, ghi, glo, _ = evaluate(net, loads, lam, mh, ml)
+        val, gl, ghi, glo, p_it = evaluate(net, loads, lam, mh, ml)
         hist.append(val)
+        psum += float(it) ** 2 * p_it       # mean of the minimisers, weight k^2
+        wsum += float(it) ** 2
         if record:
             pts.append((lam, mh.copy(), ml.copy()))
         if val > best:
@@ -310,4 +316,5 @@ def solve(net: Net, loads, rule="gdm", alpha=1.0, rho=0.9, beta1=0.9, beta2=0.99
         mh = np.maximum(mh, 0.0)
         ml = np.maximum(ml, 0.0)
     return dict(best=best, lam=best_pt[0], mu_hi=best_pt[1], mu_lo=best_pt[2],
-                iters=it, history=np.array(hist), stop=stop, points=pts)
+                iters=it, history=np.array(hist), stop=stop, points=pts,
+                mean_dispatch=psum / wsum if wsum > 0 else psum)

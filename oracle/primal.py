@@ -29,6 +29,12 @@ Steps, at a dual point (lambda, mu_hi, mu_lo):
    (f_l(p_bal) - f_l(p_ref)), and likewise below fmin_l.
 5. Bound. ub = cost(p_ub). The flows of p_ub are recomputed, and their largest
    violation (rounding only) is returned.
+
+A caller may instead pass a candidate dispatch p_cand in the box (for example the
+weighted mean of the minimisers over a solve, dcopf.solve's mean_dispatch). It then
+replaces steps 1-2 and is balanced by moving it towards a corner of the box: towards
+pmax when its total is below the demand, towards pmin when above,
+p_bal = p_cand + phi (corner - p_cand), with phi in [0, 1] chosen to meet the demand.
 """
 from __future__ import annotations
 
@@ -72,6 +78,22 @@ def balanced_minimiser(net: Net, nu_gen, demand, max_steps=2000):
     return p_hi + phi * (p_lo - p_hi), lo, hi
 
 
+def balance_candidate(net: Net, p_cand, demand):
+    """A box dispatch moved towards pmax (total below the demand) or pmin (above) until
+    its total meets the demand; None when the demand is outside the box totals."""
+    if demand > net.pmax.sum() or demand < net.pmin.sum():
+        return None
+    p = np.clip(np.asarray(p_cand, dtype=np.float64), net.pmin, net.pmax)
+    s = p.sum()
+    if s < demand:
+        room = net.pmax.sum() - s
+        phi = (demand - s) / room if room > 0 else 0.0
+        return p + min(1.0, phi) * (net.pmax - p)
+    room = s - net.pmin.sum()
+    phi = (s - demand) / room if room > 0 else 0.0
+    return p - min(1.0, phi) * (p - net.pmin)
+
+
 def proportional_dispatch(net: Net, demand):
     """pmin + theta (pmax - pmin) with the theta that meets the demand."""
     span = net.pmax.sum() - net.pmin.sum()
@@ -84,19 +106,25 @@ def violation(net: Net, f):
     return float(max(0.0, np.max(f - net.fmax, initial=0.0), np.max(net.fmin - f, initial=0.0)))
 
 
-def recover(net: Net, loads, lam, mu_hi, mu_lo, p_ref=None, tol=1e-9):
-    """Steps 1-5. Returns a dict with ub ($/h, inf without a bound), p (the dispatch),
-    t (the weight of the reference), status (0 bound, 1 demand outside the box,
-    2 reference infeasible) and maxviol (largest flow violation of p)."""
+def recover(net: Net, loads, lam, mu_hi, mu_lo, p_ref=None, tol=1e-9, p_cand=None):
+    """Steps 1-5 (steps 1-2 replaced by balance_candidate when p_cand is given).
+    Returns a dict with ub ($/h, inf without a bound), p (the dispatch), t (the weight
+    of the reference), status (0 bound, 1 demand outside the box, 2 reference
+    infeasible) and maxviol (largest flow violation of p)."""
     loads = np.asarray(loads, dtype=np.float64)
     D = float(loads.sum())
-    eta = np.asarray(mu_hi, dtype=np.float64) - np.asarray(mu_lo, dtype=np.float64)
-    nu_gen = lam + net.prices(eta)[net.gen_bus]
     out = dict(ub=np.inf, p=None, t=np.nan, status=1, maxviol=np.nan)
-    bal = balanced_minimiser(net, nu_gen, D)
-    if bal is None:
-        return out
-    p_bal = bal[0]
+    if p_cand is None:
+        eta = np.asarray(mu_hi, dtype=np.float64) - np.asarray(mu_lo, dtype=np.float64)
+        nu_gen = lam + net.prices(eta)[net.gen_bus]
+        bal = balanced_minimiser(net, nu_gen, D)
+        if bal is None:
+            return out
+        p_bal = bal[0]
+    else:
+        p_bal = balance_candidate(net, p_cand, D)
+        if p_bal is None:
+            return out
     p_ref = proportional_dispatch(net, D) if p_ref is None else np.asarray(p_ref, dtype=np.float64)
 
     def flows(p):

@@ -155,3 +155,43 @@ def test_statuses():
     assert r["status"] == 2 and r["ub"] == np.inf
     for bad in ([0.5, 1.5 + 1e-6], [-0.5, 2.0], [2.5, -1.0]):   # unbalanced; outside the box
         assert primal.recover(net, loads, -10.0, zero, zero, p_ref=np.array(bad))["status"] == 2
+
+
+def test_balance_candidate():
+    """Two-bus by hand: (0.5, 0.5) totals 1 < 1.5, the room to pmax is 3, so
+    phi = 1/6 and the candidate moves to (0.75, 0.75). Random candidates: the result
+    stays in the box and meets the demand; a balanced candidate is left as it is."""
+    net, loads, d = hand("two_bus")
+    assert np.allclose(primal.balance_candidate(net, [0.5, 0.5], 1.5), [0.75, 0.75], atol=1e-15)
+    assert np.allclose(primal.balance_candidate(net, [1.0, 0.5], 1.5), [1.0, 0.5], atol=1e-15)
+    s, loads = synth.tiny_network(50, 9, 12, 7)
+    net = onet(s)
+    rng = np.random.default_rng(3)
+    D = loads.sum()
+    for _ in range(20):
+        pc = rng.uniform(net.pmin, net.pmax)
+        p = primal.balance_candidate(net, pc, D)
+        assert np.all(p >= net.pmin - 1e-15) and np.all(p <= net.pmax + 1e-15)
+        assert abs(p.sum() - D) <= 1e-12 * D
+    assert primal.balance_candidate(net, pc, net.pmax.sum() * 1.01) is None
+
+
+@pytest.mark.parametrize("qp", [False, True])
+def test_mean_dispatch_candidate(qp):
+    """dcopf.solve's mean_dispatch is the k^2-weighted mean of the minimisers of the
+    recorded evaluations; recovered from it, the bound is feasible and above gamma*."""
+    s, loads = synth.tiny_network(60 if qp else 61, 6, 8, 4, quadratic=qp, tight=0.5)
+    net = onet(s)
+    r = dcopf.solve(net, loads, rule="adam", alpha=500.0, beta1=0.95, max_iters=150, record=True)
+    ps = [dcopf.dual_parts(net, loads, l, h, lo)[3] for (l, h, lo) in r["points"]]
+    w = np.arange(1, len(ps) + 1, dtype=float) ** 2
+    assert np.allclose(r["mean_dispatch"], (w[:, None] * np.array(ps)).sum(0) / w.sum(), rtol=1e-13)
+    gamma = exact.vertex_enumeration(net, loads)[0] if not qp else exact.ipm(net, loads)["gamma"]
+    rec = primal.recover(net, loads, r["lam"], r["mu_hi"], r["mu_lo"], p_cand=r["mean_dispatch"])
+    if rec["status"] == 0:
+        f = net.flows(net.gen_injection(rec["p"]) - loads)
+        assert np.all(f <= net.fmax + 1e-9) and np.all(f >= net.fmin - 1e-9)
+        assert abs(rec["p"].sum() - loads.sum()) <= 1e-12 * loads.sum()
+        assert rec["ub"] >= gamma - 1e-9 * abs(gamma)
+    else:
+        assert rec["status"] == 2
