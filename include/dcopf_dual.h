@@ -123,6 +123,11 @@ typedef struct {
   double tol;          /* > 0: also stop when |g_k - g_{k-1}| < tol (Algorithm 1 stop test) */
   const double* target_value; /* DEVICE [batch] optimal costs to stop at; NULL => run max_iters
                                  or until the tol test */
+  double* mean_dispatch;      /* DEVICE [batch][n_gen] or NULL: receives the mean of the
+                                 minimisers p*(lambda_k, mu_k) of the solve's evaluations,
+                                 the k-th weighted by k^2 (p.u.); a candidate for
+                                 dcopf_dual_primal_bound (averages of a dual method's
+                                 minimisers approach the primal optimum) */
 } dcopf_solve_params;
 
 /* Library version string. */
@@ -204,7 +209,11 @@ dcopf_status dcopf_dual_certify_bound(dcopf_dual_t h, int32_t batch, const doubl
  *      every flow within its limits (the feasible set is convex);
  *   3. the flows of the result recomputed, and its cost.
  *   loads [batch][n_bus]; outage [batch] or NULL (as in dcopf_dual_eval); lambda
- *   [batch]; mu_hi, mu_lo [batch][n_line], used as given.
+ *   [batch]; mu_hi, mu_lo [batch][n_line], used as given (NULL allowed with p_cand).
+ *   p_cand [batch][n_gen] or NULL: a candidate dispatch (p.u.; e.g. the solve's
+ *            mean_dispatch) that replaces step 1: clipped to the box, then moved
+ *            towards pmax (total below the demand) or pmin (above) until it meets
+ *            the demand
  *   p_ref [batch][n_gen] or NULL: a dispatch in p.u. that meets the box, the balance
  *            (to 1e-9 max(1, demand)) and every flow limit (to 1e-9 p.u.), e.g. the
  *            current operating point; NULL = the proportional dispatch
@@ -222,9 +231,10 @@ dcopf_status dcopf_dual_certify_bound(dcopf_dual_t h, int32_t batch, const doubl
  * Errors: INVALID_ARG, NETWORK (bridge outage), UNSUPPORTED, OOM, CUDA. */
 dcopf_status dcopf_dual_primal_bound(dcopf_dual_t h, int32_t batch, const double* loads,
                                      const int32_t* outage, const double* lambda,
-                                     const double* mu_hi, const double* mu_lo, const double* p_ref,
-                                     double* upper, int32_t* pstatus, double* dispatch,
-                                     double* max_violation, void* stream);
+                                     const double* mu_hi, const double* mu_lo,
+                                     const double* p_cand, const double* p_ref, double* upper,
+                                     int32_t* pstatus, double* dispatch, double* max_violation,
+                                     void* stream);
 
 /* Projected gradient ascent on the dual for a batch of instances of one network
  * (Section 3.3, Algorithm 1 and the Adam / AdaGrad rules), from the cold start

@@ -49,7 +49,8 @@ class SolveParams(C.Structure):
                 ("check_every", C.c_int32), ("reserved", C.c_int32), ("alpha", C.c_double),
                 ("alpha_lambda", C.c_double), ("rho", C.c_double), ("beta1", C.c_double),
                 ("beta2", C.c_double), ("eps", C.c_double), ("decay", C.c_double),
-                ("gap", C.c_double), ("tol", C.c_double), ("target_value", P)]
+                ("gap", C.c_double), ("tol", C.c_double), ("target_value", P),
+                ("mean_dispatch", P)]
 
 
 class GroupItem(C.Structure):

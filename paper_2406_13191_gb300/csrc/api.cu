@@ -114,6 +114,23 @@ dcopf_status ensure_state(dcopf_dual* h, int B, SolveState<S>* st) {
   return DCOPF_OK;
 }
 
+dcopf_status ensure_mean(dcopf_dual* h, int B, SolveStateBase* st, bool f32, bool on,
+                         cudaStream_t s) {
+  st->xsum = nullptr;
+  st->wsum = nullptr;
+  if (!on) return DCOPF_OK;
+  // the float state (fused, FP32 and BF16 paths) and the double state (FP64) keep
+  // separate accumulators, like the rest of their state
+  StateBufs& sb = f32 ? h->st32 : h->st64;
+  const size_t ng = h->dev.n_gen;
+  const size_t xs = ((size_t)B * ng * sizeof(float) + 255) & ~(size_t)255;
+  CUDA_TRY(h, sb.avg.alloc(xs + (size_t)B * sizeof(double)));
+  CUDA_TRY(h, cudaMemsetAsync(sb.avg.p, 0, xs + (size_t)B * sizeof(double), s));
+  st->xsum = sb.avg.as<float>();
+  st->wsum = (double*)(sb.avg.as<char>() + xs);
+  return DCOPF_OK;
+}
+
 template dcopf_status ensure_state<float>(dcopf_dual*, int, SolveState<float>*);
 template dcopf_status ensure_state<double>(dcopf_dual*, int, SolveState<double>*);
 
@@ -289,6 +306,8 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
       h->launches += 1;
     }
   }
+  // the mean of the minimisers starts after any tuning runs
+  if ((r = ensure_mean(h, B, &st, sizeof(S) == 4, p.mean_dispatch != nullptr, s))) return r;
   if (!h->h_pinned) CUDA_TRY(h, cudaMallocHost(&h->h_pinned, 4 * sizeof(int)));
   for (int round = 0;; ++round) {
     long long launches_before = h->launches;
@@ -334,6 +353,7 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
     if (active == 0) break;
     if (round > 4 * (p.max_iters / chunk + 2) + 64) break;  // cannot happen unless stuck
   }
+  if (p.mean_dispatch) launch_mean_out(h, B, st, p.mean_dispatch, s);
   CUDA_TRY(h, cudaGetLastError());
   if (h->timing) h->t_evals += h->h_pinned[1];
   return DCOPF_OK;
@@ -582,19 +602,20 @@ dcopf_status dcopf_dual_certify_bound(dcopf_dual_t h, int32_t batch, const doubl
 
 dcopf_status dcopf_dual_primal_bound(dcopf_dual_t h, int32_t batch, const double* loads,
                                      const int32_t* outage, const double* lambda,
-                                     const double* mu_hi, const double* mu_lo, const double* p_ref,
-                                     double* upper, int32_t* pstatus, double* dispatch,
-                                     double* max_violation, void* stream) {
+                                     const double* mu_hi, const double* mu_lo,
+                                     const double* p_cand, const double* p_ref, double* upper,
+                                     int32_t* pstatus, double* dispatch, double* max_violation,
+                                     void* stream) {
   dcopf_status r = check_batch(h, batch, loads);
   if (r) return r;
-  if (!lambda || !mu_hi || !mu_lo || !upper) return DCOPF_ERR_INVALID_ARG;
+  if (!upper || (!p_cand && (!lambda || !mu_hi || !mu_lo))) return DCOPF_ERR_INVALID_ARG;
   DeviceGuard guard(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   if ((r = check_outage(h, batch, outage, s))) return r;
   if ((r = ensure_workspace(h, batch))) return r;
   if ((r = run_base_flows(h, batch, loads, outage, s))) return r;
-  if ((r = run_primal(h, batch, outage, lambda, mu_hi, mu_lo, p_ref, upper, pstatus, dispatch,
-                      max_violation, s)))
+  if ((r = run_primal(h, batch, outage, lambda, mu_hi, mu_lo, p_cand, p_ref, upper, pstatus,
+                      dispatch, max_violation, s)))
     return r;
   return finish(h, s);
 }

@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   float* recv = (float*)(gk + 6 * SLp);
   float* xs = recv + ((C * SL + 3) & ~3);        // [ngp] x* of all gens (written by peers)
   float* tmp = xs + ngp;                         // [SL * NCLp] cluster partials of own slice
-  float* row = tmp + SL * NCLp;                  // per-row arrays, 12 x rpc
+  float* xacc = tmp + SL * NCLp;                 // [SL] mean of the minimisers (cluster 0)
+  float* row = xacc + ((SL + 3) & ~3);           // per-row arrays, 12 x rpc
   float *eta = row, *mh = row + rpc, *ml = row + 2 * rpc, *h1 = row + 3 * rpc, *h2 = row + 4 * rpc,
         *l1 = row + 5 * rpc, *l2 = row + 6 * rpc, *ph = row + 7 * rpc, *pl = row + 8 * rpc,
         *fmx = row + 9 * rpc, *fmn = row + 10 * rpc, *f0 = row + 11 * rpc;
@@ -182,6 +183,11 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     gk[4 * SLp + jj] = N.mid[j] * A.pscale; gk[5 * SLp + jj] = N.sigma[j] * A.pscale;
   }
   SolveState<float>& st = A.st;
+  // the mean of the minimisers: cluster 0 keeps the running sum of each slice
+  const bool mean_on = st.xsum != nullptr && cid == 0;
+  if (mean_on)
+    for (int jj = tid; jj < nj; jj += blockDim.x) xacc[jj] = st.xsum[j0 + jj];
+  double wacc = 0.0;
   for (int r = tid; r < nr; r += blockDim.x) {
     int i = r0 + r;
     mh[r] = st.mu_hi[i]; ml[r] = st.mu_lo[i];
@@ -481,6 +487,11 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       pending = false;
     }
     if (cand) break;  // uniform everywhere: every CTA assembled the same value
+    if (mean_on) {  // this loop's minimiser, evaluation t + 1, weight (t + 1)^2
+      const float kk = (float)(t + 1), wk = kk * kk;
+      for (int jj = tid; jj < nj; jj += blockDim.x) xacc[jj] += wk * xs[j0 + jj];
+      wacc += (double)wk;
+    }
     if (tid == (int)blockDim.x - 32) {
       for (int q = 0; q < C; ++q) { s_cspc[q] = s_csp[q]; s_pspc[q] = s_psp[q]; }
     }
@@ -551,6 +562,10 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   }
   // ---------------- write back (resumable state); peers may still read our smem
   cl.sync();
+  if (mean_on) {
+    for (int jj = tid; jj < nj; jj += blockDim.x) st.xsum[j0 + jj] = xacc[jj];
+    if (c == 0 && tid == 0) st.wsum[0] += wacc;
+  }
   for (int r = tid; r < nr; r += blockDim.x) {
     int i = r0 + r;
     st.mu_hi[i] = mh[r]; st.mu_lo[i] = ml[r];
@@ -578,7 +593,8 @@ static size_t fused_smem(int ng, int rpc, int C, int NCL, bool phi) {
   int SL = (ng + C - 1) / C;
   int SLp = (SL + 1) & ~1;
   int NCLp = (NCL + 3) & ~3;
-  size_t f = (size_t)((C * SL + 3) & ~3) + ngp + (size_t)SL * NCLp + 12 * (size_t)rpc;
+  size_t f = (size_t)((C * SL + 3) & ~3) + ngp + (size_t)SL * NCLp + ((SL + 3) & ~3) +
+             12 * (size_t)rpc;
   if (phi) f += (size_t)rpc * ng;
   return f * sizeof(float) + 6 * (size_t)SLp * sizeof(double);
 }

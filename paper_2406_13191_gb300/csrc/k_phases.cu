@@ -289,6 +289,42 @@ dcopf_status run_eval_unfused(dcopf_dual* h, int B, const int* outage, const dou
   return run_eval_finish(h, B, outage, lambda, mh, ml, value, glam, ghi, glo, nullptr, s);
 }
 
+// xsum[b][j] += k^2 x[b][j] and wsum[b] += k^2 for the k-th evaluation of every
+// running instance (k = evaluations before this one + 1).
+template <typename T>
+__global__ void k_accum_mean(int ng, const T* __restrict__ x, SolveStateBase st) {
+  const int b = blockIdx.x;
+  if (st.done[b]) return;
+  const float k = (float)(st.iter[b] + 1);
+  const float wk = k * k;
+  for (int j = threadIdx.x; j < ng; j += blockDim.x)
+    st.xsum[(size_t)b * ng + j] += wk * (float)x[(size_t)b * ng + j];
+  if (threadIdx.x == 0) st.wsum[b] += (double)wk;
+}
+
+__global__ void k_mean_out(DevNet N, const float* __restrict__ xsum, const double* __restrict__ wsum,
+                           double* __restrict__ out) {
+  const int b = blockIdx.x, ng = N.n_gen;
+  const double w = wsum[b];
+  for (int j = threadIdx.x; j < ng; j += blockDim.x) {
+    const double x = w > 0.0 ? (double)xsum[(size_t)b * ng + j] / w : 0.0;
+    out[(size_t)b * ng + j] = N.mid[j] + N.sigma[j] * x;
+  }
+}
+
+template <typename T>
+void launch_accum_mean(dcopf_dual* h, int B, const T* x, const SolveStateBase& st, cudaStream_t s) {
+  k_accum_mean<T><<<B, 256, 0, s>>>(h->dev.n_gen, x, st);
+  h->launches += 1;
+}
+template void launch_accum_mean<double>(dcopf_dual*, int, const double*, const SolveStateBase&, cudaStream_t);
+template void launch_accum_mean<float>(dcopf_dual*, int, const float*, const SolveStateBase&, cudaStream_t);
+
+void launch_mean_out(dcopf_dual* h, int B, const SolveStateBase& st, double* out, cudaStream_t s) {
+  k_mean_out<<<B, 256, 0, s>>>(h->dev, st.xsum, st.wsum, out);
+  h->launches += 1;
+}
+
 void launch_adjoint64(dcopf_dual* h, int B, const int* outage, const double* mh,
                       const double* ml, cudaStream_t s) {
   const DevNet& N = h->dev;
@@ -342,6 +378,7 @@ dcopf_status run_iters_unfused(dcopf_dual* h, int B, const int* outage, int prec
       k_adjoint<double><<<gg, ta, 0, s>>>(nl, ng, N.phit64, w.eta64.as<double>(), w.pit64.as<double>());
       k_minimize<double><<<B, 256, 0, s>>>(N, st.lam, w.pit64.as<double>(), w.x64.as<double>(),
                                            w.sumcost.as<double>(), w.sump.as<double>(), st.done);
+      if (st.xsum) launch_accum_mean<double>(h, B, w.x64.as<double>(), st, s);
       k_forward<double><<<gl, tf, 0, s>>>(nl, ng, N.phi64, w.x64.as<double>(), w.f0.as<double>(),
                                            w.f.as<double>(), st.done);
     } else {
@@ -349,6 +386,7 @@ dcopf_status run_iters_unfused(dcopf_dual* h, int B, const int* outage, int prec
       k_adjoint<float><<<gg, ta, 0, s>>>(nl, ng, N.phit32, w.eta32.as<float>(), w.pit32.as<float>());
       k_minimize<float><<<B, 256, 0, s>>>(N, st.lam, w.pit32.as<float>(), w.x32.as<float>(),
                                           w.sumcost.as<double>(), w.sump.as<double>(), st.done);
+      if (st.xsum) launch_accum_mean<float>(h, B, w.x32.as<float>(), st, s);
       k_forward<float><<<gl, tf, 0, s>>>(nl, ng, N.phi32, w.x32.as<float>(), w.f0.as<double>(),
                                           w.f.as<double>(), st.done);
     }

@@ -6,7 +6,9 @@
 //
 // One CTA per instance, FP64 throughout (normalised generators, Appendix A1:
 // p = mid + sigma x, |x| <= 1):
-//   k_primal_balance  w_j = ctil_j + sigma_j lambda + pi~_j from the FP64 adjoint; the
+//   k_primal_balance  (or, from a caller's candidate, its box clip moved towards a box
+//                     corner until it meets the demand)
+//                     w_j = ctil_j + sigma_j lambda + pi~_j from the FP64 adjoint; the
 //                     closed-form minimiser x_j(w_j + sigma_j delta) for a uniform price
 //                     shift delta (eq. (6) / eq. (16)); bisection on delta until the
 //                     total dispatch brackets the demand between two adjacent shifts,
@@ -37,63 +39,88 @@ __device__ __forceinline__ double reduced_cost(const DevNet& N, int j, double la
 
 __global__ void k_primal_balance(DevNet N, const double* __restrict__ lambda,
                                  const double* __restrict__ pit, const double* __restrict__ demand,
+                                 const double* __restrict__ p_cand,
                                  const double* __restrict__ p_ref, double* __restrict__ xb,
                                  double* __restrict__ xr, int* __restrict__ pst) {
   __shared__ double red[32];
   const int b = blockIdx.x, ng = N.n_gen, tid = threadIdx.x, nt = blockDim.x;
-  const double lam = lambda[b], D = demand[b];
-  const double* pi = pit + (size_t)b * ng;
+  const double D = demand[b];
   double* xbb = xb + (size_t)b * ng;
   double* xrb = xr + (size_t)b * ng;
-  // box totals, and the shifts beyond which every unit sits at pmax (below lo) or at
-  // pmin (above hi)
-  double smin = 0.0, smax = 0.0, dlo = INFINITY, dhi = -INFINITY;
+  double smin = 0.0, smax = 0.0;  // box totals
   for (int j = tid; j < ng; j += nt) {
-    const double s = N.sigma[j], m = N.mid[j];
-    smin += m - s;
-    smax += m + s;
-    if (s > 0.0) {
-      const double w = reduced_cost(N, j, lam, pi[j]);
-      dlo = fmin(dlo, (-2.0 * N.mq[j] - w) / s);
-      dhi = fmax(dhi, (2.0 * N.mq[j] - w) / s);
-    }
+    smin += N.mid[j] - N.sigma[j];
+    smax += N.mid[j] + N.sigma[j];
   }
   smin = block_sum(smin, red);
   smax = block_sum(smax, red);
-  dlo = -block_max(-dlo, red);
-  dhi = block_max(dhi, red);
   if (D > smax || D < smin) {  // no dispatch in the box meets the demand
     for (int j = tid; j < ng; j += nt) { xbb[j] = 0.0; xrb[j] = 0.0; }
     if (tid == 0) pst[b] = 1;
     return;
   }
-  auto x_at = [&](int j, double delta) {
-    const double s = N.sigma[j];
-    return s > 0.0 ? inner_x<double>(reduced_cost(N, j, lam, pi[j]) + s * delta, N.mq[j]) : 0.0;
-  };
-  auto total = [&](double delta) {
-    double acc = 0.0;
-    for (int j = tid; j < ng; j += nt) acc += N.mid[j] + N.sigma[j] * x_at(j, delta);
-    return block_sum(acc, red);
-  };
-  double lo = 0.0, hi = 0.0;
-  if (dlo <= dhi) {
-    lo = dlo - 1.0;
-    hi = dhi + 1.0;
-    // total(lo) >= D >= total(hi) throughout; every thread takes the same branch
-    for (int it = 0; it < 2000; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (mid == lo || mid == hi) break;
-      if (total(mid) >= D) lo = mid;
-      else hi = mid;
+  if (p_cand) {
+    // the caller's candidate, clipped to the box, moved towards pmax (total below the
+    // demand) or pmin (above) until it meets the demand
+    const double* pc = p_cand + (size_t)b * ng;
+    double tot = 0.0;
+    for (int j = tid; j < ng; j += nt) {
+      const double m = N.mid[j], sg = N.sigma[j];
+      tot += fmin(m + sg, fmax(m - sg, pc[j]));
     }
-  }
-  const double P_lo = total(lo), P_hi = total(hi);
-  double phi = P_lo > P_hi ? (D - P_hi) / (P_lo - P_hi) : 0.0;
-  phi = fmin(1.0, fmax(0.0, phi));
-  for (int j = tid; j < ng; j += nt) {
-    const double x_lo = x_at(j, lo), x_hi = x_at(j, hi);
-    xbb[j] = x_hi + phi * (x_lo - x_hi);
+    tot = block_sum(tot, red);
+    const bool up = tot < D;
+    const double room = up ? smax - tot : tot - smin;
+    const double phi = room > 0.0 ? fmin(1.0, (up ? D - tot : tot - D) / room) : 0.0;
+    for (int j = tid; j < ng; j += nt) {
+      const double m = N.mid[j], sg = N.sigma[j];
+      double p = fmin(m + sg, fmax(m - sg, pc[j]));
+      p = up ? p + phi * (m + sg - p) : p - phi * (p - (m - sg));
+      xbb[j] = sg > 0.0 ? (p - m) / sg : 0.0;
+    }
+  } else {
+    const double lam = lambda[b];
+    const double* pi = pit + (size_t)b * ng;
+    // the shifts beyond which every unit sits at pmax (below lo) or at pmin (above hi)
+    double dlo = INFINITY, dhi = -INFINITY;
+    for (int j = tid; j < ng; j += nt) {
+      const double s = N.sigma[j];
+      if (s > 0.0) {
+        const double w = reduced_cost(N, j, lam, pi[j]);
+        dlo = fmin(dlo, (-2.0 * N.mq[j] - w) / s);
+        dhi = fmax(dhi, (2.0 * N.mq[j] - w) / s);
+      }
+    }
+    dlo = -block_max(-dlo, red);
+    dhi = block_max(dhi, red);
+    auto x_at = [&](int j, double delta) {
+      const double s = N.sigma[j];
+      return s > 0.0 ? inner_x<double>(reduced_cost(N, j, lam, pi[j]) + s * delta, N.mq[j]) : 0.0;
+    };
+    auto total = [&](double delta) {
+      double acc = 0.0;
+      for (int j = tid; j < ng; j += nt) acc += N.mid[j] + N.sigma[j] * x_at(j, delta);
+      return block_sum(acc, red);
+    };
+    double lo = 0.0, hi = 0.0;
+    if (dlo <= dhi) {
+      lo = dlo - 1.0;
+      hi = dhi + 1.0;
+      // total(lo) >= D >= total(hi) throughout; every thread takes the same branch
+      for (int it = 0; it < 2000; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        if (total(mid) >= D) lo = mid;
+        else hi = mid;
+      }
+    }
+    const double P_lo = total(lo), P_hi = total(hi);
+    double phi = P_lo > P_hi ? (D - P_hi) / (P_lo - P_hi) : 0.0;
+    phi = fmin(1.0, fmax(0.0, phi));
+    for (int j = tid; j < ng; j += nt) {
+      const double x_lo = x_at(j, lo), x_hi = x_at(j, hi);
+      xbb[j] = x_hi + phi * (x_lo - x_hi);
+    }
   }
   // reference dispatch
   int bad = 0;
@@ -203,8 +230,9 @@ __global__ void k_primal_finish(DevNet N, const int* __restrict__ outage, const 
 }
 
 dcopf_status run_primal(dcopf_dual* h, int B, const int* outage, const double* lambda,
-                        const double* mh, const double* ml, const double* p_ref, double* upper,
-                        int* pstatus, double* dispatch, double* maxviol, cudaStream_t s) {
+                        const double* mh, const double* ml, const double* p_cand,
+                        const double* p_ref, double* upper, int* pstatus, double* dispatch,
+                        double* maxviol, cudaStream_t s) {
   const DevNet& N = h->dev;
   Workspace& w = h->ws;
   const int nl = N.n_line, ng = N.n_gen;
@@ -220,9 +248,9 @@ dcopf_status run_primal(dcopf_dual* h, int B, const int* outage, const double* l
     pb.cap = B;
   }
   int* pst = pstatus ? pstatus : pb.st.as<int>();
-  launch_adjoint64(h, B, outage, mh, ml, s);
-  k_primal_balance<<<B, 256, 0, s>>>(N, lambda, w.pit64.as<double>(), w.demand.as<double>(), p_ref,
-                                     w.x64.as<double>(), pb.xr.as<double>(), pst);
+  if (!p_cand) launch_adjoint64(h, B, outage, mh, ml, s);
+  k_primal_balance<<<B, 256, 0, s>>>(N, lambda, w.pit64.as<double>(), w.demand.as<double>(), p_cand,
+                                     p_ref, w.x64.as<double>(), pb.xr.as<double>(), pst);
   launch_forward64(h, B, w.x64.as<double>(), w.f0.as<double>(), w.f.as<double>(), s);
   launch_forward64(h, B, pb.xr.as<double>(), w.f0.as<double>(), pb.fr.as<double>(), s);
   k_primal_repair<<<B, 256, 0, s>>>(N, outage, w.u64.as<double>(), w.f.as<double>(),

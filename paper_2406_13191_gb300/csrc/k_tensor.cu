@@ -622,11 +622,13 @@ __global__ void k_bt_minimize(DevNet N, int splits, int M, int ldp, const float*
   // certified in FP64 later): per-generator terms and warp sums in FP32, FP64 across
   // warps.  w cancels (ctil + sigma lambda ~ -pi~), so it is formed in FP64.
   float c = 0.f, p = 0.f, to = 0.f;
+  const float kk = (float)(st.iter[b] + 1), wk = kk * kk;  // weight of the mean of the minimisers
   for (int j = threadIdx.x; j < ng; j += blockDim.x) {
     float s = 0.f;
     for (int q = 0; q < splits; ++q) s += P[((size_t)q * M + b) * ldp + j];
     const double w = N.ctil[j] + N.sigma[j] * lam + (double)s;
     const float x = inner_x<float>((float)w, N.mq32[j]);
+    if (st.xsum) st.xsum[(size_t)b * ng + j] += wk * x;
     split_bf16(x, Xh + (size_t)b * ldx + j, Xl + (size_t)b * ldx + j);
     c += fmaf(fmaf(N.mq32[j], x, N.ctil32[j]), x, N.cconst32[j]);
     p += fmaf(N.sigma32[j], x, N.mid32[j]);
@@ -642,6 +644,7 @@ __global__ void k_bt_minimize(DevNet N, int splits, int M, int ldp, const float*
     const double p = ps;
     bb.cost[b] = cs;
     bb.psum[b] = ps;
+    if (st.wsum) st.wsum[b] += (double)wk;
     bb.tout[b] = (float)ts;
     bb.lam_eval[b] = lam;
     // step t = iter + 1: scale decay^(t-1), bias corrections 1 - beta^t
@@ -936,7 +939,8 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   R.ga.kb_per_split = h->tune_kbps;
   R.ga.skip = bb.frozen;
   R.gf.skip = bb.frozen;
-  return DCOPF_OK;
+  // the mean of the minimisers starts after the tuning runs
+  return ensure_mean(h, B, &R.st, true, p.mean_dispatch != nullptr, cs);
 }
 
 // Enqueues `chunk` iterations (adjoint GEMM, minimiser, forward GEMM, step, value) on
@@ -987,6 +991,7 @@ static dcopf_status tensor_finish(TensorRun& R, cudaStream_t s) {
   k_output_f32(R.gi, cs, R.it.B, h->host.n_line, R.st, R.it.lam, R.it.mh, R.it.ml, R.it.bound,
                R.it.iters, R.it.status);
   h->launches += 1;
+  if (R.p.mean_dispatch) launch_mean_out(h, R.it.B, R.st, R.p.mean_dispatch, cs);
   if (cudaEventRecord(h->tev, cs) != cudaSuccess || cudaStreamWaitEvent(s, h->tev, 0) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return DCOPF_ERR_CUDA;

@@ -36,6 +36,9 @@ struct SolveStateBase {
   double* lam_s2;
   double* cert;    // certified bound of the best point
   int has_target;
+  // mean of the minimisers (NULL = off): sum_k k^2 x_k [batch][n_gen] and sum_k k^2
+  float* xsum = nullptr;
+  double* wsum = nullptr;
 };
 
 template <typename S>
@@ -114,6 +117,7 @@ struct StateBufs {
   int cap = 0;
   int elem = 0;  // sizeof(S) of the arrays below
   DBuf ints, dbls, mus;
+  DBuf avg;      // xsum and wsum of the mean of the minimisers
 };
 
 }  // namespace dcopf
@@ -173,9 +177,18 @@ void k_output_f32(unsigned grid, cudaStream_t s, int B, int nl, SolveState<float
 // k_sparse.cu
 dcopf_status run_base_flows(dcopf_dual* h, int batch, const double* loads, const int* outage,
                             cudaStream_t s);
+// The mean of the minimisers over a solve (dcopf_solve_params.mean_dispatch): zeroed
+// accumulators attached to st when `on`, detached otherwise; and the output
+// p = mid + sigma (xsum / wsum) into out [B][n_gen].
+dcopf_status ensure_mean(dcopf_dual* h, int B, SolveStateBase* st, bool f32, bool on,
+                         cudaStream_t s);
+void launch_mean_out(dcopf_dual* h, int B, const SolveStateBase& st, double* out, cudaStream_t s);
+template <typename T>
+void launch_accum_mean(dcopf_dual* h, int B, const T* x, const SolveStateBase& st, cudaStream_t s);
 dcopf_status run_primal(dcopf_dual* h, int B, const int* outage, const double* lambda,
-                        const double* mh, const double* ml, const double* p_ref, double* upper,
-                        int* pstatus, double* dispatch, double* maxviol, cudaStream_t s);
+                        const double* mh, const double* ml, const double* p_cand,
+                        const double* p_ref, double* upper, int* pstatus, double* dispatch,
+                        double* maxviol, cudaStream_t s);
 // FP64 per-phase building blocks of k_phases.cu for other files: eta and the adjoint
 // pi~ = Phi~^T eta into the workspace (eta64, pit64); and f = Phi~ x + f0.
 void launch_adjoint64(dcopf_dual* h, int B, const int* outage, const double* mh,

@@ -35,6 +35,7 @@ class SolveResult:
     bound: torch.Tensor        # [B] certified FP64 lower bound
     iters: torch.Tensor        # [B] iterations taken
     status: torch.Tensor       # [B] 0 target reached, 1 cap/tol, 2 infeasible suspected
+    mean_dispatch: torch.Tensor | None = None  # [B][n_gen] k^2-weighted mean of the minimisers
 
     def to_host(self) -> "SolveResult":
         """The results in host memory with one device-to-host transfer (packed on the
@@ -182,23 +183,26 @@ class DcopfDual:
                                                      self._stream()), "dcopf_dual_certify_bound")
         return bound, err
 
-    def primal_bound(self, loads, lam, mu_hi, mu_lo, outage=None, p_ref=None):
-        """``dcopf_dual_primal_bound``: a feasible dispatch recovered from the dual point and
-        its cost, an upper bound on gamma*.  Returns (upper, status, dispatch,
-        max_violation); upper is +inf and the dispatch NaN where status != 0 (1: demand
-        outside the generator box, 2: the reference dispatch is infeasible)."""
+    def primal_bound(self, loads, lam=None, mu_hi=None, mu_lo=None, outage=None, p_ref=None,
+                     p_cand=None):
+        """``dcopf_dual_primal_bound``: a feasible dispatch recovered from the dual point (or
+        from the candidate ``p_cand``, e.g. a solve's mean_dispatch) and its cost, an
+        upper bound on gamma*.  Returns (upper, status, dispatch, max_violation); upper
+        is +inf and the dispatch NaN where status != 0 (1: demand outside the generator
+        box, 2: the reference dispatch is infeasible)."""
         loads, out = self._batch_inputs(loads, outage)
         B = loads.shape[0]
-        lam = _as_dev(lam, torch.float64, self.device).reshape(B)
-        mh = _as_dev(mu_hi, torch.float64, self.device).reshape(B, self.n_line)
-        ml = _as_dev(mu_lo, torch.float64, self.device).reshape(B, self.n_line)
-        pr = None if p_ref is None else _as_dev(p_ref, torch.float64, self.device).reshape(B, self.n_gen)
+
+        def opt(x, shape):
+            return None if x is None else _as_dev(x, torch.float64, self.device).reshape(shape)
+        lam, mh, ml = opt(lam, (B,)), opt(mu_hi, (B, self.n_line)), opt(mu_lo, (B, self.n_line))
+        pr, pc = opt(p_ref, (B, self.n_gen)), opt(p_cand, (B, self.n_gen))
         upper = torch.empty(B, dtype=torch.float64, device=self.device)
         status = torch.empty(B, dtype=torch.int32, device=self.device)
         disp = torch.empty(B, self.n_gen, dtype=torch.float64, device=self.device)
         viol = torch.empty(B, dtype=torch.float64, device=self.device)
         _lib.check(self.lib.dcopf_dual_primal_bound(self.h, B, _ptr(loads), _ptr(out), _ptr(lam),
-                                                    _ptr(mh), _ptr(ml), _ptr(pr), _ptr(upper),
+                                                    _ptr(mh), _ptr(ml), _ptr(pc), _ptr(pr), _ptr(upper),
                                                     _ptr(status), _ptr(disp), _ptr(viol),
                                                     self._stream()), "dcopf_dual_primal_bound")
         return upper, status, disp, viol
@@ -258,14 +262,21 @@ class DcopfDual:
     def solve(self, loads, outage=None, rule="adam", precision="fp32", path="auto",
               max_iters=5000, alpha=1000.0, alpha_lambda=0.0, rho=0.9, beta1=0.9, beta2=0.999,
               eps=1e-8, decay=1.0, gap=1e-3, tol=0.0, target=None, warm=None,
-              as_printed=False, check_every=1, out: SolveResult | None = None) -> SolveResult:
+              as_printed=False, check_every=1, out: SolveResult | None = None,
+              mean_dispatch: bool = False) -> SolveResult:
         """``dcopf_dual_solve_batch``.  ``target`` ([B] optimal costs) enables the
         certified-gap stop; ``warm`` = (lambda, mu_hi, mu_lo) warm start; ``out`` (from
-        ``new_result``) receives the results instead of new tensors."""
+        ``new_result``) receives the results instead of new tensors; ``mean_dispatch``
+        also returns the k^2-weighted mean of the minimisers (a primal candidate)."""
         loads, outg, tgt, r = self._solve_arrays(loads, outage, target, warm, out)
         p = self._params(rule, precision, path, max_iters, alpha, alpha_lambda, rho, beta1, beta2,
                          eps, decay, gap, tol, as_printed, check_every, warm=warm is not None)
         p.target_value = None if tgt is None else tgt.data_ptr()
+        if mean_dispatch:
+            if r.mean_dispatch is None or r.mean_dispatch.shape != (r.lam.shape[0], self.n_gen):
+                r.mean_dispatch = torch.empty(r.lam.shape[0], self.n_gen, dtype=torch.float64,
+                                              device=self.device)
+            p.mean_dispatch = r.mean_dispatch.data_ptr()
         _lib.check(self.lib.dcopf_dual_solve_batch(self.h, r.lam.shape[0], _ptr(loads), _ptr(outg),
                                                    C.byref(p), _ptr(r.lam), _ptr(r.mu_hi),
                                                    _ptr(r.mu_lo), _ptr(r.bound), _ptr(r.iters),

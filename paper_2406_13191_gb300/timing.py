@@ -246,13 +246,16 @@ def primal(batch=1024, repeat=5):
     kw = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=4000)
     out = dict(mode="primal", network="synthetic 2000-bus QP")
 
-    def timed(loads, r):
+    def timed(loads, r, mean=False):
         res = None
         ts = []
         for _ in range(repeat + 1):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            res = g.primal_bound(loads, r.lam, r.mu_hi, r.mu_lo)
+            if mean:
+                res = g.primal_bound(loads, p_cand=r.mean_dispatch)
+            else:
+                res = g.primal_bound(loads, r.lam, r.mu_hi, r.mu_lo)
             e1.record()
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
@@ -270,21 +273,24 @@ def primal(batch=1024, repeat=5):
         return d
 
     gam1 = json.load(open(os.path.join(root, "tests", "golden", "gamma.json")))["1/0"]["gamma"]
-    r = g.solve(base[None], target=[gam1], path="fused", **kw)
-    (ub, st, _, viol), ms = timed(base[None], r)
-    out["single"] = dict(ms=ms, lower=r.bound.item(), upper=ub.item(), status=int(st.item()),
-                         max_violation=viol.item(), iterations=int(r.iters.item()),
-                         **gaps(np.array([gam1]), r.bound.cpu().numpy(), ub.cpu().numpy(),
-                                st.cpu().numpy()))
+    r = g.solve(base[None], target=[gam1], path="fused", mean_dispatch=True, **kw)
+    for cand in ("dual_point", "mean_of_minimisers"):
+        (ub, st, _, viol), ms = timed(base[None], r, mean=cand != "dual_point")
+        out[f"single_from_{cand}"] = dict(
+            ms=ms, lower=r.bound.item(), upper=ub.item(), status=int(st.item()),
+            max_violation=viol.item(), iterations=int(r.iters.item()),
+            **gaps(np.array([gam1]), r.bound.cpu().numpy(), ub.cpu().numpy(), st.cpu().numpy()))
     gam = np.array(json.load(open(os.path.join(root, "tests", "golden", "warm_gamma.json")))["gamma"][:batch])
     X = synth.warm_loads("heldout", batch)
-    r = g.solve(X, target=gam, path="batched", precision="bf16x3", **kw)
-    (ub, st, _, viol), ms = timed(X, r)
-    st_h = st.cpu().numpy()
-    out["batch"] = dict(instances=batch, ms=ms, per_instance_us=1e3 * ms / batch,
-                        reached_gap=int((r.status == 0).sum().item()),
-                        max_violation=float(np.nanmax(viol.cpu().numpy())),
-                        **gaps(gam, r.bound.cpu().numpy(), ub.cpu().numpy(), st_h))
+    r = g.solve(X, target=gam, path="batched", precision="bf16x3", mean_dispatch=True, **kw)
+    for cand in ("dual_point", "mean_of_minimisers"):
+        (ub, st, _, viol), ms = timed(X, r, mean=cand != "dual_point")
+        st_h = st.cpu().numpy()
+        out[f"batch_from_{cand}"] = dict(
+            instances=batch, ms=ms, per_instance_us=1e3 * ms / batch,
+            reached_gap=int((r.status == 0).sum().item()),
+            max_violation=float(np.nanmax(viol.cpu().numpy())),
+            **gaps(gam, r.bound.cpu().numpy(), ub.cpu().numpy(), st_h))
     print(json.dumps(out))
 
 

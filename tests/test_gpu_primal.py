@@ -12,7 +12,7 @@ flow violation below 1e-9 p.u.
 import numpy as np
 import pytest
 
-from oracle import exact, primal
+from oracle import dcopf, exact, primal
 from paper_2406_13191_gb300 import DcopfDual, synth
 
 from gpu_common import drop_line, onet, rand_point
@@ -109,3 +109,58 @@ def test_gap_without_an_oracle_after_a_solve():
     assert np.all(st == 0) and np.all(viol <= 1e-9)
     assert np.all(lb <= gam * (1 + 1e-12)) and np.all(ub >= gam * (1 - 1e-12))
     assert np.all((ub - lb) / ub < 0.5)
+
+
+def test_recovery_from_a_candidate_matches_oracle():
+    """p_cand replaces the minimiser: the oracle's k^2-weighted mean of the minimisers
+    of its own solve, balanced and repaired on both sides; FP64 parity as above."""
+    w = synth.scenario_workload(208, 90, 130, 18, True, batch=3, n_out=0)
+    g = DcopfDual(w.net)
+    on = onet(w.net)
+    cands, recs = [], []
+    for b in range(3):
+        r = dcopf_solve(on, w.loads[b])
+        cands.append(r["mean_dispatch"])
+        recs.append(primal.recover(on, w.loads[b], None, None, None, p_cand=r["mean_dispatch"]))
+    ub, st, disp, viol = (t.cpu().numpy() for t in g.primal_bound(w.loads, p_cand=np.stack(cands)))
+    for b in range(3):
+        _check(b, ub[b], st[b], disp[b], viol[b], recs[b])
+    assert np.all(st == 0)
+
+
+def dcopf_solve(on, loads):
+    return dcopf.solve(on, loads, rule="adam", alpha=1000.0, beta1=0.95, beta2=0.999, max_iters=60)
+
+
+def test_mean_dispatch_of_the_plain_path_follows_the_oracle():
+    """The plain FP64 path evaluates the oracle's points (test_gpu_solve), so its mean of
+    the minimisers (FP32 sums of k^2 x) agrees with the oracle's to FP32 rounding."""
+    w = synth.scenario_workload(209, 70, 100, 15, True, batch=1, n_out=0)
+    g = DcopfDual(w.net)
+    on = onet(w.net)
+    kw = dict(rule="gdm", alpha=10.0, alpha_lambda=0.1, rho=0.995, max_iters=40)
+    res = g.solve(w.loads, path="plain", precision="fp64", mean_dispatch=True, **kw)
+    ref = dcopf.solve(on, w.loads[0], **kw)
+    assert res.iters[0].item() == 40
+    md = res.mean_dispatch[0].cpu().numpy()
+    assert np.max(np.abs(md - ref["mean_dispatch"])) <= 1e-5 * max(1.0, np.max(np.abs(md)))
+
+
+@pytest.mark.parametrize("path", ["fused", "batched"])
+def test_mean_dispatch_gives_valid_bounds(path):
+    """The fused and batched paths return the mean of their minimisers (in the box); the
+    bound recovered from it is feasible and above gamma*."""
+    w = synth.scenario_workload(210, 120, 170, 25, True, batch=1 if path == "fused" else 5, n_out=0)
+    g = DcopfDual(w.net)
+    on = onet(w.net)
+    B = w.loads.shape[0]
+    gam = np.array([exact.ipm(on, w.loads[b])["gamma"] for b in range(B)])
+    r = g.solve(w.loads, target=gam, rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999,
+                decay=0.997, max_iters=4000, path=path,
+                precision="fp32" if path == "fused" else "bf16x3", mean_dispatch=True)
+    md = r.mean_dispatch.cpu().numpy()
+    pmin, pmax = np.asarray(w.net.pmin), np.asarray(w.net.pmax)
+    assert np.all(md >= pmin - 1e-6) and np.all(md <= pmax + 1e-6)
+    ub, st, disp, viol = (t.cpu().numpy() for t in g.primal_bound(w.loads, p_cand=r.mean_dispatch))
+    assert np.all(st == 0) and np.all(viol <= 1e-9)
+    assert np.all(ub >= gam * (1 - 1e-12))
