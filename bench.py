@@ -186,10 +186,21 @@ def cpu_baseline(target_s=10.0):
             el = time.perf_counter() - t0
             if el >= target_s:
                 break
-    return {"value": n / el, "unit": UNIT, "cores": procs, "kind": "oracle",
-            "sample": f"{n} complete solves of the 2000-bus instance ({el:.1f} s, "
-                      f"{statistics.mean(iters):.0f} iterations each, {procs} processes with one "
-                      f"BLAS thread each)"}
+    out = {"value": n / el, "unit": UNIT, "cores": procs, "kind": "oracle",
+           "sample": f"{n} complete solves of the 2000-bus instance ({el:.1f} s, "
+                     f"{statistics.mean(iters):.0f} iterations each, {procs} processes with one "
+                     f"BLAS thread each)"}
+    # latency mode: one solve at a time in one process with the default BLAS threads
+    _oracle_init()
+    _oracle_solve(0)
+    m, t0 = 0, time.perf_counter()
+    while m < 3 or time.perf_counter() - t0 < target_s / 4:
+        _oracle_solve(0)
+        m += 1
+    el = time.perf_counter() - t0
+    out["latency_mode"] = {"value": m / el, "unit": UNIT, "ms_per_solve": 1e3 * el / m,
+                           "sample": f"{m} solves one after another in one process"}
+    return out
 
 
 def warm_start_eval(n_train: int, epochs: int, n_eval: int, keep_model: bool = False):
