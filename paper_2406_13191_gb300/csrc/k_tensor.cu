@@ -346,6 +346,86 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
   }
 }
 
+// The same step with four consecutive lines per thread: 16-byte loads and stores of every
+// FP32 stream and 8-byte stores of the BF16 split (needs n_line, ldF and ldh multiples
+// of 4; the chunk of a block is the same 1024 lines as k_bt_step's).
+__global__ void __launch_bounds__(STEP_THREADS) k_bt_step4(StepEpi E, int nl) {
+  __shared__ double red[32];
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if (E.frozen[b]) return;
+  const int k = E.outage ? E.outage[b] : -1;
+  const float t_out = k >= 0 ? E.tout[b] : 0.f;
+  const int pb = E.iter[b] & 1;
+  const size_t o = (size_t)b * nl;
+  const float am = E.stepf[4 * b], bc1 = E.stepf[4 * b + 1], bc2 = E.stepf[4 * b + 2];
+  const int i = 4 * (chunk * STEP_THREADS + threadIdx.x);
+  float lacc = 0.f, oacc = 0.f;
+  if (i < nl) {
+    auto ld4 = [](const float* p) { return *reinterpret_cast<const float4*>(p); };
+    const float4 Fv = ld4(E.F + (size_t)b * E.ldF + i), f0 = ld4(E.f0 + o + i);
+    const float4 uv = k >= 0 ? ld4(E.u + o + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 fx = ld4(E.fmax + i), fn = ld4(E.fmin + i);
+    const float4 mh = ld4(E.mu_hi[pb] + o + i), ml = ld4(E.mu_lo[pb] + o + i);
+    float4 a1 = ld4(E.s1_hi + o + i), a2 = ld4(E.s2_hi + o + i);
+    float4 b1 = ld4(E.s1_lo + o + i), b2 = ld4(E.s2_lo + o + i);
+    float F[4] = {Fv.x, Fv.y, Fv.z, Fv.w}, F0[4] = {f0.x, f0.y, f0.z, f0.w};
+    float U[4] = {uv.x, uv.y, uv.z, uv.w}, FX[4] = {fx.x, fx.y, fx.z, fx.w};
+    float FN[4] = {fn.x, fn.y, fn.z, fn.w}, MH[4] = {mh.x, mh.y, mh.z, mh.w};
+    float ML[4] = {ml.x, ml.y, ml.z, ml.w}, A1[4] = {a1.x, a1.y, a1.z, a1.w};
+    float A2[4] = {a2.x, a2.y, a2.z, a2.w}, B1[4] = {b1.x, b1.y, b1.z, b1.w};
+    float B2[4] = {b2.x, b2.y, b2.z, b2.w};
+    float NH[4], NL[4];
+    __align__(8) __nv_bfloat16 hh[4], hl[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float f = F[q] + F0[q] + U[q] * t_out;
+      const float gh = f - FX[q], gl = FN[q] - f;
+      float nh = 0.f, nlo = 0.f;
+      if (i + q != k) {
+        lacc = fmaf(MH[q], gh, fmaf(ML[q], gl, lacc));
+        nh = fmaxf(step_rule(E.P, MH[q], gh, A1[q], A2[q], am, bc1, bc2), 0.f);
+        nlo = fmaxf(step_rule(E.P, ML[q], gl, B1[q], B2[q], am, bc1, bc2), 0.f);
+      }
+      NH[q] = nh;
+      NL[q] = nlo;
+      const float eta = nh - nlo;
+      hh[q] = __float2bfloat16_rn(eta);
+      hl[q] = __float2bfloat16_rn(eta - __bfloat162float(hh[q]));
+      if (k >= 0) oacc = fmaf(U[q], eta, oacc);
+    }
+    // moments of the outaged line stay as they were: their new values equal the loaded
+    // ones there, since step_rule only ran for the other lines
+    auto st4 = [](float* p, const float* v) {
+      *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    };
+    st4(E.mu_hi[pb ^ 1] + o + i, NH);
+    st4(E.mu_lo[pb ^ 1] + o + i, NL);
+    st4(E.s1_hi + o + i, A1);
+    st4(E.s2_hi + o + i, A2);
+    st4(E.s1_lo + o + i, B1);
+    st4(E.s2_lo + o + i, B2);
+    *reinterpret_cast<uint2*>(E.Hh + (size_t)b * E.ldh + i) = *reinterpret_cast<const uint2*>(hh);
+    *reinterpret_cast<uint2*>(E.Hl + (size_t)b * E.ldh + i) = *reinterpret_cast<const uint2*>(hl);
+  }
+  lacc = warp_sum(lacc);
+  oacc = warp_sum(oacc);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[w] = (double)lacc;
+    red[16 + w] = (double)oacc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ls = 0.0, os = 0.0;
+    for (int q = 0; q < STEP_THREADS / 32; ++q) {
+      ls += red[q];
+      os += red[16 + q];
+    }
+    E.line_part[(size_t)b * E.n_tiles + chunk] = ls;
+    E.out_part[(size_t)b * E.n_tiles + chunk] = os;
+  }
+}
+
 // ------------------------------------------------------------------ operand preparation
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo) {
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -961,7 +1041,10 @@ static bool tensor_enqueue_chunk(TensorRun& R, int chunk, cudaStream_t cs) {
     ok &= (h->host.qp ? launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, R.gf, 1, cs)
                       : launch_gemm<2>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, R.gf, 1, cs)) ==
           cudaSuccess;
-    k_bt_step<<<dim3(R.n_tiles, B), STEP_THREADS, 0, cs>>>(R.E, nl);
+    if (nl % 4 == 0 && R.E.ldF % 4 == 0 && R.E.ldh % 4 == 0)
+      k_bt_step4<<<dim3(R.n_tiles, B), STEP_THREADS, 0, cs>>>(R.E, nl);
+    else
+      k_bt_step<<<dim3(R.n_tiles, B), STEP_THREADS, 0, cs>>>(R.E, nl);
     k_bt_finalize<<<(B + 3) / 4, 128, 0, cs>>>(B, T.ld_l, R.p.max_iters, R.p.tol, R.st, bb,
                                                R.it.outage, w.demand.as<double>(),
                                                T.H_hi.as<__nv_bfloat16>(),
