@@ -323,7 +323,7 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
     if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev1, s));
     long long iter_launches = h->launches - launches_before;
     r = run_certify_t<S>(h, B, loads, outage, st.best_lam, st.best_hi, st.best_lo, st.cert, nullptr,
-                         st.cand, st.done, s);
+                         st.cand, st.done, s, true);
     if (r) return r;
     CUDA_TRY(h, cudaMemsetAsync(d_active, 0, sizeof(int), s));
     k_accept<<<cdiv(B, 128), 128, 0, s>>>(B, ub_any, st, d_active);

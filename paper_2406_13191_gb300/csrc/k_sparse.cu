@@ -119,7 +119,7 @@ __global__ void k_base_flows(DevNet N, const double* __restrict__ loads,
                              const int* __restrict__ outage, double* __restrict__ f0,
                              float* __restrict__ f0_32, double* __restrict__ u64,
                              float* __restrict__ u32, double* __restrict__ demand, int* err,
-                             int staged) {
+                             int staged, double* __restrict__ wcache) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ double red[32];
   PackedFactor PF;
@@ -151,6 +151,8 @@ __global__ void k_base_flows(DevNet N, const double* __restrict__ loads,
     }
     __syncthreads();
     ldl_solve(N, pf, X);
+    if (wcache)  // kept for the certificates of this solve
+      for (int q = threadIdx.x; q < N.nr; q += blockDim.x) wcache[(size_t)b * N.nr + q] = X[q];
     // PTDF of a transfer from the outaged line's from-bus to its to-bus
     const double ptdf_kk =
         N.line_b[k] * (theta_at(N, X, N.line_from[k]) - theta_at(N, X, N.line_to[k]));
@@ -194,7 +196,8 @@ __global__ void k_certify(DevNet N, const double* __restrict__ loads, const int*
                           const double* __restrict__ lambda, const S* __restrict__ mu_hi,
                           const S* __restrict__ mu_lo, double* __restrict__ bound,
                           double* __restrict__ errb, const int* __restrict__ mask,
-                          const int* __restrict__ done, int staged) {
+                          const int* __restrict__ done, int staged,
+                          const double* __restrict__ wcache) {
   // shared memory: [staged factor] [nr] prices [nr] outage transfer
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ double red[32];
@@ -232,16 +235,21 @@ __global__ void k_certify(DevNet N, const double* __restrict__ loads, const int*
   if (k >= 0) {
     double* W = X + N.nr;
     Wv = W;
-    for (int q = threadIdx.x; q < N.nr; q += blockDim.x) W[q] = 0.0;
-    __syncthreads();
     const int a = N.line_from[k], c = N.line_to[k];
-    if (threadIdx.x == 0) {
-      int pa = N.pos_of_bus[a], pc = N.pos_of_bus[c];
-      if (pa >= 0) W[pa] += 1.0;
-      if (pc >= 0) W[pc] -= 1.0;
+    if (wcache) {  // W = B_r^-1 (e_a - e_c) from the base flows of this solve
+      for (int q = threadIdx.x; q < N.nr; q += blockDim.x) W[q] = wcache[(size_t)b * N.nr + q];
+      __syncthreads();
+    } else {
+      for (int q = threadIdx.x; q < N.nr; q += blockDim.x) W[q] = 0.0;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int pa = N.pos_of_bus[a], pc = N.pos_of_bus[c];
+        if (pa >= 0) W[pa] += 1.0;
+        if (pc >= 0) W[pc] -= 1.0;
+      }
+      __syncthreads();
+      ldl_solve(N, pf, W);
     }
-    __syncthreads();
-    ldl_solve(N, pf, W);
     // eta'_k = u^T eta = (z_a - z_c) / (1 - PTDF_kk); z' = z + eta'_k b_k W
     const double denom = 1.0 - N.line_b[k] * (theta_at(N, W, a) - theta_at(N, W, c));
     const double s = (theta_at(N, X, a) - theta_at(N, X, c)) / denom;
@@ -321,10 +329,10 @@ __global__ void k_certify(DevNet N, const double* __restrict__ loads, const int*
 
 template __global__ void k_certify<double>(DevNet, const double*, const int*, const double*,
                                            const double*, const double*, double*, double*,
-                                           const int*, const int*, int);
+                                           const int*, const int*, int, const double*);
 template __global__ void k_certify<float>(DevNet, const double*, const int*, const double*,
                                           const float*, const float*, double*, double*, const int*,
-                                          const int*, int);
+                                          const int*, int, const double*);
 
 // Shared memory of a sparse kernel with n_vec solution vectors; *staged tells whether
 // the packed factor fits beside them.
@@ -360,10 +368,24 @@ dcopf_status run_base_flows(dcopf_dual* h, int B, const double* loads, const int
       cudaSuccess)
     return DCOPF_ERR_CUDA;
   Workspace& w = h->ws;
+  double* wc = nullptr;
+  w.wcache_B = 0;
+  w.wcache_outage = nullptr;
+  if (outage) {
+    if (w.wcache.alloc((size_t)B * h->dev.nr * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return DCOPF_ERR_OOM;
+    }
+    wc = w.wcache.as<double>();
+  }
   k_base_flows<<<B, sparse_threads(h), smem, s>>>(h->dev, loads, outage, w.f0.as<double>(),
                                                   w.f0_32.as<float>(), w.u64.as<double>(),
                                                   w.u32.as<float>(), w.demand.as<double>(), h->d_err,
-                                                  staged);
+                                                  staged, wc);
+  if (wc) {
+    w.wcache_B = B;
+    w.wcache_outage = outage;
+  }
   h->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
@@ -373,7 +395,7 @@ dcopf_status run_base_flows(dcopf_dual* h, int B, const double* loads, const int
 template <typename S>
 dcopf_status run_certify_t(dcopf_dual* h, int B, const double* loads, const int* outage,
                            const double* lam, const S* mh, const S* ml, double* bound, double* errb,
-                           const int* mask, const int* done, cudaStream_t s) {
+                           const int* mask, const int* done, cudaStream_t s, bool use_wcache) {
   if (dense_path_applies(h, B, outage))
     return run_dense_certify<S>(h, B, loads, lam, mh, ml, bound, errb, mask, done, s);
   int staged = 0;
@@ -382,8 +404,12 @@ dcopf_status run_certify_t(dcopf_dual* h, int B, const double* loads, const int*
   if (cudaFuncSetAttribute(k_certify<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return DCOPF_ERR_CUDA;
+  const Workspace& w = h->ws;
+  const double* wc = use_wcache && outage && w.wcache_B == B && w.wcache_outage == outage
+                         ? w.wcache.as<double>()
+                         : nullptr;
   k_certify<S><<<B, sparse_threads(h), smem, s>>>(h->dev, loads, outage, lam, mh, ml, bound, errb,
-                                                  mask, done, staged);
+                                                  mask, done, staged, wc);
   h->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
@@ -391,10 +417,10 @@ dcopf_status run_certify_t(dcopf_dual* h, int B, const double* loads, const int*
 }
 template dcopf_status run_certify_t<double>(dcopf_dual*, int, const double*, const int*,
                                             const double*, const double*, const double*, double*,
-                                            double*, const int*, const int*, cudaStream_t);
+                                            double*, const int*, const int*, cudaStream_t, bool);
 template dcopf_status run_certify_t<float>(dcopf_dual*, int, const double*, const int*,
                                            const double*, const float*, const float*, double*,
-                                           double*, const int*, const int*, cudaStream_t);
+                                           double*, const int*, const int*, cudaStream_t, bool);
 
 // Base flows into caller-provided buffers (f0 and u64 [batch][n_line], demand [batch]);
 // the same kernel as run_base_flows without touching the handle's workspace.
@@ -407,7 +433,7 @@ dcopf_status launch_base_flows_into(dcopf_dual* h, int B, const double* loads, c
       cudaSuccess)
     return DCOPF_ERR_CUDA;
   k_base_flows<<<B, sparse_threads(h), smem, s>>>(h->dev, loads, outage, f0, nullptr, u64, nullptr,
-                                                  demand, h->d_err, staged);
+                                                  demand, h->d_err, staged, nullptr);
   h->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }

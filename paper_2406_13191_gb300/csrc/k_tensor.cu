@@ -1061,7 +1061,8 @@ static dcopf_status tensor_post_round(TensorRun& R, int* d_active, cudaStream_t 
   BatchView& bb = h->bb.v;
   k_bt_select<<<dim3((nl + 255) / 256, B), 256, 0, cs>>>(B, nl, R.st, bb);
   dcopf_status r = run_certify_t<float>(h, B, R.it.loads, R.it.outage, R.st.best_lam, R.st.best_hi,
-                                        R.st.best_lo, R.st.cert, nullptr, R.st.cand, R.st.done, cs);
+                                        R.st.best_lo, R.st.cert, nullptr, R.st.cand, R.st.done, cs,
+                                        true);
   if (r) return r;
   k_bt_accept<<<(B + 127) / 128, 128, 0, cs>>>(B, h->ub_any, R.st, bb, d_active);
   h->launches += 2;

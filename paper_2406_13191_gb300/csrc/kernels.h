@@ -73,6 +73,11 @@ struct Workspace {
   DBuf f0, f0_32, u64, u32, demand;
   DBuf eta64, eta32, pit64, pit32, x64, x32, f, sumcost, sump, value, glam, ghi, glo;
   DBuf misc;  // small per-batch scratch
+  // B_r^-1 (e_from - e_to) of each instance's outaged line [batch][nr], left by the base
+  // flows for the certificates of the same solve (valid for wcache_B, wcache_outage)
+  DBuf wcache;
+  int wcache_B = 0;
+  const int* wcache_outage = nullptr;
 };
 
 // BF16 hi/lo operands and TMA descriptors of the tensor-core path.
@@ -198,7 +203,8 @@ void launch_forward64(dcopf_dual* h, int B, const double* x, const double* f0, d
 template <typename S>
 dcopf_status run_certify_t(dcopf_dual* h, int batch, const double* loads, const int* outage,
                            const double* lam, const S* mh, const S* ml, double* bound, double* errb,
-                           const int* mask, const int* done, cudaStream_t s);
+                           const int* mask, const int* done, cudaStream_t s,
+                           bool use_wcache = false);
 size_t certify_smem(const dcopf_dual* h, bool outages);
 
 // Intermediate buffers of one evaluation, all caller-provided ([batch][n] arrays).
