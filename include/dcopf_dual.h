@@ -74,7 +74,11 @@ typedef enum {
                             is launched cooperatively when the driver accepts that,
                             unless the environment sets DCOPF_FUSED_COOPERATIVE=0
                             (read by dcopf_dual_create) */
-  DCOPF_PATH_BATCHED = 3 /* batched contraction kernels replayed from a CUDA graph */
+  DCOPF_PATH_BATCHED = 3, /* batched contraction kernels replayed from a CUDA graph */
+  DCOPF_PATH_SPARSE = 4   /* one CTA per instance runs the iterations with both operator
+                             products as level-scheduled triangular solves on the sparse
+                             LDL^T factor of the reduced Laplacian (no PTDF); FP64; the
+                             iterates equal the plain path's up to rounding */
 } dcopf_path;
 
 /* Network description (Section 2, problem (1)).  Host pointers, copied by

@@ -23,7 +23,7 @@ STATUS = {0: "DCOPF_OK", 1: "DCOPF_ERR_INVALID_ARG", 2: "DCOPF_ERR_NETWORK", 3: 
           4: "DCOPF_ERR_OOM", 5: "DCOPF_ERR_TIMEOUT", 6: "DCOPF_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16x3": 2}
 RULE = {"gdm": 0, "adam": 1, "adagrad": 2}
-PATH = {"auto": 0, "plain": 1, "fused": 2, "batched": 3}
+PATH = {"auto": 0, "plain": 1, "fused": 2, "batched": 3, "sparse": 4}
 
 P = C.c_void_p
 I32P = C.POINTER(C.c_int32)

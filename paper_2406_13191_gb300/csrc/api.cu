@@ -243,7 +243,8 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
   P.decay = p.decay;
   CUDA_TRY(h, h->active.alloc(16));
   int* d_active = h->active.as<int>();
-  const int chunk = std::max(1, p.check_every);
+  // the sparse path iterates inside its kernel until a stop test fires: long rounds
+  const int chunk = std::max(path == DCOPF_PATH_SPARSE ? 64 : 1, p.check_every);
   const double ub_any = h->ub_any;
   if (h->timing && !h->ev0) {
     CUDA_TRY(h, cudaEventCreate(&h->ev0));
@@ -315,7 +316,10 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
     if constexpr (sizeof(S) == 4) {
       if (path == DCOPF_PATH_FUSED) r = run_iters_fused(h, P, st, p.max_iters, p.tol, s);
     }
-    if (path != DCOPF_PATH_FUSED) {
+    if constexpr (sizeof(S) == 8) {
+      if (path == DCOPF_PATH_SPARSE) r = run_iters_sparse(h, B, outage, P, st, chunk, p.max_iters, p.tol, s);
+    }
+    if (path != DCOPF_PATH_FUSED && path != DCOPF_PATH_SPARSE) {
       int prec = path == DCOPF_PATH_PLAIN ? DCOPF_FP64 : p.precision;
       r = run_iters_unfused<S>(h, B, outage, prec, P, st, chunk, p.max_iters, p.tol, s);
     }
@@ -472,6 +476,7 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
   UP(H.line_from, line_from) UP(H.line_to, line_to) UP(H.b, line_b) UP(H.fmax, fmax)
   UP(H.fmin, fmin) UP(fmax32, fmax32) UP(fmin32, fmin32) UP(H.phim, phim)
   UP(H.bus_line_ptr, bus_line_ptr) UP(H.bus_line_idx, bus_line_idx)
+  UP(H.bus_gen_ptr, bus_gen_ptr) UP(H.bus_gen_idx, bus_gen_idx)
   UP(H.bus_line_coef, bus_line_coef) UP(H.gen_bus, gen_bus) UP(H.pmin, pmin) UP(H.pmax, pmax)
   UP(H.cost_lin, cost_lin) UP(H.cost_quad, cost_quad) UP(H.sigma, sigma) UP(H.mid, mid)
   UP(H.ctil, ctil) UP(H.mq, mq) UP(H.cconst, cconst) UP(sig32, sigma32) UP(ctil32, ctil32)
@@ -624,7 +629,7 @@ static dcopf_status check_params(const dcopf_solve_params& p) {
   if (p.rule < DCOPF_GDM || p.rule > DCOPF_ADAGRAD || p.max_iters < 1 || !(p.alpha > 0) ||
       !std::isfinite(p.alpha) || p.check_every < 0 || !(p.gap >= 0) || !(p.decay > 0) ||
       !(p.beta1 >= 0 && p.beta1 < 1) || !(p.beta2 >= 0 && p.beta2 < 1) || !(p.eps >= 0) ||
-      p.path < DCOPF_PATH_AUTO || p.path > DCOPF_PATH_BATCHED)
+      p.path < DCOPF_PATH_AUTO || p.path > DCOPF_PATH_SPARSE)
     return DCOPF_ERR_INVALID_ARG;
   if (p.precision != DCOPF_FP64 && p.precision != DCOPF_FP32 && p.precision != DCOPF_BF16X3)
     return DCOPF_ERR_INVALID_ARG;
@@ -653,7 +658,7 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
   if ((r = run_base_flows(h, batch, loads, outage, s))) return r;
   dcopf_solve_params q = p;
   q.precision = prec;
-  if (path == DCOPF_PATH_PLAIN)
+  if (path == DCOPF_PATH_PLAIN || path == DCOPF_PATH_SPARSE)
     return solve_loop<double>(h, batch, loads, outage, q, path, lambda, mu_hi, mu_lo, best_bound,
                               iters, inst_status, s);
   if (path == DCOPF_PATH_BATCHED && prec == DCOPF_BF16X3)

@@ -35,6 +35,7 @@ struct DevNet {
   const float* fmax32; const float* fmin32;
   const double* phim;       // Phi mid [n_line]
   const int* bus_line_ptr; const int* bus_line_idx; const double* bus_line_coef;
+  const int* bus_gen_ptr; const int* bus_gen_idx;
   // generators
   const int* gen_bus;
   const double* pmin; const double* pmax; const double* cost_lin; const double* cost_quad;

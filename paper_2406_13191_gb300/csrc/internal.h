@@ -45,6 +45,8 @@ struct HostNet {
   std::vector<double> sigma, mid, ctil, mq, cconst;
   // bus -> incident lines (+1 from-bus, -1 to-bus), for E^T Omega eta
   std::vector<int> bus_line_ptr, bus_line_idx;
+  // bus -> generators at it (ascending generator index), for sparse injections
+  std::vector<int> bus_gen_ptr, bus_gen_idx;
   std::vector<double> bus_line_coef;  // +b_l or -b_l
   SparseFactor F;
   std::vector<double> phi;  // Phi~ = Phi diag(sigma), row-major [n_line][n_gen]

@@ -155,28 +155,7 @@ __global__ void k_dispatch32(DevNet N, int B, const float* __restrict__ x, doubl
 }
 
 // ---------------------------------------------------------------- ascent step
-// One projected step of the chosen rule on one coordinate (Section 3.3):
-//   GDM  (Algorithm 1, heavy ball): s1 <- rho s1 + a g;  theta <- theta + s1
-//        (as printed: additionally theta <- theta + a g)
-//   Adam: s1 <- b1 s1 + (1-b1) g; s2 <- b2 s2 + (1-b2) g^2;
-//         theta <- theta + a (s1/c1) / (sqrt(s2/c2) + eps), c = 1 - beta^t
-//   AdaGrad: s1 <- s1 + g^2; theta <- theta + a g / (sqrt(s1) + eps)
-template <typename S>
-__device__ __forceinline__ S rule_step(const StepArgs& P, S theta, S g, S& s1, S& s2, S a) {
-  if (P.rule == DCOPF_GDM) {
-    s1 = S(P.rho) * s1 + a * g;
-    theta += s1;
-    if (P.as_printed) theta += a * g;
-  } else if (P.rule == DCOPF_ADAM) {
-    s1 = S(P.beta1) * s1 + (S(1) - S(P.beta1)) * g;
-    s2 = S(P.beta2) * s2 + (S(1) - S(P.beta2)) * g * g;
-    theta += a * (s1 / S(P.bc1)) / (sqrt(s2 / S(P.bc2)) + S(P.eps));
-  } else {
-    s1 += g * g;
-    theta += a * g / (sqrt(s1) + S(P.eps));
-  }
-  return theta;
-}
+// (rule_step, the rule on one coordinate, is in kernels.h)
 
 // Step kernel: records the best point (largest in-loop value) before stepping,
 // then updates mu (projected to >= 0) and lambda.  Grid (ceil(nl/256), B).

@@ -334,6 +334,159 @@ template __global__ void k_certify<float>(DevNet, const double*, const int*, con
                                           const float*, const float*, double*, double*, const int*,
                                           const int*, int, const double*);
 
+// Sparse operator form of the iteration: one CTA runs up to n_iters iterations of its
+// instance with both operator products as level-scheduled triangular solves on the
+// LDL^T factor of the reduced Laplacian, and no Phi~ (FP64 throughout):
+//   adjoint  z = B_r^-1 E_r^T Omega eta' (eta'_k = u^T eta for an outaged line k),
+//            pi~_j = sigma_j z_bus(j)                              (eq. (6): C^T mu)
+//   minimiser x* from w = ctil + sigma lambda + pi~                (eq. (6) / eq. (16))
+//   forward  theta = B_r^-1 (G sigma x*), f = Omega E theta + f0 (+ u f_k)  (constraint (1c))
+//   value, supergradient, projected step and stop tests exactly as the per-phase path
+//   (k_grad_value, k_step, k_close_iter), so the iterates are the same up to rounding.
+// A CTA leaves its loop when its instance is done or a stop test fires (the host then
+// certifies or stops it); the state stays in the solver's arrays between launches.
+__global__ void k_sparse_iters(DevNet N, StepArgs P, SolveState<double> st,
+                               const int* __restrict__ outage, const double* __restrict__ f0,
+                               const double* __restrict__ u, const double* __restrict__ demand,
+                               int n_iters, int max_iters, double tol, int staged) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ double red[32];
+  __shared__ double s_pw[3];
+  __shared__ int s_stop;
+  const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  PackedFactor PF;
+  const PackedFactor* pf = nullptr;
+  if (staged) { PF = stage_factor(N, sm); pf = &PF; }
+  double* X = (double*)(sm + (staged ? N.fac_bytes : 0));  // [nr] solve vector
+  double* xg = X + N.nr;                                    // [n_gen] minimiser
+  const int nl = N.n_line, ng = N.n_gen;
+  const int k = outage ? outage[b] : -1;
+  const size_t o = (size_t)b * nl;
+  double* mh = st.mu_hi + o;
+  double* ml = st.mu_lo + o;
+  const double* fr0 = f0 + o;
+  const double* ur = u + o;
+  const double D = demand[b];
+  for (int it = 0; it < n_iters; ++it) {
+    if (tid == 0) s_stop = st.done[b] || st.cand[b] != 0;
+    __syncthreads();
+    if (s_stop) break;
+    // adjoint: the outaged line's multiplier is replaced by u^T eta (eta_k = 0)
+    double ue = 0.0;
+    if (k >= 0) {
+      for (int l = tid; l < nl; l += nt)
+        if (l != k) ue += ur[l] * (mh[l] - ml[l]);
+      ue = block_sum(ue, red);
+    }
+    for (int q = tid; q < N.nr; q += nt) {
+      const int bus = N.bus_of_pos[q];
+      double r = 0.0;
+      for (int p = N.bus_line_ptr[bus]; p < N.bus_line_ptr[bus + 1]; ++p) {
+        const int l = N.bus_line_idx[p];
+        r += N.bus_line_coef[p] * (l == k ? ue : mh[l] - ml[l]);
+      }
+      X[q] = r;
+    }
+    __syncthreads();
+    ldl_solve(N, pf, X);
+    // minimiser, generation cost and dispatch
+    const double lam = st.lam[b];
+    const float kk = (float)(st.iter[b] + 1), wk = kk * kk;  // weight of the mean of minimisers
+    double c = 0.0, ps = 0.0;
+    for (int j = tid; j < ng; j += nt) {
+      const double sg = N.sigma[j];
+      const double w = N.ctil[j] + sg * lam + sg * theta_at(N, X, N.gen_bus[j]);
+      const double x = inner_x<double>(w, N.mq[j]);
+      xg[j] = x;
+      c += (N.mq[j] * x + N.ctil[j]) * x + N.cconst[j];
+      ps += N.mid[j] + sg * x;
+      if (st.xsum) st.xsum[(size_t)b * ng + j] += wk * (float)x;
+    }
+    c = block_sum(c, red);   // (its barriers also publish xg and retire the reads of X)
+    ps = block_sum(ps, red);
+    if (tid == 0 && st.wsum) st.wsum[b] += (double)wk;
+    // forward: injections sigma_j x_j at the generator buses (fixed order per bus)
+    for (int q = tid; q < N.nr; q += nt) {
+      const int bus = N.bus_of_pos[q];
+      double y = 0.0;
+      for (int p = N.bus_gen_ptr[bus]; p < N.bus_gen_ptr[bus + 1]; ++p) {
+        const int j = N.bus_gen_idx[p];
+        y += N.sigma[j] * xg[j];
+      }
+      X[q] = y;
+    }
+    __syncthreads();
+    ldl_solve(N, pf, X);
+    auto flow = [&](int l) {  // Phi~ x on line l (pre-outage)
+      return N.line_b[l] * (theta_at(N, X, N.line_from[l]) - theta_at(N, X, N.line_to[l]));
+    };
+    const double fk = k >= 0 ? flow(k) + fr0[k] : 0.0;
+    // value (k_grad_value)
+    double acc = 0.0;
+    for (int l = tid; l < nl; l += nt) {
+      if (l == k) continue;
+      const double f = flow(l) + fr0[l] + (k >= 0 ? ur[l] * fk : 0.0);
+      acc += mh[l] * (f - N.fmax[l]) + ml[l] * (N.fmin[l] - f);
+    }
+    acc = block_sum(acc, red);
+    const double gl = ps - D;
+    const double value = c + lam * gl + acc;
+    // projected step (k_step): best point first, then mu and lambda
+    const int t = st.iter[b] + 1;
+    if (tid == 0) {
+      s_pw[0] = pow(P.decay, (double)(t - 1));
+      s_pw[1] = 1.0 - pow(P.beta1, (double)t);
+      s_pw[2] = 1.0 - pow(P.beta2, (double)t);
+      s_stop = value > st.best[b];  // reused: whether this point improves the best
+    }
+    __syncthreads();
+    StepArgs Q = P;
+    Q.bc1 = s_pw[1];
+    Q.bc2 = s_pw[2];
+    const double scale = s_pw[0];
+    const bool better = s_stop != 0;
+    const double am = P.alpha * scale;
+    for (int l = tid; l < nl; l += nt) {
+      const double h = mh[l], lo = ml[l];
+      if (better) {
+        st.best_hi[o + l] = h;
+        st.best_lo[o + l] = lo;
+      }
+      double gh = 0.0, gll = 0.0;
+      if (l != k) {
+        const double f = flow(l) + fr0[l] + (k >= 0 ? ur[l] * fk : 0.0);
+        gh = f - N.fmax[l];
+        gll = N.fmin[l] - f;
+      }
+      const double h2 = rule_step<double>(Q, h, gh, st.s1_hi[o + l], st.s2_hi[o + l], am);
+      const double l2 = rule_step<double>(Q, lo, gll, st.s1_lo[o + l], st.s2_lo[o + l], am);
+      mh[l] = h2 > 0.0 ? h2 : 0.0;
+      ml[l] = l2 > 0.0 ? l2 : 0.0;
+    }
+    if (tid == 0) {
+      // lambda, best value and stop tests (k_step, k_close_iter)
+      double lm = lam;
+      if (better) {
+        st.best[b] = value;
+        st.best_lam[b] = lam;
+        st.best_iter[b] = t;
+      }
+      double s1 = st.lam_s1[b], s2 = st.lam_s2[b];
+      lm = rule_step<double>(Q, lm, gl, s1, s2, P.alpha_lambda * scale);
+      st.lam[b] = lm;
+      st.lam_s1[b] = s1;
+      st.lam_s2[b] = s2;
+      st.prev[b] = value;
+      st.iter[b] = t;
+      if (st.has_target && st.best[b] >= st.thresh[b] + st.margin[b]) st.cand[b] = 1;
+      if (t >= max_iters) st.cand[b] = 2;
+      if (tol > 0.0 && t > 1 && fabs(value - st.prev2[b]) < tol) st.cand[b] = 2;
+      st.prev2[b] = value;
+    }
+    __syncthreads();  // the next loop reads mu, lambda and the flags
+  }
+}
+
 // Shared memory of a sparse kernel with n_vec solution vectors; *staged tells whether
 // the packed factor fits beside them.
 static size_t sparse_smem(const dcopf_dual* h, int n_vec, int* staged) {
@@ -356,6 +509,27 @@ static int sparse_threads(const dcopf_dual* h) {
   int w = 128;
   while (w < 512 && w < h->host.F.n / 8) w *= 2;
   return w;
+}
+
+dcopf_status run_iters_sparse(dcopf_dual* h, int B, const int* outage, const StepArgs& P,
+                              SolveState<double>& st, int n_iters, int max_iters, double tol,
+                              cudaStream_t s) {
+  // [nr] solve vector plus [n_gen] minimiser, counted as whole vectors of nr doubles
+  const int nvec = 1 + (h->dev.n_gen + h->dev.nr - 1) / std::max(1, h->dev.nr);
+  int staged = 0;
+  size_t smem = sparse_smem(h, nvec, &staged);
+  if (smem > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(k_sparse_iters, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  Workspace& w = h->ws;
+  k_sparse_iters<<<B, sparse_threads(h), smem, s>>>(h->dev, P, st, outage, w.f0.as<double>(),
+                                                     w.u64.as<double>(), w.demand.as<double>(),
+                                                     n_iters, max_iters, tol, staged);
+  h->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { h->last_error = cudaGetErrorString(e); return DCOPF_ERR_CUDA; }
+  return DCOPF_OK;
 }
 
 dcopf_status run_base_flows(dcopf_dual* h, int B, const double* loads, const int* outage,

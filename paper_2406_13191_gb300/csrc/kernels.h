@@ -17,6 +17,30 @@ struct StepArgs {
   double bc1, bc2;  // Adam bias corrections of the current step (set per step)
 };
 
+// One projected step of the chosen rule on one coordinate (Section 3.3):
+//   GDM  (Algorithm 1, heavy ball): s1 <- rho s1 + a g;  theta <- theta + s1
+//        (as printed: additionally theta <- theta + a g)
+//   Adam: s1 <- b1 s1 + (1-b1) g; s2 <- b2 s2 + (1-b2) g^2;
+//         theta <- theta + a (s1/c1) / (sqrt(s2/c2) + eps), c = 1 - beta^t
+//   AdaGrad: s1 <- s1 + g^2; theta <- theta + a g / (sqrt(s1) + eps)
+template <typename S>
+__device__ __forceinline__ S rule_step(const StepArgs& P, S theta, S g, S& s1, S& s2, S a) {
+  if (P.rule == DCOPF_GDM) {
+    s1 = S(P.rho) * s1 + a * g;
+    theta += s1;
+    if (P.as_printed) theta += a * g;
+  } else if (P.rule == DCOPF_ADAM) {
+    s1 = S(P.beta1) * s1 + (S(1) - S(P.beta1)) * g;
+    s2 = S(P.beta2) * s2 + (S(1) - S(P.beta2)) * g * g;
+    theta += a * (s1 / S(P.bc1)) / (sqrt(s2 / S(P.bc2)) + S(P.eps));
+  } else {
+    s1 += g * g;
+    theta += a * g / (sqrt(s1) + S(P.eps));
+  }
+  return theta;
+}
+
+
 // Per-instance solver bookkeeping (device pointers, [batch] each).
 struct SolveStateBase {
   int* done;       // 1 once the instance has stopped
@@ -190,6 +214,9 @@ dcopf_status ensure_mean(dcopf_dual* h, int B, SolveStateBase* st, bool f32, boo
 void launch_mean_out(dcopf_dual* h, int B, const SolveStateBase& st, double* out, cudaStream_t s);
 template <typename T>
 void launch_accum_mean(dcopf_dual* h, int B, const T* x, const SolveStateBase& st, cudaStream_t s);
+dcopf_status run_iters_sparse(dcopf_dual* h, int B, const int* outage, const StepArgs& P,
+                              SolveState<double>& st, int n_iters, int max_iters, double tol,
+                              cudaStream_t s);
 dcopf_status run_primal(dcopf_dual* h, int B, const int* outage, const double* lambda,
                         const double* mh, const double* ml, const double* p_cand,
                         const double* p_ref, double* upper, int* pstatus, double* dispatch,

@@ -217,6 +217,16 @@ dcopf_status build_host_net(const dcopf_network_desc* d, HostNet* H, std::string
     }
   }
 
+  // bus -> generators (ascending index)
+  h.bus_gen_ptr.assign(nb + 1, 0);
+  for (int j = 0; j < ng; ++j) h.bus_gen_ptr[h.gen_bus[j] + 1]++;
+  for (int i = 0; i < nb; ++i) h.bus_gen_ptr[i + 1] += h.bus_gen_ptr[i];
+  h.bus_gen_idx.resize(ng);
+  {
+    std::vector<int> fill(h.bus_gen_ptr.begin(), h.bus_gen_ptr.end() - 1);
+    for (int j = 0; j < ng; ++j) h.bus_gen_idx[fill[h.gen_bus[j]]++] = j;
+  }
+
   // ---- reduced Laplacian, minimum-degree order, symbolic + numeric LDL^T
   SparseFactor& F = h.F;
   int n = nb - 1;

@@ -8,6 +8,7 @@
     python -m paper_2406_13191_gb300.timing mlp --batch 512 --iters 50
     python -m paper_2406_13191_gb300.timing togap --config 2
     python -m paper_2406_13191_gb300.timing primal --batch 1024
+    python -m paper_2406_13191_gb300.timing sparse
 
 ``batched`` runs the tensor-core batched solve (BF16 hi/lo split products) for a
 fixed number of iterations and reports the time of the iteration kernels per batched
@@ -28,7 +29,8 @@ or of the 10000-bus batch (64) to the certified 0.1 % gap against the oracle's o
 (tests/golden/study_gamma.json, c3_gamma.json) in one batched tensor-core call.
 ``primal`` times the primal recovery (an upper bound from the dual point) after solves
 of the 2000-bus instance and of held-out scenarios, and reports the gap it gives without
-a stored optimum.
+a stored optimum.  ``sparse`` times the sparse operator form (triangular solves, no
+PTDF) against the PTDF paths.
 """
 from __future__ import annotations
 
@@ -306,10 +308,41 @@ def primal(batch=1024, repeat=5):
     print(json.dumps(out))
 
 
+def sparse(iters=100):
+    """The sparse operator form (LDL^T solves, no PTDF) against the PTDF paths for a fixed
+    number of FP64 iterations: the 2000-bus instance alone (sparse vs plain FP64 per-phase
+    kernels) and the first 256 instances of the 4600-bus batch (half with an outage;
+    sparse vs the tensor-core batched path).  Iteration-kernel time from the library's
+    events."""
+    out = dict(mode="sparse", iters=iters)
+    kw = dict(rule="adam", alpha=1000.0, beta1=0.95, beta2=0.999, max_iters=iters)
+
+    def run(g, loads, outage, path, precision):
+        g.solve(loads, outage=outage, path=path, precision=precision, **kw)  # warm-up
+        g.set_timing(True)
+        g.read_timing()
+        r = g.solve(loads, outage=outage, path=path, precision=precision, **kw)
+        ms, launches, evals = g.read_timing()
+        g.set_timing(False)
+        return dict(ms=ms, us_per_instance_iteration=1e3 * ms / max(1, evals),
+                    evaluations=evals, status_cap=int((r.status == 1).sum().item()))
+
+    net, base = synth.network_for(1)
+    g = DcopfDual(net, device=0)
+    out["single_2000bus"] = {p: run(g, base[None], None, p, "fp64") for p in ("sparse", "plain")}
+    w = synth.workload(2, batch=256)
+    g = DcopfDual(w.net, device=0)
+    L = torch.tensor(w.loads, device="cuda")
+    O = torch.tensor(w.outage, device="cuda")
+    out["batch_4600bus_256"] = dict(sparse=run(g, L, O, "sparse", "fp64"),
+                                    batched_bf16x3=run(g, L, O, "batched", "bf16x3"))
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("mode", choices=["batched", "certify", "fused", "group", "setup", "mlp", "togap",
-                                     "primal"])
+                                     "primal", "sparse"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--iters", type=int, default=16)
@@ -330,6 +363,8 @@ def main():
         togap(a.config)
     elif a.mode == "primal":
         primal(a.batch)
+    elif a.mode == "sparse":
+        sparse(a.iters if a.iters != 16 else 100)
     else:
         fused(a.repeat, a.verbose)
 

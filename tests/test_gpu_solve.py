@@ -186,3 +186,39 @@ def test_tensor_batched_solve_c1_scenarios():
     res = g.solve(w.loads, path="batched", precision="bf16x3", target=gams, **ADAM_QP)
     for b in range(4):
         _check(res, on, w.loads[b], gams[b], b=b)
+
+
+def test_sparse_path_follows_the_plain_path_and_oracle(c1):
+    """The sparse operator form (level-scheduled LDL^T solves, no PTDF) runs the same
+    FP64 iteration as the plain path: after 40 GDM iterations both agree with the
+    oracle like the plain path does."""
+    net, base, on, g, gam = c1
+    kw = dict(rule="gdm", alpha=10.0, alpha_lambda=0.1, rho=0.995, max_iters=40)
+    res = g.solve(base[None], path="sparse", precision="fp64", **kw)
+    ref = dcopf.solve(on, base, **kw)
+    assert res.iters[0].item() == 40 and res.status[0].item() == 1
+    assert abs(res.lam[0].item() - ref["lam"]) <= 1e-8 * abs(ref["lam"])
+    assert np.allclose(res.mu_hi[0].cpu().numpy(), ref["mu_hi"], rtol=1e-7, atol=1e-7)
+    assert abs(res.bound[0].item() - ref["best"]) <= 1e-8 * abs(ref["best"])
+
+
+def test_sparse_path_reaches_gap(c1):
+    net, base, on, g, gam = c1
+    res = g.solve(base[None], path="sparse", precision="fp64", target=[gam], **ADAM_QP)
+    _check(res, on, base, gam)
+
+
+def test_sparse_path_with_outages_matches_the_plain_path():
+    """A batch with line outages: the sparse path (outage through u^T eta and the
+    rank-1 flow correction) and the plain path (LODF on the PTDF) take the same 30 GDM
+    iterations to 1e-8."""
+    w = synth.scenario_workload(301, 80, 120, 15, True, batch=4, n_out=2)
+    g = DcopfDual(w.net)
+    kw = dict(rule="gdm", alpha=10.0, alpha_lambda=0.1, rho=0.99, max_iters=30, precision="fp64")
+    a = g.solve(w.loads, outage=w.outage, path="sparse", **kw)
+    b = g.solve(w.loads, outage=w.outage, path="plain", **kw)
+    assert np.all(a.iters.cpu().numpy() == 30) and np.all(b.iters.cpu().numpy() == 30)
+    la, lb = a.lam.cpu().numpy(), b.lam.cpu().numpy()
+    assert np.all(np.abs(la - lb) <= 1e-8 * np.abs(lb))
+    assert np.allclose(a.mu_hi.cpu().numpy(), b.mu_hi.cpu().numpy(), rtol=1e-7, atol=1e-7)
+    assert np.allclose(a.bound.cpu().numpy(), b.bound.cpu().numpy(), rtol=1e-9)
