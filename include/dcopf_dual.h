@@ -103,7 +103,11 @@ typedef struct {
   int32_t device;    /* CUDA device ordinal; -1 = current device */
   int32_t max_batch; /* largest batch the handle will see (workspaces sized lazily anyway) */
   int32_t verbose;   /* 1 = print setup statistics to stderr */
-  int32_t reserved;
+  int32_t operator_form; /* 0 = the PTDF Phi~ and the sparse factor (every call);
+                            1 = the sparse factor only: no Phi~ is built or stored (for
+                            networks whose n_line x n_gen PTDF does not fit); then only
+                            DCOPF_PATH_SPARSE (and PATH_AUTO, which picks it) and
+                            dcopf_dual_certify_bound run, the rest return UNSUPPORTED */
 } dcopf_options;
 
 /* Parameters of dcopf_dual_solve_batch.  Zero-initialise and set what you need;

@@ -40,7 +40,7 @@ class NetworkDesc(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("device", C.c_int32), ("max_batch", C.c_int32), ("verbose", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("operator_form", C.c_int32)]
 
 
 class SolveParams(C.Structure):

@@ -420,7 +420,9 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
     if (e && e[0] == '0') h->fused_coop = 0;
   }
   std::string err;
-  dcopf_status st = build_host_net(net, &h->host, &err, h->verbose);
+  h->sparse_only = opt && opt->operator_form == 1;
+  if (opt && (opt->operator_form < 0 || opt->operator_form > 1)) { delete h; return DCOPF_ERR_INVALID_ARG; }
+  dcopf_status st = build_host_net(net, &h->host, &err, h->verbose, !h->sparse_only);
   if (st != DCOPF_OK) {
     if (h->verbose) fprintf(stderr, "[dcopf] create: %s\n", err.c_str());
     delete h;
@@ -451,9 +453,10 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
   std::vector<float> sig32(H.sigma.begin(), H.sigma.end()), ctil32(H.ctil.begin(), H.ctil.end()),
       mq32(H.mq.begin(), H.mq.end()), cconst32(H.cconst.begin(), H.cconst.end()),
       mid32(H.mid.begin(), H.mid.end());
-  std::vector<double> phit((size_t)nl * ng);
-  std::vector<float> phi32((size_t)nl * ng), phit32((size_t)nl * ng);
-  for (int i = 0; i < nl; ++i)
+  const size_t nphi = h->sparse_only ? 0 : (size_t)nl * ng;  // no PTDF on a sparse-only handle
+  std::vector<double> phit(nphi);
+  std::vector<float> phi32(nphi), phit32(nphi);
+  for (int i = 0; i < nl && nphi; ++i)
     for (int j = 0; j < ng; ++j) {
       double v = H.phi[(size_t)i * ng + j];
       phit[(size_t)j * nl + i] = v;
@@ -574,6 +577,7 @@ dcopf_status dcopf_dual_eval(dcopf_dual_t h, int32_t batch, const double* loads,
   if (!lambda || !mu_hi || !mu_lo || !value) return DCOPF_ERR_INVALID_ARG;
   if (precision != DCOPF_FP64 && precision != DCOPF_FP32 && precision != DCOPF_BF16X3)
     return DCOPF_ERR_INVALID_ARG;
+  if (h->sparse_only) return DCOPF_ERR_UNSUPPORTED;  // the evaluation uses Phi~
   DeviceGuard guard(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   if ((r = check_outage(h, batch, outage, s))) return r;
@@ -614,6 +618,7 @@ dcopf_status dcopf_dual_primal_bound(dcopf_dual_t h, int32_t batch, const double
   dcopf_status r = check_batch(h, batch, loads);
   if (r) return r;
   if (!upper || (!p_cand && (!lambda || !mu_hi || !mu_lo))) return DCOPF_ERR_INVALID_ARG;
+  if (h->sparse_only) return DCOPF_ERR_UNSUPPORTED;  // the recovery's flows use Phi~
   DeviceGuard guard(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   if ((r = check_outage(h, batch, outage, s))) return r;
@@ -647,7 +652,10 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
   const dcopf_solve_params& p = *params;
   if ((r = check_params(p))) return r;
   int path = p.path;
-  if (path == DCOPF_PATH_AUTO) path = (batch == 1 && !outage) ? DCOPF_PATH_FUSED : DCOPF_PATH_BATCHED;
+  if (path == DCOPF_PATH_AUTO)
+    path = h->sparse_only ? DCOPF_PATH_SPARSE
+                          : (batch == 1 && !outage) ? DCOPF_PATH_FUSED : DCOPF_PATH_BATCHED;
+  if (h->sparse_only && path != DCOPF_PATH_SPARSE) return DCOPF_ERR_UNSUPPORTED;
   if (path == DCOPF_PATH_FUSED && (batch != 1 || outage)) return DCOPF_ERR_UNSUPPORTED;
   int prec = p.precision;
   DeviceGuard guard(h->device);
@@ -681,6 +689,7 @@ dcopf_status dcopf_dual_solve_group(int32_t n_items, const dcopf_group_item* ite
     const dcopf_group_item& it = items[i];
     if ((r = check_batch(it.net, it.batch, it.loads))) return r;
     if (!it.lambda || !it.mu_hi || !it.mu_lo || !it.best_bound) return DCOPF_ERR_INVALID_ARG;
+    if (it.net->sparse_only) return DCOPF_ERR_UNSUPPORTED;
     if (it.net->device != items[0].net->device) return DCOPF_ERR_INVALID_ARG;
     if (it.params) {
       if ((r = check_params(*it.params))) return r;

@@ -56,7 +56,7 @@ struct HostNet {
 // Builds a HostNet from the C description (validation, ordering, factorisation,
 // PTDF build).  Returns DCOPF_OK or an error with a message in *err.
 dcopf_status build_host_net(const dcopf_network_desc* d, HostNet* out, std::string* err,
-                            bool verbose);
+                            bool verbose, bool build_phi = true);
 
 // Solves B_r theta = rhs in place (rhs indexed by elimination position).
 void host_ldl_solve(const SparseFactor& F, double* x);

@@ -55,6 +55,7 @@ extern "C" dcopf_status dcopf_dual_eval_noalloc(dcopf_dual_t h, int32_t batch, c
   if (!h || batch < 1 || !loads || !lambda || !mu_hi || !mu_lo || !value)
     return DCOPF_ERR_INVALID_ARG;
   if (precision != DCOPF_FP64 && precision != DCOPF_FP32) return DCOPF_ERR_UNSUPPORTED;
+  if (h->sparse_only) return DCOPF_ERR_UNSUPPORTED;  // the evaluation uses Phi~
   const size_t B = (size_t)batch, nl = (size_t)h->host.n_line, ng = (size_t)h->host.n_gen;
   // scratch carve-up: every section 256-byte aligned
   size_t need = 0;

@@ -181,6 +181,7 @@ struct dcopf_dual {
   // layout of that shape, validated once (occupancy queries cost host time per solve)
   int fshape_C = 0, fshape_G = 0, fshape_phi = 0, fshape_rpc = 0, fshape_slice = 0;
   size_t fshape_smem = 0;
+  bool sparse_only = false;      // created with operator_form 1: no Phi~ on the device
   int fused_coop = -1;           // -1 unknown, 1 cooperative+cluster launch accepted, 0 not
   // split-K of the batched adjoint GEMM chosen by timing (for batch size tune_B)
   int tune_B = 0, tune_splits = 0, tune_kbps = 0;

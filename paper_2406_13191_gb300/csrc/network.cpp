@@ -114,7 +114,7 @@ void host_ldl_solve(const SparseFactor& F, double* x) {
 }
 
 dcopf_status build_host_net(const dcopf_network_desc* d, HostNet* H, std::string* err,
-                            bool verbose) {
+                            bool verbose, bool build_phi) {
   auto fail = [&](dcopf_status s, const std::string& m) {
     *err = m;
     return s;
@@ -401,8 +401,9 @@ dcopf_status build_host_net(const dcopf_network_desc* d, HostNet* H, std::string
       ((uint16_t*)(B + F.off_blev))[l] = (uint16_t)F.bwd_level_ptr[l];
   }
 
-  // ---- Phi~ = H_a G diag(sigma), built one generator bus at a time (FP64)
-  h.phi.assign((size_t)nl * ng, 0.0);
+  // ---- Phi~ = H_a G diag(sigma), built one generator bus at a time (FP64); skipped
+  // for a sparse-only handle
+  if (build_phi) h.phi.assign((size_t)nl * ng, 0.0);
   std::vector<int> gens_order(ng);
   std::iota(gens_order.begin(), gens_order.end(), 0);
   unsigned nthreads = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
@@ -422,10 +423,12 @@ dcopf_status build_host_net(const dcopf_network_desc* d, HostNet* H, std::string
       }
     }
   };
-  std::vector<std::thread> th;
-  for (unsigned t = 1; t < nthreads; ++t) th.emplace_back(worker, (int)t);
-  worker(0);
-  for (auto& t : th) t.join();
+  if (build_phi) {
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < nthreads; ++t) th.emplace_back(worker, (int)t);
+    worker(0);
+    for (auto& t : th) t.join();
+  }
   // Phi mid = Phi~ diag(1/sigma) mid, computed from the unscaled columns
   h.phim.assign(nl, 0.0);
   {

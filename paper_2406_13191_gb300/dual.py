@@ -57,7 +57,10 @@ class DcopfDual:
     line_from, line_to, line_b, flow_max, flow_min, gen_bus, pmin, pmax, cost_lin,
     cost_quad, base_mva, slack_bus)."""
 
-    def __init__(self, net, device: int | None = None, verbose: bool = False):
+    def __init__(self, net, device: int | None = None, verbose: bool = False,
+                 operator_form: str = "ptdf"):
+        """``operator_form``: "ptdf" (the PTDF Phi~ and the sparse factor, every call) or
+        "sparse" (the sparse factor only, no PTDF: path="sparse" solves and certificates)."""
         self.lib = _lib.load()
         d = net.as_dict() if hasattr(net, "as_dict") else dict(net)
         self._keep = []
@@ -89,6 +92,7 @@ class DcopfDual:
         opt = _lib.Options()
         opt.device = -1 if device is None else int(device)
         opt.verbose = 1 if verbose else 0
+        opt.operator_form = {"ptdf": 0, "sparse": 1}[operator_form]
         h = C.c_void_p()
         _lib.check(self.lib.dcopf_dual_create(C.byref(desc), C.byref(opt), C.byref(h)),
                    "dcopf_dual_create")

@@ -166,9 +166,15 @@ def setup():
                precision="bf16x3")
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        res[f"{net.n_bus}-bus"] = dict(n_line=net.n_line, n_gen=net.n_gen, create_s=t1 - t0,
-                                       first_tensor_eval_s=t2 - t1)
         del g
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        gs = DcopfDual(net, device=0, operator_form="sparse")
+        t4 = time.perf_counter()
+        res[f"{net.n_bus}-bus"] = dict(n_line=net.n_line, n_gen=net.n_gen, create_s=t1 - t0,
+                                       first_tensor_eval_s=t2 - t1,
+                                       create_sparse_only_s=t4 - t3)
+        del gs
     print(json.dumps(res))
 
 

@@ -222,3 +222,24 @@ def test_sparse_path_with_outages_matches_the_plain_path():
     assert np.all(np.abs(la - lb) <= 1e-8 * np.abs(lb))
     assert np.allclose(a.mu_hi.cpu().numpy(), b.mu_hi.cpu().numpy(), rtol=1e-7, atol=1e-7)
     assert np.allclose(a.bound.cpu().numpy(), b.bound.cpu().numpy(), rtol=1e-9)
+
+
+def test_sparse_only_handle(c1):
+    """A handle created without the PTDF (operator_form "sparse") solves on the sparse
+    path exactly like a full handle's sparse path, and refuses the PTDF calls."""
+    from paper_2406_13191_gb300._lib import DcopfError
+    net, base, on, g, gam = c1
+    gs = DcopfDual(net, operator_form="sparse")
+    kw = dict(rule="gdm", alpha=10.0, alpha_lambda=0.1, rho=0.995, max_iters=40, precision="fp64")
+    a = gs.solve(base[None], path="auto", **kw)
+    b = g.solve(base[None], path="sparse", **kw)
+    assert a.iters[0].item() == b.iters[0].item() == 40
+    assert a.bound[0].item() == b.bound[0].item()
+    assert torch.equal(a.mu_hi, b.mu_hi)
+    bd, _ = gs.certify(base[None], a.lam, a.mu_hi, a.mu_lo)
+    assert abs(bd[0].item() - a.bound[0].item()) <= 1e-12 * abs(a.bound[0].item())
+    for call in (lambda: gs.solve(base[None], path="fused", **kw),
+                 lambda: gs.eval(base[None], a.lam, a.mu_hi, a.mu_lo),
+                 lambda: gs.primal_bound(base[None], a.lam, a.mu_hi, a.mu_lo)):
+        with pytest.raises(DcopfError, match="UNSUPPORTED"):
+            call()
