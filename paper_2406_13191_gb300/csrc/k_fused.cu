@@ -102,7 +102,9 @@ __device__ __forceinline__ float fused_rule_f(const RuleF& R, float theta, float
   } else if (R.rule == DCOPF_ADAM) {
     s1 = R.beta1 * s1 + R.omb1 * g;
     s2 = R.beta2 * s2 + R.omb2 * g * g;
-    theta += a * (s1 / bc1) / (sqrtf(s2 / bc2) + R.eps);
+    // bc1, bc2 are the reciprocals of the bias corrections 1 - beta^t (one division
+    // fewer on the critical path of every line step)
+    theta += (a * bc1) * s1 / (sqrtf(s2 * bc2) + R.eps);
   } else {
     s1 += g * g;
     theta += a * g / (sqrtf(s1) + R.eps);
@@ -140,10 +142,10 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   const int ngp = (ng + 3) & ~3;
   const int rpc = A.rows_per_cta;
   // shared memory carve-up: per-slice generator constants (FP64), then floats
-  double* gk = (double*)smem_raw;                // [6][SLp] ctil, sigma, mq, cconst, mid 2^e, sigma 2^e
+  double* gk = (double*)smem_raw;                // [7][SLp] ctil, sigma, mq, cconst, mid 2^e, sigma 2^e, 1/(2 mq)
   const int SLp = (SL + 1) & ~1;
   // [C][SL] partial adjoints of own slice, one row per cluster rank (written by peers)
-  float* recv = (float*)(gk + 6 * SLp);
+  float* recv = (float*)(gk + 7 * SLp);
   float* xs = recv + ((C * SL + 3) & ~3);        // [ngp] x* of all gens (written by peers)
   float* tmp = xs + ngp;                         // [SL * NCLp] cluster partials of own slice
   float* xacc = tmp + SL * NCLp;                 // [SL] mean of the minimisers (cluster 0)
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
   // bulk copy of own slice's partials of every cluster
   __shared__ __align__(8) uint64_t s_mb[3];
   __shared__ double s_pw[6];    // decay^(t-1), 1 - beta1^t, 1 - beta2^t; running powers
-  __shared__ float s_pwf[8];    // FP32 step factors by loop parity: alpha decay^(t-1), bias corrections, alpha_lambda decay^(t-1)
+  __shared__ float s_pwf[8];    // FP32 step factors by loop parity: alpha decay^(t-1), 1 / bias corrections, alpha_lambda decay^(t-1)
 
   const float* phig = N.phi32 + (size_t)r0 * ng;  // own rows in global memory
   if (A.phi_in_smem)
@@ -178,6 +180,7 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
     const int j = j0 + jj;
     gk[jj] = N.ctil[j]; gk[SLp + jj] = N.sigma[j]; gk[2 * SLp + jj] = N.mq[j];
     gk[3 * SLp + jj] = N.cconst[j];
+    gk[6 * SLp + jj] = N.mq[j] > 0.0 ? 0.5 / N.mq[j] : 0.0;
     // the dispatch mid + sigma x in units of the fixed point (scaling by 2^e is exact,
     // so one FMA rounds exactly as the unscaled expression would)
     gk[4 * SLp + jj] = N.mid[j] * A.pscale; gk[5 * SLp + jj] = N.sigma[j] * A.pscale;
@@ -340,8 +343,8 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
         s_pw[1] = 1.0 - s_pw[4];
         s_pw[2] = 1.0 - s_pw[5];
         pf[0] = (float)(A.P.alpha * s_pw[0]);
-        pf[1] = (float)s_pw[1];
-        pf[2] = (float)s_pw[2];
+        pf[1] = (float)(1.0 / s_pw[1]);  // reciprocals of the bias corrections
+        pf[2] = (float)(1.0 / s_pw[2]);
         pf[3] = (float)(A.P.alpha_lambda * s_pw[0]);
       }
       const int waited_out = __syncthreads_or(ok ? 0 : 1);
@@ -392,7 +395,13 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
         }
         const double ct = gk[jj], sg = gk[SLp + jj], mq = gk[2 * SLp + jj];
         const double w = ct + sg * lam + (double)s;
-        const float x = inner_x<float>((float)w, (float)mq);
+        float x;
+        if (mq > 0.0) {  // eq. (16): clip(-w / (2 mq), -1, 1), with 1 / (2 mq) precomputed
+          x = -(float)w * (float)gk[6 * SLp + jj];
+          x = x > 1.f ? 1.f : (x < -1.f ? -1.f : x);
+        } else {
+          x = inner_x<float>((float)w, 0.f);
+        }
         xs[j0 + jj] = x;  // x* to every rank
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -596,7 +605,7 @@ static size_t fused_smem(int ng, int rpc, int C, int NCL, bool phi) {
   size_t f = (size_t)((C * SL + 3) & ~3) + ngp + (size_t)SL * NCLp + ((SL + 3) & ~3) +
              12 * (size_t)rpc;
   if (phi) f += (size_t)rpc * ng;
-  return f * sizeof(float) + 6 * (size_t)SLp * sizeof(double);
+  return f * sizeof(float) + 7 * (size_t)SLp * sizeof(double);
 }
 
 // g_cap bounds the grid (fewer, larger CTAs: more rows each, fewer clusters to
