@@ -132,14 +132,16 @@ def dcopf_solve(on, loads):
     return dcopf.solve(on, loads, rule="adam", alpha=1000.0, beta1=0.95, beta2=0.999, max_iters=60)
 
 
-def test_mean_dispatch_of_the_plain_path_follows_the_oracle():
-    """The plain FP64 path evaluates the oracle's points (test_gpu_solve), so its mean of
-    the minimisers (FP32 sums of k^2 x) agrees with the oracle's to FP32 rounding."""
+@pytest.mark.parametrize("path", ["plain", "sparse"])
+def test_mean_dispatch_of_the_fp64_paths_follows_the_oracle(path):
+    """The plain and sparse FP64 paths evaluate the oracle's points (test_gpu_solve), so
+    their mean of the minimisers (FP32 sums of k^2 x) agrees with the oracle's to FP32
+    rounding."""
     w = synth.scenario_workload(209, 70, 100, 15, True, batch=1, n_out=0)
     g = DcopfDual(w.net)
     on = onet(w.net)
     kw = dict(rule="gdm", alpha=10.0, alpha_lambda=0.1, rho=0.995, max_iters=40)
-    res = g.solve(w.loads, path="plain", precision="fp64", mean_dispatch=True, **kw)
+    res = g.solve(w.loads, path=path, precision="fp64", mean_dispatch=True, **kw)
     ref = dcopf.solve(on, w.loads[0], **kw)
     assert res.iters[0].item() == 40
     md = res.mean_dispatch[0].cpu().numpy()
