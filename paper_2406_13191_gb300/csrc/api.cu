@@ -20,6 +20,7 @@ dcopf_dual::~dcopf_dual() {
   if (ev1) cudaEventDestroy(ev1);
   if (tev) cudaEventDestroy(tev);
   if (tstream) cudaStreamDestroy(tstream);
+  if (cstream) cudaStreamDestroy(cstream);
   if (h_pinned) cudaFreeHost(h_pinned);
 }
 

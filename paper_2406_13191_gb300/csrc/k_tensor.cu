@@ -792,10 +792,15 @@ __global__ void k_bt_finalize(int B, int ld_l, int max_iters, double tol, SolveS
   }
 }
 
-// Copies the frozen candidates' points (state buffer of parity iter & 1) to best_*.
-__global__ void k_bt_select(int B, int nl, SolveState<float> st, BatchView bb) {
+// Copies the frozen candidates' points (state buffer of parity iter & 1) to best_*, and
+// snapshots which instances are staged (snap[b] = 1): the certificate and the accept
+// step of this round act on exactly those, while the next round's iterations may
+// freeze others.
+__global__ void k_bt_select(int B, int nl, SolveState<float> st, BatchView bb, int* snap) {
   const int b = blockIdx.y;
-  if (!st.cand[b] || st.done[b]) return;
+  const bool staged = st.cand[b] && !st.done[b];
+  if (blockIdx.x == 0 && threadIdx.x == 0) snap[b] = staged ? 1 : 0;
+  if (!staged) return;
   const int pb = st.iter[b] & 1;
   const float* sh = pb ? bb.mu2_hi : st.mu_hi;
   const float* sl = pb ? bb.mu2_lo : st.mu_lo;
@@ -808,10 +813,11 @@ __global__ void k_bt_select(int B, int nl, SolveState<float> st, BatchView bb) {
 // After certification: accept, stop, or unfreeze with a larger in-loop margin.  The
 // evaluation of a frozen point counts; an unfrozen instance moves on to the point
 // already stepped to.
-__global__ void k_bt_accept(int B, double ub_any, SolveStateBase st, BatchView bb, int* active) {
+__global__ void k_bt_accept(int B, double ub_any, SolveStateBase st, BatchView bb,
+                            const int* __restrict__ snap, int* active) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
-  if (!st.done[b] && st.cand[b]) {
+  if (snap[b] && !st.done[b] && st.cand[b]) {
     const double c = st.cert[b];
     if (st.cand[b] == 1) {
       if (c >= st.thresh[b]) {
@@ -1053,19 +1059,36 @@ static bool tensor_enqueue_chunk(TensorRun& R, int chunk, cudaStream_t cs) {
   return ok;
 }
 
-// After a chunk: stage the frozen candidates, certify them in FP64, then accept, stop
-// or resume each; adds the count of instances still running to *d_active.
-static dcopf_status tensor_post_round(TensorRun& R, int* d_active, cudaStream_t cs) {
+// After a chunk: stage and snapshot the frozen candidates (on the solve's stream cs),
+// then certify them in FP64 on the certificate stream cc, which runs beside the next
+// chunk of iterations (the staged instances stay frozen meanwhile).  `done_ev` is
+// recorded on cc when the certificate has finished.
+static dcopf_status tensor_stage_certify(TensorRun& R, cudaStream_t cs, cudaStream_t cc,
+                                         cudaEvent_t staged_ev, cudaEvent_t done_ev) {
   dcopf_dual* h = R.it.h;
   const int B = R.it.B, nl = h->host.n_line;
   BatchView& bb = h->bb.v;
-  k_bt_select<<<dim3((nl + 255) / 256, B), 256, 0, cs>>>(B, nl, R.st, bb);
+  int* snap = h->bb.snap.as<int>();
+  k_bt_select<<<dim3((nl + 255) / 256, B), 256, 0, cs>>>(B, nl, R.st, bb, snap);
+  if (cudaEventRecord(staged_ev, cs) != cudaSuccess || cudaStreamWaitEvent(cc, staged_ev, 0) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
   dcopf_status r = run_certify_t<float>(h, B, R.it.loads, R.it.outage, R.st.best_lam, R.st.best_hi,
-                                        R.st.best_lo, R.st.cert, nullptr, R.st.cand, R.st.done, cs,
-                                        true);
+                                        R.st.best_lo, R.st.cert, nullptr, snap, R.st.done, cc, true);
   if (r) return r;
-  k_bt_accept<<<(B + 127) / 128, 128, 0, cs>>>(B, h->ub_any, R.st, bb, d_active);
-  h->launches += 2;
+  h->launches += 1;
+  if (cudaEventRecord(done_ev, cc) != cudaSuccess) return DCOPF_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? DCOPF_OK : DCOPF_ERR_CUDA;
+}
+
+// Once the certificate of the staged instances is in (done_ev): accept, stop or resume
+// each of them, on cs; adds the count of instances still running to *d_active.
+static dcopf_status tensor_accept(TensorRun& R, int* d_active, cudaStream_t cs, cudaEvent_t done_ev) {
+  dcopf_dual* h = R.it.h;
+  const int B = R.it.B;
+  if (cudaStreamWaitEvent(cs, done_ev, 0) != cudaSuccess) return DCOPF_ERR_CUDA;
+  k_bt_accept<<<(B + 127) / 128, 128, 0, cs>>>(B, h->ub_any, R.st, h->bb.v, h->bb.snap.as<int>(),
+                                               d_active);
+  h->launches += 1;
   return cudaGetLastError() == cudaSuccess ? DCOPF_OK : DCOPF_ERR_CUDA;
 }
 
@@ -1091,12 +1114,14 @@ static dcopf_status tensor_finish(TensorRun& R, cudaStream_t s) {
 struct GroupObjects {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  std::vector<cudaEvent_t> ev;
+  std::vector<cudaEvent_t> ev, stage_ev, cert_ev;
   DBuf active;
   ~GroupObjects() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : stage_ev) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : cert_ev) if (e) cudaEventDestroy(e);
   }
 };
 
@@ -1151,6 +1176,20 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
   const long long per_chunk = 5LL * chunk;
   long long max_iters = 0;
   for (const TensorRun& R : runs) max_iters = std::max<long long>(max_iters, R.p.max_iters);
+  // The certificate of round r's candidates runs on a side stream beside round r + 1's
+  // iterations (the candidates stay frozen meanwhile); round r + 1 then accepts them.
+  for (int i = 0; i < n; ++i) {
+    dcopf_dual* hi = items[i].h;
+    if (!hi->cstream && cudaStreamCreateWithFlags(&hi->cstream, cudaStreamNonBlocking) != cudaSuccess)
+      return DCOPF_ERR_CUDA;
+    if (hi->bb.snap.alloc(sizeof(int) * (size_t)items[i].B) != cudaSuccess) return DCOPF_ERR_OOM;
+  }
+  G.stage_ev.resize(n, nullptr);
+  G.cert_ev.resize(n, nullptr);
+  for (int i = 0; i < n; ++i)
+    if (cudaEventCreateWithFlags(&G.stage_ev[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&G.cert_ev[i], cudaEventDisableTiming) != cudaSuccess)
+      return DCOPF_ERR_CUDA;
   std::vector<int> act(n, 1);
   for (int round = 0;; ++round) {
     if (h0->timing) cudaEventRecord(h0->ev0, cs0);
@@ -1164,17 +1203,20 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
       cudaStream_t si = items[i].h->tstream;
       if (i > 0 && cudaStreamWaitEvent(si, G.ev[2 * n], 0) != cudaSuccess) return DCOPF_ERR_CUDA;
       if (!act[i]) continue;
-      dcopf_status r = tensor_post_round(runs[i], d_active + i, si);
-      if (r) return r;
+      dcopf_status r;
+      if (round > 0 && (r = tensor_accept(runs[i], d_active + i, si, G.cert_ev[i]))) return r;
+      if ((r = tensor_stage_certify(runs[i], si, items[i].h->cstream, G.stage_ev[i], G.cert_ev[i])))
+        return r;
     }
     for (int i = 1; i < n; ++i)
       if (cudaEventRecord(G.ev[n + i], items[i].h->tstream) != cudaSuccess ||
           cudaStreamWaitEvent(cs0, G.ev[n + i], 0) != cudaSuccess)
         return DCOPF_ERR_CUDA;
-    if (cudaMemcpyAsync(act.data(), d_active, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, cs0) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(cs0) != cudaSuccess)
+    if (round > 0 &&
+        cudaMemcpyAsync(act.data(), d_active, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, cs0) !=
+            cudaSuccess)
       return DCOPF_ERR_CUDA;
+    if (cudaStreamSynchronize(cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
     if (h0->timing) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, h0->ev0, h0->ev1);
@@ -1188,8 +1230,14 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
       if (derr) return (dcopf_status)derr;
       any |= act[i];
     }
-    if (!any) break;
+    if (round > 0 && !any) break;
     if ((long long)round * chunk > 4LL * max_iters + 64) break;
+  }
+  // the last round's certificates: accept what they staged (nothing, when every
+  // instance had stopped before that round)
+  for (int i = 0; i < n; ++i) {
+    dcopf_status r = tensor_accept(runs[i], d_active + i, items[i].h->tstream, G.cert_ev[i]);
+    if (r) return r;
   }
   for (int i = 0; i < n; ++i) {
     dcopf_status r = tensor_finish(runs[i], s);

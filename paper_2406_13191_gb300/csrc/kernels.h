@@ -133,6 +133,7 @@ struct BatchView {
 
 struct BatchBufs {
   DBuf mu2, parts, small, F;
+  DBuf snap;  // [B] instances staged for the certificate in flight
   BatchView v;
 };
 
@@ -169,6 +170,7 @@ struct dcopf_dual {
   int* h_pinned = nullptr;  // pinned host mirror: [0] active count, [1] device error word
   double ub_any = 0.0;
   cudaStream_t tstream = nullptr;  // internal stream of the graph-captured batched solve
+  cudaStream_t cstream = nullptr;  // certificates of the batched solve, beside its iterations
   cudaEvent_t tev = nullptr;  // cost of the dearest dispatch (upper bound on any primal cost)
   long long launches = 0;
   // optional event timing of the iteration kernels
