@@ -20,7 +20,10 @@ def _as_dev(x, dtype, device):
     if x is None:
         return None
     t = x if isinstance(x, torch.Tensor) else torch.as_tensor(np.asarray(x))
-    return t.to(device=device, dtype=dtype).contiguous()
+    # pinned host memory goes up asynchronously, ordered on the current stream before
+    # the library call that reads it
+    nb = t.device.type == "cpu" and t.dtype == dtype and t.is_pinned()
+    return t.to(device=device, dtype=dtype, non_blocking=nb).contiguous()
 
 
 def _ptr(t):
