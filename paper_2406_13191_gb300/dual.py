@@ -30,6 +30,23 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _packed_views(flat: torch.Tensor, B: int, n: int):
+    """(lam, mu_hi, mu_lo, bound, iters, status) as views of one flat FP64 buffer laid
+    out [bound | lam | iters | status | mu_hi | mu_lo]; iters and status are int32
+    views over ceil(B/2) FP64 slots each."""
+    h = (B + 1) // 2
+    o = 2 * B
+    iters = flat[o:o + h].view(torch.int32)[:B]
+    status = flat[o + h:o + 2 * h].view(torch.int32)[:B]
+    o += 2 * h
+    return (flat[B:2 * B], flat[o:o + B * n].view(B, n), flat[o + B * n:o + 2 * B * n].view(B, n),
+            flat[:B], iters, status)
+
+
+def _packed_size(B: int, n: int) -> int:
+    return 2 * B + 2 * ((B + 1) // 2) + 2 * B * n
+
+
 @dataclass
 class SolveResult:
     lam: torch.Tensor          # [B] best iterate, lambda
@@ -39,14 +56,22 @@ class SolveResult:
     iters: torch.Tensor        # [B] iterations taken
     status: torch.Tensor       # [B] 0 target reached, 1 cap/tol, 2 infeasible suspected
     mean_dispatch: torch.Tensor | None = None  # [B][n_gen] k^2-weighted mean of the minimisers
+    flat: torch.Tensor | None = None  # the device buffer the six results are views of
 
     def to_host(self) -> "SolveResult":
-        """The results in host memory with one device-to-host transfer (packed on the
-        device first; iteration counts and statuses travel exactly as FP64)."""
-        B = self.lam.shape[0]
+        """The results in host memory with one device-to-host transfer.  Results made by
+        ``new_result`` (or by ``solve`` without ``out=``) are views of one device buffer,
+        which is copied as it is into pinned host memory, on the current stream;
+        otherwise they are packed on the device first (iteration counts and statuses
+        travel exactly as FP64)."""
+        B, n = self.mu_hi.shape
+        if self.flat is not None:
+            host = torch.empty(self.flat.shape, dtype=torch.float64, pin_memory=True)
+            host.copy_(self.flat, non_blocking=True)
+            torch.cuda.current_stream(self.flat.device).synchronize()
+            return SolveResult(*_packed_views(host, B, n), flat=host)
         packed = torch.cat([self.bound, self.lam, self.iters.double(), self.status.double(),
                             self.mu_hi.reshape(-1), self.mu_lo.reshape(-1)]).cpu()
-        n = self.mu_hi.shape[1]
         o = 4 * B
         return SolveResult(packed[B:2 * B], packed[o:o + B * n].reshape(B, n),
                            packed[o + B * n:].reshape(B, n), packed[:B],
@@ -231,12 +256,10 @@ class DcopfDual:
         return p
 
     def new_result(self, batch: int) -> SolveResult:
-        """Output tensors for ``solve(..., out=...)`` (reusable across calls)."""
-        kw = dict(dtype=torch.float64, device=self.device)
-        return SolveResult(torch.empty(batch, **kw), torch.empty(batch, self.n_line, **kw),
-                           torch.empty(batch, self.n_line, **kw), torch.empty(batch, **kw),
-                           torch.empty(batch, dtype=torch.int32, device=self.device),
-                           torch.empty(batch, dtype=torch.int32, device=self.device))
+        """Output tensors for ``solve(..., out=...)`` (reusable across calls): views of
+        one device buffer, so that ``to_host`` is a single copy."""
+        flat = torch.empty(_packed_size(batch, self.n_line), dtype=torch.float64, device=self.device)
+        return SolveResult(*_packed_views(flat, batch, self.n_line), flat=flat)
 
     def _solve_arrays(self, loads, outage, target, warm, res=None):
         loads, out = self._batch_inputs(loads, outage)
@@ -247,23 +270,12 @@ class DcopfDual:
         if res is not None:
             if res.lam.shape != (B,) or res.mu_hi.shape != (B, self.n_line) or res.lam.device != self.device:
                 raise ValueError("out= does not match the batch")
-            if warm is not None:
-                res.lam.copy_(_as_dev(warm[0], torch.float64, self.device).reshape(B))
-                res.mu_hi.copy_(_as_dev(warm[1], torch.float64, self.device).reshape(B, self.n_line))
-                res.mu_lo.copy_(_as_dev(warm[2], torch.float64, self.device).reshape(B, self.n_line))
-            return loads, out, tgt, res
-        kw = dict(dtype=torch.float64, device=self.device)
-        if warm is not None:
-            lam = _as_dev(warm[0], torch.float64, self.device).reshape(B).clone()
-            mh = _as_dev(warm[1], torch.float64, self.device).reshape(B, self.n_line).clone()
-            ml = _as_dev(warm[2], torch.float64, self.device).reshape(B, self.n_line).clone()
         else:  # cold start: the library initialises the state and only writes these
-            lam = torch.empty(B, **kw)
-            mh = torch.empty(B, self.n_line, **kw)
-            ml = torch.empty(B, self.n_line, **kw)
-        res = SolveResult(lam, mh, ml, torch.empty(B, **kw),
-                          torch.empty(B, dtype=torch.int32, device=self.device),
-                          torch.empty(B, dtype=torch.int32, device=self.device))
+            res = self.new_result(B)
+        if warm is not None:
+            res.lam.copy_(_as_dev(warm[0], torch.float64, self.device).reshape(B))
+            res.mu_hi.copy_(_as_dev(warm[1], torch.float64, self.device).reshape(B, self.n_line))
+            res.mu_lo.copy_(_as_dev(warm[2], torch.float64, self.device).reshape(B, self.n_line))
         return loads, out, tgt, res
 
     def solve(self, loads, outage=None, rule="adam", precision="fp32", path="auto",

@@ -18,6 +18,7 @@ import pytest
 import torch
 
 from paper_2406_13191_gb300 import DcopfDual, _lib, synth
+from paper_2406_13191_gb300.dual import SolveResult
 
 pytestmark = pytest.mark.gpu
 
@@ -94,12 +95,23 @@ def test_infeasible_instance_is_reported(path):
     assert np.isfinite(r.bound[0].item())
 
 
-def test_packed_host_results_equal_the_tensors():
+@pytest.mark.parametrize("scales", [(1.0, 0.9), (1.0, 0.9, 1.05)])
+def test_packed_host_results_equal_the_tensors(scales):
+    """One-copy read-back of results that are views of one device buffer (even and odd
+    batches: the int32 counts share FP64 slots), and the packing of separate tensors."""
     net, base = synth.network_for(0)
     g = DcopfDual(net)
-    r = g.solve(np.stack([base, base * 0.9]), path="batched", precision="bf16x3", rule="adam",
-                alpha=1000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=50)
-    h = r.to_host()
-    for f in ("lam", "mu_hi", "mu_lo", "bound", "iters", "status"):
-        a, b = getattr(r, f).cpu(), getattr(h, f)
-        assert a.shape == b.shape and torch.equal(a.to(b.dtype), b), f
+    loads = np.stack([base * s for s in scales])
+    kw = dict(path="batched", precision="bf16x3", rule="adam", alpha=1000.0, beta1=0.95,
+              beta2=0.999, decay=0.997, max_iters=50)
+    r = g.solve(loads, **kw)
+    out = g.new_result(len(scales))
+    r2 = g.solve(loads, out=out, **kw)
+    assert r2 is out and r.flat is not None
+    loose = SolveResult(*(getattr(r, f).clone() for f in ("lam", "mu_hi", "mu_lo", "bound", "iters",
+                                                          "status")))
+    for res in (r, r2, loose):
+        h = res.to_host()
+        for f in ("lam", "mu_hi", "mu_lo", "bound", "iters", "status"):
+            a, b = getattr(res, f).cpu(), getattr(h, f)
+            assert a.shape == b.shape and a.dtype == b.dtype and torch.equal(a, b), f
