@@ -10,9 +10,11 @@
 //
 // Kernel shape: one 128 x 128 output tile per CTA (split along K for the adjoint,
 // whose K = n_line is long and whose N = n_gen is short), 6 warps: warp 0 issues TMA
-// loads of the four BF16 tiles of a 64-wide K block into a 3- or 4-stage ring
-// (128-byte swizzle), warp 1 allocates TMEM and one of its threads issues the MMAs,
-// warps 2-5 read the accumulator from TMEM (tcgen05.ld) and run the epilogue.
+// loads of the BF16 tiles of a 64-wide K block into a ring with 128-byte swizzle,
+// warp 1 allocates TMEM and one of its threads issues the MMAs, warps 2-5 read the
+// accumulator from TMEM (tcgen05.ld) and run the epilogue.  The three-product GEMMs
+// run one CTA per SM with a 3-stage ring; the two-product LP forward runs two CTAs per
+// SM with a 2-stage ring each, so that one CTA's epilogue overlaps the other's loads.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -102,23 +104,24 @@ constexpr int GBM = 128, GBN = 128, GBK = 64;
 constexpr int GBM_ = GBM, GBN_ = GBN;
 constexpr uint32_t TILE_BYTES = GBM * GBK * 2;  // 16 KB, also GBN * GBK * 2
 
-template <int NPROD>
+template <int NPROD, int OCC = 1>
 struct GemmCfg {
-  static constexpr int STAGES = NPROD == 3 ? 3 : 4;
+  static constexpr int STAGES = NPROD == 3 ? 3 : (OCC == 2 ? 2 : 4);
   static constexpr uint32_t STAGE_BYTES = (NPROD == 3 ? 4 : 3) * TILE_BYTES;
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
+  static_assert(STAGES * STAGE_BYTES >= GBM * (GBN + 1) * 4, "the ring stages the output tile");
 };
 
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo);
 
 
 
-template <int NPROD>
-__global__ void __launch_bounds__(192, 1)
+template <int NPROD, int OCC = 1>
+__global__ void __launch_bounds__(192, OCC)
     k_gemm_bf16x(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                  const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
                  GemmArgs g) {
-  using Cfg = GemmCfg<NPROD>;
+  using Cfg = GemmCfg<NPROD, OCC>;
   constexpr int ST = Cfg::STAGES;
   extern __shared__ __align__(16) unsigned char gsm_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
@@ -224,13 +227,17 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
               for (int u = 0; u < 8; ++u)
                 reinterpret_cast<float4*>(dst)[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-            } else {
-              for (int u = 0; u < 32 && col0 + u < g.N; ++u) dst[u] = v[u];
+            } else {  // ragged tail: predicated, unrolled (v stays in registers)
+#pragma unroll
+              for (int u = 0; u < 32; ++u)
+                if (col0 + u < g.N) dst[u] = v[u];
             }
           } else {
             const double* f0 = g.f0 + (size_t)row * g.ldf + col0;
             double* f = g.f + (size_t)row * g.ldf + col0;
-            for (int u = 0; u < 32 && col0 + u < g.N; ++u) f[u] = (double)v[u] + f0[u];
+#pragma unroll
+            for (int u = 0; u < 32; ++u)
+              if (col0 + u < g.N) f[u] = (double)v[u] + f0[u];
           }
         }
       }
@@ -585,22 +592,30 @@ dcopf_status ensure_tensor_batch(dcopf_dual* h, int B) {
 
 // Sets the GEMM kernels' shared-memory limits (outside any stream capture).
 static cudaError_t prepare_gemm() {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)GemmCfg<2>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)GemmCfg<2, 2>::SMEM);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_gemm_bf16x<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)GemmCfg<3>::SMEM);
 }
 
-template <int NPROD>
+template <int NPROD, int OCC = 1>
 static cudaError_t launch_gemm(dcopf_dual* h, const CUtensorMap& Ah, const CUtensorMap& Al,
                                const CUtensorMap& Bh, const CUtensorMap& Bl, GemmArgs g, int splits,
                                cudaStream_t s) {
-  using Cfg = GemmCfg<NPROD>;
+  using Cfg = GemmCfg<NPROD, OCC>;
   dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, splits);
-  k_gemm_bf16x<NPROD><<<grid, 192, Cfg::SMEM, s>>>(Ah, Al, Bh, Bl, g);
+  k_gemm_bf16x<NPROD, OCC><<<grid, 192, Cfg::SMEM, s>>>(Ah, Al, Bh, Bl, g);
   h->launches += 1;
   return cudaGetLastError();
+}
+
+// The LP forward F = X Phi~^T (two products: x is exact in BF16).  Its K = n_gen is
+// short, so a CTA spends much of its time in the epilogue: two CTAs per SM (a 2-stage
+// ring each) let one CTA's epilogue run beside the other's main loop.
+static cudaError_t launch_forward_lp(dcopf_dual* h, const GemmArgs& g, cudaStream_t s) {
+  TensorOps& T = h->tops;
+  return launch_gemm<2, 2>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, g, 1, s);
 }
 
 // Split-K factor of the adjoint: enough CTAs to cover the SMs twice.
@@ -642,7 +657,7 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
   f.timeout_ns = 2000000000ull;
   cudaError_t e = h->host.qp
                       ? launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, f, 1, s)
-                      : launch_gemm<2>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, f, 1, s);
+                      : launch_forward_lp(h, f, s);
   if (e != cudaSuccess) return DCOPF_ERR_CUDA;
   return run_eval_finish(h, B, outage, lambda, mh, ml, value, glam, ghi, glo, dispatch, s);
 }
@@ -688,7 +703,8 @@ template __global__ void k_split_eta<float>(int, int, const float*, const float*
 // pi~ from the split-K partials, minimiser, BF16 split of x, per-instance cost and
 // dispatch, the pre-outage flow (Phi~ x)_k of an outaged line, the step factors of
 // this step (running powers), and the lambda step (Section 3.3).
-__global__ void k_bt_minimize(DevNet N, int splits, int M, int ldp, const float* __restrict__ P,
+__global__ void __launch_bounds__(256, 4)
+    k_bt_minimize(DevNet N, int splits, int M, int ldp, const float* __restrict__ P,
                               SolveStateBase st, BatchView bb, StepArgs SP, int ldx,
                               __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl,
                               const int* __restrict__ outage, const double* __restrict__ demand) {
@@ -704,8 +720,16 @@ __global__ void k_bt_minimize(DevNet N, int splits, int M, int ldp, const float*
   float c = 0.f, p = 0.f, to = 0.f;
   const float kk = (float)(st.iter[b] + 1), wk = kk * kk;  // weight of the mean of the minimisers
   for (int j = threadIdx.x; j < ng; j += blockDim.x) {
+    // split-K partials eight loads at a time, summed in split order (a missing term
+    // adds +0, which leaves the sum unchanged)
     float s = 0.f;
-    for (int q = 0; q < splits; ++q) s += P[((size_t)q * M + b) * ldp + j];
+    for (int q0 = 0; q0 < splits; q0 += 8) {
+      float t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = q0 + u < splits ? P[((size_t)(q0 + u) * M + b) * ldp + j] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += t[u];
+    }
     const double w = N.ctil[j] + N.sigma[j] * lam + (double)s;
     const float x = inner_x<float>((float)w, N.mq32[j]);
     if (st.xsum) st.xsum[(size_t)b * ng + j] += wk * x;
@@ -1045,7 +1069,7 @@ static bool tensor_enqueue_chunk(TensorRun& R, int chunk, cudaStream_t cs) {
                                      T.ld_g, T.X_hi.as<__nv_bfloat16>(), T.X_lo.as<__nv_bfloat16>(),
                                      R.it.outage, w.demand.as<double>());
     ok &= (h->host.qp ? launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, R.gf, 1, cs)
-                      : launch_gemm<2>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, R.gf, 1, cs)) ==
+                      : launch_forward_lp(h, R.gf, cs)) ==
           cudaSuccess;
     if (nl % 4 == 0 && R.E.ldF % 4 == 0 && R.E.ldh % 4 == 0)
       k_bt_step4<<<dim3(R.n_tiles, B), STEP_THREADS, 0, cs>>>(R.E, nl);
