@@ -60,7 +60,11 @@ def gamma_star():
 
 
 class Clocks:
-    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    """Samples SM clocks and throttle reasons with nvidia-smi (every 100 ms) from before
+    the warm-up until after the timed steps.  ``wait_ready`` returns once the first
+    sample is in (the tool takes a while to start), ``start``/``stop`` mark the timed
+    window; the summary takes the samples inside the window, and when the window is
+    shorter than the sampling period, the last sample before it and the first after."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -69,8 +73,12 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.lines = []          # (perf_counter, line)
+        self.t0 = self.t1 = None
+        self.reader = None
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
                                           f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -78,37 +86,68 @@ class Clocks:
                                          stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+
+        def read():
+            for line in self.proc.stdout:
+                self.lines.append((time.perf_counter(), line))
+        self.reader = threading.Thread(target=read, daemon=True)
+        self.reader.start()
         return self
 
+    def wait_ready(self, timeout=5.0):
+        t = time.perf_counter() + timeout
+        while self.proc is not None and not self.lines and time.perf_counter() < t:
+            time.sleep(0.01)
+
+    def start(self):
+        self.t0 = time.perf_counter()
+
+    def stop(self):
+        self.t1 = time.perf_counter()
+        # one more sample after the window
+        t = self.t1 + 1.0
+        while self.proc is not None and time.perf_counter() < t and \
+                not any(ts > self.t1 for ts, _ in self.lines):
+            time.sleep(0.01)
+
     def __exit__(self, *a):
-        self.out = ""
         if self.proc is not None:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                self.out = ""
+            if self.reader is not None:
+                self.reader.join(timeout=2)
 
     def summary(self):
-        sms, maxs, reasons = [], [], set()
+        rows = []
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in (self.out or "").strip().splitlines():
+        for ts, line in list(self.lines):
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sms.append(float(f[1]))
-                maxs.append(float(f[2]))
+                rows.append((ts, float(f[1]), float(f[2]),
+                             {n for n, v in zip(names, f[5:9]) if v.lower() == "active"}))
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sms:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs),
-                "reasons": sorted(reasons), "samples": len(sms)}
+        t0 = self.t0 if self.t0 is not None else float("-inf")
+        t1 = self.t1 if self.t1 is not None else float("inf")
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        use = inside
+        if not use:
+            before = [r for r in rows if r[0] < t0]
+            after = [r for r in rows if r[0] > t1]
+            use = before[-1:] + after[:1]
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "samples_in_window": 0}
+        reasons = set().union(*(r[3] for r in use))
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": sorted(reasons), "samples": len(use), "samples_in_window": len(inside),
+                "window_s": (t1 - t0) if self.t0 is not None and self.t1 is not None else None}
 
 
 def dist_setup(n_gpus):
@@ -336,7 +375,7 @@ def optimizer_study(max_iters: int = 3000) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-steps", type=int, default=3)
@@ -414,6 +453,8 @@ def main():
     r = one(OURS)   # first solve: builds the dense H_a on the host and tunes the fused shape
     torch.cuda.synchronize(dev)
     setup["first_solve_s"] = time.perf_counter() - t_first
+    clk = Clocks(local).__enter__()   # sampling from before the warm-up
+    clk.wait_ready()
     for _ in range(a.warmup):
         r = one(OURS)
     assert r.status[0].item() == 0, "warm-up solve did not reach the gap"
@@ -422,20 +463,22 @@ def main():
     launches0 = g.kernel_launches()
     times, iters, bounds = [], [], []
     barrier()
-    with Clocks(local) as clk:
-        for _ in range(a.steps):
-            flush.zero_()                       # L2 flushed between timed steps (untimed)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r = one(OURS)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            iters.append(r.iters[0].item())
-            bounds.append(r.bound[0].item())
-            assert r.status[0].item() == 0
+    clk.start()
+    for _ in range(a.steps):
+        flush.zero_()                       # L2 flushed between timed steps (untimed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = one(OURS)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        iters.append(r.iters[0].item())
+        bounds.append(r.bound[0].item())
+        assert r.status[0].item() == 0
     barrier()
+    clk.stop()
+    clk.__exit__()
     launches = g.kernel_launches() - launches0
     it_ms, it_launches, evals = g.read_timing()
     g.set_timing(False)
