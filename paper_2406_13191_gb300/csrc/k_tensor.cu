@@ -101,7 +101,6 @@ struct GemmArgs {
 };
 
 constexpr int GBM = 128, GBN = 128, GBK = 64;
-constexpr int GBM_ = GBM, GBN_ = GBN;
 constexpr uint32_t TILE_BYTES = GBM * GBK * 2;  // 16 KB, also GBN * GBK * 2
 
 template <int NPROD, int OCC = 1>
@@ -933,12 +932,17 @@ static dcopf_status tune_adjoint_split(TensorRun& R, cudaStream_t cs) {
   const int kb = (h->host.n_line + GBK - 1) / GBK;
   const int s0 = R.splits;
   std::vector<int> cand;
-  for (int num : {1, 2, 3, 4, 6, 8}) {
-    const int s = std::max(1, std::min(std::min(kb, 64), (s0 * num + 2) / 4));
+  auto add = [&](int s) {
+    s = std::max(1, std::min(std::min(kb, 64), s));
     const int per = (kb + s - 1) / s;
     const int se = (kb + per - 1) / per;
     if (std::find(cand.begin(), cand.end(), se) == cand.end()) cand.push_back(se);
-  }
+  };
+  for (int num : {1, 2, 3, 4, 6, 8}) add((s0 * num + 2) / 4);
+  // and the splits that fill whole waves (one CTA per SM): the last wave of a grid of
+  // tiles x splits CTAs is then full rather than a few CTAs on an idle GPU
+  const int tiles = ((B + GBM - 1) / GBM) * ((h->host.n_gen + GBN - 1) / GBN);
+  for (int wv = 1; wv <= 4; ++wv) add(wv * h->sm_count / tiles);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);

@@ -51,9 +51,9 @@ def _seeded_point(rng, batch, n_line, density=0.1):
     return lam, mh, np.zeros_like(mh)
 
 
-def batched(cfg, batch, iters):
+def batched(cfg, batch, iters, verbose=False):
     w = synth.workload(cfg, batch=batch)
-    g = DcopfDual(w.net, device=0)
+    g = DcopfDual(w.net, device=0, verbose=verbose)
     out = w.outage if (w.outage >= 0).any() else None
     kw = dict(rule="adam", alpha=4000.0 if w.net.is_qp else 1000.0, beta1=0.95, beta2=0.999,
               decay=0.997, max_iters=iters, path="batched", precision="bf16x3")
@@ -356,7 +356,7 @@ def main():
     ap.add_argument("--verbose", action="store_true", help="library setup and tuning messages")
     a = ap.parse_args()
     if a.mode == "batched":
-        batched(a.config, a.batch, a.iters)
+        batched(a.config, a.batch, a.iters, a.verbose)
     elif a.mode == "certify":
         certify(a.config, a.batch)
     elif a.mode == "group":
