@@ -453,32 +453,31 @@ def main():
     r = one(OURS)   # first solve: builds the dense H_a on the host and tunes the fused shape
     torch.cuda.synchronize(dev)
     setup["first_solve_s"] = time.perf_counter() - t_first
-    clk = Clocks(local).__enter__()   # sampling from before the warm-up
-    clk.wait_ready()
-    for _ in range(a.warmup):
-        r = one(OURS)
-    assert r.status[0].item() == 0, "warm-up solve did not reach the gap"
-    g.set_timing(True)
-    g.read_timing()
-    launches0 = g.kernel_launches()
-    times, iters, bounds = [], [], []
-    barrier()
-    clk.start()
-    for _ in range(a.steps):
-        flush.zero_()                       # L2 flushed between timed steps (untimed)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r = one(OURS)
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        iters.append(r.iters[0].item())
-        bounds.append(r.bound[0].item())
-        assert r.status[0].item() == 0
-    barrier()
-    clk.stop()
-    clk.__exit__()
+    with Clocks(local) as clk:   # sampling from before the warm-up
+        clk.wait_ready()
+        for _ in range(a.warmup):
+            r = one(OURS)
+        assert r.status[0].item() == 0, "warm-up solve did not reach the gap"
+        g.set_timing(True)
+        g.read_timing()
+        launches0 = g.kernel_launches()
+        times, iters, bounds = [], [], []
+        barrier()
+        clk.start()
+        for _ in range(a.steps):
+            flush.zero_()                       # L2 flushed between timed steps (untimed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = one(OURS)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            iters.append(r.iters[0].item())
+            bounds.append(r.bound[0].item())
+            assert r.status[0].item() == 0
+        barrier()
+        clk.stop()
     launches = g.kernel_launches() - launches0
     it_ms, it_launches, evals = g.read_timing()
     g.set_timing(False)
