@@ -59,16 +59,16 @@ class SolveResult:
     flat: torch.Tensor | None = None  # the device buffer the six results are views of
 
     def to_host(self) -> "SolveResult":
-        """The results in host memory with one device-to-host transfer.  Results made by
-        ``new_result`` (or by ``solve`` without ``out=``) are views of one device buffer,
-        which is copied as it is into pinned host memory, on the current stream;
+        """The results in host memory with one device-to-host transfer, ordered after
+        the work already on the current stream.  Results made by ``new_result`` (or by
+        ``solve`` without ``out=``) are views of one device buffer, which is copied as it
+        is by one blocking copy (for results of this size, faster on a Grace host than
+        an asynchronous copy into pinned memory followed by a stream synchronisation);
         otherwise they are packed on the device first (iteration counts and statuses
         travel exactly as FP64)."""
         B, n = self.mu_hi.shape
         if self.flat is not None:
-            host = torch.empty(self.flat.shape, dtype=torch.float64, pin_memory=True)
-            host.copy_(self.flat, non_blocking=True)
-            torch.cuda.current_stream(self.flat.device).synchronize()
+            host = self.flat.cpu()
             return SolveResult(*_packed_views(host, B, n), flat=host)
         packed = torch.cat([self.bound, self.lam, self.iters.double(), self.status.double(),
                             self.mu_hi.reshape(-1), self.mu_lo.reshape(-1)]).cpu()
