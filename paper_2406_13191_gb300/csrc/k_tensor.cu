@@ -698,24 +698,31 @@ template __global__ void k_split_eta<float>(int, int, const float*, const float*
                                             const float*, __nv_bfloat16*, __nv_bfloat16*);
 
 
-// Block size of the minimiser (one block per instance).  256 threads unless the batch
-// exceeds the blocks of that size the SMs hold at once (four per SM at 64 registers);
-// then 128, which halves the waves for twice the generators per thread.  Measured on
-// the same box: 1024 4600-bus instances 175.7 -> 170.8 us per batched iteration,
-// 4096 2000-bus ones 438.8 -> 421.1 us, while 256 4600-bus or 10000-bus instances run
-// slower with 128 (4992 -> 4780 instances/s to the gap; 194.7 -> 208.9 us).
-static int minimize_threads(const dcopf_dual* h, int B) { return B > 4 * h->sm_count ? 128 : 256; }
+// Block size of the minimiser (one block per instance, at most 512 threads).  256
+// threads unless the batch exceeds the blocks of that size the SMs hold at once (four
+// per SM at 64 registers); then 128, which halves the waves for twice the generators
+// per thread.  Measured on the same machine: 1024 4600-bus instances 175.7 -> 170.8 us
+// per batched iteration, 4096 2000-bus ones 438.8 -> 421.1 us, while 256 4600-bus or
+// 10000-bus instances run slower with 128 (4992 -> 4780 instances/s to the gap;
+// 194.7 -> 208.9 us).  A batch that leaves SMs idle with thousands of generators per
+// instance (the 10000-bus batch of 256) takes 512 threads instead: fewer generators
+// per thread on the same single wave.
+constexpr int MIN_MAX_THREADS = 512;
+static int minimize_threads(const dcopf_dual* h, int B) {
+  if (B > 4 * h->sm_count) return 128;
+  return (h->host.n_gen >= 1024 && B <= 2 * h->sm_count) ? MIN_MAX_THREADS : 256;
+}
 
 // ------------------------------------------------------------------ batched solve
 // pi~ from the split-K partials, minimiser, BF16 split of x, per-instance cost and
 // dispatch, the pre-outage flow (Phi~ x)_k of an outaged line, the step factors of
 // this step (running powers), and the lambda step (Section 3.3).
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
     k_bt_minimize(DevNet N, int splits, int M, int ldp, const float* __restrict__ P,
                               SolveStateBase st, BatchView bb, StepArgs SP, int ldx,
                               __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl,
                               const int* __restrict__ outage, const double* __restrict__ demand) {
-  __shared__ double red[32];
+  __shared__ double red[3 * (MIN_MAX_THREADS / 32)];
   const int b = blockIdx.x;
   if (bb.frozen[b]) return;
   const int ng = N.n_gen;
@@ -747,11 +754,12 @@ __global__ void __launch_bounds__(256, 4)
   }
   c = warp_sum(c); p = warp_sum(p); to = warp_sum(to);
   const int wid = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) { red[wid] = c; red[8 + wid] = p; red[16 + wid] = to; }
+  constexpr int RW = MIN_MAX_THREADS / 32;
+  if ((threadIdx.x & 31) == 0) { red[wid] = c; red[RW + wid] = p; red[2 * RW + wid] = to; }
   __syncthreads();
   if (threadIdx.x == 0) {
     double cs = 0.0, ps = 0.0, ts = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { cs += red[q]; ps += red[8 + q]; ts += red[16 + q]; }
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { cs += red[q]; ps += red[RW + q]; ts += red[2 * RW + q]; }
     const double p = ps;
     bb.cost[b] = cs;
     bb.psum[b] = ps;
