@@ -110,3 +110,28 @@ def test_valid_network_without_gpu_reports_cuda_error():
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
     assert _create(_good()) == 3
+
+
+@pytest.mark.parametrize("B,n", [(1, 41), (2, 5), (3, 7), (64, 3)])
+def test_packed_result_views(B, n):
+    """The binding's solve results are views of one FP64 buffer laid out
+    [bound | lambda | iters | status | mu_hi | mu_lo], the int32 counts and statuses two
+    per FP64 slot: the views tile the buffer without overlap, and writes through each
+    view land where the layout says."""
+    import torch
+    from paper_2406_13191_gb300.dual import _packed_size, _packed_views
+    flat = torch.zeros(_packed_size(B, n), dtype=torch.float64)
+    lam, mh, ml, bound, iters, status = _packed_views(flat, B, n)
+    assert lam.shape == (B,) and bound.shape == (B,) and mh.shape == (B, n) and ml.shape == (B, n)
+    assert iters.shape == (B,) and status.shape == (B,)
+    assert iters.dtype == torch.int32 and status.dtype == torch.int32
+    bound.fill_(1.0); lam.fill_(2.0); mh.fill_(3.0); ml.fill_(4.0)
+    iters.copy_(torch.arange(B, dtype=torch.int32) + 7)
+    status.copy_(torch.arange(B, dtype=torch.int32) % 3)
+    h = (B + 1) // 2
+    assert torch.all(flat[:B] == 1.0) and torch.all(flat[B:2 * B] == 2.0)
+    o = 2 * B + 2 * h
+    assert torch.all(flat[o:o + B * n] == 3.0) and torch.all(flat[o + B * n:] == 4.0)
+    ints = flat[2 * B:o].view(torch.int32)
+    assert torch.equal(ints[:B], torch.arange(B, dtype=torch.int32) + 7)
+    assert torch.equal(ints[2 * h:2 * h + B], torch.arange(B, dtype=torch.int32) % 3)
