@@ -160,8 +160,9 @@ __global__ void k_init_state(int B, int nl, int warm, const double* __restrict__
 
 // After certification of the candidates: accept (certified bound reaches the
 // threshold), stop (cap / tol), or raise the in-loop margin and continue.
-__global__ void k_accept(int B, double ub_any, SolveStateBase st, int* active) {
+__global__ void k_accept(int B, double ub_any, SolveStateBase st, int* active, const int* err) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b == 0) active[2] = *err;  // read back with the active count
   if (b >= B) return;
   if (!st.done[b] && st.cand[b]) {
     double c = st.cert[b];
@@ -331,21 +332,20 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
                          st.cand, st.done, s, true);
     if (r) return r;
     CUDA_TRY(h, cudaMemsetAsync(d_active, 0, sizeof(int), s));
-    k_accept<<<cdiv(B, 128), 128, 0, s>>>(B, ub_any, st, d_active);
+    k_accept<<<cdiv(B, 128), 128, 0, s>>>(B, ub_any, st, d_active, h->d_err);
     // the outputs of the best points so far, written every round: when this round
     // finishes every instance (the usual case) nothing is left to do after the read
     // back (the caller's lambda / mu arrays were read only by the initialisation)
     k_output<S><<<std::min<unsigned>(cdiv((long long)B * nl, 256), 4096), 256, 0, s>>>(
         B, nl, st, lam, mh, ml, bound, iters, status);
     h->launches += 2;
-    // the active count, the device error word (and, when timing, the evaluations so
-    // far), read back with one synchronisation
+    // the active count, the device error word (copied next to it by k_accept) and,
+    // when timing, the evaluations so far: one copy, one synchronisation
     if (h->timing) {
       k_sum_iters<<<1, 256, 0, s>>>(B, st.iter, d_active + 1);
       h->launches += 1;
     }
-    CUDA_TRY(h, cudaMemcpyAsync(h->h_pinned, d_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(h, cudaMemcpyAsync(h->h_pinned + 2, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_pinned, d_active, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
     const int active = h->h_pinned[0], derr = h->h_pinned[2];
     if (h->timing) {

@@ -167,11 +167,12 @@ struct dcopf_dual {
   int* d_err = nullptr;  // sticky device error word
   unsigned* d_bar = nullptr;  // grid-barrier counters
   dcopf::DBuf active;  // one int: instances still running
-  int* h_pinned = nullptr;  // pinned host mirror: [0] active count, [1] device error word
-  double ub_any = 0.0;
+  int* h_pinned = nullptr;  // pinned host mirror of a round's read-back: [0] active count,
+                            // [1] evaluations (timing), [2] device error word
+  double ub_any = 0.0;  // cost of the dearest dispatch (upper bound on any primal cost)
   cudaStream_t tstream = nullptr;  // internal stream of the graph-captured batched solve
   cudaStream_t cstream = nullptr;  // certificates of the batched solve, beside its iterations
-  cudaEvent_t tev = nullptr;  // cost of the dearest dispatch (upper bound on any primal cost)
+  cudaEvent_t tev = nullptr;  // orders the internal stream after the caller's
   long long launches = 0;
   // optional event timing of the iteration kernels
   bool timing = false;
