@@ -68,12 +68,22 @@ typedef enum {
 
 /* Execution path of dcopf_dual_solve_batch. */
 typedef enum {
-  DCOPF_PATH_AUTO = 0,   /* fused persistent kernel for batch 1, batched kernels otherwise */
+  DCOPF_PATH_AUTO = 0,   /* fused persistent kernel for batch 1, batched kernels otherwise;
+                            a single instance whose fused kernel cannot run (no cluster
+                            shape fits, or every shape is refused) runs on the unfused
+                            FP32 kernels instead */
   DCOPF_PATH_PLAIN = 1,  /* one launch per phase per iteration (the unfused baseline) */
   DCOPF_PATH_FUSED = 2,  /* one persistent thread-block-cluster kernel per instance; it
                             is launched cooperatively when the driver accepts that,
                             unless the environment sets DCOPF_FUSED_COOPERATIVE=0
-                            (read by dcopf_dual_create) */
+                            (read by dcopf_dual_create).  The kernel refuses a launch
+                            whose cluster shape is not the one its shared-memory layout
+                            was sized for (profilers that replay cooperative launches
+                            drop the shape); such a launch is repeated as a plain
+                            cluster launch.  Test hook: DCOPF_FUSED_REFUSE=1 (or 2),
+                            read by dcopf_dual_create, makes the host size every
+                            cooperative (or every) fused launch for another shape, so
+                            that the kernel refuses it */
   DCOPF_PATH_BATCHED = 3, /* batched contraction kernels replayed from a CUDA graph */
   DCOPF_PATH_SPARSE = 4   /* one CTA per instance runs the iterations with both operator
                              products as level-scheduled triangular solves on the sparse
@@ -196,8 +206,11 @@ dcopf_status dcopf_dual_eval(dcopf_dual_t h, int32_t batch, const double* loads,
  * computed in FP64 by sparse triangular solves, and
  *   bound = sum_j min_p [cost_j(p) + nu_bus(j) p] - nu^T p_d - mu_hi^T f_max + mu_lo^T f_min
  * is accumulated in FP64 (eq. (4) evaluated through the bus prices).  err_bound
- * receives an upper bound on the rounding error of that final accumulation; the
- * reported bound already has it subtracted.
+ * receives an upper bound on the total rounding error of that evaluation: of the
+ * final accumulation and each term, and of the computed bus prices nu (the residual
+ * of the sparse triangular solves, or the accumulation in the dense H_a^T products,
+ * times how much each term can move with its price).  The reported bound already
+ * has it subtracted.
  *   loads [batch][n_bus]; outage [batch] or NULL; lambda [batch]; mu_hi, mu_lo
  *   [batch][n_line]; bound [batch] (required); err_bound [batch] (NULL = skip). */
 dcopf_status dcopf_dual_certify_bound(dcopf_dual_t h, int32_t batch, const double* loads,
@@ -310,8 +323,9 @@ dcopf_status dcopf_dual_solve_group(int32_t n_items, const dcopf_group_item* ite
  * where cudaMalloc's implicit synchronisation and latency are not acceptable).  The
  * paper has no counterpart: this is an interface convenience.
  *
- * Same arguments, results and errors as dcopf_dual_eval, for precision DCOPF_FP64 or
- * DCOPF_FP32 (DCOPF_BF16X3 returns DCOPF_ERR_UNSUPPORTED).  Instead of the handle's
+ * Same arguments, host checks, results and errors as dcopf_dual_eval, for precision
+ * DCOPF_FP64 or DCOPF_FP32 (DCOPF_BF16X3 returns DCOPF_ERR_UNSUPPORTED: its BF16
+ * operands live in the handle's workspace).  Instead of the handle's
  * workspace, every intermediate array lives in one fixed device array of 16 MiB
  * compiled into the library (each GPU that loads the library holds it until the
  * process exits).  A call needs 256-byte-aligned sections of about
@@ -346,6 +360,17 @@ dcopf_status dcopf_dual_set_timing(dcopf_dual_t h, int32_t enable);
 dcopf_status dcopf_dual_read_timing(dcopf_dual_t h, double* iter_ms, int64_t* iter_launches,
                                     int64_t* evaluations);
 
+/* Device-memory budget of a handle's workspaces: the buffers that eval,
+ * certify_bound, primal_bound, solve_batch and the self-tests allocate on first use
+ * or when a larger batch arrives (the network data uploaded by dcopf_dual_create and
+ * the buffers of dcopf_dual_solve_group are not counted).  limit_bytes > 0 sets the
+ * largest number of bytes they may hold together, 0 removes the limit, < 0 leaves it
+ * unchanged.  A call that would need a workspace beyond the limit returns
+ * DCOPF_ERR_OOM before it enqueues any work and leaves the handle usable: later calls
+ * whose workspaces fit run normally.  used_bytes (host, nullable) receives the bytes
+ * the workspaces hold now.  Host only; does not synchronise. */
+dcopf_status dcopf_dual_workspace_limit(dcopf_dual_t h, int64_t limit_bytes, int64_t* used_bytes);
+
 /* Self-test of the bounded device wait used by every cross-CTA synchronisation of
  * the persistent kernels: one thread waits, with an acquire load in a loop, for a
  * device counter that nothing increments, and must give up after timeout_ns
@@ -353,6 +378,18 @@ dcopf_status dcopf_dual_read_timing(dcopf_dual_t h, double* iter_ms, int64_t* it
  * (the expected outcome), DCOPF_OK if it did not.  The device stays usable
  * either way.  Synchronises `stream`. */
 dcopf_status dcopf_selftest_bounded_wait(dcopf_dual_t h, int64_t timeout_ns, void* stream);
+
+/* Self-test of the fused persistent kernel's failure path: one fused solve of the
+ * instance `loads` (DEVICE [n_bus]) in which the wait for every cluster's arrival
+ * expects one arrival more than the clusters make, with the kernel's waits limited to
+ * timeout_ns (1 us .. 10 s).  Every cluster gives up at the first loop, the CTAs of
+ * each cluster leave together through the kernel's final cluster barrier, and the
+ * solve returns DCOPF_ERR_TIMEOUT (the expected outcome; DCOPF_OK would mean the
+ * wait did not give up).  The handle stays usable.  Needs a handle whose fused shape
+ * is already chosen (after one fused solve), else DCOPF_ERR_UNSUPPORTED.
+ * Synchronises `stream`. */
+dcopf_status dcopf_selftest_fused_timeout(dcopf_dual_t h, const double* loads, int64_t timeout_ns,
+                                          void* stream);
 
 /* Sticky device-side error word of the handle's last solve (0 = none, else a
  * dcopf_status value such as DCOPF_ERR_TIMEOUT).  Synchronises the device. */

@@ -26,6 +26,8 @@ dcopf_dual::~dcopf_dual() {
 
 namespace dcopf {
 
+thread_local AllocAccount* tl_account = nullptr;
+
 namespace {
 
 #define CUDA_TRY(h, x)                                               \
@@ -64,9 +66,21 @@ struct DeviceGuard {
 
 }  // namespace
 
+static dcopf_status alloc_workspace(dcopf_dual* h, int B);
+
+// A failed allocation may leave some buffers resized and one freed: the capacity is
+// reset so that the next call allocates every buffer again.
 dcopf_status ensure_workspace(dcopf_dual* h, int B) {
+  if (B <= h->ws.cap) return DCOPF_OK;
+  h->ws.cap = 0;
+  const dcopf_status r = alloc_workspace(h, B);
+  if (r == DCOPF_OK) h->ws.cap = B;
+  else cudaGetLastError();
+  return r;
+}
+
+static dcopf_status alloc_workspace(dcopf_dual* h, int B) {
   Workspace& w = h->ws;
-  if (B <= w.cap) return DCOPF_OK;
   const size_t nl = h->dev.n_line, ng = h->dev.n_gen;
   const size_t bl = (size_t)B * nl, bg = (size_t)B * ng;
   CUDA_TRY(h, w.f0.alloc(bl * 8));
@@ -87,7 +101,6 @@ dcopf_status ensure_workspace(dcopf_dual* h, int B) {
   CUDA_TRY(h, w.glam.alloc((size_t)B * 8));
   CUDA_TRY(h, w.ghi.alloc(bl * 8));
   CUDA_TRY(h, w.glo.alloc(bl * 8));
-  w.cap = B;
   return DCOPF_OK;
 }
 
@@ -96,9 +109,13 @@ dcopf_status ensure_state(dcopf_dual* h, int B, SolveState<S>* st) {
   StateBufs& sb = sizeof(S) == 8 ? h->st64 : h->st32;
   const size_t nl = h->dev.n_line;
   if (B > sb.cap) {
-    CUDA_TRY(h, sb.ints.alloc((size_t)B * 6 * sizeof(int)));
-    CUDA_TRY(h, sb.dbls.alloc((size_t)B * 12 * sizeof(double)));
-    CUDA_TRY(h, sb.mus.alloc((size_t)B * nl * 8 * sizeof(S)));
+    sb.cap = 0;  // reset unless every buffer below is allocated
+    if (sb.ints.alloc((size_t)B * 6 * sizeof(int)) != cudaSuccess ||
+        sb.dbls.alloc((size_t)B * 12 * sizeof(double)) != cudaSuccess ||
+        sb.mus.alloc((size_t)B * nl * 8 * sizeof(S)) != cudaSuccess) {
+      cudaGetLastError();
+      return DCOPF_ERR_OOM;
+    }
     sb.cap = B;
   }
   int* I = sb.ints.as<int>();
@@ -285,6 +302,14 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
             if (h->verbose) fused_report_refusal(h);
             cudaMemset(h->d_err, 0, sizeof(int));
             cudaGetLastError();
+            if (derr == DCOPF_ERR_UNSUPPORTED && h->fused_coop != 0) {
+              // the kernel refused the shape of a cooperative launch (profilers that
+              // replay such launches drop the cluster shape): relaunch this candidate
+              // as a plain cluster launch, whose shape they keep
+              h->fused_coop = 0;
+              --rep;
+              continue;
+            }
             per = 1e30f;
             break;
           }
@@ -302,7 +327,10 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
       }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      if (!(best < 1e30f)) return DCOPF_ERR_UNSUPPORTED;
+      if (!(best < 1e30f)) {
+        h->fused_C = 0;  // no shape ran: retune on the next fused solve
+        return DCOPF_ERR_UNSUPPORTED;
+      }
       h->fused_C = Cs[bi];
       h->fused_G = Gs[bi];
       k_init_state<S><<<g, 256, 0, s>>>(B, nl, p.warm_start, lam, mh, ml, p.target_value, p.gap, st);
@@ -353,6 +381,13 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
       CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
       h->t_iter_ms += ms;
       h->t_iter_launches += iter_launches;
+    }
+    if (derr == DCOPF_ERR_UNSUPPORTED && path == DCOPF_PATH_FUSED && h->fused_coop != 0) {
+      // the fused kernel refused this round's cooperative launch before touching any
+      // state (its shape guard runs first): run the round again as a plain launch
+      CUDA_TRY(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+      h->fused_coop = 0;
+      continue;
     }
     if (derr) return (dcopf_status)derr;
     if (active == 0) break;
@@ -419,6 +454,11 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
     // cooperative launches keep the cluster shape of a plain one.
     const char* e = getenv("DCOPF_FUSED_COOPERATIVE");
     if (e && e[0] == '0') h->fused_coop = 0;
+    // DCOPF_FUSED_REFUSE=1 or 2: test hook that makes the fused kernel's shape guard
+    // refuse cooperative launches (1, as profilers that rewrite such launches do) or
+    // every launch (2), to exercise the fallbacks of dcopf_dual_solve_batch.
+    const char* f = getenv("DCOPF_FUSED_REFUSE");
+    if (f && (f[0] == '1' || f[0] == '2')) h->fused_refuse = f[0] - '0';
   }
   std::string err;
   h->sparse_only = opt && opt->operator_form == 1;
@@ -549,8 +589,10 @@ static dcopf_status check_outage(dcopf_dual_t h, int32_t batch, const int32_t* o
   std::vector<int32_t> o(batch);
   if (cudaMemcpyAsync(o.data(), outage, sizeof(int32_t) * batch, cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return DCOPF_ERR_INVALID_ARG;  // not a readable device pointer
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();  // not a readable device pointer: leave no error behind
+    return DCOPF_ERR_INVALID_ARG;
+  }
   for (int32_t k : o) {
     if (k < -1 || k >= h->host.n_line) return DCOPF_ERR_INVALID_ARG;
     if (k >= 0 && h->host.bridge[k]) return DCOPF_ERR_NETWORK;
@@ -580,6 +622,7 @@ dcopf_status dcopf_dual_eval(dcopf_dual_t h, int32_t batch, const double* loads,
     return DCOPF_ERR_INVALID_ARG;
   if (h->sparse_only) return DCOPF_ERR_UNSUPPORTED;  // the evaluation uses Phi~
   DeviceGuard guard(h->device);
+  AccountScope account(&h->acct);
   cudaStream_t s = (cudaStream_t)stream;
   if ((r = check_outage(h, batch, outage, s))) return r;
   if ((r = ensure_workspace(h, batch))) return r;
@@ -602,6 +645,7 @@ dcopf_status dcopf_dual_certify_bound(dcopf_dual_t h, int32_t batch, const doubl
   if (r) return r;
   if (!lambda || !mu_hi || !mu_lo || !bound) return DCOPF_ERR_INVALID_ARG;
   DeviceGuard guard(h->device);
+  AccountScope account(&h->acct);
   cudaStream_t s = (cudaStream_t)stream;
   if ((r = check_outage(h, batch, outage, s))) return r;
   if ((r = run_certify_t<double>(h, batch, loads, outage, lambda, mu_hi, mu_lo, bound, err_bound,
@@ -621,6 +665,7 @@ dcopf_status dcopf_dual_primal_bound(dcopf_dual_t h, int32_t batch, const double
   if (!upper || (!p_cand && (!lambda || !mu_hi || !mu_lo))) return DCOPF_ERR_INVALID_ARG;
   if (h->sparse_only) return DCOPF_ERR_UNSUPPORTED;  // the recovery's flows use Phi~
   DeviceGuard guard(h->device);
+  AccountScope account(&h->acct);
   cudaStream_t s = (cudaStream_t)stream;
   if ((r = check_outage(h, batch, outage, s))) return r;
   if ((r = ensure_workspace(h, batch))) return r;
@@ -660,6 +705,7 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
   if (path == DCOPF_PATH_FUSED && (batch != 1 || outage)) return DCOPF_ERR_UNSUPPORTED;
   int prec = p.precision;
   DeviceGuard guard(h->device);
+  AccountScope account(&h->acct);
   cudaStream_t s = (cudaStream_t)stream;
   if ((r = check_outage(h, batch, outage, s))) return r;
   if ((r = ensure_workspace(h, batch))) return r;
@@ -673,6 +719,17 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
   if (path == DCOPF_PATH_BATCHED && prec == DCOPF_BF16X3)
     return solve_tensor<float>(h, batch, loads, outage, q, lambda, mu_hi, mu_lo, best_bound, iters,
                                inst_status, s);
+  if (path == DCOPF_PATH_FUSED && p.path == DCOPF_PATH_AUTO && h->fused_C == 0) {
+    // AUTO: the fused kernel has no tuned shape yet.  If the tuner finds none that
+    // runs (every shape refused), the same solve runs on the unfused FP32 kernels; the
+    // tuner fails before any output is written, so a warm start is still intact.
+    r = solve_loop<float>(h, batch, loads, outage, q, path, lambda, mu_hi, mu_lo, best_bound, iters,
+                          inst_status, s);
+    if (r != DCOPF_ERR_UNSUPPORTED || h->fused_C != 0) return r;
+    if (h->verbose) fprintf(stderr, "[dcopf] no fused shape runs: unfused FP32 path\n");
+    CUDA_TRY(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+    path = DCOPF_PATH_BATCHED;
+  }
   return solve_loop<float>(h, batch, loads, outage, q, path, lambda, mu_hi, mu_lo, best_bound, iters,
                            inst_status, s);
 }
@@ -736,10 +793,44 @@ dcopf_status dcopf_dual_read_timing(dcopf_dual_t h, double* iter_ms, int64_t* it
   return DCOPF_OK;
 }
 
+dcopf_status dcopf_dual_workspace_limit(dcopf_dual_t h, int64_t limit_bytes, int64_t* used_bytes) {
+  if (!h) return DCOPF_ERR_INVALID_ARG;
+  if (limit_bytes >= 0) h->acct.limit = (size_t)limit_bytes;
+  if (used_bytes) *used_bytes = (int64_t)h->acct.used;
+  return DCOPF_OK;
+}
+
 dcopf_status dcopf_selftest_bounded_wait(dcopf_dual_t h, int64_t timeout_ns, void* stream) {
   if (!h || timeout_ns < 1000 || timeout_ns > 10000000000ll) return DCOPF_ERR_INVALID_ARG;
   DeviceGuard guard(h->device);
+  AccountScope account(&h->acct);
   return run_wait_selftest(h, (long long)timeout_ns, (cudaStream_t)stream);
+}
+
+dcopf_status dcopf_selftest_fused_timeout(dcopf_dual_t h, const double* loads, int64_t timeout_ns,
+                                          void* stream) {
+  if (!h || !loads || timeout_ns < 1000 || timeout_ns > 10000000000ll) return DCOPF_ERR_INVALID_ARG;
+  if (h->sparse_only || h->fused_C == 0) return DCOPF_ERR_UNSUPPORTED;
+  DeviceGuard guard(h->device);
+  AccountScope account(&h->acct);
+  const size_t nl = h->dev.n_line;
+  CUDA_TRY(h, h->probe.alloc((2 * nl + 2) * sizeof(double) + 2 * sizeof(int)));
+  double* lam = h->probe.as<double>();
+  double* mh = lam + 1;
+  double* ml = mh + nl;
+  double* bound = ml + nl;
+  int* it = (int*)(bound + 1);
+  dcopf_solve_params p;
+  dcopf_solve_params_default(&p);
+  p.path = DCOPF_PATH_FUSED;
+  p.max_iters = 10;
+  h->fused_timeout_ns = (unsigned long long)timeout_ns;
+  h->fused_arrive_extra = 1;
+  const dcopf_status r = dcopf_dual_solve_batch(h, 1, loads, nullptr, &p, lam, mh, ml, bound, it,
+                                                it + 1, stream);
+  h->fused_timeout_ns = 2000000000ull;
+  h->fused_arrive_extra = 0;
+  return r;
 }
 
 dcopf_status dcopf_dual_device_error(dcopf_dual_t h) {

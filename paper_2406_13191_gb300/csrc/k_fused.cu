@@ -80,6 +80,7 @@ struct FusedArgs {
   int C, G;                      // launch shape the shared-memory layout was sized for
   unsigned smem_bytes;           // dynamic shared memory the layout needs
   uint64_t timeout_ns;
+  unsigned arrive_extra;         // added to the inter-cluster arrival target (self-test)
 };
 
 // The ascent rule's constants in FP32, converted once per launch (FP64 conversions and
@@ -307,7 +308,8 @@ __global__ void __launch_bounds__(256, 1) k_fused_solve(FusedArgs A) {
       if (tid < C) {
         // counter `tid` counts the arrivals of rank-tid CTAs: NCL per loop
         // acquire loads; bar.sync below extends the ordering to the whole CTA
-        const bool got = bounded_wait_geq(A.cnt + tid, (unsigned)NCL * (k + 1u), A.timeout_ns);
+        const bool got = bounded_wait_geq(A.cnt + tid, (unsigned)NCL * (k + 1u) + A.arrive_extra,
+                                          A.timeout_ns);
         if (!got) record_gave_up(2, k);
         ok = got && ok;
       }
@@ -743,7 +745,8 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
   }
   A.max_iters = max_iters;
   A.tol = tol;
-  A.timeout_ns = 2000000000ull;
+  A.timeout_ns = h->fused_timeout_ns;
+  A.arrive_extra = h->fused_arrive_extra;
   A.demand = h->ws.demand.as<double>();  // read on the device: no host round trip
   if (cudaMemsetAsync(A.cnt, 0, 256, s) != cudaSuccess) return DCOPF_ERR_CUDA;
   cudaLaunchConfig_t cfg{};
@@ -763,12 +766,17 @@ dcopf_status run_iters_fused(dcopf_dual* h, const StepArgs& P, SolveState<float>
   // it accepts that together with clusters; otherwise the grid is sized from
   // cudaOccupancyMaxActiveClusters and the bounded waits are the guard.
   cfg.numAttrs = h->fused_coop == 0 ? 1 : 2;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_fused_solve, A);
+  // the refusal hook: a shape record that does not match the launch
+  FusedArgs Ar = A;
+  Ar.C = A.C + 1;
+  const bool refuse_coop = h->fused_refuse >= 1, refuse_all = h->fused_refuse == 2;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_fused_solve,
+                                     (refuse_all || (refuse_coop && cfg.numAttrs == 2)) ? Ar : A);
   if (e != cudaSuccess && cfg.numAttrs == 2) {
     cudaGetLastError();
     h->fused_coop = 0;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_fused_solve, A);
+    e = cudaLaunchKernelEx(&cfg, k_fused_solve, refuse_all ? Ar : A);
   } else if (e == cudaSuccess && cfg.numAttrs == 2) {
     h->fused_coop = 1;
   }

@@ -52,10 +52,15 @@ extern "C" dcopf_status dcopf_dual_eval_noalloc(dcopf_dual_t h, int32_t batch, c
                                                 int32_t precision, double* value, double* g_lambda,
                                                 double* g_mu_hi, double* g_mu_lo, double* dispatch,
                                                 void* stream) {
-  if (!h || batch < 1 || !loads || !lambda || !mu_hi || !mu_lo || !value)
+  // the same host checks, in the same order, as dcopf_dual_eval
+  if (!h || batch < 1 || !loads) return DCOPF_ERR_INVALID_ARG;
+  if ((long long)batch * h->host.n_line > (1ll << 31)) return DCOPF_ERR_UNSUPPORTED;
+  if (certify_smem(h, true) > h->smem_optin) return DCOPF_ERR_UNSUPPORTED;
+  if (!lambda || !mu_hi || !mu_lo || !value) return DCOPF_ERR_INVALID_ARG;
+  if (precision != DCOPF_FP64 && precision != DCOPF_FP32 && precision != DCOPF_BF16X3)
     return DCOPF_ERR_INVALID_ARG;
-  if (precision != DCOPF_FP64 && precision != DCOPF_FP32) return DCOPF_ERR_UNSUPPORTED;
   if (h->sparse_only) return DCOPF_ERR_UNSUPPORTED;  // the evaluation uses Phi~
+  if (precision == DCOPF_BF16X3) return DCOPF_ERR_UNSUPPORTED;  // its operands need a workspace
   const size_t B = (size_t)batch, nl = (size_t)h->host.n_line, ng = (size_t)h->host.n_gen;
   // scratch carve-up: every section 256-byte aligned
   size_t need = 0;
@@ -84,6 +89,7 @@ extern "C" dcopf_status dcopf_dual_eval_noalloc(dcopf_dual_t h, int32_t batch, c
         if (cudaMemcpyAsync(chunk, outage + b0, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
+          cudaGetLastError();  // not a readable device pointer: leave no error behind
           r = DCOPF_ERR_INVALID_ARG;
           break;
         }

@@ -238,6 +238,7 @@ dcopf_status run_primal(dcopf_dual* h, int B, const int* outage, const double* l
   const int nl = N.n_line, ng = N.n_gen;
   PrimalBufs& pb = h->pb;
   if (B > pb.cap) {
+    pb.cap = 0;  // reset unless every buffer below is allocated
     const size_t bg = (size_t)B * ng * 8, bl = (size_t)B * nl * 8;
     if (pb.xr.alloc(bg) != cudaSuccess || pb.xu.alloc(bg) != cudaSuccess ||
         pb.fr.alloc(bl) != cudaSuccess || pb.t.alloc((size_t)B * 8) != cudaSuccess ||

@@ -79,10 +79,17 @@ struct StepEpi {
   const int* outage;          // [B] or null
   const float* tout;          // [B] pre-outage flow on the outaged line, (Phi~ x)_k
   const float* fmax; const float* fmin;
-  const int* iter;            // [B] evaluations done: parity selects the state buffer
+  const int* iter;            // [B] evaluations done: iter % 3 selects the state buffer
   const int* frozen;          // [B] done or waiting for certification
+  const int* best_iter;       // [B] evaluation count of the best point so far
   const float* stepf;         // [B][4] alpha scale, 1 - beta1^t, 1 - beta2^t
-  float* mu_hi[2]; float* mu_lo[2];
+  // Three state buffers in turn: point t lives in buffer t % 3, so the two points
+  // before the one being stepped are still there.  The step writing point t + 1
+  // overwrites point t - 2; if that point is still the best (the value fell after
+  // it), it is first copied to sv.  Points that are overtaken before their buffer
+  // comes round are never copied.
+  float* mu_hi[3]; float* mu_lo[3];
+  float* sv_hi; float* sv_lo;
   float* s1_hi; float* s2_hi; float* s1_lo; float* s2_lo;
   __nv_bfloat16* Hh; __nv_bfloat16* Hl; int ldh;
   double* line_part; double* out_part; int n_tiles;   // [B][n_tiles] per chunk of lines
@@ -283,12 +290,13 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
   if (E.frozen[b]) return;
   const int k = E.outage ? E.outage[b] : -1;
   const float t_out = k >= 0 ? E.tout[b] : 0.f;
-  const int pb = E.iter[b] & 1;
+  const int it = E.iter[b], pb = it % 3, pn = (it + 1) % 3;
+  const bool save = it >= 2 && E.best_iter[b] == it - 1;  // point it - 2 is the best
   const size_t o = (size_t)b * nl;
   const float* mhc = E.mu_hi[pb] + o;
   const float* mlc = E.mu_lo[pb] + o;
-  float* mhn = E.mu_hi[pb ^ 1] + o;
-  float* mln = E.mu_lo[pb ^ 1] + o;
+  float* mhn = E.mu_hi[pn] + o;
+  float* mln = E.mu_lo[pn] + o;
   const float am = E.stepf[4 * b], bc1 = E.stepf[4 * b + 1], bc2 = E.stepf[4 * b + 2];
   const float* Fr = E.F + (size_t)b * E.ldF;
   // a thread's few terms are summed in FP32 and the block sum is FP64 (FP64 throughput
@@ -326,6 +334,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
       nlo = fmaxf(step_rule(E.P, ml[q], gl, b1[q], b2[q], am, bc1, bc2), 0.f);
       E.s1_hi[o + i] = a1[q]; E.s2_hi[o + i] = a2[q]; E.s1_lo[o + i] = b1[q]; E.s2_lo[o + i] = b2[q];
     }
+    if (save) { E.sv_hi[o + i] = mhn[i]; E.sv_lo[o + i] = mln[i]; }
     mhn[i] = nh;
     mln[i] = nlo;
     const float eta = nh - nlo;
@@ -361,7 +370,8 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step4(StepEpi E, int nl) {
   if (E.frozen[b]) return;
   const int k = E.outage ? E.outage[b] : -1;
   const float t_out = k >= 0 ? E.tout[b] : 0.f;
-  const int pb = E.iter[b] & 1;
+  const int it = E.iter[b], pb = it % 3, pn = (it + 1) % 3;
+  const bool save = it >= 2 && E.best_iter[b] == it - 1;  // point it - 2 is the best
   const size_t o = (size_t)b * nl;
   const float am = E.stepf[4 * b], bc1 = E.stepf[4 * b + 1], bc2 = E.stepf[4 * b + 2];
   const int i = 4 * (chunk * STEP_THREADS + threadIdx.x);
@@ -404,8 +414,12 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step4(StepEpi E, int nl) {
     auto st4 = [](float* p, const float* v) {
       *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
     };
-    st4(E.mu_hi[pb ^ 1] + o + i, NH);
-    st4(E.mu_lo[pb ^ 1] + o + i, NL);
+    if (save) {  // the best point's buffer is about to be reused: keep a copy
+      *reinterpret_cast<float4*>(E.sv_hi + o + i) = ld4(E.mu_hi[pn] + o + i);
+      *reinterpret_cast<float4*>(E.sv_lo + o + i) = ld4(E.mu_lo[pn] + o + i);
+    }
+    st4(E.mu_hi[pn] + o + i, NH);
+    st4(E.mu_lo[pn] + o + i, NL);
     st4(E.s1_hi + o + i, A1);
     st4(E.s2_hi + o + i, A2);
     st4(E.s1_lo + o + i, B1);
@@ -572,10 +586,13 @@ dcopf_status ensure_tensor_batch(dcopf_dual* h, int B) {
   if (B <= T.cap) return DCOPF_OK;
   const int nl = h->host.n_line, ng = h->host.n_gen;
   const int ldp = (ng + 3) & ~3;
+  T.cap = 0;  // reset unless every buffer and tensor map below is made
   if (T.H_hi.alloc((size_t)B * T.ld_l * 2) || T.H_lo.alloc((size_t)B * T.ld_l * 2) ||
       T.X_hi.alloc((size_t)B * T.ld_g * 2) || T.X_lo.alloc((size_t)B * T.ld_g * 2) ||
-      T.P.alloc((size_t)64 * B * ldp * 4))
+      T.P.alloc((size_t)64 * B * ldp * 4)) {
+    cudaGetLastError();
     return DCOPF_ERR_OOM;
+  }
   cudaMemset(T.H_hi.p, 0, (size_t)B * T.ld_l * 2);
   cudaMemset(T.H_lo.p, 0, (size_t)B * T.ld_l * 2);
   cudaMemset(T.X_hi.p, 0, (size_t)B * T.ld_g * 2);
@@ -794,9 +811,10 @@ __global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
   }
 }
 
-// Dual value of the evaluated point (FP64), best value, outage patch of the next
-// eta, stop tests.  A stopping instance is frozen with its point in the state buffer
-// of parity iter & 1.  One warp per instance.
+// Dual value of the evaluated point (FP64), best value and its lambda, outage patch of
+// the next eta, stop tests.  A stopping instance is frozen: one that reached its
+// target with the point just evaluated (state buffer iter % 3), one stopped by the
+// iteration cap or the tol test with its best point.  One warp per instance.
 __global__ void k_bt_finalize(int B, int ld_l, int max_iters, double tol, SolveStateBase st,
                               BatchView bb, const int* __restrict__ outage,
                               const double* __restrict__ demand,
@@ -814,7 +832,7 @@ __global__ void k_bt_finalize(int B, int ld_l, int max_iters, double tol, SolveS
   if (lane != 0) return;
   const double val = bb.cost[b] + bb.lam_eval[b] * (bb.psum[b] - demand[b]) + ls;
   const int t = st.iter[b] + 1;
-  if (val > st.best[b]) { st.best[b] = val; st.best_iter[b] = t; }
+  if (val > st.best[b]) { st.best[b] = val; st.best_iter[b] = t; bb.lam_best[b] = bb.lam_eval[b]; }
   const int k = outage ? outage[b] : -1;
   if (k >= 0) split_bf16((float)os, Hh + (size_t)b * ld_l + k, Hl + (size_t)b * ld_l + k);
   int c = 0;
@@ -825,24 +843,30 @@ __global__ void k_bt_finalize(int B, int ld_l, int max_iters, double tol, SolveS
   if (c) {
     st.cand[b] = c;
     bb.frozen[b] = 1;
-    st.best_lam[b] = bb.lam_eval[b];
+    st.best_lam[b] = c == 1 ? bb.lam_eval[b] : bb.lam_best[b];
   } else {
     st.iter[b] = t;
   }
 }
 
-// Copies the frozen candidates' points (state buffer of parity iter & 1) to best_*, and
-// snapshots which instances are staged (snap[b] = 1): the certificate and the accept
-// step of this round act on exactly those, while the next round's iterations may
-// freeze others.
+// Copies the frozen candidates' points to best_* and snapshots which instances are
+// staged (snap[b] = 1): the certificate and the accept step of this round act on
+// exactly those, while the next round's iterations may freeze others.  A candidate
+// that reached its target is the point just evaluated (state buffer iter % 3); one
+// stopped by the iteration cap or the tol test is its best point: point iter or
+// iter - 1 (still in their buffers) or an older one (its saved copy).
 __global__ void k_bt_select(int B, int nl, SolveState<float> st, BatchView bb, int* snap) {
   const int b = blockIdx.y;
   const bool staged = st.cand[b] && !st.done[b];
   if (blockIdx.x == 0 && threadIdx.x == 0) snap[b] = staged ? 1 : 0;
   if (!staged) return;
-  const int pb = st.iter[b] & 1;
-  const float* sh = pb ? bb.mu2_hi : st.mu_hi;
-  const float* sl = pb ? bb.mu2_lo : st.mu_lo;
+  const int it = st.iter[b];
+  // how many points before the last one the staged point is (0 with no best yet)
+  const int back = (st.cand[b] == 1 || st.best_iter[b] < 1) ? 0 : it + 1 - st.best_iter[b];
+  const float* bh[3] = {st.mu_hi, bb.mu2_hi, bb.mu3_hi};
+  const float* bl[3] = {st.mu_lo, bb.mu2_lo, bb.mu3_lo};
+  const float* sh = back <= 1 ? bh[(it - back) % 3] : bb.sv_hi;
+  const float* sl = back <= 1 ? bl[(it - back) % 3] : bb.sv_lo;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
     st.best_hi[(size_t)b * nl + i] = sh[(size_t)b * nl + i];
     st.best_lo[(size_t)b * nl + i] = sl[(size_t)b * nl + i];
@@ -890,17 +914,24 @@ static dcopf_status ensure_batch_bufs(dcopf_dual* h, int B, int n_tiles) {
   BatchBufs& bb = h->bb;
   BatchView& v = bb.v;
   const size_t nl = h->host.n_line;
-  if (bb.mu2.alloc((size_t)B * nl * 2 * sizeof(float)) ||
+  if (bb.mu2.alloc((size_t)B * nl * 6 * sizeof(float)) ||
       bb.parts.alloc((size_t)B * n_tiles * 2 * sizeof(double)) ||
-      bb.small.alloc((size_t)B * 6 * sizeof(double) + (size_t)B * 6 * sizeof(float) + 1024))
+      bb.small.alloc((size_t)B * 7 * sizeof(double) + (size_t)B * 6 * sizeof(float) + 1024)) {
+    cudaGetLastError();
     return DCOPF_ERR_OOM;
+  }
   v.mu2_hi = bb.mu2.as<float>();
   v.mu2_lo = v.mu2_hi + (size_t)B * nl;
+  v.mu3_hi = v.mu2_hi + 2 * (size_t)B * nl;
+  v.mu3_lo = v.mu2_hi + 3 * (size_t)B * nl;
+  v.sv_hi = v.mu2_hi + 4 * (size_t)B * nl;
+  v.sv_lo = v.mu2_hi + 5 * (size_t)B * nl;
   v.line_part = bb.parts.as<double>();
   v.out_part = v.line_part + (size_t)B * n_tiles;
   double* d = bb.small.as<double>();
   v.lam_eval = d; v.cost = d + B; v.psum = d + 2 * (size_t)B; v.pw = d + 3 * (size_t)B;  // pw: [B][3]
-  float* f = (float*)(d + 6 * (size_t)B);
+  v.lam_best = d + 6 * (size_t)B;
+  float* f = (float*)(d + 7 * (size_t)B);
   v.tout = f; v.stepf = f + B;  // stepf: [B][4]
   v.frozen = (int*)(f + 5 * (size_t)B);
   v.n_tiles = n_tiles;
@@ -1057,7 +1088,10 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   E.outage = R.it.outage; E.tout = bb.tout;
   E.fmax = h->dev.fmax32; E.fmin = h->dev.fmin32; E.iter = R.st.iter; E.frozen = bb.frozen;
   E.stepf = bb.stepf;
-  E.mu_hi[0] = R.st.mu_hi; E.mu_hi[1] = bb.mu2_hi; E.mu_lo[0] = R.st.mu_lo; E.mu_lo[1] = bb.mu2_lo;
+  E.best_iter = R.st.best_iter;
+  E.mu_hi[0] = R.st.mu_hi; E.mu_hi[1] = bb.mu2_hi; E.mu_hi[2] = bb.mu3_hi;
+  E.mu_lo[0] = R.st.mu_lo; E.mu_lo[1] = bb.mu2_lo; E.mu_lo[2] = bb.mu3_lo;
+  E.sv_hi = bb.sv_hi; E.sv_lo = bb.sv_lo;
   E.s1_hi = R.st.s1_hi; E.s2_hi = R.st.s2_hi; E.s1_lo = R.st.s1_lo; E.s2_lo = R.st.s2_lo;
   E.Hh = T.H_hi.as<__nv_bfloat16>(); E.Hl = T.H_lo.as<__nv_bfloat16>(); E.ldh = T.ld_l;
   E.line_part = bb.line_part; E.out_part = bb.out_part; E.n_tiles = R.n_tiles;

@@ -72,21 +72,55 @@ struct SolveState : SolveStateBase {
   S* best_hi; S* best_lo;
 };
 
-// Device buffer that frees itself.
+// Device-memory account of one handle's workspaces: the bytes its buffers hold and an
+// optional limit (0 = none).  A handle's entry points make its account the calling
+// thread's current one (AccountScope); buffers allocated under it are charged to it.
+struct AllocAccount {
+  size_t used = 0, limit = 0;
+};
+extern thread_local AllocAccount* tl_account;
+struct AccountScope {
+  AllocAccount* prev;
+  explicit AccountScope(AllocAccount* a) : prev(tl_account) { tl_account = a; }
+  ~AccountScope() { tl_account = prev; }
+  AccountScope(const AccountScope&) = delete;
+  AccountScope& operator=(const AccountScope&) = delete;
+};
+
+// Device buffer that frees itself.  Growing it under an account whose limit it would
+// exceed fails with cudaErrorMemoryAllocation before anything is freed, so the
+// buffer keeps its old size and contents.
 struct DBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  AllocAccount* acct = nullptr;  // the account its bytes are charged to, if any
   DBuf() = default;
   DBuf(const DBuf&) = delete;
   DBuf& operator=(const DBuf&) = delete;
-  ~DBuf() { if (p) cudaFree(p); }
-  cudaError_t alloc(size_t n) {
-    if (n <= bytes && p) return cudaSuccess;
+  ~DBuf() { release(); }
+  void release() {
     if (p) cudaFree(p);
+    if (acct) acct->used -= bytes;
     p = nullptr;
     bytes = 0;
+    acct = nullptr;
+  }
+  cudaError_t alloc(size_t n) {
+    if (n <= bytes && p) return cudaSuccess;
+    AllocAccount* a = tl_account;
+    if (a && a->limit && a->used - (acct == a ? bytes : 0) + n > a->limit)
+      return cudaErrorMemoryAllocation;
+    release();
     cudaError_t e = cudaMalloc(&p, n ? n : 16);
-    if (e == cudaSuccess) bytes = n;
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = n;
+    if (a) {
+      a->used += n;
+      acct = a;
+    }
     return e;
   }
   template <typename T> T* as() const { return (T*)p; }
@@ -125,8 +159,13 @@ struct BatchView {
   double* pw = nullptr;        // [B][3] decay^t, beta1^t, beta2^t
   float* tout = nullptr;       // [B] pre-outage flow on the outaged line
   float* stepf = nullptr;      // [B][4] step factors of the current step
-  float* mu2_hi = nullptr;     // [B][nl] second state buffer (parity 1)
+  float* mu2_hi = nullptr;     // [B][nl] second state buffer (iteration index % 3 == 1)
   float* mu2_lo = nullptr;
+  float* mu3_hi = nullptr;     // [B][nl] third state buffer (index % 3 == 2)
+  float* mu3_lo = nullptr;
+  float* sv_hi = nullptr;      // [B][nl] the best point, saved when its buffer is reused
+  float* sv_lo = nullptr;
+  double* lam_best = nullptr;  // [B] lambda of the best point
   double* line_part = nullptr; // [B][n_tiles] per chunk of lines of the step kernel
   double* out_part = nullptr;  // [B][n_tiles]
 };
@@ -153,6 +192,8 @@ struct StateBufs {
 }  // namespace dcopf
 
 struct dcopf_dual {
+  // first member: outlives every buffer charged to it
+  dcopf::AllocAccount acct;
   int device = 0;
   dcopf::HostNet host;
   dcopf::DevNet dev{};
@@ -186,6 +227,16 @@ struct dcopf_dual {
   size_t fshape_smem = 0;
   bool sparse_only = false;      // created with operator_form 1: no Phi~ on the device
   int fused_coop = -1;           // -1 unknown, 1 cooperative+cluster launch accepted, 0 not
+  // host-side refusal injection (DCOPF_FUSED_REFUSE, read at create): 1 sizes every
+  // cooperative fused launch for another cluster shape, 2 every fused launch, so that
+  // the kernel's shape guard refuses it (no device fault: the kernel returns a status)
+  int fused_refuse = 0;
+  // limit of the fused kernel's bounded waits, and extra arrivals its inter-cluster
+  // wait expects (nonzero only inside dcopf_selftest_fused_timeout: a count that no
+  // cluster reaches, so that the wait gives up)
+  unsigned long long fused_timeout_ns = 2000000000ull;
+  unsigned fused_arrive_extra = 0;
+  dcopf::DBuf probe;  // outputs of the fused self-test
   // split-K of the batched adjoint GEMM chosen by timing (for batch size tune_B)
   int tune_B = 0, tune_splits = 0, tune_kbps = 0;
   size_t smem_optin = 0;

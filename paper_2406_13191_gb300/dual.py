@@ -180,6 +180,22 @@ class DcopfDual:
                    "read_timing")
         return ms.value, nl.value, ne.value
 
+    def workspace_limit(self, limit_bytes: int | None = None) -> int:
+        """``dcopf_dual_workspace_limit``: sets the workspace budget in bytes (0 = none;
+        None leaves it unchanged) and returns the bytes the workspaces hold now."""
+        used = C.c_int64()
+        _lib.check(self.lib.dcopf_dual_workspace_limit(
+            self.h, -1 if limit_bytes is None else int(limit_bytes), C.byref(used)),
+            "dcopf_dual_workspace_limit")
+        return used.value
+
+    def selftest_fused_timeout(self, loads, timeout_ns: int) -> int:
+        """``dcopf_selftest_fused_timeout``: the status code of a fused solve whose
+        inter-cluster wait cannot complete (DCOPF_ERR_TIMEOUT = 5 expected)."""
+        ld = _as_dev(loads, torch.float64, self.device).reshape(self.n_bus)
+        return int(self.lib.dcopf_selftest_fused_timeout(self.h, _ptr(ld), int(timeout_ns),
+                                                         self._stream()))
+
     # ------------------------------------------------------------------ entry points
     def eval(self, loads, lam, mu_hi, mu_lo, outage=None, precision: str = "fp64",
              want_grad: bool = True, want_dispatch: bool = True):

@@ -9,7 +9,7 @@ import pytest
 import torch
 
 from oracle import dcopf
-from paper_2406_13191_gb300 import DcopfDual, synth
+from paper_2406_13191_gb300 import DcopfDual, _lib, synth
 
 from gpu_common import drop_line, gamma, onet
 
@@ -262,3 +262,69 @@ def test_batched_10000bus_reaches_stored_optima():
     st = r.status.cpu().numpy()
     assert np.all(b <= T + 1e-9 * np.abs(T))
     assert np.all(st == 0) and np.all(b >= T * (1 - 1e-3))
+
+
+@pytest.mark.parametrize("mode", ["1", "2"])
+def test_fused_refusal_falls_back(c0, mode, monkeypatch):
+    """The fused kernel's shape guard refuses a launch whose cluster shape differs from
+    the one its shared-memory layout was sized for (profilers that replay cooperative
+    launches drop the cluster shape).  DCOPF_FUSED_REFUSE (read at create) makes the host
+    record another shape: 1 for cooperative launches only, 2 for every fused launch.
+    Mode 1: the solve relaunches as a plain cluster launch and the fused path itself
+    reaches the gap.  Mode 2: an explicit fused solve reports UNSUPPORTED, and an AUTO
+    solve of the same instance runs on the unfused kernels and reaches the gap."""
+    net, base, on, _, gam = c0
+    monkeypatch.setenv("DCOPF_FUSED_REFUSE", mode)
+    g = DcopfDual(net)
+    monkeypatch.delenv("DCOPF_FUSED_REFUSE")
+    if mode == "1":
+        res = g.solve(base[None], path="fused", target=[gam], **ADAM_LP)
+        _check(res, on, base, gam)
+    else:
+        with pytest.raises(_lib.DcopfError) as e:
+            g.solve(base[None], path="fused", target=[gam], **ADAM_LP)
+        assert e.value.code == 6   # DCOPF_ERR_UNSUPPORTED
+    res = g.solve(base[None], path="auto", target=[gam], **ADAM_LP)
+    torch.cuda.synchronize()
+    _check(res, on, base, gam)
+
+
+def test_workspace_limit_gives_oom_and_handle_recovers(c0):
+    """A workspace budget below what a larger batch needs: that call returns
+    DCOPF_ERR_OOM before enqueueing work, and the handle keeps solving batches whose
+    workspaces fit, and the large batch once the budget is lifted."""
+    net, base, on, _, gam = c0
+    g = DcopfDual(net)
+    small = g.solve(base[None], path="batched", precision="fp32", target=[gam], **ADAM_LP)
+    _check(small, on, base, gam)
+    used = g.workspace_limit()
+    assert used > 0
+    g.workspace_limit(used)
+    big = np.repeat(base[None], 512, 0)
+    with pytest.raises(_lib.DcopfError) as e:
+        g.solve(big, path="batched", precision="fp32", target=[gam] * 512, **ADAM_LP)
+    assert e.value.code == 4   # DCOPF_ERR_OOM
+    assert g.workspace_limit() <= used
+    res = g.solve(base[None], path="batched", precision="fp32", target=[gam], **ADAM_LP)
+    _check(res, on, base, gam)
+    g.workspace_limit(0)
+    res = g.solve(big, path="batched", precision="fp32", target=[gam] * 512, **ADAM_LP)
+    torch.cuda.synchronize()
+    for b in (0, 255, 511):
+        _check(res, on, base, gam, b=b)
+    assert g.workspace_limit() > used
+
+
+def test_fused_wait_timeout_reports_and_recovers(c0):
+    """The fused kernel's inter-cluster wait gives up (its arrival target is one more
+    than the clusters make, with a 1 ms limit): the solve returns DCOPF_ERR_TIMEOUT and
+    the next fused solve on the same handle reaches the gap."""
+    net, base, on, _, gam = c0
+    g = DcopfDual(net)
+    res = g.solve(base[None], path="fused", target=[gam], **ADAM_LP)   # picks the shape
+    _check(res, on, base, gam)
+    ld = torch.tensor(base, dtype=torch.float64, device="cuda")
+    assert g.selftest_fused_timeout(ld, 1_000_000) == 5   # DCOPF_ERR_TIMEOUT
+    res = g.solve(base[None], path="fused", target=[gam], **ADAM_LP)
+    torch.cuda.synchronize()
+    _check(res, on, base, gam)

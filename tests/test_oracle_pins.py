@@ -316,3 +316,68 @@ def test_adam_converges_on_hand_and_c0():
                         beta1=0.9, beta2=0.999, decay=0.99, max_iters=5000, target=g, gap=1e-3)
         assert r["stop"] == "target"
         assert g * (1 - 1e-3) - 1e-9 <= r["best"] <= g + 1e-9 * abs(g)
+
+
+def test_ascent_rules_decay_and_alpha_lambda():
+    """Decayed steps with a separate lambda step size, written out by hand.
+
+    Step-size decay (Section 4.1 remarks) is read as a multiplicative schedule: the k-th
+    step (k = 1, 2, ...) uses alpha * decay^(k-1) for mu and alpha_lambda * decay^(k-1)
+    for lambda.  Three GDM steps (heavy ball, the velocity keeps the undecayed earlier
+    contributions), two Adam steps and two AdaGrad steps (the second divides by the
+    root of the summed squares of both gradients)."""
+    net, loads, _ = hand("three_bus")
+    z = np.zeros(net.n_line)
+    a, al, rho, d = 3.0, 0.5, 0.6, 0.8
+
+    def grad(lam, mh, ml):
+        _, gl, ghi, glo, _ = dcopf.evaluate(net, loads, lam, mh, ml)
+        return gl, ghi, glo
+
+    # GDM: v_k = rho v_{k-1} + step_k g_{k-1}, theta_k = theta_{k-1} + v_k, mu projected
+    r = dcopf.solve(net, loads, rule="gdm", alpha=a, alpha_lambda=al, rho=rho, decay=d,
+                    max_iters=4, record=True)
+    lam, mh, ml = 0.0, z.copy(), z.copy()
+    vl, vh, vo = 0.0, z.copy(), z.copy()
+    for k in (1, 2, 3):
+        gl, ghi, glo = grad(lam, mh, ml)
+        vl = rho * vl + al * d ** (k - 1) * gl
+        vh = rho * vh + a * d ** (k - 1) * ghi
+        vo = rho * vo + a * d ** (k - 1) * glo
+        lam, mh, ml = lam + vl, np.maximum(mh + vh, 0), np.maximum(ml + vo, 0)
+        pl, ph, po = r["points"][k]
+        assert abs(pl - lam) < 1e-12 * max(1.0, abs(lam))
+        assert np.allclose(ph, mh, rtol=1e-12, atol=1e-12)
+        assert np.allclose(po, ml, rtol=1e-12, atol=1e-12)
+    assert abs(r["points"][1][0] - al * grad(0.0, z, z)[0]) < 1e-12   # undecayed first step
+
+    # Adam, eps = 0: first step alpha_lambda sign(g0); second step decayed
+    b1, b2 = 0.7, 0.9
+    r = dcopf.solve(net, loads, rule="adam", alpha=a, alpha_lambda=al, beta1=b1, beta2=b2,
+                    eps=0.0, decay=d, max_iters=3, record=True)
+    gl0, ghi0, _ = grad(0.0, z, z)
+    lam1, mh1, ml1 = r["points"][1]
+    assert abs(lam1 - al * np.sign(gl0)) < 1e-12
+    assert np.allclose(mh1, np.maximum(a * np.sign(ghi0), 0))
+    gl1, ghi1, _ = grad(lam1, mh1, ml1)
+    m = (1 - b1) * (b1 * gl0 + gl1) / (1 - b1 ** 2)
+    v = (1 - b2) * (b2 * gl0 ** 2 + gl1 ** 2) / (1 - b2 ** 2)
+    assert abs(r["points"][2][0] - (lam1 + al * d * m / np.sqrt(v))) < 1e-9
+    mv = (1 - b1) * (b1 * ghi0 + ghi1) / (1 - b1 ** 2)
+    vv = (1 - b2) * (b2 * ghi0 ** 2 + ghi1 ** 2) / (1 - b2 ** 2)
+    nz = vv > 0
+    want = mh1.copy()
+    want[nz] = np.maximum(mh1[nz] + a * d * mv[nz] / np.sqrt(vv[nz]), 0)
+    assert np.allclose(r["points"][2][1], want, rtol=1e-12, atol=1e-9)
+
+    # AdaGrad, eps = 0: theta_2 = theta_1 + step_2 g1 / sqrt(g0^2 + g1^2)
+    r = dcopf.solve(net, loads, rule="adagrad", alpha=a, alpha_lambda=al, eps=0.0, decay=d,
+                    max_iters=3, record=True)
+    lam1, mh1, ml1 = r["points"][1]
+    assert abs(lam1 - al * np.sign(gl0)) < 1e-12
+    gl1, ghi1, _ = grad(lam1, mh1, ml1)
+    assert abs(r["points"][2][0] - (lam1 + al * d * gl1 / np.sqrt(gl0 ** 2 + gl1 ** 2))) < 1e-12
+    den = np.sqrt(ghi0 ** 2 + ghi1 ** 2)
+    want = mh1.copy()
+    want[den > 0] = np.maximum(mh1[den > 0] + a * d * ghi1[den > 0] / den[den > 0], 0)
+    assert np.allclose(r["points"][2][1], want, rtol=1e-12, atol=1e-12)
