@@ -18,7 +18,9 @@ EXPORTS = ("dcopf_version", "dcopf_status_string", "dcopf_solve_params_default",
            "dcopf_mlp_create", "dcopf_mlp_destroy", "dcopf_mlp_num_params", "dcopf_mlp_set_params",
            "dcopf_mlp_get_params", "dcopf_mlp_set_normalization", "dcopf_mlp_forward",
            "dcopf_mlp_loss_grad", "dcopf_mlp_train_step", "dcopf_mlp_warm_start",
-           "dcopf_mlp_device_error", "dcopf_mlp_kernel_launches")
+           "dcopf_mlp_device_error", "dcopf_mlp_kernel_launches",
+           "dcopf_probe_read", "dcopf_probe_smem", "dcopf_probe_fma", "dcopf_probe_tma_feed",
+           "dcopf_probe_exchange")
 
 STATUS = {0: "DCOPF_OK", 1: "DCOPF_ERR_INVALID_ARG", 2: "DCOPF_ERR_NETWORK", 3: "DCOPF_ERR_CUDA",
           4: "DCOPF_ERR_OOM", 5: "DCOPF_ERR_TIMEOUT", 6: "DCOPF_ERR_UNSUPPORTED"}
@@ -128,6 +130,14 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                                          C.POINTER(AdamParams), P, P]
     lib.dcopf_mlp_warm_start.argtypes = [P, C.c_int32, P, P, P, P, P]
     lib.dcopf_mlp_device_error.argtypes = [P]
+    lib.dcopf_probe_read.argtypes = [C.c_int64, C.c_int32, F64P]
+    lib.dcopf_probe_smem.argtypes = [F64P]
+    lib.dcopf_probe_fma.argtypes = [C.c_int32, F64P, F64P]
+    lib.dcopf_probe_tma_feed.argtypes = [C.c_int64, F64P]
+    lib.dcopf_probe_exchange.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, F64P]
+    for name in ("dcopf_probe_read", "dcopf_probe_smem", "dcopf_probe_fma", "dcopf_probe_tma_feed",
+                 "dcopf_probe_exchange"):
+        getattr(lib, name).restype = C.c_int
     lib.dcopf_mlp_kernel_launches.argtypes = [P]
     lib.dcopf_mlp_kernel_launches.restype = C.c_int64
     for name in ("dcopf_mlp_create", "dcopf_mlp_destroy", "dcopf_mlp_set_params",

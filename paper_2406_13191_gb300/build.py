@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libdcopfdual.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["network.cpp", "api.cu", "k_sparse.cu", "k_phases.cu", "k_fused.cu", "k_tensor.cu", "k_noalloc.cu", "k_dense.cu",
-           "k_mlp.cu", "k_primal.cu"]
+           "k_mlp.cu", "k_primal.cu", "k_probe.cu"]
 
 
 def nvcc() -> str:
@@ -33,8 +33,6 @@ def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, src + ".o")
     cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj, "-O3", "-std=c++17", "-lineinfo",
            "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"] + ARCH
-    if src.endswith(".cpp"):
-        cmd += ["-x", "cu"] if False else []
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

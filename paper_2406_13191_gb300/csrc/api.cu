@@ -459,6 +459,13 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
     // every launch (2), to exercise the fallbacks of dcopf_dual_solve_batch.
     const char* f = getenv("DCOPF_FUSED_REFUSE");
     if (f && (f[0] == '1' || f[0] == '2')) h->fused_refuse = f[0] - '0';
+    // DCOPF_TENSOR_TILES=128, 256 or 192: the batched products on single CTAs only, or
+    // on CTA pairs of 256 x 256 or 256 x 192 tiles only, instead of the shapes the first
+    // solve of a batch size times fastest
+    const char* t = getenv("DCOPF_TENSOR_TILES");
+    if (t && strcmp(t, "128") == 0) h->tiles_mode = 1;
+    if (t && strcmp(t, "256") == 0) h->tiles_mode = 2;
+    if (t && strcmp(t, "192") == 0) h->tiles_mode = 3;
   }
   std::string err;
   h->sparse_only = opt && opt->operator_form == 1;

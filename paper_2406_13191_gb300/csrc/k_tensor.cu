@@ -279,6 +279,192 @@ __global__ void __launch_bounds__(192, OCC)
   }
 }
 
+// ------------------------------------------------------------------ CTA-pair products
+// The same products on pairs of CTAs (clusters of 2, tcgen05 cta_group::2): a pair
+// computes a 256 x 256 output tile.  Each CTA loads its own 128 rows of A and its own
+// 128 of the tile's 256 rows of B, so that per byte fed from L2 each CTA does twice the
+// MMA work of a 128 x 128 tile.  The even-ranked CTA issues every MMA; both CTAs'
+// loads count on its "full" barriers; its commits arrive on the "empty" and
+// accumulator barriers of both CTAs.  Each CTA's TMEM holds its 128 rows x 256 columns
+// of the accumulator and each CTA runs the epilogue of its rows.
+constexpr int PBM = 256;
+
+// PBN: the pair tile's width (256 or 192 output columns; each CTA loads PBN / 2 rows of B).
+template <int NPROD, int PBN>
+struct PairCfg {
+  static constexpr uint32_t B_TILE = (uint32_t)(PBN / 2) * GBK * 2;
+  static constexpr uint32_t STAGE_BYTES = (NPROD == 3 ? 2 : 1) * TILE_BYTES + 2 * B_TILE;
+  static constexpr int STAGES = (200u * 1024u / STAGE_BYTES) < 5 ? (200u * 1024u / STAGE_BYTES) : 5;
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
+  static constexpr uint32_t TMEM_COLS = PBN <= 128 ? 128 : 256;  // a power of two
+  static_assert(STAGES >= 2, "a ring of at least two stages");
+  static_assert(B_TILE % 1024 == 0, "tiles start on 1024-byte (swizzle atom) boundaries");
+  static_assert(STAGES * STAGE_BYTES >= 128 * (PBN + 1) * 4, "the ring stages the output tile");
+};
+
+template <int NPROD, int PBN>
+__global__ void __launch_bounds__(192, 1)
+    k_gemm_pair(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+                const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
+                GemmArgs g) {
+  using Cfg = PairCfg<NPROD, PBN>;
+  constexpr int ST = Cfg::STAGES;
+  extern __shared__ __align__(16) unsigned char gsm_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[ST], empty[ST], accf;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = umma::cluster_ctarank();  // 0: issues the MMAs
+  const int m0 = blockIdx.y * PBM, n0 = (blockIdx.x >> 1) * PBN;
+  const int my_m = m0 + 128 * (int)rank;  // this CTA's rows of A and of the output
+  const int my_n = n0 + (PBN / 2) * (int)rank;  // this CTA's rows of B
+  const int kb_total = (g.K + GBK - 1) / GBK;
+  const int kb0 = blockIdx.z * g.kb_per_split;
+  const int nkb = min(kb_total, kb0 + g.kb_per_split) - kb0;
+  auto a_hi = [&](int s) { return base + (size_t)s * Cfg::STAGE_BYTES; };
+  auto a_lo = [&](int s) { return a_hi(s) + TILE_BYTES; };
+  auto b_hi = [&](int s) { return a_hi(s) + (NPROD == 3 ? 2 : 1) * TILE_BYTES; };
+  auto b_lo = [&](int s) { return b_hi(s) + Cfg::B_TILE; };
+
+  if (g.skip) {
+    // both CTAs decide on all 256 rows of the pair, so that they leave together
+    int live = 0;
+    for (int r = threadIdx.x; r < PBM; r += blockDim.x)
+      live |= (m0 + r < g.M && !g.skip[m0 + r]) ? 1 : 0;
+    if (!__syncthreads_or(live)) return;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      umma::mbar_init(&full[s], 1);
+      umma::mbar_init(&empty[s], 1);
+    }
+    umma::mbar_init(&accf, 1);
+    s_abort = 0;
+    umma::fence_mbar_init();
+  }
+  if (warp == 1) umma::tmem_alloc_pair(&tmem_base, Cfg::TMEM_COLS);
+  __syncthreads();
+  umma::tc_fence_before();
+  umma::cluster_sync_all();  // both CTAs' barriers and TMEM exist before any remote signal
+  umma::tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  int issued = 0;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer (both CTAs; completion counted on rank 0's barrier)
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % ST;
+      if (i >= ST && !umma::mbar_wait(&empty[s], ((i / ST) & 1) ^ 1, g.timeout_ns)) {
+        s_abort = 1;
+        break;
+      }
+      if (rank == 0) umma::mbar_arrive_expect_tx(&full[s], 2 * Cfg::STAGE_BYTES);
+      const uint32_t bar = umma::cluster_addr(&full[s], 0);
+      const int x = (kb0 + i) * GBK;
+      umma::tma_load_2d_pair(&tAh, bar, a_hi(s), x, my_m);
+      if (NPROD == 3) umma::tma_load_2d_pair(&tAl, bar, a_lo(s), x, my_m);
+      umma::tma_load_2d_pair(&tBh, bar, b_hi(s), x, my_n);
+      umma::tma_load_2d_pair(&tBl, bar, b_lo(s), x, my_n);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ---------------- MMA issuer (rank 0 only): M = 256 over the pair, N = PBN
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(PBN, PBM);
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % ST;
+      if (!umma::mbar_wait(&full[s], (i / ST) & 1, g.timeout_ns)) {
+        s_abort = 1;
+        break;
+      }
+      umma::tc_fence_after();
+      const uint64_t dah = umma::desc_sw128(umma::smem_u32(a_hi(s)));
+      const uint64_t dal = umma::desc_sw128(umma::smem_u32(a_lo(s)));
+      const uint64_t dbh = umma::desc_sw128(umma::smem_u32(b_hi(s)));
+      const uint64_t dbl = umma::desc_sw128(umma::smem_u32(b_lo(s)));
+#pragma unroll
+      for (int kk = 0; kk < GBK / 16; ++kk) {
+        const uint64_t o = (uint64_t)(kk * 32) >> 4;
+        umma::mma_bf16_pair(tmem, dah + o, dbh + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        umma::mma_bf16_pair(tmem, dah + o, dbl + o, idesc, 1u);
+        if (NPROD == 3) umma::mma_bf16_pair(tmem, dal + o, dbh + o, idesc, 1u);
+      }
+      umma::mma_commit_pair(&empty[s], (uint16_t)0x3);
+    }
+    umma::mma_commit_pair(&accf, (uint16_t)0x3);
+  } else if (warp >= 2) {
+    // ---------------- epilogue (both CTAs): warp w reads TMEM lanes 32*(w%4) .. +31
+    const bool ready = __all_sync(0xffffffffu, umma::mbar_wait(&accf, 0, g.timeout_ns));
+    umma::tc_fence_after();
+    const int q = warp & 3;
+    const int row = my_m + 32 * q + lane;
+    if (!ready) s_abort = 1;
+    if (ready && nkb > 0) {
+#pragma unroll 1
+      for (int cc = 0; cc < PBN / 32; ++cc) {
+        float v[32];
+        umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cc), v);
+        const int col0 = n0 + 32 * cc;
+        if (g.epi == EPI_TILE) {
+          float* tile = (float*)base;
+#pragma unroll
+          for (int u = 0; u < 32; ++u) tile[(32 * q + lane) * (PBN + 1) + 32 * cc + u] = v[u];
+        } else if (row < g.M) {
+          if (g.epi == EPI_PARTIAL) {
+            float* dst = g.P + ((size_t)blockIdx.z * g.M + row) * g.ldp + col0;
+            if (col0 + 32 <= g.N) {
+#pragma unroll
+              for (int u = 0; u < 8; ++u)
+                reinterpret_cast<float4*>(dst)[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 32; ++u)
+                if (col0 + u < g.N) dst[u] = v[u];
+            }
+          } else {
+            const double* f0 = g.f0 + (size_t)row * g.ldf + col0;
+            double* f = g.f + (size_t)row * g.ldf + col0;
+#pragma unroll
+            for (int u = 0; u < 32; ++u)
+              if (col0 + u < g.N) f[u] = (double)v[u] + f0[u];
+          }
+        }
+      }
+    }
+  }
+  umma::tc_fence_before();
+  __syncthreads();
+  if (g.epi == EPI_TILE && !s_abort && nkb > 0) {
+    const float* tile = (const float*)base;
+    for (int m = warp; m < 128; m += 6) {
+      const int r = my_m + m;
+      if (r >= g.M) break;
+      float* dst = g.F32 + (size_t)r * g.ldf32;
+#pragma unroll
+      for (int q = 0; q < PBN / 32; ++q) {
+        const int c = lane + 32 * q;
+        if (n0 + c < g.N) dst[n0 + c] = tile[m * (PBN + 1) + c];
+      }
+    }
+  }
+  if (threadIdx.x == 0 && s_abort) {
+    atomicExch(g.err, (int)DCOPF_ERR_TIMEOUT);
+    // rank 0's full barriers count both CTAs' copies: let those in flight land
+    if (rank == 0)
+      for (int i = max(0, issued - ST); i < issued; ++i)
+        umma::mbar_wait(&full[i % ST], (i / ST) & 1, g.timeout_ns);
+  }
+  __syncthreads();
+  // neither CTA releases its shared memory or TMEM while the pair's copies or MMAs may
+  // still reach it
+  umma::tc_fence_before();
+  umma::cluster_sync_all();
+  if (warp == 1) {
+    umma::tc_fence_after();
+    umma::tmem_dealloc_pair(tmem, Cfg::TMEM_COLS);
+  }
+}
+
 // One block per (chunk of STEP_CHUNK lines, instance): elementwise, full occupancy,
 // coalesced; per-chunk FP64 partials of the value and of u^T eta.
 constexpr int STEP_THREADS = 256, STEP_PER_THREAD = 4;
@@ -573,7 +759,11 @@ dcopf_status ensure_tensor_operands(dcopf_dual* h) {
   if (!make_map(&T.m_phi_hi, T.phi_hi.p, nl, ng, T.ld_g, GBN) ||
       !make_map(&T.m_phi_lo, T.phi_lo.p, nl, ng, T.ld_g, GBN) ||
       !make_map(&T.m_phit_hi, T.phit_hi.p, ng, nl, T.ld_l, GBN) ||
-      !make_map(&T.m_phit_lo, T.phit_lo.p, ng, nl, T.ld_l, GBN))
+      !make_map(&T.m_phit_lo, T.phit_lo.p, ng, nl, T.ld_l, GBN) ||
+      !make_map(&T.m_phi_hi96, T.phi_hi.p, nl, ng, T.ld_g, 96) ||
+      !make_map(&T.m_phi_lo96, T.phi_lo.p, nl, ng, T.ld_g, 96) ||
+      !make_map(&T.m_phit_hi96, T.phit_hi.p, ng, nl, T.ld_l, 96) ||
+      !make_map(&T.m_phit_lo96, T.phit_lo.p, ng, nl, T.ld_l, 96))
     return DCOPF_ERR_CUDA;
   if (prepare_gemm() != cudaSuccess) return DCOPF_ERR_CUDA;
   T.ready = true;
@@ -611,8 +801,40 @@ static cudaError_t prepare_gemm() {
   cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)GemmCfg<2, 2>::SMEM);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gemm_bf16x<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)GemmCfg<3>::SMEM);
+  e = cudaFuncSetAttribute(k_gemm_bf16x<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)GemmCfg<3>::SMEM);
+  if (e != cudaSuccess) return e;
+#define DCOPF_PAIR_SMEM(NP, BN)                                                                  \
+  if ((e = cudaFuncSetAttribute(k_gemm_pair<NP, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                (int)PairCfg<NP, BN>::SMEM)) != cudaSuccess)                        \
+    return e;
+  DCOPF_PAIR_SMEM(2, 256)
+  DCOPF_PAIR_SMEM(3, 256)
+  DCOPF_PAIR_SMEM(2, 192)
+  DCOPF_PAIR_SMEM(3, 192)
+#undef DCOPF_PAIR_SMEM
+  return cudaSuccess;
+}
+
+// The CTA-pair products: clusters of two CTAs, grid (2 x pair columns, pair rows, splits).
+template <int NPROD, int PBN>
+static cudaError_t launch_gemm_pair(dcopf_dual* h, const CUtensorMap& Ah, const CUtensorMap& Al,
+                                    const CUtensorMap& Bh, const CUtensorMap& Bl, GemmArgs g, int splits,
+                                    cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(2 * ((g.N + PBN - 1) / PBN), (g.M + PBM - 1) / PBM, splits);
+  cfg.blockDim = dim3(192);
+  cfg.dynamicSmemBytes = PairCfg<NPROD, PBN>::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  h->launches += 1;
+  return cudaLaunchKernelEx(&cfg, k_gemm_pair<NPROD, PBN>, Ah, Al, Bh, Bl, g);
 }
 
 template <int NPROD, int OCC = 1>
@@ -632,6 +854,28 @@ static cudaError_t launch_gemm(dcopf_dual* h, const CUtensorMap& Ah, const CUten
 static cudaError_t launch_forward_lp(dcopf_dual* h, const GemmArgs& g, cudaStream_t s) {
   TensorOps& T = h->tops;
   return launch_gemm<2, 2>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, g, 1, s);
+}
+
+// The adjoint Pi~ = H Phi~ (split-K partials) and the forward F = X Phi~^T, each on
+// single CTAs or on CTA pairs.
+// `tiles`: 0 single CTAs (128 x 128), 1 CTA pairs of 256 x 256, 2 CTA pairs of 256 x 192.
+static cudaError_t launch_adjoint(dcopf_dual* h, const GemmArgs& g, int splits, int tiles, cudaStream_t s) {
+  TensorOps& T = h->tops;
+  if (tiles == 1) return launch_gemm_pair<3, 256>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi, T.m_phit_lo, g, splits, s);
+  if (tiles == 2)
+    return launch_gemm_pair<3, 192>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi96, T.m_phit_lo96, g, splits, s);
+  return launch_gemm<3>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi, T.m_phit_lo, g, splits, s);
+}
+static cudaError_t launch_forward(dcopf_dual* h, const GemmArgs& g, int tiles, cudaStream_t s) {
+  TensorOps& T = h->tops;
+  if (h->host.qp) {
+    if (tiles == 1) return launch_gemm_pair<3, 256>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, g, 1, s);
+    if (tiles == 2) return launch_gemm_pair<3, 192>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi96, T.m_phi_lo96, g, 1, s);
+    return launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, g, 1, s);
+  }
+  if (tiles == 1) return launch_gemm_pair<2, 256>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, g, 1, s);
+  if (tiles == 2) return launch_gemm_pair<2, 192>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi96, T.m_phi_lo96, g, 1, s);
+  return launch_forward_lp(h, g, s);
 }
 
 // Split-K factor of the adjoint: enough CTAs to cover the SMs twice.
@@ -658,11 +902,17 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
   h->launches += 1;
   int splits, kbps;
   adjoint_split(h, B, &splits, &kbps);
+  int pair_adj = (h->tiles_mode >= 2 && B > GBM) ? h->tiles_mode - 1 : 0, pair_fwd = pair_adj;
+  if (h->tune_B == B && h->tune_splits > 0) {  // the shapes a solve of this batch size chose
+    splits = h->tune_splits;
+    kbps = h->tune_kbps;
+    pair_adj = h->tune_pair_adj;
+    pair_fwd = h->tune_pair_fwd;
+  }
   GemmArgs g{};
   g.M = B; g.N = ng; g.K = nl; g.kb_per_split = kbps; g.epi = EPI_PARTIAL;
   g.P = T.P.as<float>(); g.ldp = (ng + 3) & ~3; g.err = h->d_err; g.timeout_ns = 2000000000ull;
-  if (launch_gemm<3>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi, T.m_phit_lo, g, splits, s) != cudaSuccess)
-    return DCOPF_ERR_CUDA;
+  if (launch_adjoint(h, g, splits, pair_adj, s) != cudaSuccess) return DCOPF_ERR_CUDA;
   k_reduce_min<<<B, 256, 0, s>>>(h->dev, splits, B, g.ldp, T.P.as<float>(), lambda, T.ld_g,
                                  T.X_hi.as<__nv_bfloat16>(), T.X_lo.as<__nv_bfloat16>(),
                                  w.x64.as<double>(), w.sumcost.as<double>(), w.sump.as<double>());
@@ -671,10 +921,7 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
   f.M = B; f.N = nl; f.K = ng; f.kb_per_split = (ng + GBK - 1) / GBK; f.epi = EPI_FLOW;
   f.f0 = w.f0.as<double>(); f.f = w.f.as<double>(); f.ldf = nl; f.err = h->d_err;
   f.timeout_ns = 2000000000ull;
-  cudaError_t e = h->host.qp
-                      ? launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, f, 1, s)
-                      : launch_forward_lp(h, f, s);
-  if (e != cudaSuccess) return DCOPF_ERR_CUDA;
+  if (launch_forward(h, f, pair_fwd, s) != cudaSuccess) return DCOPF_ERR_CUDA;
   return run_eval_finish(h, B, outage, lambda, mh, ml, value, glam, ghi, glo, dispatch, s);
 }
 
@@ -948,6 +1195,7 @@ struct TensorRun {
   GemmArgs ga{}, gf{};
   StepEpi E{};
   int splits = 1, n_tiles = 0;
+  int pair_adj = 0, pair_fwd = 0;  // product shapes, as launch_adjoint's `tiles`
   unsigned gi = 1;
   bool running = true;
 };
@@ -967,63 +1215,110 @@ static void tensor_init_state(TensorRun& R, cudaStream_t cs) {
   h->launches += 3;
 }
 
-// Autotuner of the adjoint's split-K factor: more splits fill the SMs with CTAs but
-// add FP32 partial traffic to the minimiser's reduction.  Times the adjoint GEMM plus
-// the minimiser (the kernels the factor changes) for factors around the heuristic,
-// with CUDA events on the solve's stream, and keeps the fastest for this batch size.
-static dcopf_status tune_adjoint_split(TensorRun& R, cudaStream_t cs) {
+// Autotuner of the batched products' shapes, on the first solve of a batch size:
+//  - the adjoint: single CTAs (128 x 128 tiles) or CTA pairs (256 x 256), each with
+//    split-K factors around a heuristic and the factors that fill whole waves; more
+//    splits fill the SMs with CTAs but add FP32 partial traffic to the minimiser's
+//    reduction, so each candidate is timed as adjoint + minimiser;
+//  - the forward product: single CTAs or CTA pairs.
+// Timed with CUDA events on the solve's stream; the fastest of each is kept per handle.
+static dcopf_status tune_tensor_shapes(TensorRun& R, cudaStream_t cs) {
   dcopf_dual* h = R.it.h;
-  const int B = R.it.B;
+  const int B = R.it.B, ng = h->host.n_gen;
   TensorOps& T = h->tops;
   Workspace& w = h->ws;
   const int kb = (h->host.n_line + GBK - 1) / GBK;
-  const int s0 = R.splits;
-  std::vector<int> cand;
-  auto add = [&](int s) {
-    s = std::max(1, std::min(std::min(kb, 64), s));
-    const int per = (kb + s - 1) / s;
+  const bool pair_ok = B > GBM && h->tiles_mode != 1;
+  const bool single_ok = h->tiles_mode <= 1 || B <= GBM;
+  const int tv_lo = h->tiles_mode == 3 ? 2 : 1, tv_hi = h->tiles_mode == 2 ? 1 : 2;
+  struct Cand { int tiles; int splits; };  // tiles as launch_adjoint's
+  std::vector<Cand> cand;
+  auto add = [&](int tiles, int sp) {
+    sp = std::max(1, std::min(std::min(kb, 64), sp));
+    const int per = (kb + sp - 1) / sp;
     const int se = (kb + per - 1) / per;
-    if (std::find(cand.begin(), cand.end(), se) == cand.end()) cand.push_back(se);
+    for (const Cand& c : cand)
+      if (c.tiles == tiles && c.splits == se) return;
+    cand.push_back({tiles, se});
   };
-  for (int num : {1, 2, 3, 4, 6, 8}) add((s0 * num + 2) / 4);
-  // and the splits that fill whole waves (one CTA per SM): the last wave of a grid of
-  // tiles x splits CTAs is then full rather than a few CTAs on an idle GPU
-  const int tiles = ((B + GBM - 1) / GBM) * ((h->host.n_gen + GBN - 1) / GBN);
-  for (int wv = 1; wv <= 4; ++wv) add(wv * h->sm_count / tiles);
+  if (single_ok) {
+    const int s0 = R.splits;
+    for (int num : {1, 2, 3, 4, 6, 8}) add(0, (s0 * num + 2) / 4);
+    // and the splits that fill whole waves (one CTA per SM): the last wave of a grid of
+    // tiles x splits CTAs is then full rather than a few CTAs on an idle GPU
+    const int tiles = ((B + GBM - 1) / GBM) * ((ng + GBN - 1) / GBN);
+    for (int wv = 1; wv <= 4; ++wv) add(0, wv * h->sm_count / tiles);
+  }
+  if (pair_ok) {
+    for (int tv = tv_lo; tv <= tv_hi; ++tv) {
+      const int bn = tv == 1 ? 256 : 192;
+      const int ptiles = ((B + PBM - 1) / PBM) * ((ng + bn - 1) / bn);
+      const int slots = h->sm_count / 2;  // one pair per two SMs
+      const int s0 = std::max(1, (slots + ptiles - 1) / ptiles);
+      for (int num : {2, 3, 4, 6}) add(tv, (s0 * num + 2) / 4);
+      for (int wv = 1; wv <= 3; ++wv) add(tv, wv * slots / ptiles);
+    }
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
     return DCOPF_ERR_CUDA;
   }
-  float best = 1e30f;
-  int best_s = s0, best_per = (kb + s0 - 1) / s0;
-  dcopf_status out = DCOPF_OK;
-  for (int se : cand) {
-    GemmArgs g = R.ga;
-    g.kb_per_split = (kb + se - 1) / se;
-    float ms = 0.f;
-    for (int rep = 0; rep < 2 && out == DCOPF_OK; ++rep) {  // first pass warms up
-      if (cudaEventRecord(e0, cs) != cudaSuccess) { out = DCOPF_ERR_CUDA; break; }
-      for (int k = 0; k < 3; ++k) {
-        if (launch_gemm<3>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi, T.m_phit_lo, g, se, cs) != cudaSuccess) {
-          out = DCOPF_ERR_CUDA;
-          break;
-        }
-        k_bt_minimize<<<B, minimize_threads(h, B), 0, cs>>>(h->dev, se, B, g.ldp, T.P.as<float>(), R.st, h->bb.v, R.P,
-                                         T.ld_g, T.X_hi.as<__nv_bfloat16>(),
-                                         T.X_lo.as<__nv_bfloat16>(), R.it.outage,
-                                         w.demand.as<double>());
-        h->launches += 1;
-      }
-      if (out != DCOPF_OK || cudaEventRecord(e1, cs) != cudaSuccess ||
-          cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-        out = DCOPF_ERR_CUDA;
+  auto timed = [&](auto&& body, float* ms) -> dcopf_status {
+    for (int rep = 0; rep < 2; ++rep) {  // the first pass warms up
+      if (cudaEventRecord(e0, cs) != cudaSuccess) return DCOPF_ERR_CUDA;
+      for (int k = 0; k < 3; ++k)
+        if (body() != cudaSuccess) return DCOPF_ERR_CUDA;
+      if (cudaEventRecord(e1, cs) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+        return DCOPF_ERR_CUDA;
     }
+    return DCOPF_OK;
+  };
+  static const char* kTiles[3] = {"single 128x128", "pairs 256x256", "pairs 256x192"};
+  float best = 1e30f;
+  Cand bc = cand.empty() ? Cand{0, 1} : cand[0];
+  int best_per = (kb + bc.splits - 1) / bc.splits;
+  dcopf_status out = DCOPF_OK;
+  for (const Cand& c : cand) {
+    GemmArgs g = R.ga;
+    g.kb_per_split = (kb + c.splits - 1) / c.splits;
+    float ms = 0.f;
+    out = timed(
+        [&] {
+          cudaError_t e = launch_adjoint(h, g, c.splits, c.tiles, cs);
+          k_bt_minimize<<<B, minimize_threads(h, B), 0, cs>>>(h->dev, c.splits, B, g.ldp, T.P.as<float>(),
+                                                              R.st, h->bb.v, R.P, T.ld_g,
+                                                              T.X_hi.as<__nv_bfloat16>(),
+                                                              T.X_lo.as<__nv_bfloat16>(), R.it.outage,
+                                                              w.demand.as<double>());
+          h->launches += 1;
+          return e != cudaSuccess ? e : cudaGetLastError();
+        },
+        &ms);
     if (out != DCOPF_OK) break;
+    if (h->verbose)
+      fprintf(stderr, "dcopf: batch %d adjoint %s split-K %d: %.1f us per GEMM+min\n", B,
+              kTiles[c.tiles], c.splits, 1e3f * ms / 3.f);
     if (ms < best) {
       best = ms;
-      best_s = se;
+      bc = c;
       best_per = g.kb_per_split;
+    }
+  }
+  // the forward product, on the operands the runs above left
+  int fwd = (pair_ok && !single_ok) ? tv_lo : 0;
+  if (out == DCOPF_OK && pair_ok) {
+    float bf = 1e30f;
+    for (int tv = single_ok ? 0 : tv_lo; tv <= tv_hi && out == DCOPF_OK; ++tv) {
+      if (tv > 0 && tv < tv_lo) continue;
+      float ms = 0.f;
+      out = timed([&] { return launch_forward(h, R.gf, tv, cs); }, &ms);
+      if (h->verbose) fprintf(stderr, "dcopf: batch %d forward %s: %.1f us\n", B, kTiles[tv], 1e3f * ms / 3.f);
+      if (out == DCOPF_OK && ms < bf) {
+        bf = ms;
+        fwd = tv;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -1034,11 +1329,13 @@ static dcopf_status tune_adjoint_split(TensorRun& R, cudaStream_t cs) {
     return DCOPF_ERR_CUDA;
   if (derr) return (dcopf_status)derr;
   h->tune_B = B;
-  h->tune_splits = best_s;
+  h->tune_splits = bc.splits;
   h->tune_kbps = best_per;
+  h->tune_pair_adj = bc.tiles;
+  h->tune_pair_fwd = fwd;
   if (h->verbose)
-    fprintf(stderr, "dcopf: batch %d adjoint split-K %d (heuristic %d), %.1f us per GEMM+min\n", B,
-            best_s, s0, 1e3f * best / 3.f);
+    fprintf(stderr, "dcopf: batch %d adjoint %s split-K %d (%.1f us per GEMM+min), forward %s\n", B,
+            kTiles[bc.tiles], bc.splits, 1e3f * best / 3.f, kTiles[fwd]);
   return DCOPF_OK;
 }
 
@@ -1096,11 +1393,13 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   E.Hh = T.H_hi.as<__nv_bfloat16>(); E.Hl = T.H_lo.as<__nv_bfloat16>(); E.ldh = T.ld_l;
   E.line_part = bb.line_part; E.out_part = bb.out_part; E.n_tiles = R.n_tiles;
   if (h->tune_B != B) {
-    if ((r = tune_adjoint_split(R, cs))) return r;
+    if ((r = tune_tensor_shapes(R, cs))) return r;
     tensor_init_state(R, cs);  // the timed runs stepped lambda: start again
   }
   R.splits = h->tune_splits;
   R.ga.kb_per_split = h->tune_kbps;
+  R.pair_adj = h->tune_pair_adj;
+  R.pair_fwd = h->tune_pair_fwd;
   R.ga.skip = bb.frozen;
   R.gf.skip = bb.frozen;
   // the mean of the minimisers starts after the tuning runs
@@ -1117,14 +1416,11 @@ static bool tensor_enqueue_chunk(TensorRun& R, int chunk, cudaStream_t cs) {
   BatchView& bb = h->bb.v;
   bool ok = true;
   for (int it = 0; it < chunk && ok; ++it) {
-    ok &= launch_gemm<3>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi, T.m_phit_lo, R.ga, R.splits, cs) ==
-          cudaSuccess;
+    ok &= launch_adjoint(h, R.ga, R.splits, R.pair_adj, cs) == cudaSuccess;
     k_bt_minimize<<<B, minimize_threads(h, B), 0, cs>>>(h->dev, R.splits, B, R.ga.ldp, T.P.as<float>(), R.st, bb, R.P,
                                      T.ld_g, T.X_hi.as<__nv_bfloat16>(), T.X_lo.as<__nv_bfloat16>(),
                                      R.it.outage, w.demand.as<double>());
-    ok &= (h->host.qp ? launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, R.gf, 1, cs)
-                      : launch_forward_lp(h, R.gf, cs)) ==
-          cudaSuccess;
+    ok &= launch_forward(h, R.gf, R.pair_fwd, cs) == cudaSuccess;
     if (nl % 4 == 0 && R.E.ldF % 4 == 0 && R.E.ldh % 4 == 0)
       k_bt_step4<<<dim3(R.n_tiles, B), STEP_THREADS, 0, cs>>>(R.E, nl);
     else

@@ -144,7 +144,8 @@ struct TensorOps {
   int ld_l = 0, ld_g = 0;  // padded row strides (elements) of [*][n_line] and [*][n_gen]
   int cap = 0;             // batch capacity of the per-batch operands
   DBuf phi_hi, phi_lo, phit_hi, phit_lo;
-  CUtensorMap m_phi_hi, m_phi_lo, m_phit_hi, m_phit_lo;
+  CUtensorMap m_phi_hi, m_phi_lo, m_phit_hi, m_phit_lo;        // 128-row boxes
+  CUtensorMap m_phi_hi96, m_phi_lo96, m_phit_hi96, m_phit_lo96;  // 96-row boxes (pair tiles of 192)
   DBuf H_hi, H_lo, X_hi, X_lo, P;
   CUtensorMap m_H_hi, m_H_lo, m_X_hi, m_X_lo;
 };
@@ -237,8 +238,15 @@ struct dcopf_dual {
   unsigned long long fused_timeout_ns = 2000000000ull;
   unsigned fused_arrive_extra = 0;
   dcopf::DBuf probe;  // outputs of the fused self-test
-  // split-K of the batched adjoint GEMM chosen by timing (for batch size tune_B)
+  // split-K of the batched adjoint GEMM chosen by timing (for batch size tune_B), and
+  // whether the adjoint and the forward product run on CTA pairs (256 x 256 tiles)
+  // rather than single CTAs (128 x 128)
   int tune_B = 0, tune_splits = 0, tune_kbps = 0;
+  int tune_pair_adj = 0, tune_pair_fwd = 0;  // 0 single CTAs, 1 pairs of 256 columns, 2 of 192
+  // DCOPF_TENSOR_TILES (read at create): 0 = choose by timing, 1 = single CTAs only,
+  // 2 / 3 = CTA pairs of 256 x 256 / 256 x 192 tiles only (where the batch has more than
+  // 128 instances)
+  int tiles_mode = 0;
   size_t smem_optin = 0;
   bool verbose = false;
   std::string last_error;

@@ -59,7 +59,13 @@ def test_eval_matches_oracle(cases, name, precision, rtol):
     for b in range(B):
         val, gl, ghi, glo, p = dcopf.evaluate(on, loads[b], lam[b], mh[b], ml[b])
         v = r["value"][b].item()
-        assert abs(v - val) <= rtol * (abs(val) + abs(lam[b]) * loads[b].sum()), (v, val)
+        scale = abs(val) + abs(lam[b]) * loads[b].sum()
+        assert abs(v - val) <= rtol * scale, (v, val)
+        if precision == "fp64":
+            # FP64 also to 1e-9 of |g| itself (plus the last bits of the summed terms)
+            assert abs(v - val) <= 1e-9 * abs(val) + 1e-14 * scale, (v, val)
+        print(f"{name} {precision} b={b}: value err {abs(v - val) / abs(val):.2e} of |g|, "
+              f"{abs(v - val) / scale:.2e} of |g|+|lambda|D")
         fscale = 1.0 + np.max(np.abs(on.fmax))
         gtol = {"fp64": 1e-9, "fp32": 2e-4, "bf16x3": 1e-3}[precision] * fscale
         assert np.max(np.abs(r["g_mu_hi"][b].cpu().numpy() - ghi)) <= gtol
@@ -199,3 +205,78 @@ def test_eval_full_size_sampled(cfg, batch, precision, rtol):
             val = dcopf.dual_value_lagrangian(on, w.loads[b], lam[b], mh[b], ml[b])
         scale = abs(val) + abs(lam[b]) * w.loads[b].sum()
         assert abs(r["value"][b].item() - val) <= rtol * scale, (b, r["value"][b].item(), val)
+
+
+def _safe_point(rng, on, phi_abs, loads, tie_rel):
+    """A seeded dual point whose LP reduced costs all stay clear of zero by more than
+    tie_rel times the size of their terms (c_j S, lambda, sum_i |Phi_ij| |eta_i|): a
+    reduced-precision adjoint cannot flip a generator between its box ends there."""
+    while True:
+        lam, mh, ml = rand_point(rng, on.n_line, density=0.05)
+        if on.qp:
+            return lam, mh, ml
+        _, _, nu, _, _ = dcopf.dual_parts(on, loads, lam, mh, ml)
+        w = on.c * on.S + nu[on.gen_bus]
+        size = np.abs(on.c * on.S) + abs(lam) + phi_abs.T @ np.abs(mh - ml)
+        if np.all(np.abs(w) > tie_rel * size):
+            return lam, mh, ml
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_eval_4600bus_b300_elementwise(precision):
+    """300 instances of the 4600-bus LP batch (150 with a line outage): three 128-row
+    tiles of the tensor path with a ragged last one, the split-K factor a solve of this
+    batch size tuned.  Eight instances spread over the tiles are compared with the
+    oracle on the network rebuilt without the outaged line: the dual value, every
+    supergradient entry and every generator's dispatch."""
+    w = synth.workload(2, batch=300)
+    net = w.net
+    on = onet(net)
+    g = DcopfDual(net)
+    if precision == "bf16x3":   # tunes the adjoint's split-K factor for B = 300
+        g.solve(w.loads, outage=w.outage, path="batched", precision="bf16x3", max_iters=20)
+    sample = [0, 1, 127, 128, 200, 255, 256, 299]
+    rng = np.random.default_rng(300)
+    nets = {b: (on if w.outage[b] < 0 else drop_line(net, int(w.outage[b]))) for b in sample}
+    pts = [rand_point(rng, net.n_line, density=0.05) for _ in range(w.batch)]
+    tie_rel = 1e-6 if precision == "fp32" else 1e-4
+    for b in sample:
+        o = nets[b]
+        mask = np.arange(net.n_line) != w.outage[b] if w.outage[b] >= 0 else slice(None)
+        phi_abs = np.abs(o.ptdf_gen())
+        lam, mh, ml = _safe_point(rng, o, phi_abs, w.loads[b], tie_rel)
+        full_h, full_l = np.zeros(net.n_line), np.zeros(net.n_line)
+        full_h[mask], full_l[mask] = mh, ml
+        pts[b] = (lam, full_h, full_l)
+    lam = np.array([p[0] for p in pts])
+    mh = np.stack([p[1] for p in pts])
+    ml = np.stack([p[2] for p in pts])
+    r = g.eval(w.loads, lam, mh, ml, outage=w.outage, precision=precision)
+    torch.cuda.synchronize()
+    rtol = 1e-5
+    gtol = {"fp32": 2e-4, "bf16x3": 1e-3}[precision] * (1.0 + np.max(np.abs(net.flow_max)))
+    worst_g = worst_s = worst_grad = worst_p = 0.0
+    for b in sample:
+        k = int(w.outage[b])
+        keep = np.arange(net.n_line) != k
+        mhb, mlb = (mh[b][keep], ml[b][keep]) if k >= 0 else (mh[b], ml[b])
+        val, gl, ghi, glo, p = dcopf.evaluate(nets[b], w.loads[b], lam[b], mhb, mlb)
+        v = r["value"][b].item()
+        scale = abs(val) + abs(lam[b]) * w.loads[b].sum()
+        worst_g = max(worst_g, abs(v - val) / abs(val))
+        worst_s = max(worst_s, abs(v - val) / scale)
+        assert abs(v - val) <= rtol * scale, (b, v, val)
+        gh = r["g_mu_hi"][b].cpu().numpy()
+        go = r["g_mu_lo"][b].cpu().numpy()
+        if k >= 0:
+            assert gh[k] == 0.0 and go[k] == 0.0
+            gh, go = gh[keep], go[keep]
+        e = max(np.max(np.abs(gh - ghi)), np.max(np.abs(go - glo)))
+        worst_grad = max(worst_grad, e)
+        assert e <= gtol, (b, e)
+        assert abs(r["g_lambda"][b].item() - gl) <= 1e-4 * (1 + w.loads[b].sum())
+        ep = np.max(np.abs(r["dispatch"][b].cpu().numpy() - p))
+        worst_p = max(worst_p, ep)
+        assert ep <= 1e-9 * (1 + np.max(net.pmax)), (b, ep)   # LP: box ends, exact
+    print(f"4600-bus B=300 {precision}: value err {worst_g:.2e} of |g|, {worst_s:.2e} of "
+          f"|g|+|lambda|D; gradient {worst_grad:.2e} p.u.; dispatch {worst_p:.1e}")
