@@ -1,14 +1,24 @@
 """Benchmark: DCOPF instances reaching a certified 0.1 % dual gap per second.
 
-Workload: the synthetic 2000-bus network (3200 lines, 540 generators, quadratic
-costs; single instance at its base loads, stand-in for the paper's 2000-bus case).
-One step = one complete solve through the library: base flows, projected Adam
-ascent in the fused persistent kernel (FP32 operator products, FP64 value), FP64
-certification, until the certified bound is within 0.1 % of gamma* (the oracle's
-stored optimum, tests/golden/gamma.json).  The plain FP64 GPU path (Algorithm 1
-heavy-ball GDM, one launch per phase, cold start) is timed on the same instance.
+Headline workload: the synthetic 10000-bus network (12700 lines, 2500 generators,
+quadratic costs) with a batch of 256 load scenarios, the stand-in for the paper's
+10000-bus case (Tables III and IX).  One step = one batched solve of all 256 instances
+through the library: base flows, projected Adam ascent with BF16 hi/lo split products
+on the tensor cores (CTA-pair tiles chosen by the autotuner) and FP32 state, FP64 dual
+values and certificates, until every instance's certified bound is within 0.1 % of
+gamma* (the oracle's stored optima, tests/golden/c3_gamma.json).  The metric's
+comparison, the plain FP64 GPU path (Algorithm 1 heavy-ball GDM, one launch per phase,
+one instance at a time, cold start), runs on a stated subset of the same instances,
+beside the same Adam rule on the same plain path.
+
+Extra legs (each in the JSON line): the 2000-bus instance on the fused persistent
+kernel (its latency floor measured by the exchange probe); the 4600-bus LP batch of
+1024 with 512 line outages; the learned warm start (trained on 50 000 scenarios) on
+4096 held-out 2000-bus scenarios; the mixed-size group (1024 x 300-bus, 256 x 2000-bus,
+128 x 4600-bus).  All inputs are seeded synthetic stand-ins (paper_2406_13191_gb300/synth.py).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       python bench.py --optimizer-study | --figure-sweeps | --warm-start-eval
 """
 from __future__ import annotations
 
@@ -16,6 +26,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -31,19 +42,35 @@ sys.path.insert(0, ROOT)
 METRIC = "DCOPF instances to 0.1% dual gap/sec on 1 GB300 vs plain FP64 GPU path"
 UNIT = "instances/s"
 GAP = 1e-3
+BATCH = 256
+# ascent settings of the headline (Adam, Section 3.3) and of the comparison arms
 OURS = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=4000,
-            path="fused", precision="fp32")
-PLAIN = dict(rule="gdm", alpha=30.0, alpha_lambda=0.1, rho=0.995, max_iters=20000, path="plain",
-             precision="fp64", check_every=20)
-WORKLOAD = ("synthetic 2000-bus DCOPF, 3200 lines, 540 generators, quadratic costs, single "
-            "instance at base loads")
-# DRAM bytes per launch of the dominant kernel from ncu, valid only for the kernel
-# source with this digest (see profiles/); null when the kernel has changed since.
-NCU_TRAFFIC = {"5ae9ce319ee08a90": 7124480 + 5376}   # profiles/fused_2000bus.md
+            path="batched", precision="bf16x3")
+# Algorithm 1 (heavy-ball GDM) on the plain FP64 path, with the settings of the GDM sweep
+# on the first 64 instances of this batch (bench.py --figure-sweeps, profiles/optimizer_study.md)
+PLAIN_GDM = dict(rule="gdm", alpha=10.0, alpha_lambda=0.3, rho=0.98, decay=1.0, max_iters=8000,
+                 path="plain", precision="fp64", check_every=8)
+PLAIN_ADAM = dict(OURS, path="plain", precision="fp64", check_every=4)
+PLAIN_SUBSET = 4          # instances of the batch the plain arms solve, one at a time
+WORKLOAD = ("synthetic 10000-bus DCOPF, 12700 lines, 2500 generators, quadratic costs, batch of "
+            "256 load scenarios (per-bus multipliers U[0.85, 1.15])")
+FUSED = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=4000,
+             path="fused", precision="fp32")
+C2 = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99, max_iters=4000,
+          path="batched", precision="bf16x3")
+QP_ADAM = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997)
+LP_ADAM = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99)
+# DRAM bytes per launch of the dominant kernel from an ncu capture, valid only for the
+# kernel source with this digest (profiles/); null once the kernel has changed.
+NCU_TRAFFIC = {}
+
+
+def golden(name):
+    return json.load(open(os.path.join(ROOT, "tests", "golden", name)))
 
 
 def kernel_digest() -> str:
-    p = os.path.join(ROOT, "paper_2406_13191_gb300", "csrc", "k_fused.cu")
+    p = os.path.join(ROOT, "paper_2406_13191_gb300", "csrc", "k_tensor.cu")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
@@ -51,20 +78,25 @@ def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
     except OSError:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def gamma_star():
-    g = json.load(open(os.path.join(ROOT, "tests", "golden", "gamma.json")))
-    return g["1/0"]["gamma"]
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
 
 
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi (every 100 ms) from before
     the warm-up until after the timed steps.  ``wait_ready`` returns once the first
-    sample is in (the tool takes a while to start), ``start``/``stop`` mark the timed
-    window; the summary takes the samples inside the window, and when the window is
-    shorter than the sampling period, the last sample before it and the first after."""
+    sample is in, ``start``/``stop`` mark the timed window; the summary takes the samples
+    inside the window, and when the window is shorter than the sampling period, the
+    last sample before it and the first after."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -105,7 +137,6 @@ class Clocks:
 
     def stop(self):
         self.t1 = time.perf_counter()
-        # one more sample after the window
         t = self.t1 + 1.0
         while self.proc is not None and time.perf_counter() < t and \
                 not any(ts > self.t1 for ts, _ in self.lines):
@@ -163,34 +194,35 @@ def dist_setup(n_gpus):
     return world, rank, local, pg
 
 
-def aggregate(total_ms: float, steps: int, world: int, dist, device=None):
-    """Whole-job throughput: every rank solved ``steps`` instances; the job took the
+def aggregate(total_ms: float, units: int, world: int, dist, device=None):
+    """Whole-job throughput: every rank processed ``units`` instances; the job took the
     slowest rank's time (max over ranks).  Returns (value per second, max total ms)."""
     if dist is not None:
         import torch
         t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = t.item()
-    return world * steps / (total_ms / 1e3), total_ms
+    return world * units / (total_ms / 1e3), total_ms
 
 
+# ------------------------------------------------------------------ the oracle on the host
 _ORACLE = None
 
 
 def _oracle_init():
-    """Pool initialiser: the oracle's network and the benchmark instance, once per process."""
+    """Pool initialiser: the oracle's 10000-bus network, the batch and its optima."""
     global _ORACLE
     from oracle import dcopf
     from paper_2406_13191_gb300 import synth
-    net, base = synth.network_for(1)
+    w = synth.workload(3, batch=BATCH)
     kw = {k: OURS[k] for k in ("rule", "alpha", "beta1", "beta2", "decay", "max_iters")}
-    _ORACLE = (dcopf.Net.from_dict(net.as_dict()), base, gamma_star(), kw)
+    _ORACLE = (dcopf.Net.from_dict(w.net.as_dict()), w.loads, golden("c3_gamma.json")["gamma"], kw)
 
 
-def _oracle_solve(_):
+def _oracle_solve(i):
     from oracle import dcopf
-    on, base, gam, kw = _ORACLE
-    return dcopf.solve(on, base, target=gam, gap=GAP, **kw)["iters"]
+    on, loads, gam, kw = _ORACLE
+    return dcopf.solve(on, loads[i % BATCH], target=gam[i % BATCH], gap=GAP, **kw)["iters"]
 
 
 def oracle_pool(procs: int):
@@ -210,38 +242,35 @@ def oracle_pool(procs: int):
                 os.environ[k] = v
 
 
-def cpu_baseline(target_s=10.0):
-    """The oracle (plain FP64 numpy/scipy) solving the benchmark instance with the same
-    ascent rule until its FP64 value is within 0.1 % of gamma*, on every host core (one
-    process per core, one BLAS thread each), in rounds of one solve per process."""
+def oracle_rounds(pool, procs, rounds=None, target_s=None, first=0):
+    """Rounds of one complete oracle solve per process (instances first, first + 1, ...
+    of the batch).  Returns (solves, seconds, iterations)."""
+    n, iters, r = 0, [], 0
+    t0 = time.perf_counter()
+    while True:
+        iters += pool.map(_oracle_solve, range(first + n, first + n + procs))
+        n += procs
+        r += 1
+        el = time.perf_counter() - t0
+        if (rounds is not None and r >= rounds) or (target_s is not None and el >= target_s):
+            return n, el, iters
+
+
+def cpu_baseline(target_s=15.0):
+    """The oracle (plain FP64 numpy/scipy) solving instances of the headline batch with
+    the headline's ascent rule until its FP64 value is within 0.1 % of gamma*, on every
+    host core (one process per core, one BLAS thread each)."""
     procs = os.cpu_count() or 1
     with oracle_pool(procs) as pool:
-        pool.map(_oracle_solve, range(procs))  # warm-up: imports, factorisation
-        n, iters = 0, []
-        t0 = time.perf_counter()
-        while True:
-            iters += pool.map(_oracle_solve, range(procs))
-            n += procs
-            el = time.perf_counter() - t0
-            if el >= target_s:
-                break
-    out = {"value": n / el, "unit": UNIT, "cores": procs, "kind": "oracle",
-           "sample": f"{n} complete solves of the 2000-bus instance ({el:.1f} s, "
-                     f"{statistics.mean(iters):.0f} iterations each, {procs} processes with one "
-                     f"BLAS thread each)"}
-    # latency mode: one solve at a time in one process with the default BLAS threads
-    _oracle_init()
-    _oracle_solve(0)
-    m, t0 = 0, time.perf_counter()
-    while m < 3 or time.perf_counter() - t0 < target_s / 4:
-        _oracle_solve(0)
-        m += 1
-    el = time.perf_counter() - t0
-    out["latency_mode"] = {"value": m / el, "unit": UNIT, "ms_per_solve": 1e3 * el / m,
-                           "sample": f"{m} solves one after another in one process"}
-    return out
+        pool.map(_oracle_solve, range(procs))          # warm-up: imports, factorisation
+        n, el, iters = oracle_rounds(pool, procs, target_s=target_s, first=procs)
+    return {"value": n / el, "unit": UNIT, "cores": procs, "cpu": cpu_model(), "kind": "oracle",
+            "sample": f"{n} complete solves of instances of the 10000-bus batch ({el:.1f} s, "
+                      f"{statistics.mean(iters):.0f} iterations each, {procs} processes with one "
+                      f"BLAS thread each)"}
 
 
+# ------------------------------------------------------------------ studies (own JSON)
 def warm_start_eval(n_train: int, epochs: int, n_eval: int, keep_model: bool = False):
     """Learned warm start on the 2000-bus network: targets from the method's own batched
     solves of ``n_train`` training scenarios, GPU training, then cold vs warm solves of
@@ -251,8 +280,7 @@ def warm_start_eval(n_train: int, epochs: int, n_eval: int, keep_model: bool = F
     from paper_2406_13191_gb300 import DcopfDual, synth, warmstart
     net, _ = synth.network_for(1)
     g = DcopfDual(net)
-    gold = os.path.join(ROOT, "tests", "golden", "warm_gamma.json")
-    gam = np.array(json.load(open(gold))["gamma"][:n_eval], dtype=float)
+    gam = np.array(golden("warm_gamma.json")["gamma"][:n_eval], dtype=float)
     tk = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=1500,
               tol=0.0, path="batched", precision="bf16x3")
     out = {"mode": "warm_start_eval", "network": "synthetic 2000-bus QP", "n_train": n_train,
@@ -310,6 +338,30 @@ def warm_start_eval(n_train: int, epochs: int, n_eval: int, keep_model: bool = F
     return (out, m) if keep_model else out
 
 
+def _sweep(g, L, O, T, grid, max_iters):
+    """One batched solve per setting; mean iterations to the certified gap (instances
+    that do not reach it count as max_iters), the share that reached it, validity."""
+    import numpy as np
+    rows = []
+    g.solve(L, outage=O, target=T, path="batched", precision="bf16x3", max_iters=64, **grid[0])
+    Tn = T.cpu().numpy() if hasattr(T, "cpu") else np.asarray(T)
+    for kw in grid:
+        t = time.perf_counter()
+        r = g.solve(L, outage=O, target=T, path="batched", precision="bf16x3", max_iters=max_iters, **kw)
+        el = time.perf_counter() - t
+        st = r.status.cpu().numpy()
+        it = np.where(st == 0, r.iters.cpu().numpy(), max_iters)
+        b = r.bound.cpu().numpy()
+        rows.append(dict(kw, mean_iters=float(it.mean()), p90_iters=float(np.percentile(it, 90)),
+                         reached=float((st == 0).mean()), seconds=el,
+                         bounds_valid=bool(np.all(b <= Tn + 1e-9 * np.abs(Tn)))))
+    return rows
+
+
+def _best(rows):
+    return min(rows, key=lambda x: (-x["reached"], x["mean_iters"]))
+
+
 def optimizer_study(max_iters: int = 3000) -> dict:
     """Ascent rules of Section 3.3 on the study instances (512 training scenarios of the
     2000-bus QP network; 256 instances of the 4600-bus LP batch, half with an outage):
@@ -318,7 +370,7 @@ def optimizer_study(max_iters: int = 3000) -> dict:
     and without step decay.  One batched solve per setting (tensor-core path)."""
     import numpy as np
     from paper_2406_13191_gb300 import DcopfDual, synth
-    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "study_gamma.json")))
+    gold = golden("study_gamma.json")
     n1, _ = synth.network_for(1)
     w2 = synth.workload(2, batch=256)
     sets = {"2000-bus QP": (n1, synth.warm_loads("train", 512), None, gold["2000"], 4000.0),
@@ -343,45 +395,249 @@ def optimizer_study(max_iters: int = 3000) -> dict:
             for al in (0.1, 1.0):
                 for rho in (0.9, 0.99, 0.995):
                     grid.append(dict(rule="gdm", alpha=a, alpha_lambda=al, rho=rho, decay=1.0))
-        rows = []
-        g.solve(L, outage=O, target=T, path="batched", precision="bf16x3", max_iters=64, **grid[0])
-        for kw in grid:
-            t = time.perf_counter()
-            r = g.solve(L, outage=O, target=T, path="batched", precision="bf16x3",
-                        max_iters=max_iters, **kw)
-            el = time.perf_counter() - t
-            st = r.status.cpu().numpy()
-            it = np.where(st == 0, r.iters.cpu().numpy(), max_iters)
-            b = r.bound.cpu().numpy()
-            rows.append(dict(kw, mean_iters=float(it.mean()), p90_iters=float(np.percentile(it, 90)),
-                             reached=float((st == 0).mean()), seconds=el,
-                             bounds_valid=bool(np.all(b <= T + 1e-9 * np.abs(T)))))
-        best = {}
-        for rule in ("adam", "adagrad", "gdm"):
-            rr = [x for x in rows if x["rule"] == rule]
-            best[rule] = min(rr, key=lambda x: (-x["reached"], x["mean_iters"]))
+        rows = _sweep(g, L, O, T, grid, max_iters)
+        best = {rule: _best([x for x in rows if x["rule"] == rule]) for rule in ("adam", "adagrad", "gdm")}
         bg = best["gdm"]
         kw = {k: bg[k] for k in ("alpha", "alpha_lambda", "rho", "decay")}
-        r = g.solve(L, outage=O, target=T, path="batched", precision="bf16x3", max_iters=max_iters,
-                    rule="gdm", as_printed=True, **kw)
-        st = r.status.cpu().numpy()
-        it = np.where(st == 0, r.iters.cpu().numpy(), max_iters)
-        best["gdm_as_printed"] = dict(rule="gdm", as_printed=True, **kw, mean_iters=float(it.mean()),
-                                      reached=float((st == 0).mean()))
+        pr = _sweep(g, L, O, T, [dict(rule="gdm", as_printed=True, **kw)], max_iters)[0]
+        best["gdm_as_printed"] = pr
         out["sets"][name] = {"instances": int(ok.sum()), "best": best, "all": rows}
     return out
+
+
+def figure_sweeps(n_inst: int = 64, max_iters: int = 6000) -> dict:
+    """The paper's Fig. 3 (GDM momentum) and Fig. 4 (Adam alpha, beta1, beta2 on the
+    10000-bus QP) on the 10000-bus stand-in: iterations to the certified 0.1 % gap of the
+    first ``n_inst`` instances of the headline batch, one batched solve per setting.
+    The paper fixes alpha = 0.15 for Fig. 3 in its own cost units; here the fixed step is
+    the best of a coarse (alpha, alpha_lambda) grid at rho = 0.9, and rho is swept there.
+    Fig. 4 varies one Adam parameter at a time around the headline setting."""
+    import torch
+    from paper_2406_13191_gb300 import DcopfDual, synth
+    w = synth.workload(3, batch=n_inst)
+    gam = golden("c3_gamma.json")["gamma"][:n_inst]
+    g = DcopfDual(w.net)
+    L = torch.tensor(w.loads, dtype=torch.float64, device="cuda")
+    T = torch.tensor(gam, dtype=torch.float64, device="cuda")
+    out = {"mode": "figure_sweeps", "network": "10000-bus QP", "instances": n_inst,
+           "max_iters": max_iters, "gap": GAP}
+    coarse = [dict(rule="gdm", alpha=a, alpha_lambda=al, rho=0.9, decay=1.0)
+              for a in (3.0, 10.0, 30.0, 100.0) for al in (0.1, 0.3, 1.0)]
+    rows = _sweep(g, L, None, T, coarse, max_iters)
+    b = _best(rows)
+    out["gdm_coarse"] = rows
+    fig3 = [dict(rule="gdm", alpha=b["alpha"], alpha_lambda=b["alpha_lambda"], rho=r, decay=1.0)
+            for r in (0.0, 0.5, 0.8, 0.9, 0.95, 0.98, 0.99, 0.995)]
+    out["fig3_gdm_rho"] = _sweep(g, L, None, T, fig3, max_iters)
+    bb = _best(out["fig3_gdm_rho"])
+    dec = [dict(rule="gdm", alpha=bb["alpha"], alpha_lambda=bb["alpha_lambda"], rho=bb["rho"], decay=d)
+           for d in (0.9995, 0.999, 0.997)]
+    out["gdm_decay"] = _sweep(g, L, None, T, dec, max_iters)
+    out["gdm_best"] = _best(out["fig3_gdm_rho"] + out["gdm_decay"] + rows)
+    base = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997)
+    fig4 = [dict(base, alpha=a) for a in (1000.0, 2000.0, 4000.0, 8000.0, 16000.0)]
+    fig4 += [dict(base, beta1=v) for v in (0.5, 0.8, 0.9, 0.98)]
+    fig4 += [dict(base, beta2=v) for v in (0.9, 0.99, 0.9999)]
+    out["fig4_adam"] = _sweep(g, L, None, T, fig4, max_iters)
+    joint = [dict(rule="adam", alpha=a, beta1=b1, beta2=b2, decay=d)
+             for a in (1500.0, 2000.0, 3000.0) for b1 in (0.95, 0.98) for b2 in (0.999, 0.9999)
+             for d in (0.997, 0.999)]
+    out["adam_joint"] = _sweep(g, L, None, T, joint, max_iters)
+    out["adam_best"] = _best(out["fig4_adam"] + out["adam_joint"])
+    return out
+
+
+# ------------------------------------------------------------------ bench legs
+def timed_solves(g, args, kw, steps, flush, stream, out=None):
+    """CUDA-event times (ms) of ``steps`` solves, L2 flushed (256 MiB write) before each."""
+    import torch
+    times, res = [], None
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = g.solve(*args, out=out, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times, res
+
+
+def fused_leg(dev, flush, stream, steps, warmup):
+    """The 2000-bus instance at its base loads on the fused persistent kernel, with the
+    latency floor of one loop of its exchange (dcopf_probe_exchange at its shape)."""
+    import ctypes as C
+    import torch
+    from paper_2406_13191_gb300 import DcopfDual, _lib, synth
+    net, base = synth.network_for(1)
+    gam = golden("gamma.json")["1/0"]["gamma"]
+    g = DcopfDual(net, device=dev.index)
+    loads = torch.tensor(base[None], dtype=torch.float64, device=dev)
+    target = torch.tensor([gam], dtype=torch.float64, device=dev)
+    res = g.new_result(1)
+    for _ in range(warmup + 1):
+        g.solve(loads, target=target, gap=GAP, out=res, **FUSED)
+    g.set_timing(True)
+    g.read_timing()
+    times, r = timed_solves(g, (loads,), dict(target=target, gap=GAP, **FUSED), steps, flush, stream, res)
+    it_ms, it_launches, evals = g.read_timing()
+    g.set_timing(False)
+    us_iter = 1e3 * it_ms / max(1, evals)
+    floor = C.c_double()
+    lib = _lib.load()
+    # the exchange of the shape the fused tuner keeps on this network: 36 clusters of 4
+    code = lib.dcopf_probe_exchange(4, 144, net.n_gen, 2000, C.byref(floor))
+    out = {"workload": "synthetic 2000-bus QP, one instance at base loads, fused persistent "
+                       "cluster kernel (FP32 operator products, FP64 value and certificate)",
+           "value": len(times) / (sum(times) / 1e3), "unit": UNIT, "ms_per_solve": statistics.mean(times),
+           "iterations": r.iters[0].item(), "us_per_iteration": us_iter,
+           "certified_gap": (gam - r.bound[0].item()) / gam}
+    if code == 0:
+        out["roofline"] = {"bound": "latency", "achieved_us_per_iteration": us_iter,
+                           "floor_us_per_iteration": floor.value,
+                           "frac": floor.value / us_iter,
+                           "floor": "one loop of the same exchange without arithmetic at 36 x 4 CTAs "
+                                    "(dcopf_probe_exchange), measured in this run"}
+    return out
+
+
+def c2_leg(dev, flush, stream, steps):
+    """The 4600-bus LP batch of 1024 instances (512 with a line outage) to the gap."""
+    import numpy as np
+    import torch
+    from paper_2406_13191_gb300 import DcopfDual, synth
+    w = synth.workload(2, batch=1024)
+    gl = golden("c2_gamma.json")["gamma"]
+    ok = np.array([x is not None for x in gl])   # instances whose optimum the oracle certified
+    gam = np.array([x for x in gl if x is not None], dtype=float)
+    B = int(ok.sum())
+    g = DcopfDual(w.net, device=dev.index)
+    L = torch.tensor(w.loads[ok], dtype=torch.float64, device=dev)
+    O = torch.tensor(w.outage[ok], dtype=torch.int32, device=dev)
+    T = torch.tensor(gam, dtype=torch.float64, device=dev)
+    res = g.new_result(B)
+    g.solve(L, outage=O, target=T, gap=GAP, out=res, **C2)
+    g.set_timing(True)
+    g.read_timing()
+    times, r = timed_solves(g, (L,), dict(outage=O, target=T, gap=GAP, **C2), steps, flush, stream, res)
+    it_ms, _, evals = g.read_timing()
+    kt, ns = g.read_kernel_timing()
+    g.set_timing(False)
+    st = r.status.cpu().numpy()
+    b = r.bound.cpu().numpy()
+    iters = r.iters.cpu().numpy()
+    reached = int((st == 0).sum())
+    return {"workload": "synthetic 4600-bus LP, 7200 lines, 410 generators, batch of 1024 with 512 "
+                        "line outages, tensor-core BF16x3 path, certified 0.1 % gap vs gamma*",
+            "instances": B, "outages": int((w.outage[ok] >= 0).sum()),
+            "excluded": "instances whose oracle sandwich did not close (no stored optimum)",
+            "value": reached * len(times) / (sum(times) / 1e3), "unit": UNIT,
+            "counted": "instances that reached the gap within max_iters",
+            "ms_per_solve": statistics.mean(times), "mean_iters": float(iters.mean()),
+            "p90_iters": float(np.percentile(iters, 90)), "most_iters": int(iters.max()),
+            "reached_gap": reached,
+            "all_bounds_valid": bool(np.all(b <= gam + 1e-9 * np.abs(gam))),
+            "us_per_batched_iteration": 1e3 * it_ms / max(1, evals) * B,
+            "kernel_us": {k: 1e3 * v / max(1, ns) for k, v in kt.items()}}
+
+
+def group_leg(dev, steps):
+    """The mixed-size group: 1024 instances of a 300-bus network, 256 of the 2000-bus one
+    and 128 of the 4600-bus one (64 with an outage), one CUDA-graph launch per round over
+    all three, to the certified gap against their optima."""
+    import numpy as np
+    import torch
+    from paper_2406_13191_gb300 import DcopfDual, solve_group, synth
+    gg = golden("group_gamma.json")
+    n300, b300 = synth.network_for(300)
+    w1 = synth.workload(1, batch=256)
+    w2 = synth.workload(2, batch=128)
+    items = [(n300, synth.scenario_loads(b300, 1024, 4301), None, QP_ADAM, gg["300"]),
+             (w1.net, w1.loads, None, QP_ADAM, gg["2000"]),
+             (w2.net, w2.loads, w2.outage, LP_ADAM, golden("c2_gamma.json")["gamma"][:128])]
+    duals = [DcopfDual(n, device=dev.index) for n, *_ in items]
+    tg = [np.array(t, dtype=float) for *_, t in items]
+    kw = dict(max_iters=4000, precision="bf16x3", path="batched", check_every=16)
+
+    def run():
+        return solve_group(duals, [L for _, L, *_ in items], outage=[o for _, _, o, *_ in items],
+                           target=tg, per_network=[k for *_, k, _ in items], **kw)
+    run()
+    ts = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = run()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    n = sum(len(t) for t in tg)
+    ok = all(bool(((r.status.cpu().numpy() == 0)).all()) for r in res)
+    valid = all(bool(np.all(r.bound.cpu().numpy() <= t + 1e-9 * np.abs(t))) for r, t in zip(res, tg))
+    return {"workload": "1024 x 300-bus QP + 256 x 2000-bus QP + 128 x 4600-bus LP (64 outages), "
+                        "one group solve, certified 0.1 % gap vs gamma*",
+            "value": n * len(ts) / sum(ts), "unit": UNIT, "ms_per_solve": 1e3 * statistics.mean(ts),
+            "timing": "host wall clock around the call (it synchronises)",
+            "all_reached_gap": ok, "all_bounds_valid": valid,
+            "mean_iters": [float(r.iters.float().mean().item()) for r in res]}
+
+
+def plain_arm(g, w, gam, kw, dev, flush, stream):
+    """The plain FP64 path on the first PLAIN_SUBSET instances, one solve per instance."""
+    import torch
+    times, iters, st = [], [], []
+    res = g.new_result(1)
+    L = torch.tensor(w.loads[:PLAIN_SUBSET], dtype=torch.float64, device=dev)
+    T = torch.tensor(gam[:PLAIN_SUBSET], dtype=torch.float64, device=dev)
+    g.solve(L[:1], target=T[:1], gap=GAP, out=res, **kw)            # warm-up
+    for i in range(PLAIN_SUBSET):
+        t, r = timed_solves(g, (L[i:i + 1],), dict(target=T[i:i + 1], gap=GAP, **kw), 1, flush,
+                            stream, res)
+        times += t
+        iters.append(r.iters[0].item())
+        st.append(r.status[0].item())
+    return {"value": len(times) / (sum(times) / 1e3), "unit": UNIT,
+            "ms_per_solve": statistics.mean(times), "iterations": statistics.mean(iters),
+            "reached_gap": sum(s == 0 for s in st), "instances": PLAIN_SUBSET,
+            "rule": kw["rule"], "settings": {k: v for k, v in kw.items() if k not in ("path", "precision")},
+            "precision": "fp64", "launch": "one per phase, one instance at a time"}
+
+
+def reference_arm(a):
+    """The oracle as it stands on the host cores (the reference arm of this tier)."""
+    procs = os.cpu_count() or 1
+    with oracle_pool(procs) as pool:
+        for _ in range(a.warmup):
+            pool.map(_oracle_solve, range(procs))
+        n, el, iters = oracle_rounds(pool, procs, rounds=a.steps, first=procs)
+    v = n / el
+    cb = {"value": v, "unit": UNIT, "cores": procs, "cpu": cpu_model(), "kind": "oracle",
+          "sample": f"{a.steps} rounds of {procs} concurrent complete solves of instances of the "
+                    f"10000-bus batch by the FP64 oracle, one BLAS thread each "
+                    f"({statistics.mean(iters):.0f} iterations each)"}
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * el / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": bench_config(1), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def bench_config(world):
+    return {"workload": WORKLOAD, "n_bus": 10000, "n_line": 12700, "n_gen": 2500, "batch": BATCH,
+            "gap": GAP, "rule": "adam", "path": "batched tensor-core (tcgen05 BF16x3, CTA pairs)",
+            "operator_precision": "bf16x3", "value_and_certificate": "fp64",
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--plain-steps", type=int, default=3)
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--no-batched-leg", dest="batched_leg", action="store_false",
-                    help="skip the batched cold/warm-start leg of the bench line")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-legs", dest="legs", action="store_false",
+                    help="skip the extra legs (fused, 4600-bus batch, warm start, group)")
     ap.add_argument("--warm-start-eval", action="store_true",
                     help="evaluate the learned warm start (prints its own JSON, not the bench line)")
     ap.add_argument("--n-train", type=int, default=50000)
@@ -389,38 +645,22 @@ def main():
     ap.add_argument("--n-eval", type=int, default=4096)
     ap.add_argument("--optimizer-study", action="store_true",
                     help="sweep the ascent rules on the study instances (prints its own JSON)")
+    ap.add_argument("--figure-sweeps", action="store_true",
+                    help="the paper's Fig. 3 and Fig. 4 sweeps on the 10000-bus QP (own JSON)")
     a = ap.parse_args()
     if a.optimizer_study:
         print(json.dumps(optimizer_study()))
+        return
+    if a.figure_sweeps:
+        print(json.dumps(figure_sweeps()))
         return
     if a.warm_start_eval:
         print(json.dumps(warm_start_eval(a.n_train, a.epochs, a.n_eval)))
         return
     world, rank, local, dist = dist_setup(a.gpus)
-
     if a.impl == "reference":
-        if rank != 0:
-            return
-        procs = os.cpu_count() or 1
-        with oracle_pool(procs) as pool:
-            for _ in range(a.warmup):
-                pool.map(_oracle_solve, range(procs))
-            t0 = time.perf_counter()
-            for _ in range(a.steps):   # a step: one solve per host core
-                pool.map(_oracle_solve, range(procs))
-            el = time.perf_counter() - t0
-        v = procs * a.steps / el
-        cb = {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
-              "sample": f"{a.steps} rounds of {procs} concurrent complete solves of the 2000-bus "
-                        "instance by the FP64 oracle, one BLAS thread each"}
-        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
-                          "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-                          "ms_per_step": 1e3 * el / a.steps, "higher_is_better": True,
-                          "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": {"workload": WORKLOAD},
-                          "cpu_baseline": cb,
-                          "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
-                                  "d2h_bytes_per_step": 0}}))
+        if rank == 0:
+            print(json.dumps(reference_arm(a)))
         return
 
     import numpy as np
@@ -429,159 +669,124 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    net, base = synth.network_for(1)
-    gam = gamma_star()
+    w = synth.workload(3, batch=BATCH)
+    net = w.net
+    gam = np.array(golden("c3_gamma.json")["gamma"], dtype=float)
     t_setup = time.perf_counter()
     g = DcopfDual(net, device=local)     # a0: validation, LDL^T, Phi~ build, upload (not timed)
     setup = {"create_s": time.perf_counter() - t_setup}
-    loads = torch.tensor(base[None], dtype=torch.float64, device=dev)
-    target = torch.tensor([gam], dtype=torch.float64, device=dev)
+    loads = torch.tensor(w.loads, dtype=torch.float64, device=dev)
+    target = torch.tensor(gam, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MiB)
     stream = torch.cuda.current_stream(dev)
+    res = g.new_result(BATCH)   # output tensors reused across steps (no allocation per solve)
+    kw = dict(target=target, gap=GAP, **OURS)
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    res = g.new_result(1)   # output tensors reused across steps (no allocation per solve)
-
-    def one(kw):
-        return g.solve(loads, target=target, gap=GAP, out=res, **kw)
-
     t_first = time.perf_counter()
-    r = one(OURS)   # first solve: builds the dense H_a on the host and tunes the fused shape
+    g.solve(loads, out=res, **kw)   # first solve: tensor operands, shape tuning, graph
     torch.cuda.synchronize(dev)
     setup["first_solve_s"] = time.perf_counter() - t_first
-    with Clocks(local) as clk:   # sampling from before the warm-up
+    with Clocks(local) as clk:      # sampling from before the warm-up
         clk.wait_ready()
         for _ in range(a.warmup):
-            r = one(OURS)
-        assert r.status[0].item() == 0, "warm-up solve did not reach the gap"
+            r = g.solve(loads, out=res, **kw)
+        assert (r.status == 0).all().item(), "warm-up solve did not reach the gap"
         g.set_timing(True)
         g.read_timing()
+        g.read_kernel_timing()
         launches0 = g.kernel_launches()
-        times, iters, bounds = [], [], []
         barrier()
         clk.start()
-        for _ in range(a.steps):
-            flush.zero_()                       # L2 flushed between timed steps (untimed)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r = one(OURS)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            iters.append(r.iters[0].item())
-            bounds.append(r.bound[0].item())
-            assert r.status[0].item() == 0
+        times, r = timed_solves(g, (loads,), kw, a.steps, flush, stream, res)
         barrier()
         clk.stop()
-    launches = g.kernel_launches() - launches0
-    it_ms, it_launches, evals = g.read_timing()
-    g.set_timing(False)
-    value, total_ms = aggregate(sum(times), a.steps, world, dist, dev)
+        launches = g.kernel_launches() - launches0
+        it_ms, it_launches, evals = g.read_timing()
+        ktime, ksamples = g.read_kernel_timing()
+        g.set_timing(False)
+        st = r.status.cpu().numpy()
+        bnd = r.bound.cpu().numpy()
+        iters = r.iters.cpu().numpy()
+        assert (st == 0).all()
+    value, total_ms = aggregate(sum(times), BATCH * a.steps, world, dist, dev)
 
     # e2e: public API, pinned host inputs in, results read back to the host each step
-    loads_h = torch.tensor(base[None], dtype=torch.float64).pin_memory()
-    target_h = torch.tensor([gam], dtype=torch.float64).pin_memory()
-    res_e = g.new_result(1)   # the caller's reusable output buffer (solve(..., out=))
+    loads_h = torch.tensor(w.loads, dtype=torch.float64).pin_memory()
+    target_h = torch.tensor(gam, dtype=torch.float64).pin_memory()
+    res_e = g.new_result(BATCH)
     e2e_times = []
     for k in range(a.warmup + max(3, a.steps // 2)):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        r = g.solve(loads_h, target=target_h, gap=GAP, out=res_e, **OURS).to_host()
-        if k >= a.warmup:                       # the first calls are its warm-up
+        g.solve(loads_h, target=target_h, gap=GAP, out=res_e, **OURS).to_host()
+        if k >= a.warmup:
             e2e_times.append(time.perf_counter() - t0)
-    h2d = loads_h.numel() * 8 + 8
-    d2h = (4 + 2 * net.n_line) * 8   # bound, lambda, iters, status, mu_hi, mu_lo (packed FP64)
-    e2e = {"value": world * len(e2e_times) / sum(e2e_times), "unit": UNIT,
+    h2d = loads_h.numel() * 8 + target_h.numel() * 8
+    d2h = res_e.flat.numel() * 8   # bound, lambda, iters, status, mu_hi, mu_lo (one FP64 buffer)
+    e2e = {"value": world * BATCH * len(e2e_times) / sum(e2e_times), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # the plain FP64 GPU path on the same instance (the metric's comparison)
-    pt, pit = [], []
-    for k in range(a.plain_steps + 1):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rp = one(PLAIN)
-        e1.record(stream)
-        e1.synchronize()
-        if k > 0:                               # first run is its warm-up
-            pt.append(e0.elapsed_time(e1))
-            pit.append(rp.iters[0].item())
-    plain = {"value": len(pt) / (sum(pt) / 1e3), "unit": UNIT, "ms_per_solve": statistics.mean(pt),
-             "iterations": statistics.mean(pit), "status": int(rp.status[0].item()),
-             "rule": "gdm (Algorithm 1, heavy ball)", "precision": "fp64", "launch": "one per phase"}
+    # the metric's comparison: the plain FP64 GPU path, one instance at a time
+    plain = plain_arm(g, w, gam, PLAIN_GDM, dev, flush, stream)
+    plain_adam = plain_arm(g, w, gam, PLAIN_ADAM, dev, flush, stream)
 
+    # roofline of the dominant kernel, from the per-kernel events of the timed region
     peaks, which = load_peaks()
     nl, ng = net.n_line, net.n_gen
-    bytes_per_eval = 2 * 4 * nl * ng + nl * (12 * 4 + 3 * 4) + ng * 5 * 8
-    avg_launch_ms = it_ms / max(1, it_launches)
-    evals_per_launch = evals / max(1, it_launches)
-    achieved = bytes_per_eval * evals_per_launch / (avg_launch_ms * 1e-3) / 1e9
-    tr = NCU_TRAFFIC.get(kernel_digest())
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": tr, "peak_source": which,
-            "kernel": "k_fused_solve", "bytes_per_iteration": bytes_per_eval,
-            "iterations_per_launch": evals_per_launch, "us_per_iteration": 1e3 * it_ms / max(1, evals)}
-    batched = warm_single = None
-    if a.batched_leg:
-        ws, mlp = warm_start_eval(8192, 30, 4096, keep_model=True)
-        batched = {"workload": "4096 held-out load scenarios of the 2000-bus network, one batched "
-                               "call (tensor-core BF16x3 path), certified 0.1 % gap vs gamma*",
-                   "cold_instances_per_s": ws["cold"]["instances_per_s"],
-                   "warm_instances_per_s": ws["warm"]["instances_per_s"],
-                   "cold_mean_iters": ws["cold"]["mean_iters"],
-                   "warm_mean_iters": ws["warm"]["mean_iters"],
-                   "all_reached_gap": ws["cold"]["reached_gap"] == ws["warm"]["reached_gap"] == 4096,
-                   "all_bounds_valid": ws["cold"]["all_bounds_valid"] and ws["warm"]["all_bounds_valid"],
-                   "warm_start": "perceptron trained on the GPU on 8192 training scenarios "
-                                 f"({ws['targets_s'] + ws['train_s']:.1f} s, not timed)"}
-        # the benchmark instance from the learned warm start: MLP inference, the warm-
-        # started fused solve and its FP64 certificate, all inside the timed region
-        wkw = dict(OURS, rule="adam", alpha=300.0, beta1=0.9, beta2=0.999, decay=0.997)
-        res_w = g.new_result(1)
-        for _ in range(a.warmup):
-            g.solve(loads, target=target, gap=GAP, warm=mlp.warm_start(loads), out=res_w, **wkw)
-        wt, wit, wb = [], [], []
-        for _ in range(a.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r = g.solve(loads, target=target, gap=GAP, warm=mlp.warm_start(loads), out=res_w, **wkw)
-            e1.record(stream)
-            e1.synchronize()
-            wt.append(e0.elapsed_time(e1))
-            wit.append(r.iters[0].item())
-            wb.append(r.bound[0].item())
-            assert r.status[0].item() == 0 and r.bound[0].item() <= gam * (1 + 1e-12)
-        warm_single = {"value": len(wt) / (sum(wt) / 1e3), "unit": UNIT,
-                       "ms_per_step": statistics.mean(wt), "iterations": statistics.mean(wit),
-                       "certified_gap": (gam - statistics.mean(wb)) / gam,
-                       "settings": "adam alpha 300, beta1 0.9, beta2 0.999, decay 0.997",
-                       "timed": "perceptron inference + warm-started fused solve + FP64 certificate"}
+    kus = {k: 1e3 * v / max(1, ksamples) for k, v in ktime.items()}
+    flops = {"adjoint": 2.0 * 3 * BATCH * nl * ng, "forward": 2.0 * 3 * BATCH * nl * ng}
+    dom = max(("adjoint", "forward"), key=lambda k: kus[k])
+    achieved = flops[dom] / (kus[dom] * 1e-6) / 1e12
+    peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(kernel_digest()),
+            "peak_source": f"{which} (BF16 sustained: the kernel runs inside a long solve)",
+            "kernel": f"{dom} product (k_gemm_pair / k_gemm_bf16x as tuned)",
+            "flops_per_launch": flops[dom], "us_per_launch": kus[dom],
+            "kernel_us_per_iteration": kus, "kernel_samples": ksamples,
+            "iteration": {"us": 1e3 * it_ms / max(1, evals) * BATCH,
+                          "flops": 2 * flops["adjoint"],
+                          "bytes": 2 * 2 * 2 * nl * ng + BATCH * nl * 60,
+                          "tensor_frac": 2 * flops["adjoint"] / (1e3 * it_ms / max(1, evals) * BATCH * 1e-6)
+                          / 1e12 / peak}}
+    legs = {}
+    if a.legs:
+        legs["fused_2000bus"] = fused_leg(dev, flush, stream, max(50, 5 * a.steps), a.warmup)
+        legs["batched_4600bus_b1024"] = c2_leg(dev, flush, stream, max(3, a.steps // 4))
+        ws = warm_start_eval(a.n_train, a.epochs, a.n_eval)
+        legs["learned_warm_start_2000bus"] = {
+            "workload": f"{a.n_eval} held-out load scenarios of the 2000-bus network, one batched call, "
+                        "certified 0.1 % gap vs gamma*",
+            "cold_instances_per_s": ws["cold"]["instances_per_s"],
+            "warm_instances_per_s": ws["warm"]["instances_per_s"],
+            "cold_mean_iters": ws["cold"]["mean_iters"], "warm_mean_iters": ws["warm"]["mean_iters"],
+            "all_reached_gap": ws["cold"]["reached_gap"] == ws["warm"]["reached_gap"] == a.n_eval,
+            "all_bounds_valid": ws["cold"]["all_bounds_valid"] and ws["warm"]["all_bounds_valid"],
+            "warm_start": f"perceptron trained on the GPU on {a.n_train} training scenarios, "
+                          f"{a.epochs} epochs ({ws['targets_s']:.1f} s targets + {ws['train_s']:.1f} s "
+                          "training, not timed)"}
+        legs["group_mixed"] = group_leg(dev, max(2, a.steps // 10))
     if rank != 0:
         return
     cb = cpu_baseline(a.cpu_seconds) if world == 1 else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_bus": net.n_bus, "n_line": nl, "n_gen": ng,
-                       "batch": 1, "gap": GAP, "rule": "adam", "path": "fused persistent kernel",
-                       "operator_precision": "fp32", "value_and_certificate": "fp64",
-                       "l2": "flushed between timed steps (256 MiB write)",
-                       "parallelism": f"replicas x{world}"},
-            "iterations": statistics.mean(iters), "certified_gap": (gam - statistics.mean(bounds)) / gam,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+            "config": bench_config(world),
+            "mean_iterations": float(iters.mean()), "most_iterations": int(iters.max()),
+            "certified_gap_max": float(np.max((gam - bnd) / gam)),
+            "all_bounds_valid": bool(np.all(bnd <= gam + 1e-9 * np.abs(gam))),
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb,
             "plain_fp64_gpu": plain, "speedup_vs_plain_fp64_gpu": value / plain["value"],
-            "batched_2000bus": batched, "learned_warm_start_single": warm_single,
-            "setup_per_network": setup,
-            "clocks": clk.summary()}
+            "plain_fp64_gpu_same_rule": plain_adam,
+            "speedup_vs_plain_fp64_gpu_same_rule": value / plain_adam["value"],
+            "legs": legs, "setup_per_network": setup, "clocks": clk.summary()}
     print(json.dumps(line))
 
 

@@ -130,7 +130,14 @@ typedef struct {
   int32_t warm_start;  /* 1 = start from lambda/mu given in the in/out arrays */
   int32_t as_printed;  /* 1 = GDM applies Algorithm 1's printed extra gradient update */
   int32_t check_every; /* certify a candidate at most every k iterations (>= 1) */
-  int32_t reserved;
+  int32_t screen_lines; /* 1 = constraint screening on the batched tensor-core path
+                           (DCOPF_BF16X3, batches without outages): lines whose flow
+                           provably stays inside its limits for every dispatch of the
+                           generator box that meets the balance, at every instance's
+                           loads, are left out of the iterations (their multipliers stay
+                           0, so every point is still a valid bound, Remarks 1 and 2;
+                           the certificate evaluates the full problem); 0 = every line
+                           (Algorithm 1's C_r, d_r read as all flow rows) */
   double alpha;        /* step size for mu (and lambda unless alpha_lambda > 0) */
   double alpha_lambda; /* step size for lambda; <= 0 => alpha */
   double rho;          /* GDM momentum */
@@ -359,6 +366,20 @@ dcopf_status dcopf_dual_set_timing(dcopf_dual_t h, int32_t enable);
  * performed summed over instances.  Host pointers; NULL outputs are skipped. */
 dcopf_status dcopf_dual_read_timing(dcopf_dual_t h, double* iter_ms, int64_t* iter_launches,
                                     int64_t* evaluations);
+
+/* The lines the last screened solve (screen_lines = 1) iterated on: *n_kept (host,
+ * nullable) their number, kept_mask (host [n_line], nullable) 1 for each of them.  The
+ * kept set is a multiple of 8 lines: besides every line that may bind it holds the
+ * first lines that cannot, up to that multiple.  0 kept lines: no screen yet. */
+dcopf_status dcopf_dual_screened_lines(dcopf_dual_t h, int32_t* n_kept, uint8_t* kept_mask);
+
+/* Per-kernel timing of the batched tensor-core solve, while dcopf_dual_set_timing is
+ * on: CUDA events recorded inside the iteration graph around the five kernels of the
+ * last iteration of every round (the adjoint product, the minimiser, the forward
+ * product, the step, the dual value).  ms (host [5], nullable) receives the summed
+ * milliseconds of each over the sampled iterations, samples (host, nullable) their
+ * count; both are then reset.  Host only. */
+dcopf_status dcopf_dual_read_kernel_timing(dcopf_dual_t h, double* ms, int64_t* samples);
 
 /* Device-memory budget of a handle's workspaces: the buffers that eval,
  * certify_bound, primal_bound, solve_batch and the self-tests allocate on first use

@@ -13,7 +13,8 @@ EXPORTS = ("dcopf_version", "dcopf_status_string", "dcopf_solve_params_default",
            "dcopf_dual_certify_bound", "dcopf_dual_primal_bound", "dcopf_dual_solve_batch",
            "dcopf_dual_kernel_launches",
            "dcopf_dual_device_error", "dcopf_dual_set_timing", "dcopf_dual_read_timing",
-           "dcopf_dual_workspace_limit", "dcopf_selftest_bounded_wait",
+           "dcopf_dual_screened_lines", "dcopf_dual_read_kernel_timing", "dcopf_dual_workspace_limit",
+           "dcopf_selftest_bounded_wait",
            "dcopf_selftest_fused_timeout", "dcopf_dual_eval_noalloc", "dcopf_dual_solve_group",
            "dcopf_mlp_create", "dcopf_mlp_destroy", "dcopf_mlp_num_params", "dcopf_mlp_set_params",
            "dcopf_mlp_get_params", "dcopf_mlp_set_normalization", "dcopf_mlp_forward",
@@ -49,7 +50,7 @@ class Options(C.Structure):
 class SolveParams(C.Structure):
     _fields_ = [("rule", C.c_int32), ("precision", C.c_int32), ("path", C.c_int32),
                 ("max_iters", C.c_int32), ("warm_start", C.c_int32), ("as_printed", C.c_int32),
-                ("check_every", C.c_int32), ("reserved", C.c_int32), ("alpha", C.c_double),
+                ("check_every", C.c_int32), ("screen_lines", C.c_int32), ("alpha", C.c_double),
                 ("alpha_lambda", C.c_double), ("rho", C.c_double), ("beta1", C.c_double),
                 ("beta2", C.c_double), ("eps", C.c_double), ("decay", C.c_double),
                 ("gap", C.c_double), ("tol", C.c_double), ("target_value", P),
@@ -112,6 +113,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.dcopf_selftest_bounded_wait.argtypes = [P, C.c_int64, P]
     lib.dcopf_selftest_fused_timeout.argtypes = [P, P, C.c_int64, P]
     lib.dcopf_dual_workspace_limit.argtypes = [P, C.c_int64, C.POINTER(C.c_int64)]
+    lib.dcopf_dual_read_kernel_timing.argtypes = [P, F64P, C.POINTER(C.c_int64)]
+    lib.dcopf_dual_screened_lines.argtypes = [P, I32P, C.POINTER(C.c_uint8)]
     lib.dcopf_dual_eval_noalloc.argtypes = [P, C.c_int32, P, P, P, P, P, C.c_int32, P, P, P, P,
                                             P, P]
     lib.dcopf_dual_read_timing.argtypes = [P, F64P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
@@ -150,6 +153,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                  "dcopf_dual_set_timing", "dcopf_dual_read_timing",
                  "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc", "dcopf_dual_solve_group",
                  "dcopf_selftest_fused_timeout", "dcopf_dual_workspace_limit",
+                 "dcopf_dual_read_kernel_timing", "dcopf_dual_screened_lines",
            "dcopf_mlp_create", "dcopf_mlp_destroy", "dcopf_mlp_num_params", "dcopf_mlp_set_params",
            "dcopf_mlp_get_params", "dcopf_mlp_set_normalization", "dcopf_mlp_forward",
            "dcopf_mlp_loss_grad", "dcopf_mlp_train_step", "dcopf_mlp_warm_start",

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libdcopfdual.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["network.cpp", "api.cu", "k_sparse.cu", "k_phases.cu", "k_fused.cu", "k_tensor.cu", "k_noalloc.cu", "k_dense.cu",
-           "k_mlp.cu", "k_primal.cu", "k_probe.cu"]
+           "k_mlp.cu", "k_primal.cu", "k_probe.cu", "k_screen.cu"]
 
 
 def nvcc() -> str:

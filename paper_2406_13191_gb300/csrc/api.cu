@@ -19,6 +19,8 @@ dcopf_dual::~dcopf_dual() {
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
   if (tev) cudaEventDestroy(tev);
+  for (cudaEvent_t e : kev)
+    if (e) cudaEventDestroy(e);
   if (tstream) cudaStreamDestroy(tstream);
   if (cstream) cudaStreamDestroy(cstream);
   if (h_pinned) cudaFreeHost(h_pinned);
@@ -466,6 +468,14 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
     if (t && strcmp(t, "128") == 0) h->tiles_mode = 1;
     if (t && strcmp(t, "256") == 0) h->tiles_mode = 2;
     if (t && strcmp(t, "192") == 0) h->tiles_mode = 3;
+    const char* sh = getenv("DCOPF_TENSOR_SHAPE");
+    int a = -1, sp = 0, fw = -1;
+    if (sh && sscanf(sh, "%d,%d,%d", &a, &sp, &fw) == 3 && a >= 0 && a <= 2 && sp >= 1 && sp <= 64 &&
+        fw >= 0 && fw <= 2) {
+      h->shape_adj = a;
+      h->shape_splits = sp;
+      h->shape_fwd = fw;
+    }
   }
   std::string err;
   h->sparse_only = opt && opt->operator_form == 1;
@@ -797,6 +807,28 @@ dcopf_status dcopf_dual_read_timing(dcopf_dual_t h, double* iter_ms, int64_t* it
   h->t_iter_ms = 0.0;
   h->t_iter_launches = 0;
   h->t_evals = 0;
+  return DCOPF_OK;
+}
+
+dcopf_status dcopf_dual_screened_lines(dcopf_dual_t h, int32_t* n_kept, uint8_t* kept_mask) {
+  if (!h) return DCOPF_ERR_INVALID_ARG;
+  const LineScreen& S = h->scr;
+  if (n_kept) *n_kept = S.ready ? S.nk : 0;
+  if (kept_mask) {
+    memset(kept_mask, 0, (size_t)h->host.n_line);
+    if (S.ready)
+      for (int l : S.kept_host) kept_mask[l] = 1;
+  }
+  return DCOPF_OK;
+}
+
+dcopf_status dcopf_dual_read_kernel_timing(dcopf_dual_t h, double* ms, int64_t* samples) {
+  if (!h) return DCOPF_ERR_INVALID_ARG;
+  if (ms)
+    for (int q = 0; q < 5; ++q) ms[q] = h->t_kernel_ms[q];
+  if (samples) *samples = h->t_kernel_samples;
+  for (int q = 0; q < 5; ++q) h->t_kernel_ms[q] = 0.0;
+  h->t_kernel_samples = 0;
   return DCOPF_OK;
 }
 

@@ -1,0 +1,261 @@
+// Constraint screening for the batched solves: Algorithm 1 writes the flow rows it
+// iterates on as C_r, d_r, a subset of all 2 n_line rows.  A line whose flow stays
+// strictly inside its limits for every dispatch of the generator box that meets the
+// balance, at the loads of every instance of the batch, can never bind: dropping it
+// leaves the primal optimum unchanged, and fixing its multipliers at zero keeps every
+// dual point a valid bound (Remarks 1 and 2).  The certificate always evaluates the
+// full problem, so a screen never affects the validity of a bound, only which rows the
+// iterations carry.
+//
+// In the normalised variables (Appendix A1) the flow of line l is Phi~_l x + f0_l with
+// x in [-1, 1]^n_gen and sigma^T x = R_b = D_b - sum_j mid_j.  For every t,
+//   max { Phi~_l x : |x| <= 1, sigma^T x = R, R in [R_lo, R_hi] }
+//     <= psi_l(t) = max(t R_lo, t R_hi) + sum_j |Phi~_lj - t sigma_j|
+// (weak duality of the fractional knapsack for each R, then the max over R of a min
+// over t is at most the min over t of the max).  psi_l is convex in t; a bisection on
+// the sign of its subgradient in FP32 finds a good t, and psi_l(t) evaluated in FP64 is
+// the bound, whatever the accuracy of the search.  The same with -Phi~_l bounds the
+// flow from below.
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "dev.cuh"
+#include "kernels.h"
+
+namespace dcopf {
+
+namespace {
+
+// Extremes over the batch of each line's base flow f0 and of the balance R.
+__global__ void k_screen_envelope(int B, int nl, const double* __restrict__ f0,
+                                  const double* __restrict__ demand, double sum_mid,
+                                  double* __restrict__ lo, double* __restrict__ hi, double* __restrict__ r) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += gridDim.x * blockDim.x) {
+    double a = INFINITY, z = -INFINITY;
+    for (int b = 0; b < B; ++b) {
+      const double v = f0[(size_t)b * nl + l];
+      a = fmin(a, v);
+      z = fmax(z, v);
+    }
+    lo[l] = a;
+    hi[l] = z;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double a = INFINITY, z = -INFINITY;
+    for (int b = 0; b < B; ++b) {
+      a = fmin(a, demand[b] - sum_mid);
+      z = fmax(z, demand[b] - sum_mid);
+    }
+    r[0] = a;
+    r[1] = z;
+  }
+}
+
+// One warp per line: the knapsack bounds up_l >= max Phi~_l x and dn_l >= max -Phi~_l x
+// over the box and every balance R in [rlo, rhi].
+__global__ void __launch_bounds__(256) k_screen_knapsack(DevNet N, double rlo, double rhi,
+                                                         double* __restrict__ up, double* __restrict__ dn) {
+  const int l = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (l >= N.n_line) return;  // whole warps
+  const int ng = N.n_gen;
+  const float* p32 = N.phi32 + (size_t)l * ng;
+  const double* p64 = N.phi64 + (size_t)l * ng;
+  const float rlof = (float)rlo, rhif = (float)rhi;
+  for (int dir = 0; dir < 2; ++dir) {
+    const float sg = dir == 0 ? 1.f : -1.f;
+    float rmin = INFINITY, rmax = -INFINITY;
+    for (int j = lane; j < ng; j += 32) {
+      const float s = N.sigma32[j];
+      if (s > 0.f) {
+        const float q = sg * p32[j] / s;
+        rmin = fminf(rmin, q);
+        rmax = fmaxf(rmax, q);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+      rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    }
+    float a = rmin < INFINITY ? rmin : 0.f, b = rmax > -INFINITY ? rmax : 0.f;
+    // the subgradient (t > 0 ? R_hi : R_lo) - sum_j sigma_j sgn(Phi~_lj - t sigma_j) is
+    // non-decreasing in t: bisection on its sign change
+    for (int it = 0; it < 24; ++it) {
+      const float t = 0.5f * (a + b);
+      float g = 0.f;
+      for (int j = lane; j < ng; j += 32) {
+        const float s = N.sigma32[j], d = sg * p32[j] - t * s;
+        g += d > 0.f ? s : (d < 0.f ? -s : 0.f);
+      }
+      g = warp_sum(g);
+      const float sub = (t > 0.f ? rhif : rlof) - g;
+      if (sub < 0.f) a = t;
+      else b = t;
+    }
+    const double t = 0.5 * ((double)a + (double)b);
+    double psi = 0.0;
+    for (int j = lane; j < ng; j += 32) psi += fabs((double)sg * p64[j] - t * N.sigma[j]);
+    psi = warp_sum(psi) + fmax(t * rlo, t * rhi);
+    if (lane == 0) (dir == 0 ? up : dn)[l] = psi;
+  }
+}
+
+// keep[l] = 0 when line l's flow provably stays inside its limits for the batch: its
+// knapsack bounds plus the batch's extremes of its base flow, with a rounding margin.
+__global__ void k_screen_decide(DevNet N, const double* __restrict__ up, const double* __restrict__ dn,
+                                const double* __restrict__ lo, const double* __restrict__ hi,
+                                unsigned char* __restrict__ keep) {
+  const int nl = N.n_line, ng = N.n_gen;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += gridDim.x * blockDim.x) {
+    const double fup = up[l] + hi[l], fdn = -dn[l] + lo[l];
+    // psi is a sum of n_gen + 1 FP64 terms (each within a few units in the last place) and
+    // the flow adds one more: 8 (n_gen + 2) units of 2^-53 of the magnitudes involved
+    const double mag = fabs(up[l]) + fabs(dn[l]) + fabs(lo[l]) + fabs(hi[l]) + fabs(N.fmax[l]) + fabs(N.fmin[l]);
+    const double margin = 8.0 * (ng + 2) * 1.1102230246251565e-16 * mag + 1e-12;
+    keep[l] = (fup <= N.fmax[l] - margin && fdn >= N.fmin[l] + margin) ? 0 : 1;
+  }
+}
+
+// Compact BF16 operands of the kept lines: rows of the forward operand [n_line][ld_g]
+// and columns (the K dimension) of the adjoint operand [n_gen][ld_l].
+__global__ void k_screen_gather_rows(int nk, int ld, const int* __restrict__ kept,
+                                     const __nv_bfloat16* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+  const size_t n = (size_t)nk * ld;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = q / ld, c = q - r * ld;
+    dst[q] = src[(size_t)kept[r] * ld + c];
+  }
+}
+__global__ void k_screen_gather_cols(int rows, int nk, int ld_src, int ld_dst, const int* __restrict__ kept,
+                                     const __nv_bfloat16* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+  const size_t n = (size_t)rows * ld_dst;
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = q / ld_dst, c = q - r * ld_dst;
+    dst[q] = c < (size_t)nk ? src[r * ld_src + kept[c]] : z;
+  }
+}
+__global__ void k_screen_gather_lines(int nk, const int* __restrict__ kept, const float* __restrict__ a,
+                                      const float* __restrict__ b, float* __restrict__ ca, float* __restrict__ cb) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nk; r += gridDim.x * blockDim.x) {
+    ca[r] = a[kept[r]];
+    cb[r] = b[kept[r]];
+  }
+}
+
+}  // namespace
+
+// Per batch [B][n_line] FP32 rows -> [B][nk] compact rows (the base flows of the kept lines).
+__global__ void k_screen_compact_rows(int B, int nl, int nk, const int* __restrict__ kept,
+                                      const float* __restrict__ src, float* __restrict__ dst) {
+  const size_t n = (size_t)B * nk;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = q / nk, r = q - b * nk;
+    dst[q] = src[b * nl + kept[r]];
+  }
+}
+
+// [B][nk] compact multipliers -> [B][n_line], zero on the screened lines.
+__global__ void k_screen_scatter_rows(int B, int nl, int nk, const int* __restrict__ pos,
+                                      const float* __restrict__ src, float* __restrict__ dst) {
+  const size_t n = (size_t)B * nl;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = q / nl, l = q - b * nl;
+    const int r = pos[l];
+    dst[q] = r >= 0 ? src[b * nk + r] : 0.f;
+  }
+}
+
+dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s) {
+  LineScreen& S = h->scr;
+  const int nl = h->host.n_line, ng = h->host.n_gen;
+  if (S.env.alloc((size_t)(2 * nl + 2) * sizeof(double)) != cudaSuccess ||
+      S.knap.alloc((size_t)2 * nl * sizeof(double)) != cudaSuccess ||
+      S.keep.alloc((size_t)nl) != cudaSuccess) {
+    cudaGetLastError();
+    return DCOPF_ERR_OOM;
+  }
+  double* lo = S.env.as<double>();
+  double* hi = lo + nl;
+  double* r = hi + nl;
+  double sum_mid = 0.0;
+  for (int j = 0; j < ng; ++j) sum_mid += h->host.mid[j];
+  const unsigned grid = (unsigned)std::min(1024, (nl + 255) / 256);
+  k_screen_envelope<<<grid, 256, 0, s>>>(B, nl, h->ws.f0.as<double>(), h->ws.demand.as<double>(), sum_mid,
+                                         lo, hi, r);
+  double rr[2];
+  if (cudaMemcpyAsync(rr, r, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  double* up = S.knap.as<double>();
+  double* dn = up + nl;
+  // the knapsack bounds hold for any balance range inside the one they were taken on
+  if (!(S.knap_valid && rr[0] >= S.rlo && rr[1] <= S.rhi)) {
+    // a little wider than this batch, so that nearby batches reuse them
+    const double w = 0.02 * (fabs(rr[0]) + fabs(rr[1])) + 1e-9;
+    S.rlo = rr[0] - w;
+    S.rhi = rr[1] + w;
+    k_screen_knapsack<<<(unsigned)((nl + 7) / 8), 256, 0, s>>>(h->dev, S.rlo, S.rhi, up, dn);
+    S.knap_valid = true;
+  }
+  k_screen_decide<<<grid, 256, 0, s>>>(h->dev, up, dn, lo, hi, S.keep.as<unsigned char>());
+  h->launches += 3;
+  std::vector<unsigned char> keep(nl);
+  if (cudaMemcpyAsync(keep.data(), S.keep.p, nl, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  std::vector<int> kept;
+  for (int l = 0; l < nl; ++l)
+    if (keep[l]) kept.push_back(l);
+  // a multiple of 8 rows (16-byte row strides for TMA, four-line vector steps): the
+  // first screened lines are kept as well, which only adds rows that cannot bind
+  for (int l = 0; l < nl && (kept.size() % 8 != 0 || kept.empty()); ++l)
+    if (!keep[l]) { keep[l] = 1; kept.push_back(l); }
+  std::sort(kept.begin(), kept.end());
+  if (S.ready && kept == S.kept_host) return DCOPF_OK;
+  // the compact operands of this set of lines
+  const int nk = (int)kept.size();
+  TensorOps& T = h->tops;
+  const int ld_lk = (nk + 7) & ~7;
+  std::vector<int> pos(nl, -1);
+  for (int q = 0; q < nk; ++q) pos[kept[q]] = q;
+  S.ready = false;
+  if (S.kept.alloc((size_t)nk * sizeof(int)) != cudaSuccess || S.pos.alloc((size_t)nl * sizeof(int)) != cudaSuccess ||
+      S.phi_hi.alloc((size_t)nk * T.ld_g * 2) || S.phi_lo.alloc((size_t)nk * T.ld_g * 2) ||
+      S.phit_hi.alloc((size_t)ng * ld_lk * 2) || S.phit_lo.alloc((size_t)ng * ld_lk * 2) ||
+      S.lim.alloc((size_t)2 * nk * sizeof(float))) {
+    cudaGetLastError();
+    return DCOPF_ERR_OOM;
+  }
+  if (cudaMemcpyAsync(S.kept.p, kept.data(), (size_t)nk * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(S.pos.p, pos.data(), (size_t)nl * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  const int* kd = S.kept.as<int>();
+  k_screen_gather_rows<<<1024, 256, 0, s>>>(nk, T.ld_g, kd, T.phi_hi.as<__nv_bfloat16>(), S.phi_hi.as<__nv_bfloat16>());
+  k_screen_gather_rows<<<1024, 256, 0, s>>>(nk, T.ld_g, kd, T.phi_lo.as<__nv_bfloat16>(), S.phi_lo.as<__nv_bfloat16>());
+  k_screen_gather_cols<<<1024, 256, 0, s>>>(ng, nk, T.ld_l, ld_lk, kd, T.phit_hi.as<__nv_bfloat16>(),
+                                            S.phit_hi.as<__nv_bfloat16>());
+  k_screen_gather_cols<<<1024, 256, 0, s>>>(ng, nk, T.ld_l, ld_lk, kd, T.phit_lo.as<__nv_bfloat16>(),
+                                            S.phit_lo.as<__nv_bfloat16>());
+  float* lim = S.lim.as<float>();
+  k_screen_gather_lines<<<(nk + 255) / 256, 256, 0, s>>>(nk, kd, h->dev.fmax32, h->dev.fmin32, lim, lim + nk);
+  h->launches += 5;
+  if (cudaGetLastError() != cudaSuccess) return DCOPF_ERR_CUDA;
+  if (!tc_make_map(&S.m_phi_hi, S.phi_hi.p, nk, ng, T.ld_g) || !tc_make_map(&S.m_phi_lo, S.phi_lo.p, nk, ng, T.ld_g) ||
+      !tc_make_map(&S.m_phit_hi, S.phit_hi.p, ng, nk, ld_lk) ||
+      !tc_make_map(&S.m_phit_lo, S.phit_lo.p, ng, nk, ld_lk) ||
+      !tc_make_map_rows(&S.m_phi_hi96, S.phi_hi.p, nk, ng, T.ld_g, 96) ||
+      !tc_make_map_rows(&S.m_phi_lo96, S.phi_lo.p, nk, ng, T.ld_g, 96) ||
+      !tc_make_map_rows(&S.m_phit_hi96, S.phit_hi.p, ng, nk, ld_lk, 96) ||
+      !tc_make_map_rows(&S.m_phit_lo96, S.phit_lo.p, ng, nk, ld_lk, 96))
+    return DCOPF_ERR_CUDA;
+  S.nk = nk;
+  S.ld_lk = ld_lk;
+  S.kept_host = kept;
+  S.ready = true;
+  S.map_B = 0;  // the per-batch A operand maps are made for the next batch size
+  return DCOPF_OK;
+}
+
+}  // namespace dcopf

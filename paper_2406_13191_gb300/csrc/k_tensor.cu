@@ -294,7 +294,8 @@ template <int NPROD, int PBN>
 struct PairCfg {
   static constexpr uint32_t B_TILE = (uint32_t)(PBN / 2) * GBK * 2;
   static constexpr uint32_t STAGE_BYTES = (NPROD == 3 ? 2 : 1) * TILE_BYTES + 2 * B_TILE;
-  static constexpr int STAGES = (200u * 1024u / STAGE_BYTES) < 5 ? (200u * 1024u / STAGE_BYTES) : 5;
+  // as many stages as fit in 224 KB of the 227 KB a CTA may hold (at most five)
+  static constexpr int STAGES = (224u * 1024u / STAGE_BYTES) < 5 ? (224u * 1024u / STAGE_BYTES) : 5;
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
   static constexpr uint32_t TMEM_COLS = PBN <= 128 ? 128 : 256;  // a power of two
   static_assert(STAGES >= 2, "a ring of at least two stages");
@@ -536,21 +537,26 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
     red[16 + w] = (double)oacc;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double ls = 0.0, os = 0.0;
-    for (int q = 0; q < STEP_THREADS / 32; ++q) {
-      ls += red[q];
-      os += red[16 + q];
+  if (threadIdx.x < 32) {
+    // the warps' partials in FP64, a shuffle tree (fixed order)
+    const int l = threadIdx.x;
+    double ls = l < STEP_THREADS / 32 ? red[l] : 0.0, os = l < STEP_THREADS / 32 ? red[16 + l] : 0.0;
+#pragma unroll
+    for (int o = STEP_THREADS / 64; o > 0; o >>= 1) {
+      ls += __shfl_xor_sync(0xffffffffu, ls, o);
+      os += __shfl_xor_sync(0xffffffffu, os, o);
     }
-    E.line_part[(size_t)b * E.n_tiles + chunk] = ls;
-    E.out_part[(size_t)b * E.n_tiles + chunk] = os;
+    if (l == 0) {
+      E.line_part[(size_t)b * E.n_tiles + chunk] = ls;
+      E.out_part[(size_t)b * E.n_tiles + chunk] = os;
+    }
   }
 }
 
 // The same step with four consecutive lines per thread: 16-byte loads and stores of every
 // FP32 stream and 8-byte stores of the BF16 split (needs n_line, ldF and ldh multiples
 // of 4; the chunk of a block is the same 1024 lines as k_bt_step's).
-__global__ void __launch_bounds__(STEP_THREADS) k_bt_step4(StepEpi E, int nl) {
+__global__ void __launch_bounds__(STEP_THREADS, 4) k_bt_step4(StepEpi E, int nl) {
   __shared__ double red[32];
   const int b = blockIdx.y, chunk = blockIdx.x;
   if (E.frozen[b]) return;
@@ -621,14 +627,19 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step4(StepEpi E, int nl) {
     red[16 + w] = (double)oacc;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double ls = 0.0, os = 0.0;
-    for (int q = 0; q < STEP_THREADS / 32; ++q) {
-      ls += red[q];
-      os += red[16 + q];
+  if (threadIdx.x < 32) {
+    // the warps' partials in FP64, a shuffle tree (fixed order)
+    const int l = threadIdx.x;
+    double ls = l < STEP_THREADS / 32 ? red[l] : 0.0, os = l < STEP_THREADS / 32 ? red[16 + l] : 0.0;
+#pragma unroll
+    for (int o = STEP_THREADS / 64; o > 0; o >>= 1) {
+      ls += __shfl_xor_sync(0xffffffffu, ls, o);
+      os += __shfl_xor_sync(0xffffffffu, os, o);
     }
-    E.line_part[(size_t)b * E.n_tiles + chunk] = ls;
-    E.out_part[(size_t)b * E.n_tiles + chunk] = os;
+    if (l == 0) {
+      E.line_part[(size_t)b * E.n_tiles + chunk] = ls;
+      E.out_part[(size_t)b * E.n_tiles + chunk] = os;
+    }
   }
 }
 
@@ -848,40 +859,63 @@ static cudaError_t launch_gemm(dcopf_dual* h, const CUtensorMap& Ah, const CUten
   return cudaGetLastError();
 }
 
-// The LP forward F = X Phi~^T (two products: x is exact in BF16).  Its K = n_gen is
-// short, so a CTA spends much of its time in the epilogue: two CTAs per SM (a 2-stage
-// ring each) let one CTA's epilogue run beside the other's main loop.
-static cudaError_t launch_forward_lp(dcopf_dual* h, const GemmArgs& g, cudaStream_t s) {
-  TensorOps& T = h->tops;
-  return launch_gemm<2, 2>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, g, 1, s);
-}
-
 // The adjoint Pi~ = H Phi~ (split-K partials) and the forward F = X Phi~^T, each on
 // single CTAs or on CTA pairs.
-// `tiles`: 0 single CTAs (128 x 128), 1 CTA pairs of 256 x 256, 2 CTA pairs of 256 x 192.
-static cudaError_t launch_adjoint(dcopf_dual* h, const GemmArgs& g, int splits, int tiles, cudaStream_t s) {
+// The lines a batched solve iterates on: every line of the network, or the lines a
+// constraint screen kept (k_screen.cu), with the operands, limits and base flows of
+// those lines in compact [*][nl] layouts.
+struct LineSet {
+  int nl = 0, ld_l = 0;            // lines iterated on, row stride of [*][nl] BF16 operands
+  const CUtensorMap *H_hi = nullptr, *H_lo = nullptr;   // adjoint A operand [B][ld_l]
+  const CUtensorMap *phit_hi = nullptr, *phit_lo = nullptr, *phit_hi96 = nullptr, *phit_lo96 = nullptr;
+  const CUtensorMap *phi_hi = nullptr, *phi_lo = nullptr, *phi_hi96 = nullptr, *phi_lo96 = nullptr;
+  const float* fmax = nullptr;     // [nl]
+  const float* fmin = nullptr;
+  const float* f0 = nullptr;       // [B][nl] base flows
+  const int* kept = nullptr;       // [nl] network line of each row (null: all lines)
+  const int* pos = nullptr;        // [n_line] row of each line or -1 (null: all lines)
+};
+
+static LineSet full_lines(dcopf_dual* h) {
   TensorOps& T = h->tops;
-  if (tiles == 1) return launch_gemm_pair<3, 256>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi, T.m_phit_lo, g, splits, s);
-  if (tiles == 2)
-    return launch_gemm_pair<3, 192>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi96, T.m_phit_lo96, g, splits, s);
-  return launch_gemm<3>(h, T.m_H_hi, T.m_H_lo, T.m_phit_hi, T.m_phit_lo, g, splits, s);
-}
-static cudaError_t launch_forward(dcopf_dual* h, const GemmArgs& g, int tiles, cudaStream_t s) {
-  TensorOps& T = h->tops;
-  if (h->host.qp) {
-    if (tiles == 1) return launch_gemm_pair<3, 256>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, g, 1, s);
-    if (tiles == 2) return launch_gemm_pair<3, 192>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi96, T.m_phi_lo96, g, 1, s);
-    return launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, g, 1, s);
-  }
-  if (tiles == 1) return launch_gemm_pair<2, 256>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi, T.m_phi_lo, g, 1, s);
-  if (tiles == 2) return launch_gemm_pair<2, 192>(h, T.m_X_hi, T.m_X_lo, T.m_phi_hi96, T.m_phi_lo96, g, 1, s);
-  return launch_forward_lp(h, g, s);
+  LineSet L;
+  L.nl = h->host.n_line;
+  L.ld_l = T.ld_l;
+  L.H_hi = &T.m_H_hi; L.H_lo = &T.m_H_lo;
+  L.phit_hi = &T.m_phit_hi; L.phit_lo = &T.m_phit_lo; L.phit_hi96 = &T.m_phit_hi96; L.phit_lo96 = &T.m_phit_lo96;
+  L.phi_hi = &T.m_phi_hi; L.phi_lo = &T.m_phi_lo; L.phi_hi96 = &T.m_phi_hi96; L.phi_lo96 = &T.m_phi_lo96;
+  L.fmax = h->dev.fmax32;
+  L.fmin = h->dev.fmin32;
+  L.f0 = h->ws.f0_32.as<float>();
+  return L;
 }
 
-// Split-K factor of the adjoint: enough CTAs to cover the SMs twice.
-static void adjoint_split(const dcopf_dual* h, int B, int* splits, int* kbps) {
+// `tiles`: 0 single CTAs (128 x 128), 1 CTA pairs of 256 x 256, 2 CTA pairs of 256 x 192.
+static cudaError_t launch_adjoint(dcopf_dual* h, const LineSet& L, const GemmArgs& g, int splits, int tiles,
+                                  cudaStream_t s) {
+  if (tiles == 1) return launch_gemm_pair<3, 256>(h, *L.H_hi, *L.H_lo, *L.phit_hi, *L.phit_lo, g, splits, s);
+  if (tiles == 2) return launch_gemm_pair<3, 192>(h, *L.H_hi, *L.H_lo, *L.phit_hi96, *L.phit_lo96, g, splits, s);
+  return launch_gemm<3>(h, *L.H_hi, *L.H_lo, *L.phit_hi, *L.phit_lo, g, splits, s);
+}
+static cudaError_t launch_forward(dcopf_dual* h, const LineSet& L, const GemmArgs& g, int tiles, cudaStream_t s) {
+  TensorOps& T = h->tops;
+  if (h->host.qp) {
+    if (tiles == 1) return launch_gemm_pair<3, 256>(h, T.m_X_hi, T.m_X_lo, *L.phi_hi, *L.phi_lo, g, 1, s);
+    if (tiles == 2) return launch_gemm_pair<3, 192>(h, T.m_X_hi, T.m_X_lo, *L.phi_hi96, *L.phi_lo96, g, 1, s);
+    return launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, *L.phi_hi, *L.phi_lo, g, 1, s);
+  }
+  if (tiles == 1) return launch_gemm_pair<2, 256>(h, T.m_X_hi, T.m_X_lo, *L.phi_hi, *L.phi_lo, g, 1, s);
+  if (tiles == 2) return launch_gemm_pair<2, 192>(h, T.m_X_hi, T.m_X_lo, *L.phi_hi96, *L.phi_lo96, g, 1, s);
+  // the LP forward on single CTAs (two products: x is exact in BF16): its K = n_gen is
+  // short, so a CTA spends much of its time in the epilogue; two CTAs per SM (a 2-stage
+  // ring each) let one CTA's epilogue run beside the other's main loop
+  return launch_gemm<2, 2>(h, T.m_X_hi, T.m_X_lo, *L.phi_hi, *L.phi_lo, g, 1, s);
+}
+
+// Split-K factor of the adjoint over nl lines: enough CTAs to cover the SMs twice.
+static void adjoint_split(const dcopf_dual* h, int B, int nl, int* splits, int* kbps) {
   const int tiles = ((B + GBM - 1) / GBM) * ((h->host.n_gen + GBN - 1) / GBN);
-  const int kb = (h->host.n_line + GBK - 1) / GBK;
+  const int kb = (nl + GBK - 1) / GBK;
   int s = std::max(1, std::min(kb, std::min(64, (2 * h->sm_count + tiles - 1) / tiles)));
   int per = (kb + s - 1) / s;
   *kbps = per;
@@ -901,9 +935,10 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
                                         T.H_hi.as<__nv_bfloat16>(), T.H_lo.as<__nv_bfloat16>());
   h->launches += 1;
   int splits, kbps;
-  adjoint_split(h, B, &splits, &kbps);
+  adjoint_split(h, B, nl, &splits, &kbps);
+  const LineSet L = full_lines(h);
   int pair_adj = (h->tiles_mode >= 2 && B > GBM) ? h->tiles_mode - 1 : 0, pair_fwd = pair_adj;
-  if (h->tune_B == B && h->tune_splits > 0) {  // the shapes a solve of this batch size chose
+  if (h->tune_B == B && h->tune_nl == nl && h->tune_splits > 0) {  // the shapes a solve of this batch chose
     splits = h->tune_splits;
     kbps = h->tune_kbps;
     pair_adj = h->tune_pair_adj;
@@ -912,7 +947,7 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
   GemmArgs g{};
   g.M = B; g.N = ng; g.K = nl; g.kb_per_split = kbps; g.epi = EPI_PARTIAL;
   g.P = T.P.as<float>(); g.ldp = (ng + 3) & ~3; g.err = h->d_err; g.timeout_ns = 2000000000ull;
-  if (launch_adjoint(h, g, splits, pair_adj, s) != cudaSuccess) return DCOPF_ERR_CUDA;
+  if (launch_adjoint(h, L, g, splits, pair_adj, s) != cudaSuccess) return DCOPF_ERR_CUDA;
   k_reduce_min<<<B, 256, 0, s>>>(h->dev, splits, B, g.ldp, T.P.as<float>(), lambda, T.ld_g,
                                  T.X_hi.as<__nv_bfloat16>(), T.X_lo.as<__nv_bfloat16>(),
                                  w.x64.as<double>(), w.sumcost.as<double>(), w.sump.as<double>());
@@ -921,13 +956,17 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
   f.M = B; f.N = nl; f.K = ng; f.kb_per_split = (ng + GBK - 1) / GBK; f.epi = EPI_FLOW;
   f.f0 = w.f0.as<double>(); f.f = w.f.as<double>(); f.ldf = nl; f.err = h->d_err;
   f.timeout_ns = 2000000000ull;
-  if (launch_forward(h, f, pair_fwd, s) != cudaSuccess) return DCOPF_ERR_CUDA;
+  if (launch_forward(h, L, f, pair_fwd, s) != cudaSuccess) return DCOPF_ERR_CUDA;
   return run_eval_finish(h, B, outage, lambda, mh, ml, value, glam, ghi, glo, dispatch, s);
 }
 
 // ------------------------------------------------------------------ for other users
 bool tc_make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint64_t ld) {
   return make_map(m, ptr, rows, cols, ld, GBM);
+}
+bool tc_make_map_rows(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint64_t ld,
+                      uint32_t box_rows) {
+  return make_map(m, ptr, rows, cols, ld, box_rows);
 }
 
 // P[s][m][ldp] = the K-slice s of A[m][:] . B[n][:] (BF16 hi/lo split operands, three
@@ -992,39 +1031,62 @@ __global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
   const int ng = N.n_gen;
   const int k = outage ? outage[b] : -1;
   const double lam = st.lam[b];
-  // the in-loop value and the lambda gradient only steer the iteration (the bound is
+  // The in-loop value and the lambda gradient only steer the iteration (the bound is
   // certified in FP64 later): per-generator terms and warp sums in FP32, FP64 across
-  // warps.  w cancels (ctil + sigma lambda ~ -pi~), so it is formed in FP64.
+  // warps.  The reduced cost w = ctil + sigma lambda + pi~ is formed in FP32: its
+  // rounding there (a few 2^-24 of |ctil| + |sigma lambda|) is far below the error of
+  // the split BF16 products that give pi~.
+  const float lamf = (float)lam;
   float c = 0.f, p = 0.f, to = 0.f;
   const float kk = (float)(st.iter[b] + 1), wk = kk * kk;  // weight of the mean of the minimisers
-  for (int j = threadIdx.x; j < ng; j += blockDim.x) {
-    // split-K partials eight loads at a time, summed in split order (a missing term
-    // adds +0, which leaves the sum unchanged)
-    float s = 0.f;
+  const int nt = blockDim.x;
+  // two generators per thread and loop, every load in flight before the arithmetic;
+  // split-K partials summed in split order (a missing term adds +0)
+  for (int ja = threadIdx.x; ja < ng; ja += 2 * nt) {
+    const int jb = ja + nt;
+    const bool vb = jb < ng;
+    float sa = 0.f, sb = 0.f;
     for (int q0 = 0; q0 < splits; q0 += 8) {
-      float t[8];
+      float ta[8], tb[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) t[u] = q0 + u < splits ? P[((size_t)(q0 + u) * M + b) * ldp + j] : 0.f;
+      for (int u = 0; u < 8; ++u) {
+        const size_t row = ((size_t)(q0 + u) * M + b) * ldp;
+        ta[u] = q0 + u < splits ? P[row + ja] : 0.f;
+        tb[u] = (q0 + u < splits && vb) ? P[row + jb] : 0.f;
+      }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s += t[u];
+      for (int u = 0; u < 8; ++u) { sa += ta[u]; sb += tb[u]; }
     }
-    const double w = N.ctil[j] + N.sigma[j] * lam + (double)s;
-    const float x = inner_x<float>((float)w, N.mq32[j]);
-    if (st.xsum) st.xsum[(size_t)b * ng + j] += wk * x;
-    split_bf16(x, Xh + (size_t)b * ldx + j, Xl + (size_t)b * ldx + j);
-    c += fmaf(fmaf(N.mq32[j], x, N.ctil32[j]), x, N.cconst32[j]);
-    p += fmaf(N.sigma32[j], x, N.mid32[j]);
-    if (k >= 0) to = fmaf(N.phi32[(size_t)k * ng + j], x, to);
+    auto gen = [&](int j, float sj) {
+      const float mq = N.mq32[j];
+      const float w = fmaf(N.sigma32[j], lamf, N.ctil32[j]) + sj;
+      const float x = inner_x<float>(w, mq);
+      if (st.xsum) st.xsum[(size_t)b * ng + j] += wk * x;
+      split_bf16(x, Xh + (size_t)b * ldx + j, Xl + (size_t)b * ldx + j);
+      c += fmaf(fmaf(mq, x, N.ctil32[j]), x, N.cconst32[j]);
+      p += fmaf(N.sigma32[j], x, N.mid32[j]);
+      if (k >= 0) to = fmaf(N.phi32[(size_t)k * ng + j], x, to);
+    };
+    gen(ja, sa);
+    if (vb) gen(jb, sb);
   }
   c = warp_sum(c); p = warp_sum(p); to = warp_sum(to);
-  const int wid = threadIdx.x >> 5;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int RW = MIN_MAX_THREADS / 32;
-  if ((threadIdx.x & 31) == 0) { red[wid] = c; red[RW + wid] = p; red[2 * RW + wid] = to; }
+  if (lane == 0) { red[wid] = c; red[RW + wid] = p; red[2 * RW + wid] = to; }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double cs = 0.0, ps = 0.0, ts = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { cs += red[q]; ps += red[RW + q]; ts += red[2 * RW + q]; }
-    const double p = ps;
+  if (wid == 0) {
+    // the warps' partials in FP64, a shuffle tree over lanes (fixed order)
+    const int nw = (int)(blockDim.x >> 5);
+    double cs = lane < nw ? red[lane] : 0.0, ps = lane < nw ? red[RW + lane] : 0.0,
+           ts = lane < nw ? red[2 * RW + lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      cs += __shfl_xor_sync(0xffffffffu, cs, o);
+      ps += __shfl_xor_sync(0xffffffffu, ps, o);
+      ts += __shfl_xor_sync(0xffffffffu, ts, o);
+    }
+    if (lane != 0) return;
     bb.cost[b] = cs;
     bb.psum[b] = ps;
     if (st.wsum) st.wsum[b] += (double)wk;
@@ -1032,13 +1094,16 @@ __global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
     bb.lam_eval[b] = lam;
     // step t = iter + 1: scale decay^(t-1), bias corrections 1 - beta^t
     const double d = bb.pw[3 * b], b1 = bb.pw[3 * b + 1] * SP.beta1, b2 = bb.pw[3 * b + 2] * SP.beta2;
+    const float bc1 = (float)(1.0 - b1), bc2 = (float)(1.0 - b2);
     bb.stepf[4 * b] = (float)(SP.alpha * d);
-    bb.stepf[4 * b + 1] = (float)(1.0 - b1);
-    bb.stepf[4 * b + 2] = (float)(1.0 - b2);
+    bb.stepf[4 * b + 1] = bc1;
+    bb.stepf[4 * b + 2] = bc2;
     bb.pw[3 * b] = d * SP.decay;
     bb.pw[3 * b + 1] = b1;
     bb.pw[3 * b + 2] = b2;
-    const double g = p - demand[b], a = SP.alpha_lambda * d;
+    // lambda's step: the moments and lambda in FP64, the Adam / AdaGrad direction in
+    // FP32 (FP64 division and square root are slow on this part)
+    const double g = ps - demand[b], a = SP.alpha_lambda * d;
     double s1 = st.lam_s1[b], s2 = st.lam_s2[b], l = lam;
     if (SP.rule == DCOPF_GDM) {
       s1 = SP.rho * s1 + a * g;
@@ -1047,10 +1112,10 @@ __global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
     } else if (SP.rule == DCOPF_ADAM) {
       s1 = SP.beta1 * s1 + (1.0 - SP.beta1) * g;
       s2 = SP.beta2 * s2 + (1.0 - SP.beta2) * g * g;
-      l += a * (s1 / (1.0 - b1)) / (sqrt(s2 / (1.0 - b2)) + SP.eps);
+      l += a * (double)(((float)s1 / bc1) / (sqrtf((float)s2 / bc2) + (float)SP.eps));
     } else {
       s1 += g * g;
-      l += a * g / (sqrt(s1) + SP.eps);
+      l += a * (double)((float)g / (sqrtf((float)s1) + (float)SP.eps));
     }
     st.lam[b] = l;
     st.lam_s1[b] = s1;
@@ -1196,6 +1261,7 @@ struct TensorRun {
   StepEpi E{};
   int splits = 1, n_tiles = 0;
   int pair_adj = 0, pair_fwd = 0;  // product shapes, as launch_adjoint's `tiles`
+  LineSet ls;                      // the lines iterated on
   unsigned gi = 1;
   bool running = true;
 };
@@ -1204,12 +1270,30 @@ struct TensorRun {
 // first eta, on stream cs.
 static void tensor_init_state(TensorRun& R, cudaStream_t cs) {
   dcopf_dual* h = R.it.h;
-  const int B = R.it.B, nl = h->host.n_line;
+  const int B = R.it.B, nl = h->host.n_line, nk = R.ls.nl;
   TensorOps& T = h->tops;
-  k_init_state_f32(R.gi, cs, B, nl, R.p.warm_start, R.it.lam, R.it.mh, R.it.ml, R.it.target, R.p.gap,
-                   R.st);
+  if (R.ls.kept) {
+    // the warm start of every line into the (still unused) saved-point buffers, then
+    // the rows of the kept lines into the compact state; the moments start at zero
+    SolveState<float> tmp = R.st;
+    tmp.mu_hi = h->bb.v.sv_hi;
+    tmp.mu_lo = h->bb.v.sv_lo;
+    tmp.best_hi = h->scr.full.as<float>();
+    tmp.best_lo = tmp.best_hi + (size_t)B * nl;
+    k_init_state_f32(R.gi, cs, B, nl, R.p.warm_start, R.it.lam, R.it.mh, R.it.ml, R.it.target, R.p.gap,
+                     tmp);
+    const unsigned g = (unsigned)std::min<long long>(((long long)B * nk + 255) / 256, 4096);
+    k_screen_compact_rows<<<g, 256, 0, cs>>>(B, nl, nk, R.ls.kept, tmp.mu_hi, R.st.mu_hi);
+    k_screen_compact_rows<<<g, 256, 0, cs>>>(B, nl, nk, R.ls.kept, tmp.mu_lo, R.st.mu_lo);
+    k_screen_compact_rows<<<g, 256, 0, cs>>>(B, nl, nk, R.ls.kept, tmp.best_hi, R.st.best_hi);
+    k_screen_compact_rows<<<g, 256, 0, cs>>>(B, nl, nk, R.ls.kept, tmp.best_lo, R.st.best_lo);
+    h->launches += 4;
+  } else {
+    k_init_state_f32(R.gi, cs, B, nl, R.p.warm_start, R.it.lam, R.it.mh, R.it.ml, R.it.target, R.p.gap,
+                     R.st);
+  }
   k_bt_init<<<(B + 255) / 256, 256, 0, cs>>>(B, h->bb.v);
-  k_split_eta<float><<<B, 256, 0, cs>>>(nl, T.ld_l, R.st.mu_hi, R.st.mu_lo, R.it.outage,
+  k_split_eta<float><<<B, 256, 0, cs>>>(nk, R.ls.ld_l, R.st.mu_hi, R.st.mu_lo, R.it.outage,
                                         h->ws.u32.as<float>(), T.H_hi.as<__nv_bfloat16>(),
                                         T.H_lo.as<__nv_bfloat16>());
   h->launches += 3;
@@ -1227,7 +1311,7 @@ static dcopf_status tune_tensor_shapes(TensorRun& R, cudaStream_t cs) {
   const int B = R.it.B, ng = h->host.n_gen;
   TensorOps& T = h->tops;
   Workspace& w = h->ws;
-  const int kb = (h->host.n_line + GBK - 1) / GBK;
+  const int kb = (R.ls.nl + GBK - 1) / GBK;
   const bool pair_ok = B > GBM && h->tiles_mode != 1;
   const bool single_ok = h->tiles_mode <= 1 || B <= GBM;
   const int tv_lo = h->tiles_mode == 3 ? 2 : 1, tv_hi = h->tiles_mode == 2 ? 1 : 2;
@@ -1286,7 +1370,7 @@ static dcopf_status tune_tensor_shapes(TensorRun& R, cudaStream_t cs) {
     float ms = 0.f;
     out = timed(
         [&] {
-          cudaError_t e = launch_adjoint(h, g, c.splits, c.tiles, cs);
+          cudaError_t e = launch_adjoint(h, R.ls, g, c.splits, c.tiles, cs);
           k_bt_minimize<<<B, minimize_threads(h, B), 0, cs>>>(h->dev, c.splits, B, g.ldp, T.P.as<float>(),
                                                               R.st, h->bb.v, R.P, T.ld_g,
                                                               T.X_hi.as<__nv_bfloat16>(),
@@ -1313,7 +1397,7 @@ static dcopf_status tune_tensor_shapes(TensorRun& R, cudaStream_t cs) {
     for (int tv = single_ok ? 0 : tv_lo; tv <= tv_hi && out == DCOPF_OK; ++tv) {
       if (tv > 0 && tv < tv_lo) continue;
       float ms = 0.f;
-      out = timed([&] { return launch_forward(h, R.gf, tv, cs); }, &ms);
+      out = timed([&] { return launch_forward(h, R.ls, R.gf, tv, cs); }, &ms);
       if (h->verbose) fprintf(stderr, "dcopf: batch %d forward %s: %.1f us\n", B, kTiles[tv], 1e3f * ms / 3.f);
       if (out == DCOPF_OK && ms < bf) {
         bf = ms;
@@ -1329,6 +1413,7 @@ static dcopf_status tune_tensor_shapes(TensorRun& R, cudaStream_t cs) {
     return DCOPF_ERR_CUDA;
   if (derr) return (dcopf_status)derr;
   h->tune_B = B;
+  h->tune_nl = R.ls.nl;
   h->tune_splits = bc.splits;
   h->tune_kbps = best_per;
   h->tune_pair_adj = bc.tiles;
@@ -1347,15 +1432,48 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   dcopf_status r;
   if ((r = ensure_tensor_operands(h)) || (r = ensure_tensor_batch(h, B))) return r;
   if ((r = ensure_state<float>(h, B, &R.st))) return r;
-  const int nl = h->host.n_line, ng = h->host.n_gen;
+  const int n_line = h->host.n_line, ng = h->host.n_gen;
+  TensorOps& T = h->tops;
+  Workspace& w = h->ws;
+  const dcopf_solve_params& p = R.p;
+  R.ls = full_lines(h);
+  if (p.screen_lines && !R.it.outage) {
+    // constraint screening: the iterations carry only the lines that can bind
+    if ((r = screen_batch(h, B, s))) return r;
+    LineScreen& S = h->scr;
+    const int nk = S.nk;
+    if (S.f0c.alloc((size_t)B * nk * sizeof(float)) != cudaSuccess ||
+        S.full.alloc((size_t)2 * B * n_line * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return DCOPF_ERR_OOM;
+    }
+    if (S.map_B != B) {
+      if (!tc_make_map(&S.m_H_hi, T.H_hi.p, B, nk, S.ld_lk) || !tc_make_map(&S.m_H_lo, T.H_lo.p, B, nk, S.ld_lk))
+        return DCOPF_ERR_CUDA;
+      S.map_B = B;
+    }
+    const unsigned g = (unsigned)std::min<long long>(((long long)B * nk + 255) / 256, 4096);
+    k_screen_compact_rows<<<g, 256, 0, s>>>(B, n_line, nk, S.kept.as<int>(), w.f0_32.as<float>(),
+                                            S.f0c.as<float>());
+    h->launches += 1;
+    LineSet& L = R.ls;
+    L.nl = nk;
+    L.ld_l = S.ld_lk;
+    L.H_hi = &S.m_H_hi; L.H_lo = &S.m_H_lo;
+    L.phit_hi = &S.m_phit_hi; L.phit_lo = &S.m_phit_lo; L.phit_hi96 = &S.m_phit_hi96; L.phit_lo96 = &S.m_phit_lo96;
+    L.phi_hi = &S.m_phi_hi; L.phi_lo = &S.m_phi_lo; L.phi_hi96 = &S.m_phi_hi96; L.phi_lo96 = &S.m_phi_lo96;
+    L.fmax = S.lim.as<float>();
+    L.fmin = S.lim.as<float>() + nk;
+    L.f0 = S.f0c.as<float>();
+    L.kept = S.kept.as<int>();
+    L.pos = S.pos.as<int>();
+  }
+  const int nl = R.ls.nl;
   R.n_tiles = (nl + STEP_CHUNK - 1) / STEP_CHUNK;
   if ((r = ensure_batch_bufs(h, B, R.n_tiles))) return r;
   const int ldF = (nl + 3) & ~3;
   if (h->bb.F.alloc((size_t)B * ldF * sizeof(float)) != cudaSuccess) return DCOPF_ERR_OOM;
-  TensorOps& T = h->tops;
-  Workspace& w = h->ws;
   BatchView& bb = h->bb.v;
-  const dcopf_solve_params& p = R.p;
   R.st.has_target = R.it.target != nullptr;
   StepArgs& P = R.P;
   P.rule = p.rule; P.as_printed = p.as_printed; P.alpha = p.alpha;
@@ -1369,10 +1487,10 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
     return DCOPF_ERR_CUDA;
   if (cudaEventRecord(h->tev, s) != cudaSuccess || cudaStreamWaitEvent(cs, h->tev, 0) != cudaSuccess)
     return DCOPF_ERR_CUDA;
-  R.gi = std::min<unsigned>((unsigned)(((long long)B * nl + 255) / 256), 4096);
+  R.gi = std::min<unsigned>((unsigned)(((long long)B * n_line + 255) / 256), 4096);
   tensor_init_state(R, cs);
   int kbps;
-  adjoint_split(h, B, &R.splits, &kbps);
+  adjoint_split(h, B, nl, &R.splits, &kbps);
   GemmArgs& ga = R.ga;
   ga.M = B; ga.N = ng; ga.K = nl; ga.kb_per_split = kbps; ga.epi = EPI_PARTIAL;
   ga.P = T.P.as<float>(); ga.ldp = (ng + 3) & ~3; ga.err = h->d_err; ga.timeout_ns = 2000000000ull;
@@ -1381,18 +1499,31 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   gf.F32 = h->bb.F.as<float>(); gf.ldf32 = ldF;
   gf.err = h->d_err; gf.timeout_ns = 2000000000ull;
   StepEpi& E = R.E;
-  E.P = to_float_args(P); E.F = gf.F32; E.ldF = ldF; E.f0 = w.f0_32.as<float>(); E.u = w.u32.as<float>();
+  E.P = to_float_args(P); E.F = gf.F32; E.ldF = ldF; E.f0 = R.ls.f0; E.u = w.u32.as<float>();
   E.outage = R.it.outage; E.tout = bb.tout;
-  E.fmax = h->dev.fmax32; E.fmin = h->dev.fmin32; E.iter = R.st.iter; E.frozen = bb.frozen;
+  E.fmax = R.ls.fmax; E.fmin = R.ls.fmin; E.iter = R.st.iter; E.frozen = bb.frozen;
   E.stepf = bb.stepf;
   E.best_iter = R.st.best_iter;
   E.mu_hi[0] = R.st.mu_hi; E.mu_hi[1] = bb.mu2_hi; E.mu_hi[2] = bb.mu3_hi;
   E.mu_lo[0] = R.st.mu_lo; E.mu_lo[1] = bb.mu2_lo; E.mu_lo[2] = bb.mu3_lo;
   E.sv_hi = bb.sv_hi; E.sv_lo = bb.sv_lo;
   E.s1_hi = R.st.s1_hi; E.s2_hi = R.st.s2_hi; E.s1_lo = R.st.s1_lo; E.s2_lo = R.st.s2_lo;
-  E.Hh = T.H_hi.as<__nv_bfloat16>(); E.Hl = T.H_lo.as<__nv_bfloat16>(); E.ldh = T.ld_l;
+  E.Hh = T.H_hi.as<__nv_bfloat16>(); E.Hl = T.H_lo.as<__nv_bfloat16>(); E.ldh = R.ls.ld_l;
   E.line_part = bb.line_part; E.out_part = bb.out_part; E.n_tiles = R.n_tiles;
-  if (h->tune_B != B) {
+  if (h->timing && !h->kev[0])
+    for (int q = 0; q < 6; ++q)
+      if (cudaEventCreate(&h->kev[q]) != cudaSuccess) return DCOPF_ERR_CUDA;
+  if (h->shape_adj >= 0 && (h->tune_B != B || h->tune_nl != nl)) {  // shapes fixed at create: no timing
+    const int kb = (nl + GBK - 1) / GBK;
+    const bool pairs_fit = B > GBM;
+    h->tune_B = B;
+    h->tune_nl = nl;
+    h->tune_kbps = (kb + h->shape_splits - 1) / h->shape_splits;
+    h->tune_splits = (kb + h->tune_kbps - 1) / h->tune_kbps;
+    h->tune_pair_adj = pairs_fit ? h->shape_adj : 0;
+    h->tune_pair_fwd = pairs_fit ? h->shape_fwd : 0;
+  }
+  if (h->tune_B != B || h->tune_nl != nl) {
     if ((r = tune_tensor_shapes(R, cs))) return r;
     tensor_init_state(R, cs);  // the timed runs stepped lambda: start again
   }
@@ -1410,25 +1541,37 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
 // cs, which is capturing.
 static bool tensor_enqueue_chunk(TensorRun& R, int chunk, cudaStream_t cs) {
   dcopf_dual* h = R.it.h;
-  const int B = R.it.B, nl = h->host.n_line;
+  const int B = R.it.B, nl = R.ls.nl;
   TensorOps& T = h->tops;
   Workspace& w = h->ws;
   BatchView& bb = h->bb.v;
   bool ok = true;
   for (int it = 0; it < chunk && ok; ++it) {
-    ok &= launch_adjoint(h, R.ga, R.splits, R.pair_adj, cs) == cudaSuccess;
+    // timing on: event nodes around the kernels of the round's last iteration
+    const bool mark = h->timing && h->kev[0] && it == chunk - 1;
+    // (external event-record nodes: a plain record during capture only orders streams)
+    auto ev = [&](int q) {
+      if (mark) ok &= cudaEventRecordWithFlags(h->kev[q], cs, cudaEventRecordExternal) == cudaSuccess;
+    };
+    ev(0);
+    ok &= launch_adjoint(h, R.ls, R.ga, R.splits, R.pair_adj, cs) == cudaSuccess;
+    ev(1);
     k_bt_minimize<<<B, minimize_threads(h, B), 0, cs>>>(h->dev, R.splits, B, R.ga.ldp, T.P.as<float>(), R.st, bb, R.P,
                                      T.ld_g, T.X_hi.as<__nv_bfloat16>(), T.X_lo.as<__nv_bfloat16>(),
                                      R.it.outage, w.demand.as<double>());
-    ok &= launch_forward(h, R.gf, R.pair_fwd, cs) == cudaSuccess;
+    ev(2);
+    ok &= launch_forward(h, R.ls, R.gf, R.pair_fwd, cs) == cudaSuccess;
+    ev(3);
     if (nl % 4 == 0 && R.E.ldF % 4 == 0 && R.E.ldh % 4 == 0)
       k_bt_step4<<<dim3(R.n_tiles, B), STEP_THREADS, 0, cs>>>(R.E, nl);
     else
       k_bt_step<<<dim3(R.n_tiles, B), STEP_THREADS, 0, cs>>>(R.E, nl);
-    k_bt_finalize<<<(B + 3) / 4, 128, 0, cs>>>(B, T.ld_l, R.p.max_iters, R.p.tol, R.st, bb,
+    ev(4);
+    k_bt_finalize<<<(B + 3) / 4, 128, 0, cs>>>(B, R.ls.ld_l, R.p.max_iters, R.p.tol, R.st, bb,
                                                R.it.outage, w.demand.as<double>(),
                                                T.H_hi.as<__nv_bfloat16>(),
                                                T.H_lo.as<__nv_bfloat16>());
+    ev(5);
   }
   return ok;
 }
@@ -1440,14 +1583,28 @@ static bool tensor_enqueue_chunk(TensorRun& R, int chunk, cudaStream_t cs) {
 static dcopf_status tensor_stage_certify(TensorRun& R, cudaStream_t cs, cudaStream_t cc,
                                          cudaEvent_t staged_ev, cudaEvent_t done_ev) {
   dcopf_dual* h = R.it.h;
-  const int B = R.it.B, nl = h->host.n_line;
+  const int B = R.it.B, nl = R.ls.nl, n_line = h->host.n_line;
   BatchView& bb = h->bb.v;
   int* snap = h->bb.snap.as<int>();
   k_bt_select<<<dim3((nl + 255) / 256, B), 256, 0, cs>>>(B, nl, R.st, bb, snap);
+  const float* bh = R.st.best_hi;
+  const float* bl = R.st.best_lo;
+  if (R.ls.kept) {
+    // the certificate evaluates the full problem: the staged points on every line,
+    // zero on the screened ones
+    float* fh = h->scr.full.as<float>();
+    float* fl = fh + (size_t)B * n_line;
+    const unsigned g = (unsigned)std::min<long long>(((long long)B * n_line + 255) / 256, 4096);
+    k_screen_scatter_rows<<<g, 256, 0, cs>>>(B, n_line, nl, R.ls.pos, R.st.best_hi, fh);
+    k_screen_scatter_rows<<<g, 256, 0, cs>>>(B, n_line, nl, R.ls.pos, R.st.best_lo, fl);
+    h->launches += 2;
+    bh = fh;
+    bl = fl;
+  }
   if (cudaEventRecord(staged_ev, cs) != cudaSuccess || cudaStreamWaitEvent(cc, staged_ev, 0) != cudaSuccess)
     return DCOPF_ERR_CUDA;
-  dcopf_status r = run_certify_t<float>(h, B, R.it.loads, R.it.outage, R.st.best_lam, R.st.best_hi,
-                                        R.st.best_lo, R.st.cert, nullptr, snap, R.st.done, cc, true);
+  dcopf_status r = run_certify_t<float>(h, B, R.it.loads, R.it.outage, R.st.best_lam, bh, bl, R.st.cert,
+                                        nullptr, snap, R.st.done, cc, true);
   if (r) return r;
   h->launches += 1;
   if (cudaEventRecord(done_ev, cc) != cudaSuccess) return DCOPF_ERR_CUDA;
@@ -1469,7 +1626,12 @@ static dcopf_status tensor_accept(TensorRun& R, int* d_active, cudaStream_t cs, 
 static dcopf_status tensor_finish(TensorRun& R, cudaStream_t s) {
   dcopf_dual* h = R.it.h;
   cudaStream_t cs = h->tstream;
-  k_output_f32(R.gi, cs, R.it.B, h->host.n_line, R.st, R.it.lam, R.it.mh, R.it.ml, R.it.bound,
+  SolveState<float> out = R.st;
+  if (R.ls.kept) {  // the full-length copies of the last staged points
+    out.best_hi = h->scr.full.as<float>();
+    out.best_lo = out.best_hi + (size_t)R.it.B * h->host.n_line;
+  }
+  k_output_f32(R.gi, cs, R.it.B, h->host.n_line, out, R.it.lam, R.it.mh, R.it.ml, R.it.bound,
                R.it.iters, R.it.status);
   h->launches += 1;
   if (R.p.mean_dispatch) launch_mean_out(h, R.it.B, R.st, R.p.mean_dispatch, cs);
@@ -1596,6 +1758,16 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
       cudaEventElapsedTime(&ms, h0->ev0, h0->ev1);
       h0->t_iter_ms += ms;
       h0->t_iter_launches += per_chunk * n;
+    }
+    for (int i = 0; i < n; ++i) {
+      dcopf_dual* hi = items[i].h;
+      if (!hi->timing || !hi->kev[0] || !act[i]) continue;
+      float km[5];
+      bool kok = true;
+      for (int q = 0; q < 5; ++q) kok &= cudaEventElapsedTime(&km[q], hi->kev[q], hi->kev[q + 1]) == cudaSuccess;
+      if (!kok) { cudaGetLastError(); continue; }
+      for (int q = 0; q < 5; ++q) hi->t_kernel_ms[q] += km[q];
+      hi->t_kernel_samples += 1;
     }
     int any = 0;
     for (int i = 0; i < n; ++i) {

@@ -150,6 +150,25 @@ struct TensorOps {
   CUtensorMap m_H_hi, m_H_lo, m_X_hi, m_X_lo;
 };
 
+// Constraint screening of the batched solve (k_screen.cu): the lines kept for the
+// iterations and their compact operands, and the knapsack bounds of every line for a
+// range of the balance right-hand side.
+struct LineScreen {
+  DBuf env, knap, keep;          // batch envelope [2][n_line] + range [2]; bounds [2][n_line]; flags
+  bool knap_valid = false;
+  double rlo = 0.0, rhi = 0.0;   // balance range the knapsack bounds hold for
+  bool ready = false;            // the compact operands below match kept_host
+  int nk = 0, ld_lk = 0;         // kept lines (a multiple of 8) and their row stride
+  std::vector<int> kept_host;
+  DBuf kept, pos;                // [nk] line of each compact row; [n_line] compact row or -1
+  DBuf phi_hi, phi_lo, phit_hi, phit_lo, lim;  // compact BF16 operands; fmax, fmin [2][nk]
+  CUtensorMap m_phi_hi, m_phi_lo, m_phit_hi, m_phit_lo;
+  CUtensorMap m_phi_hi96, m_phi_lo96, m_phit_hi96, m_phit_lo96;
+  int map_B = 0;                 // batch size of the maps below
+  CUtensorMap m_H_hi, m_H_lo;    // the adjoint's A operand [B][ld_lk]
+  DBuf f0c, full;                // compact base flows [B][nk]; full-length best point [2][B][n_line]
+};
+
 // Extra per-instance state of the batched tensor-core solve (device pointers).
 struct BatchView {
   int n_tiles = 0;             // line tiles of the forward product
@@ -205,6 +224,7 @@ struct dcopf_dual {
   dcopf::DBuf dense_ha, dense_part;  // dense FP64 PTDF [n_line][n_bus] (built on first use)
   dcopf::DBuf dense_colabs;           // [n_bus] column sums of |H_a| (price rounding bound)
   dcopf::BatchBufs bb;
+  dcopf::LineScreen scr;
   dcopf::PrimalBufs pb;
   int* d_err = nullptr;  // sticky device error word
   unsigned* d_bar = nullptr;  // grid-barrier counters
@@ -221,6 +241,12 @@ struct dcopf_dual {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double t_iter_ms = 0.0;
   long long t_iter_launches = 0, t_evals = 0;
+  // per-kernel timing of the batched solve (timing on): events around the adjoint,
+  // minimiser, forward, step and value kernels of the last iteration of every round,
+  // recorded inside the iteration graph
+  cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double t_kernel_ms[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  long long t_kernel_samples = 0;
   int sm_count = 0;
   int fused_C = 0, fused_G = 0;  // cluster shape of the fused kernel (chosen on first use)
   // layout of that shape, validated once (occupancy queries cost host time per solve)
@@ -241,12 +267,16 @@ struct dcopf_dual {
   // split-K of the batched adjoint GEMM chosen by timing (for batch size tune_B), and
   // whether the adjoint and the forward product run on CTA pairs (256 x 256 tiles)
   // rather than single CTAs (128 x 128)
-  int tune_B = 0, tune_splits = 0, tune_kbps = 0;
+  int tune_B = 0, tune_nl = 0, tune_splits = 0, tune_kbps = 0;
   int tune_pair_adj = 0, tune_pair_fwd = 0;  // 0 single CTAs, 1 pairs of 256 columns, 2 of 192
   // DCOPF_TENSOR_TILES (read at create): 0 = choose by timing, 1 = single CTAs only,
   // 2 / 3 = CTA pairs of 256 x 256 / 256 x 192 tiles only (where the batch has more than
   // 128 instances)
   int tiles_mode = 0;
+  // DCOPF_TENSOR_SHAPE="a,s,f" (read at create): the adjoint's tiles (0 single, 1 pairs
+  // of 256, 2 pairs of 192), its split-K factor, the forward's tiles; no timing (for
+  // profilers, whose per-launch overhead changes what the timing would pick)
+  int shape_adj = -1, shape_splits = 0, shape_fwd = -1;
   size_t smem_optin = 0;
   bool verbose = false;
   std::string last_error;
@@ -341,6 +371,13 @@ dcopf_status solve_tensor(dcopf_dual* h, int batch, const double* loads, const i
 // maps of row-major BF16 [rows][ld] with cols valid columns (K-major operands), and
 // split-K partial products C = A B^T.
 bool tc_make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint64_t ld);
+bool tc_make_map_rows(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint64_t ld,
+                      uint32_t box_rows);
+// Constraint screening of a batch (k_screen.cu): base flows in ws.f0, demands in
+// ws.demand; leaves h->scr ready with the kept lines and their compact operands.
+dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s);
+__global__ void k_screen_compact_rows(int B, int nl, int nk, const int* kept, const float* src, float* dst);
+__global__ void k_screen_scatter_rows(int B, int nl, int nk, const int* pos, const float* src, float* dst);
 cudaError_t tc_gemm_partial(const CUtensorMap& Ah, const CUtensorMap& Al, const CUtensorMap& Bh,
                             const CUtensorMap& Bl, int M, int N, int K, float* P, int ldp,
                             int max_splits, int sm_count, int* err, int* splits_used,

@@ -180,6 +180,26 @@ class DcopfDual:
                    "read_timing")
         return ms.value, nl.value, ne.value
 
+    def screened_lines(self) -> np.ndarray:
+        """``dcopf_dual_screened_lines``: boolean [n_line], True for the lines the last
+        screened solve iterated on (all False before any screened solve)."""
+        m = np.zeros(self.n_line, dtype=np.uint8)
+        n = C.c_int32()
+        _lib.check(self.lib.dcopf_dual_screened_lines(self.h, C.byref(n), m.ctypes.data_as(C.POINTER(C.c_uint8))),
+                   "dcopf_dual_screened_lines")
+        return m.astype(bool)
+
+    KERNELS = ("adjoint", "minimiser", "forward", "step", "value")
+
+    def read_kernel_timing(self):
+        """``dcopf_dual_read_kernel_timing``: {kernel: summed ms} over the sampled
+        iterations of batched solves, and the sample count; then reset."""
+        ms = (C.c_double * 5)()
+        n = C.c_int64()
+        _lib.check(self.lib.dcopf_dual_read_kernel_timing(self.h, ms, C.byref(n)),
+                   "dcopf_dual_read_kernel_timing")
+        return dict(zip(self.KERNELS, list(ms))), n.value
+
     def workspace_limit(self, limit_bytes: int | None = None) -> int:
         """``dcopf_dual_workspace_limit``: sets the workspace budget in bytes (0 = none;
         None leaves it unchanged) and returns the bytes the workspaces hold now."""
@@ -256,7 +276,7 @@ class DcopfDual:
         return upper, status, disp, viol
 
     def _params(self, rule, precision, path, max_iters, alpha, alpha_lambda, rho, beta1, beta2, eps,
-                decay, gap, tol, as_printed, check_every, warm=False):
+                decay, gap, tol, as_printed, check_every, screen=False, warm=False):
         p = _lib.SolveParams()
         self.lib.dcopf_solve_params_default(C.byref(p))
         p.rule = _lib.RULE[rule]
@@ -266,6 +286,7 @@ class DcopfDual:
         p.warm_start = 1 if warm else 0
         p.as_printed = 1 if as_printed else 0
         p.check_every = int(check_every)
+        p.screen_lines = 1 if screen else 0
         p.alpha, p.alpha_lambda, p.rho = float(alpha), float(alpha_lambda), float(rho)
         p.beta1, p.beta2, p.eps, p.decay = float(beta1), float(beta2), float(eps), float(decay)
         p.gap, p.tol = float(gap), float(tol)
@@ -298,14 +319,16 @@ class DcopfDual:
               max_iters=5000, alpha=1000.0, alpha_lambda=0.0, rho=0.9, beta1=0.9, beta2=0.999,
               eps=1e-8, decay=1.0, gap=1e-3, tol=0.0, target=None, warm=None,
               as_printed=False, check_every=1, out: SolveResult | None = None,
-              mean_dispatch: bool = False) -> SolveResult:
+              mean_dispatch: bool = False, screen: bool = False) -> SolveResult:
         """``dcopf_dual_solve_batch``.  ``target`` ([B] optimal costs) enables the
         certified-gap stop; ``warm`` = (lambda, mu_hi, mu_lo) warm start; ``out`` (from
         ``new_result``) receives the results instead of new tensors; ``mean_dispatch``
-        also returns the k^2-weighted mean of the minimisers (a primal candidate)."""
+        also returns the k^2-weighted mean of the minimisers (a primal candidate); ``screen``
+        turns on constraint screening (batched tensor-core solves without outages)."""
         loads, outg, tgt, r = self._solve_arrays(loads, outage, target, warm, out)
         p = self._params(rule, precision, path, max_iters, alpha, alpha_lambda, rho, beta1, beta2,
-                         eps, decay, gap, tol, as_printed, check_every, warm=warm is not None)
+                         eps, decay, gap, tol, as_printed, check_every, screen=screen,
+                         warm=warm is not None)
         p.target_value = None if tgt is None else tgt.data_ptr()
         if mean_dispatch:
             if r.mean_dispatch is None or r.mean_dispatch.shape != (r.lam.shape[0], self.n_gen):
@@ -322,7 +345,7 @@ class DcopfDual:
 
 _SOLVE_DEFAULTS = dict(rule="adam", precision="bf16x3", path="batched", max_iters=5000,
                       alpha=1000.0, alpha_lambda=0.0, rho=0.9, beta1=0.9, beta2=0.999, eps=1e-8,
-                      decay=1.0, gap=1e-3, tol=0.0, as_printed=False, check_every=1)
+                      decay=1.0, gap=1e-3, tol=0.0, as_printed=False, check_every=1, screen=False)
 
 
 def solve_group(duals, loads, outage=None, target=None, warm=None, per_network=None,

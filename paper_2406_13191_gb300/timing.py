@@ -1,6 +1,6 @@
 """Timing utility for the library's paths on the seeded synthetic workloads.
 
-    python -m paper_2406_13191_gb300.timing batched --config 2 --batch 1024 --iters 16
+    python -m paper_2406_13191_gb300.timing batched --config 2 --batch 1024 --iters 16 [--screen]
     python -m paper_2406_13191_gb300.timing certify --config 1 --batch 1
     python -m paper_2406_13191_gb300.timing fused --config 1 --repeat 3
     python -m paper_2406_13191_gb300.timing group --iters 400
@@ -51,12 +51,12 @@ def _seeded_point(rng, batch, n_line, density=0.1):
     return lam, mh, np.zeros_like(mh)
 
 
-def batched(cfg, batch, iters, verbose=False):
+def batched(cfg, batch, iters, verbose=False, screen=False):
     w = synth.workload(cfg, batch=batch)
     g = DcopfDual(w.net, device=0, verbose=verbose)
     out = w.outage if (w.outage >= 0).any() else None
     kw = dict(rule="adam", alpha=4000.0 if w.net.is_qp else 1000.0, beta1=0.95, beta2=0.999,
-              decay=0.997, max_iters=iters, path="batched", precision="bf16x3")
+              decay=0.997, max_iters=iters, path="batched", precision="bf16x3", screen=screen)
     g.solve(w.loads, outage=out, **kw)                 # warm-up (graph capture, operands)
     g.set_timing(True)
     g.read_timing()
@@ -67,7 +67,8 @@ def batched(cfg, batch, iters, verbose=False):
     wall = time.perf_counter() - t0
     ms, launches, evals = g.read_timing()
     per_iter_us = 1e3 * ms / max(1.0, evals / batch)
-    print(json.dumps(dict(mode="batched", config=cfg, batch=batch, iters=iters,
+    print(json.dumps(dict(mode="batched", config=cfg, batch=batch, iters=iters, screen=screen,
+                          kept_lines=int(g.screened_lines().sum()) if screen else w.net.n_line,
                           wall_ms=1e3 * wall, iteration_kernels_ms=ms,
                           us_per_batched_iteration=per_iter_us,
                           instance_iterations_per_s=evals / (ms * 1e-3),
@@ -206,7 +207,7 @@ def mlp(batch, steps):
     print(json.dumps(res))
 
 
-def togap(cfg, repeat=2):
+def togap(cfg, repeat=2, screen=False):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if cfg == 2:
         gam = json.load(open(os.path.join(root, "tests", "golden", "study_gamma.json")))["4600"]
@@ -221,6 +222,7 @@ def togap(cfg, repeat=2):
     O = torch.tensor(w.outage[ok], device="cuda") if (w.outage >= 0).any() else None
     Td = torch.tensor(T, device="cuda")
     g = DcopfDual(w.net, device=0)
+    kw = dict(kw, screen=screen)
     g.solve(L, outage=O, target=Td, path="batched", precision="bf16x3", **kw)
     best = None
     for _ in range(repeat):
@@ -354,9 +356,10 @@ def main():
     ap.add_argument("--iters", type=int, default=16)
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--verbose", action="store_true", help="library setup and tuning messages")
+    ap.add_argument("--screen", action="store_true", help="constraint screening (batched, togap)")
     a = ap.parse_args()
     if a.mode == "batched":
-        batched(a.config, a.batch, a.iters, a.verbose)
+        batched(a.config, a.batch, a.iters, a.verbose, a.screen)
     elif a.mode == "certify":
         certify(a.config, a.batch)
     elif a.mode == "group":
@@ -366,7 +369,7 @@ def main():
     elif a.mode == "mlp":
         mlp(a.batch, a.iters)
     elif a.mode == "togap":
-        togap(a.config)
+        togap(a.config, screen=a.screen)
     elif a.mode == "primal":
         primal(a.batch)
     elif a.mode == "sparse":
