@@ -153,6 +153,14 @@ typedef struct {
                                  the k-th weighted by k^2 (p.u.); a candidate for
                                  dcopf_dual_primal_bound (averages of a dual method's
                                  minimisers approach the primal optimum) */
+  int32_t qp_dual_s;  /* 1 = quadratic costs: ascend on eq. (16)'s dual g_q(lambda, mu, s)
+                         with s (one per generator, free, starting at 0, mu's step size)
+                         as a third ascent variable (Section 3.2, Remark 2) instead of
+                         the closed form max_s g_q; the in-loop value is g_q, the
+                         certificate still evaluates (lambda, mu) in closed form, which
+                         bounds at least as tightly.  DCOPF_PATH_PLAIN only, else
+                         DCOPF_ERR_UNSUPPORTED; 0 = the closed form */
+  int32_t reserved;
 } dcopf_solve_params;
 
 /* Library version string. */

@@ -221,6 +221,81 @@ def evaluate(net: Net, loads, lam, mu_hi, mu_lo):
     return val, gl, ghi, glo, p
 
 
+def evaluate_qp_s(net: Net, can, loads, lam, mu_hi, mu_lo, s):
+    """The QP dual of eq. (16) with s as a variable (Section 3.2, Remark 2), in the
+    canonical form of eq. (2) built by Appendix A1 (``can = canonical(net, loads)``):
+
+        g_q(lambda, mu, s) = -||c + A^T lambda + C^T mu - sqrt(M) s||_1 - s^T s / 4
+                             - lambda^T b - mu^T d (+ the constant of the substitution).
+
+    The inner minimiser over the unit box is x* = -sign(w), w = c + A^T lambda + C^T mu -
+    sqrt(M) s (0 where w = 0), and the supergradient is (A x* - b, C x* - d,
+    -sqrt(M) x* - s / 2).  Returns (value, g_lambda, g_mu_hi, g_mu_lo, g_s, p*) with the
+    mu gradients split into the two flow-limit rows of C (f - f_max, f_min - f)."""
+    mu = np.concatenate([np.asarray(mu_hi, dtype=np.float64), np.asarray(mu_lo, dtype=np.float64)])
+    s = np.asarray(s, dtype=np.float64)
+    sq = np.sqrt(can["M"])
+    w = can["c"] + can["A"].T @ np.atleast_1d(lam) + can["C"].T @ mu - sq * s
+    x = -np.sign(w)
+    value = dual_value_canonical_qp(can, lam, mu, s)
+    gl = float((can["A"] @ x - can["b"])[0])
+    gmu = can["C"] @ x - can["d"]
+    nl = net.n_line
+    return value, gl, gmu[:nl], gmu[nl:], -sq * x - 0.5 * s, can["mid"] + can["sigma"] * x
+
+
+def solve_qp_s(net: Net, loads, rule="adam", alpha=1.0, rho=0.9, beta1=0.9, beta2=0.999,
+               eps=1e-8, decay=1.0, max_iters=1000, alpha_lambda=None, target=None, gap=1e-3,
+               record=False):
+    """Projected ascent on eq. (16)'s dual in (lambda, mu, s) (Section 3.2, Remark 2),
+    with the rules of ``solve`` (Section 3.3): mu >= 0 projected after every step, lambda
+    and s free, s with mu's step size alpha.  Starts from lambda = mu = s = 0.  The best
+    point is the one with the largest g_q; ``best_closed`` is the closed-form dual value
+    g(lambda, mu) = max_s g_q at that point (the bound a certificate of (lambda, mu)
+    gives).  Stops when best_closed reaches target (1 - gap) if a target is given."""
+    loads = np.asarray(loads, dtype=np.float64)
+    can = canonical(net, loads)
+    nl, ng = net.n_line, net.n_gen
+    a_l = alpha if alpha_lambda is None else alpha_lambda
+    th = dict(lam=np.zeros(1), mh=np.zeros(nl), ml=np.zeros(nl), s=np.zeros(ng))
+    m1 = {k: np.zeros_like(v) for k, v in th.items()}
+    m2 = {k: np.zeros_like(v) for k, v in th.items()}
+    best, best_closed, best_pt, hist, pts = -np.inf, -np.inf, None, [], []
+    it = 0
+    for it in range(1, max_iters + 1):
+        val, gl, gh, go, gs, _ = evaluate_qp_s(net, can, loads, th["lam"][0], th["mh"], th["ml"], th["s"])
+        hist.append(val)
+        if record:
+            pts.append({k: v.copy() for k, v in th.items()})
+        if val > best:
+            best = val
+            best_pt = {k: v.copy() for k, v in th.items()}
+            best_closed = dual_value_prices(net, loads, th["lam"][0], th["mh"], th["ml"])
+        if target is not None and best_closed >= target - gap * abs(target):
+            break
+        grads = dict(lam=np.array([gl]), mh=gh, ml=go, s=gs)
+        scale = decay ** (it - 1)
+        for k in th:
+            a = (a_l if k == "lam" else alpha) * scale
+            g = grads[k]
+            if rule == "gdm":
+                m1[k] = rho * m1[k] + a * g
+                th[k] = th[k] + m1[k]
+            elif rule == "adam":
+                m1[k] = beta1 * m1[k] + (1 - beta1) * g
+                m2[k] = beta2 * m2[k] + (1 - beta2) * g * g
+                th[k] = th[k] + a * (m1[k] / (1 - beta1 ** it)) / (np.sqrt(m2[k] / (1 - beta2 ** it)) + eps)
+            elif rule == "adagrad":
+                m1[k] = m1[k] + g * g
+                th[k] = th[k] + a * g / (np.sqrt(m1[k]) + eps)
+            else:
+                raise ValueError(rule)
+        th["mh"] = np.maximum(th["mh"], 0.0)
+        th["ml"] = np.maximum(th["ml"], 0.0)
+    return dict(best=best, best_closed=best_closed, lam=best_pt["lam"][0], mu_hi=best_pt["mh"],
+                mu_lo=best_pt["ml"], s=best_pt["s"], iters=it, history=np.array(hist), points=pts)
+
+
 # ---------------------------------------------------------------- ascent rules
 
 def solve(net: Net, loads, rule="gdm", alpha=1.0, rho=0.9, beta1=0.9, beta2=0.999,

@@ -54,7 +54,7 @@ class SolveParams(C.Structure):
                 ("alpha_lambda", C.c_double), ("rho", C.c_double), ("beta1", C.c_double),
                 ("beta2", C.c_double), ("eps", C.c_double), ("decay", C.c_double),
                 ("gap", C.c_double), ("tol", C.c_double), ("target_value", P),
-                ("mean_dispatch", P)]
+                ("mean_dispatch", P), ("qp_dual_s", C.c_int32), ("reserved", C.c_int32)]
 
 
 class GroupItem(C.Structure):

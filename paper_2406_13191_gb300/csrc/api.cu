@@ -262,6 +262,18 @@ dcopf_status solve_loop(dcopf_dual* h, int B, const double* loads, const int* ou
   P.beta2 = p.beta2;
   P.eps = p.eps;
   P.decay = p.decay;
+  if constexpr (sizeof(S) == 8) {
+    if (p.qp_dual_s) {  // eq. (16)'s s and its moments, from s = 0
+      const size_t n = (size_t)B * h->dev.n_gen;
+      StateBufs& sb = h->st64;
+      CUDA_TRY(h, sb.sbuf.alloc(3 * n * sizeof(double)));
+      CUDA_TRY(h, cudaMemsetAsync(sb.sbuf.p, 0, 3 * n * sizeof(double), s));
+      st.s = sb.sbuf.as<double>();
+      st.s1_s = st.s + n;
+      st.s2_s = st.s + 2 * n;
+      P.qp_s = 1;
+    }
+  }
   CUDA_TRY(h, h->active.alloc(16));
   int* d_active = h->active.as<int>();
   // the sparse path iterates inside its kernel until a stop test fires: long rounds
@@ -697,7 +709,8 @@ static dcopf_status check_params(const dcopf_solve_params& p) {
   if (p.rule < DCOPF_GDM || p.rule > DCOPF_ADAGRAD || p.max_iters < 1 || !(p.alpha > 0) ||
       !std::isfinite(p.alpha) || p.check_every < 0 || !(p.gap >= 0) || !(p.decay > 0) ||
       !(p.beta1 >= 0 && p.beta1 < 1) || !(p.beta2 >= 0 && p.beta2 < 1) || !(p.eps >= 0) ||
-      p.path < DCOPF_PATH_AUTO || p.path > DCOPF_PATH_SPARSE)
+      p.path < DCOPF_PATH_AUTO || p.path > DCOPF_PATH_SPARSE || p.qp_dual_s < 0 || p.qp_dual_s > 1 ||
+      p.screen_lines < 0 || p.screen_lines > 1)
     return DCOPF_ERR_INVALID_ARG;
   if (p.precision != DCOPF_FP64 && p.precision != DCOPF_FP32 && p.precision != DCOPF_BF16X3)
     return DCOPF_ERR_INVALID_ARG;
@@ -720,6 +733,7 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
                           : (batch == 1 && !outage) ? DCOPF_PATH_FUSED : DCOPF_PATH_BATCHED;
   if (h->sparse_only && path != DCOPF_PATH_SPARSE) return DCOPF_ERR_UNSUPPORTED;
   if (path == DCOPF_PATH_FUSED && (batch != 1 || outage)) return DCOPF_ERR_UNSUPPORTED;
+  if (p.qp_dual_s && (path != DCOPF_PATH_PLAIN || !h->host.qp)) return DCOPF_ERR_UNSUPPORTED;
   int prec = p.precision;
   DeviceGuard guard(h->device);
   AccountScope account(&h->acct);

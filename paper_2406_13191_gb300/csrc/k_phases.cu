@@ -56,10 +56,14 @@ __global__ void k_adjoint(int nl, int ng, const T* __restrict__ phit, const T* _
 
 // x*[b][j] from w = ctil_j + sigma_j lambda_b + pi~_bj (FP64), plus per-instance
 // sums of the generation cost and of the dispatch.
+// sv (nullable, FP64 path): eq. (16)'s s.  With it the quadratic term M x^2 is replaced
+// by its lower envelope -sqrt(M) s x - s^2 / 4 (equal at s = -2 sqrt(M) x), so the
+// minimiser over the box is the vertex x = -sign(w - sqrt(M) s) (Remark 2).
 template <typename T>
 __global__ void k_minimize(DevNet N, const double* __restrict__ lambda, const T* __restrict__ pit,
                            T* __restrict__ x, double* __restrict__ sumcost,
-                           double* __restrict__ sump, const int* __restrict__ done) {
+                           double* __restrict__ sump, const int* __restrict__ done,
+                           const double* __restrict__ sv) {
   __shared__ double red[32];
   const int b = blockIdx.x;
   if (done && done[b]) return;
@@ -68,9 +72,16 @@ __global__ void k_minimize(DevNet N, const double* __restrict__ lambda, const T*
   double c = 0.0, p = 0.0;
   for (int j = threadIdx.x; j < ng; j += blockDim.x) {
     double w = N.ctil[j] + N.sigma[j] * lam + (double)pit[(size_t)b * ng + j];
-    double xx = inner_x<double>(w, N.mq[j]);
+    double xx;
+    if (sv) {
+      const double sq = sqrt(N.mq[j]), sj = sv[(size_t)b * ng + j];
+      xx = inner_x<double>(w - sq * sj, 0.0);
+      c += (N.ctil[j] - sq * sj) * xx - 0.25 * sj * sj + N.cconst[j];
+    } else {
+      xx = inner_x<double>(w, N.mq[j]);
+      c += (N.mq[j] * xx + N.ctil[j]) * xx + N.cconst[j];
+    }
     x[(size_t)b * ng + j] = (T)xx;
-    c += (N.mq[j] * xx + N.ctil[j]) * xx + N.cconst[j];
     p += N.mid[j] + N.sigma[j] * xx;
   }
   c = block_sum(c, red);
@@ -213,6 +224,31 @@ __global__ void k_step(int nl, StepArgs P, const double* __restrict__ value,
   }
 }
 
+// Step of eq. (16)'s s (free, mu's step size): supergradient -sqrt(M) x* - s / 2 at the
+// evaluated point.  Runs before k_step (which advances the iteration count).
+__global__ void k_step_s(DevNet N, StepArgs P, const double* __restrict__ x, SolveStateBase st) {
+  const int b = blockIdx.y;
+  if (st.done[b] || st.cand[b] == 2) return;
+  const int ng = N.n_gen;
+  const int t = st.iter[b] + 1;
+  __shared__ double s_pw[3];
+  if (threadIdx.x == 0) {
+    s_pw[0] = pow(P.decay, (double)(t - 1));
+    s_pw[1] = 1.0 - pow(P.beta1, (double)t);
+    s_pw[2] = 1.0 - pow(P.beta2, (double)t);
+  }
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ng) return;
+  StepArgs Q = P;
+  Q.bc1 = s_pw[1];
+  Q.bc2 = s_pw[2];
+  const size_t o = (size_t)b * ng + j;
+  const double sj = st.s[o];
+  const double g = -sqrt(N.mq[j]) * x[o] - 0.5 * sj;
+  st.s[o] = rule_step<double>(Q, sj, g, st.s1_s[o], st.s2_s[o], P.alpha * s_pw[0]);
+}
+
 // Closes an iteration: publishes best_next, applies the stop tests on the in-loop
 // value (target crossing -> candidate for certification; |g_t - g_{t-1}| < tol;
 // iteration cap).  One thread per instance.
@@ -251,7 +287,7 @@ dcopf_status run_eval_unfused(dcopf_dual* h, int B, const int* outage, const dou
     k_eta<double, double><<<B, 256, 0, s>>>(nl, mh, ml, outage, w.u64.as<double>(), w.eta64.as<double>());
     k_adjoint<double><<<gg, ta, 0, s>>>(nl, ng, N.phit64, w.eta64.as<double>(), w.pit64.as<double>());
     k_minimize<double><<<B, 256, 0, s>>>(N, lambda, w.pit64.as<double>(), w.x64.as<double>(),
-                                         w.sumcost.as<double>(), w.sump.as<double>(), nullptr);
+                                         w.sumcost.as<double>(), w.sump.as<double>(), nullptr, nullptr);
     k_forward<double><<<gl, tf, 0, s>>>(nl, ng, N.phi64, w.x64.as<double>(), w.f0.as<double>(),
                                          w.f.as<double>(), nullptr);
     if (dispatch) k_dispatch<<<cdiv((long long)B * ng, 256), 256, 0, s>>>(N, B, w.x64.as<double>(), dispatch);
@@ -259,7 +295,7 @@ dcopf_status run_eval_unfused(dcopf_dual* h, int B, const int* outage, const dou
     k_eta<float, double><<<B, 256, 0, s>>>(nl, mh, ml, outage, w.u32.as<float>(), w.eta32.as<float>());
     k_adjoint<float><<<gg, ta, 0, s>>>(nl, ng, N.phit32, w.eta32.as<float>(), w.pit32.as<float>());
     k_minimize<float><<<B, 256, 0, s>>>(N, lambda, w.pit32.as<float>(), w.x32.as<float>(),
-                                        w.sumcost.as<double>(), w.sump.as<double>(), nullptr);
+                                        w.sumcost.as<double>(), w.sump.as<double>(), nullptr, nullptr);
     k_forward<float><<<gl, tf, 0, s>>>(nl, ng, N.phi32, w.x32.as<float>(), w.f0.as<double>(),
                                         w.f.as<double>(), nullptr);
     if (dispatch) k_dispatch32<<<cdiv((long long)B * ng, 256), 256, 0, s>>>(N, B, w.x32.as<float>(), dispatch);
@@ -356,7 +392,7 @@ dcopf_status run_iters_unfused(dcopf_dual* h, int B, const int* outage, int prec
       k_eta<double, S><<<B, 256, 0, s>>>(nl, st.mu_hi, st.mu_lo, outage, w.u64.as<double>(), w.eta64.as<double>());
       k_adjoint<double><<<gg, ta, 0, s>>>(nl, ng, N.phit64, w.eta64.as<double>(), w.pit64.as<double>());
       k_minimize<double><<<B, 256, 0, s>>>(N, st.lam, w.pit64.as<double>(), w.x64.as<double>(),
-                                           w.sumcost.as<double>(), w.sump.as<double>(), st.done);
+                                           w.sumcost.as<double>(), w.sump.as<double>(), st.done, st.s);
       if (st.xsum) launch_accum_mean<double>(h, B, w.x64.as<double>(), st, s);
       k_forward<double><<<gl, tf, 0, s>>>(nl, ng, N.phi64, w.x64.as<double>(), w.f0.as<double>(),
                                            w.f.as<double>(), st.done);
@@ -364,7 +400,7 @@ dcopf_status run_iters_unfused(dcopf_dual* h, int B, const int* outage, int prec
       k_eta<float, S><<<B, 256, 0, s>>>(nl, st.mu_hi, st.mu_lo, outage, w.u32.as<float>(), w.eta32.as<float>());
       k_adjoint<float><<<gg, ta, 0, s>>>(nl, ng, N.phit32, w.eta32.as<float>(), w.pit32.as<float>());
       k_minimize<float><<<B, 256, 0, s>>>(N, st.lam, w.pit32.as<float>(), w.x32.as<float>(),
-                                          w.sumcost.as<double>(), w.sump.as<double>(), st.done);
+                                          w.sumcost.as<double>(), w.sump.as<double>(), st.done, nullptr);
       if (st.xsum) launch_accum_mean<float>(h, B, w.x32.as<float>(), st, s);
       k_forward<float><<<gl, tf, 0, s>>>(nl, ng, N.phi32, w.x32.as<float>(), w.f0.as<double>(),
                                           w.f.as<double>(), st.done);
@@ -374,6 +410,10 @@ dcopf_status run_iters_unfused(dcopf_dual* h, int B, const int* outage, int prec
                                               w.sump.as<double>(), w.demand.as<double>(),
                                               w.value.as<double>(), w.glam.as<double>(),
                                               w.ghi.as<double>(), w.glo.as<double>(), st.done);
+    if (st.s && precision == DCOPF_FP64) {
+      k_step_s<<<dim3(cdiv(ng, 256), B), 256, 0, s>>>(N, P, w.x64.as<double>(), st);
+      h->launches += 1;
+    }
     k_step<S><<<gs, 256, 0, s>>>(nl, P, w.value.as<double>(), w.glam.as<double>(),
                                  w.ghi.as<double>(), w.glo.as<double>(), st);
     k_close_iter<<<cdiv(B, 128), 128, 0, s>>>(B, max_iters, tol, st);
@@ -397,14 +437,14 @@ dcopf_status launch_eval_into(dcopf_dual* h, int B, const int* outage, const dou
   if (precision == DCOPF_FP64) {
     k_eta<double, double><<<B, 256, 0, s>>>(nl, mh, ml, outage, E.u64, E.eta64);
     k_adjoint<double><<<gg, ta, 0, s>>>(nl, ng, N.phit64, E.eta64, E.pit64);
-    k_minimize<double><<<B, 256, 0, s>>>(N, lambda, E.pit64, E.x64, E.sumcost, E.sump, nullptr);
+    k_minimize<double><<<B, 256, 0, s>>>(N, lambda, E.pit64, E.x64, E.sumcost, E.sump, nullptr, nullptr);
     k_forward<double><<<gl, tf, 0, s>>>(nl, ng, N.phi64, E.x64, E.f0, E.f, nullptr);
     if (dispatch) k_dispatch<<<cdiv((long long)B * ng, 256), 256, 0, s>>>(N, B, E.x64, dispatch);
   } else {
     k_to_float<<<cdiv((long long)B * nl, 256), 256, 0, s>>>((long long)B * nl, E.u64, E.u32);
     k_eta<float, double><<<B, 256, 0, s>>>(nl, mh, ml, outage, E.u32, E.eta32);
     k_adjoint<float><<<gg, ta, 0, s>>>(nl, ng, N.phit32, E.eta32, E.pit32);
-    k_minimize<float><<<B, 256, 0, s>>>(N, lambda, E.pit32, E.x32, E.sumcost, E.sump, nullptr);
+    k_minimize<float><<<B, 256, 0, s>>>(N, lambda, E.pit32, E.x32, E.sumcost, E.sump, nullptr, nullptr);
     k_forward<float><<<gl, tf, 0, s>>>(nl, ng, N.phi32, E.x32, E.f0, E.f, nullptr);
     if (dispatch) k_dispatch32<<<cdiv((long long)B * ng, 256), 256, 0, s>>>(N, B, E.x32, dispatch);
     h->launches += 1;
@@ -432,9 +472,9 @@ template __global__ void k_eta<float, float>(int, const float*, const float*, co
 template __global__ void k_adjoint<double>(int, int, const double*, const double*, double*);
 template __global__ void k_adjoint<float>(int, int, const float*, const float*, float*);
 template __global__ void k_minimize<double>(DevNet, const double*, const double*, double*, double*,
-                                            double*, const int*);
+                                            double*, const int*, const double*);
 template __global__ void k_minimize<float>(DevNet, const double*, const float*, float*, double*,
-                                           double*, const int*);
+                                           double*, const int*, const double*);
 template __global__ void k_forward<double>(int, int, const double*, const double*, const double*,
                                            double*, const int*);
 template __global__ void k_forward<float>(int, int, const float*, const float*, const double*,

@@ -13,6 +13,7 @@ namespace dcopf {
 
 struct StepArgs {
   int rule, as_printed;
+  int qp_s;         // 1 = eq. (16) with s as an ascent variable (plain path)
   double alpha, alpha_lambda, rho, beta1, beta2, eps, decay;
   double bc1, bc2;  // Adam bias corrections of the current step (set per step)
 };
@@ -43,6 +44,10 @@ __device__ __forceinline__ S rule_step(const StepArgs& P, S theta, S g, S& s1, S
 
 // Per-instance solver bookkeeping (device pointers, [batch] each).
 struct SolveStateBase {
+  // eq. (16)'s s [batch][n_gen] and its two moments (plain FP64 path; null = closed form)
+  double* s = nullptr;
+  double* s1_s = nullptr;
+  double* s2_s = nullptr;
   int* done;       // 1 once the instance has stopped
   int* cand;       // 1 = in-loop value reached the target (certify), 2 = stop (cap / tol)
   int* iter;       // evaluations so far
@@ -207,6 +212,7 @@ struct StateBufs {
   int elem = 0;  // sizeof(S) of the arrays below
   DBuf ints, dbls, mus;
   DBuf avg;      // xsum and wsum of the mean of the minimisers
+  DBuf sbuf;     // eq. (16)'s s and its moments [3][batch][n_gen] (FP64 state only)
 };
 
 }  // namespace dcopf

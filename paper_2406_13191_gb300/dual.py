@@ -276,7 +276,7 @@ class DcopfDual:
         return upper, status, disp, viol
 
     def _params(self, rule, precision, path, max_iters, alpha, alpha_lambda, rho, beta1, beta2, eps,
-                decay, gap, tol, as_printed, check_every, screen=False, warm=False):
+                decay, gap, tol, as_printed, check_every, screen=False, qp_dual="closed", warm=False):
         p = _lib.SolveParams()
         self.lib.dcopf_solve_params_default(C.byref(p))
         p.rule = _lib.RULE[rule]
@@ -287,6 +287,7 @@ class DcopfDual:
         p.as_printed = 1 if as_printed else 0
         p.check_every = int(check_every)
         p.screen_lines = 1 if screen else 0
+        p.qp_dual_s = {"closed": 0, "s": 1}[qp_dual]
         p.alpha, p.alpha_lambda, p.rho = float(alpha), float(alpha_lambda), float(rho)
         p.beta1, p.beta2, p.eps, p.decay = float(beta1), float(beta2), float(eps), float(decay)
         p.gap, p.tol = float(gap), float(tol)
@@ -319,16 +320,17 @@ class DcopfDual:
               max_iters=5000, alpha=1000.0, alpha_lambda=0.0, rho=0.9, beta1=0.9, beta2=0.999,
               eps=1e-8, decay=1.0, gap=1e-3, tol=0.0, target=None, warm=None,
               as_printed=False, check_every=1, out: SolveResult | None = None,
-              mean_dispatch: bool = False, screen: bool = False) -> SolveResult:
+              mean_dispatch: bool = False, screen: bool = False, qp_dual: str = "closed") -> SolveResult:
         """``dcopf_dual_solve_batch``.  ``target`` ([B] optimal costs) enables the
         certified-gap stop; ``warm`` = (lambda, mu_hi, mu_lo) warm start; ``out`` (from
         ``new_result``) receives the results instead of new tensors; ``mean_dispatch``
         also returns the k^2-weighted mean of the minimisers (a primal candidate); ``screen``
-        turns on constraint screening (batched tensor-core solves without outages)."""
+        turns on constraint screening (batched tensor-core solves without outages);
+        ``qp_dual="s"`` ascends on eq. (16) with s as a variable (plain path, QP)."""
         loads, outg, tgt, r = self._solve_arrays(loads, outage, target, warm, out)
         p = self._params(rule, precision, path, max_iters, alpha, alpha_lambda, rho, beta1, beta2,
                          eps, decay, gap, tol, as_printed, check_every, screen=screen,
-                         warm=warm is not None)
+                         qp_dual=qp_dual, warm=warm is not None)
         p.target_value = None if tgt is None else tgt.data_ptr()
         if mean_dispatch:
             if r.mean_dispatch is None or r.mean_dispatch.shape != (r.lam.shape[0], self.n_gen):
@@ -345,7 +347,8 @@ class DcopfDual:
 
 _SOLVE_DEFAULTS = dict(rule="adam", precision="bf16x3", path="batched", max_iters=5000,
                       alpha=1000.0, alpha_lambda=0.0, rho=0.9, beta1=0.9, beta2=0.999, eps=1e-8,
-                      decay=1.0, gap=1e-3, tol=0.0, as_printed=False, check_every=1, screen=False)
+                      decay=1.0, gap=1e-3, tol=0.0, as_printed=False, check_every=1, screen=False,
+                      qp_dual="closed")
 
 
 def solve_group(duals, loads, outage=None, target=None, warm=None, per_network=None,

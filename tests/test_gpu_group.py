@@ -58,3 +58,31 @@ def test_group_rejects_repeated_handles_and_other_precisions(cases):
     with pytest.raises(_lib.DcopfError) as e:
         solve_group([g], [w.loads], precision="fp32", **ADAM_QP)
     assert e.value.code == 6                     # DCOPF_ERR_UNSUPPORTED
+
+
+def test_group_mix_300_2000_4600_reaches_stored_optima():
+    """The mixed-size workload at full size: 1024 scenarios of the 300-bus QP network,
+    256 of the 2000-bus QP network and 128 instances of the 4600-bus LP batch (64 with
+    a line outage), one group solve against the oracle's optima
+    (tests/golden/group_gamma.json, c2_gamma.json)."""
+    import json
+    import os
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    gg = json.load(open(os.path.join(gold, "group_gamma.json")))
+    g2 = json.load(open(os.path.join(gold, "c2_gamma.json")))["gamma"][:128]
+    n300, b300 = synth.network_for(300)
+    w1 = synth.workload(1, batch=256)
+    w2 = synth.workload(2, batch=128)
+    assert all(x is not None for x in gg["300"] + gg["2000"] + g2)
+    qp = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997)
+    lp = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99)
+    targets = [np.array(gg["300"]), np.array(gg["2000"]), np.array(g2)]
+    duals = [DcopfDual(n300), DcopfDual(w1.net), DcopfDual(w2.net)]
+    res = solve_group(duals, [synth.scenario_loads(b300, 1024, 4301), w1.loads, w2.loads],
+                      outage=[None, None, w2.outage], target=targets, per_network=[qp, qp, lp],
+                      max_iters=4000, precision="bf16x3", path="batched", check_every=16)
+    torch.cuda.synchronize()
+    for r, t in zip(res, targets):
+        b = r.bound.cpu().numpy()
+        assert (r.status.cpu().numpy() == 0).all()
+        assert np.all(b <= t + 1e-9 * np.abs(t)) and np.all(b >= t * (1 - 1e-3) - 1e-9 * np.abs(t))

@@ -381,3 +381,47 @@ def test_ascent_rules_decay_and_alpha_lambda():
     want = mh1.copy()
     want[den > 0] = np.maximum(mh1[den > 0] + a * d * ghi1[den > 0] / den[den > 0], 0)
     assert np.allclose(r["points"][2][1], want, rtol=1e-12, atol=1e-12)
+
+
+def test_qp_dual_with_s_variable():
+    """Eq. (16) with s as an ascent variable (Remark 2): at s = -2 sqrt(M) x* it equals the
+    closed-form dual (minimax), any other s gives less; its s-gradient -sqrt(M) x* - s/2
+    matches central finite differences where no reduced cost ties; the first Adam step
+    from the cold start moves every coordinate by alpha sign(gradient), written out by
+    hand; and the s-ascent reaches the 0.1 % gap on a small QP, its in-loop value g_q
+    staying below the certified closed-form value."""
+    s_, loads = synth.tiny_network(23, 16, 24, 6, quadratic=True)
+    net = onet(s_)
+    can = dcopf.canonical(net, loads)
+    rng = np.random.default_rng(12)
+    lam, mh, ml = _rand_point(rng, net, scale=20.0)
+    sv = rng.normal(scale=30.0, size=net.n_gen)
+    val, gl, gh, go, gs, p = dcopf.evaluate_qp_s(net, can, loads, lam, mh, ml, sv)
+    x = (p - can["mid"]) / can["sigma"]
+    sq = np.sqrt(can["M"])
+    assert np.all(np.isin(np.round(x, 12), [-1.0, 1.0]))
+    closed = dcopf.dual_value_prices(net, loads, lam, mh, ml)
+    assert val <= closed + 1e-9 * abs(closed)
+    h = 1e-4
+    for j in range(net.n_gen):
+        e = np.zeros(net.n_gen)
+        e[j] = h
+        fd = (dcopf.evaluate_qp_s(net, can, loads, lam, mh, ml, sv + e)[0]
+              - dcopf.evaluate_qp_s(net, can, loads, lam, mh, ml, sv - e)[0]) / (2 * h)
+        assert abs(fd - gs[j]) < 1e-5 * max(1.0, abs(gs[j]))
+    assert abs(gs[0] - (-sq[0] * x[0] - 0.5 * sv[0])) < 1e-12 * max(1.0, abs(gs[0]))
+    # first Adam step, eps = 0: theta_1 = alpha * sign(g_0)
+    a = 2.0
+    r = dcopf.solve_qp_s(net, loads, rule="adam", alpha=a, eps=0.0, max_iters=2, record=True)
+    z = np.zeros(net.n_line)
+    _, gl0, gh0, _, gs0, _ = dcopf.evaluate_qp_s(net, can, loads, 0.0, z, z, np.zeros(net.n_gen))
+    p1 = r["points"][1]
+    assert abs(p1["lam"][0] - a * np.sign(gl0)) < 1e-12
+    assert np.allclose(p1["s"], a * np.sign(gs0)) and np.allclose(p1["mh"], np.maximum(a * np.sign(gh0), 0))
+    # convergence to the gap (certified through the closed form at (lambda, mu))
+    gam = exact.ipm(net, loads)["gamma"]
+    r = dcopf.solve_qp_s(net, loads, rule="adam", alpha=1000.0, beta1=0.9, beta2=0.999, decay=0.998,
+                         max_iters=5000, target=gam, gap=1e-3)
+    assert r["iters"] < 5000
+    assert gam * (1 - 1e-3) - 1e-9 * abs(gam) <= r["best_closed"] <= gam + 1e-9 * abs(gam)
+    assert r["best"] <= r["best_closed"] + 1e-9 * abs(gam)
