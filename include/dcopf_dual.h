@@ -382,12 +382,24 @@ dcopf_status dcopf_dual_read_timing(dcopf_dual_t h, double* iter_ms, int64_t* it
 dcopf_status dcopf_dual_screened_lines(dcopf_dual_t h, int32_t* n_kept, uint8_t* kept_mask);
 
 /* Per-kernel timing of the batched tensor-core solve, while dcopf_dual_set_timing is
- * on: CUDA events recorded inside the iteration graph around the five kernels of the
- * last iteration of every round (the adjoint product, the minimiser, the forward
- * product, the step, the dual value).  ms (host [5], nullable) receives the summed
- * milliseconds of each over the sampled iterations, samples (host, nullable) their
- * count; both are then reset.  Host only. */
+ * on: CUDA events recorded inside the iteration graph around the kernels of the last
+ * iteration of every round of the first instance group (the adjoint product, the
+ * minimiser, the forward product, the step, and a fifth slot for the dual value and
+ * stop tests, which run inside the step kernel, so that it reads about zero).  ms (host
+ * [5], nullable) receives the summed milliseconds of each over the sampled iterations,
+ * samples (host, nullable) their count; both are then reset.  Host only. */
 dcopf_status dcopf_dual_read_kernel_timing(dcopf_dual_t h, double* ms, int64_t* samples);
+
+/* The shapes the batched tensor-core solve chose for its last batch (by timing on the
+ * first solve of a batch size, or as DCOPF_TENSOR_SHAPE fixed them), into shapes (host
+ * [7]): the batch, the lines iterated on, the adjoint product's tiles (0 single CTAs of
+ * 128 x 128; CTA pairs of 1: 256 x 256, 2: 256 x 192, 3: 256 x 160), its split-K factor,
+ * the forward product's tiles (same codes), the number of instance groups iterated as
+ * parallel branches of the iteration graph (1 or 2; the tiles are those of one group's
+ * share of the batch), and the first group's instances (its kernels are the ones that
+ * dcopf_dual_read_kernel_timing times).  All zero before the first batched solve.
+ * Host only. */
+dcopf_status dcopf_dual_tensor_shapes(dcopf_dual_t h, int32_t* shapes);
 
 /* Device-memory budget of a handle's workspaces: the buffers that eval,
  * certify_bound, primal_bound, solve_batch and the self-tests allocate on first use

@@ -13,8 +13,8 @@ EXPORTS = ("dcopf_version", "dcopf_status_string", "dcopf_solve_params_default",
            "dcopf_dual_certify_bound", "dcopf_dual_primal_bound", "dcopf_dual_solve_batch",
            "dcopf_dual_kernel_launches",
            "dcopf_dual_device_error", "dcopf_dual_set_timing", "dcopf_dual_read_timing",
-           "dcopf_dual_screened_lines", "dcopf_dual_read_kernel_timing", "dcopf_dual_workspace_limit",
-           "dcopf_selftest_bounded_wait",
+           "dcopf_dual_screened_lines", "dcopf_dual_read_kernel_timing", "dcopf_dual_tensor_shapes",
+           "dcopf_dual_workspace_limit", "dcopf_selftest_bounded_wait",
            "dcopf_selftest_fused_timeout", "dcopf_dual_eval_noalloc", "dcopf_dual_solve_group",
            "dcopf_mlp_create", "dcopf_mlp_destroy", "dcopf_mlp_num_params", "dcopf_mlp_set_params",
            "dcopf_mlp_get_params", "dcopf_mlp_set_normalization", "dcopf_mlp_forward",
@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.dcopf_selftest_fused_timeout.argtypes = [P, P, C.c_int64, P]
     lib.dcopf_dual_workspace_limit.argtypes = [P, C.c_int64, C.POINTER(C.c_int64)]
     lib.dcopf_dual_read_kernel_timing.argtypes = [P, F64P, C.POINTER(C.c_int64)]
+    lib.dcopf_dual_tensor_shapes.argtypes = [P, I32P]
     lib.dcopf_dual_screened_lines.argtypes = [P, I32P, C.POINTER(C.c_uint8)]
     lib.dcopf_dual_eval_noalloc.argtypes = [P, C.c_int32, P, P, P, P, P, C.c_int32, P, P, P, P,
                                             P, P]
@@ -154,6 +155,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                  "dcopf_selftest_bounded_wait", "dcopf_dual_eval_noalloc", "dcopf_dual_solve_group",
                  "dcopf_selftest_fused_timeout", "dcopf_dual_workspace_limit",
                  "dcopf_dual_read_kernel_timing", "dcopf_dual_screened_lines",
+                 "dcopf_dual_tensor_shapes",
            "dcopf_mlp_create", "dcopf_mlp_destroy", "dcopf_mlp_num_params", "dcopf_mlp_set_params",
            "dcopf_mlp_get_params", "dcopf_mlp_set_normalization", "dcopf_mlp_forward",
            "dcopf_mlp_loss_grad", "dcopf_mlp_train_step", "dcopf_mlp_warm_start",

@@ -21,8 +21,13 @@ dcopf_dual::~dcopf_dual() {
   if (tev) cudaEventDestroy(tev);
   for (cudaEvent_t e : kev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : kev2)
+    if (e) cudaEventDestroy(e);
   if (tstream) cudaStreamDestroy(tstream);
   if (cstream) cudaStreamDestroy(cstream);
+  if (tstream2) cudaStreamDestroy(tstream2);
+  if (fork_ev) cudaEventDestroy(fork_ev);
+  if (join_ev) cudaEventDestroy(join_ev);
   if (h_pinned) cudaFreeHost(h_pinned);
 }
 
@@ -480,13 +485,16 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
     if (t && strcmp(t, "128") == 0) h->tiles_mode = 1;
     if (t && strcmp(t, "256") == 0) h->tiles_mode = 2;
     if (t && strcmp(t, "192") == 0) h->tiles_mode = 3;
+    if (t && strcmp(t, "160") == 0) h->tiles_mode = 4;
     const char* sh = getenv("DCOPF_TENSOR_SHAPE");
-    int a = -1, sp = 0, fw = -1;
-    if (sh && sscanf(sh, "%d,%d,%d", &a, &sp, &fw) == 3 && a >= 0 && a <= 2 && sp >= 1 && sp <= 64 &&
-        fw >= 0 && fw <= 2) {
+    int a = -1, sp = 0, fw = -1, br = 1;
+    const int nf = sh ? sscanf(sh, "%d,%d,%d,%d", &a, &sp, &fw, &br) : 0;
+    if (nf >= 3 && a >= 0 && a <= 3 && sp >= 1 && sp <= 64 && fw >= 0 && fw <= 3 && br >= 1 &&
+        br <= 2) {
       h->shape_adj = a;
       h->shape_splits = sp;
       h->shape_fwd = fw;
+      h->shape_branches = br;
     }
   }
   std::string err;
@@ -843,6 +851,15 @@ dcopf_status dcopf_dual_read_kernel_timing(dcopf_dual_t h, double* ms, int64_t* 
   if (samples) *samples = h->t_kernel_samples;
   for (int q = 0; q < 5; ++q) h->t_kernel_ms[q] = 0.0;
   h->t_kernel_samples = 0;
+  return DCOPF_OK;
+}
+
+dcopf_status dcopf_dual_tensor_shapes(dcopf_dual_t h, int32_t* shapes) {
+  if (!h || !shapes) return DCOPF_ERR_INVALID_ARG;
+  const int g0 = h->tune_branches > 1 ? tensor_first_group(h->tune_B) : h->tune_B;
+  const int v[7] = {h->tune_B, h->tune_nl, h->tune_pair_adj, h->tune_splits, h->tune_pair_fwd,
+                    h->tune_branches, g0};
+  for (int q = 0; q < 7; ++q) shapes[q] = h->tune_B > 0 ? v[q] : 0;
   return DCOPF_OK;
 }
 

@@ -156,17 +156,6 @@ __global__ void k_screen_compact_rows(int B, int nl, int nk, const int* __restri
   }
 }
 
-// [B][nk] compact multipliers -> [B][n_line], zero on the screened lines.
-__global__ void k_screen_scatter_rows(int B, int nl, int nk, const int* __restrict__ pos,
-                                      const float* __restrict__ src, float* __restrict__ dst) {
-  const size_t n = (size_t)B * nl;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t b = q / nl, l = q - b * nl;
-    const int r = pos[l];
-    dst[q] = r >= 0 ? src[b * nk + r] : 0.f;
-  }
-}
-
 dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s) {
   LineScreen& S = h->scr;
   const int nl = h->host.n_line, ng = h->host.n_gen;
@@ -248,7 +237,11 @@ dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s) {
       !tc_make_map_rows(&S.m_phi_hi96, S.phi_hi.p, nk, ng, T.ld_g, 96) ||
       !tc_make_map_rows(&S.m_phi_lo96, S.phi_lo.p, nk, ng, T.ld_g, 96) ||
       !tc_make_map_rows(&S.m_phit_hi96, S.phit_hi.p, ng, nk, ld_lk, 96) ||
-      !tc_make_map_rows(&S.m_phit_lo96, S.phit_lo.p, ng, nk, ld_lk, 96))
+      !tc_make_map_rows(&S.m_phit_lo96, S.phit_lo.p, ng, nk, ld_lk, 96) ||
+      !tc_make_map_rows(&S.m_phi_hi80, S.phi_hi.p, nk, ng, T.ld_g, 80) ||
+      !tc_make_map_rows(&S.m_phi_lo80, S.phi_lo.p, nk, ng, T.ld_g, 80) ||
+      !tc_make_map_rows(&S.m_phit_hi80, S.phit_hi.p, ng, nk, ld_lk, 80) ||
+      !tc_make_map_rows(&S.m_phit_lo80, S.phit_lo.p, ng, nk, ld_lk, 80))
     return DCOPF_ERR_CUDA;
   S.nk = nk;
   S.ld_lk = ld_lk;

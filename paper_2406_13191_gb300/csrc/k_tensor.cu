@@ -3,32 +3,23 @@
 // forward F = X Phi~^T (X = [batch][n_gen] normalised dispatch), the two dense
 // contractions of every iteration (eq. (6): c + A^T lambda + C^T mu, and C x*).
 //
-// Precision: each FP32 operand v is split into BF16 v_hi = bf16(v) and
-// v_lo = bf16(v - v_hi) and the product is hi*hi + hi*lo + lo*hi with FP32 accumulation
-// in TMEM (3 MMAs per K step).  When one operand is exact in BF16 (the LP dispatch
-// x in {-1, 0, 1}) its lo part is zero and 2 MMAs suffice.
-//
-// Kernel shape: one 128 x 128 output tile per CTA (split along K for the adjoint,
-// whose K = n_line is long and whose N = n_gen is short), 6 warps: warp 0 issues TMA
-// loads of the BF16 tiles of a 64-wide K block into a ring with 128-byte swizzle,
-// warp 1 allocates TMEM and one of its threads issues the MMAs, warps 2-5 read the
-// accumulator from TMEM (tcgen05.ld) and run the epilogue.  The three-product GEMMs
-// run one CTA per SM with a 3-stage ring; the two-product LP forward runs two CTAs per
-// SM with a 2-stage ring each, so that one CTA's epilogue overlaps the other's loads.
+// The products themselves (tcgen05, BF16 hi/lo split operands, single CTAs or CTA
+// pairs) are in k_gemm.cuh; this file holds the iteration's other kernels (minimiser,
+// step, value), the shape autotuner and the host driver of the batched solve.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <vector>
 
 #include "dev.cuh"
 #include "kernels.h"
+#include "k_gemm.cuh"
 #include "umma.cuh"
 
 namespace dcopf {
-
-enum { EPI_PARTIAL = 0, EPI_FLOW = 1, EPI_TILE = 2 };
 
 // Step-rule constants in FP32, converted once on the host (FP64 conversions per
 // element are not free on this part).
@@ -67,6 +58,14 @@ __device__ __forceinline__ float step_rule(const StepArgsF& P, float theta, floa
   return theta;
 }
 
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo);
+__device__ __forceinline__ void finalize_instance(int b, int lane, int ld_l, int max_iters, double tol,
+                                                  const SolveStateBase& st, const BatchView& bb,
+                                                  const int* __restrict__ outage,
+                                                  const double* __restrict__ demand,
+                                                  __nv_bfloat16* __restrict__ Hh,
+                                                  __nv_bfloat16* __restrict__ Hl);
+
 // Step of the batched solve after the forward product: flows (with the rank-1 outage
 // term), supergradient, line part of the dual value, projected step of mu into the
 // parity-buffered state, BF16 split of the next eta, outage partial u^T eta.
@@ -93,378 +92,33 @@ struct StepEpi {
   float* s1_hi; float* s2_hi; float* s1_lo; float* s2_lo;
   __nv_bfloat16* Hh; __nv_bfloat16* Hl; int ldh;
   double* line_part; double* out_part; int n_tiles;   // [B][n_tiles] per chunk of lines
+  // the dual value and the stop tests of the evaluated point (finalize_instance), run by
+  // the last of an instance's blocks to finish: step_done [B] counts them
+  SolveStateBase st;
+  BatchView bb;
+  const double* demand;
+  int max_iters;
+  double tol;
+  int* step_done;
 };
 
-struct GemmArgs {
-  int M, N, K;           // rows of A (instances), rows of B (outputs), contraction length
-  int kb_per_split;      // 64-wide K blocks per split
-  int epi;
-  float* P; int ldp;     // EPI_PARTIAL: P[split][M][ldp]
-  const double* f0; double* f; int ldf;  // EPI_FLOW: f = acc + f0, [M][ldf]
-  float* F32; int ldf32;  // EPI_TILE: raw accumulator, [M][ldf32]
-  int* err;
-  uint64_t timeout_ns;
-  const int* skip;       // nullable [M]: rows whose instance is frozen (a tile of them is skipped)
-};
-
-constexpr int GBM = 128, GBN = 128, GBK = 64;
-constexpr uint32_t TILE_BYTES = GBM * GBK * 2;  // 16 KB, also GBN * GBK * 2
-
-template <int NPROD, int OCC = 1>
-struct GemmCfg {
-  static constexpr int STAGES = NPROD == 3 ? 3 : (OCC == 2 ? 2 : 4);
-  static constexpr uint32_t STAGE_BYTES = (NPROD == 3 ? 4 : 3) * TILE_BYTES;
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
-  static_assert(STAGES * STAGE_BYTES >= GBM * (GBN + 1) * 4, "the ring stages the output tile");
-};
-
-__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo);
-
-
-
-template <int NPROD, int OCC = 1>
-__global__ void __launch_bounds__(192, OCC)
-    k_gemm_bf16x(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
-                 const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
-                 GemmArgs g) {
-  using Cfg = GemmCfg<NPROD, OCC>;
-  constexpr int ST = Cfg::STAGES;
-  extern __shared__ __align__(16) unsigned char gsm_raw[];
-  unsigned char* base = (unsigned char*)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[ST], empty[ST], accf;
-  __shared__ uint32_t tmem_base;
-  __shared__ int s_abort;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-  const int kb_total = (g.K + GBK - 1) / GBK;
-  const int kb0 = blockIdx.z * g.kb_per_split;
-  const int nkb = min(kb_total, kb0 + g.kb_per_split) - kb0;
-  auto a_hi = [&](int s) { return base + (size_t)s * Cfg::STAGE_BYTES; };
-  auto a_lo = [&](int s) { return a_hi(s) + TILE_BYTES; };
-  auto b_hi = [&](int s) { return a_hi(s) + (NPROD == 3 ? 2 : 1) * TILE_BYTES; };
-  auto b_lo = [&](int s) { return b_hi(s) + TILE_BYTES; };
-
-  if (g.skip) {
-    // a tile whose instances are all frozen has nothing to compute: the kernels that
-    // read its output skip frozen instances too.  Decided before any barrier, TMA or
-    // TMEM work, by every thread alike.
-    int live = 0;
-    for (int r = threadIdx.x; r < GBM; r += blockDim.x)
-      live |= (m0 + r < g.M && !g.skip[m0 + r]) ? 1 : 0;
-    if (!__syncthreads_or(live)) return;
-  }
+// The tail of both step kernels: the block's partials are in (thread 0 wrote them);
+// the last block of instance b runs its value and stop tests.
+__device__ __forceinline__ void step_tail(const StepEpi& E, int b) {
+  __shared__ int s_last;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < ST; ++s) {
-      umma::mbar_init(&full[s], 1);
-      umma::mbar_init(&empty[s], 1);
-    }
-    umma::mbar_init(&accf, 1);
-    s_abort = 0;
-    umma::fence_mbar_init();
-  }
-  if (warp == 1) umma::tmem_alloc(&tmem_base, GBN);
-  __syncthreads();
-  umma::tc_fence_after();
-  const uint32_t tmem = tmem_base;
-  int issued = 0;
-
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    for (int i = 0; i < nkb && nkb > 0; ++i) {
-      const int s = i % ST;
-      if (i >= ST && !umma::mbar_wait(&empty[s], ((i / ST) & 1) ^ 1, g.timeout_ns)) {
-        s_abort = 1;
-        break;
-      }
-      umma::mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
-      const int x = (kb0 + i) * GBK;
-      umma::tma_load_2d(&tAh, &full[s], a_hi(s), x, m0);
-      if (NPROD == 3) umma::tma_load_2d(&tAl, &full[s], a_lo(s), x, m0);
-      umma::tma_load_2d(&tBh, &full[s], b_hi(s), x, n0);
-      umma::tma_load_2d(&tBl, &full[s], b_lo(s), x, n0);
-      ++issued;
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t idesc = umma::idesc_bf16_f32(GBN);
-    for (int i = 0; i < nkb; ++i) {
-      const int s = i % ST;
-      if (!umma::mbar_wait(&full[s], (i / ST) & 1, g.timeout_ns)) {
-        s_abort = 1;
-        break;
-      }
-      umma::tc_fence_after();
-      const uint64_t dah = umma::desc_sw128(umma::smem_u32(a_hi(s)));
-      const uint64_t dal = umma::desc_sw128(umma::smem_u32(a_lo(s)));
-      const uint64_t dbh = umma::desc_sw128(umma::smem_u32(b_hi(s)));
-      const uint64_t dbl = umma::desc_sw128(umma::smem_u32(b_lo(s)));
-#pragma unroll
-      for (int kk = 0; kk < GBK / 16; ++kk) {
-        const uint64_t o = (uint64_t)(kk * 32) >> 4;  // 16 BF16 = 32 bytes along the row
-        umma::mma_bf16(tmem, dah + o, dbh + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-        umma::mma_bf16(tmem, dah + o, dbl + o, idesc, 1u);
-        if (NPROD == 3) umma::mma_bf16(tmem, dal + o, dbh + o, idesc, 1u);
-      }
-      umma::mma_commit(&empty[s]);
-    }
-    umma::mma_commit(&accf);
-  } else if (warp >= 2) {
-    // ---------------- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
-    const bool ready = __all_sync(0xffffffffu, umma::mbar_wait(&accf, 0, g.timeout_ns));
-    umma::tc_fence_after();
-    const int q = warp & 3;
-    const int row = m0 + 32 * q + lane;
-    if (!ready) s_abort = 1;
-    if (ready && nkb > 0) {
-#pragma unroll 1
-      for (int cc = 0; cc < GBN / 32; ++cc) {
-        float v[32];
-        umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cc), v);
-        const int col0 = n0 + 32 * cc;
-        if (g.epi == EPI_TILE) {
-          // stage the accumulator in the (now idle) pipeline ring, stride GBN + 1
-          float* tile = (float*)base;
-#pragma unroll
-          for (int u = 0; u < 32; ++u) tile[(32 * q + lane) * (GBN + 1) + 32 * cc + u] = v[u];
-        } else if (row < g.M) {
-          if (g.epi == EPI_PARTIAL) {
-            float* dst = g.P + ((size_t)blockIdx.z * g.M + row) * g.ldp + col0;
-            if (col0 + 32 <= g.N) {
-#pragma unroll
-              for (int u = 0; u < 8; ++u)
-                reinterpret_cast<float4*>(dst)[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-            } else {  // ragged tail: predicated, unrolled (v stays in registers)
-#pragma unroll
-              for (int u = 0; u < 32; ++u)
-                if (col0 + u < g.N) dst[u] = v[u];
-            }
-          } else {
-            const double* f0 = g.f0 + (size_t)row * g.ldf + col0;
-            double* f = g.f + (size_t)row * g.ldf + col0;
-#pragma unroll
-            for (int u = 0; u < 32; ++u)
-              if (col0 + u < g.N) f[u] = (double)v[u] + f0[u];
-          }
-        }
-      }
-    }
-  }
-  umma::tc_fence_before();  // order this thread's tcgen05 work before the teardown barrier
-  __syncthreads();
-  if (g.epi == EPI_TILE && !s_abort && nkb > 0) {
-    // coalesced store of the staged tile: a warp per row, lanes along columns
-    const float* tile = (const float*)base;
-    for (int m = warp; m < GBM; m += 6) {
-      const int r = m0 + m;
-      if (r >= g.M) break;
-      float* dst = g.F32 + (size_t)r * g.ldf32;
-#pragma unroll
-      for (int q = 0; q < GBN / 32; ++q) {
-        const int c = lane + 32 * q;
-        if (n0 + c < g.N) dst[n0 + c] = tile[m * (GBN + 1) + c];
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && s_abort) {
-    atomicExch(g.err, (int)DCOPF_ERR_TIMEOUT);
-    // let the copies still in flight land before the CTA's shared memory is released
-    for (int i = max(0, issued - ST); i < issued; ++i)
-      umma::mbar_wait(&full[i % ST], (i / ST) & 1, g.timeout_ns);
+    __threadfence();  // this block's partials and H entries before its count
+    s_last = atomicAdd(&E.step_done[b], 1) == E.n_tiles - 1;
   }
   __syncthreads();
-  if (warp == 1) {
-    umma::tc_fence_after();
-    umma::tmem_dealloc(tmem, GBN);
+  if (s_last && threadIdx.x < 32) {
+    __threadfence();  // every other block's, before they are read
+    if (threadIdx.x == 0) E.step_done[b] = 0;
+    finalize_instance(b, threadIdx.x, E.ldh, E.max_iters, E.tol, E.st, E.bb, E.outage, E.demand, E.Hh,
+                      E.Hl);
   }
 }
 
-// ------------------------------------------------------------------ CTA-pair products
-// The same products on pairs of CTAs (clusters of 2, tcgen05 cta_group::2): a pair
-// computes a 256 x 256 output tile.  Each CTA loads its own 128 rows of A and its own
-// 128 of the tile's 256 rows of B, so that per byte fed from L2 each CTA does twice the
-// MMA work of a 128 x 128 tile.  The even-ranked CTA issues every MMA; both CTAs'
-// loads count on its "full" barriers; its commits arrive on the "empty" and
-// accumulator barriers of both CTAs.  Each CTA's TMEM holds its 128 rows x 256 columns
-// of the accumulator and each CTA runs the epilogue of its rows.
-constexpr int PBM = 256;
-
-// PBN: the pair tile's width (256 or 192 output columns; each CTA loads PBN / 2 rows of B).
-template <int NPROD, int PBN>
-struct PairCfg {
-  static constexpr uint32_t B_TILE = (uint32_t)(PBN / 2) * GBK * 2;
-  static constexpr uint32_t STAGE_BYTES = (NPROD == 3 ? 2 : 1) * TILE_BYTES + 2 * B_TILE;
-  // as many stages as fit in 224 KB of the 227 KB a CTA may hold (at most five)
-  static constexpr int STAGES = (224u * 1024u / STAGE_BYTES) < 5 ? (224u * 1024u / STAGE_BYTES) : 5;
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
-  static constexpr uint32_t TMEM_COLS = PBN <= 128 ? 128 : 256;  // a power of two
-  static_assert(STAGES >= 2, "a ring of at least two stages");
-  static_assert(B_TILE % 1024 == 0, "tiles start on 1024-byte (swizzle atom) boundaries");
-  static_assert(STAGES * STAGE_BYTES >= 128 * (PBN + 1) * 4, "the ring stages the output tile");
-};
-
-template <int NPROD, int PBN>
-__global__ void __launch_bounds__(192, 1)
-    k_gemm_pair(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
-                const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
-                GemmArgs g) {
-  using Cfg = PairCfg<NPROD, PBN>;
-  constexpr int ST = Cfg::STAGES;
-  extern __shared__ __align__(16) unsigned char gsm_raw[];
-  unsigned char* base = (unsigned char*)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[ST], empty[ST], accf;
-  __shared__ uint32_t tmem_base;
-  __shared__ int s_abort;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = umma::cluster_ctarank();  // 0: issues the MMAs
-  const int m0 = blockIdx.y * PBM, n0 = (blockIdx.x >> 1) * PBN;
-  const int my_m = m0 + 128 * (int)rank;  // this CTA's rows of A and of the output
-  const int my_n = n0 + (PBN / 2) * (int)rank;  // this CTA's rows of B
-  const int kb_total = (g.K + GBK - 1) / GBK;
-  const int kb0 = blockIdx.z * g.kb_per_split;
-  const int nkb = min(kb_total, kb0 + g.kb_per_split) - kb0;
-  auto a_hi = [&](int s) { return base + (size_t)s * Cfg::STAGE_BYTES; };
-  auto a_lo = [&](int s) { return a_hi(s) + TILE_BYTES; };
-  auto b_hi = [&](int s) { return a_hi(s) + (NPROD == 3 ? 2 : 1) * TILE_BYTES; };
-  auto b_lo = [&](int s) { return b_hi(s) + Cfg::B_TILE; };
-
-  if (g.skip) {
-    // both CTAs decide on all 256 rows of the pair, so that they leave together
-    int live = 0;
-    for (int r = threadIdx.x; r < PBM; r += blockDim.x)
-      live |= (m0 + r < g.M && !g.skip[m0 + r]) ? 1 : 0;
-    if (!__syncthreads_or(live)) return;
-  }
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < ST; ++s) {
-      umma::mbar_init(&full[s], 1);
-      umma::mbar_init(&empty[s], 1);
-    }
-    umma::mbar_init(&accf, 1);
-    s_abort = 0;
-    umma::fence_mbar_init();
-  }
-  if (warp == 1) umma::tmem_alloc_pair(&tmem_base, Cfg::TMEM_COLS);
-  __syncthreads();
-  umma::tc_fence_before();
-  umma::cluster_sync_all();  // both CTAs' barriers and TMEM exist before any remote signal
-  umma::tc_fence_after();
-  const uint32_t tmem = tmem_base;
-  int issued = 0;
-
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer (both CTAs; completion counted on rank 0's barrier)
-    for (int i = 0; i < nkb; ++i) {
-      const int s = i % ST;
-      if (i >= ST && !umma::mbar_wait(&empty[s], ((i / ST) & 1) ^ 1, g.timeout_ns)) {
-        s_abort = 1;
-        break;
-      }
-      if (rank == 0) umma::mbar_arrive_expect_tx(&full[s], 2 * Cfg::STAGE_BYTES);
-      const uint32_t bar = umma::cluster_addr(&full[s], 0);
-      const int x = (kb0 + i) * GBK;
-      umma::tma_load_2d_pair(&tAh, bar, a_hi(s), x, my_m);
-      if (NPROD == 3) umma::tma_load_2d_pair(&tAl, bar, a_lo(s), x, my_m);
-      umma::tma_load_2d_pair(&tBh, bar, b_hi(s), x, my_n);
-      umma::tma_load_2d_pair(&tBl, bar, b_lo(s), x, my_n);
-      ++issued;
-    }
-  } else if (warp == 1 && lane == 0 && rank == 0) {
-    // ---------------- MMA issuer (rank 0 only): M = 256 over the pair, N = PBN
-    constexpr uint32_t idesc = umma::idesc_bf16_f32(PBN, PBM);
-    for (int i = 0; i < nkb; ++i) {
-      const int s = i % ST;
-      if (!umma::mbar_wait(&full[s], (i / ST) & 1, g.timeout_ns)) {
-        s_abort = 1;
-        break;
-      }
-      umma::tc_fence_after();
-      const uint64_t dah = umma::desc_sw128(umma::smem_u32(a_hi(s)));
-      const uint64_t dal = umma::desc_sw128(umma::smem_u32(a_lo(s)));
-      const uint64_t dbh = umma::desc_sw128(umma::smem_u32(b_hi(s)));
-      const uint64_t dbl = umma::desc_sw128(umma::smem_u32(b_lo(s)));
-#pragma unroll
-      for (int kk = 0; kk < GBK / 16; ++kk) {
-        const uint64_t o = (uint64_t)(kk * 32) >> 4;
-        umma::mma_bf16_pair(tmem, dah + o, dbh + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-        umma::mma_bf16_pair(tmem, dah + o, dbl + o, idesc, 1u);
-        if (NPROD == 3) umma::mma_bf16_pair(tmem, dal + o, dbh + o, idesc, 1u);
-      }
-      umma::mma_commit_pair(&empty[s], (uint16_t)0x3);
-    }
-    umma::mma_commit_pair(&accf, (uint16_t)0x3);
-  } else if (warp >= 2) {
-    // ---------------- epilogue (both CTAs): warp w reads TMEM lanes 32*(w%4) .. +31
-    const bool ready = __all_sync(0xffffffffu, umma::mbar_wait(&accf, 0, g.timeout_ns));
-    umma::tc_fence_after();
-    const int q = warp & 3;
-    const int row = my_m + 32 * q + lane;
-    if (!ready) s_abort = 1;
-    if (ready && nkb > 0) {
-#pragma unroll 1
-      for (int cc = 0; cc < PBN / 32; ++cc) {
-        float v[32];
-        umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cc), v);
-        const int col0 = n0 + 32 * cc;
-        if (g.epi == EPI_TILE) {
-          float* tile = (float*)base;
-#pragma unroll
-          for (int u = 0; u < 32; ++u) tile[(32 * q + lane) * (PBN + 1) + 32 * cc + u] = v[u];
-        } else if (row < g.M) {
-          if (g.epi == EPI_PARTIAL) {
-            float* dst = g.P + ((size_t)blockIdx.z * g.M + row) * g.ldp + col0;
-            if (col0 + 32 <= g.N) {
-#pragma unroll
-              for (int u = 0; u < 8; ++u)
-                reinterpret_cast<float4*>(dst)[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-            } else {
-#pragma unroll
-              for (int u = 0; u < 32; ++u)
-                if (col0 + u < g.N) dst[u] = v[u];
-            }
-          } else {
-            const double* f0 = g.f0 + (size_t)row * g.ldf + col0;
-            double* f = g.f + (size_t)row * g.ldf + col0;
-#pragma unroll
-            for (int u = 0; u < 32; ++u)
-              if (col0 + u < g.N) f[u] = (double)v[u] + f0[u];
-          }
-        }
-      }
-    }
-  }
-  umma::tc_fence_before();
-  __syncthreads();
-  if (g.epi == EPI_TILE && !s_abort && nkb > 0) {
-    const float* tile = (const float*)base;
-    for (int m = warp; m < 128; m += 6) {
-      const int r = my_m + m;
-      if (r >= g.M) break;
-      float* dst = g.F32 + (size_t)r * g.ldf32;
-#pragma unroll
-      for (int q = 0; q < PBN / 32; ++q) {
-        const int c = lane + 32 * q;
-        if (n0 + c < g.N) dst[n0 + c] = tile[m * (PBN + 1) + c];
-      }
-    }
-  }
-  if (threadIdx.x == 0 && s_abort) {
-    atomicExch(g.err, (int)DCOPF_ERR_TIMEOUT);
-    // rank 0's full barriers count both CTAs' copies: let those in flight land
-    if (rank == 0)
-      for (int i = max(0, issued - ST); i < issued; ++i)
-        umma::mbar_wait(&full[i % ST], (i / ST) & 1, g.timeout_ns);
-  }
-  __syncthreads();
-  // neither CTA releases its shared memory or TMEM while the pair's copies or MMAs may
-  // still reach it
-  umma::tc_fence_before();
-  umma::cluster_sync_all();
-  if (warp == 1) {
-    umma::tc_fence_after();
-    umma::tmem_dealloc_pair(tmem, Cfg::TMEM_COLS);
-  }
-}
 
 // One block per (chunk of STEP_CHUNK lines, instance): elementwise, full occupancy,
 // coalesced; per-chunk FP64 partials of the value and of u^T eta.
@@ -551,6 +205,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
       E.out_part[(size_t)b * E.n_tiles + chunk] = os;
     }
   }
+  step_tail(E, b);
 }
 
 // The same step with four consecutive lines per thread: 16-byte loads and stores of every
@@ -641,6 +296,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) k_bt_step4(StepEpi E, int nl)
       E.out_part[(size_t)b * E.n_tiles + chunk] = os;
     }
   }
+  step_tail(E, b);
 }
 
 // ------------------------------------------------------------------ operand preparation
@@ -774,7 +430,11 @@ dcopf_status ensure_tensor_operands(dcopf_dual* h) {
       !make_map(&T.m_phi_hi96, T.phi_hi.p, nl, ng, T.ld_g, 96) ||
       !make_map(&T.m_phi_lo96, T.phi_lo.p, nl, ng, T.ld_g, 96) ||
       !make_map(&T.m_phit_hi96, T.phit_hi.p, ng, nl, T.ld_l, 96) ||
-      !make_map(&T.m_phit_lo96, T.phit_lo.p, ng, nl, T.ld_l, 96))
+      !make_map(&T.m_phit_lo96, T.phit_lo.p, ng, nl, T.ld_l, 96) ||
+      !make_map(&T.m_phi_hi80, T.phi_hi.p, nl, ng, T.ld_g, 80) ||
+      !make_map(&T.m_phi_lo80, T.phi_lo.p, nl, ng, T.ld_g, 80) ||
+      !make_map(&T.m_phit_hi80, T.phit_hi.p, ng, nl, T.ld_l, 80) ||
+      !make_map(&T.m_phit_lo80, T.phit_lo.p, ng, nl, T.ld_l, 80))
     return DCOPF_ERR_CUDA;
   if (prepare_gemm() != cudaSuccess) return DCOPF_ERR_CUDA;
   T.ready = true;
@@ -823,6 +483,8 @@ static cudaError_t prepare_gemm() {
   DCOPF_PAIR_SMEM(3, 256)
   DCOPF_PAIR_SMEM(2, 192)
   DCOPF_PAIR_SMEM(3, 192)
+  DCOPF_PAIR_SMEM(2, 160)
+  DCOPF_PAIR_SMEM(3, 160)
 #undef DCOPF_PAIR_SMEM
   return cudaSuccess;
 }
@@ -869,6 +531,7 @@ struct LineSet {
   const CUtensorMap *H_hi = nullptr, *H_lo = nullptr;   // adjoint A operand [B][ld_l]
   const CUtensorMap *phit_hi = nullptr, *phit_lo = nullptr, *phit_hi96 = nullptr, *phit_lo96 = nullptr;
   const CUtensorMap *phi_hi = nullptr, *phi_lo = nullptr, *phi_hi96 = nullptr, *phi_lo96 = nullptr;
+  const CUtensorMap *phit_hi80 = nullptr, *phit_lo80 = nullptr, *phi_hi80 = nullptr, *phi_lo80 = nullptr;
   const float* fmax = nullptr;     // [nl]
   const float* fmin = nullptr;
   const float* f0 = nullptr;       // [B][nl] base flows
@@ -884,32 +547,37 @@ static LineSet full_lines(dcopf_dual* h) {
   L.H_hi = &T.m_H_hi; L.H_lo = &T.m_H_lo;
   L.phit_hi = &T.m_phit_hi; L.phit_lo = &T.m_phit_lo; L.phit_hi96 = &T.m_phit_hi96; L.phit_lo96 = &T.m_phit_lo96;
   L.phi_hi = &T.m_phi_hi; L.phi_lo = &T.m_phi_lo; L.phi_hi96 = &T.m_phi_hi96; L.phi_lo96 = &T.m_phi_lo96;
+  L.phit_hi80 = &T.m_phit_hi80; L.phit_lo80 = &T.m_phit_lo80; L.phi_hi80 = &T.m_phi_hi80; L.phi_lo80 = &T.m_phi_lo80;
   L.fmax = h->dev.fmax32;
   L.fmin = h->dev.fmin32;
   L.f0 = h->ws.f0_32.as<float>();
   return L;
 }
 
-// `tiles`: 0 single CTAs (128 x 128), 1 CTA pairs of 256 x 256, 2 CTA pairs of 256 x 192.
-static cudaError_t launch_adjoint(dcopf_dual* h, const LineSet& L, const GemmArgs& g, int splits, int tiles,
-                                  cudaStream_t s) {
-  if (tiles == 1) return launch_gemm_pair<3, 256>(h, *L.H_hi, *L.H_lo, *L.phit_hi, *L.phit_lo, g, splits, s);
-  if (tiles == 2) return launch_gemm_pair<3, 192>(h, *L.H_hi, *L.H_lo, *L.phit_hi96, *L.phit_lo96, g, splits, s);
-  return launch_gemm<3>(h, *L.H_hi, *L.H_lo, *L.phit_hi, *L.phit_lo, g, splits, s);
+// `tiles`: 0 single CTAs (128 x 128), 1 / 2 / 3 CTA pairs of 256 x 256 / 256 x 192 / 256 x 160.
+// Ah / Al: the A operand's rows (the batch's, or one group's of it).
+static cudaError_t launch_adjoint(dcopf_dual* h, const LineSet& L, const CUtensorMap& Ah, const CUtensorMap& Al,
+                                  const GemmArgs& g, int splits, int tiles, cudaStream_t s) {
+  if (tiles == 1) return launch_gemm_pair<3, 256>(h, Ah, Al, *L.phit_hi, *L.phit_lo, g, splits, s);
+  if (tiles == 2) return launch_gemm_pair<3, 192>(h, Ah, Al, *L.phit_hi96, *L.phit_lo96, g, splits, s);
+  if (tiles == 3) return launch_gemm_pair<3, 160>(h, Ah, Al, *L.phit_hi80, *L.phit_lo80, g, splits, s);
+  return launch_gemm<3>(h, Ah, Al, *L.phit_hi, *L.phit_lo, g, splits, s);
 }
-static cudaError_t launch_forward(dcopf_dual* h, const LineSet& L, const GemmArgs& g, int tiles, cudaStream_t s) {
-  TensorOps& T = h->tops;
+static cudaError_t launch_forward(dcopf_dual* h, const LineSet& L, const CUtensorMap& Ah, const CUtensorMap& Al,
+                                  const GemmArgs& g, int tiles, cudaStream_t s) {
   if (h->host.qp) {
-    if (tiles == 1) return launch_gemm_pair<3, 256>(h, T.m_X_hi, T.m_X_lo, *L.phi_hi, *L.phi_lo, g, 1, s);
-    if (tiles == 2) return launch_gemm_pair<3, 192>(h, T.m_X_hi, T.m_X_lo, *L.phi_hi96, *L.phi_lo96, g, 1, s);
-    return launch_gemm<3>(h, T.m_X_hi, T.m_X_lo, *L.phi_hi, *L.phi_lo, g, 1, s);
+    if (tiles == 1) return launch_gemm_pair<3, 256>(h, Ah, Al, *L.phi_hi, *L.phi_lo, g, 1, s);
+    if (tiles == 2) return launch_gemm_pair<3, 192>(h, Ah, Al, *L.phi_hi96, *L.phi_lo96, g, 1, s);
+    if (tiles == 3) return launch_gemm_pair<3, 160>(h, Ah, Al, *L.phi_hi80, *L.phi_lo80, g, 1, s);
+    return launch_gemm<3>(h, Ah, Al, *L.phi_hi, *L.phi_lo, g, 1, s);
   }
-  if (tiles == 1) return launch_gemm_pair<2, 256>(h, T.m_X_hi, T.m_X_lo, *L.phi_hi, *L.phi_lo, g, 1, s);
-  if (tiles == 2) return launch_gemm_pair<2, 192>(h, T.m_X_hi, T.m_X_lo, *L.phi_hi96, *L.phi_lo96, g, 1, s);
+  if (tiles == 1) return launch_gemm_pair<2, 256>(h, Ah, Al, *L.phi_hi, *L.phi_lo, g, 1, s);
+  if (tiles == 2) return launch_gemm_pair<2, 192>(h, Ah, Al, *L.phi_hi96, *L.phi_lo96, g, 1, s);
+  if (tiles == 3) return launch_gemm_pair<2, 160>(h, Ah, Al, *L.phi_hi80, *L.phi_lo80, g, 1, s);
   // the LP forward on single CTAs (two products: x is exact in BF16): its K = n_gen is
   // short, so a CTA spends much of its time in the epilogue; two CTAs per SM (a 2-stage
   // ring each) let one CTA's epilogue run beside the other's main loop
-  return launch_gemm<2, 2>(h, T.m_X_hi, T.m_X_lo, *L.phi_hi, *L.phi_lo, g, 1, s);
+  return launch_gemm<2, 2>(h, Ah, Al, *L.phi_hi, *L.phi_lo, g, 1, s);
 }
 
 // Split-K factor of the adjoint over nl lines: enough CTAs to cover the SMs twice.
@@ -938,7 +606,8 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
   adjoint_split(h, B, nl, &splits, &kbps);
   const LineSet L = full_lines(h);
   int pair_adj = (h->tiles_mode >= 2 && B > GBM) ? h->tiles_mode - 1 : 0, pair_fwd = pair_adj;
-  if (h->tune_B == B && h->tune_nl == nl && h->tune_splits > 0) {  // the shapes a solve of this batch chose
+  if (h->tune_B == B && h->tune_nl == nl && h->tune_splits > 0 && h->tune_branches == 1) {
+    // the shapes a solve of this batch chose
     splits = h->tune_splits;
     kbps = h->tune_kbps;
     pair_adj = h->tune_pair_adj;
@@ -947,7 +616,7 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
   GemmArgs g{};
   g.M = B; g.N = ng; g.K = nl; g.kb_per_split = kbps; g.epi = EPI_PARTIAL;
   g.P = T.P.as<float>(); g.ldp = (ng + 3) & ~3; g.err = h->d_err; g.timeout_ns = 2000000000ull;
-  if (launch_adjoint(h, L, g, splits, pair_adj, s) != cudaSuccess) return DCOPF_ERR_CUDA;
+  if (launch_adjoint(h, L, *L.H_hi, *L.H_lo, g, splits, pair_adj, s) != cudaSuccess) return DCOPF_ERR_CUDA;
   k_reduce_min<<<B, 256, 0, s>>>(h->dev, splits, B, g.ldp, T.P.as<float>(), lambda, T.ld_g,
                                  T.X_hi.as<__nv_bfloat16>(), T.X_lo.as<__nv_bfloat16>(),
                                  w.x64.as<double>(), w.sumcost.as<double>(), w.sump.as<double>());
@@ -956,7 +625,7 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
   f.M = B; f.N = nl; f.K = ng; f.kb_per_split = (ng + GBK - 1) / GBK; f.epi = EPI_FLOW;
   f.f0 = w.f0.as<double>(); f.f = w.f.as<double>(); f.ldf = nl; f.err = h->d_err;
   f.timeout_ns = 2000000000ull;
-  if (launch_forward(h, L, f, pair_fwd, s) != cudaSuccess) return DCOPF_ERR_CUDA;
+  if (launch_forward(h, L, T.m_X_hi, T.m_X_lo, f, pair_fwd, s) != cudaSuccess) return DCOPF_ERR_CUDA;
   return run_eval_finish(h, B, outage, lambda, mh, ml, value, glam, ghi, glo, dispatch, s);
 }
 
@@ -1124,15 +793,16 @@ __global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
 }
 
 // Dual value of the evaluated point (FP64), best value and its lambda, outage patch of
-// the next eta, stop tests.  A stopping instance is frozen: one that reached its
-// target with the point just evaluated (state buffer iter % 3), one stopped by the
-// iteration cap or the tol test with its best point.  One warp per instance.
-__global__ void k_bt_finalize(int B, int ld_l, int max_iters, double tol, SolveStateBase st,
-                              BatchView bb, const int* __restrict__ outage,
-                              const double* __restrict__ demand,
-                              __nv_bfloat16* __restrict__ Hh, __nv_bfloat16* __restrict__ Hl) {
-  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (b >= B || bb.frozen[b]) return;
+// the next eta, stop tests, for instance b, by one warp of the step kernel's last block
+// for the instance.  A stopping instance is frozen: one that reached its target with the
+// point just evaluated (state buffer iter % 3), one stopped by the iteration cap or the
+// tol test with its best point.
+__device__ __forceinline__ void finalize_instance(int b, int lane, int ld_l, int max_iters, double tol,
+                                                  const SolveStateBase& st, const BatchView& bb,
+                                                  const int* __restrict__ outage,
+                                                  const double* __restrict__ demand,
+                                                  __nv_bfloat16* __restrict__ Hh,
+                                                  __nv_bfloat16* __restrict__ Hl) {
   const int nt = bb.n_tiles;
   double ls = 0.0, os = 0.0;
   for (int q = lane; q < nt; q += 32) {
@@ -1161,13 +831,16 @@ __global__ void k_bt_finalize(int B, int ld_l, int max_iters, double tol, SolveS
   }
 }
 
-// Copies the frozen candidates' points to best_* and snapshots which instances are
-// staged (snap[b] = 1): the certificate and the accept step of this round act on
-// exactly those, while the next round's iterations may freeze others.  A candidate
-// that reached its target is the point just evaluated (state buffer iter % 3); one
-// stopped by the iteration cap or the tol test is its best point: point iter or
-// iter - 1 (still in their buffers) or an older one (its saved copy).
-__global__ void k_bt_select(int B, int nl, SolveState<float> st, BatchView bb, int* snap) {
+// Stages the frozen candidates: snap[b] = 1 for each (the certificate and the accept
+// step of this round act on exactly those, while the next round's iterations may freeze
+// others), and copies each one's point into rows of dh / dl ([B][len]): its compact row
+// (pos null, len = nl) or, behind a constraint screen, its full-length row (len = n_line,
+// pos the compact row of each line or -1, zero on the screened lines).  A candidate that
+// reached its target is the point just evaluated (state buffer iter % 3); one stopped by
+// the iteration cap or the tol test is its best point: point iter or iter - 1 (still in
+// their buffers) or an older one (its saved copy).
+__global__ void k_bt_stage(int B, int nl, int len, const int* __restrict__ pos, SolveState<float> st,
+                           BatchView bb, int* snap, float* __restrict__ dh, float* __restrict__ dl) {
   const int b = blockIdx.y;
   const bool staged = st.cand[b] && !st.done[b];
   if (blockIdx.x == 0 && threadIdx.x == 0) snap[b] = staged ? 1 : 0;
@@ -1177,45 +850,63 @@ __global__ void k_bt_select(int B, int nl, SolveState<float> st, BatchView bb, i
   const int back = (st.cand[b] == 1 || st.best_iter[b] < 1) ? 0 : it + 1 - st.best_iter[b];
   const float* bh[3] = {st.mu_hi, bb.mu2_hi, bb.mu3_hi};
   const float* bl[3] = {st.mu_lo, bb.mu2_lo, bb.mu3_lo};
-  const float* sh = back <= 1 ? bh[(it - back) % 3] : bb.sv_hi;
-  const float* sl = back <= 1 ? bl[(it - back) % 3] : bb.sv_lo;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
-    st.best_hi[(size_t)b * nl + i] = sh[(size_t)b * nl + i];
-    st.best_lo[(size_t)b * nl + i] = sl[(size_t)b * nl + i];
+  const float* sh = (back <= 1 ? bh[(it - back) % 3] : bb.sv_hi) + (size_t)b * nl;
+  const float* sl = (back <= 1 ? bl[(it - back) % 3] : bb.sv_lo) + (size_t)b * nl;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+    const int r = pos ? pos[i] : i;
+    dh[(size_t)b * len + i] = r >= 0 ? sh[r] : 0.f;
+    dl[(size_t)b * len + i] = r >= 0 ? sl[r] : 0.f;
   }
 }
 
-// After certification: accept, stop, or unfreeze with a larger in-loop margin.  The
-// evaluation of a frozen point counts; an unfrozen instance moves on to the point
-// already stepped to.
-__global__ void k_bt_accept(int B, double ub_any, SolveStateBase st, BatchView bb,
-                            const int* __restrict__ snap, int* active) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
-  if (snap[b] && !st.done[b] && st.cand[b]) {
-    const double c = st.cert[b];
-    if (st.cand[b] == 1) {
-      if (c >= st.thresh[b]) {
-        st.done[b] = 1;
-        st.status[b] = 0;
+// After certification: accept, stop, or unfreeze with a larger in-loop margin each
+// staged instance (when `accept`; the evaluation of a frozen point counts, and an
+// unfrozen instance moves on to the point already stepped to); then the number of
+// instances still running into *out_active and the device error word into *out_err
+// (host-mapped memory).  One block.
+constexpr int ACCEPT_THREADS = 512;
+__global__ void __launch_bounds__(ACCEPT_THREADS)
+    k_bt_accept(int B, int accept, double ub_any, SolveStateBase st, BatchView bb,
+                const int* __restrict__ snap, const int* __restrict__ err, int* out_active,
+                int* out_err) {
+  __shared__ int red[ACCEPT_THREADS / 32];
+  int running = 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    if (accept && snap[b] && !st.done[b] && st.cand[b]) {
+      const double c = st.cert[b];
+      if (st.cand[b] == 1) {
+        if (c >= st.thresh[b]) {
+          st.done[b] = 1;
+          st.status[b] = 0;
+        } else {
+          st.margin[b] += fmax(st.thresh[b] - c, 1e-7 * fabs(st.thresh[b]));
+          st.cand[b] = 0;
+          bb.frozen[b] = 0;
+        }
       } else {
-        st.margin[b] += fmax(st.thresh[b] - c, 1e-7 * fabs(st.thresh[b]));
-        st.cand[b] = 0;
-        bb.frozen[b] = 0;
+        st.done[b] = 1;
+        st.status[b] = (c >= st.thresh[b]) ? 0 : 1;
       }
-    } else {
-      st.done[b] = 1;
-      st.status[b] = (c >= st.thresh[b]) ? 0 : 1;
+      if (c > ub_any) { st.done[b] = 1; st.status[b] = 2; bb.frozen[b] = 1; }
+      st.iter[b] += 1;
     }
-    if (c > ub_any) { st.done[b] = 1; st.status[b] = 2; bb.frozen[b] = 1; }
-    st.iter[b] += 1;
+    running += st.done[b] ? 0 : 1;
   }
-  if (!st.done[b]) atomicAdd(active, 1);
+  running = __reduce_add_sync(0xffffffffu, running);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = running;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) n += red[w];
+    *out_active = n;
+    *out_err = *err;
+  }
 }
 
 __global__ void k_bt_init(int B, BatchView bb) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
     bb.frozen[b] = 0;
+    bb.step_done[b] = 0;
     bb.pw[3 * b] = 1.0;
     bb.pw[3 * b + 1] = 1.0;
     bb.pw[3 * b + 2] = 1.0;
@@ -1228,7 +919,7 @@ static dcopf_status ensure_batch_bufs(dcopf_dual* h, int B, int n_tiles) {
   const size_t nl = h->host.n_line;
   if (bb.mu2.alloc((size_t)B * nl * 6 * sizeof(float)) ||
       bb.parts.alloc((size_t)B * n_tiles * 2 * sizeof(double)) ||
-      bb.small.alloc((size_t)B * 7 * sizeof(double) + (size_t)B * 6 * sizeof(float) + 1024)) {
+      bb.small.alloc((size_t)B * 7 * sizeof(double) + (size_t)B * 7 * sizeof(float) + 1024)) {
     cudaGetLastError();
     return DCOPF_ERR_OOM;
   }
@@ -1246,9 +937,33 @@ static dcopf_status ensure_batch_bufs(dcopf_dual* h, int B, int n_tiles) {
   float* f = (float*)(d + 7 * (size_t)B);
   v.tout = f; v.stepf = f + B;  // stepf: [B][4]
   v.frozen = (int*)(f + 5 * (size_t)B);
+  v.step_done = (int*)(f + 6 * (size_t)B);
   v.n_tiles = n_tiles;
   return DCOPF_OK;
 }
+
+// One group of a batch's instances, [b0, b0 + B): the kernel arguments of its
+// iteration chain, every per-instance pointer advanced to the group's first instance.
+struct IterView {
+  int b0 = 0, B = 0;
+  SolveState<float> st{};
+  BatchView bb{};
+  GemmArgs ga{}, gf{};
+  StepEpi E{};
+  CUtensorMap Hh{}, Hl{}, Xh{}, Xl{};  // the group's rows of the two products' A operands
+  const int* outage = nullptr;         // [B] or null
+  const double* demand = nullptr;      // [B]
+  __nv_bfloat16 *Xhp = nullptr, *Xlp = nullptr, *Hhp = nullptr, *Hlp = nullptr;
+};
+// A batch runs as one group, or as two whose iteration chains are parallel branches of
+// the iteration graph: one group's HBM-bound step and latency-bound minimiser then run
+// beside the other's tensor-core products.
+constexpr int MAX_BRANCHES = 2;
+
+// Product shapes of the batched iteration, as launch_adjoint's `tiles`.
+struct TensorShapes {
+  int adj = 0, splits = 1, kbps = 1, fwd = 0;
+};
 
 // One network's share of a batched tensor-core solve: the instances, the kernel
 // arguments of one iteration, and the solve state.
@@ -1264,7 +979,147 @@ struct TensorRun {
   LineSet ls;                      // the lines iterated on
   unsigned gi = 1;
   bool running = true;
+  int nv = 1;                      // instance groups, iterated as parallel graph branches
+  IterView v[MAX_BRANCHES];
 };
+
+template <typename T>
+static void adv(T*& p, size_t n) {
+  if (p) p += n;
+}
+
+// The view of instances [b0, b0 + Bg) of R's batch.
+static bool make_view(TensorRun& R, int b0, int Bg, IterView* V) {
+  dcopf_dual* h = R.it.h;
+  TensorOps& T = h->tops;
+  const size_t nl = R.ls.nl, ng = h->host.n_gen, nt = R.n_tiles, o = b0;
+  IterView& W = *V;
+  W = IterView{};
+  W.b0 = b0;
+  W.B = Bg;
+  SolveState<float>& st = W.st;
+  st = R.st;
+  adv(st.s, o * ng); adv(st.s1_s, o * ng); adv(st.s2_s, o * ng);
+  for (int** q : {&st.done, &st.cand, &st.iter, &st.best_iter, &st.status}) adv(*q, o);
+  for (double** q : {&st.best, &st.best_next, &st.best_lam, &st.thresh, &st.margin, &st.prev,
+                     &st.prev2, &st.lam, &st.lam_s1, &st.lam_s2, &st.cert, &st.wsum})
+    adv(*q, o);
+  adv(st.xsum, o * ng);
+  for (float** q : {&st.mu_hi, &st.mu_lo, &st.s1_hi, &st.s2_hi, &st.s1_lo, &st.s2_lo, &st.best_hi,
+                    &st.best_lo})
+    adv(*q, o * nl);
+  BatchView& bb = W.bb;
+  bb = h->bb.v;
+  adv(bb.frozen, o); adv(bb.lam_eval, o); adv(bb.cost, o); adv(bb.psum, o); adv(bb.pw, 3 * o);
+  adv(bb.tout, o); adv(bb.stepf, 4 * o); adv(bb.lam_best, o); adv(bb.step_done, o);
+  for (float** q : {&bb.mu2_hi, &bb.mu2_lo, &bb.mu3_hi, &bb.mu3_lo, &bb.sv_hi, &bb.sv_lo}) adv(*q, o * nl);
+  adv(bb.line_part, o * nt); adv(bb.out_part, o * nt);
+  W.ga = R.ga;
+  W.ga.M = Bg;
+  W.ga.P = R.ga.P + (size_t)64 * o * R.ga.ldp;  // the partials' [64][B][ldp] share of the group
+  W.ga.skip = bb.frozen;
+  W.gf = R.gf;
+  W.gf.M = Bg;
+  W.gf.F32 = R.gf.F32 + o * R.gf.ldf32;
+  W.gf.skip = bb.frozen;
+  StepEpi& E = W.E;
+  E = R.E;
+  E.F = R.E.F + o * R.E.ldF;
+  E.f0 = R.E.f0 + o * nl;
+  adv(E.u, o * nl);
+  adv(E.outage, o);
+  E.tout = bb.tout; E.iter = st.iter; E.frozen = bb.frozen; E.best_iter = st.best_iter; E.stepf = bb.stepf;
+  E.mu_hi[0] = st.mu_hi; E.mu_hi[1] = bb.mu2_hi; E.mu_hi[2] = bb.mu3_hi;
+  E.mu_lo[0] = st.mu_lo; E.mu_lo[1] = bb.mu2_lo; E.mu_lo[2] = bb.mu3_lo;
+  E.sv_hi = bb.sv_hi; E.sv_lo = bb.sv_lo;
+  E.s1_hi = st.s1_hi; E.s2_hi = st.s2_hi; E.s1_lo = st.s1_lo; E.s2_lo = st.s2_lo;
+  E.Hh = R.E.Hh + o * E.ldh;
+  E.Hl = R.E.Hl + o * E.ldh;
+  E.line_part = bb.line_part; E.out_part = bb.out_part;
+  E.st = st;
+  E.bb = bb;
+  E.step_done = bb.step_done;
+  W.outage = R.it.outage ? R.it.outage + o : nullptr;
+  W.demand = h->ws.demand.as<double>() + o;
+  E.demand = W.demand;
+  W.Xhp = T.X_hi.as<__nv_bfloat16>() + o * T.ld_g;
+  W.Xlp = T.X_lo.as<__nv_bfloat16>() + o * T.ld_g;
+  W.Hhp = E.Hh;
+  W.Hlp = E.Hl;
+  return make_map(&W.Hh, W.Hhp, Bg, nl, R.ls.ld_l, GBM) && make_map(&W.Hl, W.Hlp, Bg, nl, R.ls.ld_l, GBM) &&
+         make_map(&W.Xh, W.Xhp, Bg, ng, T.ld_g, GBM) && make_map(&W.Xl, W.Xlp, Bg, ng, T.ld_g, GBM);
+}
+
+// The first group's size when the batch runs as two: half the batch, rounded up to
+// whole 256-row pair tiles where the batch has at least 1024 instances, else to
+// 128-row tiles.
+int tensor_first_group(int B) {
+  const int q = B >= 1024 ? 256 : 128;
+  return std::min(B - 1, ((B + 1) / 2 + q - 1) / q * q);
+}
+
+// R's groups: the whole batch (nv = 1) or its two groups (nv = 2).
+static dcopf_status make_views(TensorRun& R, int nv) {
+  const int B = R.it.B;
+  R.nv = nv;
+  if (nv == 1) return make_view(R, 0, B, &R.v[0]) ? DCOPF_OK : DCOPF_ERR_CUDA;
+  const int b1 = tensor_first_group(B);
+  return make_view(R, 0, b1, &R.v[0]) && make_view(R, b1, B - b1, &R.v[1]) ? DCOPF_OK : DCOPF_ERR_CUDA;
+}
+
+static void apply_shapes(TensorRun& R, const TensorShapes& S) {
+  R.splits = S.splits;
+  R.pair_adj = S.adj;
+  R.pair_fwd = S.fwd;
+  for (IterView& V : R.v) V.ga.kb_per_split = S.kbps;
+}
+
+// Enqueues n iterations of group V's chain (adjoint GEMM, minimiser, forward GEMM,
+// step, value) on cs; with `mark`, the timing events around the kernels of the last.
+static bool enqueue_iters(TensorRun& R, IterView& V, int n, cudaStream_t cs, bool mark_last) {
+  dcopf_dual* h = R.it.h;
+  const int nl = R.ls.nl;
+  TensorOps& T = h->tops;
+  bool ok = true;
+  for (int it = 0; it < n && ok; ++it) {
+    // timing on: event nodes around the kernels of the round's last iteration
+    const bool mark = mark_last && h->timing && h->kev[0] && it == n - 1;
+    // (external event-record nodes: a plain record during capture only orders streams)
+    auto ev = [&](int q) {
+      if (mark) ok &= cudaEventRecordWithFlags(h->kev[q], cs, cudaEventRecordExternal) == cudaSuccess;
+    };
+    ev(0);
+    ok &= launch_adjoint(h, R.ls, V.Hh, V.Hl, V.ga, R.splits, R.pair_adj, cs) == cudaSuccess;
+    ev(1);
+    k_bt_minimize<<<V.B, minimize_threads(h, V.B), 0, cs>>>(h->dev, R.splits, V.B, V.ga.ldp, V.ga.P, V.st,
+                                                            V.bb, R.P, T.ld_g, V.Xhp, V.Xlp, V.outage,
+                                                            V.demand);
+    ev(2);
+    ok &= launch_forward(h, R.ls, V.Xh, V.Xl, V.gf, R.pair_fwd, cs) == cudaSuccess;
+    ev(3);
+    if (nl % 4 == 0 && V.E.ldF % 4 == 0 && V.E.ldh % 4 == 0)
+      k_bt_step4<<<dim3(R.n_tiles, V.B), STEP_THREADS, 0, cs>>>(V.E, nl);
+    else
+      k_bt_step<<<dim3(R.n_tiles, V.B), STEP_THREADS, 0, cs>>>(V.E, nl);
+    ev(4);  // the value and stop tests run in the step kernel's last block per instance
+    ev(5);
+  }
+  return ok;
+}
+
+// Enqueues `chunk` iterations of every group on cs (the groups after the first on the
+// handle's second stream, forked from cs and joined back to it).
+static bool tensor_enqueue_chunk(TensorRun& R, int chunk, cudaStream_t cs) {
+  dcopf_dual* h = R.it.h;
+  if (R.nv == 1) return enqueue_iters(R, R.v[0], chunk, cs, true);
+  bool ok = cudaEventRecord(h->fork_ev, cs) == cudaSuccess &&
+            cudaStreamWaitEvent(h->tstream2, h->fork_ev, 0) == cudaSuccess;
+  ok = ok && enqueue_iters(R, R.v[0], chunk, cs, true);
+  ok = ok && enqueue_iters(R, R.v[1], chunk, h->tstream2, false);
+  ok = ok && cudaEventRecord(h->join_ev, h->tstream2) == cudaSuccess &&
+       cudaStreamWaitEvent(cs, h->join_ev, 0) == cudaSuccess;
+  return ok;
+}
 
 // Initial state (cold or warm start), per-instance flags, and the BF16 split of the
 // first eta, on stream cs.
@@ -1299,22 +1154,23 @@ static void tensor_init_state(TensorRun& R, cudaStream_t cs) {
   h->launches += 3;
 }
 
-// Autotuner of the batched products' shapes, on the first solve of a batch size:
-//  - the adjoint: single CTAs (128 x 128 tiles) or CTA pairs (256 x 256), each with
-//    split-K factors around a heuristic and the factors that fill whole waves; more
-//    splits fill the SMs with CTAs but add FP32 partial traffic to the minimiser's
-//    reduction, so each candidate is timed as adjoint + minimiser;
+// Autotuner of the batched products' shapes for the instances of group V, on the
+// first solve of a batch size:
+//  - the adjoint: single CTAs (128 x 128 tiles) or CTA pairs (256 x 256 or 256 x 192),
+//    each with split-K factors around a heuristic and the factors that fill whole
+//    waves; more splits fill the SMs with CTAs but add FP32 partial traffic to the
+//    minimiser's reduction, so each candidate is timed as adjoint + minimiser;
 //  - the forward product: single CTAs or CTA pairs.
-// Timed with CUDA events on the solve's stream; the fastest of each is kept per handle.
-static dcopf_status tune_tensor_shapes(TensorRun& R, cudaStream_t cs) {
+// Timed with CUDA events on the solve's stream; the fastest of each goes to *out.
+static dcopf_status tune_view_shapes(TensorRun& R, IterView& V, cudaStream_t cs, TensorShapes* out) {
   dcopf_dual* h = R.it.h;
-  const int B = R.it.B, ng = h->host.n_gen;
+  const int B = V.B, ng = h->host.n_gen;
   TensorOps& T = h->tops;
-  Workspace& w = h->ws;
   const int kb = (R.ls.nl + GBK - 1) / GBK;
   const bool pair_ok = B > GBM && h->tiles_mode != 1;
   const bool single_ok = h->tiles_mode <= 1 || B <= GBM;
-  const int tv_lo = h->tiles_mode == 3 ? 2 : 1, tv_hi = h->tiles_mode == 2 ? 1 : 2;
+  // pair widths tried: tiles codes tv_lo .. tv_hi (all three unless DCOPF_TENSOR_TILES fixes one)
+  const int tv_lo = h->tiles_mode >= 2 ? h->tiles_mode - 1 : 1, tv_hi = h->tiles_mode >= 2 ? h->tiles_mode - 1 : 3;
   struct Cand { int tiles; int splits; };  // tiles as launch_adjoint's
   std::vector<Cand> cand;
   auto add = [&](int tiles, int sp) {
@@ -1326,7 +1182,8 @@ static dcopf_status tune_tensor_shapes(TensorRun& R, cudaStream_t cs) {
     cand.push_back({tiles, se});
   };
   if (single_ok) {
-    const int s0 = R.splits;
+    int s0 = 1, kb0 = 1;
+    adjoint_split(h, B, R.ls.nl, &s0, &kb0);
     for (int num : {1, 2, 3, 4, 6, 8}) add(0, (s0 * num + 2) / 4);
     // and the splits that fill whole waves (one CTA per SM): the last wave of a grid of
     // tiles x splits CTAs is then full rather than a few CTAs on an idle GPU
@@ -1335,7 +1192,7 @@ static dcopf_status tune_tensor_shapes(TensorRun& R, cudaStream_t cs) {
   }
   if (pair_ok) {
     for (int tv = tv_lo; tv <= tv_hi; ++tv) {
-      const int bn = tv == 1 ? 256 : 192;
+      const int bn = tv == 1 ? 256 : tv == 2 ? 192 : 160;
       const int ptiles = ((B + PBM - 1) / PBM) * ((ng + bn - 1) / bn);
       const int slots = h->sm_count / 2;  // one pair per two SMs
       const int s0 = std::max(1, (slots + ptiles - 1) / ptiles);
@@ -1359,28 +1216,25 @@ static dcopf_status tune_tensor_shapes(TensorRun& R, cudaStream_t cs) {
     }
     return DCOPF_OK;
   };
-  static const char* kTiles[3] = {"single 128x128", "pairs 256x256", "pairs 256x192"};
+  static const char* kTiles[4] = {"single 128x128", "pairs 256x256", "pairs 256x192", "pairs 256x160"};
   float best = 1e30f;
   Cand bc = cand.empty() ? Cand{0, 1} : cand[0];
   int best_per = (kb + bc.splits - 1) / bc.splits;
-  dcopf_status out = DCOPF_OK;
+  dcopf_status res = DCOPF_OK;
   for (const Cand& c : cand) {
-    GemmArgs g = R.ga;
+    GemmArgs g = V.ga;
     g.kb_per_split = (kb + c.splits - 1) / c.splits;
     float ms = 0.f;
-    out = timed(
+    res = timed(
         [&] {
-          cudaError_t e = launch_adjoint(h, R.ls, g, c.splits, c.tiles, cs);
-          k_bt_minimize<<<B, minimize_threads(h, B), 0, cs>>>(h->dev, c.splits, B, g.ldp, T.P.as<float>(),
-                                                              R.st, h->bb.v, R.P, T.ld_g,
-                                                              T.X_hi.as<__nv_bfloat16>(),
-                                                              T.X_lo.as<__nv_bfloat16>(), R.it.outage,
-                                                              w.demand.as<double>());
+          cudaError_t e = launch_adjoint(h, R.ls, V.Hh, V.Hl, g, c.splits, c.tiles, cs);
+          k_bt_minimize<<<B, minimize_threads(h, B), 0, cs>>>(h->dev, c.splits, B, g.ldp, g.P, V.st, V.bb, R.P,
+                                                              T.ld_g, V.Xhp, V.Xlp, V.outage, V.demand);
           h->launches += 1;
           return e != cudaSuccess ? e : cudaGetLastError();
         },
         &ms);
-    if (out != DCOPF_OK) break;
+    if (res != DCOPF_OK) break;
     if (h->verbose)
       fprintf(stderr, "dcopf: batch %d adjoint %s split-K %d: %.1f us per GEMM+min\n", B,
               kTiles[c.tiles], c.splits, 1e3f * ms / 3.f);
@@ -1392,14 +1246,14 @@ static dcopf_status tune_tensor_shapes(TensorRun& R, cudaStream_t cs) {
   }
   // the forward product, on the operands the runs above left
   int fwd = (pair_ok && !single_ok) ? tv_lo : 0;
-  if (out == DCOPF_OK && pair_ok) {
+  if (res == DCOPF_OK && pair_ok) {
     float bf = 1e30f;
-    for (int tv = single_ok ? 0 : tv_lo; tv <= tv_hi && out == DCOPF_OK; ++tv) {
+    for (int tv = single_ok ? 0 : tv_lo; tv <= tv_hi && res == DCOPF_OK; ++tv) {
       if (tv > 0 && tv < tv_lo) continue;
       float ms = 0.f;
-      out = timed([&] { return launch_forward(h, R.ls, R.gf, tv, cs); }, &ms);
+      res = timed([&] { return launch_forward(h, R.ls, V.Xh, V.Xl, V.gf, tv, cs); }, &ms);
       if (h->verbose) fprintf(stderr, "dcopf: batch %d forward %s: %.1f us\n", B, kTiles[tv], 1e3f * ms / 3.f);
-      if (out == DCOPF_OK && ms < bf) {
+      if (res == DCOPF_OK && ms < bf) {
         bf = ms;
         fwd = tv;
       }
@@ -1407,20 +1261,74 @@ static dcopf_status tune_tensor_shapes(TensorRun& R, cudaStream_t cs) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (out != DCOPF_OK) return out;
+  if (res != DCOPF_OK) return res;
   int derr = 0;
   if (cudaMemcpy(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return DCOPF_ERR_CUDA;
   if (derr) return (dcopf_status)derr;
-  h->tune_B = B;
-  h->tune_nl = R.ls.nl;
-  h->tune_splits = bc.splits;
-  h->tune_kbps = best_per;
-  h->tune_pair_adj = bc.tiles;
-  h->tune_pair_fwd = fwd;
+  out->adj = bc.tiles;
+  out->splits = bc.splits;
+  out->kbps = best_per;
+  out->fwd = fwd;
   if (h->verbose)
     fprintf(stderr, "dcopf: batch %d adjoint %s split-K %d (%.1f us per GEMM+min), forward %s\n", B,
             kTiles[bc.tiles], bc.splits, 1e3f * best / 3.f, kTiles[fwd]);
+  return DCOPF_OK;
+}
+
+// Milliseconds of 6 whole iterations of every group of R (after 6 that warm up).
+static dcopf_status time_iterations(TensorRun& R, cudaStream_t cs, float* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return DCOPF_ERR_CUDA;
+  }
+  dcopf_status res = DCOPF_OK;
+  for (int rep = 0; rep < 2 && res == DCOPF_OK; ++rep) {
+    if (cudaEventRecord(e0, cs) != cudaSuccess || !tensor_enqueue_chunk(R, 6, cs) ||
+        cudaEventRecord(e1, cs) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      res = DCOPF_ERR_CUDA;
+  }
+  R.it.h->launches += 2LL * 6 * 2 * R.nv;  // the products count themselves
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return res;
+}
+
+// The shapes and the grouping of the batch: each grouping's product shapes by
+// tune_view_shapes, then the whole iteration under each grouping, timed; the faster
+// is kept per handle.
+static dcopf_status tune_tensor(TensorRun& R, cudaStream_t cs) {
+  dcopf_dual* h = R.it.h;
+  const int B = R.it.B;
+  dcopf_status r;
+  TensorShapes s1, s2;
+  if ((r = make_views(R, 1)) || (r = tune_view_shapes(R, R.v[0], cs, &s1))) return r;
+  int nv = 1;
+  TensorShapes best = s1;
+  if (B >= 2 * GBM) {
+    float t1 = 0.f, t2 = 0.f;
+    apply_shapes(R, s1);
+    if ((r = time_iterations(R, cs, &t1))) return r;
+    if ((r = make_views(R, 2)) || (r = tune_view_shapes(R, R.v[0], cs, &s2))) return r;
+    apply_shapes(R, s2);
+    if ((r = time_iterations(R, cs, &t2))) return r;
+    if (h->verbose)
+      fprintf(stderr, "dcopf: batch %d one group %.1f us, two groups %.1f us per iteration\n", B,
+              1e3f * t1 / 6.f, 1e3f * t2 / 6.f);
+    if (t2 < t1) {
+      nv = 2;
+      best = s2;
+    }
+  }
+  h->tune_B = B;
+  h->tune_nl = R.ls.nl;
+  h->tune_splits = best.splits;
+  h->tune_kbps = best.kbps;
+  h->tune_pair_adj = best.adj;
+  h->tune_pair_fwd = best.fwd;
+  h->tune_branches = nv;
   return DCOPF_OK;
 }
 
@@ -1462,6 +1370,7 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
     L.H_hi = &S.m_H_hi; L.H_lo = &S.m_H_lo;
     L.phit_hi = &S.m_phit_hi; L.phit_lo = &S.m_phit_lo; L.phit_hi96 = &S.m_phit_hi96; L.phit_lo96 = &S.m_phit_lo96;
     L.phi_hi = &S.m_phi_hi; L.phi_lo = &S.m_phi_lo; L.phi_hi96 = &S.m_phi_hi96; L.phi_lo96 = &S.m_phi_lo96;
+    L.phit_hi80 = &S.m_phit_hi80; L.phit_lo80 = &S.m_phit_lo80; L.phi_hi80 = &S.m_phi_hi80; L.phi_lo80 = &S.m_phi_lo80;
     L.fmax = S.lim.as<float>();
     L.fmin = S.lim.as<float>() + nk;
     L.f0 = S.f0c.as<float>();
@@ -1510,70 +1419,39 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   E.s1_hi = R.st.s1_hi; E.s2_hi = R.st.s2_hi; E.s1_lo = R.st.s1_lo; E.s2_lo = R.st.s2_lo;
   E.Hh = T.H_hi.as<__nv_bfloat16>(); E.Hl = T.H_lo.as<__nv_bfloat16>(); E.ldh = R.ls.ld_l;
   E.line_part = bb.line_part; E.out_part = bb.out_part; E.n_tiles = R.n_tiles;
+  E.st = R.st; E.bb = bb; E.demand = w.demand.as<double>(); E.step_done = bb.step_done;
+  E.max_iters = p.max_iters; E.tol = p.tol;
   if (h->timing && !h->kev[0])
     for (int q = 0; q < 6; ++q)
       if (cudaEventCreate(&h->kev[q]) != cudaSuccess) return DCOPF_ERR_CUDA;
   if (h->shape_adj >= 0 && (h->tune_B != B || h->tune_nl != nl)) {  // shapes fixed at create: no timing
     const int kb = (nl + GBK - 1) / GBK;
-    const bool pairs_fit = B > GBM;
+    const int nv = B >= 2 * GBM ? h->shape_branches : 1;
+    const bool pairs_fit = (nv == 1 ? B : tensor_first_group(B)) > GBM;
     h->tune_B = B;
     h->tune_nl = nl;
     h->tune_kbps = (kb + h->shape_splits - 1) / h->shape_splits;
     h->tune_splits = (kb + h->tune_kbps - 1) / h->tune_kbps;
     h->tune_pair_adj = pairs_fit ? h->shape_adj : 0;
     h->tune_pair_fwd = pairs_fit ? h->shape_fwd : 0;
+    h->tune_branches = nv;
   }
+  if (!h->tstream2 && cudaStreamCreateWithFlags(&h->tstream2, cudaStreamNonBlocking) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
+  if ((!h->fork_ev && cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess) ||
+      (!h->join_ev && cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess))
+    return DCOPF_ERR_CUDA;
   if (h->tune_B != B || h->tune_nl != nl) {
-    if ((r = tune_tensor_shapes(R, cs))) return r;
+    if ((r = tune_tensor(R, cs))) return r;
     tensor_init_state(R, cs);  // the timed runs stepped lambda: start again
   }
-  R.splits = h->tune_splits;
-  R.ga.kb_per_split = h->tune_kbps;
-  R.pair_adj = h->tune_pair_adj;
-  R.pair_fwd = h->tune_pair_fwd;
   R.ga.skip = bb.frozen;
   R.gf.skip = bb.frozen;
   // the mean of the minimisers starts after the tuning runs
-  return ensure_mean(h, B, &R.st, true, p.mean_dispatch != nullptr, cs);
-}
-
-// Enqueues `chunk` iterations (adjoint GEMM, minimiser, forward GEMM, step, value) on
-// cs, which is capturing.
-static bool tensor_enqueue_chunk(TensorRun& R, int chunk, cudaStream_t cs) {
-  dcopf_dual* h = R.it.h;
-  const int B = R.it.B, nl = R.ls.nl;
-  TensorOps& T = h->tops;
-  Workspace& w = h->ws;
-  BatchView& bb = h->bb.v;
-  bool ok = true;
-  for (int it = 0; it < chunk && ok; ++it) {
-    // timing on: event nodes around the kernels of the round's last iteration
-    const bool mark = h->timing && h->kev[0] && it == chunk - 1;
-    // (external event-record nodes: a plain record during capture only orders streams)
-    auto ev = [&](int q) {
-      if (mark) ok &= cudaEventRecordWithFlags(h->kev[q], cs, cudaEventRecordExternal) == cudaSuccess;
-    };
-    ev(0);
-    ok &= launch_adjoint(h, R.ls, R.ga, R.splits, R.pair_adj, cs) == cudaSuccess;
-    ev(1);
-    k_bt_minimize<<<B, minimize_threads(h, B), 0, cs>>>(h->dev, R.splits, B, R.ga.ldp, T.P.as<float>(), R.st, bb, R.P,
-                                     T.ld_g, T.X_hi.as<__nv_bfloat16>(), T.X_lo.as<__nv_bfloat16>(),
-                                     R.it.outage, w.demand.as<double>());
-    ev(2);
-    ok &= launch_forward(h, R.ls, R.gf, R.pair_fwd, cs) == cudaSuccess;
-    ev(3);
-    if (nl % 4 == 0 && R.E.ldF % 4 == 0 && R.E.ldh % 4 == 0)
-      k_bt_step4<<<dim3(R.n_tiles, B), STEP_THREADS, 0, cs>>>(R.E, nl);
-    else
-      k_bt_step<<<dim3(R.n_tiles, B), STEP_THREADS, 0, cs>>>(R.E, nl);
-    ev(4);
-    k_bt_finalize<<<(B + 3) / 4, 128, 0, cs>>>(B, R.ls.ld_l, R.p.max_iters, R.p.tol, R.st, bb,
-                                               R.it.outage, w.demand.as<double>(),
-                                               T.H_hi.as<__nv_bfloat16>(),
-                                               T.H_lo.as<__nv_bfloat16>());
-    ev(5);
-  }
-  return ok;
+  if ((r = ensure_mean(h, B, &R.st, true, p.mean_dispatch != nullptr, cs))) return r;
+  if ((r = make_views(R, h->tune_branches))) return r;
+  apply_shapes(R, TensorShapes{h->tune_pair_adj, h->tune_splits, h->tune_kbps, h->tune_pair_fwd});
+  return DCOPF_OK;
 }
 
 // After a chunk: stage and snapshot the frozen candidates (on the solve's stream cs),
@@ -1586,21 +1464,19 @@ static dcopf_status tensor_stage_certify(TensorRun& R, cudaStream_t cs, cudaStre
   const int B = R.it.B, nl = R.ls.nl, n_line = h->host.n_line;
   BatchView& bb = h->bb.v;
   int* snap = h->bb.snap.as<int>();
-  k_bt_select<<<dim3((nl + 255) / 256, B), 256, 0, cs>>>(B, nl, R.st, bb, snap);
-  const float* bh = R.st.best_hi;
-  const float* bl = R.st.best_lo;
+  // the certificate evaluates the full problem: behind a screen, the staged points on
+  // every line, zero on the screened ones
+  float* bh = R.st.best_hi;
+  float* bl = R.st.best_lo;
+  int len = nl;
   if (R.ls.kept) {
-    // the certificate evaluates the full problem: the staged points on every line,
-    // zero on the screened ones
-    float* fh = h->scr.full.as<float>();
-    float* fl = fh + (size_t)B * n_line;
-    const unsigned g = (unsigned)std::min<long long>(((long long)B * n_line + 255) / 256, 4096);
-    k_screen_scatter_rows<<<g, 256, 0, cs>>>(B, n_line, nl, R.ls.pos, R.st.best_hi, fh);
-    k_screen_scatter_rows<<<g, 256, 0, cs>>>(B, n_line, nl, R.ls.pos, R.st.best_lo, fl);
-    h->launches += 2;
-    bh = fh;
-    bl = fl;
+    bh = h->scr.full.as<float>();
+    bl = bh + (size_t)B * n_line;
+    len = n_line;
   }
+  k_bt_stage<<<dim3((len + 1023) / 1024, B), 256, 0, cs>>>(B, nl, len, R.ls.kept ? R.ls.pos : nullptr, R.st, bb,
+                                                          snap, bh, bl);
+  h->launches += 1;
   if (cudaEventRecord(staged_ev, cs) != cudaSuccess || cudaStreamWaitEvent(cc, staged_ev, 0) != cudaSuccess)
     return DCOPF_ERR_CUDA;
   dcopf_status r = run_certify_t<float>(h, B, R.it.loads, R.it.outage, R.st.best_lam, bh, bl, R.st.cert,
@@ -1612,13 +1488,14 @@ static dcopf_status tensor_stage_certify(TensorRun& R, cudaStream_t cs, cudaStre
 }
 
 // Once the certificate of the staged instances is in (done_ev): accept, stop or resume
-// each of them, on cs; adds the count of instances still running to *d_active.
-static dcopf_status tensor_accept(TensorRun& R, int* d_active, cudaStream_t cs, cudaEvent_t done_ev) {
+// each of them (when `accept`), on cs; the count of instances still running and the
+// device error word go to out[0] and out[1] (host-mapped).
+static dcopf_status tensor_accept(TensorRun& R, bool accept, int* out_active, int* out_err, cudaStream_t cs,
+                                  cudaEvent_t done_ev) {
   dcopf_dual* h = R.it.h;
-  const int B = R.it.B;
-  if (cudaStreamWaitEvent(cs, done_ev, 0) != cudaSuccess) return DCOPF_ERR_CUDA;
-  k_bt_accept<<<(B + 127) / 128, 128, 0, cs>>>(B, h->ub_any, R.st, h->bb.v, h->bb.snap.as<int>(),
-                                               d_active);
+  if (accept && cudaStreamWaitEvent(cs, done_ev, 0) != cudaSuccess) return DCOPF_ERR_CUDA;
+  k_bt_accept<<<1, ACCEPT_THREADS, 0, cs>>>(R.it.B, accept ? 1 : 0, h->ub_any, R.st, h->bb.v,
+                                           h->bb.snap.as<int>(), h->d_err, out_active, out_err);
   h->launches += 1;
   return cudaGetLastError() == cudaSuccess ? DCOPF_OK : DCOPF_ERR_CUDA;
 }
@@ -1651,13 +1528,26 @@ struct GroupObjects {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<cudaEvent_t> ev, stage_ev, cert_ev;
-  DBuf active;
+  // host-mapped [2][2n]: per round parity, each network's running count and device
+  // error word, written by its accept kernel
+  int* pin = nullptr;
+  int* pin_dev = nullptr;
+  cudaEvent_t done[2] = {nullptr, nullptr};      // a round's read-back has landed
+  cudaEvent_t t0[2] = {nullptr, nullptr}, t1[2] = {nullptr, nullptr};  // around a round's graph
+  // the graph's per-kernel timing nodes: (node, network, event index), pointed at the
+  // network's event set of the round's parity before each launch
+  struct KNode { cudaGraphNode_t node; int net, q; };
+  std::vector<KNode> knodes;
+  std::vector<cudaEvent_t> vev;                  // verbose: graph start / end of every round
   ~GroupObjects() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (cudaEvent_t e : stage_ev) if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : cert_ev) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : {done[0], done[1], t0[0], t0[1], t1[0], t1[1]}) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : vev) if (e) cudaEventDestroy(e);
+    if (pin) cudaFreeHost(pin);
   }
 };
 
@@ -1666,6 +1556,10 @@ struct GroupObjects {
 // of iterations as parallel branches, followed by each network's FP64 certification.
 dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solve_params& p,
                                 cudaStream_t s) {
+  const auto t_start = std::chrono::steady_clock::now();
+  auto host_ms = [t_start] {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  };
   std::vector<TensorRun> runs(n);
   for (int i = 0; i < n; ++i) {
     runs[i].it = items[i];
@@ -1680,8 +1574,15 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
   G.ev.resize(2 * n + 1, nullptr);
   for (auto& e : G.ev)
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return DCOPF_ERR_CUDA;
-  if (G.active.alloc(sizeof(int) * (size_t)n) != cudaSuccess) return DCOPF_ERR_OOM;
-  int* d_active = G.active.as<int>();
+  if (cudaHostAlloc(&G.pin, 4 * sizeof(int) * (size_t)n, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(&G.pin_dev, G.pin, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return DCOPF_ERR_OOM;
+  }
+  for (int q = 0; q < 2; ++q)
+    if (cudaEventCreateWithFlags(&G.done[q], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&G.t0[q]) != cudaSuccess || cudaEventCreate(&G.t1[q]) != cudaSuccess)
+      return DCOPF_ERR_CUDA;
   // every stream starts after every setup
   for (int i = 1; i < n; ++i) {
     if (cudaEventRecord(G.ev[i], items[i].h->tstream) != cudaSuccess ||
@@ -1705,11 +1606,34 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
     cudaGetLastError();
     return DCOPF_ERR_CUDA;
   }
-  if (h0->timing && !h0->ev0) {
-    cudaEventCreate(&h0->ev0);
-    cudaEventCreate(&h0->ev1);
+  // the per-kernel timing nodes of the graph, and each timed network's second event set
+  bool ktimed = false;
+  for (int i = 0; i < n; ++i) ktimed |= items[i].h->timing && items[i].h->kev[0];
+  if (ktimed) {
+    size_t nn = 0;
+    if (cudaGraphGetNodes(G.graph, nullptr, &nn) != cudaSuccess) return DCOPF_ERR_CUDA;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn && cudaGraphGetNodes(G.graph, nodes.data(), &nn) != cudaSuccess) return DCOPF_ERR_CUDA;
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType ty;
+      cudaEvent_t e = nullptr;
+      if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord ||
+          cudaGraphEventRecordNodeGetEvent(nd, &e) != cudaSuccess)
+        continue;
+      for (int i = 0; i < n; ++i)
+        for (int q = 0; q < 6; ++q)
+          if (items[i].h->kev[q] && e == items[i].h->kev[q]) G.knodes.push_back({nd, i, q});
+    }
+    for (int i = 0; i < n; ++i) {
+      dcopf_dual* hi = items[i].h;
+      if (!hi->timing || !hi->kev[0]) continue;
+      for (int q = 0; q < 6; ++q)
+        if (!hi->kev2[q] && cudaEventCreate(&hi->kev2[q]) != cudaSuccess) return DCOPF_ERR_CUDA;
+    }
   }
-  const long long per_chunk = 5LL * chunk;
+  const bool verbose = h0->verbose;
+  const double t_captured = host_ms();
+  double t_wait = 0.0;
   long long max_iters = 0;
   for (const TensorRun& R : runs) max_iters = std::max<long long>(max_iters, R.p.max_iters);
   // The certificate of round r's candidates runs on a side stream beside round r + 1's
@@ -1726,63 +1650,120 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
     if (cudaEventCreateWithFlags(&G.stage_ev[i], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&G.cert_ev[i], cudaEventDisableTiming) != cudaSuccess)
       return DCOPF_ERR_CUDA;
+  // Rounds are pipelined: the host enqueues round r (its graph, the accept of round
+  // r - 1's certificates, the staging and certificate of round r's candidates, the
+  // read-back of the running counts and device error words) and only then waits for
+  // round r - 1's read-back, so that the GPU does not idle while the host turns a round
+  // around.  A batch whose last instance stopped in round r - 2's certificate thus also
+  // runs rounds r - 1 and r, whose iterations skip every (frozen) instance.
   std::vector<int> act(n, 1);
+  int rounds = 0;
   for (int round = 0;; ++round) {
-    if (h0->timing) cudaEventRecord(h0->ev0, cs0);
+    const int sl = round & 1;
+    rounds = round + 1;
+    for (const GroupObjects::KNode& k : G.knodes) {
+      dcopf_dual* hk = items[k.net].h;
+      if (cudaGraphExecEventRecordNodeSetEvent(G.exec, k.node, sl ? hk->kev2[k.q] : hk->kev[k.q]) != cudaSuccess)
+        return DCOPF_ERR_CUDA;
+    }
+    if (verbose) {
+      cudaEvent_t a = nullptr, b = nullptr;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      G.vev.push_back(a);
+      G.vev.push_back(b);
+      cudaEventRecord(a, cs0);
+    }
+    if (h0->timing) cudaEventRecord(G.t0[sl], cs0);
     if (cudaGraphLaunch(G.exec, cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
-    for (int i = 0; i < n; ++i) items[i].h->launches += per_chunk;
-    if (h0->timing) cudaEventRecord(h0->ev1, cs0);
-    if (cudaMemsetAsync(d_active, 0, sizeof(int) * (size_t)n, cs0) != cudaSuccess ||
-        cudaEventRecord(G.ev[2 * n], cs0) != cudaSuccess)
-      return DCOPF_ERR_CUDA;
+    long long round_launches = 0;
+    for (int i = 0; i < n; ++i) {
+      items[i].h->launches += 4LL * chunk * runs[i].nv;
+      round_launches += 4LL * chunk * runs[i].nv;
+    }
+    if (h0->timing) cudaEventRecord(G.t1[sl], cs0);
+    if (verbose) cudaEventRecord(G.vev.back(), cs0);
+    int* slot = G.pin_dev + (size_t)sl * 2 * n;
+    if (cudaEventRecord(G.ev[2 * n], cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
     for (int i = 0; i < n; ++i) {
       cudaStream_t si = items[i].h->tstream;
       if (i > 0 && cudaStreamWaitEvent(si, G.ev[2 * n], 0) != cudaSuccess) return DCOPF_ERR_CUDA;
-      if (!act[i]) continue;
+      // every network reports its count and error word; a network still running accepts
+      // the certificates of the last round and stages this round's candidates
       dcopf_status r;
-      if (round > 0 && (r = tensor_accept(runs[i], d_active + i, si, G.cert_ev[i]))) return r;
-      if ((r = tensor_stage_certify(runs[i], si, items[i].h->cstream, G.stage_ev[i], G.cert_ev[i])))
+      if ((r = tensor_accept(runs[i], round > 0 && act[i], slot + i, slot + n + i, si, G.cert_ev[i]))) return r;
+      if (act[i] &&
+          (r = tensor_stage_certify(runs[i], si, items[i].h->cstream, G.stage_ev[i], G.cert_ev[i])))
         return r;
     }
     for (int i = 1; i < n; ++i)
       if (cudaEventRecord(G.ev[n + i], items[i].h->tstream) != cudaSuccess ||
           cudaStreamWaitEvent(cs0, G.ev[n + i], 0) != cudaSuccess)
         return DCOPF_ERR_CUDA;
-    if (round > 0 &&
-        cudaMemcpyAsync(act.data(), d_active, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, cs0) !=
-            cudaSuccess)
-      return DCOPF_ERR_CUDA;
-    if (cudaStreamSynchronize(cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
+    if (cudaEventRecord(G.done[sl], cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
+    if ((long long)round * chunk > 4LL * max_iters + 64) {  // a cap no solve should reach
+      if (cudaEventSynchronize(G.done[sl]) != cudaSuccess) return DCOPF_ERR_CUDA;
+      break;
+    }
+    if (round == 0) continue;
+    // round r - 1's read-back (round r is already queued behind it)
+    const int pv_sl = sl ^ 1;
+    const double tw = verbose ? host_ms() : 0.0;
+    if (cudaEventSynchronize(G.done[pv_sl]) != cudaSuccess) return DCOPF_ERR_CUDA;
+    if (verbose) t_wait += host_ms() - tw;
+    const int* pv = G.pin + (size_t)pv_sl * 2 * n;
+    for (int i = 0; i < n; ++i)
+      if (pv[n + i]) return (dcopf_status)pv[n + i];
     if (h0->timing) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, h0->ev0, h0->ev1);
+      cudaEventElapsedTime(&ms, G.t0[pv_sl], G.t1[pv_sl]);
       h0->t_iter_ms += ms;
-      h0->t_iter_launches += per_chunk * n;
+      h0->t_iter_launches += round_launches;
     }
     for (int i = 0; i < n; ++i) {
       dcopf_dual* hi = items[i].h;
-      if (!hi->timing || !hi->kev[0] || !act[i]) continue;
+      if (!hi->timing || !hi->kev[0] || !act[i] || G.knodes.empty()) continue;
+      cudaEvent_t* ks = pv_sl ? hi->kev2 : hi->kev;
       float km[5];
       bool kok = true;
-      for (int q = 0; q < 5; ++q) kok &= cudaEventElapsedTime(&km[q], hi->kev[q], hi->kev[q + 1]) == cudaSuccess;
+      for (int q = 0; q < 5; ++q) kok &= cudaEventElapsedTime(&km[q], ks[q], ks[q + 1]) == cudaSuccess;
       if (!kok) { cudaGetLastError(); continue; }
       for (int q = 0; q < 5; ++q) hi->t_kernel_ms[q] += km[q];
       hi->t_kernel_samples += 1;
     }
+    if (round < 2) continue;  // round 0's read-back counts no accept
     int any = 0;
     for (int i = 0; i < n; ++i) {
-      int derr = 0;
-      cudaMemcpy(&derr, items[i].h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-      if (derr) return (dcopf_status)derr;
+      act[i] = pv[i];
       any |= act[i];
     }
-    if (round > 0 && !any) break;
-    if ((long long)round * chunk > 4LL * max_iters + 64) break;
+    if (!any) break;
+  }
+  // the last round's graph time (timing), once everything queued has run
+  if (cudaStreamSynchronize(cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
+  if (h0->timing) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, G.t0[(rounds - 1) & 1], G.t1[(rounds - 1) & 1]);
+    h0->t_iter_ms += ms;
+  }
+  if (verbose) {
+    double graphs = 0.0, gaps = 0.0;
+    for (size_t q = 0; q + 1 < G.vev.size(); q += 2) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, G.vev[q], G.vev[q + 1]);
+      graphs += a;
+      if (q + 2 < G.vev.size() && cudaEventElapsedTime(&b, G.vev[q + 1], G.vev[q + 2]) == cudaSuccess) gaps += b;
+    }
+    fprintf(stderr,
+            "dcopf: group solve: setup + capture %.2f ms (host), %d rounds: graphs %.2f ms, between "
+            "graphs %.2f ms (GPU), host waits %.2f ms, loop %.2f ms (host)\n",
+            t_captured, rounds, graphs, gaps, t_wait, host_ms() - t_captured);
   }
   // the last round's certificates: accept what they staged (nothing, when every
   // instance had stopped before that round)
   for (int i = 0; i < n; ++i) {
-    dcopf_status r = tensor_accept(runs[i], d_active + i, items[i].h->tstream, G.cert_ev[i]);
+    int* slot = G.pin_dev + (size_t)(rounds & 1) * 2 * n;  // free: everything queued has run
+    dcopf_status r = tensor_accept(runs[i], true, slot + i, slot + n + i, items[i].h->tstream, G.cert_ev[i]);
     if (r) return r;
   }
   for (int i = 0; i < n; ++i) {

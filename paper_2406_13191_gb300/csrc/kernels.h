@@ -151,6 +151,7 @@ struct TensorOps {
   DBuf phi_hi, phi_lo, phit_hi, phit_lo;
   CUtensorMap m_phi_hi, m_phi_lo, m_phit_hi, m_phit_lo;        // 128-row boxes
   CUtensorMap m_phi_hi96, m_phi_lo96, m_phit_hi96, m_phit_lo96;  // 96-row boxes (pair tiles of 192)
+  CUtensorMap m_phi_hi80, m_phi_lo80, m_phit_hi80, m_phit_lo80;  // 80-row boxes (pair tiles of 160)
   DBuf H_hi, H_lo, X_hi, X_lo, P;
   CUtensorMap m_H_hi, m_H_lo, m_X_hi, m_X_lo;
 };
@@ -169,6 +170,7 @@ struct LineScreen {
   DBuf phi_hi, phi_lo, phit_hi, phit_lo, lim;  // compact BF16 operands; fmax, fmin [2][nk]
   CUtensorMap m_phi_hi, m_phi_lo, m_phit_hi, m_phit_lo;
   CUtensorMap m_phi_hi96, m_phi_lo96, m_phit_hi96, m_phit_lo96;
+  CUtensorMap m_phi_hi80, m_phi_lo80, m_phit_hi80, m_phit_lo80;
   int map_B = 0;                 // batch size of the maps below
   CUtensorMap m_H_hi, m_H_lo;    // the adjoint's A operand [B][ld_lk]
   DBuf f0c, full;                // compact base flows [B][nk]; full-length best point [2][B][n_line]
@@ -178,6 +180,7 @@ struct LineScreen {
 struct BatchView {
   int n_tiles = 0;             // line tiles of the forward product
   int* frozen = nullptr;       // [B] done or waiting for certification
+  int* step_done = nullptr;    // [B] blocks of the step kernel finished with the instance
   double* lam_eval = nullptr;  // [B] lambda of the evaluated point
   double* cost = nullptr;      // [B] generation cost at the minimiser
   double* psum = nullptr;      // [B] total dispatch
@@ -240,6 +243,10 @@ struct dcopf_dual {
   double ub_any = 0.0;  // cost of the dearest dispatch (upper bound on any primal cost)
   cudaStream_t tstream = nullptr;  // internal stream of the graph-captured batched solve
   cudaStream_t cstream = nullptr;  // certificates of the batched solve, beside its iterations
+  // second branch of the batched solve's iteration graph (its second group of
+  // instances), forked from tstream and joined back to it once per round
+  cudaStream_t tstream2 = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaEvent_t tev = nullptr;  // orders the internal stream after the caller's
   long long launches = 0;
   // optional event timing of the iteration kernels
@@ -251,6 +258,7 @@ struct dcopf_dual {
   // minimiser, forward, step and value kernels of the last iteration of every round,
   // recorded inside the iteration graph
   cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t kev2[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // odd rounds
   double t_kernel_ms[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   long long t_kernel_samples = 0;
   int sm_count = 0;
@@ -274,15 +282,19 @@ struct dcopf_dual {
   // whether the adjoint and the forward product run on CTA pairs (256 x 256 tiles)
   // rather than single CTAs (128 x 128)
   int tune_B = 0, tune_nl = 0, tune_splits = 0, tune_kbps = 0;
-  int tune_pair_adj = 0, tune_pair_fwd = 0;  // 0 single CTAs, 1 pairs of 256 columns, 2 of 192
+  int tune_pair_adj = 0, tune_pair_fwd = 0;  // 0 single CTAs; pairs of 1: 256 columns, 2: 192, 3: 160
+  // instance groups iterated as parallel branches of the iteration graph (1 or 2); the
+  // product shapes above are those of one group's batch
+  int tune_branches = 1;
   // DCOPF_TENSOR_TILES (read at create): 0 = choose by timing, 1 = single CTAs only,
-  // 2 / 3 = CTA pairs of 256 x 256 / 256 x 192 tiles only (where the batch has more than
-  // 128 instances)
+  // 2 / 3 / 4 = CTA pairs of 256 x 256 / 256 x 192 / 256 x 160 tiles only (where the
+  // batch has more than 128 instances)
   int tiles_mode = 0;
-  // DCOPF_TENSOR_SHAPE="a,s,f" (read at create): the adjoint's tiles (0 single, 1 pairs
-  // of 256, 2 pairs of 192), its split-K factor, the forward's tiles; no timing (for
-  // profilers, whose per-launch overhead changes what the timing would pick)
-  int shape_adj = -1, shape_splits = 0, shape_fwd = -1;
+  // DCOPF_TENSOR_SHAPE="a,s,f[,g]" (read at create): the adjoint's tiles (0 single, 1
+  // pairs of 256, 2 pairs of 192, 3 pairs of 160), its split-K factor, the forward's tiles, the branches
+  // (default 1); no timing (for profilers, whose per-launch overhead changes what the
+  // timing would pick)
+  int shape_adj = -1, shape_splits = 0, shape_fwd = -1, shape_branches = 1;
   size_t smem_optin = 0;
   bool verbose = false;
   std::string last_error;
@@ -383,7 +395,6 @@ bool tc_make_map_rows(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t c
 // ws.demand; leaves h->scr ready with the kept lines and their compact operands.
 dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s);
 __global__ void k_screen_compact_rows(int B, int nl, int nk, const int* kept, const float* src, float* dst);
-__global__ void k_screen_scatter_rows(int B, int nl, int nk, const int* pos, const float* src, float* dst);
 cudaError_t tc_gemm_partial(const CUtensorMap& Ah, const CUtensorMap& Al, const CUtensorMap& Bh,
                             const CUtensorMap& Bl, int M, int N, int K, float* P, int ldp,
                             int max_splits, int sm_count, int* err, int* splits_used,
@@ -403,6 +414,8 @@ struct TensorItem {
 };
 dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solve_params& p,
                                 cudaStream_t s);
+// Instances in the first of the two groups a batch of B splits into.
+int tensor_first_group(int B);
 dcopf_status run_eval_tensor(dcopf_dual* h, int batch, const int* outage, const double* lambda,
                              const double* mh, const double* ml, double* value, double* glam,
                              double* ghi, double* glo, double* dispatch, cudaStream_t s);
