@@ -64,9 +64,10 @@ C2 = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99, max_ite
           path="batched", precision="bf16x3")
 QP_ADAM = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997)
 LP_ADAM = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99)
-# DRAM bytes per launch of the dominant kernel from an ncu capture, valid only for the
-# kernel source with this digest (profiles/); null once the kernel has changed.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the two products from an ncu capture of the
+# 10000-bus batch of 256 with screening (profiles/bench_10000bus_b256.md), valid for the
+# product kernels' source with this digest and the product shapes named; null otherwise.
+NCU_TRAFFIC = {"416e5b070f67b443": {"shape": "3,4,3", "adjoint": 114.6e6, "forward": 105.0e6}}
 
 
 def golden(name):
@@ -76,6 +77,15 @@ def golden(name):
 def kernel_digest() -> str:
     p = os.path.join(ROOT, "paper_2406_13191_gb300", "csrc", "k_gemm.cuh")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def traffic_for(shapes, kernel):
+    """ncu DRAM bytes per launch of `kernel` ("adjoint" / "forward"), or None when the
+    capture does not cover the current kernel source or product shapes."""
+    t = NCU_TRAFFIC.get(kernel_digest())
+    if t is None or not shapes["code"].startswith(t["shape"] + ","):
+        return None
+    return t[kernel]
 
 
 def load_peaks():
@@ -524,7 +534,11 @@ def c2_leg(dev, flush, stream, steps):
     g.solve(L, outage=O, target=T, gap=GAP, out=res, **C2)
     g.set_timing(True)
     g.read_timing()
-    times, r = timed_solves(g, (L,), dict(outage=O, target=T, gap=GAP, **C2), steps, flush, stream, res)
+    with Clocks(dev.index) as clk:
+        clk.wait_ready()
+        clk.start()
+        times, r = timed_solves(g, (L,), dict(outage=O, target=T, gap=GAP, **C2), steps, flush, stream, res)
+        clk.stop()
     it_ms, _, evals = g.read_timing()
     kt, ns = g.read_kernel_timing()
     g.set_timing(False)
@@ -543,7 +557,8 @@ def c2_leg(dev, flush, stream, steps):
             "reached_gap": reached,
             "all_bounds_valid": bool(np.all(b <= gam + 1e-9 * np.abs(gam))),
             "us_per_batched_iteration": 1e3 * it_ms / max(1, evals) * B,
-            "kernel_us": {k: 1e3 * v / max(1, ns) for k, v in kt.items()}}
+            "kernel_us": {k: 1e3 * v / max(1, ns) for k, v in kt.items()},
+            "shapes": g.tensor_shapes(), "clocks": clk.summary()}
 
 
 def group_leg(dev, steps):
@@ -758,7 +773,7 @@ def main():
     achieved = flops[dom] / (kus[dom] * 1e-6) / 1e12
     peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(kernel_digest()),
+            "frac": achieved / peak, "traffic": traffic_for(shapes, dom),
             "peak_source": f"{which} (BF16 sustained: the kernel runs inside a long solve)",
             "kernel": f"{dom} product (k_gemm_pair / k_gemm_bf16x as tuned)",
             "flops_per_launch": flops[dom], "us_per_launch": kus[dom],

@@ -41,8 +41,12 @@ static StepArgsF to_float_args(const StepArgs& P) {
   return f;
 }
 
+// One coordinate's step (Section 3.3) in FP32 with the instance's step factors of this
+// step: a = alpha decay^(t-1) (GDM, AdaGrad), and for Adam a1 = a / (1 - beta1^t) and
+// r2 = 1 / sqrt(1 - beta2^t), so that a (s1 / c1) / (sqrt(s2 / c2) + eps) is
+// a1 s1 / (sqrt(s2) r2 + eps) with one division.
 __device__ __forceinline__ float step_rule(const StepArgsF& P, float theta, float g, float& s1,
-                                           float& s2, float a, float bc1, float bc2) {
+                                           float& s2, float a, float a1, float r2) {
   if (P.rule == DCOPF_GDM) {
     s1 = P.rho * s1 + a * g;
     theta += s1;
@@ -50,7 +54,7 @@ __device__ __forceinline__ float step_rule(const StepArgsF& P, float theta, floa
   } else if (P.rule == DCOPF_ADAM) {
     s1 = P.beta1 * s1 + P.omb1 * g;
     s2 = P.beta2 * s2 + P.omb2 * g * g;
-    theta += a * (s1 / bc1) / (sqrtf(s2 / bc2) + P.eps);
+    theta += a1 * s1 / fmaf(sqrtf(s2), r2, P.eps);
   } else {
     s1 += g * g;
     theta += a * g / (sqrtf(s1) + P.eps);
@@ -81,7 +85,7 @@ struct StepEpi {
   const int* iter;            // [B] evaluations done: iter % 3 selects the state buffer
   const int* frozen;          // [B] done or waiting for certification
   const int* best_iter;       // [B] evaluation count of the best point so far
-  const float* stepf;         // [B][4] alpha scale, 1 - beta1^t, 1 - beta2^t
+  const float* stepf;         // [B][4] step factors a, a1, r2 of step_rule
   // Three state buffers in turn: point t lives in buffer t % 3, so the two points
   // before the one being stepped are still there.  The step writing point t + 1
   // overwrites point t - 2; if that point is still the best (the value fell after
@@ -91,7 +95,8 @@ struct StepEpi {
   float* sv_hi; float* sv_lo;
   float* s1_hi; float* s2_hi; float* s1_lo; float* s2_lo;
   __nv_bfloat16* Hh; __nv_bfloat16* Hl; int ldh;
-  double* line_part; double* out_part; int n_tiles;   // [B][n_tiles] per chunk of lines
+  double* line_part; double* out_part; int n_tiles;   // [B][n_tiles x STEP_WARPS] per warp of a chunk
+  int B;                      // instances
   // the dual value and the stop tests of the evaluated point (finalize_instance), run by
   // the last of an instance's blocks to finish: step_done [B] counts them
   SolveStateBase st;
@@ -102,32 +107,41 @@ struct StepEpi {
   int* step_done;
 };
 
-// The tail of both step kernels: the block's partials are in (thread 0 wrote them);
-// the last block of instance b runs its value and stop tests.
-__device__ __forceinline__ void step_tail(const StepEpi& E, int b) {
-  __shared__ int s_last;
-  if (threadIdx.x == 0) {
-    __threadfence();  // this block's partials and H entries before its count
-    s_last = atomicAdd(&E.step_done[b], 1) == E.n_tiles - 1;
-  }
-  __syncthreads();
-  if (s_last && threadIdx.x < 32) {
-    __threadfence();  // every other block's, before they are read
-    if (threadIdx.x == 0) E.step_done[b] = 0;
-    finalize_instance(b, threadIdx.x, E.ldh, E.max_iters, E.tol, E.st, E.bb, E.outage, E.demand, E.Hh,
-                      E.Hl);
-  }
-}
-
+// The tail of both step kernels, per warp: the warp's partials of the value and of
+// u^T eta go to slot `part` of the instance's [n_tiles * STEP_WARPS]; the last warp of
+// instance b to finish runs its value and stop tests.  No block-wide barrier: warps
+// finish on their own.
+__device__ __forceinline__ void step_tail(const StepEpi& E, int b, int part, float lacc, float oacc);
 
 // One block per (chunk of STEP_CHUNK lines, instance): elementwise, full occupancy,
 // coalesced; per-chunk FP64 partials of the value and of u^T eta.
 constexpr int STEP_THREADS = 256, STEP_PER_THREAD = 4;
 constexpr int STEP_CHUNK = STEP_THREADS * STEP_PER_THREAD;
+constexpr int STEP_WARPS = STEP_THREADS / 32;  // partials per chunk
 
-__global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
-  __shared__ double red[32];
-  const int b = blockIdx.y, chunk = blockIdx.x;
+__device__ __forceinline__ void step_tail(const StepEpi& E, int b, int part, float lacc, float oacc) {
+  const int lane = threadIdx.x & 31;
+  const int np = E.n_tiles * STEP_WARPS;
+  // release / acquire at GPU scope around a relaxed count: the warp's writes (ordered
+  // before lane 0's fence by __syncwarp) before its count, every other warp's before
+  // the last one reads them
+  __syncwarp();
+  int last = 0;
+  if (lane == 0) {
+    E.line_part[(size_t)b * np + part] = (double)lacc;
+    E.out_part[(size_t)b * np + part] = (double)oacc;
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    last = atomicAdd(&E.step_done[b], 1) == np - 1;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    if (lane == 0) E.step_done[b] = 0;
+    finalize_instance(b, lane, E.ldh, E.max_iters, E.tol, E.st, E.bb, E.outage, E.demand, E.Hh, E.Hl);
+  }
+}
+
+__device__ __forceinline__ void step_item(const StepEpi& E, int nl, int b, int chunk) {
   if (E.frozen[b]) return;
   const int k = E.outage ? E.outage[b] : -1;
   const float t_out = k >= 0 ? E.tout[b] : 0.f;
@@ -138,7 +152,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
   const float* mlc = E.mu_lo[pb] + o;
   float* mhn = E.mu_hi[pn] + o;
   float* mln = E.mu_lo[pn] + o;
-  const float am = E.stepf[4 * b], bc1 = E.stepf[4 * b + 1], bc2 = E.stepf[4 * b + 2];
+  const float am = E.stepf[4 * b], a1s = E.stepf[4 * b + 1], r2 = E.stepf[4 * b + 2];
   const float* Fr = E.F + (size_t)b * E.ldF;
   // a thread's few terms are summed in FP32 and the block sum is FP64 (FP64 throughput
   // is low on this part: per-element FP64 would dominate the kernel)
@@ -171,8 +185,8 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
     float nh = 0.f, nlo = 0.f;
     if (i != k) {
       lacc = fmaf(mh[q], gh, fmaf(ml[q], gl, lacc));
-      nh = fmaxf(step_rule(E.P, mh[q], gh, a1[q], a2[q], am, bc1, bc2), 0.f);
-      nlo = fmaxf(step_rule(E.P, ml[q], gl, b1[q], b2[q], am, bc1, bc2), 0.f);
+      nh = fmaxf(step_rule(E.P, mh[q], gh, a1[q], a2[q], am, a1s, r2), 0.f);
+      nlo = fmaxf(step_rule(E.P, ml[q], gl, b1[q], b2[q], am, a1s, r2), 0.f);
       E.s1_hi[o + i] = a1[q]; E.s2_hi[o + i] = a2[q]; E.s1_lo[o + i] = b1[q]; E.s2_lo[o + i] = b2[q];
     }
     if (save) { E.sv_hi[o + i] = mhn[i]; E.sv_lo[o + i] = mln[i]; }
@@ -183,44 +197,23 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
     if (k >= 0) oacc = fmaf(ui[q], eta, oacc);
   }
   // warp sums in FP32, the 8 warp partials in FP64 (fixed order)
+  // a warp's terms in FP32, its partials in FP64 (summed in a fixed order by the value)
   lacc = warp_sum(lacc);
   oacc = warp_sum(oacc);
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    red[w] = (double)lacc;
-    red[16 + w] = (double)oacc;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    // the warps' partials in FP64, a shuffle tree (fixed order)
-    const int l = threadIdx.x;
-    double ls = l < STEP_THREADS / 32 ? red[l] : 0.0, os = l < STEP_THREADS / 32 ? red[16 + l] : 0.0;
-#pragma unroll
-    for (int o = STEP_THREADS / 64; o > 0; o >>= 1) {
-      ls += __shfl_xor_sync(0xffffffffu, ls, o);
-      os += __shfl_xor_sync(0xffffffffu, os, o);
-    }
-    if (l == 0) {
-      E.line_part[(size_t)b * E.n_tiles + chunk] = ls;
-      E.out_part[(size_t)b * E.n_tiles + chunk] = os;
-    }
-  }
-  step_tail(E, b);
+  step_tail(E, b, chunk * STEP_WARPS + (int)(threadIdx.x >> 5), lacc, oacc);
 }
 
 // The same step with four consecutive lines per thread: 16-byte loads and stores of every
 // FP32 stream and 8-byte stores of the BF16 split (needs n_line, ldF and ldh multiples
 // of 4; the chunk of a block is the same 1024 lines as k_bt_step's).
-__global__ void __launch_bounds__(STEP_THREADS, 4) k_bt_step4(StepEpi E, int nl) {
-  __shared__ double red[32];
-  const int b = blockIdx.y, chunk = blockIdx.x;
+__device__ __forceinline__ void step4_item(const StepEpi& E, int nl, int b, int chunk) {
   if (E.frozen[b]) return;
   const int k = E.outage ? E.outage[b] : -1;
   const float t_out = k >= 0 ? E.tout[b] : 0.f;
   const int it = E.iter[b], pb = it % 3, pn = (it + 1) % 3;
   const bool save = it >= 2 && E.best_iter[b] == it - 1;  // point it - 2 is the best
   const size_t o = (size_t)b * nl;
-  const float am = E.stepf[4 * b], bc1 = E.stepf[4 * b + 1], bc2 = E.stepf[4 * b + 2];
+  const float am = E.stepf[4 * b], a1s = E.stepf[4 * b + 1], r2 = E.stepf[4 * b + 2];
   const int i = 4 * (chunk * STEP_THREADS + threadIdx.x);
   float lacc = 0.f, oacc = 0.f;
   if (i < nl) {
@@ -246,8 +239,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) k_bt_step4(StepEpi E, int nl)
       float nh = 0.f, nlo = 0.f;
       if (i + q != k) {
         lacc = fmaf(MH[q], gh, fmaf(ML[q], gl, lacc));
-        nh = fmaxf(step_rule(E.P, MH[q], gh, A1[q], A2[q], am, bc1, bc2), 0.f);
-        nlo = fmaxf(step_rule(E.P, ML[q], gl, B1[q], B2[q], am, bc1, bc2), 0.f);
+        nh = fmaxf(step_rule(E.P, MH[q], gh, A1[q], A2[q], am, a1s, r2), 0.f);
+        nlo = fmaxf(step_rule(E.P, ML[q], gl, B1[q], B2[q], am, a1s, r2), 0.f);
       }
       NH[q] = nh;
       NL[q] = nlo;
@@ -274,29 +267,24 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) k_bt_step4(StepEpi E, int nl)
     *reinterpret_cast<uint2*>(E.Hh + (size_t)b * E.ldh + i) = *reinterpret_cast<const uint2*>(hh);
     *reinterpret_cast<uint2*>(E.Hl + (size_t)b * E.ldh + i) = *reinterpret_cast<const uint2*>(hl);
   }
+  // a warp's terms in FP32, its partials in FP64 (summed in a fixed order by the value)
   lacc = warp_sum(lacc);
   oacc = warp_sum(oacc);
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    red[w] = (double)lacc;
-    red[16 + w] = (double)oacc;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    // the warps' partials in FP64, a shuffle tree (fixed order)
-    const int l = threadIdx.x;
-    double ls = l < STEP_THREADS / 32 ? red[l] : 0.0, os = l < STEP_THREADS / 32 ? red[16 + l] : 0.0;
-#pragma unroll
-    for (int o = STEP_THREADS / 64; o > 0; o >>= 1) {
-      ls += __shfl_xor_sync(0xffffffffu, ls, o);
-      os += __shfl_xor_sync(0xffffffffu, os, o);
-    }
-    if (l == 0) {
-      E.line_part[(size_t)b * E.n_tiles + chunk] = ls;
-      E.out_part[(size_t)b * E.n_tiles + chunk] = os;
-    }
-  }
-  step_tail(E, b);
+  step_tail(E, b, chunk * STEP_WARPS + (int)(threadIdx.x >> 5), lacc, oacc);
+}
+
+// The step kernels: work item w = (instance w / n_tiles, chunk of lines w % n_tiles),
+// taken in turn by the launched blocks: one per item, or fewer, so that the step leaves
+// room on the SMs for another instance group's products (a block holds 64 registers x
+// 256 threads).  An instance's items run in any order (its last one runs the value).
+__global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
+  const int total = E.n_tiles * E.B;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) step_item(E, nl, w / E.n_tiles, w % E.n_tiles);
+}
+
+__global__ void __launch_bounds__(STEP_THREADS, 4) k_bt_step4(StepEpi E, int nl) {
+  const int total = E.n_tiles * E.B;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) step4_item(E, nl, w / E.n_tiles, w % E.n_tiles);
 }
 
 // ------------------------------------------------------------------ operand preparation
@@ -689,13 +677,12 @@ static int minimize_threads(const dcopf_dual* h, int B) {
 // pi~ from the split-K partials, minimiser, BF16 split of x, per-instance cost and
 // dispatch, the pre-outage flow (Phi~ x)_k of an outaged line, the step factors of
 // this step (running powers), and the lambda step (Section 3.3).
-__global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
-    k_bt_minimize(DevNet N, int splits, int M, int ldp, const float* __restrict__ P,
-                              SolveStateBase st, BatchView bb, StepArgs SP, int ldx,
-                              __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl,
-                              const int* __restrict__ outage, const double* __restrict__ demand) {
-  __shared__ double red[3 * (MIN_MAX_THREADS / 32)];
-  const int b = blockIdx.x;
+__device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M, int ldp,
+                                              const float* __restrict__ P, const SolveStateBase& st,
+                                              const BatchView& bb, const StepArgs& SP, int ldx,
+                                              __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl,
+                                              const int* __restrict__ outage,
+                                              const double* __restrict__ demand, int b, double* red) {
   if (bb.frozen[b]) return;
   const int ng = N.n_gen;
   const int k = outage ? outage[b] : -1;
@@ -764,9 +751,10 @@ __global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
     // step t = iter + 1: scale decay^(t-1), bias corrections 1 - beta^t
     const double d = bb.pw[3 * b], b1 = bb.pw[3 * b + 1] * SP.beta1, b2 = bb.pw[3 * b + 2] * SP.beta2;
     const float bc1 = (float)(1.0 - b1), bc2 = (float)(1.0 - b2);
-    bb.stepf[4 * b] = (float)(SP.alpha * d);
-    bb.stepf[4 * b + 1] = bc1;
-    bb.stepf[4 * b + 2] = bc2;
+    const float am = (float)(SP.alpha * d);
+    bb.stepf[4 * b] = am;
+    bb.stepf[4 * b + 1] = am / bc1;             // Adam: alpha decay^(t-1) / (1 - beta1^t)
+    bb.stepf[4 * b + 2] = 1.0f / sqrtf(bc2);    // and 1 / sqrt(1 - beta2^t)
     bb.pw[3 * b] = d * SP.decay;
     bb.pw[3 * b + 1] = b1;
     bb.pw[3 * b + 2] = b2;
@@ -792,6 +780,20 @@ __global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
   }
 }
 
+// The minimiser kernel: instance b taken in turn by the launched blocks (one per
+// instance, or fewer to leave room for another instance group's products).
+__global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
+    k_bt_minimize(DevNet N, int splits, int M, int ldp, const float* __restrict__ P,
+                  SolveStateBase st, BatchView bb, StepArgs SP, int ldx,
+                  __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl,
+                  const int* __restrict__ outage, const double* __restrict__ demand) {
+  __shared__ double red[3 * (MIN_MAX_THREADS / 32)];
+  for (int b = blockIdx.x; b < M; b += gridDim.x) {
+    minimize_item(N, splits, M, ldp, P, st, bb, SP, ldx, Xh, Xl, outage, demand, b, red);
+    __syncthreads();  // red is read by warp 0 before the next instance's partials land
+  }
+}
+
 // Dual value of the evaluated point (FP64), best value and its lambda, outage patch of
 // the next eta, stop tests, for instance b, by one warp of the step kernel's last block
 // for the instance.  A stopping instance is frozen: one that reached its target with the
@@ -803,7 +805,7 @@ __device__ __forceinline__ void finalize_instance(int b, int lane, int ld_l, int
                                                   const double* __restrict__ demand,
                                                   __nv_bfloat16* __restrict__ Hh,
                                                   __nv_bfloat16* __restrict__ Hl) {
-  const int nt = bb.n_tiles;
+  const int nt = bb.n_tiles * STEP_WARPS;
   double ls = 0.0, os = 0.0;
   for (int q = lane; q < nt; q += 32) {
     ls += bb.line_part[(size_t)b * nt + q];
@@ -862,8 +864,8 @@ __global__ void k_bt_stage(int B, int nl, int len, const int* __restrict__ pos, 
 // After certification: accept, stop, or unfreeze with a larger in-loop margin each
 // staged instance (when `accept`; the evaluation of a frozen point counts, and an
 // unfrozen instance moves on to the point already stepped to); then the number of
-// instances still running into *out_active and the device error word into *out_err
-// (host-mapped memory).  One block.
+// instances still running into *out_active and the device error word into *out_err.
+// One block.
 constexpr int ACCEPT_THREADS = 512;
 __global__ void __launch_bounds__(ACCEPT_THREADS)
     k_bt_accept(int B, int accept, double ub_any, SolveStateBase st, BatchView bb,
@@ -918,7 +920,7 @@ static dcopf_status ensure_batch_bufs(dcopf_dual* h, int B, int n_tiles) {
   BatchView& v = bb.v;
   const size_t nl = h->host.n_line;
   if (bb.mu2.alloc((size_t)B * nl * 6 * sizeof(float)) ||
-      bb.parts.alloc((size_t)B * n_tiles * 2 * sizeof(double)) ||
+      bb.parts.alloc((size_t)B * n_tiles * STEP_WARPS * 2 * sizeof(double)) ||
       bb.small.alloc((size_t)B * 7 * sizeof(double) + (size_t)B * 7 * sizeof(float) + 1024)) {
     cudaGetLastError();
     return DCOPF_ERR_OOM;
@@ -930,7 +932,7 @@ static dcopf_status ensure_batch_bufs(dcopf_dual* h, int B, int n_tiles) {
   v.sv_hi = v.mu2_hi + 4 * (size_t)B * nl;
   v.sv_lo = v.mu2_hi + 5 * (size_t)B * nl;
   v.line_part = bb.parts.as<double>();
-  v.out_part = v.line_part + (size_t)B * n_tiles;
+  v.out_part = v.line_part + (size_t)B * n_tiles * STEP_WARPS;
   double* d = bb.small.as<double>();
   v.lam_eval = d; v.cost = d + B; v.psum = d + 2 * (size_t)B; v.pw = d + 3 * (size_t)B;  // pw: [B][3]
   v.lam_best = d + 6 * (size_t)B;
@@ -981,6 +983,10 @@ struct TensorRun {
   bool running = true;
   int nv = 1;                      // instance groups, iterated as parallel graph branches
   IterView v[MAX_BRANCHES];
+  // blocks of the step and the minimiser kernels (0: one per work item); with two
+  // groups, two step blocks and one minimiser block per SM, which leaves each SM the
+  // registers of a product CTA of the other group
+  int step_blocks = 0, min_blocks = 0;
 };
 
 template <typename T>
@@ -1013,7 +1019,7 @@ static bool make_view(TensorRun& R, int b0, int Bg, IterView* V) {
   adv(bb.frozen, o); adv(bb.lam_eval, o); adv(bb.cost, o); adv(bb.psum, o); adv(bb.pw, 3 * o);
   adv(bb.tout, o); adv(bb.stepf, 4 * o); adv(bb.lam_best, o); adv(bb.step_done, o);
   for (float** q : {&bb.mu2_hi, &bb.mu2_lo, &bb.mu3_hi, &bb.mu3_lo, &bb.sv_hi, &bb.sv_lo}) adv(*q, o * nl);
-  adv(bb.line_part, o * nt); adv(bb.out_part, o * nt);
+  adv(bb.line_part, o * nt * STEP_WARPS); adv(bb.out_part, o * nt * STEP_WARPS);
   W.ga = R.ga;
   W.ga.M = Bg;
   W.ga.P = R.ga.P + (size_t)64 * o * R.ga.ldp;  // the partials' [64][B][ldp] share of the group
@@ -1036,6 +1042,7 @@ static bool make_view(TensorRun& R, int b0, int Bg, IterView* V) {
   E.Hh = R.E.Hh + o * E.ldh;
   E.Hl = R.E.Hl + o * E.ldh;
   E.line_part = bb.line_part; E.out_part = bb.out_part;
+  E.B = Bg;
   E.st = st;
   E.bb = bb;
   E.step_done = bb.step_done;
@@ -1062,6 +1069,8 @@ int tensor_first_group(int B) {
 static dcopf_status make_views(TensorRun& R, int nv) {
   const int B = R.it.B;
   R.nv = nv;
+  R.step_blocks = nv > 1 ? 2 * R.it.h->sm_count : 0;
+  R.min_blocks = nv > 1 ? R.it.h->sm_count : 0;
   if (nv == 1) return make_view(R, 0, B, &R.v[0]) ? DCOPF_OK : DCOPF_ERR_CUDA;
   const int b1 = tensor_first_group(B);
   return make_view(R, 0, b1, &R.v[0]) && make_view(R, b1, B - b1, &R.v[1]) ? DCOPF_OK : DCOPF_ERR_CUDA;
@@ -1091,16 +1100,19 @@ static bool enqueue_iters(TensorRun& R, IterView& V, int n, cudaStream_t cs, boo
     ev(0);
     ok &= launch_adjoint(h, R.ls, V.Hh, V.Hl, V.ga, R.splits, R.pair_adj, cs) == cudaSuccess;
     ev(1);
-    k_bt_minimize<<<V.B, minimize_threads(h, V.B), 0, cs>>>(h->dev, R.splits, V.B, V.ga.ldp, V.ga.P, V.st,
-                                                            V.bb, R.P, T.ld_g, V.Xhp, V.Xlp, V.outage,
-                                                            V.demand);
+    const int mb = R.min_blocks ? std::min(V.B, R.min_blocks) : V.B;
+    k_bt_minimize<<<mb, minimize_threads(h, V.B), 0, cs>>>(h->dev, R.splits, V.B, V.ga.ldp, V.ga.P, V.st,
+                                                           V.bb, R.P, T.ld_g, V.Xhp, V.Xlp, V.outage,
+                                                           V.demand);
     ev(2);
     ok &= launch_forward(h, R.ls, V.Xh, V.Xl, V.gf, R.pair_fwd, cs) == cudaSuccess;
     ev(3);
+    const int items = R.n_tiles * V.B;
+    const int sb = R.step_blocks ? std::min(items, R.step_blocks) : items;
     if (nl % 4 == 0 && V.E.ldF % 4 == 0 && V.E.ldh % 4 == 0)
-      k_bt_step4<<<dim3(R.n_tiles, V.B), STEP_THREADS, 0, cs>>>(V.E, nl);
+      k_bt_step4<<<sb, STEP_THREADS, 0, cs>>>(V.E, nl);
     else
-      k_bt_step<<<dim3(R.n_tiles, V.B), STEP_THREADS, 0, cs>>>(V.E, nl);
+      k_bt_step<<<sb, STEP_THREADS, 0, cs>>>(V.E, nl);
     ev(4);  // the value and stop tests run in the step kernel's last block per instance
     ev(5);
   }
@@ -1419,7 +1431,7 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   E.s1_hi = R.st.s1_hi; E.s2_hi = R.st.s2_hi; E.s1_lo = R.st.s1_lo; E.s2_lo = R.st.s2_lo;
   E.Hh = T.H_hi.as<__nv_bfloat16>(); E.Hl = T.H_lo.as<__nv_bfloat16>(); E.ldh = R.ls.ld_l;
   E.line_part = bb.line_part; E.out_part = bb.out_part; E.n_tiles = R.n_tiles;
-  E.st = R.st; E.bb = bb; E.demand = w.demand.as<double>(); E.step_done = bb.step_done;
+  E.st = R.st; E.bb = bb; E.demand = w.demand.as<double>(); E.step_done = bb.step_done; E.B = B;
   E.max_iters = p.max_iters; E.tol = p.tol;
   if (h->timing && !h->kev[0])
     for (int q = 0; q < 6; ++q)
@@ -1489,7 +1501,7 @@ static dcopf_status tensor_stage_certify(TensorRun& R, cudaStream_t cs, cudaStre
 
 // Once the certificate of the staged instances is in (done_ev): accept, stop or resume
 // each of them (when `accept`), on cs; the count of instances still running and the
-// device error word go to out[0] and out[1] (host-mapped).
+// device error word go to *out_active and *out_err (device memory).
 static dcopf_status tensor_accept(TensorRun& R, bool accept, int* out_active, int* out_err, cudaStream_t cs,
                                   cudaEvent_t done_ev) {
   dcopf_dual* h = R.it.h;
@@ -1523,33 +1535,41 @@ static dcopf_status tensor_finish(TensorRun& R, cudaStream_t s) {
   return DCOPF_OK;
 }
 
-// Owns the CUDA objects of one group solve.
+// Verbose diagnostics of one group solve: events around every round's graph.
 struct GroupObjects {
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  std::vector<cudaEvent_t> ev, stage_ev, cert_ev;
-  // host-mapped [2][2n]: per round parity, each network's running count and device
-  // error word, written by its accept kernel
-  int* pin = nullptr;
-  int* pin_dev = nullptr;
-  cudaEvent_t done[2] = {nullptr, nullptr};      // a round's read-back has landed
-  cudaEvent_t t0[2] = {nullptr, nullptr}, t1[2] = {nullptr, nullptr};  // around a round's graph
-  // the graph's per-kernel timing nodes: (node, network, event index), pointed at the
-  // network's event set of the round's parity before each launch
-  struct KNode { cudaGraphNode_t node; int net, q; };
-  std::vector<KNode> knodes;
-  std::vector<cudaEvent_t> vev;                  // verbose: graph start / end of every round
+  std::vector<cudaEvent_t> vev;
   ~GroupObjects() {
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    for (cudaEvent_t e : ev) cudaEventDestroy(e);
-    for (cudaEvent_t e : stage_ev) if (e) cudaEventDestroy(e);
-    for (cudaEvent_t e : cert_ev) if (e) cudaEventDestroy(e);
-    for (cudaEvent_t e : {done[0], done[1], t0[0], t0[1], t1[0], t1[1]}) if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : vev) if (e) cudaEventDestroy(e);
-    if (pin) cudaFreeHost(pin);
   }
 };
+
+// The bytes of every kernel argument of the iteration graph of runs[0..n): a later solve
+// with the same bytes replays the graph captured for them.
+static std::vector<unsigned char> graph_signature(const std::vector<TensorRun>& runs, int chunk) {
+  std::vector<unsigned char> sig;
+  auto put = [&](const void* p, size_t n) {
+    const unsigned char* c = (const unsigned char*)p;
+    sig.insert(sig.end(), c, c + n);
+  };
+  put(&chunk, sizeof chunk);
+  for (const TensorRun& R : runs) {
+    const dcopf_dual* h = R.it.h;
+    put(&h, sizeof h);
+    const int timed = h->timing && h->kev[0];
+    put(&timed, sizeof timed);
+    if (timed) put(h->kev, sizeof h->kev);
+    put(&R.nv, sizeof R.nv);
+    put(R.v, sizeof(IterView) * R.nv);
+    put(&R.P, sizeof R.P);
+    const int ints[7] = {R.splits, R.pair_adj, R.pair_fwd, R.n_tiles, R.step_blocks, R.min_blocks, R.ls.nl};
+    put(ints, sizeof ints);
+    for (const CUtensorMap* m : {R.ls.phit_hi, R.ls.phit_lo, R.ls.phit_hi96, R.ls.phit_lo96, R.ls.phit_hi80,
+                                 R.ls.phit_lo80, R.ls.phi_hi, R.ls.phi_lo, R.ls.phi_hi96, R.ls.phi_lo96,
+                                 R.ls.phi_hi80, R.ls.phi_lo80})
+      if (m) put(m, sizeof(CUtensorMap));
+  }
+  return sig;
+}
 
 // Batched solves of several networks (distinct handles on one device) that advance
 // together: each round is ONE launch of a CUDA graph holding every network's chunk
@@ -1571,65 +1591,85 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
   cudaStream_t cs0 = h0->tstream;
   const int chunk = std::max(16, p.check_every);
   GroupObjects G;
-  G.ev.resize(2 * n + 1, nullptr);
-  for (auto& e : G.ev)
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return DCOPF_ERR_CUDA;
-  if (cudaHostAlloc(&G.pin, 4 * sizeof(int) * (size_t)n, cudaHostAllocMapped) != cudaSuccess ||
-      cudaHostGetDevicePointer(&G.pin_dev, G.pin, 0) != cudaSuccess) {
-    cudaGetLastError();
-    return DCOPF_ERR_OOM;
+  RoundKit& K = h0->kit;
+  const double t_setup = host_ms();
+  if (K.n != n) {  // events and read-back for n networks
+    K.release();
+    K.ev.assign(2 * n + 1, nullptr);
+    K.stage_ev.assign(n, nullptr);
+    K.cert_ev.assign(n, nullptr);
+    for (auto* v : {&K.ev, &K.stage_ev, &K.cert_ev})
+      for (cudaEvent_t& e : *v)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return DCOPF_ERR_CUDA;
+    for (int q = 0; q < 2; ++q)
+      if (cudaEventCreateWithFlags(&K.done[q], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&K.acc[q], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreate(&K.t0[q]) != cudaSuccess || cudaEventCreate(&K.t1[q]) != cudaSuccess)
+        return DCOPF_ERR_CUDA;
+    if (cudaStreamCreateWithFlags(&K.rs, cudaStreamNonBlocking) != cudaSuccess) return DCOPF_ERR_CUDA;
+    if (cudaMallocHost(&K.pin, 4 * sizeof(int) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&K.rb_dev, 4 * sizeof(int) * (size_t)n) != cudaSuccess) {
+      cudaGetLastError();
+      K.release();
+      return DCOPF_ERR_OOM;
+    }
+    K.n = n;
   }
-  for (int q = 0; q < 2; ++q)
-    if (cudaEventCreateWithFlags(&G.done[q], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreate(&G.t0[q]) != cudaSuccess || cudaEventCreate(&G.t1[q]) != cudaSuccess)
-      return DCOPF_ERR_CUDA;
   // every stream starts after every setup
   for (int i = 1; i < n; ++i) {
-    if (cudaEventRecord(G.ev[i], items[i].h->tstream) != cudaSuccess ||
-        cudaStreamWaitEvent(cs0, G.ev[i], 0) != cudaSuccess)
+    if (cudaEventRecord(K.ev[i], items[i].h->tstream) != cudaSuccess ||
+        cudaStreamWaitEvent(cs0, K.ev[i], 0) != cudaSuccess)
       return DCOPF_ERR_CUDA;
   }
-  std::vector<long long> before(n);
-  for (int i = 0; i < n; ++i) before[i] = items[i].h->launches;
-  if (cudaStreamBeginCapture(cs0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-    return DCOPF_ERR_CUDA;
-  bool cap_ok = cudaEventRecord(G.ev[0], cs0) == cudaSuccess;
-  for (int i = 1; i < n && cap_ok; ++i)
-    cap_ok = cudaStreamWaitEvent(items[i].h->tstream, G.ev[0], 0) == cudaSuccess;
-  for (int i = 0; i < n && cap_ok; ++i) cap_ok = tensor_enqueue_chunk(runs[i], chunk, items[i].h->tstream);
-  for (int i = 1; i < n && cap_ok; ++i)
-    cap_ok = cudaEventRecord(G.ev[n + i], items[i].h->tstream) == cudaSuccess &&
-             cudaStreamWaitEvent(cs0, G.ev[n + i], 0) == cudaSuccess;
-  cudaError_t ce = cudaStreamEndCapture(cs0, &G.graph);
-  for (int i = 0; i < n; ++i) items[i].h->launches = before[i];  // counted per replay below
-  if (!cap_ok || ce != cudaSuccess || cudaGraphInstantiate(&G.exec, G.graph, 0) != cudaSuccess) {
-    cudaGetLastError();
-    return DCOPF_ERR_CUDA;
+  std::vector<unsigned char> sig = graph_signature(runs, chunk);
+  const bool reuse = K.exec && sig == K.sig;
+  if (!reuse) {
+    K.drop_graph();
+    std::vector<long long> before(n);
+    for (int i = 0; i < n; ++i) before[i] = items[i].h->launches;
+    if (cudaStreamBeginCapture(cs0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return DCOPF_ERR_CUDA;
+    bool cap_ok = cudaEventRecord(K.ev[0], cs0) == cudaSuccess;
+    for (int i = 1; i < n && cap_ok; ++i)
+      cap_ok = cudaStreamWaitEvent(items[i].h->tstream, K.ev[0], 0) == cudaSuccess;
+    for (int i = 0; i < n && cap_ok; ++i) cap_ok = tensor_enqueue_chunk(runs[i], chunk, items[i].h->tstream);
+    for (int i = 1; i < n && cap_ok; ++i)
+      cap_ok = cudaEventRecord(K.ev[n + i], items[i].h->tstream) == cudaSuccess &&
+               cudaStreamWaitEvent(cs0, K.ev[n + i], 0) == cudaSuccess;
+    cudaError_t ce = cudaStreamEndCapture(cs0, &K.graph);
+    for (int i = 0; i < n; ++i) items[i].h->launches = before[i];  // counted per replay below
+    if (!cap_ok || ce != cudaSuccess || cudaGraphInstantiate(&K.exec, K.graph, 0) != cudaSuccess) {
+      cudaGetLastError();
+      K.drop_graph();
+      return DCOPF_ERR_CUDA;
+    }
+    // the per-kernel timing nodes of the graph
+    bool ktimed = false;
+    for (int i = 0; i < n; ++i) ktimed |= items[i].h->timing && items[i].h->kev[0];
+    if (ktimed) {
+      size_t nn = 0;
+      if (cudaGraphGetNodes(K.graph, nullptr, &nn) != cudaSuccess) return DCOPF_ERR_CUDA;
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (nn && cudaGraphGetNodes(K.graph, nodes.data(), &nn) != cudaSuccess) return DCOPF_ERR_CUDA;
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        cudaEvent_t e = nullptr;
+        if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord ||
+            cudaGraphEventRecordNodeGetEvent(nd, &e) != cudaSuccess)
+          continue;
+        for (int i = 0; i < n; ++i)
+          for (int q = 0; q < 6; ++q)
+            if (items[i].h->kev[q] && e == items[i].h->kev[q]) K.knodes.push_back({nd, i, q});
+      }
+    }
+    K.sig = std::move(sig);
   }
-  // the per-kernel timing nodes of the graph, and each timed network's second event set
-  bool ktimed = false;
-  for (int i = 0; i < n; ++i) ktimed |= items[i].h->timing && items[i].h->kev[0];
-  if (ktimed) {
-    size_t nn = 0;
-    if (cudaGraphGetNodes(G.graph, nullptr, &nn) != cudaSuccess) return DCOPF_ERR_CUDA;
-    std::vector<cudaGraphNode_t> nodes(nn);
-    if (nn && cudaGraphGetNodes(G.graph, nodes.data(), &nn) != cudaSuccess) return DCOPF_ERR_CUDA;
-    for (cudaGraphNode_t nd : nodes) {
-      cudaGraphNodeType ty;
-      cudaEvent_t e = nullptr;
-      if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord ||
-          cudaGraphEventRecordNodeGetEvent(nd, &e) != cudaSuccess)
-        continue;
-      for (int i = 0; i < n; ++i)
-        for (int q = 0; q < 6; ++q)
-          if (items[i].h->kev[q] && e == items[i].h->kev[q]) G.knodes.push_back({nd, i, q});
-    }
-    for (int i = 0; i < n; ++i) {
-      dcopf_dual* hi = items[i].h;
-      if (!hi->timing || !hi->kev[0]) continue;
-      for (int q = 0; q < 6; ++q)
-        if (!hi->kev2[q] && cudaEventCreate(&hi->kev2[q]) != cudaSuccess) return DCOPF_ERR_CUDA;
-    }
+  // each timed network's second event set (odd rounds)
+  for (int i = 0; i < n; ++i) {
+    dcopf_dual* hi = items[i].h;
+    if (!hi->timing || !hi->kev[0]) continue;
+    for (int q = 0; q < 6; ++q)
+      if (!hi->kev2[q] && cudaEventCreate(&hi->kev2[q]) != cudaSuccess) return DCOPF_ERR_CUDA;
   }
   const bool verbose = h0->verbose;
   const double t_captured = host_ms();
@@ -1644,12 +1684,6 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
       return DCOPF_ERR_CUDA;
     if (hi->bb.snap.alloc(sizeof(int) * (size_t)items[i].B) != cudaSuccess) return DCOPF_ERR_OOM;
   }
-  G.stage_ev.resize(n, nullptr);
-  G.cert_ev.resize(n, nullptr);
-  for (int i = 0; i < n; ++i)
-    if (cudaEventCreateWithFlags(&G.stage_ev[i], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&G.cert_ev[i], cudaEventDisableTiming) != cudaSuccess)
-      return DCOPF_ERR_CUDA;
   // Rounds are pipelined: the host enqueues round r (its graph, the accept of round
   // r - 1's certificates, the staging and certificate of round r's candidates, the
   // read-back of the running counts and device error words) and only then waits for
@@ -1661,9 +1695,9 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
   for (int round = 0;; ++round) {
     const int sl = round & 1;
     rounds = round + 1;
-    for (const GroupObjects::KNode& k : G.knodes) {
+    for (const RoundKit::KNode& k : K.knodes) {
       dcopf_dual* hk = items[k.net].h;
-      if (cudaGraphExecEventRecordNodeSetEvent(G.exec, k.node, sl ? hk->kev2[k.q] : hk->kev[k.q]) != cudaSuccess)
+      if (cudaGraphExecEventRecordNodeSetEvent(K.exec, k.node, sl ? hk->kev2[k.q] : hk->kev[k.q]) != cudaSuccess)
         return DCOPF_ERR_CUDA;
     }
     if (verbose) {
@@ -1674,55 +1708,60 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
       G.vev.push_back(b);
       cudaEventRecord(a, cs0);
     }
-    if (h0->timing) cudaEventRecord(G.t0[sl], cs0);
-    if (cudaGraphLaunch(G.exec, cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
+    if (h0->timing) cudaEventRecord(K.t0[sl], cs0);
+    if (cudaGraphLaunch(K.exec, cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
     long long round_launches = 0;
     for (int i = 0; i < n; ++i) {
       items[i].h->launches += 4LL * chunk * runs[i].nv;
       round_launches += 4LL * chunk * runs[i].nv;
     }
-    if (h0->timing) cudaEventRecord(G.t1[sl], cs0);
+    if (h0->timing) cudaEventRecord(K.t1[sl], cs0);
     if (verbose) cudaEventRecord(G.vev.back(), cs0);
-    int* slot = G.pin_dev + (size_t)sl * 2 * n;
-    if (cudaEventRecord(G.ev[2 * n], cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
+    int* slot = K.rb_dev + (size_t)sl * 2 * n;
+    if (cudaEventRecord(K.ev[2 * n], cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
     for (int i = 0; i < n; ++i) {
       cudaStream_t si = items[i].h->tstream;
-      if (i > 0 && cudaStreamWaitEvent(si, G.ev[2 * n], 0) != cudaSuccess) return DCOPF_ERR_CUDA;
+      if (i > 0 && cudaStreamWaitEvent(si, K.ev[2 * n], 0) != cudaSuccess) return DCOPF_ERR_CUDA;
       // every network reports its count and error word; a network still running accepts
       // the certificates of the last round and stages this round's candidates
       dcopf_status r;
-      if ((r = tensor_accept(runs[i], round > 0 && act[i], slot + i, slot + n + i, si, G.cert_ev[i]))) return r;
+      if ((r = tensor_accept(runs[i], round > 0 && act[i], slot + i, slot + n + i, si, K.cert_ev[i]))) return r;
       if (act[i] &&
-          (r = tensor_stage_certify(runs[i], si, items[i].h->cstream, G.stage_ev[i], G.cert_ev[i])))
+          (r = tensor_stage_certify(runs[i], si, items[i].h->cstream, K.stage_ev[i], K.cert_ev[i])))
         return r;
     }
     for (int i = 1; i < n; ++i)
-      if (cudaEventRecord(G.ev[n + i], items[i].h->tstream) != cudaSuccess ||
-          cudaStreamWaitEvent(cs0, G.ev[n + i], 0) != cudaSuccess)
+      if (cudaEventRecord(K.ev[n + i], items[i].h->tstream) != cudaSuccess ||
+          cudaStreamWaitEvent(cs0, K.ev[n + i], 0) != cudaSuccess)
         return DCOPF_ERR_CUDA;
-    if (cudaEventRecord(G.done[sl], cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
+    // the read-back of this round's counts, on its own stream
+    if (cudaEventRecord(K.acc[sl], cs0) != cudaSuccess || cudaStreamWaitEvent(K.rs, K.acc[sl], 0) != cudaSuccess ||
+        cudaMemcpyAsync(K.pin + (size_t)sl * 2 * n, slot, 2 * sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost,
+                        K.rs) != cudaSuccess ||
+        cudaEventRecord(K.done[sl], K.rs) != cudaSuccess)
+      return DCOPF_ERR_CUDA;
     if ((long long)round * chunk > 4LL * max_iters + 64) {  // a cap no solve should reach
-      if (cudaEventSynchronize(G.done[sl]) != cudaSuccess) return DCOPF_ERR_CUDA;
+      if (cudaEventSynchronize(K.done[sl]) != cudaSuccess) return DCOPF_ERR_CUDA;
       break;
     }
     if (round == 0) continue;
     // round r - 1's read-back (round r is already queued behind it)
     const int pv_sl = sl ^ 1;
     const double tw = verbose ? host_ms() : 0.0;
-    if (cudaEventSynchronize(G.done[pv_sl]) != cudaSuccess) return DCOPF_ERR_CUDA;
+    if (cudaEventSynchronize(K.done[pv_sl]) != cudaSuccess) return DCOPF_ERR_CUDA;
     if (verbose) t_wait += host_ms() - tw;
-    const int* pv = G.pin + (size_t)pv_sl * 2 * n;
+    const int* pv = K.pin + (size_t)pv_sl * 2 * n;
     for (int i = 0; i < n; ++i)
       if (pv[n + i]) return (dcopf_status)pv[n + i];
     if (h0->timing) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, G.t0[pv_sl], G.t1[pv_sl]);
+      cudaEventElapsedTime(&ms, K.t0[pv_sl], K.t1[pv_sl]);
       h0->t_iter_ms += ms;
       h0->t_iter_launches += round_launches;
     }
     for (int i = 0; i < n; ++i) {
       dcopf_dual* hi = items[i].h;
-      if (!hi->timing || !hi->kev[0] || !act[i] || G.knodes.empty()) continue;
+      if (!hi->timing || !hi->kev[0] || !act[i] || K.knodes.empty()) continue;
       cudaEvent_t* ks = pv_sl ? hi->kev2 : hi->kev;
       float km[5];
       bool kok = true;
@@ -1740,10 +1779,11 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
     if (!any) break;
   }
   // the last round's graph time (timing), once everything queued has run
-  if (cudaStreamSynchronize(cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
+  if (cudaStreamSynchronize(cs0) != cudaSuccess || cudaStreamSynchronize(K.rs) != cudaSuccess)
+    return DCOPF_ERR_CUDA;
   if (h0->timing) {
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, G.t0[(rounds - 1) & 1], G.t1[(rounds - 1) & 1]);
+    cudaEventElapsedTime(&ms, K.t0[(rounds - 1) & 1], K.t1[(rounds - 1) & 1]);
     h0->t_iter_ms += ms;
   }
   if (verbose) {
@@ -1755,15 +1795,16 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
       if (q + 2 < G.vev.size() && cudaEventElapsedTime(&b, G.vev[q + 1], G.vev[q + 2]) == cudaSuccess) gaps += b;
     }
     fprintf(stderr,
-            "dcopf: group solve: setup + capture %.2f ms (host), %d rounds: graphs %.2f ms, between "
-            "graphs %.2f ms (GPU), host waits %.2f ms, loop %.2f ms (host)\n",
-            t_captured, rounds, graphs, gaps, t_wait, host_ms() - t_captured);
+            "dcopf: group solve: setup %.2f ms, graph %s %.2f ms (host), %d rounds: graphs %.2f ms, "
+            "between graphs %.2f ms (GPU), host waits %.2f ms, loop %.2f ms (host)\n",
+            t_setup, reuse ? "reused" : "captured", t_captured - t_setup, rounds, graphs, gaps, t_wait,
+            host_ms() - t_captured);
   }
   // the last round's certificates: accept what they staged (nothing, when every
   // instance had stopped before that round)
   for (int i = 0; i < n; ++i) {
-    int* slot = G.pin_dev + (size_t)(rounds & 1) * 2 * n;  // free: everything queued has run
-    dcopf_status r = tensor_accept(runs[i], true, slot + i, slot + n + i, items[i].h->tstream, G.cert_ev[i]);
+    int* slot = K.rb_dev + (size_t)(rounds & 1) * 2 * n;  // free: everything queued has run
+    dcopf_status r = tensor_accept(runs[i], true, slot + i, slot + n + i, items[i].h->tstream, K.cert_ev[i]);
     if (r) return r;
   }
   for (int i = 0; i < n; ++i) {

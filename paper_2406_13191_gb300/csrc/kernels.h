@@ -194,8 +194,60 @@ struct BatchView {
   float* sv_hi = nullptr;      // [B][nl] the best point, saved when its buffer is reused
   float* sv_lo = nullptr;
   double* lam_best = nullptr;  // [B] lambda of the best point
-  double* line_part = nullptr; // [B][n_tiles] per chunk of lines of the step kernel
-  double* out_part = nullptr;  // [B][n_tiles]
+  double* line_part = nullptr; // [B][n_tiles x 8] per warp of the step kernel's chunks
+  double* out_part = nullptr;  // [B][n_tiles x 8]
+};
+
+// Objects a batched solve reuses from call to call (kept by the first network's handle):
+// the round loop's events and host-mapped read-back, and the iteration graph of the
+// last solve with the bytes of the kernel arguments it was captured with.
+struct RoundKit {
+  int n = 0;  // networks the events and the read-back are made for
+  std::vector<cudaEvent_t> ev, stage_ev, cert_ev;
+  // per round parity [2][2n]: each network's running count and device error word,
+  // written by its accept kernel on the device and copied to pinned host memory on the
+  // read-back stream, off the iterations' critical path
+  int* rb_dev = nullptr;
+  int* pin = nullptr;
+  cudaStream_t rs = nullptr;
+  cudaEvent_t acc[2] = {nullptr, nullptr};   // a round's accept kernels have run
+  cudaEvent_t done[2] = {nullptr, nullptr};  // a round's read-back has landed
+  cudaEvent_t t0[2] = {nullptr, nullptr}, t1[2] = {nullptr, nullptr};  // around a round's graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<unsigned char> sig;
+  // the graph's per-kernel timing nodes: (node, network, event index)
+  struct KNode {
+    cudaGraphNode_t node;
+    int net, q;
+  };
+  std::vector<KNode> knodes;
+  void drop_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    sig.clear();
+    knodes.clear();
+  }
+  void release() {
+    drop_graph();
+    for (auto* v : {&ev, &stage_ev, &cert_ev})
+      for (cudaEvent_t e : *v)
+        if (e) cudaEventDestroy(e);
+    ev.clear(); stage_ev.clear(); cert_ev.clear();
+    for (cudaEvent_t* e : {&acc[0], &acc[1], &done[0], &done[1], &t0[0], &t0[1], &t1[0], &t1[1]}) {
+      if (*e) cudaEventDestroy(*e);
+      *e = nullptr;
+    }
+    if (rs) cudaStreamDestroy(rs);
+    if (pin) cudaFreeHost(pin);
+    if (rb_dev) cudaFree(rb_dev);
+    rs = nullptr;
+    pin = rb_dev = nullptr;
+    n = 0;
+  }
+  ~RoundKit() { release(); }
 };
 
 struct BatchBufs {
@@ -248,6 +300,7 @@ struct dcopf_dual {
   cudaStream_t tstream2 = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaEvent_t tev = nullptr;  // orders the internal stream after the caller's
+  dcopf::RoundKit kit;         // round-loop objects and the cached iteration graph
   long long launches = 0;
   // optional event timing of the iteration kernels
   bool timing = false;

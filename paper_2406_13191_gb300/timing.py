@@ -66,8 +66,11 @@ def batched(cfg, batch, iters, verbose=False, screen=False):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     ms, launches, evals = g.read_timing()
+    kt, ks = g.read_kernel_timing()
     per_iter_us = 1e3 * ms / max(1.0, evals / batch)
     print(json.dumps(dict(mode="batched", config=cfg, batch=batch, iters=iters, screen=screen,
+                          shapes=g.tensor_shapes(),
+                          kernel_us={k: round(1e3 * v / max(1, ks), 2) for k, v in kt.items()},
                           kept_lines=int(g.screened_lines().sum()) if screen else w.net.n_line,
                           wall_ms=1e3 * wall, iteration_kernels_ms=ms,
                           us_per_batched_iteration=per_iter_us,

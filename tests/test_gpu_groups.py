@@ -107,3 +107,29 @@ def test_kernel_timing_samples_every_round():
         assert samples >= rounds - 1
         assert ms["adjoint"] > 0 and ms["forward"] > 0 and ms["step"] > 0 and ms["minimiser"] > 0
         assert it_ms > 0 and evals == int(r.iters.sum().item())
+
+
+def test_iteration_graph_reused_only_for_the_same_arguments():
+    """A handle keeps the iteration graph of its last batched solve and replays it for a
+    solve whose kernel arguments are the same bytes.  Solves with settings A, B, A on one
+    handle: the second A solve (a replay) equals the first bit for bit, and the B solve
+    (captured anew) equals B on a fresh handle."""
+    gg = json.load(open(os.path.join(GOLDEN, "group_gamma.json")))
+    w = synth.workload(1, batch=256)
+    gam = np.array(gg["2000"], dtype=float)
+    kw_a = dict(QP_ADAM)
+    kw_b = dict(QP_ADAM, alpha=2000.0, beta1=0.9)
+
+    def run(g, kw):
+        r = g.solve(w.loads, target=gam, gap=1e-3, path="batched", precision="bf16x3", **kw)
+        torch.cuda.synchronize()
+        return [t.cpu().numpy().copy() for t in (r.bound, r.iters, r.lam, r.mu_hi)]
+
+    g = _handle(w.net, "0,3,0,1")
+    a1, b1, a2 = run(g, kw_a), run(g, kw_b), run(g, kw_a)
+    fresh = run(_handle(w.net, "0,3,0,1"), kw_b)
+    for x, y in zip(a1, a2):
+        np.testing.assert_array_equal(x, y)
+    for x, y in zip(b1, fresh):
+        np.testing.assert_array_equal(x, y)
+    assert not np.array_equal(a1[1], b1[1])   # the settings differ in iterations taken
