@@ -64,10 +64,14 @@ C2 = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99, max_ite
           path="batched", precision="bf16x3")
 QP_ADAM = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997)
 LP_ADAM = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99)
-# DRAM bytes (read + write) per launch of the two products from an ncu capture of the
-# 10000-bus batch of 256 with screening (profiles/bench_10000bus_b256.md), valid for the
-# product kernels' source with this digest and the product shapes named; null otherwise.
-NCU_TRAFFIC = {"416e5b070f67b443": {"shape": "3,4,3", "adjoint": 114.6e6, "forward": 105.0e6}}
+# DRAM bytes (read + write) per launch of the two products from ncu captures of the
+# 10000-bus batch of 256 with screening (profiles/bench_10000bus_b256.md), one per CTA-pair
+# tile width (the tiles code of the shapes), valid for the product kernels' source with
+# this digest; null for another source or for single-CTA tiles.
+NCU_TRAFFIC = {"3d24969031fee2d2": {1: {"adjoint": 116.8e6, "forward": 105.0e6},
+                          2: {"adjoint": 115.5e6, "forward": 105.2e6},
+                          3: {"adjoint": 114.8e6, "forward": 104.7e6},
+                          4: {"adjoint": 114.9e6, "forward": 105.1e6}}}
 
 
 def golden(name):
@@ -80,12 +84,13 @@ def kernel_digest() -> str:
 
 
 def traffic_for(shapes, kernel):
-    """ncu DRAM bytes per launch of `kernel` ("adjoint" / "forward"), or None when the
-    capture does not cover the current kernel source or product shapes."""
+    """ncu DRAM bytes per launch of `kernel` ("adjoint" / "forward"), or None when no
+    capture covers the current kernel source and that product's tiles."""
     t = NCU_TRAFFIC.get(kernel_digest())
-    if t is None or not shapes["code"].startswith(t["shape"] + ","):
+    tiles = int(shapes["code"].split(",")[0 if kernel == "adjoint" else 2])
+    if t is None or tiles not in t:
         return None
-    return t[kernel]
+    return t[tiles][kernel]
 
 
 def load_peaks():

@@ -486,10 +486,11 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
     if (t && strcmp(t, "256") == 0) h->tiles_mode = 2;
     if (t && strcmp(t, "192") == 0) h->tiles_mode = 3;
     if (t && strcmp(t, "160") == 0) h->tiles_mode = 4;
+    if (t && strcmp(t, "144") == 0) h->tiles_mode = 5;
     const char* sh = getenv("DCOPF_TENSOR_SHAPE");
     int a = -1, sp = 0, fw = -1, br = 1;
     const int nf = sh ? sscanf(sh, "%d,%d,%d,%d", &a, &sp, &fw, &br) : 0;
-    if (nf >= 3 && a >= 0 && a <= 3 && sp >= 1 && sp <= 64 && fw >= 0 && fw <= 3 && br >= 1 &&
+    if (nf >= 3 && a >= 0 && a <= 4 && sp >= 1 && sp <= 64 && fw >= 0 && fw <= 4 && br >= 1 &&
         br <= 2) {
       h->shape_adj = a;
       h->shape_splits = sp;
@@ -531,6 +532,12 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
   std::vector<float> sig32(H.sigma.begin(), H.sigma.end()), ctil32(H.ctil.begin(), H.ctil.end()),
       mq32(H.mq.begin(), H.mq.end()), cconst32(H.cconst.begin(), H.cconst.end()),
       mid32(H.mid.begin(), H.mid.end());
+  std::vector<float> gen4(4 * (size_t)ng), gen2(2 * (size_t)ng);
+  for (int j = 0; j < ng; ++j) {
+    gen4[4 * j] = sig32[j]; gen4[4 * j + 1] = ctil32[j]; gen4[4 * j + 2] = mq32[j]; gen4[4 * j + 3] = cconst32[j];
+    gen2[2 * j] = mid32[j];
+    gen2[2 * j + 1] = mq32[j] > 0.f ? 1.0f / (2.0f * mq32[j]) : 0.f;
+  }
   const size_t nphi = h->sparse_only ? 0 : (size_t)nl * ng;  // no PTDF on a sparse-only handle
   std::vector<double> phit(nphi);
   std::vector<float> phi32(nphi), phit32(nphi);
@@ -561,7 +568,14 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
   UP(H.bus_line_coef, bus_line_coef) UP(H.gen_bus, gen_bus) UP(H.pmin, pmin) UP(H.pmax, pmax)
   UP(H.cost_lin, cost_lin) UP(H.cost_quad, cost_quad) UP(H.sigma, sigma) UP(H.mid, mid)
   UP(H.ctil, ctil) UP(H.mq, mq) UP(H.cconst, cconst) UP(sig32, sigma32) UP(ctil32, ctil32)
-  UP(mq32, mq32) UP(cconst32, cconst32) UP(mid32, mid32) UP(H.phi, phi64) UP(phit, phit64) UP(phi32, phi32) UP(phit32, phit32)
+  UP(mq32, mq32) UP(cconst32, cconst32) UP(mid32, mid32)
+  {
+    const float* g4 = nullptr;
+    const float* g2 = nullptr;
+    if ((st = upload(h, gen4, &g4)) != DCOPF_OK || (st = upload(h, gen2, &g2)) != DCOPF_OK) { delete h; return st; }
+    D.gen4 = (const float4*)g4;
+    D.gen2 = (const float2*)g2;
+  } UP(H.phi, phi64) UP(phit, phit64) UP(phi32, phi32) UP(phit32, phit32)
 #undef UP
   if (!H.F.blob.empty()) {
     if ((st = upload(h, H.F.blob, &D.fac_blob)) != DCOPF_OK) { delete h; return st; }
@@ -748,7 +762,7 @@ dcopf_status dcopf_dual_solve_batch(dcopf_dual_t h, int32_t batch, const double*
   cudaStream_t s = (cudaStream_t)stream;
   if ((r = check_outage(h, batch, outage, s))) return r;
   if ((r = ensure_workspace(h, batch))) return r;
-  CUDA_TRY(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_err, 0, 2 * sizeof(int), s));  // error word, re-screen flag
   if ((r = run_base_flows(h, batch, loads, outage, s))) return r;
   dcopf_solve_params q = p;
   q.precision = prec;
@@ -806,7 +820,7 @@ dcopf_status dcopf_dual_solve_group(int32_t n_items, const dcopf_group_item* ite
     dcopf_dual* h = items[i].net;
     if ((r = check_outage(h, items[i].batch, items[i].outage, s))) return r;
     if ((r = ensure_workspace(h, items[i].batch))) return r;
-    CUDA_TRY(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_err, 0, 2 * sizeof(int), s));  // error word, re-screen flag
     if ((r = run_base_flows(h, items[i].batch, items[i].loads, items[i].outage, s))) return r;
   }
   return solve_tensor_group(ti.data(), n_items, *params, s);

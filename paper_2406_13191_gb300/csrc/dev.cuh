@@ -42,6 +42,9 @@ struct DevNet {
   const double* sigma; const double* mid; const double* ctil; const double* mq; const double* cconst;
   const float* sigma32; const float* ctil32; const float* mq32; const float* cconst32;
   const float* mid32;
+  // the minimiser's constants packed per generator: (sigma, ctil, mq, cconst) and
+  // (mid, 1 / (2 mq), 0 for a linear cost)
+  const float4* gen4; const float2* gen2;
   // dense operators
   const double* phi64; const double* phit64;
   const float* phi32; const float* phit32;

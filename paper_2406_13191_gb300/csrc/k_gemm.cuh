@@ -219,8 +219,10 @@ __global__ void __launch_bounds__(192, OCC)
 // of the accumulator and each CTA runs the epilogue of its rows.
 constexpr int PBM = 256;
 
-// PBN: the pair tile's width (256, 192 or 160 output columns, a multiple of 32; each CTA
-// loads PBN / 2 rows of B).
+// PBN: the pair tile's width (256, 192, 160 or 144 output columns, a multiple of 16;
+// each CTA loads PBN / 2 rows of B).  The epilogue reads TMEM 32 columns at a time: for a
+// width that is not a multiple of 32 the last read runs past the tile's columns into
+// the rest of the (256-column) allocation, and those columns are not stored.
 template <int NPROD, int PBN>
 struct PairCfg {
   static constexpr uint32_t B_TILE = (uint32_t)(PBN / 2) * GBK * 2;
@@ -231,7 +233,8 @@ struct PairCfg {
   static constexpr uint32_t TMEM_COLS = PBN <= 128 ? 128 : 256;  // a power of two
   static_assert(STAGES >= 2, "a ring of at least two stages");
   static_assert(B_TILE % 1024 == 0, "tiles start on 1024-byte (swizzle atom) boundaries");
-  static_assert(PBN % 32 == 0 && PBN <= 256, "the epilogue reads TMEM 32 columns at a time");
+  static_assert(PBN % 16 == 0 && PBN <= 256 && (PBN + 31) / 32 * 32 <= (int)TMEM_COLS,
+                "the epilogue's 32-column TMEM reads stay inside the allocation");
   static_assert(STAGES * STAGE_BYTES >= 128 * (PBN + 1) * 4, "the ring stages the output tile");
 };
 
@@ -334,32 +337,34 @@ __global__ void __launch_bounds__(192, 1)
     if (!ready) s_abort = 1;
     if (ready && nkb > 0) {
 #pragma unroll 1
-      for (int cc = 0; cc < PBN / 32; ++cc) {
+      for (int cc = 0; cc < (PBN + 31) / 32; ++cc) {
         float v[32];
         umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cc), v);
         const int col0 = n0 + 32 * cc;
+        const int lim = min(PBN - 32 * cc, g.N - col0);  // columns of this read that are output
         if (g.epi == EPI_TILE) {
           float* tile = (float*)base;
 #pragma unroll
-          for (int u = 0; u < 32; ++u) tile[(32 * q + lane) * (PBN + 1) + 32 * cc + u] = v[u];
+          for (int u = 0; u < 32; ++u)
+            if (u < PBN - 32 * cc) tile[(32 * q + lane) * (PBN + 1) + 32 * cc + u] = v[u];
         } else if (row < g.M) {
           if (g.epi == EPI_PARTIAL) {
             float* dst = g.P + ((size_t)blockIdx.z * g.M + row) * g.ldp + col0;
-            if (col0 + 32 <= g.N) {
+            if (lim >= 32) {
 #pragma unroll
               for (int u = 0; u < 8; ++u)
                 reinterpret_cast<float4*>(dst)[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
             } else {
 #pragma unroll
               for (int u = 0; u < 32; ++u)
-                if (col0 + u < g.N) dst[u] = v[u];
+                if (u < lim) dst[u] = v[u];
             }
           } else {
             const double* f0 = g.f0 + (size_t)row * g.ldf + col0;
             double* f = g.f + (size_t)row * g.ldf + col0;
 #pragma unroll
             for (int u = 0; u < 32; ++u)
-              if (col0 + u < g.N) f[u] = (double)v[u] + f0[u];
+              if (u < lim) f[u] = (double)v[u] + f0[u];
           }
         }
       }
@@ -374,9 +379,9 @@ __global__ void __launch_bounds__(192, 1)
       if (r >= g.M) break;
       float* dst = g.F32 + (size_t)r * g.ldf32;
 #pragma unroll
-      for (int q = 0; q < PBN / 32; ++q) {
+      for (int q = 0; q < (PBN + 31) / 32; ++q) {
         const int c = lane + 32 * q;
-        if (n0 + c < g.N) dst[n0 + c] = tile[m * (PBN + 1) + c];
+        if (c < PBN && n0 + c < g.N) dst[n0 + c] = tile[m * (PBN + 1) + c];
       }
     }
   }

@@ -52,12 +52,31 @@ __global__ void k_screen_envelope(int B, int nl, const double* __restrict__ f0,
   }
 }
 
+// Whether the knapsack bounds must be taken again: they hold for any balance range
+// inside the one they were taken on (rng[0..1], valid when rng[2] != 0).  If the batch's
+// range r[0..1] leaves it, the new range is the batch's widened a little (so that nearby
+// batches reuse the bounds) and *redo = 1.  One thread.
+__global__ void k_screen_range(const double* __restrict__ r, double* __restrict__ rng, int* __restrict__ redo) {
+  if (rng[2] != 0.0 && r[0] >= rng[0] && r[1] <= rng[1]) {
+    *redo = 0;
+    return;
+  }
+  const double w = 0.02 * (fabs(r[0]) + fabs(r[1])) + 1e-9;
+  rng[0] = r[0] - w;
+  rng[1] = r[1] + w;
+  rng[2] = 1.0;
+  *redo = 1;
+}
+
 // One warp per line: the knapsack bounds up_l >= max Phi~_l x and dn_l >= max -Phi~_l x
-// over the box and every balance R in [rlo, rhi].
-__global__ void __launch_bounds__(256) k_screen_knapsack(DevNet N, double rlo, double rhi,
+// over the box and every balance R in [rng[0], rng[1]] (when *redo; else the bounds
+// already in up / dn hold).
+__global__ void __launch_bounds__(256) k_screen_knapsack(DevNet N, const double* __restrict__ rng,
+                                                         const int* __restrict__ redo,
                                                          double* __restrict__ up, double* __restrict__ dn) {
   const int l = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (l >= N.n_line) return;  // whole warps
+  if (l >= N.n_line || !*redo) return;  // whole warps
+  const double rlo = rng[0], rhi = rng[1];
   const int ng = N.n_gen;
   const float* p32 = N.phi32 + (size_t)l * ng;
   const double* p64 = N.phi64 + (size_t)l * ng;
@@ -117,6 +136,14 @@ __global__ void k_screen_decide(DevNet N, const double* __restrict__ up, const d
   }
 }
 
+// *flag = 1 if a line that this batch must keep (keep[l]) is not in the kept set of the
+// compact operands (pos[l] < 0): the solve that went ahead with them screens again.
+__global__ void k_screen_cover(int nl, const unsigned char* __restrict__ keep, const int* __restrict__ pos,
+                               int* __restrict__ flag) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += gridDim.x * blockDim.x)
+    if (keep[l] && pos[l] < 0) *flag = 1;
+}
+
 // Compact BF16 operands of the kept lines: rows of the forward operand [n_line][ld_g]
 // and columns (the K dimension) of the adjoint operand [n_gen][ld_l].
 __global__ void k_screen_gather_rows(int nk, int ld, const int* __restrict__ kept,
@@ -159,12 +186,15 @@ __global__ void k_screen_compact_rows(int B, int nl, int nk, const int* __restri
 dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s) {
   LineScreen& S = h->scr;
   const int nl = h->host.n_line, ng = h->host.n_gen;
+  const bool fresh = S.rng.p == nullptr;
   if (S.env.alloc((size_t)(2 * nl + 2) * sizeof(double)) != cudaSuccess ||
       S.knap.alloc((size_t)2 * nl * sizeof(double)) != cudaSuccess ||
-      S.keep.alloc((size_t)nl) != cudaSuccess) {
+      S.keep.alloc((size_t)nl) != cudaSuccess || S.rng.alloc(4 * sizeof(double)) != cudaSuccess ||
+      S.flags.alloc(4 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return DCOPF_ERR_OOM;
   }
+  if (fresh && cudaMemsetAsync(S.rng.p, 0, 4 * sizeof(double), s) != cudaSuccess) return DCOPF_ERR_CUDA;
   double* lo = S.env.as<double>();
   double* hi = lo + nl;
   double* r = hi + nl;
@@ -173,23 +203,21 @@ dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s) {
   const unsigned grid = (unsigned)std::min(1024, (nl + 255) / 256);
   k_screen_envelope<<<grid, 256, 0, s>>>(B, nl, h->ws.f0.as<double>(), h->ws.demand.as<double>(), sum_mid,
                                          lo, hi, r);
-  double rr[2];
-  if (cudaMemcpyAsync(rr, r, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return DCOPF_ERR_CUDA;
   double* up = S.knap.as<double>();
   double* dn = up + nl;
-  // the knapsack bounds hold for any balance range inside the one they were taken on
-  if (!(S.knap_valid && rr[0] >= S.rlo && rr[1] <= S.rhi)) {
-    // a little wider than this batch, so that nearby batches reuse them
-    const double w = 0.02 * (fabs(rr[0]) + fabs(rr[1])) + 1e-9;
-    S.rlo = rr[0] - w;
-    S.rhi = rr[1] + w;
-    k_screen_knapsack<<<(unsigned)((nl + 7) / 8), 256, 0, s>>>(h->dev, S.rlo, S.rhi, up, dn);
-    S.knap_valid = true;
-  }
+  double* rng = S.rng.as<double>();
+  int* redo = S.flags.as<int>();
+  k_screen_range<<<1, 1, 0, s>>>(r, rng, redo);
+  k_screen_knapsack<<<(unsigned)((nl + 7) / 8), 256, 0, s>>>(h->dev, rng, redo, up, dn);
   k_screen_decide<<<grid, 256, 0, s>>>(h->dev, up, dn, lo, hi, S.keep.as<unsigned char>());
-  h->launches += 3;
+  h->launches += 4;
+  if (S.ready && !S.exact) {
+    // go ahead with the kept set of the compact operands, and let the solve find out
+    // (device error word [1]) whether this batch needs a line outside it
+    k_screen_cover<<<grid, 256, 0, s>>>(nl, S.keep.as<unsigned char>(), S.pos.as<int>(), h->d_err + 1);
+    h->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? DCOPF_OK : DCOPF_ERR_CUDA;
+  }
   std::vector<unsigned char> keep(nl);
   if (cudaMemcpyAsync(keep.data(), S.keep.p, nl, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -241,12 +269,17 @@ dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s) {
       !tc_make_map_rows(&S.m_phi_hi80, S.phi_hi.p, nk, ng, T.ld_g, 80) ||
       !tc_make_map_rows(&S.m_phi_lo80, S.phi_lo.p, nk, ng, T.ld_g, 80) ||
       !tc_make_map_rows(&S.m_phit_hi80, S.phit_hi.p, ng, nk, ld_lk, 80) ||
-      !tc_make_map_rows(&S.m_phit_lo80, S.phit_lo.p, ng, nk, ld_lk, 80))
+      !tc_make_map_rows(&S.m_phit_lo80, S.phit_lo.p, ng, nk, ld_lk, 80) ||
+      !tc_make_map_rows(&S.m_phi_hi72, S.phi_hi.p, nk, ng, T.ld_g, 72) ||
+      !tc_make_map_rows(&S.m_phi_lo72, S.phi_lo.p, nk, ng, T.ld_g, 72) ||
+      !tc_make_map_rows(&S.m_phit_hi72, S.phit_hi.p, ng, nk, ld_lk, 72) ||
+      !tc_make_map_rows(&S.m_phit_lo72, S.phit_lo.p, ng, nk, ld_lk, 72))
     return DCOPF_ERR_CUDA;
   S.nk = nk;
   S.ld_lk = ld_lk;
   S.kept_host = kept;
   S.ready = true;
+  S.exact = false;
   S.map_B = 0;  // the per-batch A operand maps are made for the next batch size
   return DCOPF_OK;
 }

@@ -21,6 +21,9 @@
 
 namespace dcopf {
 
+// Internal status of a batched solve that must run again with a fresh constraint screen.
+constexpr dcopf_status kRescreen = (dcopf_status)1000;
+
 // Step-rule constants in FP32, converted once on the host (FP64 conversions per
 // element are not free on this part).
 struct StepArgsF {
@@ -95,7 +98,7 @@ struct StepEpi {
   float* sv_hi; float* sv_lo;
   float* s1_hi; float* s2_hi; float* s1_lo; float* s2_lo;
   __nv_bfloat16* Hh; __nv_bfloat16* Hl; int ldh;
-  double* line_part; double* out_part; int n_tiles;   // [B][n_tiles x STEP_WARPS] per warp of a chunk
+  double* line_part; double* out_part; int n_tiles;   // [B][n_tiles] per slice of lines
   int B;                      // instances
   // the dual value and the stop tests of the evaluated point (finalize_instance), run by
   // the last of an instance's blocks to finish: step_done [B] counts them
@@ -107,21 +110,17 @@ struct StepEpi {
   int* step_done;
 };
 
-// The tail of both step kernels, per warp: the warp's partials of the value and of
-// u^T eta go to slot `part` of the instance's [n_tiles * STEP_WARPS]; the last warp of
-// instance b to finish runs its value and stop tests.  No block-wide barrier: warps
-// finish on their own.
-__device__ __forceinline__ void step_tail(const StepEpi& E, int b, int part, float lacc, float oacc);
+// The step's work is a slice of STEP_SLICE lines of one instance per warp (four lines
+// per lane, coalesced), elementwise; slices of an instance are numbered 0 .. n_tiles - 1
+// and each leaves FP64 partials of the value and of u^T eta.
+constexpr int STEP_THREADS = 256, STEP_SLICE = 128;
 
-// One block per (chunk of STEP_CHUNK lines, instance): elementwise, full occupancy,
-// coalesced; per-chunk FP64 partials of the value and of u^T eta.
-constexpr int STEP_THREADS = 256, STEP_PER_THREAD = 4;
-constexpr int STEP_CHUNK = STEP_THREADS * STEP_PER_THREAD;
-constexpr int STEP_WARPS = STEP_THREADS / 32;  // partials per chunk
-
+// The tail of both step kernels, per warp: the warp's partials go to slot `part` of the
+// instance's [n_tiles]; the last warp of instance b to finish runs its value and stop
+// tests.  No block-wide barrier: warps finish on their own.
 __device__ __forceinline__ void step_tail(const StepEpi& E, int b, int part, float lacc, float oacc) {
   const int lane = threadIdx.x & 31;
-  const int np = E.n_tiles * STEP_WARPS;
+  const int np = E.n_tiles;
   // release / acquire at GPU scope around a relaxed count: the warp's writes (ordered
   // before lane 0's fence by __syncwarp) before its count, every other warp's before
   // the last one reads them
@@ -141,7 +140,7 @@ __device__ __forceinline__ void step_tail(const StepEpi& E, int b, int part, flo
   }
 }
 
-__device__ __forceinline__ void step_item(const StepEpi& E, int nl, int b, int chunk) {
+__device__ __forceinline__ void step_item(const StepEpi& E, int nl, int b, int part) {
   if (E.frozen[b]) return;
   const int k = E.outage ? E.outage[b] : -1;
   const float t_out = k >= 0 ? E.tout[b] : 0.f;
@@ -154,16 +153,14 @@ __device__ __forceinline__ void step_item(const StepEpi& E, int nl, int b, int c
   float* mln = E.mu_lo[pn] + o;
   const float am = E.stepf[4 * b], a1s = E.stepf[4 * b + 1], r2 = E.stepf[4 * b + 2];
   const float* Fr = E.F + (size_t)b * E.ldF;
-  // a thread's few terms are summed in FP32 and the block sum is FP64 (FP64 throughput
-  // is low on this part: per-element FP64 would dominate the kernel)
+  // a lane's few terms are summed in FP32 and the warp's partial is FP64 (FP64
+  // throughput is low on this part: per-element FP64 would dominate the kernel)
   float lacc = 0.f, oacc = 0.f;
-  const int i0 = chunk * STEP_CHUNK + threadIdx.x;
-  float fl[STEP_PER_THREAD], ui[STEP_PER_THREAD], mh[STEP_PER_THREAD], ml[STEP_PER_THREAD],
-      a1[STEP_PER_THREAD], a2[STEP_PER_THREAD], b1[STEP_PER_THREAD], b2[STEP_PER_THREAD],
-      fx[STEP_PER_THREAD], fn[STEP_PER_THREAD];
+  const int i0 = part * STEP_SLICE + (int)(threadIdx.x & 31);
+  float fl[4], ui[4], mh[4], ml[4], a1[4], a2[4], b1[4], b2[4], fx[4], fn[4];
 #pragma unroll
-  for (int q = 0; q < STEP_PER_THREAD; ++q) {  // all loads in flight before any arithmetic
-    const int i = i0 + q * STEP_THREADS;
+  for (int q = 0; q < 4; ++q) {  // all loads in flight before any arithmetic
+    const int i = i0 + 32 * q;
     const bool in = i < nl;
     fl[q] = in ? Fr[i] + E.f0[o + i] : 0.f;
     ui[q] = (in && k >= 0) ? E.u[o + i] : 0.f;
@@ -177,8 +174,8 @@ __device__ __forceinline__ void step_item(const StepEpi& E, int nl, int b, int c
     b2[q] = in ? E.s2_lo[o + i] : 0.f;
   }
 #pragma unroll
-  for (int q = 0; q < STEP_PER_THREAD; ++q) {
-    const int i = i0 + q * STEP_THREADS;
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + 32 * q;
     if (i >= nl) continue;
     const float f = fl[q] + ui[q] * t_out;
     const float gh = f - fx[q], gl = fn[q] - f;
@@ -196,17 +193,16 @@ __device__ __forceinline__ void step_item(const StepEpi& E, int nl, int b, int c
     split_bf16(eta, E.Hh + (size_t)b * E.ldh + i, E.Hl + (size_t)b * E.ldh + i);
     if (k >= 0) oacc = fmaf(ui[q], eta, oacc);
   }
-  // warp sums in FP32, the 8 warp partials in FP64 (fixed order)
   // a warp's terms in FP32, its partials in FP64 (summed in a fixed order by the value)
   lacc = warp_sum(lacc);
   oacc = warp_sum(oacc);
-  step_tail(E, b, chunk * STEP_WARPS + (int)(threadIdx.x >> 5), lacc, oacc);
+  step_tail(E, b, part, lacc, oacc);
 }
 
-// The same step with four consecutive lines per thread: 16-byte loads and stores of every
+// The same step with four consecutive lines per lane: 16-byte loads and stores of every
 // FP32 stream and 8-byte stores of the BF16 split (needs n_line, ldF and ldh multiples
-// of 4; the chunk of a block is the same 1024 lines as k_bt_step's).
-__device__ __forceinline__ void step4_item(const StepEpi& E, int nl, int b, int chunk) {
+// of 4).
+__device__ __forceinline__ void step4_item(const StepEpi& E, int nl, int b, int part) {
   if (E.frozen[b]) return;
   const int k = E.outage ? E.outage[b] : -1;
   const float t_out = k >= 0 ? E.tout[b] : 0.f;
@@ -214,7 +210,7 @@ __device__ __forceinline__ void step4_item(const StepEpi& E, int nl, int b, int 
   const bool save = it >= 2 && E.best_iter[b] == it - 1;  // point it - 2 is the best
   const size_t o = (size_t)b * nl;
   const float am = E.stepf[4 * b], a1s = E.stepf[4 * b + 1], r2 = E.stepf[4 * b + 2];
-  const int i = 4 * (chunk * STEP_THREADS + threadIdx.x);
+  const int i = part * STEP_SLICE + 4 * (int)(threadIdx.x & 31);
   float lacc = 0.f, oacc = 0.f;
   if (i < nl) {
     auto ld4 = [](const float* p) { return *reinterpret_cast<const float4*>(p); };
@@ -270,21 +266,23 @@ __device__ __forceinline__ void step4_item(const StepEpi& E, int nl, int b, int 
   // a warp's terms in FP32, its partials in FP64 (summed in a fixed order by the value)
   lacc = warp_sum(lacc);
   oacc = warp_sum(oacc);
-  step_tail(E, b, chunk * STEP_WARPS + (int)(threadIdx.x >> 5), lacc, oacc);
+  step_tail(E, b, part, lacc, oacc);
 }
 
-// The step kernels: work item w = (instance w / n_tiles, chunk of lines w % n_tiles),
-// taken in turn by the launched blocks: one per item, or fewer, so that the step leaves
-// room on the SMs for another instance group's products (a block holds 64 registers x
-// 256 threads).  An instance's items run in any order (its last one runs the value).
+// The step kernels: slice w = (instance w / n_tiles, slice w % n_tiles of its lines),
+// one per warp of the grid, or taken in turn by the warps of a smaller grid (that leaves
+// room on the SMs for another instance group's products; a block holds 64 registers x
+// 256 threads).  An instance's slices run in any order (its last one runs the value).
 __global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
-  const int total = E.n_tiles * E.B;
-  for (int w = blockIdx.x; w < total; w += gridDim.x) step_item(E, nl, w / E.n_tiles, w % E.n_tiles);
+  const int nw = blockDim.x >> 5, total = E.n_tiles * E.B;
+  for (int w = blockIdx.x * nw + (int)(threadIdx.x >> 5); w < total; w += gridDim.x * nw)
+    step_item(E, nl, w / E.n_tiles, w % E.n_tiles);
 }
 
 __global__ void __launch_bounds__(STEP_THREADS, 4) k_bt_step4(StepEpi E, int nl) {
-  const int total = E.n_tiles * E.B;
-  for (int w = blockIdx.x; w < total; w += gridDim.x) step4_item(E, nl, w / E.n_tiles, w % E.n_tiles);
+  const int nw = blockDim.x >> 5, total = E.n_tiles * E.B;
+  for (int w = blockIdx.x * nw + (int)(threadIdx.x >> 5); w < total; w += gridDim.x * nw)
+    step4_item(E, nl, w / E.n_tiles, w % E.n_tiles);
 }
 
 // ------------------------------------------------------------------ operand preparation
@@ -422,7 +420,11 @@ dcopf_status ensure_tensor_operands(dcopf_dual* h) {
       !make_map(&T.m_phi_hi80, T.phi_hi.p, nl, ng, T.ld_g, 80) ||
       !make_map(&T.m_phi_lo80, T.phi_lo.p, nl, ng, T.ld_g, 80) ||
       !make_map(&T.m_phit_hi80, T.phit_hi.p, ng, nl, T.ld_l, 80) ||
-      !make_map(&T.m_phit_lo80, T.phit_lo.p, ng, nl, T.ld_l, 80))
+      !make_map(&T.m_phit_lo80, T.phit_lo.p, ng, nl, T.ld_l, 80) ||
+      !make_map(&T.m_phi_hi72, T.phi_hi.p, nl, ng, T.ld_g, 72) ||
+      !make_map(&T.m_phi_lo72, T.phi_lo.p, nl, ng, T.ld_g, 72) ||
+      !make_map(&T.m_phit_hi72, T.phit_hi.p, ng, nl, T.ld_l, 72) ||
+      !make_map(&T.m_phit_lo72, T.phit_lo.p, ng, nl, T.ld_l, 72))
     return DCOPF_ERR_CUDA;
   if (prepare_gemm() != cudaSuccess) return DCOPF_ERR_CUDA;
   T.ready = true;
@@ -473,6 +475,8 @@ static cudaError_t prepare_gemm() {
   DCOPF_PAIR_SMEM(3, 192)
   DCOPF_PAIR_SMEM(2, 160)
   DCOPF_PAIR_SMEM(3, 160)
+  DCOPF_PAIR_SMEM(2, 144)
+  DCOPF_PAIR_SMEM(3, 144)
 #undef DCOPF_PAIR_SMEM
   return cudaSuccess;
 }
@@ -520,6 +524,7 @@ struct LineSet {
   const CUtensorMap *phit_hi = nullptr, *phit_lo = nullptr, *phit_hi96 = nullptr, *phit_lo96 = nullptr;
   const CUtensorMap *phi_hi = nullptr, *phi_lo = nullptr, *phi_hi96 = nullptr, *phi_lo96 = nullptr;
   const CUtensorMap *phit_hi80 = nullptr, *phit_lo80 = nullptr, *phi_hi80 = nullptr, *phi_lo80 = nullptr;
+  const CUtensorMap *phit_hi72 = nullptr, *phit_lo72 = nullptr, *phi_hi72 = nullptr, *phi_lo72 = nullptr;
   const float* fmax = nullptr;     // [nl]
   const float* fmin = nullptr;
   const float* f0 = nullptr;       // [B][nl] base flows
@@ -536,19 +541,21 @@ static LineSet full_lines(dcopf_dual* h) {
   L.phit_hi = &T.m_phit_hi; L.phit_lo = &T.m_phit_lo; L.phit_hi96 = &T.m_phit_hi96; L.phit_lo96 = &T.m_phit_lo96;
   L.phi_hi = &T.m_phi_hi; L.phi_lo = &T.m_phi_lo; L.phi_hi96 = &T.m_phi_hi96; L.phi_lo96 = &T.m_phi_lo96;
   L.phit_hi80 = &T.m_phit_hi80; L.phit_lo80 = &T.m_phit_lo80; L.phi_hi80 = &T.m_phi_hi80; L.phi_lo80 = &T.m_phi_lo80;
+  L.phit_hi72 = &T.m_phit_hi72; L.phit_lo72 = &T.m_phit_lo72; L.phi_hi72 = &T.m_phi_hi72; L.phi_lo72 = &T.m_phi_lo72;
   L.fmax = h->dev.fmax32;
   L.fmin = h->dev.fmin32;
   L.f0 = h->ws.f0_32.as<float>();
   return L;
 }
 
-// `tiles`: 0 single CTAs (128 x 128), 1 / 2 / 3 CTA pairs of 256 x 256 / 256 x 192 / 256 x 160.
+// `tiles`: 0 single CTAs (128 x 128), 1 / 2 / 3 / 4 CTA pairs of 256 x 256 / 192 / 160 / 144.
 // Ah / Al: the A operand's rows (the batch's, or one group's of it).
 static cudaError_t launch_adjoint(dcopf_dual* h, const LineSet& L, const CUtensorMap& Ah, const CUtensorMap& Al,
                                   const GemmArgs& g, int splits, int tiles, cudaStream_t s) {
   if (tiles == 1) return launch_gemm_pair<3, 256>(h, Ah, Al, *L.phit_hi, *L.phit_lo, g, splits, s);
   if (tiles == 2) return launch_gemm_pair<3, 192>(h, Ah, Al, *L.phit_hi96, *L.phit_lo96, g, splits, s);
   if (tiles == 3) return launch_gemm_pair<3, 160>(h, Ah, Al, *L.phit_hi80, *L.phit_lo80, g, splits, s);
+  if (tiles == 4) return launch_gemm_pair<3, 144>(h, Ah, Al, *L.phit_hi72, *L.phit_lo72, g, splits, s);
   return launch_gemm<3>(h, Ah, Al, *L.phit_hi, *L.phit_lo, g, splits, s);
 }
 static cudaError_t launch_forward(dcopf_dual* h, const LineSet& L, const CUtensorMap& Ah, const CUtensorMap& Al,
@@ -557,11 +564,13 @@ static cudaError_t launch_forward(dcopf_dual* h, const LineSet& L, const CUtenso
     if (tiles == 1) return launch_gemm_pair<3, 256>(h, Ah, Al, *L.phi_hi, *L.phi_lo, g, 1, s);
     if (tiles == 2) return launch_gemm_pair<3, 192>(h, Ah, Al, *L.phi_hi96, *L.phi_lo96, g, 1, s);
     if (tiles == 3) return launch_gemm_pair<3, 160>(h, Ah, Al, *L.phi_hi80, *L.phi_lo80, g, 1, s);
+    if (tiles == 4) return launch_gemm_pair<3, 144>(h, Ah, Al, *L.phi_hi72, *L.phi_lo72, g, 1, s);
     return launch_gemm<3>(h, Ah, Al, *L.phi_hi, *L.phi_lo, g, 1, s);
   }
   if (tiles == 1) return launch_gemm_pair<2, 256>(h, Ah, Al, *L.phi_hi, *L.phi_lo, g, 1, s);
   if (tiles == 2) return launch_gemm_pair<2, 192>(h, Ah, Al, *L.phi_hi96, *L.phi_lo96, g, 1, s);
   if (tiles == 3) return launch_gemm_pair<2, 160>(h, Ah, Al, *L.phi_hi80, *L.phi_lo80, g, 1, s);
+  if (tiles == 4) return launch_gemm_pair<2, 144>(h, Ah, Al, *L.phi_hi72, *L.phi_lo72, g, 1, s);
   // the LP forward on single CTAs (two products: x is exact in BF16): its K = n_gen is
   // short, so a CTA spends much of its time in the epilogue; two CTAs per SM (a 2-stage
   // ring each) let one CTA's epilogue run beside the other's main loop
@@ -677,6 +686,7 @@ static int minimize_threads(const dcopf_dual* h, int B) {
 // pi~ from the split-K partials, minimiser, BF16 split of x, per-instance cost and
 // dispatch, the pre-outage flow (Phi~ x)_k of an outaged line, the step factors of
 // this step (running powers), and the lambda step (Section 3.3).
+template <int SG>
 __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M, int ldp,
                                               const float* __restrict__ P, const SolveStateBase& st,
                                               const BatchView& bb, const StepArgs& SP, int ldx,
@@ -697,30 +707,32 @@ __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M
   const float kk = (float)(st.iter[b] + 1), wk = kk * kk;  // weight of the mean of the minimisers
   const int nt = blockDim.x;
   // two generators per thread and loop, every load in flight before the arithmetic;
-  // split-K partials summed in split order (a missing term adds +0)
+  // split-K partials summed in split order, SG at a time (a missing term adds +0)
   for (int ja = threadIdx.x; ja < ng; ja += 2 * nt) {
     const int jb = ja + nt;
     const bool vb = jb < ng;
     float sa = 0.f, sb = 0.f;
-    for (int q0 = 0; q0 < splits; q0 += 8) {
-      float ta[8], tb[8];
+    for (int q0 = 0; q0 < splits; q0 += SG) {
+      float ta[SG], tb[SG];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < SG; ++u) {
         const size_t row = ((size_t)(q0 + u) * M + b) * ldp;
         ta[u] = q0 + u < splits ? P[row + ja] : 0.f;
         tb[u] = (q0 + u < splits && vb) ? P[row + jb] : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) { sa += ta[u]; sb += tb[u]; }
+      for (int u = 0; u < SG; ++u) { sa += ta[u]; sb += tb[u]; }
     }
     auto gen = [&](int j, float sj) {
-      const float mq = N.mq32[j];
-      const float w = fmaf(N.sigma32[j], lamf, N.ctil32[j]) + sj;
-      const float x = inner_x<float>(w, mq);
+      const float4 g = N.gen4[j];   // sigma, ctil, mq, cconst
+      const float2 g2 = N.gen2[j];  // mid, 1 / (2 mq) (0 for a linear cost)
+      const float w = fmaf(g.x, lamf, g.y) + sj;
+      // the closed-form minimiser of eq. (6) / (16) on the normalised box [-1, 1]
+      const float x = g.z > 0.f ? fminf(1.f, fmaxf(-1.f, -w * g2.y)) : (w > 0.f ? -1.f : (w < 0.f ? 1.f : 0.f));
       if (st.xsum) st.xsum[(size_t)b * ng + j] += wk * x;
       split_bf16(x, Xh + (size_t)b * ldx + j, Xl + (size_t)b * ldx + j);
-      c += fmaf(fmaf(mq, x, N.ctil32[j]), x, N.cconst32[j]);
-      p += fmaf(N.sigma32[j], x, N.mid32[j]);
+      c += fmaf(fmaf(g.z, x, g.y), x, g.w);
+      p += fmaf(g.x, x, g2.x);
       if (k >= 0) to = fmaf(N.phi32[(size_t)k * ng + j], x, to);
     };
     gen(ja, sa);
@@ -789,7 +801,10 @@ __global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
                   const int* __restrict__ outage, const double* __restrict__ demand) {
   __shared__ double red[3 * (MIN_MAX_THREADS / 32)];
   for (int b = blockIdx.x; b < M; b += gridDim.x) {
-    minimize_item(N, splits, M, ldp, P, st, bb, SP, ldx, Xh, Xl, outage, demand, b, red);
+    if (splits <= 4)
+      minimize_item<4>(N, splits, M, ldp, P, st, bb, SP, ldx, Xh, Xl, outage, demand, b, red);
+    else
+      minimize_item<8>(N, splits, M, ldp, P, st, bb, SP, ldx, Xh, Xl, outage, demand, b, red);
     __syncthreads();  // red is read by warp 0 before the next instance's partials land
   }
 }
@@ -805,7 +820,7 @@ __device__ __forceinline__ void finalize_instance(int b, int lane, int ld_l, int
                                                   const double* __restrict__ demand,
                                                   __nv_bfloat16* __restrict__ Hh,
                                                   __nv_bfloat16* __restrict__ Hl) {
-  const int nt = bb.n_tiles * STEP_WARPS;
+  const int nt = bb.n_tiles;
   double ls = 0.0, os = 0.0;
   for (int q = lane; q < nt; q += 32) {
     ls += bb.line_part[(size_t)b * nt + q];
@@ -833,18 +848,20 @@ __device__ __forceinline__ void finalize_instance(int b, int lane, int ld_l, int
   }
 }
 
-// Stages the frozen candidates: snap[b] = 1 for each (the certificate and the accept
-// step of this round act on exactly those, while the next round's iterations may freeze
-// others), and copies each one's point into rows of dh / dl ([B][len]): its compact row
+// Stages the frozen candidates whose certificate is not already pending (snap_prev,
+// the set of the round before): snap[b] = 1 for each (the certificate and, two rounds
+// later, the accept step act on exactly those, while the next rounds' iterations may
+// freeze others), and copies each one's point into rows of dh / dl ([B][len]): its compact row
 // (pos null, len = nl) or, behind a constraint screen, its full-length row (len = n_line,
 // pos the compact row of each line or -1, zero on the screened lines).  A candidate that
 // reached its target is the point just evaluated (state buffer iter % 3); one stopped by
 // the iteration cap or the tol test is its best point: point iter or iter - 1 (still in
 // their buffers) or an older one (its saved copy).
 __global__ void k_bt_stage(int B, int nl, int len, const int* __restrict__ pos, SolveState<float> st,
-                           BatchView bb, int* snap, float* __restrict__ dh, float* __restrict__ dl) {
+                           BatchView bb, int* snap, const int* __restrict__ snap_prev, float* __restrict__ dh,
+                           float* __restrict__ dl) {
   const int b = blockIdx.y;
-  const bool staged = st.cand[b] && !st.done[b];
+  const bool staged = st.cand[b] && !st.done[b] && !snap_prev[b];
   if (blockIdx.x == 0 && threadIdx.x == 0) snap[b] = staged ? 1 : 0;
   if (!staged) return;
   const int it = st.iter[b];
@@ -864,13 +881,13 @@ __global__ void k_bt_stage(int B, int nl, int len, const int* __restrict__ pos, 
 // After certification: accept, stop, or unfreeze with a larger in-loop margin each
 // staged instance (when `accept`; the evaluation of a frozen point counts, and an
 // unfrozen instance moves on to the point already stepped to); then the number of
-// instances still running into *out_active and the device error word into *out_err.
-// One block.
+// instances still running into *out_active, the device error word into *out_err and
+// the re-screen flag (error word [1]) into *out_flag.  One block.
 constexpr int ACCEPT_THREADS = 512;
 __global__ void __launch_bounds__(ACCEPT_THREADS)
     k_bt_accept(int B, int accept, double ub_any, SolveStateBase st, BatchView bb,
                 const int* __restrict__ snap, const int* __restrict__ err, int* out_active,
-                int* out_err) {
+                int* out_err, int* out_flag) {
   __shared__ int red[ACCEPT_THREADS / 32];
   int running = 0;
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
@@ -901,7 +918,8 @@ __global__ void __launch_bounds__(ACCEPT_THREADS)
     int n = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) n += red[w];
     *out_active = n;
-    *out_err = *err;
+    *out_err = err[0];
+    *out_flag = err[1];
   }
 }
 
@@ -920,7 +938,7 @@ static dcopf_status ensure_batch_bufs(dcopf_dual* h, int B, int n_tiles) {
   BatchView& v = bb.v;
   const size_t nl = h->host.n_line;
   if (bb.mu2.alloc((size_t)B * nl * 6 * sizeof(float)) ||
-      bb.parts.alloc((size_t)B * n_tiles * STEP_WARPS * 2 * sizeof(double)) ||
+      bb.parts.alloc((size_t)B * n_tiles * 2 * sizeof(double)) ||
       bb.small.alloc((size_t)B * 7 * sizeof(double) + (size_t)B * 7 * sizeof(float) + 1024)) {
     cudaGetLastError();
     return DCOPF_ERR_OOM;
@@ -932,7 +950,7 @@ static dcopf_status ensure_batch_bufs(dcopf_dual* h, int B, int n_tiles) {
   v.sv_hi = v.mu2_hi + 4 * (size_t)B * nl;
   v.sv_lo = v.mu2_hi + 5 * (size_t)B * nl;
   v.line_part = bb.parts.as<double>();
-  v.out_part = v.line_part + (size_t)B * n_tiles * STEP_WARPS;
+  v.out_part = v.line_part + (size_t)B * n_tiles;
   double* d = bb.small.as<double>();
   v.lam_eval = d; v.cost = d + B; v.psum = d + 2 * (size_t)B; v.pw = d + 3 * (size_t)B;  // pw: [B][3]
   v.lam_best = d + 6 * (size_t)B;
@@ -965,6 +983,12 @@ constexpr int MAX_BRANCHES = 2;
 // Product shapes of the batched iteration, as launch_adjoint's `tiles`.
 struct TensorShapes {
   int adj = 0, splits = 1, kbps = 1, fwd = 0;
+};
+// The tuner's two fastest adjoint shapes and forward tiles, each timed on its own.
+struct ShapeChoices {
+  TensorShapes best;
+  int adj2 = -1, splits2 = 1, kbps2 = 1;  // the second adjoint (adj2 < 0: none)
+  int fwd2 = -1;                          // the second forward (< 0: none)
 };
 
 // One network's share of a batched tensor-core solve: the instances, the kernel
@@ -1019,7 +1043,7 @@ static bool make_view(TensorRun& R, int b0, int Bg, IterView* V) {
   adv(bb.frozen, o); adv(bb.lam_eval, o); adv(bb.cost, o); adv(bb.psum, o); adv(bb.pw, 3 * o);
   adv(bb.tout, o); adv(bb.stepf, 4 * o); adv(bb.lam_best, o); adv(bb.step_done, o);
   for (float** q : {&bb.mu2_hi, &bb.mu2_lo, &bb.mu3_hi, &bb.mu3_lo, &bb.sv_hi, &bb.sv_lo}) adv(*q, o * nl);
-  adv(bb.line_part, o * nt * STEP_WARPS); adv(bb.out_part, o * nt * STEP_WARPS);
+  adv(bb.line_part, o * nt); adv(bb.out_part, o * nt);
   W.ga = R.ga;
   W.ga.M = Bg;
   W.ga.P = R.ga.P + (size_t)64 * o * R.ga.ldp;  // the partials' [64][B][ldp] share of the group
@@ -1107,8 +1131,8 @@ static bool enqueue_iters(TensorRun& R, IterView& V, int n, cudaStream_t cs, boo
     ev(2);
     ok &= launch_forward(h, R.ls, V.Xh, V.Xl, V.gf, R.pair_fwd, cs) == cudaSuccess;
     ev(3);
-    const int items = R.n_tiles * V.B;
-    const int sb = R.step_blocks ? std::min(items, R.step_blocks) : items;
+    const int blocks = (R.n_tiles * V.B + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32);
+    const int sb = R.step_blocks ? std::min(blocks, R.step_blocks) : blocks;
     if (nl % 4 == 0 && V.E.ldF % 4 == 0 && V.E.ldh % 4 == 0)
       k_bt_step4<<<sb, STEP_THREADS, 0, cs>>>(V.E, nl);
     else
@@ -1174,7 +1198,7 @@ static void tensor_init_state(TensorRun& R, cudaStream_t cs) {
 //    minimiser's reduction, so each candidate is timed as adjoint + minimiser;
 //  - the forward product: single CTAs or CTA pairs.
 // Timed with CUDA events on the solve's stream; the fastest of each goes to *out.
-static dcopf_status tune_view_shapes(TensorRun& R, IterView& V, cudaStream_t cs, TensorShapes* out) {
+static dcopf_status tune_view_shapes(TensorRun& R, IterView& V, cudaStream_t cs, ShapeChoices* out) {
   dcopf_dual* h = R.it.h;
   const int B = V.B, ng = h->host.n_gen;
   TensorOps& T = h->tops;
@@ -1182,7 +1206,7 @@ static dcopf_status tune_view_shapes(TensorRun& R, IterView& V, cudaStream_t cs,
   const bool pair_ok = B > GBM && h->tiles_mode != 1;
   const bool single_ok = h->tiles_mode <= 1 || B <= GBM;
   // pair widths tried: tiles codes tv_lo .. tv_hi (all three unless DCOPF_TENSOR_TILES fixes one)
-  const int tv_lo = h->tiles_mode >= 2 ? h->tiles_mode - 1 : 1, tv_hi = h->tiles_mode >= 2 ? h->tiles_mode - 1 : 3;
+  const int tv_lo = h->tiles_mode >= 2 ? h->tiles_mode - 1 : 1, tv_hi = h->tiles_mode >= 2 ? h->tiles_mode - 1 : 4;
   struct Cand { int tiles; int splits; };  // tiles as launch_adjoint's
   std::vector<Cand> cand;
   auto add = [&](int tiles, int sp) {
@@ -1204,7 +1228,7 @@ static dcopf_status tune_view_shapes(TensorRun& R, IterView& V, cudaStream_t cs,
   }
   if (pair_ok) {
     for (int tv = tv_lo; tv <= tv_hi; ++tv) {
-      const int bn = tv == 1 ? 256 : tv == 2 ? 192 : 160;
+      const int bn = tv == 1 ? 256 : tv == 2 ? 192 : tv == 3 ? 160 : 144;
       const int ptiles = ((B + PBM - 1) / PBM) * ((ng + bn - 1) / bn);
       const int slots = h->sm_count / 2;  // one pair per two SMs
       const int s0 = std::max(1, (slots + ptiles - 1) / ptiles);
@@ -1218,20 +1242,24 @@ static dcopf_status tune_view_shapes(TensorRun& R, IterView& V, cudaStream_t cs,
     return DCOPF_ERR_CUDA;
   }
   auto timed = [&](auto&& body, float* ms) -> dcopf_status {
-    for (int rep = 0; rep < 2; ++rep) {  // the first pass warms up
+    *ms = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {  // the first pass warms up; the fastest of the others
+      float t = 0.f;
       if (cudaEventRecord(e0, cs) != cudaSuccess) return DCOPF_ERR_CUDA;
       for (int k = 0; k < 3; ++k)
         if (body() != cudaSuccess) return DCOPF_ERR_CUDA;
       if (cudaEventRecord(e1, cs) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-          cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+          cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
         return DCOPF_ERR_CUDA;
+      if (rep > 0) *ms = std::min(*ms, t);
     }
     return DCOPF_OK;
   };
-  static const char* kTiles[4] = {"single 128x128", "pairs 256x256", "pairs 256x192", "pairs 256x160"};
-  float best = 1e30f;
-  Cand bc = cand.empty() ? Cand{0, 1} : cand[0];
-  int best_per = (kb + bc.splits - 1) / bc.splits;
+  static const char* kTiles[5] = {"single 128x128", "pairs 256x256", "pairs 256x192", "pairs 256x160",
+                                  "pairs 256x144"};
+  float best = 1e30f, second = 1e30f;
+  Cand bc = cand.empty() ? Cand{0, 1} : cand[0], bc2{-1, 1};
+  int best_per = (kb + bc.splits - 1) / bc.splits, per2 = 1;
   dcopf_status res = DCOPF_OK;
   for (const Cand& c : cand) {
     GemmArgs g = V.ga;
@@ -1251,23 +1279,36 @@ static dcopf_status tune_view_shapes(TensorRun& R, IterView& V, cudaStream_t cs,
       fprintf(stderr, "dcopf: batch %d adjoint %s split-K %d: %.1f us per GEMM+min\n", B,
               kTiles[c.tiles], c.splits, 1e3f * ms / 3.f);
     if (ms < best) {
+      second = best;
+      bc2 = bc;
+      per2 = best_per;
       best = ms;
       bc = c;
       best_per = g.kb_per_split;
+    } else if (ms < second) {
+      second = ms;
+      bc2 = c;
+      per2 = g.kb_per_split;
     }
   }
+  if (second >= 1e30f) bc2.tiles = -1;
   // the forward product, on the operands the runs above left
-  int fwd = (pair_ok && !single_ok) ? tv_lo : 0;
+  int fwd = (pair_ok && !single_ok) ? tv_lo : 0, fwd2 = -1;
   if (res == DCOPF_OK && pair_ok) {
-    float bf = 1e30f;
+    float bf = 1e30f, bf2 = 1e30f;
     for (int tv = single_ok ? 0 : tv_lo; tv <= tv_hi && res == DCOPF_OK; ++tv) {
       if (tv > 0 && tv < tv_lo) continue;
       float ms = 0.f;
       res = timed([&] { return launch_forward(h, R.ls, V.Xh, V.Xl, V.gf, tv, cs); }, &ms);
       if (h->verbose) fprintf(stderr, "dcopf: batch %d forward %s: %.1f us\n", B, kTiles[tv], 1e3f * ms / 3.f);
       if (res == DCOPF_OK && ms < bf) {
+        bf2 = bf;
+        fwd2 = bf < 1e30f ? fwd : -1;
         bf = ms;
         fwd = tv;
+      } else if (res == DCOPF_OK && ms < bf2) {
+        bf2 = ms;
+        fwd2 = tv;
       }
     }
   }
@@ -1278,17 +1319,20 @@ static dcopf_status tune_view_shapes(TensorRun& R, IterView& V, cudaStream_t cs,
   if (cudaMemcpy(&derr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return DCOPF_ERR_CUDA;
   if (derr) return (dcopf_status)derr;
-  out->adj = bc.tiles;
-  out->splits = bc.splits;
-  out->kbps = best_per;
-  out->fwd = fwd;
+  out->best = TensorShapes{bc.tiles, bc.splits, best_per, fwd};
+  out->adj2 = bc2.tiles;
+  out->splits2 = bc2.splits;
+  out->kbps2 = per2;
+  out->fwd2 = fwd2;
   if (h->verbose)
     fprintf(stderr, "dcopf: batch %d adjoint %s split-K %d (%.1f us per GEMM+min), forward %s\n", B,
             kTiles[bc.tiles], bc.splits, 1e3f * best / 3.f, kTiles[fwd]);
   return DCOPF_OK;
 }
 
-// Milliseconds of 6 whole iterations of every group of R (after 6 that warm up).
+// Milliseconds of 6 whole iterations of every group of R: the fastest of three runs
+// after one that warms up, each from the initial state (so that no instance has stopped
+// and had its work skipped).
 static dcopf_status time_iterations(TensorRun& R, cudaStream_t cs, float* ms) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -1296,13 +1340,17 @@ static dcopf_status time_iterations(TensorRun& R, cudaStream_t cs, float* ms) {
     return DCOPF_ERR_CUDA;
   }
   dcopf_status res = DCOPF_OK;
-  for (int rep = 0; rep < 2 && res == DCOPF_OK; ++rep) {
+  *ms = 1e30f;
+  for (int rep = 0; rep < 4 && res == DCOPF_OK; ++rep) {
+    float t = 0.f;
+    tensor_init_state(R, cs);
     if (cudaEventRecord(e0, cs) != cudaSuccess || !tensor_enqueue_chunk(R, 6, cs) ||
         cudaEventRecord(e1, cs) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+        cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
       res = DCOPF_ERR_CUDA;
+    if (rep > 0) *ms = std::min(*ms, t);
   }
-  R.it.h->launches += 2LL * 6 * 2 * R.nv;  // the products count themselves
+  R.it.h->launches += 4LL * 6 * 2 * R.nv;  // the products count themselves
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return res;
@@ -1315,15 +1363,33 @@ static dcopf_status tune_tensor(TensorRun& R, cudaStream_t cs) {
   dcopf_dual* h = R.it.h;
   const int B = R.it.B;
   dcopf_status r;
-  TensorShapes s1, s2;
-  if ((r = make_views(R, 1)) || (r = tune_view_shapes(R, R.v[0], cs, &s1))) return r;
+  ShapeChoices c1, c2;
+  if ((r = make_views(R, 1)) || (r = tune_view_shapes(R, R.v[0], cs, &c1))) return r;
   int nv = 1;
-  TensorShapes best = s1;
+  // the two fastest of each product, each timed on its own, combined and timed as whole
+  // iterations: a product's time beside the others' differs from its own
+  std::vector<TensorShapes> combos{c1.best};
+  if (c1.adj2 >= 0) combos.push_back(TensorShapes{c1.adj2, c1.splits2, c1.kbps2, c1.best.fwd});
+  if (c1.fwd2 >= 0) combos.push_back(TensorShapes{c1.best.adj, c1.best.splits, c1.best.kbps, c1.fwd2});
+  if (c1.adj2 >= 0 && c1.fwd2 >= 0) combos.push_back(TensorShapes{c1.adj2, c1.splits2, c1.kbps2, c1.fwd2});
+  TensorShapes best = c1.best;
+  float t1 = 1e30f;
+  for (const TensorShapes& c : combos) {
+    float t = 0.f;
+    apply_shapes(R, c);
+    if ((r = time_iterations(R, cs, &t))) return r;
+    if (h->verbose)
+      fprintf(stderr, "dcopf: batch %d shapes %d,%d,%d: %.1f us per iteration\n", B, c.adj, c.splits, c.fwd,
+              1e3f * t / 6.f);
+    if (t < t1) {
+      t1 = t;
+      best = c;
+    }
+  }
   if (B >= 2 * GBM) {
-    float t1 = 0.f, t2 = 0.f;
-    apply_shapes(R, s1);
-    if ((r = time_iterations(R, cs, &t1))) return r;
-    if ((r = make_views(R, 2)) || (r = tune_view_shapes(R, R.v[0], cs, &s2))) return r;
+    float t2 = 0.f;
+    if ((r = make_views(R, 2)) || (r = tune_view_shapes(R, R.v[0], cs, &c2))) return r;
+    const TensorShapes s2 = c2.best;
     apply_shapes(R, s2);
     if ((r = time_iterations(R, cs, &t2))) return r;
     if (h->verbose)
@@ -1383,6 +1449,7 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
     L.phit_hi = &S.m_phit_hi; L.phit_lo = &S.m_phit_lo; L.phit_hi96 = &S.m_phit_hi96; L.phit_lo96 = &S.m_phit_lo96;
     L.phi_hi = &S.m_phi_hi; L.phi_lo = &S.m_phi_lo; L.phi_hi96 = &S.m_phi_hi96; L.phi_lo96 = &S.m_phi_lo96;
     L.phit_hi80 = &S.m_phit_hi80; L.phit_lo80 = &S.m_phit_lo80; L.phi_hi80 = &S.m_phi_hi80; L.phi_lo80 = &S.m_phi_lo80;
+    L.phit_hi72 = &S.m_phit_hi72; L.phit_lo72 = &S.m_phit_lo72; L.phi_hi72 = &S.m_phi_hi72; L.phi_lo72 = &S.m_phi_lo72;
     L.fmax = S.lim.as<float>();
     L.fmin = S.lim.as<float>() + nk;
     L.f0 = S.f0c.as<float>();
@@ -1390,7 +1457,7 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
     L.pos = S.pos.as<int>();
   }
   const int nl = R.ls.nl;
-  R.n_tiles = (nl + STEP_CHUNK - 1) / STEP_CHUNK;
+  R.n_tiles = (nl + STEP_SLICE - 1) / STEP_SLICE;
   if ((r = ensure_batch_bufs(h, B, R.n_tiles))) return r;
   const int ldF = (nl + 3) & ~3;
   if (h->bb.F.alloc((size_t)B * ldF * sizeof(float)) != cudaSuccess) return DCOPF_ERR_OOM;
@@ -1466,16 +1533,18 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   return DCOPF_OK;
 }
 
-// After a chunk: stage and snapshot the frozen candidates (on the solve's stream cs),
-// then certify them in FP64 on the certificate stream cc, which runs beside the next
-// chunk of iterations (the staged instances stay frozen meanwhile).  `done_ev` is
-// recorded on cc when the certificate has finished.
-static dcopf_status tensor_stage_certify(TensorRun& R, cudaStream_t cs, cudaStream_t cc,
+// After round `round`'s chunk: stage and snapshot the frozen candidates (on the solve's
+// stream cs) into the snapshot of the round's parity, then certify them in FP64 on the
+// certificate stream cc, which runs beside the next two chunks of iterations (the staged
+// instances stay frozen meanwhile; round + 2 accepts them).  `done_ev` is recorded on cc
+// when the certificate has finished.
+static dcopf_status tensor_stage_certify(TensorRun& R, int round, cudaStream_t cs, cudaStream_t cc,
                                          cudaEvent_t staged_ev, cudaEvent_t done_ev) {
   dcopf_dual* h = R.it.h;
   const int B = R.it.B, nl = R.ls.nl, n_line = h->host.n_line;
   BatchView& bb = h->bb.v;
-  int* snap = h->bb.snap.as<int>();
+  int* snap = h->bb.snap.as<int>() + (size_t)(round & 1) * B;
+  const int* snap_prev = h->bb.snap.as<int>() + (size_t)((round + 1) & 1) * B;
   // the certificate evaluates the full problem: behind a screen, the staged points on
   // every line, zero on the screened ones
   float* bh = R.st.best_hi;
@@ -1487,7 +1556,7 @@ static dcopf_status tensor_stage_certify(TensorRun& R, cudaStream_t cs, cudaStre
     len = n_line;
   }
   k_bt_stage<<<dim3((len + 1023) / 1024, B), 256, 0, cs>>>(B, nl, len, R.ls.kept ? R.ls.pos : nullptr, R.st, bb,
-                                                          snap, bh, bl);
+                                                          snap, snap_prev, bh, bl);
   h->launches += 1;
   if (cudaEventRecord(staged_ev, cs) != cudaSuccess || cudaStreamWaitEvent(cc, staged_ev, 0) != cudaSuccess)
     return DCOPF_ERR_CUDA;
@@ -1499,15 +1568,17 @@ static dcopf_status tensor_stage_certify(TensorRun& R, cudaStream_t cs, cudaStre
   return cudaGetLastError() == cudaSuccess ? DCOPF_OK : DCOPF_ERR_CUDA;
 }
 
-// Once the certificate of the staged instances is in (done_ev): accept, stop or resume
-// each of them (when `accept`), on cs; the count of instances still running and the
-// device error word go to *out_active and *out_err (device memory).
-static dcopf_status tensor_accept(TensorRun& R, bool accept, int* out_active, int* out_err, cudaStream_t cs,
-                                  cudaEvent_t done_ev) {
+// Once the certificate of the instances staged in round `staged` is in (done_ev): accept,
+// stop or resume each of them (when `accept`), on cs; the count of instances still
+// running, the device error word and the re-screen flag go to *out_active, *out_err,
+// *out_flag (device memory).
+static dcopf_status tensor_accept(TensorRun& R, bool accept, int staged, int* out_active, int* out_err,
+                                  int* out_flag, cudaStream_t cs, cudaEvent_t done_ev) {
   dcopf_dual* h = R.it.h;
   if (accept && cudaStreamWaitEvent(cs, done_ev, 0) != cudaSuccess) return DCOPF_ERR_CUDA;
-  k_bt_accept<<<1, ACCEPT_THREADS, 0, cs>>>(R.it.B, accept ? 1 : 0, h->ub_any, R.st, h->bb.v,
-                                           h->bb.snap.as<int>(), h->d_err, out_active, out_err);
+  const int* snap = h->bb.snap.as<int>() + (size_t)(staged & 1) * R.it.B;
+  k_bt_accept<<<1, ACCEPT_THREADS, 0, cs>>>(R.it.B, accept ? 1 : 0, h->ub_any, R.st, h->bb.v, snap, h->d_err,
+                                           out_active, out_err, out_flag);
   h->launches += 1;
   return cudaGetLastError() == cudaSuccess ? DCOPF_OK : DCOPF_ERR_CUDA;
 }
@@ -1565,7 +1636,8 @@ static std::vector<unsigned char> graph_signature(const std::vector<TensorRun>& 
     put(ints, sizeof ints);
     for (const CUtensorMap* m : {R.ls.phit_hi, R.ls.phit_lo, R.ls.phit_hi96, R.ls.phit_lo96, R.ls.phit_hi80,
                                  R.ls.phit_lo80, R.ls.phi_hi, R.ls.phi_lo, R.ls.phi_hi96, R.ls.phi_lo96,
-                                 R.ls.phi_hi80, R.ls.phi_lo80})
+                                 R.ls.phi_hi80, R.ls.phi_lo80, R.ls.phit_hi72, R.ls.phit_lo72, R.ls.phi_hi72,
+                                 R.ls.phi_lo72})
       if (m) put(m, sizeof(CUtensorMap));
   }
   return sig;
@@ -1574,8 +1646,8 @@ static std::vector<unsigned char> graph_signature(const std::vector<TensorRun>& 
 // Batched solves of several networks (distinct handles on one device) that advance
 // together: each round is ONE launch of a CUDA graph holding every network's chunk
 // of iterations as parallel branches, followed by each network's FP64 certification.
-dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solve_params& p,
-                                cudaStream_t s) {
+static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, const dcopf_solve_params& p,
+                                           cudaStream_t s) {
   const auto t_start = std::chrono::steady_clock::now();
   auto host_ms = [t_start] {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
@@ -1597,7 +1669,7 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
     K.release();
     K.ev.assign(2 * n + 1, nullptr);
     K.stage_ev.assign(n, nullptr);
-    K.cert_ev.assign(n, nullptr);
+    K.cert_ev.assign(2 * n, nullptr);  // per network and round parity
     for (auto* v : {&K.ev, &K.stage_ev, &K.cert_ev})
       for (cudaEvent_t& e : *v)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return DCOPF_ERR_CUDA;
@@ -1607,8 +1679,8 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
           cudaEventCreate(&K.t0[q]) != cudaSuccess || cudaEventCreate(&K.t1[q]) != cudaSuccess)
         return DCOPF_ERR_CUDA;
     if (cudaStreamCreateWithFlags(&K.rs, cudaStreamNonBlocking) != cudaSuccess) return DCOPF_ERR_CUDA;
-    if (cudaMallocHost(&K.pin, 4 * sizeof(int) * (size_t)n) != cudaSuccess ||
-        cudaMalloc(&K.rb_dev, 4 * sizeof(int) * (size_t)n) != cudaSuccess) {
+    if (cudaMallocHost(&K.pin, 6 * sizeof(int) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&K.rb_dev, 6 * sizeof(int) * (size_t)n) != cudaSuccess) {
       cudaGetLastError();
       K.release();
       return DCOPF_ERR_OOM;
@@ -1680,16 +1752,25 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
   // iterations (the candidates stay frozen meanwhile); round r + 1 then accepts them.
   for (int i = 0; i < n; ++i) {
     dcopf_dual* hi = items[i].h;
-    if (!hi->cstream && cudaStreamCreateWithFlags(&hi->cstream, cudaStreamNonBlocking) != cudaSuccess)
+    // the certificates at the highest stream priority: their CTAs take SMs as the
+    // iterations' blocks retire, so that they are in when the next round accepts them
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if (!hi->cstream &&
+        cudaStreamCreateWithPriority(&hi->cstream, cudaStreamNonBlocking, hi_prio) != cudaSuccess)
       return DCOPF_ERR_CUDA;
-    if (hi->bb.snap.alloc(sizeof(int) * (size_t)items[i].B) != cudaSuccess) return DCOPF_ERR_OOM;
+    if (hi->bb.snap.alloc(2 * sizeof(int) * (size_t)items[i].B) != cudaSuccess ||
+        cudaMemsetAsync(hi->bb.snap.p, 0, 2 * sizeof(int) * (size_t)items[i].B, hi->tstream) != cudaSuccess)
+      return DCOPF_ERR_OOM;
   }
-  // Rounds are pipelined: the host enqueues round r (its graph, the accept of round
-  // r - 1's certificates, the staging and certificate of round r's candidates, the
-  // read-back of the running counts and device error words) and only then waits for
+  // Rounds are pipelined: the host enqueues round r (its graph, the accept of the
+  // certificates of round r - 2's candidates, the staging and certificate of round r's,
+  // the read-back of the running counts and device error words) and only then waits for
   // round r - 1's read-back, so that the GPU does not idle while the host turns a round
-  // around.  A batch whose last instance stopped in round r - 2's certificate thus also
-  // runs rounds r - 1 and r, whose iterations skip every (frozen) instance.
+  // around.  A certificate has two rounds of iterations to run beside (it competes with
+  // them for SMs), so that its accept does not wait for it.  A batch whose last instance
+  // was accepted in round r - 1 thus also runs round r, whose iterations skip every
+  // (frozen) instance.
   std::vector<int> act(n, 1);
   int rounds = 0;
   for (int round = 0;; ++round) {
@@ -1701,11 +1782,13 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
         return DCOPF_ERR_CUDA;
     }
     if (verbose) {
-      cudaEvent_t a = nullptr, b = nullptr;
+      cudaEvent_t a = nullptr, b = nullptr, c = nullptr;
       cudaEventCreate(&a);
       cudaEventCreate(&b);
+      cudaEventCreate(&c);
       G.vev.push_back(a);
       G.vev.push_back(b);
+      G.vev.push_back(c);
       cudaEventRecord(a, cs0);
     }
     if (h0->timing) cudaEventRecord(K.t0[sl], cs0);
@@ -1716,8 +1799,8 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
       round_launches += 4LL * chunk * runs[i].nv;
     }
     if (h0->timing) cudaEventRecord(K.t1[sl], cs0);
-    if (verbose) cudaEventRecord(G.vev.back(), cs0);
-    int* slot = K.rb_dev + (size_t)sl * 2 * n;
+    if (verbose) cudaEventRecord(G.vev[G.vev.size() - 2], cs0);
+    int* slot = K.rb_dev + (size_t)sl * 3 * n;
     if (cudaEventRecord(K.ev[2 * n], cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
     for (int i = 0; i < n; ++i) {
       cudaStream_t si = items[i].h->tstream;
@@ -1725,9 +1808,13 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
       // every network reports its count and error word; a network still running accepts
       // the certificates of the last round and stages this round's candidates
       dcopf_status r;
-      if ((r = tensor_accept(runs[i], round > 0 && act[i], slot + i, slot + n + i, si, K.cert_ev[i]))) return r;
+      if ((r = tensor_accept(runs[i], round > 1 && act[i], round - 2, slot + i, slot + n + i, slot + 2 * n + i, si,
+                             K.cert_ev[2 * i + (round & 1)])))
+        return r;
+      if (verbose && i == 0) cudaEventRecord(G.vev.back(), cs0);
       if (act[i] &&
-          (r = tensor_stage_certify(runs[i], si, items[i].h->cstream, K.stage_ev[i], K.cert_ev[i])))
+          (r = tensor_stage_certify(runs[i], round, si, items[i].h->cstream, K.stage_ev[i],
+                                    K.cert_ev[2 * i + (round & 1)])))
         return r;
     }
     for (int i = 1; i < n; ++i)
@@ -1736,7 +1823,7 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
         return DCOPF_ERR_CUDA;
     // the read-back of this round's counts, on its own stream
     if (cudaEventRecord(K.acc[sl], cs0) != cudaSuccess || cudaStreamWaitEvent(K.rs, K.acc[sl], 0) != cudaSuccess ||
-        cudaMemcpyAsync(K.pin + (size_t)sl * 2 * n, slot, 2 * sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost,
+        cudaMemcpyAsync(K.pin + (size_t)sl * 3 * n, slot, 3 * sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost,
                         K.rs) != cudaSuccess ||
         cudaEventRecord(K.done[sl], K.rs) != cudaSuccess)
       return DCOPF_ERR_CUDA;
@@ -1750,9 +1837,25 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
     const double tw = verbose ? host_ms() : 0.0;
     if (cudaEventSynchronize(K.done[pv_sl]) != cudaSuccess) return DCOPF_ERR_CUDA;
     if (verbose) t_wait += host_ms() - tw;
-    const int* pv = K.pin + (size_t)pv_sl * 2 * n;
+    const int* pv = K.pin + (size_t)pv_sl * 3 * n;
     for (int i = 0; i < n; ++i)
       if (pv[n + i]) return (dcopf_status)pv[n + i];
+    bool rescreen = false;
+    for (int i = 0; i < n; ++i)
+      if (pv[2 * n + i]) {  // this batch needs a line the network's kept set screens out
+        items[i].h->scr.exact = true;
+        rescreen = true;
+      }
+    if (rescreen) {
+      for (int i = 0; i < n; ++i)
+        if (cudaStreamSynchronize(items[i].h->tstream) != cudaSuccess ||
+            (items[i].h->tstream2 && cudaStreamSynchronize(items[i].h->tstream2) != cudaSuccess) ||
+            (items[i].h->cstream && cudaStreamSynchronize(items[i].h->cstream) != cudaSuccess) ||
+            cudaMemset(items[i].h->d_err + 1, 0, sizeof(int)) != cudaSuccess)
+          return DCOPF_ERR_CUDA;
+      if (cudaStreamSynchronize(K.rs) != cudaSuccess) return DCOPF_ERR_CUDA;
+      return kRescreen;
+    }
     if (h0->timing) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, K.t0[pv_sl], K.t1[pv_sl]);
@@ -1787,31 +1890,43 @@ dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solv
     h0->t_iter_ms += ms;
   }
   if (verbose) {
-    double graphs = 0.0, gaps = 0.0;
-    for (size_t q = 0; q + 1 < G.vev.size(); q += 2) {
-      float a = 0.f, b = 0.f;
+    double graphs = 0.0, gaps = 0.0, accepts = 0.0;
+    for (size_t q = 0; q + 2 < G.vev.size(); q += 3) {
+      float a = 0.f, b = 0.f, c = 0.f;
       cudaEventElapsedTime(&a, G.vev[q], G.vev[q + 1]);
       graphs += a;
-      if (q + 2 < G.vev.size() && cudaEventElapsedTime(&b, G.vev[q + 1], G.vev[q + 2]) == cudaSuccess) gaps += b;
+      if (cudaEventElapsedTime(&c, G.vev[q + 1], G.vev[q + 2]) == cudaSuccess) accepts += c;
+      if (q + 3 < G.vev.size() && cudaEventElapsedTime(&b, G.vev[q + 1], G.vev[q + 3]) == cudaSuccess) gaps += b;
     }
     fprintf(stderr,
             "dcopf: group solve: setup %.2f ms, graph %s %.2f ms (host), %d rounds: graphs %.2f ms, "
-            "between graphs %.2f ms (GPU), host waits %.2f ms, loop %.2f ms (host)\n",
-            t_setup, reuse ? "reused" : "captured", t_captured - t_setup, rounds, graphs, gaps, t_wait,
+            "between graphs %.2f ms (of which accepts, with their wait for the certificates, %.2f ms; "
+            "GPU), host waits %.2f ms, loop %.2f ms (host)\n",
+            t_setup, reuse ? "reused" : "captured", t_captured - t_setup, rounds, graphs, gaps, accepts, t_wait,
             host_ms() - t_captured);
   }
-  // the last round's certificates: accept what they staged (nothing, when every
-  // instance had stopped before that round)
-  for (int i = 0; i < n; ++i) {
-    int* slot = K.rb_dev + (size_t)(rounds & 1) * 2 * n;  // free: everything queued has run
-    dcopf_status r = tensor_accept(runs[i], true, slot + i, slot + n + i, items[i].h->tstream, K.cert_ev[i]);
-    if (r) return r;
-  }
+  // the last two rounds' certificates: accept what they staged (nothing, when every
+  // instance had stopped before those rounds)
+  for (int i = 0; i < n; ++i)
+    for (int q = std::max(0, rounds - 2); q < rounds; ++q) {
+      int* slot = K.rb_dev;  // free: everything queued has run
+      dcopf_status r = tensor_accept(runs[i], true, q, slot + i, slot + n + i, slot + 2 * n + i, items[i].h->tstream,
+                                     K.cert_ev[2 * i + (q & 1)]);
+      if (r) return r;
+    }
   for (int i = 0; i < n; ++i) {
     dcopf_status r = tensor_finish(runs[i], s);
     if (r) return r;
   }
   return DCOPF_OK;
+}
+
+dcopf_status solve_tensor_group(const TensorItem* items, int n, const dcopf_solve_params& p,
+                                cudaStream_t s) {
+  dcopf_status r = solve_tensor_group_once(items, n, p, s);
+  // a screen that went ahead with a kept set this batch outgrew: again, with the batch's own
+  if (r == kRescreen) r = solve_tensor_group_once(items, n, p, s);
+  return r == kRescreen ? DCOPF_ERR_CUDA : r;
 }
 
 template <typename S>

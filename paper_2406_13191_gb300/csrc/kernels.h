@@ -152,6 +152,7 @@ struct TensorOps {
   CUtensorMap m_phi_hi, m_phi_lo, m_phit_hi, m_phit_lo;        // 128-row boxes
   CUtensorMap m_phi_hi96, m_phi_lo96, m_phit_hi96, m_phit_lo96;  // 96-row boxes (pair tiles of 192)
   CUtensorMap m_phi_hi80, m_phi_lo80, m_phit_hi80, m_phit_lo80;  // 80-row boxes (pair tiles of 160)
+  CUtensorMap m_phi_hi72, m_phi_lo72, m_phit_hi72, m_phit_lo72;  // 72-row boxes (pair tiles of 144)
   DBuf H_hi, H_lo, X_hi, X_lo, P;
   CUtensorMap m_H_hi, m_H_lo, m_X_hi, m_X_lo;
 };
@@ -161,9 +162,13 @@ struct TensorOps {
 // range of the balance right-hand side.
 struct LineScreen {
   DBuf env, knap, keep;          // batch envelope [2][n_line] + range [2]; bounds [2][n_line]; flags
-  bool knap_valid = false;
-  double rlo = 0.0, rhi = 0.0;   // balance range the knapsack bounds hold for
+  DBuf rng;                      // balance range the knapsack bounds hold for [2], valid flag
+  DBuf flags;                    // [0]: the knapsack bounds are taken again for this batch
   bool ready = false;            // the compact operands below match kept_host
+  // the next screen builds the batch's own kept set (synchronously) rather than going
+  // ahead with the current one: set after a solve found that its batch needs a line the
+  // current set screens out
+  bool exact = false;
   int nk = 0, ld_lk = 0;         // kept lines (a multiple of 8) and their row stride
   std::vector<int> kept_host;
   DBuf kept, pos;                // [nk] line of each compact row; [n_line] compact row or -1
@@ -171,6 +176,7 @@ struct LineScreen {
   CUtensorMap m_phi_hi, m_phi_lo, m_phit_hi, m_phit_lo;
   CUtensorMap m_phi_hi96, m_phi_lo96, m_phit_hi96, m_phit_lo96;
   CUtensorMap m_phi_hi80, m_phi_lo80, m_phit_hi80, m_phit_lo80;
+  CUtensorMap m_phi_hi72, m_phi_lo72, m_phit_hi72, m_phit_lo72;
   int map_B = 0;                 // batch size of the maps below
   CUtensorMap m_H_hi, m_H_lo;    // the adjoint's A operand [B][ld_lk]
   DBuf f0c, full;                // compact base flows [B][nk]; full-length best point [2][B][n_line]
@@ -178,7 +184,7 @@ struct LineScreen {
 
 // Extra per-instance state of the batched tensor-core solve (device pointers).
 struct BatchView {
-  int n_tiles = 0;             // line tiles of the forward product
+  int n_tiles = 0;             // slices of lines of the step kernel
   int* frozen = nullptr;       // [B] done or waiting for certification
   int* step_done = nullptr;    // [B] blocks of the step kernel finished with the instance
   double* lam_eval = nullptr;  // [B] lambda of the evaluated point
@@ -194,8 +200,8 @@ struct BatchView {
   float* sv_hi = nullptr;      // [B][nl] the best point, saved when its buffer is reused
   float* sv_lo = nullptr;
   double* lam_best = nullptr;  // [B] lambda of the best point
-  double* line_part = nullptr; // [B][n_tiles x 8] per warp of the step kernel's chunks
-  double* out_part = nullptr;  // [B][n_tiles x 8]
+  double* line_part = nullptr; // [B][n_tiles] per slice of lines of the step kernel
+  double* out_part = nullptr;  // [B][n_tiles]
 };
 
 // Objects a batched solve reuses from call to call (kept by the first network's handle):
@@ -204,7 +210,8 @@ struct BatchView {
 struct RoundKit {
   int n = 0;  // networks the events and the read-back are made for
   std::vector<cudaEvent_t> ev, stage_ev, cert_ev;
-  // per round parity [2][2n]: each network's running count and device error word,
+  // per round parity [2][3n]: each network's running count, device error word and
+  // re-screen flag,
   // written by its accept kernel on the device and copied to pinned host memory on the
   // read-back stream, off the iterations' critical path
   int* rb_dev = nullptr;
@@ -335,16 +342,16 @@ struct dcopf_dual {
   // whether the adjoint and the forward product run on CTA pairs (256 x 256 tiles)
   // rather than single CTAs (128 x 128)
   int tune_B = 0, tune_nl = 0, tune_splits = 0, tune_kbps = 0;
-  int tune_pair_adj = 0, tune_pair_fwd = 0;  // 0 single CTAs; pairs of 1: 256 columns, 2: 192, 3: 160
+  int tune_pair_adj = 0, tune_pair_fwd = 0;  // 0 single CTAs; pairs of 1: 256 columns, 2: 192, 3: 160, 4: 144
   // instance groups iterated as parallel branches of the iteration graph (1 or 2); the
   // product shapes above are those of one group's batch
   int tune_branches = 1;
   // DCOPF_TENSOR_TILES (read at create): 0 = choose by timing, 1 = single CTAs only,
-  // 2 / 3 / 4 = CTA pairs of 256 x 256 / 256 x 192 / 256 x 160 tiles only (where the
-  // batch has more than 128 instances)
+  // 2 / 3 / 4 / 5 = CTA pairs of 256 x 256 / 256 x 192 / 256 x 160 / 256 x 144 tiles
+  // only (where the batch has more than 128 instances)
   int tiles_mode = 0;
   // DCOPF_TENSOR_SHAPE="a,s,f[,g]" (read at create): the adjoint's tiles (0 single, 1
-  // pairs of 256, 2 pairs of 192, 3 pairs of 160), its split-K factor, the forward's tiles, the branches
+  // pairs of 256, 2 pairs of 192, 3 pairs of 160, 4 pairs of 144), its split-K factor, the forward's tiles, the branches
   // (default 1); no timing (for profilers, whose per-launch overhead changes what the
   // timing would pick)
   int shape_adj = -1, shape_splits = 0, shape_fwd = -1, shape_branches = 1;

@@ -105,3 +105,37 @@ def test_screened_10000bus_batch_reaches_stored_optima():
     assert abs(it1.mean() - it0.mean()) <= 0.05 * it0.mean()
     print(f"10000-bus: {kept.sum()} of {w.net.n_line} lines kept; iterations {it0.mean():.1f} "
           f"unscreened, {it1.mean():.1f} screened")
+
+
+def test_speculative_screen_rescreens_a_batch_that_needs_more_lines(monkeypatch):
+    """A handle goes ahead with its last kept set when a new batch comes; the solve then
+    learns on the device whether the batch needs a line outside it and, if so, runs
+    again with the batch's own screen.  A batch of 16 copies of 0.85 x the mean load, then
+    16 scenarios of the workload: the second must keep lines the first screened out, and
+    its solve on the reused handle equals the solve of the same batch on a fresh handle."""
+    w = synth.scenario_workload(81, 80, 130, 14, True, batch=40, n_out=0)
+    on = onet(w.net)
+    base = w.loads.mean(axis=0)
+    narrow = np.repeat(0.85 * base[None], 16, 0)
+    wide = w.loads[:16]
+    gam_w = [gamma(on, wide[b]) for b in range(16)]
+    gam_n = [gamma(on, narrow[b]) for b in range(16)]
+    kw = dict(path="batched", precision="bf16x3", screen=True, **ADAM_QP)
+    monkeypatch.setenv("DCOPF_TENSOR_SHAPE", "0,2,0,1")   # the same product shapes on both handles
+    g = DcopfDual(w.net)
+    g.solve(narrow, target=gam_n, **kw)
+    kept_n = g.screened_lines()
+    r = g.solve(wide, target=gam_w, **kw)
+    torch.cuda.synchronize()
+    kept_w = g.screened_lines()
+    f = DcopfDual(w.net)
+    monkeypatch.delenv("DCOPF_TENSOR_SHAPE")
+    rf = f.solve(wide, target=gam_w, **kw)
+    torch.cuda.synchronize()
+    kept_f = f.screened_lines()
+    print(f"kept: {kept_n.sum()} narrow, {kept_f.sum()} wide (fresh), {kept_w.sum()} wide (reused)")
+    assert np.any(kept_f & ~kept_n), "the wide batch should need a line the narrow one screens out"
+    np.testing.assert_array_equal(kept_w, kept_f)
+    for a, b in ((r.bound, rf.bound), (r.iters, rf.iters), (r.status, rf.status), (r.lam, rf.lam)):
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    assert np.all(r.bound.cpu().numpy() <= np.array(gam_w) + 1e-9 * np.abs(gam_w))
