@@ -561,6 +561,9 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
   UP(H.F.lcol_ptr, lcol_ptr) UP(H.F.lcol_row, lcol_row) UP(H.F.lcol_val, lcol_val)
   UP(H.F.diag, diag) UP(H.F.fwd_rows, fwd_rows) UP(H.F.fwd_level_ptr, fwd_lev)
   UP(H.F.bwd_rows, bwd_rows) UP(H.F.bwd_level_ptr, bwd_lev)
+  UP(H.F.fell_col, fell_col) UP(H.F.fell_val, fell_val) UP(H.F.fovf_ptr, fovf_ptr) UP(H.F.fovf_col, fovf_col)
+  UP(H.F.fovf_val, fovf_val) UP(H.F.bell_col, bell_col) UP(H.F.bell_val, bell_val) UP(H.F.bovf_ptr, bovf_ptr)
+  UP(H.F.bovf_col, bovf_col) UP(H.F.bovf_val, bovf_val)
   UP(H.line_from, line_from) UP(H.line_to, line_to) UP(H.b, line_b) UP(H.fmax, fmax)
   UP(H.fmin, fmin) UP(fmax32, fmax32) UP(fmin32, fmin32) UP(H.phim, phim)
   UP(H.bus_line_ptr, bus_line_ptr) UP(H.bus_line_idx, bus_line_idx)

@@ -23,6 +23,9 @@ struct DevNet {
   const double* diag;
   const int* fwd_rows; const int* fwd_lev; int n_fwd_lev;
   const int* bwd_rows; const int* bwd_lev; int n_bwd_lev;
+  // the same schedules ELL-packed (SparseFactor::kEll slots per row, then an overflow)
+  const int* fell_col; const double* fell_val; const int* fovf_ptr; const int* fovf_col; const double* fovf_val;
+  const int* bell_col; const double* bell_val; const int* bovf_ptr; const int* bovf_col; const double* bovf_val;
   const double* winv1;     // [nr] upper bound of B_r^{-1} 1 (entries >= 0: B_r is an M-matrix)
   // packed copy of the factor for shared-memory staging (nullptr when unavailable)
   const unsigned char* fac_blob; int fac_bytes;

@@ -25,6 +25,13 @@ struct SparseFactor {
   // level schedules: rows listed level by level
   std::vector<int> fwd_rows, fwd_level_ptr;
   std::vector<int> bwd_rows, bwd_level_ptr;
+  // The same rows in schedule order, ELL-packed: for the row at schedule position idx,
+  // its first kEll entries at [a * n + idx] (a < kEll; unused slots the row itself with
+  // value 0), the rest in a schedule-ordered CSR overflow (ptr [n + 1]).  Entries keep
+  // the CSR (forward) / CSC (backward) order, so sums are the same as the plain walk's.
+  static constexpr int kEll = 4;
+  std::vector<int> fell_col, bell_col, fovf_ptr, fovf_col, bovf_ptr, bovf_col;
+  std::vector<double> fell_val, bell_val, fovf_val, bovf_val;
   int64_t nnz() const { return (int64_t)lrow_col.size(); }
   // Packed copy for shared-memory staging (empty when indices do not fit 16 bits):
   // 16-byte aligned sections at the byte offsets below.

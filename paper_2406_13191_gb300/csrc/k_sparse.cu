@@ -16,27 +16,42 @@
 
 namespace dcopf {
 
+// The solve of a row at schedule position idx: its kEll packed entries (all loaded in
+// one round trip, as they depend on idx only), then its overflow entries, in the same
+// order as the row's CSR / CSC walk (unused slots subtract 0 x X[i]).
+__device__ __forceinline__ void ell_row(int nr, int idx, int i, const int* __restrict__ ecol,
+                                        const double* __restrict__ eval, const int* __restrict__ optr,
+                                        const int* __restrict__ ocol, const double* __restrict__ oval,
+                                        double* X) {
+  constexpr int K = SparseFactor::kEll;
+  int c[K];
+  double w[K];
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    c[a] = ecol[(size_t)a * nr + idx];
+    w[a] = eval[(size_t)a * nr + idx];
+  }
+  const int o0 = optr[idx], o1 = optr[idx + 1];
+  double v = X[i];
+#pragma unroll
+  for (int a = 0; a < K; ++a) v -= w[a] * X[c[a]];
+  for (int p = o0; p < o1; ++p) v -= oval[p] * X[ocol[p]];
+  X[i] = v;
+}
+
 __device__ void ldl_solve_smem(const DevNet& N, double* X) {
   for (int lev = 0; lev < N.n_fwd_lev; ++lev) {
     int s = N.fwd_lev[lev], e = N.fwd_lev[lev + 1];
-    for (int idx = s + threadIdx.x; idx < e; idx += blockDim.x) {
-      int i = N.fwd_rows[idx];
-      double v = X[i];
-      for (int p = N.lrow_ptr[i]; p < N.lrow_ptr[i + 1]; ++p) v -= N.lrow_val[p] * X[N.lrow_col[p]];
-      X[i] = v;
-    }
+    for (int idx = s + threadIdx.x; idx < e; idx += blockDim.x)
+      ell_row(N.nr, idx, N.fwd_rows[idx], N.fell_col, N.fell_val, N.fovf_ptr, N.fovf_col, N.fovf_val, X);
     __syncthreads();
   }
   for (int i = threadIdx.x; i < N.nr; i += blockDim.x) X[i] /= N.diag[i];
   __syncthreads();
   for (int lev = 0; lev < N.n_bwd_lev; ++lev) {
     int s = N.bwd_lev[lev], e = N.bwd_lev[lev + 1];
-    for (int idx = s + threadIdx.x; idx < e; idx += blockDim.x) {
-      int i = N.bwd_rows[idx];
-      double v = X[i];
-      for (int p = N.lcol_ptr[i]; p < N.lcol_ptr[i + 1]; ++p) v -= N.lcol_val[p] * X[N.lcol_row[p]];
-      X[i] = v;
-    }
+    for (int idx = s + threadIdx.x; idx < e; idx += blockDim.x)
+      ell_row(N.nr, idx, N.bwd_rows[idx], N.bell_col, N.bell_val, N.bovf_ptr, N.bovf_col, N.bovf_val, X);
     __syncthreads();
   }
 }

@@ -351,6 +351,36 @@ dcopf_status build_host_net(const dcopf_network_desc* d, HostNet* H, std::string
   };
   schedule(true, &F.fwd_rows, &F.fwd_level_ptr);
   schedule(false, &F.bwd_rows, &F.bwd_level_ptr);
+  // ELL packing of the rows in schedule order (a row's entries load in one round trip)
+  auto ell = [&](const std::vector<int>& order, const std::vector<int>& ptr, const std::vector<int>& idx_of,
+                 const std::vector<double>& val, std::vector<int>* ecol, std::vector<double>* eval,
+                 std::vector<int>* optr, std::vector<int>* ocol, std::vector<double>* oval) {
+    const int K = SparseFactor::kEll;
+    ecol->assign((size_t)K * n, 0);
+    eval->assign((size_t)K * n, 0.0);
+    optr->assign(n + 1, 0);
+    ocol->clear();
+    oval->clear();
+    for (int q = 0; q < n; ++q) {
+      const int i = order[q];
+      for (int a = 0; a < K; ++a) (*ecol)[(size_t)a * n + q] = i;
+      int a = 0;
+      for (int p = ptr[i]; p < ptr[i + 1]; ++p, ++a) {
+        if (a < K) {
+          (*ecol)[(size_t)a * n + q] = idx_of[p];
+          (*eval)[(size_t)a * n + q] = val[p];
+        } else {
+          ocol->push_back(idx_of[p]);
+          oval->push_back(val[p]);
+        }
+      }
+      (*optr)[q + 1] = (int)ocol->size();
+    }
+  };
+  ell(F.fwd_rows, F.lrow_ptr, F.lrow_col, F.lrow_val, &F.fell_col, &F.fell_val, &F.fovf_ptr, &F.fovf_col,
+      &F.fovf_val);
+  ell(F.bwd_rows, F.lcol_ptr, F.lcol_row, F.lcol_val, &F.bell_col, &F.bell_val, &F.bovf_ptr, &F.bovf_col,
+      &F.bovf_val);
   // packed factor for shared-memory staging: FP64 values stored once (CSR order),
   // the CSC walk reads them through a position map; indices in 16 bits
   if (n > 0 && n < 65535) {
