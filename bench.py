@@ -101,6 +101,15 @@ def load_peaks():
 
 
 def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else /proc/cpuinfo's model name or part number
+    (Arm parts list only "CPU part", e.g. 0xd4f, the Neoverse V2 of Grace)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         for line in open("/proc/cpuinfo"):
             if line.lower().startswith(("model name", "cpu part")):
