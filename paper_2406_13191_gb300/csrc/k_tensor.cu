@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <string>
 #include <vector>
 
 #include "dev.cuh"
@@ -66,12 +67,9 @@ __device__ __forceinline__ float step_rule(const StepArgsF& P, float theta, floa
 }
 
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo);
-__device__ __forceinline__ void finalize_instance(int b, int lane, int ld_l, int max_iters, double tol,
+__device__ __forceinline__ void finalize_instance(int b, int lane, int max_iters, double tol,
                                                   const SolveStateBase& st, const BatchView& bb,
-                                                  const int* __restrict__ outage,
-                                                  const double* __restrict__ demand,
-                                                  __nv_bfloat16* __restrict__ Hh,
-                                                  __nv_bfloat16* __restrict__ Hl);
+                                                  const double* __restrict__ demand);
 
 // Step of the batched solve after the forward product: flows (with the rank-1 outage
 // term), supergradient, line part of the dual value, projected step of mu into the
@@ -79,8 +77,8 @@ __device__ __forceinline__ void finalize_instance(int b, int lane, int ld_l, int
 struct StepEpi {
   StepArgsF P;
   const float* F;             // [B][ldF] forward product Phi~ x
-  int ldF;
   const float* f0;            // [B][nl] flows of the mid-box dispatch minus the loads
+  int ldF;
   const float* u;             // [B][nl] outage vectors (rows of outage instances)
   const int* outage;          // [B] or null
   const float* tout;          // [B] pre-outage flow on the outaged line, (Phi~ x)_k
@@ -100,14 +98,10 @@ struct StepEpi {
   __nv_bfloat16* Hh; __nv_bfloat16* Hl; int ldh;
   double* line_part; double* out_part; int n_tiles;   // [B][n_tiles] per slice of lines
   int B;                      // instances
-  // the dual value and the stop tests of the evaluated point (finalize_instance), run by
-  // the last of an instance's blocks to finish: step_done [B] counts them
-  SolveStateBase st;
-  BatchView bb;
-  const double* demand;
-  int max_iters;
-  double tol;
-  int* step_done;
+  // [B]: the step has left the value partials of the instance's evaluated point (its
+  // value and stop tests, finalize_instance, run in the next minimiser or at the end
+  // of the round)
+  int* pend;
 };
 
 // The step's work is a slice of STEP_SLICE lines of one instance per warp (four lines
@@ -116,27 +110,14 @@ struct StepEpi {
 constexpr int STEP_THREADS = 256, STEP_SLICE = 128;
 
 // The tail of both step kernels, per warp: the warp's partials go to slot `part` of the
-// instance's [n_tiles]; the last warp of instance b to finish runs its value and stop
-// tests.  No block-wide barrier: warps finish on their own.
+// instance's [n_tiles], and the instance is marked as having partials to finalise (every
+// warp stores the same flag; the kernels that read it run later in the stream).  No
+// barrier and no fence: warps finish on their own.
 __device__ __forceinline__ void step_tail(const StepEpi& E, int b, int part, float lacc, float oacc) {
-  const int lane = threadIdx.x & 31;
-  const int np = E.n_tiles;
-  // release / acquire at GPU scope around a relaxed count: the warp's writes (ordered
-  // before lane 0's fence by __syncwarp) before its count, every other warp's before
-  // the last one reads them
-  __syncwarp();
-  int last = 0;
-  if (lane == 0) {
-    E.line_part[(size_t)b * np + part] = (double)lacc;
-    E.out_part[(size_t)b * np + part] = (double)oacc;
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    last = atomicAdd(&E.step_done[b], 1) == np - 1;
-  }
-  last = __shfl_sync(0xffffffffu, last, 0);
-  if (last) {
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    if (lane == 0) E.step_done[b] = 0;
-    finalize_instance(b, lane, E.ldh, E.max_iters, E.tol, E.st, E.bb, E.outage, E.demand, E.Hh, E.Hl);
+  if ((threadIdx.x & 31) == 0) {
+    E.line_part[(size_t)b * E.n_tiles + part] = (double)lacc;
+    E.out_part[(size_t)b * E.n_tiles + part] = (double)oacc;
+    E.pend[b] = 1;
   }
 }
 
@@ -692,10 +673,43 @@ __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M
                                               const BatchView& bb, const StepArgs& SP, int ldx,
                                               __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl,
                                               const int* __restrict__ outage,
-                                              const double* __restrict__ demand, int b, double* red) {
-  if (bb.frozen[b]) return;
+                                              const double* __restrict__ demand, int max_iters, double tol,
+                                              int b, double* red) {
+  // Warp 0 first runs the value and stop tests of the point the last step evaluated,
+  // while the other warps start on the generators (whose terms do not depend on them);
+  // the block's step at the end is skipped if those tests stopped the instance.  With
+  // the mean of the minimisers on, whose weight is the iteration count the tests
+  // advance, every warp waits for them instead.  (pend and frozen are read by every
+  // thread before warp 0 changes them; an instance frozen on entry has nothing pending.)
+  const int pend = bb.pend[b];
+  const int frozen0 = bb.frozen[b];
+  __syncthreads();
+  if (frozen0) return;
+  if (pend && threadIdx.x < 32) {
+    finalize_instance(b, (int)threadIdx.x, max_iters, tol, st, bb, demand);
+    if (threadIdx.x == 0) bb.pend[b] = 0;
+  }
+  if (st.xsum) {
+    __syncthreads();
+    if (bb.frozen[b]) return;
+  }
   const int ng = N.n_gen;
   const int k = outage ? outage[b] : -1;
+  // the outaged line's term of the adjoint: the step left its multiplier difference out
+  // of H (0 there) and its u^T eta in the slices' partials (summed here in the value
+  // tests' order, so that it is their ueta), else ueta holds it (0 before the first step,
+  // when H holds it)
+  float ueta = 0.f;
+  if (k >= 0) {
+    if (pend) {
+      const int nt = bb.n_tiles, ln = threadIdx.x & 31;
+      double os = 0.0;
+      for (int q = ln; q < nt; q += 32) os += bb.out_part[(size_t)b * nt + q];
+      ueta = (float)warp_sum(os);
+    } else {
+      ueta = bb.ueta[b];
+    }
+  }
   const double lam = st.lam[b];
   // The in-loop value and the lambda gradient only steer the iteration (the bound is
   // certified in FP64 later): per-generator terms and warp sums in FP32, FP64 across
@@ -726,6 +740,7 @@ __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M
     auto gen = [&](int j, float sj) {
       const float4 g = N.gen4[j];   // sigma, ctil, mq, cconst
       const float2 g2 = N.gen2[j];  // mid, 1 / (2 mq) (0 for a linear cost)
+      if (k >= 0) sj = fmaf(N.phi32[(size_t)k * ng + j], ueta, sj);
       const float w = fmaf(g.x, lamf, g.y) + sj;
       // the closed-form minimiser of eq. (6) / (16) on the normalised box [-1, 1]
       const float x = g.z > 0.f ? fminf(1.f, fmaxf(-1.f, -w * g2.y)) : (w > 0.f ? -1.f : (w < 0.f ? 1.f : 0.f));
@@ -755,6 +770,7 @@ __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M
       ts += __shfl_xor_sync(0xffffffffu, ts, o);
     }
     if (lane != 0) return;
+    if (bb.frozen[b]) return;  // stopped by this kernel's value tests (warp 0's own write)
     bb.cost[b] = cs;
     bb.psum[b] = ps;
     if (st.wsum) st.wsum[b] += (double)wk;
@@ -798,28 +814,26 @@ __global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
     k_bt_minimize(DevNet N, int splits, int M, int ldp, const float* __restrict__ P,
                   SolveStateBase st, BatchView bb, StepArgs SP, int ldx,
                   __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl,
-                  const int* __restrict__ outage, const double* __restrict__ demand) {
+                  const int* __restrict__ outage, const double* __restrict__ demand, int max_iters,
+                  double tol) {
   __shared__ double red[3 * (MIN_MAX_THREADS / 32)];
   for (int b = blockIdx.x; b < M; b += gridDim.x) {
     if (splits <= 4)
-      minimize_item<4>(N, splits, M, ldp, P, st, bb, SP, ldx, Xh, Xl, outage, demand, b, red);
+      minimize_item<4>(N, splits, M, ldp, P, st, bb, SP, ldx, Xh, Xl, outage, demand, max_iters, tol, b, red);
     else
-      minimize_item<8>(N, splits, M, ldp, P, st, bb, SP, ldx, Xh, Xl, outage, demand, b, red);
+      minimize_item<8>(N, splits, M, ldp, P, st, bb, SP, ldx, Xh, Xl, outage, demand, max_iters, tol, b, red);
     __syncthreads();  // red is read by warp 0 before the next instance's partials land
   }
 }
 
-// Dual value of the evaluated point (FP64), best value and its lambda, outage patch of
-// the next eta, stop tests, for instance b, by one warp of the step kernel's last block
-// for the instance.  A stopping instance is frozen: one that reached its target with the
-// point just evaluated (state buffer iter % 3), one stopped by the iteration cap or the
-// tol test with its best point.
-__device__ __forceinline__ void finalize_instance(int b, int lane, int ld_l, int max_iters, double tol,
+// Dual value of the evaluated point (FP64), best value and its lambda, u^T eta of the
+// point stepped to, stop tests, for instance b, by one warp: of the next iteration's
+// minimiser block for the instance, or of the end-of-round kernel.  A stopping instance
+// is frozen: one that reached its target with the point just evaluated (state buffer
+// iter % 3), one stopped by the iteration cap or the tol test with its best point.
+__device__ __forceinline__ void finalize_instance(int b, int lane, int max_iters, double tol,
                                                   const SolveStateBase& st, const BatchView& bb,
-                                                  const int* __restrict__ outage,
-                                                  const double* __restrict__ demand,
-                                                  __nv_bfloat16* __restrict__ Hh,
-                                                  __nv_bfloat16* __restrict__ Hl) {
+                                                  const double* __restrict__ demand) {
   const int nt = bb.n_tiles;
   double ls = 0.0, os = 0.0;
   for (int q = lane; q < nt; q += 32) {
@@ -832,8 +846,9 @@ __device__ __forceinline__ void finalize_instance(int b, int lane, int ld_l, int
   const double val = bb.cost[b] + bb.lam_eval[b] * (bb.psum[b] - demand[b]) + ls;
   const int t = st.iter[b] + 1;
   if (val > st.best[b]) { st.best[b] = val; st.best_iter[b] = t; bb.lam_best[b] = bb.lam_eval[b]; }
-  const int k = outage ? outage[b] : -1;
-  if (k >= 0) split_bf16((float)os, Hh + (size_t)b * ld_l + k, Hl + (size_t)b * ld_l + k);
+  // u^T eta of the point stepped to, the outaged line's multiplier difference in the
+  // post-outage adjoint: the next minimiser adds its column of the product
+  bb.ueta[b] = (float)os;
   int c = 0;
   if (st.has_target && val >= st.thresh[b] + st.margin[b]) c = 1;
   else if (t >= max_iters) c = 2;
@@ -846,6 +861,18 @@ __device__ __forceinline__ void finalize_instance(int b, int lane, int ld_l, int
   } else {
     st.iter[b] = t;
   }
+}
+
+// The value and stop tests of the points the last step of a round evaluated (those
+// the next round's first minimiser would otherwise take), so that the round's staging
+// sees them.  One warp per instance.
+__global__ void k_bt_finalize(int B, int max_iters, double tol, SolveStateBase st, BatchView bb,
+                              const double* __restrict__ demand) {
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (b >= B) return;
+  if (!__shfl_sync(0xffffffffu, lane == 0 ? bb.pend[b] : 0, 0)) return;
+  finalize_instance(b, lane, max_iters, tol, st, bb, demand);
+  if (lane == 0) bb.pend[b] = 0;
 }
 
 // Stages the frozen candidates whose certificate is not already pending (snap_prev,
@@ -926,7 +953,8 @@ __global__ void __launch_bounds__(ACCEPT_THREADS)
 __global__ void k_bt_init(int B, BatchView bb) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
     bb.frozen[b] = 0;
-    bb.step_done[b] = 0;
+    bb.pend[b] = 0;
+    bb.ueta[b] = 0.f;
     bb.pw[3 * b] = 1.0;
     bb.pw[3 * b + 1] = 1.0;
     bb.pw[3 * b + 2] = 1.0;
@@ -939,7 +967,7 @@ static dcopf_status ensure_batch_bufs(dcopf_dual* h, int B, int n_tiles) {
   const size_t nl = h->host.n_line;
   if (bb.mu2.alloc((size_t)B * nl * 6 * sizeof(float)) ||
       bb.parts.alloc((size_t)B * n_tiles * 2 * sizeof(double)) ||
-      bb.small.alloc((size_t)B * 7 * sizeof(double) + (size_t)B * 7 * sizeof(float) + 1024)) {
+      bb.small.alloc((size_t)B * 7 * sizeof(double) + (size_t)B * 8 * sizeof(float) + 1024)) {
     cudaGetLastError();
     return DCOPF_ERR_OOM;
   }
@@ -957,7 +985,8 @@ static dcopf_status ensure_batch_bufs(dcopf_dual* h, int B, int n_tiles) {
   float* f = (float*)(d + 7 * (size_t)B);
   v.tout = f; v.stepf = f + B;  // stepf: [B][4]
   v.frozen = (int*)(f + 5 * (size_t)B);
-  v.step_done = (int*)(f + 6 * (size_t)B);
+  v.pend = (int*)(f + 6 * (size_t)B);
+  v.ueta = f + 7 * (size_t)B;
   v.n_tiles = n_tiles;
   return DCOPF_OK;
 }
@@ -1041,7 +1070,7 @@ static bool make_view(TensorRun& R, int b0, int Bg, IterView* V) {
   BatchView& bb = W.bb;
   bb = h->bb.v;
   adv(bb.frozen, o); adv(bb.lam_eval, o); adv(bb.cost, o); adv(bb.psum, o); adv(bb.pw, 3 * o);
-  adv(bb.tout, o); adv(bb.stepf, 4 * o); adv(bb.lam_best, o); adv(bb.step_done, o);
+  adv(bb.tout, o); adv(bb.stepf, 4 * o); adv(bb.lam_best, o); adv(bb.pend, o); adv(bb.ueta, o);
   for (float** q : {&bb.mu2_hi, &bb.mu2_lo, &bb.mu3_hi, &bb.mu3_lo, &bb.sv_hi, &bb.sv_lo}) adv(*q, o * nl);
   adv(bb.line_part, o * nt); adv(bb.out_part, o * nt);
   W.ga = R.ga;
@@ -1067,12 +1096,10 @@ static bool make_view(TensorRun& R, int b0, int Bg, IterView* V) {
   E.Hl = R.E.Hl + o * E.ldh;
   E.line_part = bb.line_part; E.out_part = bb.out_part;
   E.B = Bg;
-  E.st = st;
-  E.bb = bb;
-  E.step_done = bb.step_done;
+  E.pend = bb.pend;
   W.outage = R.it.outage ? R.it.outage + o : nullptr;
   W.demand = h->ws.demand.as<double>() + o;
-  E.demand = W.demand;
+
   W.Xhp = T.X_hi.as<__nv_bfloat16>() + o * T.ld_g;
   W.Xlp = T.X_lo.as<__nv_bfloat16>() + o * T.ld_g;
   W.Hhp = E.Hh;
@@ -1127,7 +1154,7 @@ static bool enqueue_iters(TensorRun& R, IterView& V, int n, cudaStream_t cs, boo
     const int mb = R.min_blocks ? std::min(V.B, R.min_blocks) : V.B;
     k_bt_minimize<<<mb, minimize_threads(h, V.B), 0, cs>>>(h->dev, R.splits, V.B, V.ga.ldp, V.ga.P, V.st,
                                                            V.bb, R.P, T.ld_g, V.Xhp, V.Xlp, V.outage,
-                                                           V.demand);
+                                                           V.demand, R.p.max_iters, R.p.tol);
     ev(2);
     ok &= launch_forward(h, R.ls, V.Xh, V.Xl, V.gf, R.pair_fwd, cs) == cudaSuccess;
     ev(3);
@@ -1137,10 +1164,12 @@ static bool enqueue_iters(TensorRun& R, IterView& V, int n, cudaStream_t cs, boo
       k_bt_step4<<<sb, STEP_THREADS, 0, cs>>>(V.E, nl);
     else
       k_bt_step<<<sb, STEP_THREADS, 0, cs>>>(V.E, nl);
-    ev(4);  // the value and stop tests run in the step kernel's last block per instance
+    ev(4);  // the value and stop tests run in the next minimiser (or below, for the last)
     ev(5);
   }
-  return ok;
+  // the value and stop tests of the round's last step
+  k_bt_finalize<<<(V.B + 3) / 4, 128, 0, cs>>>(V.B, R.p.max_iters, R.p.tol, V.st, V.bb, V.demand);
+  return ok && cudaGetLastError() == cudaSuccess;
 }
 
 // Enqueues `chunk` iterations of every group on cs (the groups after the first on the
@@ -1269,7 +1298,8 @@ static dcopf_status tune_view_shapes(TensorRun& R, IterView& V, cudaStream_t cs,
         [&] {
           cudaError_t e = launch_adjoint(h, R.ls, V.Hh, V.Hl, g, c.splits, c.tiles, cs);
           k_bt_minimize<<<B, minimize_threads(h, B), 0, cs>>>(h->dev, c.splits, B, g.ldp, g.P, V.st, V.bb, R.P,
-                                                              T.ld_g, V.Xhp, V.Xlp, V.outage, V.demand);
+                                                              T.ld_g, V.Xhp, V.Xlp, V.outage, V.demand,
+                                                              R.p.max_iters, R.p.tol);
           h->launches += 1;
           return e != cudaSuccess ? e : cudaGetLastError();
         },
@@ -1350,7 +1380,7 @@ static dcopf_status time_iterations(TensorRun& R, cudaStream_t cs, float* ms) {
       res = DCOPF_ERR_CUDA;
     if (rep > 0) *ms = std::min(*ms, t);
   }
-  R.it.h->launches += 4LL * 6 * 2 * R.nv;  // the products count themselves
+  R.it.h->launches += 4LL * (6 * 2 + 1) * R.nv;  // the products count themselves
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return res;
@@ -1498,8 +1528,7 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   E.s1_hi = R.st.s1_hi; E.s2_hi = R.st.s2_hi; E.s1_lo = R.st.s1_lo; E.s2_lo = R.st.s2_lo;
   E.Hh = T.H_hi.as<__nv_bfloat16>(); E.Hl = T.H_lo.as<__nv_bfloat16>(); E.ldh = R.ls.ld_l;
   E.line_part = bb.line_part; E.out_part = bb.out_part; E.n_tiles = R.n_tiles;
-  E.st = R.st; E.bb = bb; E.demand = w.demand.as<double>(); E.step_done = bb.step_done; E.B = B;
-  E.max_iters = p.max_iters; E.tol = p.tol;
+  E.pend = bb.pend; E.B = B;
   if (h->timing && !h->kev[0])
     for (int q = 0; q < 6; ++q)
       if (cudaEventCreate(&h->kev[q]) != cudaSuccess) return DCOPF_ERR_CUDA;
@@ -1614,8 +1643,9 @@ struct GroupObjects {
   }
 };
 
-// The bytes of every kernel argument of the iteration graph of runs[0..n): a later solve
-// with the same bytes replays the graph captured for them.
+// The bytes of every kernel argument of the iteration graph of runs[0..n) (the views,
+// the step rule, the stop parameters, the shapes, the operand maps, the network's device
+// data): a later solve with the same bytes replays the graph captured for them.
 static std::vector<unsigned char> graph_signature(const std::vector<TensorRun>& runs, int chunk) {
   std::vector<unsigned char> sig;
   auto put = [&](const void* p, size_t n) {
@@ -1632,6 +1662,9 @@ static std::vector<unsigned char> graph_signature(const std::vector<TensorRun>& 
     put(&R.nv, sizeof R.nv);
     put(R.v, sizeof(IterView) * R.nv);
     put(&R.P, sizeof R.P);
+    put(&R.p.max_iters, sizeof R.p.max_iters);  // arguments of the minimiser and the value kernel
+    put(&R.p.tol, sizeof R.p.tol);
+    put(&h->dev, sizeof h->dev);
     const int ints[7] = {R.splits, R.pair_adj, R.pair_fwd, R.n_tiles, R.step_blocks, R.min_blocks, R.ls.nl};
     put(ints, sizeof ints);
     for (const CUtensorMap* m : {R.ls.phit_hi, R.ls.phit_lo, R.ls.phit_hi96, R.ls.phit_lo96, R.ls.phit_hi80,
@@ -1795,8 +1828,8 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
     if (cudaGraphLaunch(K.exec, cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
     long long round_launches = 0;
     for (int i = 0; i < n; ++i) {
-      items[i].h->launches += 4LL * chunk * runs[i].nv;
-      round_launches += 4LL * chunk * runs[i].nv;
+      items[i].h->launches += (4LL * chunk + 1) * runs[i].nv;
+      round_launches += (4LL * chunk + 1) * runs[i].nv;
     }
     if (h0->timing) cudaEventRecord(K.t1[sl], cs0);
     if (verbose) cudaEventRecord(G.vev[G.vev.size() - 2], cs0);
@@ -1891,10 +1924,14 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
   }
   if (verbose) {
     double graphs = 0.0, gaps = 0.0, accepts = 0.0;
+    std::string per_round;
     for (size_t q = 0; q + 2 < G.vev.size(); q += 3) {
       float a = 0.f, b = 0.f, c = 0.f;
       cudaEventElapsedTime(&a, G.vev[q], G.vev[q + 1]);
       graphs += a;
+      char buf[16];
+      snprintf(buf, sizeof buf, " %.2f", a);
+      per_round += buf;
       if (cudaEventElapsedTime(&c, G.vev[q + 1], G.vev[q + 2]) == cudaSuccess) accepts += c;
       if (q + 3 < G.vev.size() && cudaEventElapsedTime(&b, G.vev[q + 1], G.vev[q + 3]) == cudaSuccess) gaps += b;
     }
@@ -1904,6 +1941,7 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
             "GPU), host waits %.2f ms, loop %.2f ms (host)\n",
             t_setup, reuse ? "reused" : "captured", t_captured - t_setup, rounds, graphs, gaps, accepts, t_wait,
             host_ms() - t_captured);
+    fprintf(stderr, "dcopf: graph ms per round:%s\n", per_round.c_str());
   }
   // the last two rounds' certificates: accept what they staged (nothing, when every
   // instance had stopped before those rounds)

@@ -186,7 +186,8 @@ struct LineScreen {
 struct BatchView {
   int n_tiles = 0;             // slices of lines of the step kernel
   int* frozen = nullptr;       // [B] done or waiting for certification
-  int* step_done = nullptr;    // [B] blocks of the step kernel finished with the instance
+  int* pend = nullptr;         // [B] value partials of the evaluated point not yet finalised
+  float* ueta = nullptr;       // [B] u^T eta of the point stepped to (outaged line's term)
   double* lam_eval = nullptr;  // [B] lambda of the evaluated point
   double* cost = nullptr;      // [B] generation cost at the minimiser
   double* psum = nullptr;      // [B] total dispatch

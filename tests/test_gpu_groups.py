@@ -133,3 +133,16 @@ def test_iteration_graph_reused_only_for_the_same_arguments():
     for x, y in zip(b1, fresh):
         np.testing.assert_array_equal(x, y)
     assert not np.array_equal(a1[1], b1[1])   # the settings differ in iterations taken
+
+
+def test_iteration_graph_recaptured_for_another_iteration_cap():
+    """The iteration cap is an argument of the graph's kernels (the stop tests): solves
+    capped at 40 and then 72 iterations on one handle, with no target, take exactly 40
+    and 72 iterations."""
+    w = synth.workload(1, batch=256)
+    g = _handle(w.net, "0,3,0,1")
+    for cap in (40, 72, 40):
+        r = g.solve(w.loads, path="batched", precision="bf16x3", **dict(QP_ADAM, max_iters=cap))
+        torch.cuda.synchronize()
+        it = r.iters.cpu().numpy()
+        assert np.all(it == cap), (cap, np.unique(it))
