@@ -394,8 +394,10 @@ dcopf_status dcopf_dual_read_kernel_timing(dcopf_dual_t h, double* ms, int64_t* 
 /* The shapes the batched tensor-core solve chose for its last batch (by timing on the
  * first solve of a batch size, or as DCOPF_TENSOR_SHAPE fixed them), into shapes (host
  * [7]): the batch, the lines iterated on, the adjoint product's tiles (0 single CTAs of
- * 128 x 128; CTA pairs of 1: 256 x 256, 2: 256 x 192, 3: 256 x 160, 4: 256 x 144), its
- * split-K factor, the forward product's tiles (same codes), the number of instance groups iterated as
+ * 128 x 128; CTA pairs of 1: 256 x 256, 2: 256 x 192, 3: 256 x 160, 4: 256 x 144;
+ * 5 .. 8: the widths of 1 .. 4 in clusters of two pairs that load each box of the batch
+ * operand once for both), its split-K factor, the forward product's tiles (same codes),
+ * the number of instance groups iterated as
  * parallel branches of the iteration graph (1 or 2; the tiles are those of one group's
  * share of the batch), and the first group's instances (its kernels are the ones that
  * dcopf_dual_read_kernel_timing times).  All zero before the first batched solve.

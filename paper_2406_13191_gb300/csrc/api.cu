@@ -490,7 +490,7 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
     const char* sh = getenv("DCOPF_TENSOR_SHAPE");
     int a = -1, sp = 0, fw = -1, br = 1;
     const int nf = sh ? sscanf(sh, "%d,%d,%d,%d", &a, &sp, &fw, &br) : 0;
-    if (nf >= 3 && a >= 0 && a <= 4 && sp >= 1 && sp <= 64 && fw >= 0 && fw <= 4 && br >= 1 &&
+    if (nf >= 3 && a >= 0 && a <= 8 && sp >= 1 && sp <= 64 && fw >= 0 && fw <= 8 && br >= 1 &&
         br <= 2) {
       h->shape_adj = a;
       h->shape_splits = sp;

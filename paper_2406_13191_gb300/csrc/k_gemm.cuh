@@ -36,6 +36,7 @@ struct GemmArgs {
   int* err;
   uint64_t timeout_ns;
   const int* skip;       // nullable [M]: rows whose instance is frozen (a tile of them is skipped)
+  int bblk;              // B in 8-row blocks (4-D maps: element (r, c) at ((r/8 KB + c/64) 8 + r%8) 64 + c%64)
 };
 
 constexpr int GBM = 128, GBN = 128, GBK = 64;
@@ -110,8 +111,13 @@ __global__ void __launch_bounds__(192, OCC)
       const int x = (kb0 + i) * GBK;
       umma::tma_load_2d(&tAh, &full[s], a_hi(s), x, m0);
       if (NPROD == 3) umma::tma_load_2d(&tAl, &full[s], a_lo(s), x, m0);
-      umma::tma_load_2d(&tBh, &full[s], b_hi(s), x, n0);
-      umma::tma_load_2d(&tBl, &full[s], b_lo(s), x, n0);
+      if (g.bblk) {
+        umma::tma_load_4d(&tBh, &full[s], b_hi(s), kb0 + i, n0 >> 3);
+        umma::tma_load_4d(&tBl, &full[s], b_lo(s), kb0 + i, n0 >> 3);
+      } else {
+        umma::tma_load_2d(&tBh, &full[s], b_hi(s), x, n0);
+        umma::tma_load_2d(&tBl, &full[s], b_lo(s), x, n0);
+      }
       ++issued;
     }
   } else if (warp == 1 && lane == 0) {
@@ -238,11 +244,17 @@ struct PairCfg {
   static_assert(STAGES * STAGE_BYTES >= 128 * (PBN + 1) * 4, "the ring stages the output tile");
 };
 
-template <int NPROD, int PBN>
+// MC pairs per cluster (1 or 2).  With two, the pairs of a cluster compute neighbouring
+// column tiles from the same A rows, and each A box is loaded once for both: the CTA of
+// the first pair multicasts A's high part, the CTA of the second its low part, to the
+// CTAs of the same rank in both pairs.  A stage is then free only when both pairs' MMAs
+// have read it: every MMA commit arrives on the empty barriers of all four CTAs.
+template <int NPROD, int PBN, int MC = 1>
 __global__ void __launch_bounds__(192, 1)
     k_gemm_pair(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                 const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
                 GemmArgs g) {
+  static_assert(MC == 1 || MC == 2, "one or two pairs per cluster");
   using Cfg = PairCfg<NPROD, PBN>;
   constexpr int ST = Cfg::STAGES;
   extern __shared__ __align__(16) unsigned char gsm_raw[];
@@ -251,7 +263,10 @@ __global__ void __launch_bounds__(192, 1)
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = umma::cluster_ctarank();  // 0: issues the MMAs
+  const uint32_t crank = umma::cluster_ctarank();
+  const uint32_t rank = crank & 1u;  // in the pair; 0 issues the pair's MMAs
+  const uint32_t pc = crank >> 1;    // the pair in the cluster
+  const uint16_t pair_mask = (uint16_t)(0x3u << (2 * pc)), all_mask = MC == 2 ? 0xF : 0x3;
   const int m0 = blockIdx.y * PBM, n0 = (blockIdx.x >> 1) * PBN;
   const int my_m = m0 + 128 * (int)rank;  // this CTA's rows of A and of the output
   const int my_n = n0 + (PBN / 2) * (int)rank;  // this CTA's rows of B
@@ -273,7 +288,7 @@ __global__ void __launch_bounds__(192, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       umma::mbar_init(&full[s], 1);
-      umma::mbar_init(&empty[s], 1);
+      umma::mbar_init(&empty[s], MC);
     }
     umma::mbar_init(&accf, 1);
     s_abort = 0;
@@ -296,12 +311,23 @@ __global__ void __launch_bounds__(192, 1)
         break;
       }
       if (rank == 0) umma::mbar_arrive_expect_tx(&full[s], 2 * Cfg::STAGE_BYTES);
-      const uint32_t bar = umma::cluster_addr(&full[s], 0);
+      const uint32_t bar = umma::cluster_addr(&full[s], (int)(crank & ~1u));
       const int x = (kb0 + i) * GBK;
-      umma::tma_load_2d_pair(&tAh, bar, a_hi(s), x, my_m);
-      if (NPROD == 3) umma::tma_load_2d_pair(&tAl, bar, a_lo(s), x, my_m);
-      umma::tma_load_2d_pair(&tBh, bar, b_hi(s), x, my_n);
-      umma::tma_load_2d_pair(&tBl, bar, b_lo(s), x, my_n);
+      if (MC == 1) {
+        umma::tma_load_2d_pair(&tAh, bar, a_hi(s), x, my_m);
+        if (NPROD == 3) umma::tma_load_2d_pair(&tAl, bar, a_lo(s), x, my_m);
+      } else {
+        const uint16_t amask = (uint16_t)((1u << crank) | (1u << (crank ^ 2u)));
+        if (pc == 0) umma::tma_load_2d_pair_mc(&tAh, bar, a_hi(s), x, my_m, amask);
+        if (NPROD == 3 && pc == 1) umma::tma_load_2d_pair_mc(&tAl, bar, a_lo(s), x, my_m, amask);
+      }
+      if (g.bblk) {
+        umma::tma_load_4d_pair(&tBh, bar, b_hi(s), kb0 + i, my_n >> 3);
+        umma::tma_load_4d_pair(&tBl, bar, b_lo(s), kb0 + i, my_n >> 3);
+      } else {
+        umma::tma_load_2d_pair(&tBh, bar, b_hi(s), x, my_n);
+        umma::tma_load_2d_pair(&tBl, bar, b_lo(s), x, my_n);
+      }
       ++issued;
     }
   } else if (warp == 1 && lane == 0 && rank == 0) {
@@ -325,9 +351,9 @@ __global__ void __launch_bounds__(192, 1)
         umma::mma_bf16_pair(tmem, dah + o, dbl + o, idesc, 1u);
         if (NPROD == 3) umma::mma_bf16_pair(tmem, dal + o, dbh + o, idesc, 1u);
       }
-      umma::mma_commit_pair(&empty[s], (uint16_t)0x3);
+      umma::mma_commit_pair(&empty[s], all_mask);
     }
-    umma::mma_commit_pair(&accf, (uint16_t)0x3);
+    umma::mma_commit_pair(&accf, pair_mask);
   } else if (warp >= 2) {
     // ---------------- epilogue (both CTAs): warp w reads TMEM lanes 32*(w%4) .. +31
     const bool ready = __all_sync(0xffffffffu, umma::mbar_wait(&accf, 0, g.timeout_ns));

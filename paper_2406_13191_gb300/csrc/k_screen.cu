@@ -163,6 +163,36 @@ __global__ void k_screen_gather_cols(int rows, int nk, int ld_src, int ld_dst, c
     dst[q] = c < (size_t)nk ? src[r * ld_src + kept[c]] : z;
   }
 }
+// The same gathers into the products' blocked B layout: element (r, c) of a rows x K
+// matrix at ((r / 8 * kb + c / 64) * 8 + r % 8) * 64 + c % 64 (kb = ceil(K / 64)), zero
+// outside it, so that a TMA box of 64 columns and 8 j rows is j contiguous 1 KB runs.
+__device__ __forceinline__ void blk_coords(size_t q, int kb, int* r, int* c) {
+  const size_t per = (size_t)kb * 512;
+  const size_t rb = q / per;
+  const int rem = (int)(q - rb * per);
+  *r = (int)rb * 8 + ((rem >> 6) & 7);
+  *c = (rem >> 9) * 64 + (rem & 63);
+}
+__global__ void k_screen_gather_rows_blk(int nk, int ng, int ld, int kb, const int* __restrict__ kept,
+                                         const __nv_bfloat16* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+  const size_t n = (size_t)((nk + 7) / 8) * kb * 512;
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    int r, c;
+    blk_coords(q, kb, &r, &c);
+    dst[q] = (r < nk && c < ng) ? src[(size_t)kept[r] * ld + c] : z;
+  }
+}
+__global__ void k_screen_gather_cols_blk(int rows, int nk, int ld_src, int kb, const int* __restrict__ kept,
+                                         const __nv_bfloat16* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+  const size_t n = (size_t)((rows + 7) / 8) * kb * 512;
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    int r, c;
+    blk_coords(q, kb, &r, &c);
+    dst[q] = (r < rows && c < nk) ? src[(size_t)r * ld_src + kept[c]] : z;
+  }
+}
 __global__ void k_screen_gather_lines(int nk, const int* __restrict__ kept, const float* __restrict__ a,
                                       const float* __restrict__ b, float* __restrict__ ca, float* __restrict__ cb) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nk; r += gridDim.x * blockDim.x) {
@@ -238,9 +268,13 @@ dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s) {
   std::vector<int> pos(nl, -1);
   for (int q = 0; q < nk; ++q) pos[kept[q]] = q;
   S.ready = false;
+  // the products' B operands in 8-row blocks of whole 64-column K blocks
+  const int kb_g = (ng + 63) / 64, kb_l = (nk + 63) / 64;
+  const size_t phi_bytes = (size_t)((nk + 7) / 8) * kb_g * 512 * 2;
+  const size_t phit_bytes = (size_t)((ng + 7) / 8) * kb_l * 512 * 2;
   if (S.kept.alloc((size_t)nk * sizeof(int)) != cudaSuccess || S.pos.alloc((size_t)nl * sizeof(int)) != cudaSuccess ||
-      S.phi_hi.alloc((size_t)nk * T.ld_g * 2) || S.phi_lo.alloc((size_t)nk * T.ld_g * 2) ||
-      S.phit_hi.alloc((size_t)ng * ld_lk * 2) || S.phit_lo.alloc((size_t)ng * ld_lk * 2) ||
+      S.phi_hi.alloc(phi_bytes) || S.phi_lo.alloc(phi_bytes) || S.phit_hi.alloc(phit_bytes) ||
+      S.phit_lo.alloc(phit_bytes) ||
       S.lim.alloc((size_t)2 * nk * sizeof(float))) {
     cudaGetLastError();
     return DCOPF_ERR_OOM;
@@ -249,31 +283,28 @@ dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s) {
       cudaMemcpyAsync(S.pos.p, pos.data(), (size_t)nl * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return DCOPF_ERR_CUDA;
   const int* kd = S.kept.as<int>();
-  k_screen_gather_rows<<<1024, 256, 0, s>>>(nk, T.ld_g, kd, T.phi_hi.as<__nv_bfloat16>(), S.phi_hi.as<__nv_bfloat16>());
-  k_screen_gather_rows<<<1024, 256, 0, s>>>(nk, T.ld_g, kd, T.phi_lo.as<__nv_bfloat16>(), S.phi_lo.as<__nv_bfloat16>());
-  k_screen_gather_cols<<<1024, 256, 0, s>>>(ng, nk, T.ld_l, ld_lk, kd, T.phit_hi.as<__nv_bfloat16>(),
-                                            S.phit_hi.as<__nv_bfloat16>());
-  k_screen_gather_cols<<<1024, 256, 0, s>>>(ng, nk, T.ld_l, ld_lk, kd, T.phit_lo.as<__nv_bfloat16>(),
-                                            S.phit_lo.as<__nv_bfloat16>());
+  k_screen_gather_rows_blk<<<1024, 256, 0, s>>>(nk, ng, T.ld_g, kb_g, kd, T.phi_hi.as<__nv_bfloat16>(),
+                                                S.phi_hi.as<__nv_bfloat16>());
+  k_screen_gather_rows_blk<<<1024, 256, 0, s>>>(nk, ng, T.ld_g, kb_g, kd, T.phi_lo.as<__nv_bfloat16>(),
+                                                S.phi_lo.as<__nv_bfloat16>());
+  k_screen_gather_cols_blk<<<1024, 256, 0, s>>>(ng, nk, T.ld_l, kb_l, kd, T.phit_hi.as<__nv_bfloat16>(),
+                                                S.phit_hi.as<__nv_bfloat16>());
+  k_screen_gather_cols_blk<<<1024, 256, 0, s>>>(ng, nk, T.ld_l, kb_l, kd, T.phit_lo.as<__nv_bfloat16>(),
+                                                S.phit_lo.as<__nv_bfloat16>());
   float* lim = S.lim.as<float>();
   k_screen_gather_lines<<<(nk + 255) / 256, 256, 0, s>>>(nk, kd, h->dev.fmax32, h->dev.fmin32, lim, lim + nk);
   h->launches += 5;
   if (cudaGetLastError() != cudaSuccess) return DCOPF_ERR_CUDA;
-  if (!tc_make_map(&S.m_phi_hi, S.phi_hi.p, nk, ng, T.ld_g) || !tc_make_map(&S.m_phi_lo, S.phi_lo.p, nk, ng, T.ld_g) ||
-      !tc_make_map(&S.m_phit_hi, S.phit_hi.p, ng, nk, ld_lk) ||
-      !tc_make_map(&S.m_phit_lo, S.phit_lo.p, ng, nk, ld_lk) ||
-      !tc_make_map_rows(&S.m_phi_hi96, S.phi_hi.p, nk, ng, T.ld_g, 96) ||
-      !tc_make_map_rows(&S.m_phi_lo96, S.phi_lo.p, nk, ng, T.ld_g, 96) ||
-      !tc_make_map_rows(&S.m_phit_hi96, S.phit_hi.p, ng, nk, ld_lk, 96) ||
-      !tc_make_map_rows(&S.m_phit_lo96, S.phit_lo.p, ng, nk, ld_lk, 96) ||
-      !tc_make_map_rows(&S.m_phi_hi80, S.phi_hi.p, nk, ng, T.ld_g, 80) ||
-      !tc_make_map_rows(&S.m_phi_lo80, S.phi_lo.p, nk, ng, T.ld_g, 80) ||
-      !tc_make_map_rows(&S.m_phit_hi80, S.phit_hi.p, ng, nk, ld_lk, 80) ||
-      !tc_make_map_rows(&S.m_phit_lo80, S.phit_lo.p, ng, nk, ld_lk, 80) ||
-      !tc_make_map_rows(&S.m_phi_hi72, S.phi_hi.p, nk, ng, T.ld_g, 72) ||
-      !tc_make_map_rows(&S.m_phi_lo72, S.phi_lo.p, nk, ng, T.ld_g, 72) ||
-      !tc_make_map_rows(&S.m_phit_hi72, S.phit_hi.p, ng, nk, ld_lk, 72) ||
-      !tc_make_map_rows(&S.m_phit_lo72, S.phit_lo.p, ng, nk, ld_lk, 72))
+  bool mok = true;
+  for (const uint32_t br : {128u, 96u, 80u, 72u}) {
+    CUtensorMap* fh = br == 128 ? &S.m_phi_hi : br == 96 ? &S.m_phi_hi96 : br == 80 ? &S.m_phi_hi80 : &S.m_phi_hi72;
+    CUtensorMap* fl = br == 128 ? &S.m_phi_lo : br == 96 ? &S.m_phi_lo96 : br == 80 ? &S.m_phi_lo80 : &S.m_phi_lo72;
+    CUtensorMap* ah = br == 128 ? &S.m_phit_hi : br == 96 ? &S.m_phit_hi96 : br == 80 ? &S.m_phit_hi80 : &S.m_phit_hi72;
+    CUtensorMap* al = br == 128 ? &S.m_phit_lo : br == 96 ? &S.m_phit_lo96 : br == 80 ? &S.m_phit_lo80 : &S.m_phit_lo72;
+    mok = mok && tc_make_map_blocked(fh, S.phi_hi.p, nk, ng, br) && tc_make_map_blocked(fl, S.phi_lo.p, nk, ng, br) &&
+          tc_make_map_blocked(ah, S.phit_hi.p, ng, nk, br) && tc_make_map_blocked(al, S.phit_lo.p, ng, nk, br);
+  }
+  if (!mok)
     return DCOPF_ERR_CUDA;
   S.nk = nk;
   S.ld_lk = ld_lk;

@@ -446,9 +446,11 @@ static cudaError_t prepare_gemm() {
   e = cudaFuncSetAttribute(k_gemm_bf16x<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)GemmCfg<3>::SMEM);
   if (e != cudaSuccess) return e;
-#define DCOPF_PAIR_SMEM(NP, BN)                                                                  \
-  if ((e = cudaFuncSetAttribute(k_gemm_pair<NP, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                (int)PairCfg<NP, BN>::SMEM)) != cudaSuccess)                        \
+#define DCOPF_PAIR_SMEM(NP, BN)                                                                     \
+  if ((e = cudaFuncSetAttribute(k_gemm_pair<NP, BN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                (int)PairCfg<NP, BN>::SMEM)) != cudaSuccess ||                         \
+      (e = cudaFuncSetAttribute(k_gemm_pair<NP, BN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                (int)PairCfg<NP, BN>::SMEM)) != cudaSuccess)                           \
     return e;
   DCOPF_PAIR_SMEM(2, 256)
   DCOPF_PAIR_SMEM(3, 256)
@@ -466,21 +468,25 @@ static cudaError_t prepare_gemm() {
 template <int NPROD, int PBN>
 static cudaError_t launch_gemm_pair(dcopf_dual* h, const CUtensorMap& Ah, const CUtensorMap& Al,
                                     const CUtensorMap& Bh, const CUtensorMap& Bl, GemmArgs g, int splits,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, int mc) {
+  // mc = 2: two pairs per cluster share their A boxes (the column tiles rounded up to an
+  // even count; a tile past N loads zeros and stores nothing)
+  const int pairs = (g.N + PBN - 1) / PBN;
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(2 * ((g.N + PBN - 1) / PBN), (g.M + PBM - 1) / PBM, splits);
+  cfg.gridDim = dim3(2 * ((pairs + mc - 1) / mc * mc), (g.M + PBM - 1) / PBM, splits);
   cfg.blockDim = dim3(192);
   cfg.dynamicSmemBytes = PairCfg<NPROD, PBN>::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.x = 2 * mc;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
   h->launches += 1;
-  return cudaLaunchKernelEx(&cfg, k_gemm_pair<NPROD, PBN>, Ah, Al, Bh, Bl, g);
+  if (mc == 2) return cudaLaunchKernelEx(&cfg, k_gemm_pair<NPROD, PBN, 2>, Ah, Al, Bh, Bl, g);
+  return cudaLaunchKernelEx(&cfg, k_gemm_pair<NPROD, PBN, 1>, Ah, Al, Bh, Bl, g);
 }
 
 template <int NPROD, int OCC = 1>
@@ -511,6 +517,7 @@ struct LineSet {
   const float* f0 = nullptr;       // [B][nl] base flows
   const int* kept = nullptr;       // [nl] network line of each row (null: all lines)
   const int* pos = nullptr;        // [n_line] row of each line or -1 (null: all lines)
+  int blocked = 0;                 // the B operands' maps are 4-D over 8-row blocks
 };
 
 static LineSet full_lines(dcopf_dual* h) {
@@ -531,27 +538,30 @@ static LineSet full_lines(dcopf_dual* h) {
 
 // `tiles`: 0 single CTAs (128 x 128), 1 / 2 / 3 / 4 CTA pairs of 256 x 256 / 192 / 160 / 144.
 // Ah / Al: the A operand's rows (the batch's, or one group's of it).
+// `tiles` 5 .. 8: the widths of 1 .. 4 with two pairs per cluster sharing A.
 static cudaError_t launch_adjoint(dcopf_dual* h, const LineSet& L, const CUtensorMap& Ah, const CUtensorMap& Al,
                                   const GemmArgs& g, int splits, int tiles, cudaStream_t s) {
-  if (tiles == 1) return launch_gemm_pair<3, 256>(h, Ah, Al, *L.phit_hi, *L.phit_lo, g, splits, s);
-  if (tiles == 2) return launch_gemm_pair<3, 192>(h, Ah, Al, *L.phit_hi96, *L.phit_lo96, g, splits, s);
-  if (tiles == 3) return launch_gemm_pair<3, 160>(h, Ah, Al, *L.phit_hi80, *L.phit_lo80, g, splits, s);
-  if (tiles == 4) return launch_gemm_pair<3, 144>(h, Ah, Al, *L.phit_hi72, *L.phit_lo72, g, splits, s);
+  const int mc = tiles > 4 ? 2 : 1, w = tiles > 4 ? tiles - 4 : tiles;
+  if (w == 1) return launch_gemm_pair<3, 256>(h, Ah, Al, *L.phit_hi, *L.phit_lo, g, splits, s, mc);
+  if (w == 2) return launch_gemm_pair<3, 192>(h, Ah, Al, *L.phit_hi96, *L.phit_lo96, g, splits, s, mc);
+  if (w == 3) return launch_gemm_pair<3, 160>(h, Ah, Al, *L.phit_hi80, *L.phit_lo80, g, splits, s, mc);
+  if (w == 4) return launch_gemm_pair<3, 144>(h, Ah, Al, *L.phit_hi72, *L.phit_lo72, g, splits, s, mc);
   return launch_gemm<3>(h, Ah, Al, *L.phit_hi, *L.phit_lo, g, splits, s);
 }
 static cudaError_t launch_forward(dcopf_dual* h, const LineSet& L, const CUtensorMap& Ah, const CUtensorMap& Al,
                                   const GemmArgs& g, int tiles, cudaStream_t s) {
+  const int mc = tiles > 4 ? 2 : 1, w = tiles > 4 ? tiles - 4 : tiles;
   if (h->host.qp) {
-    if (tiles == 1) return launch_gemm_pair<3, 256>(h, Ah, Al, *L.phi_hi, *L.phi_lo, g, 1, s);
-    if (tiles == 2) return launch_gemm_pair<3, 192>(h, Ah, Al, *L.phi_hi96, *L.phi_lo96, g, 1, s);
-    if (tiles == 3) return launch_gemm_pair<3, 160>(h, Ah, Al, *L.phi_hi80, *L.phi_lo80, g, 1, s);
-    if (tiles == 4) return launch_gemm_pair<3, 144>(h, Ah, Al, *L.phi_hi72, *L.phi_lo72, g, 1, s);
+    if (w == 1) return launch_gemm_pair<3, 256>(h, Ah, Al, *L.phi_hi, *L.phi_lo, g, 1, s, mc);
+    if (w == 2) return launch_gemm_pair<3, 192>(h, Ah, Al, *L.phi_hi96, *L.phi_lo96, g, 1, s, mc);
+    if (w == 3) return launch_gemm_pair<3, 160>(h, Ah, Al, *L.phi_hi80, *L.phi_lo80, g, 1, s, mc);
+    if (w == 4) return launch_gemm_pair<3, 144>(h, Ah, Al, *L.phi_hi72, *L.phi_lo72, g, 1, s, mc);
     return launch_gemm<3>(h, Ah, Al, *L.phi_hi, *L.phi_lo, g, 1, s);
   }
-  if (tiles == 1) return launch_gemm_pair<2, 256>(h, Ah, Al, *L.phi_hi, *L.phi_lo, g, 1, s);
-  if (tiles == 2) return launch_gemm_pair<2, 192>(h, Ah, Al, *L.phi_hi96, *L.phi_lo96, g, 1, s);
-  if (tiles == 3) return launch_gemm_pair<2, 160>(h, Ah, Al, *L.phi_hi80, *L.phi_lo80, g, 1, s);
-  if (tiles == 4) return launch_gemm_pair<2, 144>(h, Ah, Al, *L.phi_hi72, *L.phi_lo72, g, 1, s);
+  if (w == 1) return launch_gemm_pair<2, 256>(h, Ah, Al, *L.phi_hi, *L.phi_lo, g, 1, s, mc);
+  if (w == 2) return launch_gemm_pair<2, 192>(h, Ah, Al, *L.phi_hi96, *L.phi_lo96, g, 1, s, mc);
+  if (w == 3) return launch_gemm_pair<2, 160>(h, Ah, Al, *L.phi_hi80, *L.phi_lo80, g, 1, s, mc);
+  if (w == 4) return launch_gemm_pair<2, 144>(h, Ah, Al, *L.phi_hi72, *L.phi_lo72, g, 1, s, mc);
   // the LP forward on single CTAs (two products: x is exact in BF16): its K = n_gen is
   // short, so a CTA spends much of its time in the epilogue; two CTAs per SM (a 2-stage
   // ring each) let one CTA's epilogue run beside the other's main loop
@@ -614,6 +624,18 @@ bool tc_make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, 
 bool tc_make_map_rows(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint64_t ld,
                       uint32_t box_rows) {
   return make_map(m, ptr, rows, cols, ld, box_rows);
+}
+bool tc_make_map_blocked(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t K, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || ((uintptr_t)ptr & 15) || box_rows % 8 || box_rows > 256) return false;
+  const uint64_t kb = (K + 63) / 64, rb = (rows + 7) / 8;
+  cuuint64_t dims[4] = {64, 8, kb, rb};
+  cuuint64_t strides[3] = {128, 1024, kb * 1024};
+  cuuint32_t box[4] = {64, 8, 1, box_rows / 8};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // P[s][m][ldp] = the K-slice s of A[m][:] . B[n][:] (BF16 hi/lo split operands, three
@@ -1261,8 +1283,11 @@ static dcopf_status tune_view_shapes(TensorRun& R, IterView& V, cudaStream_t cs,
       const int ptiles = ((B + PBM - 1) / PBM) * ((ng + bn - 1) / bn);
       const int slots = h->sm_count / 2;  // one pair per two SMs
       const int s0 = std::max(1, (slots + ptiles - 1) / ptiles);
-      for (int num : {2, 3, 4, 6}) add(tv, (s0 * num + 2) / 4);
-      for (int wv = 1; wv <= 3; ++wv) add(tv, wv * slots / ptiles);
+      for (int mc : {0, 4})  // one pair per cluster, or two sharing A
+        if (mc == 0 || ptiles >= 2) {
+          for (int num : {2, 3, 4, 6}) add(tv + mc, (s0 * num + 2) / 4);
+          for (int wv = 1; wv <= 3; ++wv) add(tv + mc, wv * slots / ptiles);
+        }
     }
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1284,8 +1309,9 @@ static dcopf_status tune_view_shapes(TensorRun& R, IterView& V, cudaStream_t cs,
     }
     return DCOPF_OK;
   };
-  static const char* kTiles[5] = {"single 128x128", "pairs 256x256", "pairs 256x192", "pairs 256x160",
-                                  "pairs 256x144"};
+  static const char* kTiles[9] = {"single 128x128", "pairs 256x256", "pairs 256x192", "pairs 256x160",
+                                  "pairs 256x144", "2 pairs 256x256", "2 pairs 256x192", "2 pairs 256x160",
+                                  "2 pairs 256x144"};
   float best = 1e30f, second = 1e30f;
   Cand bc = cand.empty() ? Cand{0, 1} : cand[0], bc2{-1, 1};
   int best_per = (kb + bc.splits - 1) / bc.splits, per2 = 1;
@@ -1326,8 +1352,12 @@ static dcopf_status tune_view_shapes(TensorRun& R, IterView& V, cudaStream_t cs,
   int fwd = (pair_ok && !single_ok) ? tv_lo : 0, fwd2 = -1;
   if (res == DCOPF_OK && pair_ok) {
     float bf = 1e30f, bf2 = 1e30f;
-    for (int tv = single_ok ? 0 : tv_lo; tv <= tv_hi && res == DCOPF_OK; ++tv) {
-      if (tv > 0 && tv < tv_lo) continue;
+    std::vector<int> tvs;
+    if (single_ok) tvs.push_back(0);
+    for (int tv = tv_lo; tv <= tv_hi; ++tv) tvs.push_back(tv);
+    for (int tv = tv_lo; tv <= tv_hi; ++tv) tvs.push_back(tv + 4);
+    for (int tv : tvs) {
+      if (res != DCOPF_OK) break;
       float ms = 0.f;
       res = timed([&] { return launch_forward(h, R.ls, V.Xh, V.Xl, V.gf, tv, cs); }, &ms);
       if (h->verbose) fprintf(stderr, "dcopf: batch %d forward %s: %.1f us\n", B, kTiles[tv], 1e3f * ms / 3.f);
@@ -1485,6 +1515,7 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
     L.f0 = S.f0c.as<float>();
     L.kept = S.kept.as<int>();
     L.pos = S.pos.as<int>();
+    L.blocked = 1;
   }
   const int nl = R.ls.nl;
   R.n_tiles = (nl + STEP_SLICE - 1) / STEP_SLICE;
@@ -1516,6 +1547,7 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   gf.M = B; gf.N = nl; gf.K = ng; gf.kb_per_split = (ng + GBK - 1) / GBK; gf.epi = EPI_TILE;
   gf.F32 = h->bb.F.as<float>(); gf.ldf32 = ldF;
   gf.err = h->d_err; gf.timeout_ns = 2000000000ull;
+  ga.bblk = gf.bblk = R.ls.blocked;
   StepEpi& E = R.E;
   E.P = to_float_args(P); E.F = gf.F32; E.ldF = ldF; E.f0 = R.ls.f0; E.u = w.u32.as<float>();
   E.outage = R.it.outage; E.tout = bb.tout;

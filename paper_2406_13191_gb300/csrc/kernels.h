@@ -452,6 +452,10 @@ dcopf_status solve_tensor(dcopf_dual* h, int batch, const double* loads, const i
 bool tc_make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint64_t ld);
 bool tc_make_map_rows(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint64_t ld,
                       uint32_t box_rows);
+// A 4-D map over a rows x K BF16 matrix held in 8-row blocks of 64-column K blocks
+// (element (r, c) at ((r / 8 * KB + c / 64) * 8 + r % 8) * 64 + c % 64, KB = ceil(K / 64)):
+// dims {64, 8, KB, ceil(rows / 8)}, box {64, 8, 1, box_rows / 8}, 128-byte swizzle.
+bool tc_make_map_blocked(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t K, uint32_t box_rows);
 // Constraint screening of a batch (k_screen.cu): base flows in ws.f0, demands in
 // ws.demand; leaves h->scr ready with the kept lines and their compact operands.
 dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s);

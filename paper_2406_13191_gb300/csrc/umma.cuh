@@ -123,6 +123,14 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* ba
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// A box {64 columns, 8 rows, K block kb, row blocks from rb} of a 4-D map.
+__device__ __forceinline__ void tma_load_4d(const CUtensorMap* map, uint64_t* bar, void* dst, int kb, int rb) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(0), "r"(kb), "r"(rb), "r"(smem_u32(bar))
+      : "memory");
+}
 
 // ------------------------------------------------------------------ tcgen05
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
@@ -194,6 +202,28 @@ __device__ __forceinline__ void tma_load_2d_pair(const CUtensorMap* map, uint32_
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// The same load multicast to the CTAs of `cta_mask` (this CTA among them): the box lands
+// at dst's offset in each, and each one's completion is counted on the mbarrier at bar's
+// offset in the even-ranked CTA of that destination's pair (bar must name an even CTA).
+__device__ __forceinline__ void tma_load_2d_pair_mc(const CUtensorMap* map, uint32_t bar, void* dst, int x,
+                                                    int y, uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      ".cta_group::2 [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar), "h"(cta_mask)
+      : "memory");
+}
+// A box of a 4-D map (the products' blocked B operand: 64 columns x 8 rows x 1 K block
+// x nb row blocks), counted like tma_load_2d_pair; it lands in shared memory as the
+// 8 nb rows of 64 columns that a 2-D box of 8 nb rows would give.
+__device__ __forceinline__ void tma_load_4d_pair(const CUtensorMap* map, uint32_t bar, void* dst, int kb,
+                                                 int rb) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%2, %2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(0), "r"(kb), "r"(rb), "r"(bar)
       : "memory");
 }
 __device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst_smem, uint32_t ncols) {

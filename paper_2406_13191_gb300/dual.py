@@ -204,7 +204,8 @@ class DcopfDual:
         """``dcopf_dual_tensor_shapes``: the product shapes of the last batched solve."""
         v = (C.c_int32 * 7)()
         _lib.check(self.lib.dcopf_dual_tensor_shapes(self.h, v), "dcopf_dual_tensor_shapes")
-        tiles = ("single 128x128", "pairs 256x256", "pairs 256x192", "pairs 256x160", "pairs 256x144")
+        tiles = ("single 128x128", "pairs 256x256", "pairs 256x192", "pairs 256x160", "pairs 256x144",
+                 "2 pairs 256x256", "2 pairs 256x192", "2 pairs 256x160", "2 pairs 256x144")
         return {"batch": v[0], "lines": v[1], "adjoint": tiles[v[2]], "adjoint_split_k": v[3],
                 "forward": tiles[v[4]], "branches": v[5], "first_group": v[6],
                 "code": f"{v[2]},{v[3]},{v[4]},{v[5]}"}
