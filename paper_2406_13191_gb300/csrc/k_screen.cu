@@ -144,28 +144,9 @@ __global__ void k_screen_cover(int nl, const unsigned char* __restrict__ keep, c
     if (keep[l] && pos[l] < 0) *flag = 1;
 }
 
-// Compact BF16 operands of the kept lines: rows of the forward operand [n_line][ld_g]
-// and columns (the K dimension) of the adjoint operand [n_gen][ld_l].
-__global__ void k_screen_gather_rows(int nk, int ld, const int* __restrict__ kept,
-                                     const __nv_bfloat16* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
-  const size_t n = (size_t)nk * ld;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t r = q / ld, c = q - r * ld;
-    dst[q] = src[(size_t)kept[r] * ld + c];
-  }
-}
-__global__ void k_screen_gather_cols(int rows, int nk, int ld_src, int ld_dst, const int* __restrict__ kept,
-                                     const __nv_bfloat16* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
-  const size_t n = (size_t)rows * ld_dst;
-  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t r = q / ld_dst, c = q - r * ld_dst;
-    dst[q] = c < (size_t)nk ? src[r * ld_src + kept[c]] : z;
-  }
-}
-// The same gathers into the products' blocked B layout: element (r, c) of a rows x K
-// matrix at ((r / 8 * kb + c / 64) * 8 + r % 8) * 64 + c % 64 (kb = ceil(K / 64)), zero
-// outside it, so that a TMA box of 64 columns and 8 j rows is j contiguous 1 KB runs.
+// The products' B operands of the kept lines, from the network's (both in the blocked
+// layout of blk_index, zero outside the matrix): rows of Phi~ (nk of n_line, K = ng)
+// and columns of Phi~^T (ng rows, K = nk of n_line).
 __device__ __forceinline__ void blk_coords(size_t q, int kb, int* r, int* c) {
   const size_t per = (size_t)kb * 512;
   const size_t rb = q / per;
@@ -173,24 +154,24 @@ __device__ __forceinline__ void blk_coords(size_t q, int kb, int* r, int* c) {
   *r = (int)rb * 8 + ((rem >> 6) & 7);
   *c = (rem >> 9) * 64 + (rem & 63);
 }
-__global__ void k_screen_gather_rows_blk(int nk, int ng, int ld, int kb, const int* __restrict__ kept,
+__global__ void k_screen_gather_rows_blk(int nk, int ng, int kb, const int* __restrict__ kept,
                                          const __nv_bfloat16* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
   const size_t n = (size_t)((nk + 7) / 8) * kb * 512;
   const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
     int r, c;
     blk_coords(q, kb, &r, &c);
-    dst[q] = (r < nk && c < ng) ? src[(size_t)kept[r] * ld + c] : z;
+    dst[q] = (r < nk && c < ng) ? src[blk_index(kept[r], c, kb)] : z;
   }
 }
-__global__ void k_screen_gather_cols_blk(int rows, int nk, int ld_src, int kb, const int* __restrict__ kept,
+__global__ void k_screen_gather_cols_blk(int rows, int nk, int kb_src, int kb, const int* __restrict__ kept,
                                          const __nv_bfloat16* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
   const size_t n = (size_t)((rows + 7) / 8) * kb * 512;
   const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
     int r, c;
     blk_coords(q, kb, &r, &c);
-    dst[q] = (r < rows && c < nk) ? src[(size_t)r * ld_src + kept[c]] : z;
+    dst[q] = (r < rows && c < nk) ? src[blk_index(r, kept[c], kb_src)] : z;
   }
 }
 __global__ void k_screen_gather_lines(int nk, const int* __restrict__ kept, const float* __restrict__ a,
@@ -283,13 +264,14 @@ dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s) {
       cudaMemcpyAsync(S.pos.p, pos.data(), (size_t)nl * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return DCOPF_ERR_CUDA;
   const int* kd = S.kept.as<int>();
-  k_screen_gather_rows_blk<<<1024, 256, 0, s>>>(nk, ng, T.ld_g, kb_g, kd, T.phi_hi.as<__nv_bfloat16>(),
+  const int kb_n = (nl + 63) / 64;  // K blocks of the network's Phi~^T
+  k_screen_gather_rows_blk<<<1024, 256, 0, s>>>(nk, ng, kb_g, kd, T.phi_hi.as<__nv_bfloat16>(),
                                                 S.phi_hi.as<__nv_bfloat16>());
-  k_screen_gather_rows_blk<<<1024, 256, 0, s>>>(nk, ng, T.ld_g, kb_g, kd, T.phi_lo.as<__nv_bfloat16>(),
+  k_screen_gather_rows_blk<<<1024, 256, 0, s>>>(nk, ng, kb_g, kd, T.phi_lo.as<__nv_bfloat16>(),
                                                 S.phi_lo.as<__nv_bfloat16>());
-  k_screen_gather_cols_blk<<<1024, 256, 0, s>>>(ng, nk, T.ld_l, kb_l, kd, T.phit_hi.as<__nv_bfloat16>(),
+  k_screen_gather_cols_blk<<<1024, 256, 0, s>>>(ng, nk, kb_n, kb_l, kd, T.phit_hi.as<__nv_bfloat16>(),
                                                 S.phit_hi.as<__nv_bfloat16>());
-  k_screen_gather_cols_blk<<<1024, 256, 0, s>>>(ng, nk, T.ld_l, kb_l, kd, T.phit_lo.as<__nv_bfloat16>(),
+  k_screen_gather_cols_blk<<<1024, 256, 0, s>>>(ng, nk, kb_n, kb_l, kd, T.phit_lo.as<__nv_bfloat16>(),
                                                 S.phit_lo.as<__nv_bfloat16>());
   float* lim = S.lim.as<float>();
   k_screen_gather_lines<<<(nk + 255) / 256, 256, 0, s>>>(nk, kd, h->dev.fmax32, h->dev.fmin32, lim, lim + nk);

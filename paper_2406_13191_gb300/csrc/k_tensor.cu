@@ -362,8 +362,9 @@ static bool make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t co
 static int round8(int n) { return (n + 7) & ~7; }
 static cudaError_t prepare_gemm();
 
-// BF16 hi/lo copies of Phi~ (forward B operand, [n_line][ld_g]) and Phi~^T (adjoint B
-// operand, [n_gen][ld_l]), built once per handle.
+// BF16 hi/lo copies of Phi~ (forward B operand, n_line x n_gen) and Phi~^T (adjoint B
+// operand, n_gen x n_line), built once per handle, in 8-row blocks of 64-column K blocks
+// (blk_index): a TMA box of 64 columns and 8 j rows is then j contiguous 1 KB runs.
 dcopf_status ensure_tensor_operands(dcopf_dual* h) {
   TensorOps& T = h->tops;
   if (T.ready) return DCOPF_OK;
@@ -371,18 +372,18 @@ dcopf_status ensure_tensor_operands(dcopf_dual* h) {
   const int nl = H.n_line, ng = H.n_gen;
   T.ld_l = round8(nl);
   T.ld_g = round8(ng);
-  std::vector<__nv_bfloat16> ph((size_t)nl * T.ld_g), pl((size_t)nl * T.ld_g);
-  std::vector<__nv_bfloat16> th((size_t)ng * T.ld_l), tl((size_t)ng * T.ld_l);
+  const int kb_g = (ng + 63) / 64, kb_l = (nl + 63) / 64;
   const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
-  std::fill(ph.begin(), ph.end(), z); std::fill(pl.begin(), pl.end(), z);
-  std::fill(th.begin(), th.end(), z); std::fill(tl.begin(), tl.end(), z);
+  std::vector<__nv_bfloat16> ph((size_t)round8(nl) * kb_g * 64, z), pl(ph.size(), z);
+  std::vector<__nv_bfloat16> th((size_t)round8(ng) * kb_l * 64, z), tl(th.size(), z);
   for (int i = 0; i < nl; ++i)
     for (int j = 0; j < ng; ++j) {
       const float v = (float)H.phi[(size_t)i * ng + j];
       const __nv_bfloat16 hi = __float2bfloat16_rn(v);
       const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-      ph[(size_t)i * T.ld_g + j] = hi; pl[(size_t)i * T.ld_g + j] = lo;
-      th[(size_t)j * T.ld_l + i] = hi; tl[(size_t)j * T.ld_l + i] = lo;
+      const size_t f = blk_index(i, j, kb_g), a = blk_index(j, i, kb_l);
+      ph[f] = hi; pl[f] = lo;
+      th[a] = hi; tl[a] = lo;
     }
   auto up = [&](DBuf& d, const std::vector<__nv_bfloat16>& v) {
     if (d.alloc(v.size() * 2) != cudaSuccess) return false;
@@ -390,23 +391,16 @@ dcopf_status ensure_tensor_operands(dcopf_dual* h) {
   };
   if (!up(T.phi_hi, ph) || !up(T.phi_lo, pl) || !up(T.phit_hi, th) || !up(T.phit_lo, tl))
     return DCOPF_ERR_OOM;
-  if (!make_map(&T.m_phi_hi, T.phi_hi.p, nl, ng, T.ld_g, GBN) ||
-      !make_map(&T.m_phi_lo, T.phi_lo.p, nl, ng, T.ld_g, GBN) ||
-      !make_map(&T.m_phit_hi, T.phit_hi.p, ng, nl, T.ld_l, GBN) ||
-      !make_map(&T.m_phit_lo, T.phit_lo.p, ng, nl, T.ld_l, GBN) ||
-      !make_map(&T.m_phi_hi96, T.phi_hi.p, nl, ng, T.ld_g, 96) ||
-      !make_map(&T.m_phi_lo96, T.phi_lo.p, nl, ng, T.ld_g, 96) ||
-      !make_map(&T.m_phit_hi96, T.phit_hi.p, ng, nl, T.ld_l, 96) ||
-      !make_map(&T.m_phit_lo96, T.phit_lo.p, ng, nl, T.ld_l, 96) ||
-      !make_map(&T.m_phi_hi80, T.phi_hi.p, nl, ng, T.ld_g, 80) ||
-      !make_map(&T.m_phi_lo80, T.phi_lo.p, nl, ng, T.ld_g, 80) ||
-      !make_map(&T.m_phit_hi80, T.phit_hi.p, ng, nl, T.ld_l, 80) ||
-      !make_map(&T.m_phit_lo80, T.phit_lo.p, ng, nl, T.ld_l, 80) ||
-      !make_map(&T.m_phi_hi72, T.phi_hi.p, nl, ng, T.ld_g, 72) ||
-      !make_map(&T.m_phi_lo72, T.phi_lo.p, nl, ng, T.ld_g, 72) ||
-      !make_map(&T.m_phit_hi72, T.phit_hi.p, ng, nl, T.ld_l, 72) ||
-      !make_map(&T.m_phit_lo72, T.phit_lo.p, ng, nl, T.ld_l, 72))
-    return DCOPF_ERR_CUDA;
+  bool mok = true;
+  for (const uint32_t br : {128u, 96u, 80u, 72u}) {
+    CUtensorMap* fh = br == 128 ? &T.m_phi_hi : br == 96 ? &T.m_phi_hi96 : br == 80 ? &T.m_phi_hi80 : &T.m_phi_hi72;
+    CUtensorMap* fl = br == 128 ? &T.m_phi_lo : br == 96 ? &T.m_phi_lo96 : br == 80 ? &T.m_phi_lo80 : &T.m_phi_lo72;
+    CUtensorMap* ah = br == 128 ? &T.m_phit_hi : br == 96 ? &T.m_phit_hi96 : br == 80 ? &T.m_phit_hi80 : &T.m_phit_hi72;
+    CUtensorMap* al = br == 128 ? &T.m_phit_lo : br == 96 ? &T.m_phit_lo96 : br == 80 ? &T.m_phit_lo80 : &T.m_phit_lo72;
+    mok = mok && tc_make_map_blocked(fh, T.phi_hi.p, nl, ng, br) && tc_make_map_blocked(fl, T.phi_lo.p, nl, ng, br) &&
+          tc_make_map_blocked(ah, T.phit_hi.p, ng, nl, br) && tc_make_map_blocked(al, T.phit_lo.p, ng, nl, br);
+  }
+  if (!mok) return DCOPF_ERR_CUDA;
   if (prepare_gemm() != cudaSuccess) return DCOPF_ERR_CUDA;
   T.ready = true;
   return DCOPF_OK;
@@ -533,6 +527,7 @@ static LineSet full_lines(dcopf_dual* h) {
   L.fmax = h->dev.fmax32;
   L.fmin = h->dev.fmin32;
   L.f0 = h->ws.f0_32.as<float>();
+  L.blocked = 1;
   return L;
 }
 
@@ -604,6 +599,7 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
   GemmArgs g{};
   g.M = B; g.N = ng; g.K = nl; g.kb_per_split = kbps; g.epi = EPI_PARTIAL;
   g.P = T.P.as<float>(); g.ldp = (ng + 3) & ~3; g.err = h->d_err; g.timeout_ns = 2000000000ull;
+  g.bblk = L.blocked;
   if (launch_adjoint(h, L, *L.H_hi, *L.H_lo, g, splits, pair_adj, s) != cudaSuccess) return DCOPF_ERR_CUDA;
   k_reduce_min<<<B, 256, 0, s>>>(h->dev, splits, B, g.ldp, T.P.as<float>(), lambda, T.ld_g,
                                  T.X_hi.as<__nv_bfloat16>(), T.X_lo.as<__nv_bfloat16>(),
@@ -613,6 +609,7 @@ dcopf_status run_eval_tensor(dcopf_dual* h, int B, const int* outage, const doub
   f.M = B; f.N = nl; f.K = ng; f.kb_per_split = (ng + GBK - 1) / GBK; f.epi = EPI_FLOW;
   f.f0 = w.f0.as<double>(); f.f = w.f.as<double>(); f.ldf = nl; f.err = h->d_err;
   f.timeout_ns = 2000000000ull;
+  f.bblk = L.blocked;
   if (launch_forward(h, L, T.m_X_hi, T.m_X_lo, f, pair_fwd, s) != cudaSuccess) return DCOPF_ERR_CUDA;
   return run_eval_finish(h, B, outage, lambda, mh, ml, value, glam, ghi, glo, dispatch, s);
 }
@@ -689,7 +686,7 @@ static int minimize_threads(const dcopf_dual* h, int B) {
 // pi~ from the split-K partials, minimiser, BF16 split of x, per-instance cost and
 // dispatch, the pre-outage flow (Phi~ x)_k of an outaged line, the step factors of
 // this step (running powers), and the lambda step (Section 3.3).
-template <int SG>
+template <int SG, int MG>
 __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M, int ldp,
                                               const float* __restrict__ P, const SolveStateBase& st,
                                               const BatchView& bb, const StepArgs& SP, int ldx,
@@ -741,39 +738,46 @@ __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M
   const float lamf = (float)lam;
   float c = 0.f, p = 0.f, to = 0.f;
   const float kk = (float)(st.iter[b] + 1), wk = kk * kk;  // weight of the mean of the minimisers
-  const int nt = blockDim.x;
-  // two generators per thread and loop, every load in flight before the arithmetic;
-  // split-K partials summed in split order, SG at a time (a missing term adds +0)
-  for (int ja = threadIdx.x; ja < ng; ja += 2 * nt) {
-    const int jb = ja + nt;
-    const bool vb = jb < ng;
-    float sa = 0.f, sb = 0.f;
+  // MG generators per thread and pass, every split-K partial of a group of SG splits in
+  // flight before the arithmetic, summed in split order (a missing term adds +0).  While
+  // warp 0 runs the value and stop tests, the other warps take all the generators.
+  const bool w0_busy = pend && !st.xsum;
+  const int nt = w0_busy ? (int)blockDim.x - 32 : (int)blockDim.x;
+  const int tg = w0_busy ? (int)threadIdx.x - 32 : (int)threadIdx.x;
+  auto gen = [&](int j, float sj) {
+    const float4 g = N.gen4[j];   // sigma, ctil, mq, cconst
+    const float2 g2 = N.gen2[j];  // mid, 1 / (2 mq) (0 for a linear cost)
+    if (k >= 0) sj = fmaf(N.phi32[(size_t)k * ng + j], ueta, sj);
+    const float w = fmaf(g.x, lamf, g.y) + sj;
+    // the closed-form minimiser of eq. (6) / (16) on the normalised box [-1, 1]
+    const float x = g.z > 0.f ? fminf(1.f, fmaxf(-1.f, -w * g2.y)) : (w > 0.f ? -1.f : (w < 0.f ? 1.f : 0.f));
+    if (st.xsum) st.xsum[(size_t)b * ng + j] += wk * x;
+    split_bf16(x, Xh + (size_t)b * ldx + j, Xl + (size_t)b * ldx + j);
+    c += fmaf(fmaf(g.z, x, g.y), x, g.w);
+    p += fmaf(g.x, x, g2.x);
+    if (k >= 0) to = fmaf(N.phi32[(size_t)k * ng + j], x, to);
+  };
+  for (int j0 = tg; tg >= 0 && j0 < ng; j0 += MG * nt) {
+    float sg[MG];
+#pragma unroll
+    for (int u = 0; u < MG; ++u) sg[u] = 0.f;
     for (int q0 = 0; q0 < splits; q0 += SG) {
-      float ta[SG], tb[SG];
+      float t[SG][MG];
 #pragma unroll
-      for (int u = 0; u < SG; ++u) {
-        const size_t row = ((size_t)(q0 + u) * M + b) * ldp;
-        ta[u] = q0 + u < splits ? P[row + ja] : 0.f;
-        tb[u] = (q0 + u < splits && vb) ? P[row + jb] : 0.f;
-      }
+      for (int v = 0; v < SG; ++v)
 #pragma unroll
-      for (int u = 0; u < SG; ++u) { sa += ta[u]; sb += tb[u]; }
+        for (int u = 0; u < MG; ++u) {
+          const int j = j0 + u * nt;
+          t[v][u] = (q0 + v < splits && j < ng) ? P[((size_t)(q0 + v) * M + b) * ldp + j] : 0.f;
+        }
+#pragma unroll
+      for (int v = 0; v < SG; ++v)
+#pragma unroll
+        for (int u = 0; u < MG; ++u) sg[u] += t[v][u];
     }
-    auto gen = [&](int j, float sj) {
-      const float4 g = N.gen4[j];   // sigma, ctil, mq, cconst
-      const float2 g2 = N.gen2[j];  // mid, 1 / (2 mq) (0 for a linear cost)
-      if (k >= 0) sj = fmaf(N.phi32[(size_t)k * ng + j], ueta, sj);
-      const float w = fmaf(g.x, lamf, g.y) + sj;
-      // the closed-form minimiser of eq. (6) / (16) on the normalised box [-1, 1]
-      const float x = g.z > 0.f ? fminf(1.f, fmaxf(-1.f, -w * g2.y)) : (w > 0.f ? -1.f : (w < 0.f ? 1.f : 0.f));
-      if (st.xsum) st.xsum[(size_t)b * ng + j] += wk * x;
-      split_bf16(x, Xh + (size_t)b * ldx + j, Xl + (size_t)b * ldx + j);
-      c += fmaf(fmaf(g.z, x, g.y), x, g.w);
-      p += fmaf(g.x, x, g2.x);
-      if (k >= 0) to = fmaf(N.phi32[(size_t)k * ng + j], x, to);
-    };
-    gen(ja, sa);
-    if (vb) gen(jb, sb);
+#pragma unroll
+    for (int u = 0; u < MG; ++u)
+      if (j0 + u * nt < ng) gen(j0 + u * nt, sg[u]);
   }
   c = warp_sum(c); p = warp_sum(p); to = warp_sum(to);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -841,9 +845,9 @@ __global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
   __shared__ double red[3 * (MIN_MAX_THREADS / 32)];
   for (int b = blockIdx.x; b < M; b += gridDim.x) {
     if (splits <= 4)
-      minimize_item<4>(N, splits, M, ldp, P, st, bb, SP, ldx, Xh, Xl, outage, demand, max_iters, tol, b, red);
+      minimize_item<4, 6>(N, splits, M, ldp, P, st, bb, SP, ldx, Xh, Xl, outage, demand, max_iters, tol, b, red);
     else
-      minimize_item<8>(N, splits, M, ldp, P, st, bb, SP, ldx, Xh, Xl, outage, demand, max_iters, tol, b, red);
+      minimize_item<3, 6>(N, splits, M, ldp, P, st, bb, SP, ldx, Xh, Xl, outage, demand, max_iters, tol, b, red);
     __syncthreads();  // red is read by warp 0 before the next instance's partials land
   }
 }
@@ -1515,7 +1519,6 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
     L.f0 = S.f0c.as<float>();
     L.kept = S.kept.as<int>();
     L.pos = S.pos.as<int>();
-    L.blocked = 1;
   }
   const int nl = R.ls.nl;
   R.n_tiles = (nl + STEP_SLICE - 1) / STEP_SLICE;

@@ -456,6 +456,9 @@ bool tc_make_map_rows(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t c
 // (element (r, c) at ((r / 8 * KB + c / 64) * 8 + r % 8) * 64 + c % 64, KB = ceil(K / 64)):
 // dims {64, 8, KB, ceil(rows / 8)}, box {64, 8, 1, box_rows / 8}, 128-byte swizzle.
 bool tc_make_map_blocked(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t K, uint32_t box_rows);
+__host__ __device__ inline size_t blk_index(int r, int c, int kb) {
+  return ((size_t)(r >> 3) * kb + (c >> 6)) * 512 + (size_t)(r & 7) * 64 + (c & 63);
+}
 // Constraint screening of a batch (k_screen.cu): base flows in ws.f0, demands in
 // ws.demand; leaves h->scr ready with the kept lines and their compact operands.
 dcopf_status screen_batch(dcopf_dual* h, int B, cudaStream_t s);
