@@ -45,11 +45,11 @@ GAP = 1e-3
 BATCH = 256
 # ascent settings of the headline (Adam, Section 3.3): the best of the Adam grid of
 # bench.py --figure-sweeps (Fig. 4 and a joint refinement) on the first 64 instances of
-# this batch, 158 iterations to the gap there (profiles/optimizer_study.md)
+# this batch, 158 iterations to the gap there
 OURS = dict(rule="adam", alpha=3000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=4000,
             path="batched", precision="bf16x3", screen=True)
 # Algorithm 1 (heavy-ball GDM) on the plain FP64 path, with the settings of the GDM sweep
-# on the first 64 instances of this batch (bench.py --figure-sweeps, profiles/optimizer_study.md)
+# on the first 64 instances of this batch (bench.py --figure-sweeps)
 PLAIN_GDM = dict(rule="gdm", alpha=10.0, alpha_lambda=0.3, rho=0.98, decay=1.0, max_iters=8000,
                  path="plain", precision="fp64", check_every=8)
 PLAIN_ADAM = dict(OURS, path="plain", precision="fp64", check_every=4, screen=False)
@@ -65,13 +65,16 @@ C2 = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99, max_ite
 QP_ADAM = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997)
 LP_ADAM = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99)
 # DRAM bytes (read + write) per launch of the two products from ncu captures of the
-# 10000-bus batch of 256 with screening (profiles/bench_10000bus_b256.md), one per CTA-pair
-# tile width (the tiles code of the shapes), valid for the product kernels' source with
-# this digest; null for another source or for single-CTA tiles.
-NCU_TRAFFIC = {"3d24969031fee2d2": {1: {"adjoint": 116.8e6, "forward": 105.0e6},
-                          2: {"adjoint": 115.5e6, "forward": 105.2e6},
-                          3: {"adjoint": 114.8e6, "forward": 104.7e6},
-                          4: {"adjoint": 114.9e6, "forward": 105.1e6}}}
+# 10000-bus batch of 256 with screening (the mean of two launches of each), one per CTA-pair tile code of the shapes (2, 3: single pairs of 256 x
+# 192 and 256 x 160; 5-8: clusters of two pairs, 256 x 256 .. 256 x 144), valid for the
+# product kernels' source with this digest; null for another source, another code or
+# single-CTA tiles.
+NCU_TRAFFIC = {"54de6319f7048f04": {2: {"adjoint": 112.3e6, "forward": 104.7e6},
+                          3: {"adjoint": 112.3e6, "forward": 104.6e6},
+                          5: {"adjoint": 112.2e6, "forward": 104.7e6},
+                          6: {"adjoint": 112.3e6, "forward": 104.6e6},
+                          7: {"adjoint": 112.5e6, "forward": 104.6e6},
+                          8: {"adjoint": 112.1e6, "forward": 104.6e6}}}
 
 
 def golden(name):
@@ -757,12 +760,13 @@ def main():
     loads_h = torch.tensor(w.loads, dtype=torch.float64).pin_memory()
     target_h = torch.tensor(gam, dtype=torch.float64).pin_memory()
     res_e = g.new_result(BATCH)
+    res_h = g.new_host_result(BATCH)   # pinned, reused: the read-back runs at the link's rate
     e2e_times = []
     for k in range(a.warmup + max(3, a.steps // 2)):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        g.solve(loads_h, target=target_h, gap=GAP, out=res_e, **OURS).to_host()
+        g.solve(loads_h, target=target_h, gap=GAP, out=res_e, **OURS).to_host(into=res_h)
         if k >= a.warmup:
             e2e_times.append(time.perf_counter() - t0)
     h2d = loads_h.numel() * 8 + target_h.numel() * 8

@@ -67,9 +67,9 @@ __device__ __forceinline__ float step_rule(const StepArgsF& P, float theta, floa
 }
 
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo);
-__device__ __forceinline__ void finalize_instance(int b, int lane, int max_iters, double tol,
-                                                  const SolveStateBase& st, const BatchView& bb,
-                                                  const double* __restrict__ demand);
+__device__ __forceinline__ int finalize_instance(int b, int lane, int max_iters, double tol,
+                                                 const SolveStateBase& st, const BatchView& bb,
+                                                 const double* __restrict__ demand);
 
 // Step of the batched solve after the forward product: flows (with the rank-1 outage
 // term), supergradient, line part of the dual value, projected step of mu into the
@@ -180,14 +180,29 @@ __device__ __forceinline__ void step_item(const StepEpi& E, int nl, int b, int p
   step_tail(E, b, part, lacc, oacc);
 }
 
+// The per-instance scalars that a step item's loads depend on (whether it runs, the
+// state buffer, the outage), loaded together one item ahead of their use; none of them
+// changes during the step.  The step factors and the outage flow come with the data.
+struct StepScalars {
+  int frozen, k, it;
+};
+__device__ __forceinline__ StepScalars step_scalars(const StepEpi& E, int b) {
+  StepScalars S;
+  S.frozen = E.frozen[b];
+  S.k = E.outage ? E.outage[b] : -1;
+  S.it = E.iter[b];
+  return S;
+}
+
 // The same step with four consecutive lines per lane: 16-byte loads and stores of every
 // FP32 stream and 8-byte stores of the BF16 split (needs n_line, ldF and ldh multiples
-// of 4).
-__device__ __forceinline__ void step4_item(const StepEpi& E, int nl, int b, int part) {
-  if (E.frozen[b]) return;
-  const int k = E.outage ? E.outage[b] : -1;
+// of 4).  The instance's scalars come in S; every load of the item is then issued at
+// once.
+__device__ __forceinline__ void step4_item(const StepEpi& E, int nl, int b, int part, const StepScalars& S) {
+  if (S.frozen) return;
+  const int k = S.k;
   const float t_out = k >= 0 ? E.tout[b] : 0.f;
-  const int it = E.iter[b], pb = it % 3, pn = (it + 1) % 3;
+  const int it = S.it, pb = it % 3, pn = (it + 1) % 3;
   const bool save = it >= 2 && E.best_iter[b] == it - 1;  // point it - 2 is the best
   const size_t o = (size_t)b * nl;
   const float am = E.stepf[4 * b], a1s = E.stepf[4 * b + 1], r2 = E.stepf[4 * b + 2];
@@ -260,10 +275,21 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
     step_item(E, nl, w / E.n_tiles, w % E.n_tiles);
 }
 
+// The vectorised step runs as a persistent grid (four blocks per SM) whose warps take
+// the slices in turn, each loading the next slice's instance scalars while it works on
+// the current one, so that a slice's data loads wait on nothing.
 __global__ void __launch_bounds__(STEP_THREADS, 4) k_bt_step4(StepEpi E, int nl) {
-  const int nw = blockDim.x >> 5, total = E.n_tiles * E.B;
-  for (int w = blockIdx.x * nw + (int)(threadIdx.x >> 5); w < total; w += gridDim.x * nw)
-    step4_item(E, nl, w / E.n_tiles, w % E.n_tiles);
+  const int nw = blockDim.x >> 5, total = E.n_tiles * E.B, stride = gridDim.x * nw;
+  int w = blockIdx.x * nw + (int)(threadIdx.x >> 5);
+  if (w >= total) return;
+  StepScalars S = step_scalars(E, w / E.n_tiles);
+  for (; w < total; w += stride) {
+    const int wn = w + stride;
+    StepScalars Sn = S;
+    if (wn < total) Sn = step_scalars(E, wn / E.n_tiles);
+    step4_item(E, nl, w / E.n_tiles, w % E.n_tiles, S);
+    S = Sn;
+  }
 }
 
 // ------------------------------------------------------------------ operand preparation
@@ -700,12 +726,20 @@ __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M
   // the mean of the minimisers on, whose weight is the iteration count the tests
   // advance, every warp waits for them instead.  (pend and frozen are read by every
   // thread before warp 0 changes them; an instance frozen on entry has nothing pending.)
+  // Every per-instance scalar that the generator warps need is loaded here, with pend
+  // and frozen, in one round trip (none of them is written by the tests: ueta is, but it
+  // is only used when nothing is pending).
   const int pend = bb.pend[b];
   const int frozen0 = bb.frozen[b];
+  const int k = outage ? outage[b] : -1;
+  const float ueta_st = outage ? bb.ueta[b] : 0.f;
+  const double lam = st.lam[b];
   __syncthreads();
   if (frozen0) return;
+  // warp 0, lane 0: whether its tests froze the instance
+  int froze = 0;
   if (pend && threadIdx.x < 32) {
-    finalize_instance(b, (int)threadIdx.x, max_iters, tol, st, bb, demand);
+    froze = finalize_instance(b, (int)threadIdx.x, max_iters, tol, st, bb, demand);
     if (threadIdx.x == 0) bb.pend[b] = 0;
   }
   if (st.xsum) {
@@ -713,7 +747,6 @@ __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M
     if (bb.frozen[b]) return;
   }
   const int ng = N.n_gen;
-  const int k = outage ? outage[b] : -1;
   // the outaged line's term of the adjoint: the step left its multiplier difference out
   // of H (0 there) and its u^T eta in the slices' partials (summed here in the value
   // tests' order, so that it is their ueta), else ueta holds it (0 before the first step,
@@ -726,10 +759,9 @@ __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M
       for (int q = ln; q < nt; q += 32) os += bb.out_part[(size_t)b * nt + q];
       ueta = (float)warp_sum(os);
     } else {
-      ueta = bb.ueta[b];
+      ueta = ueta_st;
     }
   }
-  const double lam = st.lam[b];
   // The in-loop value and the lambda gradient only steer the iteration (the bound is
   // certified in FP64 later): per-generator terms and warp sums in FP32, FP64 across
   // warps.  The reduced cost w = ctil + sigma lambda + pi~ is formed in FP32: its
@@ -737,7 +769,11 @@ __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M
   // the split BF16 products that give pi~.
   const float lamf = (float)lam;
   float c = 0.f, p = 0.f, to = 0.f;
-  const float kk = (float)(st.iter[b] + 1), wk = kk * kk;  // weight of the mean of the minimisers
+  float wk = 0.f;  // weight of the mean of the minimisers, (iteration + 1)^2
+  if (st.xsum || st.wsum) {
+    const float kk = (float)(st.iter[b] + 1);
+    wk = kk * kk;
+  }
   // MG generators per thread and pass, every split-K partial of a group of SG splits in
   // flight before the arithmetic, summed in split order (a missing term adds +0).  While
   // warp 0 runs the value and stop tests, the other warps take all the generators.
@@ -782,6 +818,17 @@ __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M
   c = warp_sum(c); p = warp_sum(p); to = warp_sum(to);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int RW = MIN_MAX_THREADS / 32;
+  // the lambda step's state, loaded by the thread that takes the step before it waits
+  // for the other warps
+  double pw0 = 0.0, pw1 = 0.0, pw2 = 0.0, ls1 = 0.0, ls2 = 0.0, dem = 0.0;
+  if (threadIdx.x == 0) {
+    pw0 = bb.pw[3 * b];
+    pw1 = bb.pw[3 * b + 1];
+    pw2 = bb.pw[3 * b + 2];
+    ls1 = st.lam_s1[b];
+    ls2 = st.lam_s2[b];
+    dem = demand[b];
+  }
   if (lane == 0) { red[wid] = c; red[RW + wid] = p; red[2 * RW + wid] = to; }
   __syncthreads();
   if (wid == 0) {
@@ -796,14 +843,14 @@ __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M
       ts += __shfl_xor_sync(0xffffffffu, ts, o);
     }
     if (lane != 0) return;
-    if (bb.frozen[b]) return;  // stopped by this kernel's value tests (warp 0's own write)
+    if (froze) return;  // stopped by this kernel's value tests
     bb.cost[b] = cs;
     bb.psum[b] = ps;
     if (st.wsum) st.wsum[b] += (double)wk;
     bb.tout[b] = (float)ts;
     bb.lam_eval[b] = lam;
     // step t = iter + 1: scale decay^(t-1), bias corrections 1 - beta^t
-    const double d = bb.pw[3 * b], b1 = bb.pw[3 * b + 1] * SP.beta1, b2 = bb.pw[3 * b + 2] * SP.beta2;
+    const double d = pw0, b1 = pw1 * SP.beta1, b2 = pw2 * SP.beta2;
     const float bc1 = (float)(1.0 - b1), bc2 = (float)(1.0 - b2);
     const float am = (float)(SP.alpha * d);
     bb.stepf[4 * b] = am;
@@ -814,8 +861,8 @@ __device__ __forceinline__ void minimize_item(const DevNet& N, int splits, int M
     bb.pw[3 * b + 2] = b2;
     // lambda's step: the moments and lambda in FP64, the Adam / AdaGrad direction in
     // FP32 (FP64 division and square root are slow on this part)
-    const double g = ps - demand[b], a = SP.alpha_lambda * d;
-    double s1 = st.lam_s1[b], s2 = st.lam_s2[b], l = lam;
+    const double g = ps - dem, a = SP.alpha_lambda * d;
+    double s1 = ls1, s2 = ls2, l = lam;
     if (SP.rule == DCOPF_GDM) {
       s1 = SP.rho * s1 + a * g;
       l += s1;
@@ -857,10 +904,24 @@ __global__ void __launch_bounds__(MIN_MAX_THREADS, 2)
 // minimiser block for the instance, or of the end-of-round kernel.  A stopping instance
 // is frozen: one that reached its target with the point just evaluated (state buffer
 // iter % 3), one stopped by the iteration cap or the tol test with its best point.
-__device__ __forceinline__ void finalize_instance(int b, int lane, int max_iters, double tol,
-                                                  const SolveStateBase& st, const BatchView& bb,
-                                                  const double* __restrict__ demand) {
+// Lane 0 loads the instance's scalars before the partial sums (one round trip for
+// both) and returns 1 if the tests froze the instance (0 on the other lanes).
+__device__ __forceinline__ int finalize_instance(int b, int lane, int max_iters, double tol,
+                                                 const SolveStateBase& st, const BatchView& bb,
+                                                 const double* __restrict__ demand) {
   const int nt = bb.n_tiles;
+  double cost = 0.0, lam_e = 0.0, psum = 0.0, dem = 0.0, best = 0.0, prev = 0.0, thr = 0.0;
+  int iter = 0;
+  if (lane == 0) {
+    cost = bb.cost[b];
+    lam_e = bb.lam_eval[b];
+    psum = bb.psum[b];
+    dem = demand[b];
+    best = st.best[b];
+    prev = st.prev[b];
+    iter = st.iter[b];
+    if (st.has_target) thr = st.thresh[b] + st.margin[b];
+  }
   double ls = 0.0, os = 0.0;
   for (int q = lane; q < nt; q += 32) {
     ls += bb.line_part[(size_t)b * nt + q];
@@ -868,25 +929,26 @@ __device__ __forceinline__ void finalize_instance(int b, int lane, int max_iters
   }
   ls = warp_sum(ls);
   os = warp_sum(os);
-  if (lane != 0) return;
-  const double val = bb.cost[b] + bb.lam_eval[b] * (bb.psum[b] - demand[b]) + ls;
-  const int t = st.iter[b] + 1;
-  if (val > st.best[b]) { st.best[b] = val; st.best_iter[b] = t; bb.lam_best[b] = bb.lam_eval[b]; }
+  if (lane != 0) return 0;
+  const double val = cost + lam_e * (psum - dem) + ls;
+  const int t = iter + 1;
+  if (val > best) { st.best[b] = val; st.best_iter[b] = t; bb.lam_best[b] = lam_e; }
   // u^T eta of the point stepped to, the outaged line's multiplier difference in the
   // post-outage adjoint: the next minimiser adds its column of the product
   bb.ueta[b] = (float)os;
   int c = 0;
-  if (st.has_target && val >= st.thresh[b] + st.margin[b]) c = 1;
+  if (st.has_target && val >= thr) c = 1;
   else if (t >= max_iters) c = 2;
-  else if (tol > 0.0 && t > 1 && fabs(val - st.prev[b]) < tol) c = 2;
+  else if (tol > 0.0 && t > 1 && fabs(val - prev) < tol) c = 2;
   st.prev[b] = val;
   if (c) {
     st.cand[b] = c;
     bb.frozen[b] = 1;
-    st.best_lam[b] = c == 1 ? bb.lam_eval[b] : bb.lam_best[b];
-  } else {
-    st.iter[b] = t;
+    st.best_lam[b] = c == 1 ? lam_e : bb.lam_best[b];
+    return 1;
   }
+  st.iter[b] = t;
+  return 0;
 }
 
 // The value and stop tests of the points the last step of a round evaluated (those
@@ -1187,7 +1249,7 @@ static bool enqueue_iters(TensorRun& R, IterView& V, int n, cudaStream_t cs, boo
     const int blocks = (R.n_tiles * V.B + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32);
     const int sb = R.step_blocks ? std::min(blocks, R.step_blocks) : blocks;
     if (nl % 4 == 0 && V.E.ldF % 4 == 0 && V.E.ldh % 4 == 0)
-      k_bt_step4<<<sb, STEP_THREADS, 0, cs>>>(V.E, nl);
+      k_bt_step4<<<std::min(sb, 4 * h->sm_count), STEP_THREADS, 0, cs>>>(V.E, nl);
     else
       k_bt_step<<<sb, STEP_THREADS, 0, cs>>>(V.E, nl);
     ev(4);  // the value and stop tests run in the next minimiser (or below, for the last)

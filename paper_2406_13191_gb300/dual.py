@@ -58,16 +58,24 @@ class SolveResult:
     mean_dispatch: torch.Tensor | None = None  # [B][n_gen] k^2-weighted mean of the minimisers
     flat: torch.Tensor | None = None  # the device buffer the six results are views of
 
-    def to_host(self) -> "SolveResult":
+    def to_host(self, into: "SolveResult | None" = None) -> "SolveResult":
         """The results in host memory with one device-to-host transfer, ordered after
         the work already on the current stream.  Results made by ``new_result`` (or by
         ``solve`` without ``out=``) are views of one device buffer, which is copied as it
-        is by one blocking copy (for results of this size, faster on a Grace host than
-        an asynchronous copy into pinned memory followed by a stream synchronisation);
-        otherwise they are packed on the device first (iteration counts and statuses
-        travel exactly as FP64)."""
+        is: into ``into`` when given (a result from ``new_host_result``, whose buffer is
+        pinned, so that the copy runs at the host link's rate; it is reused, and the call
+        returns once the copy is in), else by one blocking copy into new host memory
+        (for small results faster on a Grace host than an asynchronous copy followed by
+        a stream synchronisation).  Results that are not such views are packed on the
+        device first (iteration counts and statuses travel exactly as FP64)."""
         B, n = self.mu_hi.shape
         if self.flat is not None:
+            if into is not None:
+                if into.flat is None or into.flat.shape != self.flat.shape or into.flat.device.type != "cpu":
+                    raise ValueError("into= is not a host result of this batch")
+                into.flat.copy_(self.flat, non_blocking=into.flat.is_pinned())
+                torch.cuda.current_stream(self.flat.device).synchronize()
+                return into
             host = self.flat.cpu()
             return SolveResult(*_packed_views(host, B, n), flat=host)
         packed = torch.cat([self.bound, self.lam, self.iters.double(), self.status.double(),
@@ -307,6 +315,12 @@ class DcopfDual:
         """Output tensors for ``solve(..., out=...)`` (reusable across calls): views of
         one device buffer, so that ``to_host`` is a single copy."""
         flat = torch.empty(_packed_size(batch, self.n_line), dtype=torch.float64, device=self.device)
+        return SolveResult(*_packed_views(flat, batch, self.n_line), flat=flat)
+
+    def new_host_result(self, batch: int) -> SolveResult:
+        """A pinned host buffer laid out like ``new_result``'s, for ``to_host(into=...)``
+        (reusable across calls)."""
+        flat = torch.empty(_packed_size(batch, self.n_line), dtype=torch.float64).pin_memory()
         return SolveResult(*_packed_views(flat, batch, self.n_line), flat=flat)
 
     def _solve_arrays(self, loads, outage, target, warm, res=None):

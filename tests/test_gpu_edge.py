@@ -115,3 +115,14 @@ def test_packed_host_results_equal_the_tensors(scales):
         for f in ("lam", "mu_hi", "mu_lo", "bound", "iters", "status"):
             a, b = getattr(res, f).cpu(), getattr(h, f)
             assert a.shape == b.shape and a.dtype == b.dtype and torch.equal(a, b), f
+    # into a reused pinned host result: the same values, twice in a row
+    hp = g.new_host_result(len(scales))
+    assert hp.flat.is_pinned()
+    for res in (r, r2):
+        h = res.to_host(into=hp)
+        assert h is hp
+        for f in ("lam", "mu_hi", "mu_lo", "bound", "iters", "status"):
+            a, b = getattr(res, f).cpu(), getattr(h, f)
+            assert a.shape == b.shape and a.dtype == b.dtype and torch.equal(a, b), f
+    with pytest.raises(ValueError):
+        r.to_host(into=g.new_host_result(len(scales) + 1))
