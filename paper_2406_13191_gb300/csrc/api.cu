@@ -25,6 +25,7 @@ dcopf_dual::~dcopf_dual() {
     if (e) cudaEventDestroy(e);
   if (tstream) cudaStreamDestroy(tstream);
   if (cstream) cudaStreamDestroy(cstream);
+  if (cstream2) cudaStreamDestroy(cstream2);
   if (tstream2) cudaStreamDestroy(tstream2);
   if (fork_ev) cudaEventDestroy(fork_ev);
   if (join_ev) cudaEventDestroy(join_ev);

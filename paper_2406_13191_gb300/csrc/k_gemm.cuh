@@ -37,6 +37,8 @@ struct GemmArgs {
   uint64_t timeout_ns;
   const int* skip;       // nullable [M]: rows whose instance is frozen (a tile of them is skipped)
   int bblk;              // B in 8-row blocks (4-D maps: element (r, c) at ((r/8 KB + c/64) 8 + r%8) 64 + c%64)
+  int bpol;              // L2 policy of the CTA-pair B loads: 0 none, 1 evict_last, 2 evict_first,
+                         // 3 evict_last for B's high part and evict_first for its low part
 };
 
 constexpr int GBM = 128, GBN = 128, GBK = 64;
@@ -304,6 +306,7 @@ __global__ void __launch_bounds__(192, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer (both CTAs; completion counted on rank 0's barrier)
+    const uint64_t pol_last = umma::l2_policy_evict_last(), pol_first = umma::l2_policy_evict_first();
     for (int i = 0; i < nkb; ++i) {
       const int s = i % ST;
       if (i >= ST && !umma::mbar_wait(&empty[s], ((i / ST) & 1) ^ 1, g.timeout_ns)) {
@@ -321,7 +324,16 @@ __global__ void __launch_bounds__(192, 1)
         if (pc == 0) umma::tma_load_2d_pair_mc(&tAh, bar, a_hi(s), x, my_m, amask);
         if (NPROD == 3 && pc == 1) umma::tma_load_2d_pair_mc(&tAl, bar, a_lo(s), x, my_m, amask);
       }
-      if (g.bblk) {
+      if (g.bpol) {
+        const uint64_t ph = g.bpol == 2 ? pol_first : pol_last, pl = g.bpol == 1 ? pol_last : pol_first;
+        if (g.bblk) {
+          umma::tma_load_4d_pair_hint(&tBh, bar, b_hi(s), kb0 + i, my_n >> 3, ph);
+          umma::tma_load_4d_pair_hint(&tBl, bar, b_lo(s), kb0 + i, my_n >> 3, pl);
+        } else {
+          umma::tma_load_2d_pair_hint(&tBh, bar, b_hi(s), x, my_n, ph);
+          umma::tma_load_2d_pair_hint(&tBl, bar, b_lo(s), x, my_n, pl);
+        }
+      } else if (g.bblk) {
         umma::tma_load_4d_pair(&tBh, bar, b_hi(s), kb0 + i, my_n >> 3);
         umma::tma_load_4d_pair(&tBl, bar, b_lo(s), kb0 + i, my_n >> 3);
       } else {

@@ -181,8 +181,8 @@ __device__ __forceinline__ void step_item(const StepEpi& E, int nl, int b, int p
 }
 
 // The per-instance scalars that a step item's loads depend on (whether it runs, the
-// state buffer, the outage), loaded together one item ahead of their use; none of them
-// changes during the step.  The step factors and the outage flow come with the data.
+// state buffer, the outage), loaded together in one round trip; the step factors, the
+// outage flow and the best point's count then come with the data.
 struct StepScalars {
   int frozen, k, it;
 };
@@ -275,20 +275,11 @@ __global__ void __launch_bounds__(STEP_THREADS) k_bt_step(StepEpi E, int nl) {
     step_item(E, nl, w / E.n_tiles, w % E.n_tiles);
 }
 
-// The vectorised step runs as a persistent grid (four blocks per SM) whose warps take
-// the slices in turn, each loading the next slice's instance scalars while it works on
-// the current one, so that a slice's data loads wait on nothing.
 __global__ void __launch_bounds__(STEP_THREADS, 4) k_bt_step4(StepEpi E, int nl) {
-  const int nw = blockDim.x >> 5, total = E.n_tiles * E.B, stride = gridDim.x * nw;
-  int w = blockIdx.x * nw + (int)(threadIdx.x >> 5);
-  if (w >= total) return;
-  StepScalars S = step_scalars(E, w / E.n_tiles);
-  for (; w < total; w += stride) {
-    const int wn = w + stride;
-    StepScalars Sn = S;
-    if (wn < total) Sn = step_scalars(E, wn / E.n_tiles);
-    step4_item(E, nl, w / E.n_tiles, w % E.n_tiles, S);
-    S = Sn;
+  const int nw = blockDim.x >> 5, total = E.n_tiles * E.B;
+  for (int w = blockIdx.x * nw + (int)(threadIdx.x >> 5); w < total; w += gridDim.x * nw) {
+    const int b = w / E.n_tiles;
+    step4_item(E, nl, b, w % E.n_tiles, step_scalars(E, b));
   }
 }
 
@@ -1002,9 +993,9 @@ constexpr int ACCEPT_THREADS = 512;
 __global__ void __launch_bounds__(ACCEPT_THREADS)
     k_bt_accept(int B, int accept, double ub_any, SolveStateBase st, BatchView bb,
                 const int* __restrict__ snap, const int* __restrict__ err, int* out_active,
-                int* out_err, int* out_flag) {
-  __shared__ int red[ACCEPT_THREADS / 32];
-  int running = 0;
+                int* out_err, int* out_flag, int* out_iter) {
+  __shared__ int red[ACCEPT_THREADS / 32], red2[ACCEPT_THREADS / 32];
+  int running = 0, iterating = 0;
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
     if (accept && snap[b] && !st.done[b] && st.cand[b]) {
       const double c = st.cert[b];
@@ -1025,16 +1016,25 @@ __global__ void __launch_bounds__(ACCEPT_THREADS)
       st.iter[b] += 1;
     }
     running += st.done[b] ? 0 : 1;
+    iterating += bb.frozen[b] ? 0 : 1;
   }
   running = __reduce_add_sync(0xffffffffu, running);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = running;
+  iterating = __reduce_add_sync(0xffffffffu, iterating);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = running;
+    red2[threadIdx.x >> 5] = iterating;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int n = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) n += red[w];
+    int n = 0, m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      n += red[w];
+      m += red2[w];
+    }
     *out_active = n;
     *out_err = err[0];
     *out_flag = err[1];
+    *out_iter = m;
   }
 }
 
@@ -1249,7 +1249,7 @@ static bool enqueue_iters(TensorRun& R, IterView& V, int n, cudaStream_t cs, boo
     const int blocks = (R.n_tiles * V.B + STEP_THREADS / 32 - 1) / (STEP_THREADS / 32);
     const int sb = R.step_blocks ? std::min(blocks, R.step_blocks) : blocks;
     if (nl % 4 == 0 && V.E.ldF % 4 == 0 && V.E.ldh % 4 == 0)
-      k_bt_step4<<<std::min(sb, 4 * h->sm_count), STEP_THREADS, 0, cs>>>(V.E, nl);
+      k_bt_step4<<<sb, STEP_THREADS, 0, cs>>>(V.E, nl);
     else
       k_bt_step<<<sb, STEP_THREADS, 0, cs>>>(V.E, nl);
     ev(4);  // the value and stop tests run in the next minimiser (or below, for the last)
@@ -1613,6 +1613,10 @@ static dcopf_status tensor_setup(TensorRun& R, cudaStream_t s) {
   gf.F32 = h->bb.F.as<float>(); gf.ldf32 = ldF;
   gf.err = h->d_err; gf.timeout_ns = 2000000000ull;
   ga.bblk = gf.bblk = R.ls.blocked;
+  // the CTA-pair products keep Phi~'s high part in L2 in preference to its low part
+  // (the two layouts' high parts, 99 MB on the 10000-bus batch, fit where all four do
+  // not)
+  ga.bpol = gf.bpol = 3;
   StepEpi& E = R.E;
   E.P = to_float_args(P); E.F = gf.F32; E.ldF = ldF; E.f0 = R.ls.f0; E.u = w.u32.as<float>();
   E.outage = R.it.outage; E.tout = bb.tout;
@@ -1694,17 +1698,26 @@ static dcopf_status tensor_stage_certify(TensorRun& R, int round, cudaStream_t c
   return cudaGetLastError() == cudaSuccess ? DCOPF_OK : DCOPF_ERR_CUDA;
 }
 
+// The stream of round `round`'s certificates: one per round parity, so that two rounds'
+// certificates can run at once; the dense certificate (small batches without outages)
+// keeps one stream, as its launches share the handle's partial-sum buffer.
+static cudaStream_t cert_stream(const TensorRun& R, int round) {
+  dcopf_dual* h = R.it.h;
+  const bool two = h->cstream2 && !dense_path_applies(h, R.it.B, R.it.outage);
+  return (round & 1) && two ? h->cstream2 : h->cstream;
+}
+
 // Once the certificate of the instances staged in round `staged` is in (done_ev): accept,
 // stop or resume each of them (when `accept`), on cs; the count of instances still
 // running, the device error word and the re-screen flag go to *out_active, *out_err,
 // *out_flag (device memory).
 static dcopf_status tensor_accept(TensorRun& R, bool accept, int staged, int* out_active, int* out_err,
-                                  int* out_flag, cudaStream_t cs, cudaEvent_t done_ev) {
+                                  int* out_flag, int* out_iter, cudaStream_t cs, cudaEvent_t done_ev) {
   dcopf_dual* h = R.it.h;
   if (accept && cudaStreamWaitEvent(cs, done_ev, 0) != cudaSuccess) return DCOPF_ERR_CUDA;
   const int* snap = h->bb.snap.as<int>() + (size_t)(staged & 1) * R.it.B;
   k_bt_accept<<<1, ACCEPT_THREADS, 0, cs>>>(R.it.B, accept ? 1 : 0, h->ub_any, R.st, h->bb.v, snap, h->d_err,
-                                           out_active, out_err, out_flag);
+                                           out_active, out_err, out_flag, out_iter);
   h->launches += 1;
   return cudaGetLastError() == cudaSuccess ? DCOPF_OK : DCOPF_ERR_CUDA;
 }
@@ -1809,8 +1822,8 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
           cudaEventCreate(&K.t0[q]) != cudaSuccess || cudaEventCreate(&K.t1[q]) != cudaSuccess)
         return DCOPF_ERR_CUDA;
     if (cudaStreamCreateWithFlags(&K.rs, cudaStreamNonBlocking) != cudaSuccess) return DCOPF_ERR_CUDA;
-    if (cudaMallocHost(&K.pin, 6 * sizeof(int) * (size_t)n) != cudaSuccess ||
-        cudaMalloc(&K.rb_dev, 6 * sizeof(int) * (size_t)n) != cudaSuccess) {
+    if (cudaMallocHost(&K.pin, 8 * sizeof(int) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&K.rb_dev, 8 * sizeof(int) * (size_t)n) != cudaSuccess) {
       cudaGetLastError();
       K.release();
       return DCOPF_ERR_OOM;
@@ -1878,17 +1891,18 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
   double t_wait = 0.0;
   long long max_iters = 0;
   for (const TensorRun& R : runs) max_iters = std::max<long long>(max_iters, R.p.max_iters);
-  // The certificate of round r's candidates runs on a side stream beside round r + 1's
-  // iterations (the candidates stay frozen meanwhile); round r + 1 then accepts them.
+  // The certificate of round r's candidates runs on a side stream (one per round parity)
+  // beside the next rounds' iterations (the candidates stay frozen meanwhile); round
+  // r + 2 then accepts them.
   for (int i = 0; i < n; ++i) {
     dcopf_dual* hi = items[i].h;
     // the certificates at the highest stream priority: their CTAs take SMs as the
     // iterations' blocks retire, so that they are in when the next round accepts them
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
-    if (!hi->cstream &&
-        cudaStreamCreateWithPriority(&hi->cstream, cudaStreamNonBlocking, hi_prio) != cudaSuccess)
-      return DCOPF_ERR_CUDA;
+    for (cudaStream_t* cst : {&hi->cstream, &hi->cstream2})
+      if (!*cst && cudaStreamCreateWithPriority(cst, cudaStreamNonBlocking, hi_prio) != cudaSuccess)
+        return DCOPF_ERR_CUDA;
     if (hi->bb.snap.alloc(2 * sizeof(int) * (size_t)items[i].B) != cudaSuccess ||
         cudaMemsetAsync(hi->bb.snap.p, 0, 2 * sizeof(int) * (size_t)items[i].B, hi->tstream) != cudaSuccess)
       return DCOPF_ERR_OOM;
@@ -1900,12 +1914,20 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
   // around.  A certificate has two rounds of iterations to run beside (it competes with
   // them for SMs), so that its accept does not wait for it.  A batch whose last instance
   // was accepted in round r - 1 thus also runs round r, whose iterations skip every
-  // (frozen) instance.
-  std::vector<int> act(n, 1);
+  // (frozen) instance.  A round whose graph would find every instance frozen (by the
+  // latest read-back, round r - 2's: none was iterating after its accept) launches no
+  // graph, only its accept, staging and read-back; an instance that a later accept
+  // resumes (its certificate fell short) iterates again from the round after the
+  // read-back that shows it.
+  std::vector<int> act(n, 1), iterating(n, 1);
+  bool ran[2] = {true, true};
   int rounds = 0;
   for (int round = 0;; ++round) {
     const int sl = round & 1;
     rounds = round + 1;
+    bool run_graph = round < 2;
+    for (int i = 0; i < n; ++i) run_graph |= act[i] && iterating[i] > 0;
+    ran[sl] = run_graph;
     for (const RoundKit::KNode& k : K.knodes) {
       dcopf_dual* hk = items[k.net].h;
       if (cudaGraphExecEventRecordNodeSetEvent(K.exec, k.node, sl ? hk->kev2[k.q] : hk->kev[k.q]) != cudaSuccess)
@@ -1922,15 +1944,15 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
       cudaEventRecord(a, cs0);
     }
     if (h0->timing) cudaEventRecord(K.t0[sl], cs0);
-    if (cudaGraphLaunch(K.exec, cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
+    if (run_graph && cudaGraphLaunch(K.exec, cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
     long long round_launches = 0;
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n && run_graph; ++i) {
       items[i].h->launches += (4LL * chunk + 1) * runs[i].nv;
       round_launches += (4LL * chunk + 1) * runs[i].nv;
     }
     if (h0->timing) cudaEventRecord(K.t1[sl], cs0);
     if (verbose) cudaEventRecord(G.vev[G.vev.size() - 2], cs0);
-    int* slot = K.rb_dev + (size_t)sl * 3 * n;
+    int* slot = K.rb_dev + (size_t)sl * 4 * n;
     if (cudaEventRecord(K.ev[2 * n], cs0) != cudaSuccess) return DCOPF_ERR_CUDA;
     for (int i = 0; i < n; ++i) {
       cudaStream_t si = items[i].h->tstream;
@@ -1938,12 +1960,12 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
       // every network reports its count and error word; a network still running accepts
       // the certificates of the last round and stages this round's candidates
       dcopf_status r;
-      if ((r = tensor_accept(runs[i], round > 1 && act[i], round - 2, slot + i, slot + n + i, slot + 2 * n + i, si,
-                             K.cert_ev[2 * i + (round & 1)])))
+      if ((r = tensor_accept(runs[i], round > 1 && act[i], round - 2, slot + i, slot + n + i, slot + 2 * n + i,
+                             slot + 3 * n + i, si, K.cert_ev[2 * i + (round & 1)])))
         return r;
       if (verbose && i == 0) cudaEventRecord(G.vev.back(), cs0);
       if (act[i] &&
-          (r = tensor_stage_certify(runs[i], round, si, items[i].h->cstream, K.stage_ev[i],
+          (r = tensor_stage_certify(runs[i], round, si, cert_stream(runs[i], round), K.stage_ev[i],
                                     K.cert_ev[2 * i + (round & 1)])))
         return r;
     }
@@ -1953,7 +1975,7 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
         return DCOPF_ERR_CUDA;
     // the read-back of this round's counts, on its own stream
     if (cudaEventRecord(K.acc[sl], cs0) != cudaSuccess || cudaStreamWaitEvent(K.rs, K.acc[sl], 0) != cudaSuccess ||
-        cudaMemcpyAsync(K.pin + (size_t)sl * 3 * n, slot, 3 * sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost,
+        cudaMemcpyAsync(K.pin + (size_t)sl * 4 * n, slot, 4 * sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost,
                         K.rs) != cudaSuccess ||
         cudaEventRecord(K.done[sl], K.rs) != cudaSuccess)
       return DCOPF_ERR_CUDA;
@@ -1967,9 +1989,10 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
     const double tw = verbose ? host_ms() : 0.0;
     if (cudaEventSynchronize(K.done[pv_sl]) != cudaSuccess) return DCOPF_ERR_CUDA;
     if (verbose) t_wait += host_ms() - tw;
-    const int* pv = K.pin + (size_t)pv_sl * 3 * n;
+    const int* pv = K.pin + (size_t)pv_sl * 4 * n;
     for (int i = 0; i < n; ++i)
       if (pv[n + i]) return (dcopf_status)pv[n + i];
+    for (int i = 0; i < n; ++i) iterating[i] = pv[3 * n + i];
     bool rescreen = false;
     for (int i = 0; i < n; ++i)
       if (pv[2 * n + i]) {  // this batch needs a line the network's kept set screens out
@@ -1981,6 +2004,7 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
         if (cudaStreamSynchronize(items[i].h->tstream) != cudaSuccess ||
             (items[i].h->tstream2 && cudaStreamSynchronize(items[i].h->tstream2) != cudaSuccess) ||
             (items[i].h->cstream && cudaStreamSynchronize(items[i].h->cstream) != cudaSuccess) ||
+            (items[i].h->cstream2 && cudaStreamSynchronize(items[i].h->cstream2) != cudaSuccess) ||
             cudaMemset(items[i].h->d_err + 1, 0, sizeof(int)) != cudaSuccess)
           return DCOPF_ERR_CUDA;
       if (cudaStreamSynchronize(K.rs) != cudaSuccess) return DCOPF_ERR_CUDA;
@@ -1992,7 +2016,7 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
       h0->t_iter_ms += ms;
       h0->t_iter_launches += round_launches;
     }
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n && ran[pv_sl]; ++i) {
       dcopf_dual* hi = items[i].h;
       if (!hi->timing || !hi->kev[0] || !act[i] || K.knodes.empty()) continue;
       cudaEvent_t* ks = pv_sl ? hi->kev2 : hi->kev;
@@ -2045,8 +2069,8 @@ static dcopf_status solve_tensor_group_once(const TensorItem* items, int n, cons
   for (int i = 0; i < n; ++i)
     for (int q = std::max(0, rounds - 2); q < rounds; ++q) {
       int* slot = K.rb_dev;  // free: everything queued has run
-      dcopf_status r = tensor_accept(runs[i], true, q, slot + i, slot + n + i, slot + 2 * n + i, items[i].h->tstream,
-                                     K.cert_ev[2 * i + (q & 1)]);
+      dcopf_status r = tensor_accept(runs[i], true, q, slot + i, slot + n + i, slot + 2 * n + i, slot + 3 * n + i,
+                                     items[i].h->tstream, K.cert_ev[2 * i + (q & 1)]);
       if (r) return r;
     }
   for (int i = 0; i < n; ++i) {

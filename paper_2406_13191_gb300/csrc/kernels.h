@@ -211,10 +211,10 @@ struct BatchView {
 struct RoundKit {
   int n = 0;  // networks the events and the read-back are made for
   std::vector<cudaEvent_t> ev, stage_ev, cert_ev;
-  // per round parity [2][3n]: each network's running count, device error word and
-  // re-screen flag,
-  // written by its accept kernel on the device and copied to pinned host memory on the
-  // read-back stream, off the iterations' critical path
+  // per round parity [2][4n]: each network's running count, device error word,
+  // re-screen flag and count of instances iterating (not frozen), written by its accept
+  // kernel on the device and copied to pinned host memory on the read-back stream, off
+  // the iterations' critical path
   int* rb_dev = nullptr;
   int* pin = nullptr;
   cudaStream_t rs = nullptr;
@@ -302,7 +302,9 @@ struct dcopf_dual {
                             // [1] evaluations (timing), [2] device error word
   double ub_any = 0.0;  // cost of the dearest dispatch (upper bound on any primal cost)
   cudaStream_t tstream = nullptr;  // internal stream of the graph-captured batched solve
-  cudaStream_t cstream = nullptr;  // certificates of the batched solve, beside its iterations
+  // certificates of the batched solve, beside its iterations: one stream per round
+  // parity, so that a round's certificates need not wait for the previous round's
+  cudaStream_t cstream = nullptr, cstream2 = nullptr;
   // second branch of the batched solve's iteration graph (its second group of
   // instances), forked from tstream and joined back to it once per round
   cudaStream_t tstream2 = nullptr;
