@@ -554,9 +554,11 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
   std::vector<double> winv1(std::max(1, H.F.n), 1.0);
   if (H.F.n > 0) host_ldl_solve(H.F, winv1.data());
   for (double& v : winv1) v = std::fabs(v) * (1.0 + 1e-6);
+  std::vector<double> inv_diag(H.F.diag.size());
+  for (size_t i = 0; i < inv_diag.size(); ++i) inv_diag[i] = 1.0 / H.F.diag[i];
 #define UP(vec, field) \
   if ((st = upload(h, vec, &D.field)) != DCOPF_OK) { delete h; return st; }
-  UP(winv1, winv1)
+  UP(winv1, winv1) UP(inv_diag, inv_diag)
   UP(H.F.pos_of_bus, pos_of_bus) UP(H.F.bus_of_pos, bus_of_pos)
   UP(H.F.lrow_ptr, lrow_ptr) UP(H.F.lrow_col, lrow_col) UP(H.F.lrow_val, lrow_val)
   UP(H.F.lcol_ptr, lcol_ptr) UP(H.F.lcol_row, lcol_row) UP(H.F.lcol_val, lcol_val)

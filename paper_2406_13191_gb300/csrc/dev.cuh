@@ -27,6 +27,7 @@ struct DevNet {
   const int* fell_col; const double* fell_val; const int* fovf_ptr; const int* fovf_col; const double* fovf_val;
   const int* bell_col; const double* bell_val; const int* bovf_ptr; const int* bovf_col; const double* bovf_val;
   const double* winv1;     // [nr] upper bound of B_r^{-1} 1 (entries >= 0: B_r is an M-matrix)
+  const double* inv_diag;  // [nr] 1 / diag (the solves that scale by a product)
   // packed copy of the factor for shared-memory staging (nullptr when unavailable)
   const unsigned char* fac_blob; int fac_bytes;
   int off_diag, off_val, off_rptr, off_cptr, off_rcol, off_crow, off_cmap, off_frows, off_brows,

@@ -39,20 +39,82 @@ __device__ __forceinline__ void ell_row(int nr, int idx, int i, const int* __res
   X[i] = v;
 }
 
-__device__ void ldl_solve_smem(const DevNet& N, double* X) {
-  for (int lev = 0; lev < N.n_fwd_lev; ++lev) {
-    int s = N.fwd_lev[lev], e = N.fwd_lev[lev + 1];
-    for (int idx = s + threadIdx.x; idx < e; idx += blockDim.x)
-      ell_row(N.nr, idx, N.fwd_rows[idx], N.fell_col, N.fell_val, N.fovf_ptr, N.fovf_col, N.fovf_val, X);
+// One triangular sweep over a level schedule with the factor in global memory.  The
+// rows near the root of the elimination tree are few per level but long (a separator
+// row of the 10000-bus factor has up to ~100 entries), so each level splits its rows'
+// entries over groups of G lanes, G the largest power of two up to 32 with one row per
+// group covering the level in one pass: a long row's products are then summed by a
+// group (each lane its strided share, then a shuffle tree) instead of one after another
+// by one thread.  The next level's bounds are loaded a level ahead.
+__device__ __forceinline__ void ell_sweep(int nr, int nlev, const int* __restrict__ lev,
+                                          const int* __restrict__ rows, const int* __restrict__ ecol,
+                                          const double* __restrict__ eval, const int* __restrict__ optr,
+                                          const int* __restrict__ ocol, const double* __restrict__ oval,
+                                          double* X) {
+  if (nlev <= 0) return;
+  constexpr int K = SparseFactor::kEll;
+  const int tid = (int)threadIdx.x, bd = (int)blockDim.x;
+  int s = lev[0], e = lev[1];
+  for (int l = 0; l < nlev; ++l) {
+    const int e_next = l + 2 <= nlev ? lev[l + 2] : e;
+    const int w = e - s;
+    int G = 1;
+    while (G < 32 && 2 * G * w <= bd) G *= 2;
+    const int gid = tid / G, gl = tid % G, ng = bd / G;
+    for (int base = s; base < e; base += ng) {  // the same trip count for every lane
+      const int idx = base + gid;
+      const bool act = idx < e;
+      double part = 0.0;
+      int i = 0;
+      if (act) {
+        i = rows[idx];
+        const int o0 = optr[idx], o1 = optr[idx + 1];
+        for (int a = gl; a < K; a += G) part += eval[(size_t)a * nr + idx] * X[ecol[(size_t)a * nr + idx]];
+        for (int p = o0 + gl; p < o1; p += G) part += oval[p] * X[ocol[p]];
+      }
+      for (int off = G >> 1; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+      if (act && gl == 0) X[i] -= part;
+    }
     __syncthreads();
+    s = e;
+    e = e_next;
   }
-  for (int i = threadIdx.x; i < N.nr; i += blockDim.x) X[i] /= N.diag[i];
+}
+
+// PF: the sweeps of ell_sweep; without, one thread per row in the stored order of its
+// entries (fewer registers, for the kernels that inline several solves).
+template <bool PF>
+__device__ void ldl_solve_smem(const DevNet& N, double* X) {
+  if (PF) {
+    ell_sweep(N.nr, N.n_fwd_lev, N.fwd_lev, N.fwd_rows, N.fell_col, N.fell_val, N.fovf_ptr, N.fovf_col,
+              N.fovf_val, X);
+  } else {
+    for (int lev = 0; lev < N.n_fwd_lev; ++lev) {
+      int s = N.fwd_lev[lev], e = N.fwd_lev[lev + 1];
+      for (int idx = s + threadIdx.x; idx < e; idx += blockDim.x)
+        ell_row(N.nr, idx, N.fwd_rows[idx], N.fell_col, N.fell_val, N.fovf_ptr, N.fovf_col, N.fovf_val, X);
+      __syncthreads();
+    }
+  }
+  // with PF the diagonal scaling multiplies by the reciprocal (FP64 division is a long
+  // instruction sequence here; the certificate bounds the prices' error from their
+  // residual, whatever the solve's rounding)
+  if (PF) {
+    for (int i = threadIdx.x; i < N.nr; i += blockDim.x) X[i] *= N.inv_diag[i];
+  } else {
+    for (int i = threadIdx.x; i < N.nr; i += blockDim.x) X[i] /= N.diag[i];
+  }
   __syncthreads();
-  for (int lev = 0; lev < N.n_bwd_lev; ++lev) {
-    int s = N.bwd_lev[lev], e = N.bwd_lev[lev + 1];
-    for (int idx = s + threadIdx.x; idx < e; idx += blockDim.x)
-      ell_row(N.nr, idx, N.bwd_rows[idx], N.bell_col, N.bell_val, N.bovf_ptr, N.bovf_col, N.bovf_val, X);
-    __syncthreads();
+  if (PF) {
+    ell_sweep(N.nr, N.n_bwd_lev, N.bwd_lev, N.bwd_rows, N.bell_col, N.bell_val, N.bovf_ptr, N.bovf_col,
+              N.bovf_val, X);
+  } else {
+    for (int lev = 0; lev < N.n_bwd_lev; ++lev) {
+      int s = N.bwd_lev[lev], e = N.bwd_lev[lev + 1];
+      for (int idx = s + threadIdx.x; idx < e; idx += blockDim.x)
+        ell_row(N.nr, idx, N.bwd_rows[idx], N.bell_col, N.bell_val, N.bovf_ptr, N.bovf_col, N.bovf_val, X);
+      __syncthreads();
+    }
   }
 }
 
@@ -119,10 +181,12 @@ __device__ void ldl_solve_packed(const DevNet& N, const PackedFactor& F, double*
   }
 }
 
-// Solve with the staged factor when `staged`, else walk the factor in global memory.
+// Solve with the staged factor when `staged`, else walk the factor in global memory
+// (with ell_sweep when PF).
+template <bool PF = true>
 __device__ __forceinline__ void ldl_solve(const DevNet& N, const PackedFactor* F, double* X) {
   if (F) ldl_solve_packed(N, *F, X);
-  else ldl_solve_smem(N, X);
+  else ldl_solve_smem<PF>(N, X);
 }
 
 __device__ __forceinline__ double theta_at(const DevNet& N, const double* X, int bus) {
@@ -130,7 +194,7 @@ __device__ __forceinline__ double theta_at(const DevNet& N, const double* X, int
   return p >= 0 ? X[p] : 0.0;
 }
 
-__global__ void k_base_flows(DevNet N, const double* __restrict__ loads,
+__global__ void __launch_bounds__(512, 2) k_base_flows(DevNet N, const double* __restrict__ loads,
                              const int* __restrict__ outage, double* __restrict__ f0,
                              float* __restrict__ f0_32, double* __restrict__ u64,
                              float* __restrict__ u32, double* __restrict__ demand, int* err,
@@ -174,13 +238,14 @@ __global__ void k_base_flows(DevNet N, const double* __restrict__ loads,
     const double denom = 1.0 - ptdf_kk;
     const bool bridge = fabs(denom) < 1e-9;
     if (bridge && threadIdx.x == 0) atomicExch(err, (int)DCOPF_ERR_NETWORK);
+    const double rden = bridge ? 0.0 : 1.0 / denom;
     const double f0k = frow[k];
     __syncthreads();
     for (int l = threadIdx.x; l < nl; l += blockDim.x) {
       double u = 0.0;
       if (!bridge) {
         double ptdf = N.line_b[l] * (theta_at(N, X, N.line_from[l]) - theta_at(N, X, N.line_to[l]));
-        u = (l == k) ? -1.0 : ptdf / denom;
+        u = (l == k) ? -1.0 : ptdf * rden;
       }
       if (u64) u64[(size_t)b * nl + l] = u;
       if (u32) u32[(size_t)b * nl + l] = (float)u;
@@ -204,10 +269,13 @@ __device__ __forceinline__ double gamma_fp64(double m) {
   return (m * u) / (1.0 - m * u);
 }
 
+constexpr int kGamTab = 32;
+
 // S is the storage type of the multipliers (double for the API, float for the FP32
 // solver state); `mask` (nullable) selects the instances to certify (mask[b] != 0).
 template <typename S>
-__global__ void k_certify(DevNet N, const double* __restrict__ loads, const int* __restrict__ outage,
+__global__ void __launch_bounds__(512, 2)
+    k_certify(DevNet N, const double* __restrict__ loads, const int* __restrict__ outage,
                           const double* __restrict__ lambda, const S* __restrict__ mu_hi,
                           const S* __restrict__ mu_lo, double* __restrict__ bound,
                           double* __restrict__ errb, const int* __restrict__ mask,
@@ -216,8 +284,12 @@ __global__ void k_certify(DevNet N, const double* __restrict__ loads, const int*
   // shared memory: [staged factor] [nr] prices [nr] outage transfer
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ double red[32];
+  // gamma of the residual's roundings per bus degree, evaluated once (the same values
+  // the residual loop would compute per bus)
+  __shared__ double gam_tab[kGamTab];
   const int b = blockIdx.x;
   if (mask && (mask[b] == 0 || (done && done[b]))) return;
+  if (threadIdx.x < kGamTab) gam_tab[threadIdx.x] = gamma_fp64(2.0 * threadIdx.x + 6.0);
   PackedFactor PF;
   const PackedFactor* pf = nullptr;
   if (staged) { PF = stage_factor(N, sm); pf = &PF; }
@@ -297,7 +369,7 @@ __global__ void k_certify(DevNet N, const double* __restrict__ loads, const int*
       acc += fabs(N.bus_line_coef[p] * eta) + N.line_b[l] * (fabs(zi) + fabs(zo));
       ++deg;
     }
-    rmax = fmax(rmax, fabs(r - bz) + gamma_fp64(2.0 * deg + 6.0) * acc);
+    rmax = fmax(rmax, fabs(r - bz) + (deg < kGamTab ? gam_tab[deg] : gamma_fp64(2.0 * deg + 6.0)) * acc);
   }
   rmax = block_max(rmax, red);
   auto wq = [&](int bus) {
@@ -403,7 +475,7 @@ __global__ void k_sparse_iters(DevNet N, StepArgs P, SolveState<double> st,
       X[q] = r;
     }
     __syncthreads();
-    ldl_solve(N, pf, X);
+    ldl_solve<false>(N, pf, X);
     // minimiser, generation cost and dispatch
     const double lam = st.lam[b];
     const float kk = (float)(st.iter[b] + 1), wk = kk * kk;  // weight of the mean of minimisers
@@ -431,7 +503,7 @@ __global__ void k_sparse_iters(DevNet N, StepArgs P, SolveState<double> st,
       X[q] = y;
     }
     __syncthreads();
-    ldl_solve(N, pf, X);
+    ldl_solve<false>(N, pf, X);
     auto flow = [&](int l) {  // Phi~ x on line l (pre-outage)
       return N.line_b[l] * (theta_at(N, X, N.line_from[l]) - theta_at(N, X, N.line_to[l]));
     };
