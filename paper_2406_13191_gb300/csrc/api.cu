@@ -556,9 +556,41 @@ dcopf_status dcopf_dual_create(const dcopf_network_desc* net, const dcopf_option
   for (double& v : winv1) v = std::fabs(v) * (1.0 + 1e-6);
   std::vector<double> inv_diag(H.F.diag.size());
   for (size_t i = 0; i < inv_diag.size(); ++i) inv_diag[i] = 1.0 / H.F.diag[i];
+  // the bus incidences by elimination position (DevNet::qe_*, qo_*)
+  const int nrp = std::max(1, H.F.n);
+  std::vector<int> qe_line((size_t)kIncEll * nrp, -1), qe_opos((size_t)kIncEll * nrp, -1), qo_ptr(nrp + 1, 0);
+  std::vector<double> qe_coef((size_t)kIncEll * nrp, 0.0), qe_b((size_t)kIncEll * nrp, 0.0);
+  std::vector<int> qo_line, qo_opos;
+  std::vector<double> qo_coef, qo_b;
+  for (int q = 0; q < H.F.n; ++q) {
+    const int bus = H.F.bus_of_pos[q];
+    int a = 0;
+    for (int p = H.bus_line_ptr[bus]; p < H.bus_line_ptr[bus + 1]; ++p, ++a) {
+      const int l = H.bus_line_idx[p];
+      const int o = H.line_from[l] == bus ? H.line_to[l] : H.line_from[l];
+      const int op = H.F.pos_of_bus[o];
+      if (a < kIncEll) {
+        qe_line[(size_t)a * nrp + q] = l;
+        qe_opos[(size_t)a * nrp + q] = op;
+        qe_coef[(size_t)a * nrp + q] = H.bus_line_coef[p];
+        qe_b[(size_t)a * nrp + q] = H.b[l];
+      } else {
+        qo_line.push_back(l);
+        qo_opos.push_back(op);
+        qo_coef.push_back(H.bus_line_coef[p]);
+        qo_b.push_back(H.b[l]);
+      }
+    }
+    qo_ptr[q + 1] = (int)qo_line.size();
+  }
+  if (qo_line.empty()) {  // keep every upload non-empty
+    qo_line.push_back(0); qo_opos.push_back(-1); qo_coef.push_back(0.0); qo_b.push_back(0.0);
+  }
 #define UP(vec, field) \
   if ((st = upload(h, vec, &D.field)) != DCOPF_OK) { delete h; return st; }
   UP(winv1, winv1) UP(inv_diag, inv_diag)
+  UP(qe_line, qe_line) UP(qe_opos, qe_opos) UP(qe_coef, qe_coef) UP(qe_b, qe_b)
+  UP(qo_ptr, qo_ptr) UP(qo_line, qo_line) UP(qo_opos, qo_opos) UP(qo_coef, qo_coef) UP(qo_b, qo_b)
   UP(H.F.pos_of_bus, pos_of_bus) UP(H.F.bus_of_pos, bus_of_pos)
   UP(H.F.lrow_ptr, lrow_ptr) UP(H.F.lrow_col, lrow_col) UP(H.F.lrow_val, lrow_val)
   UP(H.F.lcol_ptr, lcol_ptr) UP(H.F.lcol_row, lcol_row) UP(H.F.lcol_val, lcol_val)

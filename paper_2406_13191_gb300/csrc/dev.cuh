@@ -11,6 +11,8 @@ namespace dcopf {
 // Everything the kernels need to know about one network, as device pointers.
 // Layouts: Phi~ row-major [n_line][n_gen] ("phi*"), its transpose [n_gen][n_line]
 // ("phit*"); per-line and per-generator vectors are plain arrays.
+constexpr int kIncEll = 4;
+
 struct DevNet {
   int n_bus, n_line, n_gen, slack, qp;
   double S;
@@ -39,6 +41,12 @@ struct DevNet {
   const float* fmax32; const float* fmin32;
   const double* phim;       // Phi mid [n_line]
   const int* bus_line_ptr; const int* bus_line_idx; const double* bus_line_coef;
+  // the same incidences by elimination position q (the bus at q), in the same order: the
+  // first kIncEll in slots [a * nr + q] (line -1 and coefficient 0 where unused), the rest
+  // in an overflow CSR; each with the line, the other end's position (-1 for the slack
+  // bus), the coefficient +-b_l and b_l
+  const int* qe_line; const int* qe_opos; const double* qe_coef; const double* qe_b;
+  const int* qo_ptr; const int* qo_line; const int* qo_opos; const double* qo_coef; const double* qo_b;
   const int* bus_gen_ptr; const int* bus_gen_idx;
   // generators
   const int* gen_bus;

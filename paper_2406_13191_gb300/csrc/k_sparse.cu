@@ -300,15 +300,30 @@ __global__ void __launch_bounds__(512, 2)
   const S* ml = mu_lo + (size_t)b * nl;
   const double* d = loads + (size_t)b * N.n_bus;
   const double lam = lambda[b];
-  // rhs = E_r^T Omega eta with eta = max(mu_hi,0) - max(mu_lo,0), eta_k = 0
+  // rhs = E_r^T Omega eta with eta = max(mu_hi,0) - max(mu_lo,0), eta_k = 0; a
+  // position's first kIncEll incidences load in one round trip, their multipliers in
+  // the next (the sums keep the incidence order)
+  auto eta_of = [&](int l) { return fmax((double)mh[l], 0.0) - fmax((double)ml[l], 0.0); };
   for (int q = threadIdx.x; q < N.nr; q += blockDim.x) {
-    int bus = N.bus_of_pos[q];
+    int ln[kIncEll];
+    double cf[kIncEll];
+#pragma unroll
+    for (int a = 0; a < kIncEll; ++a) {
+      ln[a] = N.qe_line[(size_t)a * N.nr + q];
+      cf[a] = N.qe_coef[(size_t)a * N.nr + q];
+    }
+    const int o0 = N.qo_ptr[q], o1 = N.qo_ptr[q + 1];
+    double et[kIncEll];
+#pragma unroll
+    for (int a = 0; a < kIncEll; ++a) et[a] = (ln[a] >= 0 && ln[a] != k) ? eta_of(ln[a]) : 0.0;
     double r = 0.0;
-    for (int p = N.bus_line_ptr[bus]; p < N.bus_line_ptr[bus + 1]; ++p) {
-      int l = N.bus_line_idx[p];
+#pragma unroll
+    for (int a = 0; a < kIncEll; ++a)
+      if (ln[a] >= 0 && ln[a] != k) r += cf[a] * et[a];
+    for (int p = o0; p < o1; ++p) {
+      const int l = N.qo_line[p];
       if (l == k) continue;
-      double eta = fmax((double)mh[l], 0.0) - fmax((double)ml[l], 0.0);
-      r += N.bus_line_coef[p] * eta;
+      r += N.qo_coef[p] * eta_of(l);
     }
     X[q] = r;
   }
@@ -354,21 +369,33 @@ __global__ void __launch_bounds__(512, 2)
   // rmax >= |r - B' z^|_inf.  As B'^{-1} >= 0 elementwise, |z - z^| <= rmax B'^{-1} 1.
   double rmax = 0.0;
   for (int q = threadIdx.x; q < N.nr; q += blockDim.x) {
-    const int bus = N.bus_of_pos[q];
+    int ln[kIncEll], op[kIncEll];
+    double cf[kIncEll], bl[kIncEll];
+#pragma unroll
+    for (int a = 0; a < kIncEll; ++a) {
+      ln[a] = N.qe_line[(size_t)a * N.nr + q];
+      op[a] = N.qe_opos[(size_t)a * N.nr + q];
+      cf[a] = N.qe_coef[(size_t)a * N.nr + q];
+      bl[a] = N.qe_b[(size_t)a * N.nr + q];
+    }
+    const int o0 = N.qo_ptr[q], o1 = N.qo_ptr[q + 1];
     const double zi = X[q];
     double r = 0.0, bz = 0.0, acc = 0.0;
     int deg = 0;
-    for (int p = N.bus_line_ptr[bus]; p < N.bus_line_ptr[bus + 1]; ++p) {
-      const int l = N.bus_line_idx[p];
-      if (l == k) continue;
-      const double eta = fmax((double)mh[l], 0.0) - fmax((double)ml[l], 0.0);
-      const int o = N.line_from[l] == bus ? N.line_to[l] : N.line_from[l];
-      const double zo = theta_at(N, X, o);
-      r += N.bus_line_coef[p] * eta;
-      bz += N.line_b[l] * (zi - zo);
-      acc += fabs(N.bus_line_coef[p] * eta) + N.line_b[l] * (fabs(zi) + fabs(zo));
+    // one incidence: the line, the other end's position, +-b_l and b_l
+    auto inc = [&](int l, int o, double c, double bv) {
+      const double eta = eta_of(l);
+      const double zo = o >= 0 ? X[o] : 0.0;
+      r += c * eta;
+      bz += bv * (zi - zo);
+      acc += fabs(c * eta) + bv * (fabs(zi) + fabs(zo));
       ++deg;
-    }
+    };
+#pragma unroll
+    for (int a = 0; a < kIncEll; ++a)
+      if (ln[a] >= 0 && ln[a] != k) inc(ln[a], op[a], cf[a], bl[a]);
+    for (int p = o0; p < o1; ++p)
+      if (N.qo_line[p] != k) inc(N.qo_line[p], N.qo_opos[p], N.qo_coef[p], N.qo_b[p]);
     rmax = fmax(rmax, fabs(r - bz) + (deg < kGamTab ? gam_tab[deg] : gamma_fp64(2.0 * deg + 6.0)) * acc);
   }
   rmax = block_max(rmax, red);
