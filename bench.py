@@ -65,16 +65,16 @@ C2 = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99, max_ite
 QP_ADAM = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997)
 LP_ADAM = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99)
 # DRAM bytes (read + write) per launch of the two products from ncu captures of the
-# 10000-bus batch of 256 with screening (the mean of two launches of each), one per CTA-pair tile code of the shapes (2, 3: single pairs of 256 x
-# 192 and 256 x 160; 5-8: clusters of two pairs, 256 x 256 .. 256 x 144), valid for the
-# product kernels' source with this digest; null for another source, another code or
-# single-CTA tiles.
-NCU_TRAFFIC = {"54de6319f7048f04": {2: {"adjoint": 112.3e6, "forward": 104.7e6},
-                          3: {"adjoint": 112.3e6, "forward": 104.6e6},
-                          5: {"adjoint": 112.2e6, "forward": 104.7e6},
-                          6: {"adjoint": 112.3e6, "forward": 104.6e6},
-                          7: {"adjoint": 112.5e6, "forward": 104.6e6},
-                          8: {"adjoint": 112.1e6, "forward": 104.6e6}}}
+# 10000-bus batch of 256 with screening (the mean of two launches of each), one per
+# CTA-pair tile code of the shapes (2, 3: single pairs of 256 x 192 and 256 x 160; 5-8:
+# clusters of two pairs, 256 x 256 .. 256 x 144), valid for the product kernels' source
+# with this digest; null for another source, another code or single-CTA tiles.
+NCU_TRAFFIC = {"99d8af509655c406": {2: {"adjoint": 111.8e6, "forward": 104.5e6},
+                          3: {"adjoint": 111.7e6, "forward": 104.6e6},
+                          5: {"adjoint": 111.7e6, "forward": 104.5e6},
+                          6: {"adjoint": 111.7e6, "forward": 104.5e6},
+                          7: {"adjoint": 111.8e6, "forward": 104.7e6},
+                          8: {"adjoint": 111.7e6, "forward": 104.6e6}}}
 
 
 def golden(name):
@@ -654,7 +654,7 @@ def reference_arm(a):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * el / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": bench_config(1), "cpu_baseline": cb,
+            "data": "synthetic", "config": bench_config(a.gpus), "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
