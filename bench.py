@@ -256,13 +256,13 @@ def _oracle_solve(i):
     return dcopf.solve(on, loads[i % BATCH], target=gam[i % BATCH], gap=GAP, **kw)["iters"]
 
 
-def oracle_pool(procs: int):
-    """A spawn-context pool of oracle processes with one BLAS thread each (spawned, not
-    forked: the parent may already hold a CUDA context)."""
+def oracle_pool(procs: int, blas_threads: int = 1):
+    """A spawn-context pool of oracle processes with `blas_threads` BLAS threads each
+    (spawned, not forked: the parent may already hold a CUDA context)."""
     import multiprocessing as mp
     keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     old = {k: os.environ.get(k) for k in keys}
-    os.environ.update({k: "1" for k in keys})
+    os.environ.update({k: str(blas_threads) for k in keys})
     try:
         return mp.get_context("spawn").Pool(procs, initializer=_oracle_init)
     finally:
@@ -287,18 +287,28 @@ def oracle_rounds(pool, procs, rounds=None, target_s=None, first=0):
             return n, el, iters
 
 
-def cpu_baseline(target_s=15.0):
+def cpu_baseline(target_s=15.0, latency_s=5.0):
     """The oracle (plain FP64 numpy/scipy) solving instances of the headline batch with
     the headline's ascent rule until its FP64 value is within 0.1 % of gamma*, on every
-    host core (one process per core, one BLAS thread each)."""
+    host core (throughput mode: one process per core, one BLAS thread each), and, for
+    `latency_s`, one solve at a time in one process with every core's BLAS thread
+    (latency mode)."""
     procs = os.cpu_count() or 1
     with oracle_pool(procs) as pool:
         pool.map(_oracle_solve, range(procs))          # warm-up: imports, factorisation
         n, el, iters = oracle_rounds(pool, procs, target_s=target_s, first=procs)
+    lat = None
+    if latency_s > 0:
+        with oracle_pool(1, blas_threads=procs) as pool:
+            pool.map(_oracle_solve, [0])               # warm-up
+            ln, lel, liters = oracle_rounds(pool, 1, target_s=latency_s, first=1)
+        lat = {"value": ln / lel, "unit": UNIT, "ms_per_solve": 1e3 * lel / ln,
+               "sample": f"{ln} solves one at a time ({lel:.1f} s, {statistics.mean(liters):.0f} "
+                         f"iterations each), one process with {procs} BLAS threads"}
     return {"value": n / el, "unit": UNIT, "cores": procs, "cpu": cpu_model(), "kind": "oracle",
             "sample": f"{n} complete solves of instances of the 10000-bus batch ({el:.1f} s, "
                       f"{statistics.mean(iters):.0f} iterations each, {procs} processes with one "
-                      f"BLAS thread each)"}
+                      f"BLAS thread each)", "latency_mode": lat}
 
 
 # ------------------------------------------------------------------ studies (own JSON)
@@ -821,7 +831,7 @@ def main():
         legs["group_mixed"] = group_leg(dev, max(2, a.steps // 10))
     if rank != 0:
         return
-    cb = cpu_baseline(a.cpu_seconds) if world == 1 else None
+    cb = cpu_baseline(a.cpu_seconds, max(1.0, a.cpu_seconds / 3)) if world == 1 else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
