@@ -763,6 +763,7 @@ def main():
         iters = r.iters.cpu().numpy()
         assert (st == 0).all()
     value, total_ms = aggregate(sum(times), BATCH * a.steps, world, dist, dev)
+    median_ms = statistics.median(times)
     iter_graph_ms = it_ms / a.steps   # of each step, in the iteration graphs (the rest: base
                                       # flows, screen, certificates, per-round read-backs)
 
@@ -836,6 +837,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
             "config": bench_config(world),
+            "median_ms_per_step": median_ms,
             "mean_iterations": float(iters.mean()), "most_iterations": int(iters.max()),
             "iteration_graph_ms_per_step": iter_graph_ms,
             "certified_gap_max": float(np.max((gam - bnd) / gam)),
