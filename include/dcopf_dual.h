@@ -385,8 +385,9 @@ dcopf_status dcopf_dual_screened_lines(dcopf_dual_t h, int32_t* n_kept, uint8_t*
  * on: CUDA events recorded inside the iteration graph around the kernels of the last
  * iteration of every round of the first instance group (the adjoint product, the
  * minimiser, the forward product, the step, and a fifth slot for the dual value and
- * stop tests, which run beside the next iteration's minimiser, so that it reads about
- * zero).  ms (host
+ * stop tests, which run beside the next iteration's minimiser, so that it reads only
+ * the events' own cost, about 2 us).  A round in which every instance was frozen
+ * launches no graph and adds no sample.  ms (host
  * [5], nullable) receives the summed milliseconds of each over the sampled iterations,
  * samples (host, nullable) their count; both are then reset.  Host only. */
 dcopf_status dcopf_dual_read_kernel_timing(dcopf_dual_t h, double* ms, int64_t* samples);
