@@ -225,7 +225,7 @@ def togap(cfg, repeat=2, screen=False, verbose=False):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if cfg == 2:   # the 4600-bus LP batch of 1024 (512 outages) and the bench's settings for it
         gam = json.load(open(os.path.join(root, "tests", "golden", "c2_gamma.json")))["gamma"]
-        kw = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99, max_iters=1500)
+        kw = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99, max_iters=1000)
     else:          # the 10000-bus QP batch of 256 and the bench's headline settings
         gam = json.load(open(os.path.join(root, "tests", "golden", "c3_gamma.json")))["gamma"]
         kw = dict(rule="adam", alpha=3000.0, beta1=0.95, beta2=0.999, decay=0.997, max_iters=4000)
