@@ -147,6 +147,36 @@ def test_certify_outage_matches_rebuilt(cases):
         assert 0 < err[b].item() and bound[b].item() <= ref + 1e-12 * abs(ref)
 
 
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_sparse_certificate_full_size_matches_oracle(cfg):
+    """The sparse certificate (level-scheduled LDL^T sweeps, batches above eight or with
+    outages) on the 4600-bus network with line outages and on the 10000-bus network,
+    twelve instances each: bound + err equals the oracle's FP64 price-form value of the
+    projected point (on the network rebuilt without an outaged line), err is small and
+    the bound is below the value."""
+    w = synth.workload(cfg, batch=12)
+    net = w.net
+    on = onet(net)
+    g = DcopfDual(net)
+    rng = np.random.default_rng(41 + cfg)
+    pts = [rand_point(rng, net.n_line, density=0.1) for _ in range(w.batch)]
+    lam = np.array([p[0] for p in pts])
+    mh = np.stack([p[1] for p in pts]) - 20.0   # some negative entries: projected by certify
+    ml = np.stack([p[2] for p in pts])
+    outage = w.outage if (w.outage >= 0).any() else None
+    bound, err = g.certify(w.loads, lam, mh, ml, outage=outage)
+    for b in range(w.batch):
+        k = int(outage[b]) if outage is not None else -1
+        keep = np.arange(net.n_line) != k
+        o = on if k < 0 else drop_line(net, k)
+        ref = dcopf.dual_value_prices(o, w.loads[b], lam[b], np.maximum(mh[b], 0)[keep],
+                                      np.maximum(ml[b], 0)[keep])
+        e = err[b].item()
+        assert 0 < e <= 1e-9 * (1 + abs(ref)), (b, e)
+        assert abs(bound[b].item() + e - ref) <= 1e-10 * abs(ref), (b, bound[b].item() + e, ref)
+        assert bound[b].item() <= ref + 1e-12 * abs(ref), b
+
+
 def test_eval_rejects_bad_outages(cases):
     from paper_2406_13191_gb300._lib import DcopfError
     net, base, on, g = cases["c0"]
