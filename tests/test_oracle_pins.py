@@ -425,3 +425,33 @@ def test_qp_dual_with_s_variable():
     assert r["iters"] < 5000
     assert gam * (1 - 1e-3) - 1e-9 * abs(gam) <= r["best_closed"] <= gam + 1e-9 * abs(gam)
     assert r["best"] <= r["best_closed"] + 1e-9 * abs(gam)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_outage_network_matches_lodf_identity(seed):
+    """The post-outage reference of the GPU outage tests (the network rebuilt without
+    line k) against the textbook line-outage distribution factor: for an injection y,
+    f'_l = f_l + LODF_lk f_k with LODF_lk = PTDF_l,(a->c) / (1 - PTDF_k,(a->c)), where
+    PTDF_.,(a->c) are the full network's flows of a unit transfer from line k's from-bus
+    a to its to-bus c.  Also: the two-bus closed form PTDF = 1 of a lone line."""
+    from gpu_common import drop_line
+    net, base = synth.network_for(0)
+    on = onet(net)
+    rng = np.random.default_rng(seed)
+    # non-bridge lines: removing one leaves the network connected (finite LODF)
+    for k in rng.permutation(net.n_line)[:6]:
+        a, c = int(net.line_from[k]), int(net.line_to[k])
+        t = np.zeros(net.n_bus)
+        t[a], t[c] = 1.0, -1.0
+        ptdf_t = on.flows(t)
+        if abs(1.0 - ptdf_t[k]) < 1e-9:
+            continue   # a bridge
+        y = base * rng.uniform(0.8, 1.2, net.n_bus)
+        y[on.slack] -= y.sum()                       # balanced injection
+        f = on.flows(y)
+        lodf = ptdf_t / (1.0 - ptdf_t[k])
+        expect = np.delete(f + lodf * f[k], k)
+        got = drop_line(net, int(k)).flows(y)
+        assert np.allclose(got, expect, rtol=1e-10, atol=1e-10 * np.max(np.abs(f)))
+    two = dcopf.Net(2, [0], [1], [5.0], [1.0], None, [0], [0.0], [1.0], [1.0], None, base_mva=1.0)
+    assert abs(two.flows(np.array([1.0, -1.0]))[0] - 1.0) <= 1e-15
