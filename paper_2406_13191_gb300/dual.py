@@ -78,6 +78,8 @@ class SolveResult:
                 return into
             host = self.flat.cpu()
             return SolveResult(*_packed_views(host, B, n), flat=host)
+        if into is not None:
+            raise ValueError("into= needs results that are views of one device buffer (new_result)")
         packed = torch.cat([self.bound, self.lam, self.iters.double(), self.status.double(),
                             self.mu_hi.reshape(-1), self.mu_lo.reshape(-1)]).cpu()
         o = 4 * B

@@ -126,3 +126,5 @@ def test_packed_host_results_equal_the_tensors(scales):
             assert a.shape == b.shape and a.dtype == b.dtype and torch.equal(a, b), f
     with pytest.raises(ValueError):
         r.to_host(into=g.new_host_result(len(scales) + 1))
+    with pytest.raises(ValueError):
+        loose.to_host(into=hp)
