@@ -48,7 +48,9 @@ static StepArgsF to_float_args(const StepArgs& P) {
 // One coordinate's step (Section 3.3) in FP32 with the instance's step factors of this
 // step: a = alpha decay^(t-1) (GDM, AdaGrad), and for Adam a1 = a / (1 - beta1^t) and
 // r2 = 1 / sqrt(1 - beta2^t), so that a (s1 / c1) / (sqrt(s2 / c2) + eps) is
-// a1 s1 / (sqrt(s2) r2 + eps) with one division.
+// a1 s1 / (sqrt(s2) r2 + eps) with one division.  The division is the fast one
+// (__fdividef, within two units in the last place for these operand ranges): the step
+// only steers the iteration, the bound is certified in FP64.
 __device__ __forceinline__ float step_rule(const StepArgsF& P, float theta, float g, float& s1,
                                            float& s2, float a, float a1, float r2) {
   if (P.rule == DCOPF_GDM) {
@@ -58,10 +60,10 @@ __device__ __forceinline__ float step_rule(const StepArgsF& P, float theta, floa
   } else if (P.rule == DCOPF_ADAM) {
     s1 = P.beta1 * s1 + P.omb1 * g;
     s2 = P.beta2 * s2 + P.omb2 * g * g;
-    theta += a1 * s1 / fmaf(sqrtf(s2), r2, P.eps);
+    theta += __fdividef(a1 * s1, fmaf(sqrtf(s2), r2, P.eps));
   } else {
     s1 += g * g;
-    theta += a * g / (sqrtf(s1) + P.eps);
+    theta += __fdividef(a * g, sqrtf(s1) + P.eps);
   }
   return theta;
 }
