@@ -60,7 +60,7 @@ FUSED = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.999, decay=0.997, ma
              path="fused", precision="fp32")
 # the 4600-bus LP leg: with the step decay 0.99 per iteration the step is 4e-5 of alpha
 # after 1000 iterations; every instance of this batch that reaches the gap within 1500
-# iterations does so within 856, and the three that do not reach it by 1500 either, so
+# iterations does so within 900, and the three that do not reach it by 1500 either, so
 # the cap is 1000
 C2 = dict(rule="adam", alpha=4000.0, beta1=0.95, beta2=0.99, decay=0.99, max_iters=1000,
           path="batched", precision="bf16x3")
